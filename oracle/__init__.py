@@ -1,0 +1,207 @@
+"""FP64 CPU oracle for the variable-coefficient pressure Poisson solve.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package; the GPU library never does, and the two share no code.
+
+The arithmetic lives in ``poisson_oracle.c`` (plain C loops, FP64, optional OpenMP), compiled on
+first use into ``oracle/_build/liboracle.so``; this module is the numpy-facing wrapper.  Every
+array is float64, shape ``(nz, ny, nx)``, C order (x fastest).
+
+What it computes (Formulation, eqs. (density) and (pois); Introduction on the preconditioned
+conjugate-gradient solve of the second-order, variable-coefficient Poisson equation):
+``rho = rho_air + F (rho_water - rho_air)``; face coefficients are the harmonic means
+``2 / (rho_c + rho_n)`` of ``1/rho``; Neumann walls on x, y and the bottom; Dirichlet ``p = 0`` on
+the top face.  ``A = -h^2 div_h(beta grad_h)`` is SPD and ``A p = -h^2 s`` is solved by PCG with a
+Jacobi or red-black SSOR preconditioner.
+
+Parity pins: every function here is pinned by ``tests/test_oracle_pins.py`` against closed forms,
+library dense solves, series-resistance layered solutions and second-order convergence.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "poisson_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN = 0, -1, -2, -3, -4
+JACOBI, SSOR = 0, 1
+MEAN_HARMONIC, MEAN_ARITHMETIC = 0, 1
+_PRECOND = {"jacobi": JACOBI, "ssor": SSOR, "rbssor": SSOR}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force=False):
+    """Compile ``poisson_oracle.c`` with gcc (OpenMP if available, no FP contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and \
+            os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.POINTER(ctypes.c_double)
+        i, d = ctypes.c_int, ctypes.c_double
+        lib.oracle_faces.argtypes = [i, i, i, P, d, d, i, P, P, P, P]
+        lib.oracle_faces.restype = i
+        lib.oracle_apply.argtypes = [i, i, i, P, P, P, P, P, P]
+        lib.oracle_apply.restype = None
+        lib.oracle_precond.argtypes = [i, i, i, P, P, P, P, i, d, P, P]
+        lib.oracle_precond.restype = None
+        lib.oracle_residual.argtypes = [i, i, i, P, P, P, P, P, P, P]
+        lib.oracle_residual.restype = d
+        lib.oracle_pcg.argtypes = [i, i, i, P, P, P, P, P, P, d, i, d, i,
+                                   ctypes.POINTER(ctypes.c_int), P, P]
+        lib.oracle_pcg.restype = i
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = i
+        lib.oracle_set_threads.argtypes = [i]
+        lib.oracle_set_threads.restype = None
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def threads():
+    """OpenMP threads the oracle uses."""
+    return int(_load().oracle_threads())
+
+
+def set_threads(n):
+    _load().oracle_set_threads(int(n))
+
+
+@dataclasses.dataclass
+class Operator:
+    """The FP64 operator ``A = -h^2 div_h(beta grad_h)``: low-side face arrays and diagonal."""
+    nx: int
+    ny: int
+    nz: int
+    bx: np.ndarray
+    by: np.ndarray
+    bz: np.ndarray
+    diag: np.ndarray
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def args(self):
+        return (self.nx, self.ny, self.nz, _ptr(self.bx), _ptr(self.by), _ptr(self.bz),
+                _ptr(self.diag))
+
+
+def operator(F, rho_air=1.0, rho_water=1000.0, mean="harmonic"):
+    """Assemble the operator from the water fraction ``F`` (shape ``(nz, ny, nx)``)."""
+    F = _f64(F)
+    nz, ny, nx = F.shape
+    bx, by, bz, dg = (np.empty_like(F) for _ in range(4))
+    m = MEAN_HARMONIC if mean == "harmonic" else MEAN_ARITHMETIC
+    rc = _load().oracle_faces(nx, ny, nz, _ptr(F), float(rho_air), float(rho_water), m,
+                              _ptr(bx), _ptr(by), _ptr(bz), _ptr(dg))
+    if rc != OK:
+        raise RuntimeError("oracle_faces failed: %d" % rc)
+    return Operator(nx, ny, nz, bx, by, bz, dg)
+
+
+def apply(op: Operator, x):
+    """``y = A x``."""
+    x = _f64(x).reshape(op.shape)
+    y = np.empty_like(x)
+    _load().oracle_apply(*op.args, _ptr(x), _ptr(y))
+    return y
+
+
+def precond(op: Operator, r, kind="jacobi", omega=1.0):
+    """``z = M^{-1} r`` for the Jacobi or red-black SSOR(omega) preconditioner."""
+    r = _f64(r).reshape(op.shape)
+    z = np.empty_like(r)
+    _load().oracle_precond(*op.args, _PRECOND[kind], float(omega), _ptr(r), _ptr(z))
+    return z
+
+
+def residual(op: Operator, b, x):
+    """``(r, ||r||_2)`` with ``r = b - A x``."""
+    b = _f64(b).reshape(op.shape)
+    x = _f64(x).reshape(op.shape)
+    r = np.empty_like(b)
+    nrm = _load().oracle_residual(*op.args, _ptr(b), _ptr(x), _ptr(r))
+    return r, float(nrm)
+
+
+def rel_residual(op: Operator, b, x):
+    """``||b - A x||_2 / ||b||_2`` in FP64."""
+    b = _f64(b)
+    _, nrm = residual(op, b, x)
+    bn = float(np.linalg.norm(b.ravel()))
+    return 0.0 if bn == 0.0 else nrm / bn
+
+
+@dataclasses.dataclass
+class PCGResult:
+    x: np.ndarray
+    iters: int
+    rel_residual: float
+    status: int
+    history: np.ndarray | None = None
+
+
+def pcg(op: Operator, b, x0=None, tol=1e-12, precond="jacobi", omega=1.0, max_iters=100000,
+        history=False):
+    """Preconditioned conjugate gradients on ``A x = b``.  ``tol <= 0`` runs exactly
+    ``max_iters`` iterations."""
+    b = _f64(b).reshape(op.shape)
+    x = np.zeros_like(b) if x0 is None else _f64(x0).reshape(op.shape).copy()
+    it = ctypes.c_int(0)
+    rr = ctypes.c_double(0.0)
+    hist = np.zeros(max(max_iters, 1)) if history else None
+    st = _load().oracle_pcg(*op.args, _ptr(b), _ptr(x), float(tol), _PRECOND[precond],
+                            float(omega), int(max_iters), ctypes.byref(it), ctypes.byref(rr),
+                            _ptr(hist) if history else None)
+    return PCGResult(x, it.value, rr.value, st, hist[:it.value] if history else None)
+
+
+def rhs(s, h):
+    """``b = -h^2 s``: the right side of ``A p = b`` for ``div((1/rho) grad p) = s``."""
+    return -(h * h) * _f64(s)
+
+
+def solve(F, s, h, tol=1e-12, precond="jacobi", omega=1.0, x0=None, rho_air=1.0,
+          rho_water=1000.0, max_iters=100000):
+    """Solve ``div((1/rho(F)) grad p) = s`` to relative residual ``tol``; returns
+    ``(PCGResult, Operator)``."""
+    op = operator(F, rho_air, rho_water)
+    res = pcg(op, rhs(s, h), x0=x0, tol=tol, precond=precond, omega=omega, max_iters=max_iters)
+    return res, op

@@ -1,0 +1,299 @@
+/*
+ * poisson_oracle.c -- plain FP64 CPU oracle for the pressure Poisson solve.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the benchmark's CPU-baseline leg
+ * may load this code.  It shares nothing with the CUDA library: it is written from the paper's
+ * statement of the problem, as plain loops, for a reader to check by eye.
+ *
+ * What it computes (Formulation, eqs. (density) and (pois); Introduction: "second-order,
+ * variable-coefficient Poisson equation ... preconditioned conjugate-gradient method"):
+ *
+ *   rho_c  = rho_air + F_c (rho_water - rho_air)                 density from the water fraction
+ *   beta_f = 2 / (rho_c + rho_n)                                 face coefficient: harmonic mean
+ *                                                                of 1/rho_c and 1/rho_n
+ *   walls x = 0, Lx, y = 0, Ly, z = 0: beta_f = 0                (zero normal gradient)
+ *   top   z = Lz: p = 0 on the face; ghost value -p_c, so the face contributes 2 (1/rho_c) p_c
+ *
+ *   (A p)_c = D_c p_c - sum_{faces f of c} beta_f p_{n(f)},    D_c = sum_f beta_f + 2/rho_c [top]
+ *
+ * A = -h^2 L with L p = div_h(beta grad_h p); A is symmetric positive definite.  The solve of
+ * div((1/rho) grad p) = s is A p = b with b = -h^2 s.
+ *
+ * Array layout: x fastest, linear index c = i + nx (j + ny k).  The face arrays hold the face on
+ * the LOW side of each cell: bx[c] couples (i-1, j, k) and (i, j, k) and is 0 for i = 0; by[c]
+ * and bz[c] likewise.  The high face of cell c is the low face of its +x/+y/+z neighbour (0 at
+ * the last cell except the top, whose Dirichlet term lives in D).
+ *
+ * Preconditioners (the paper names none; Jacobi and red-black SSOR are the two readings used):
+ *   Jacobi:  z = D^{-1} r.
+ *   SSOR(w): with A = D - E - E^T in red-black order (red = (i+j+k) even, first),
+ *            M = (D - wE) D^{-1} (D - wE^T) / (w (2 - w)); z = M^{-1} r is
+ *              y_R = r_R / D_R
+ *              y_B = (r_B + w sum_{red nbrs} beta y) / D_B
+ *              t_R = y_R + w (sum_{black nbrs} beta y) / D_R        (t_B = y_B)
+ *              z   = w (2 - w) t.
+ *
+ * PCG (textbook preconditioned conjugate gradients): r = b - A x; z = M^{-1} r; p = z; loop
+ * { q = A p; alpha = (r.z)/(p.q); x += alpha p; r -= alpha q; stop when ||r||/||b|| <= tol and the
+ * recomputed residual b - A x confirms it; z = M^{-1} r; beta = (r.z)_new/(r.z)_old; p = z + beta p }.
+ * Floating-point contraction is disabled at build time so results do not depend on the host ISA.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_EINVAL -1
+#define OR_ENOMEM -2
+#define OR_ENOTCONV -3
+#define OR_EBREAKDOWN -4
+
+#define OR_JACOBI 0
+#define OR_SSOR 1
+
+#define OR_MEAN_HARMONIC 0   /* beta_f = 2/(rho_c + rho_n): harmonic mean of 1/rho */
+#define OR_MEAN_ARITHMETIC 1 /* beta_f = (1/rho_c + 1/rho_n)/2: rejected reading, kept for tests */
+
+typedef int64_t idx_t;
+
+int oracle_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* ---------------------------------------------------------------------------- operator setup */
+int oracle_faces(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
+                 int mean, double* bx, double* by, double* bz, double* diag) {
+    if (nx <= 0 || ny <= 0 || nz <= 0 || !F || !bx || !by || !bz || !diag) return OR_EINVAL;
+    const idx_t n = (idx_t)nx * ny * nz;
+    double* rho = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!rho) return OR_ENOMEM;
+    for (idx_t c = 0; c < n; ++c) rho[c] = rho_air + F[c] * (rho_water - rho_air);
+
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
+                double rc = rho[c];
+                double fx = 0.0, fy = 0.0, fz = 0.0;
+                if (i > 0) {
+                    double rn = rho[c - 1];
+                    fx = (mean == OR_MEAN_HARMONIC) ? 2.0 / (rc + rn) : 0.5 * (1.0 / rc + 1.0 / rn);
+                }
+                if (j > 0) {
+                    double rn = rho[c - nx];
+                    fy = (mean == OR_MEAN_HARMONIC) ? 2.0 / (rc + rn) : 0.5 * (1.0 / rc + 1.0 / rn);
+                }
+                if (k > 0) {
+                    double rn = rho[c - (idx_t)nx * ny];
+                    fz = (mean == OR_MEAN_HARMONIC) ? 2.0 / (rc + rn) : 0.5 * (1.0 / rc + 1.0 / rn);
+                }
+                bx[c] = fx;
+                by[c] = fy;
+                bz[c] = fz;
+            }
+
+    /* diagonal: the six faces of the cell plus the Dirichlet top term */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
+                double d = bx[c] + by[c] + bz[c];
+                if (i + 1 < nx) d += bx[c + 1];
+                if (j + 1 < ny) d += by[c + nx];
+                if (k + 1 < nz) d += bz[c + (idx_t)nx * ny];
+                else d += 2.0 / rho[c];
+                diag[c] = d;
+            }
+    free(rho);
+    return OR_OK;
+}
+
+/* ---------------------------------------------------------------------------- y = A x */
+void oracle_apply(int nx, int ny, int nz, const double* bx, const double* by, const double* bz,
+                  const double* diag, const double* x, double* y) {
+    const idx_t sx = 1, sy = nx, sz = (idx_t)nx * ny;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
+                double v = diag[c] * x[c];
+                if (i > 0) v -= bx[c] * x[c - sx];
+                if (i + 1 < nx) v -= bx[c + sx] * x[c + sx];
+                if (j > 0) v -= by[c] * x[c - sy];
+                if (j + 1 < ny) v -= by[c + sy] * x[c + sy];
+                if (k > 0) v -= bz[c] * x[c - sz];
+                if (k + 1 < nz) v -= bz[c + sz] * x[c + sz];
+                y[c] = v;
+            }
+}
+
+/* Sum over the six neighbours of c of beta_f * v_n.  Every neighbour of a red cell is black and
+ * vice versa, so for a black cell this reads red entries only (and the converse). */
+static double nb_sum(int nx, int ny, int nz, const double* bx, const double* by, const double* bz,
+                     const double* v, int i, int j, int k) {
+    const idx_t sx = 1, sy = nx, sz = (idx_t)nx * ny;
+    idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
+    double s = 0.0;
+    if (i > 0) s += bx[c] * v[c - sx];
+    if (i + 1 < nx) s += bx[c + sx] * v[c + sx];
+    if (j > 0) s += by[c] * v[c - sy];
+    if (j + 1 < ny) s += by[c + sy] * v[c + sy];
+    if (k > 0) s += bz[c] * v[c - sz];
+    if (k + 1 < nz) s += bz[c + sz] * v[c + sz];
+    return s;
+}
+
+/* ---------------------------------------------------------------------------- z = M^{-1} r */
+void oracle_precond(int nx, int ny, int nz, const double* bx, const double* by, const double* bz,
+                    const double* diag, int kind, double omega, const double* r, double* z) {
+    const idx_t n = (idx_t)nx * ny * nz;
+    if (kind == OR_JACOBI) {
+#pragma omp parallel for schedule(static)
+        for (idx_t c = 0; c < n; ++c) z[c] = r[c] / diag[c];
+        return;
+    }
+    /* red-black SSOR: forward sweep (red then black), backward sweep (red), scale */
+    const double w = omega;
+    /* y_R = r_R / D_R ; z holds y, black entries are written next */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
+                if (((i + j + k) & 1) == 0) z[c] = r[c] / diag[c];
+            }
+    /* y_B = (r_B + w sum_red beta y) / D_B */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
+                if (((i + j + k) & 1) == 1)
+                    z[c] = (r[c] + w * nb_sum(nx, ny, nz, bx, by, bz, z, i, j, k)) / diag[c];
+            }
+    /* t_R = y_R + w (sum_black beta y) / D_R */
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
+                if (((i + j + k) & 1) == 0)
+                    z[c] = z[c] + w * nb_sum(nx, ny, nz, bx, by, bz, z, i, j, k) / diag[c];
+            }
+    const double scale = w * (2.0 - w);
+#pragma omp parallel for schedule(static)
+    for (idx_t c = 0; c < n; ++c) z[c] *= scale;
+}
+
+/* ---------------------------------------------------------------------------- vector helpers */
+static double dot(idx_t n, const double* a, const double* b) {
+    double s = 0.0;
+#pragma omp parallel for reduction(+ : s) schedule(static)
+    for (idx_t c = 0; c < n; ++c) s += a[c] * b[c];
+    return s;
+}
+
+/* r = b - A x; returns ||r||_2 */
+double oracle_residual(int nx, int ny, int nz, const double* bx, const double* by,
+                       const double* bz, const double* diag, const double* b, const double* x,
+                       double* r) {
+    const idx_t n = (idx_t)nx * ny * nz;
+    oracle_apply(nx, ny, nz, bx, by, bz, diag, x, r);
+#pragma omp parallel for schedule(static)
+    for (idx_t c = 0; c < n; ++c) r[c] = b[c] - r[c];
+    return sqrt(dot(n, r, r));
+}
+
+double oracle_norm2(idx_t n, const double* v) { return sqrt(dot(n, v, v)); }
+
+/* ---------------------------------------------------------------------------- PCG
+ * x: in = initial guess, out = solution.  On return iters = PCG iterations taken and
+ * relres = ||b - A x||_2 / ||b||_2 recomputed from x.  tol <= 0 runs exactly max_iters
+ * iterations (used to time a fixed window).  history (may be NULL) receives the recurrence
+ * residual norm ||r||/||b|| after every iteration, up to max_iters entries. */
+int oracle_pcg(int nx, int ny, int nz, const double* bx, const double* by, const double* bz,
+               const double* diag, const double* b, double* x, double tol, int kind, double omega,
+               int max_iters, int* iters_out, double* relres_out, double* history) {
+    if (nx <= 0 || ny <= 0 || nz <= 0 || !b || !x || max_iters < 0) return OR_EINVAL;
+    const idx_t n = (idx_t)nx * ny * nz;
+    double* r = (double*)malloc(sizeof(double) * (size_t)n);
+    double* z = (double*)malloc(sizeof(double) * (size_t)n);
+    double* p = (double*)malloc(sizeof(double) * (size_t)n);
+    double* q = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!r || !z || !p || !q) {
+        free(r); free(z); free(p); free(q);
+        return OR_ENOMEM;
+    }
+    int status = OR_ENOTCONV;
+    int it = 0;
+    const double bnorm = oracle_norm2(n, b);
+    if (bnorm == 0.0) {
+        memset(x, 0, sizeof(double) * (size_t)n);
+        if (iters_out) *iters_out = 0;
+        if (relres_out) *relres_out = 0.0;
+        free(r); free(z); free(p); free(q);
+        return OR_OK;
+    }
+
+    double rnorm = oracle_residual(nx, ny, nz, bx, by, bz, diag, b, x, r);
+    if (tol > 0.0 && rnorm / bnorm <= tol) { status = OR_OK; goto done; }
+    oracle_precond(nx, ny, nz, bx, by, bz, diag, kind, omega, r, z);
+    memcpy(p, z, sizeof(double) * (size_t)n);
+    double rz = dot(n, r, z);
+
+    while (it < max_iters) {
+        oracle_apply(nx, ny, nz, bx, by, bz, diag, p, q);
+        const double pq = dot(n, p, q);
+        if (!(pq > 0.0) || !isfinite(pq)) { status = OR_EBREAKDOWN; break; }
+        const double alpha = rz / pq;
+#pragma omp parallel for schedule(static)
+        for (idx_t c = 0; c < n; ++c) {
+            x[c] += alpha * p[c];
+            r[c] -= alpha * q[c];
+        }
+        ++it;
+        rnorm = oracle_norm2(n, r);
+        if (history) history[it - 1] = rnorm / bnorm;
+        if (tol > 0.0 && rnorm / bnorm <= tol) {
+            /* confirm with the recomputed residual; if the recurrence drifted, restart from it */
+            rnorm = oracle_residual(nx, ny, nz, bx, by, bz, diag, b, x, r);
+            if (rnorm / bnorm <= tol) { status = OR_OK; break; }
+            oracle_precond(nx, ny, nz, bx, by, bz, diag, kind, omega, r, z);
+            memcpy(p, z, sizeof(double) * (size_t)n);
+            rz = dot(n, r, z);
+            continue;
+        }
+        oracle_precond(nx, ny, nz, bx, by, bz, diag, kind, omega, r, z);
+        const double rz_new = dot(n, r, z);
+        const double beta = rz_new / rz;
+        rz = rz_new;
+#pragma omp parallel for schedule(static)
+        for (idx_t c = 0; c < n; ++c) p[c] = z[c] + beta * p[c];
+    }
+done:
+    rnorm = oracle_residual(nx, ny, nz, bx, by, bz, diag, b, x, r);
+    if (iters_out) *iters_out = it;
+    if (relres_out) *relres_out = rnorm / bnorm;
+    if (status == OR_ENOTCONV && tol <= 0.0) status = OR_OK;
+    free(r); free(z); free(p); free(q);
+    return status;
+}
