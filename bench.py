@@ -1,0 +1,383 @@
+"""Benchmark of the pressure Poisson solve on one or more GB300s.
+
+One step = one pass of the whole solve path over one synthetic input: set the density from the
+water fraction (operator set-up) and solve div((1/rho) grad p) = s to relative residual 1e-9 from
+a zero start (FP32 inner PCG inside FP64 refinement by default).  The workload is the
+surface-piercing elliptic strut on a 256 x 128 x 128 grid (4,194,304 cells, density ratio 1000).
+
+value  = cells x CG iterations / device seconds, summed over ranks (Gcell-iters/s), inputs
+         resident in HBM, L2 flushed between steps.
+e2e    = the same metric through the C ABI with pinned HOST arrays: the H2D copy of F, s and the
+         start p and the D2H copy of the solution are inside the timed region.
+roofline: the dominant CG kernel's algorithmic bytes per launch / its mean CUDA-event duration.
+cpu_baseline: the FP64 CPU oracle timed on this host on a bounded sample of the same workload.
+
+--impl reference times the oracle instead (the reference arm: a plain CPU program).
+Multi-GPU (torchrun): independent replicas, one solve per rank per step (weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+CELLS_NOTE = "strut 256x128x128"
+WORKLOAD = ("surface-piercing elliptic strut (0.1 x 0.02, water density) in a Kelvin-like "
+            "two-phase surface, 256x128x128 cells, h = 1/128, rho 1/1000, source div(u*)/dt of "
+            "8 random modes; tol 1e-9 rel. residual, zero start")
+# Algorithmic bytes per cell of one launch of each CG pass (FP32 vectors; rho/2 per cell as the
+# coefficient array, FP32 = 4 B, BF16 = 2 B; neighbour re-reads served on chip, not counted):
+#   phase A: read z, p_old, eta; write p                     = 3 vec + eta + 1 vec
+#   phase B: read x, r, p, eta; write x, r, z                = 6 vec + eta
+BYTES_PER_CELL = {
+    "fp32": {"cg_phase_a": 4 * 3 + 4, "cg_phase_b": 4 * 6 + 4},
+    "bf16": {"cg_phase_a": 4 * 3 + 2, "cg_phase_b": 4 * 6 + 2},
+    # FP64 PCG: vectors 8 B, stored FP64 faces bx, by, bz + diag (+ dinv in phase B)
+    "fp64": {"cg_phase_a": 8 * 3 + 8 * 4, "cg_phase_b": 8 * 6 + 8 * 5},
+}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "rbssor"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1410_1942_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, precision):
+    """DRAM bytes per launch for `kernel` from the committed ncu summary, if it was taken on the
+    current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get("%s/%s" % (precision, kernel))
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("bytes_per_launch_full")
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.strip()]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 8:
+                continue
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[4:8]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle (plain FP64 CPU PCG) timed on this host's cores, same workload and metric."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1410_1942_gb300 import inputs
+    oracle.build()
+    c = inputs.strut_case(256, 128, 128, seed=args.seed)
+    op = oracle.operator(c.F)
+    b = oracle.rhs(c.s, c.grid.h)
+    iters_per_step = 20
+    precond = "ssor" if args.precond == "rbssor" else "jacobi"
+    x = np.zeros(c.grid.shape)
+    for _ in range(args.warmup):
+        oracle.pcg(op, b, x0=x, tol=0.0, precond=precond, max_iters=iters_per_step)
+    t0 = time.perf_counter()
+    its = 0
+    for _ in range(args.steps):
+        r = oracle.pcg(op, b, x0=x, tol=0.0, precond=precond, max_iters=iters_per_step)
+        its += r.iters
+    dt = time.perf_counter() - t0
+    val = c.grid.n * its / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "Poisson PCG Gcell-iters/s", "value": val,
+        "unit": "Gcell-iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precond": precond},
+        "cpu_baseline": {"value": val, "unit": "Gcell-iters/s", "cores": oracle.threads(),
+                         "kind": "oracle",
+                         "sample": "%d FP64 %s-PCG iterations per step of the CPU oracle on the "
+                                   "%s workload" % (iters_per_step, precond, CELLS_NOTE)},
+        "e2e": {"value": val, "unit": "Gcell-iters/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(case, seconds, precond):
+    """The oracle as it stands on this host's cores: fixed 20-iteration PCG windows of the same
+    workload until `seconds` of CPU work have run."""
+    import oracle
+    oracle.build()
+    op = oracle.operator(case.F)
+    b = oracle.rhs(case.s, case.grid.h)
+    x = np.zeros(case.grid.shape)
+    its, t0 = 0, time.perf_counter()
+    while True:
+        r = oracle.pcg(op, b, x0=x, tol=0.0, precond=precond, max_iters=20)
+        its += r.iters
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": case.grid.n * its / dt / 1e9, "unit": "Gcell-iters/s",
+            "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d FP64 %s-PCG iterations (windows of 20) of the CPU oracle on the %s "
+                      "workload, %.1f s" % (its, precond, CELLS_NOTE, dt)}
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as tdist
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1410_1942_gb300 import build as _build
+    from paper_1410_1942_gb300 import capi, inputs
+    _build.build()
+    capi.load()
+
+    case = inputs.strut_case(256, 128, 128, seed=args.seed + rank)
+    g = case.grid
+    F_d = torch.from_numpy(case.F).to(dev)
+    s_d = torch.from_numpy(case.s).to(dev)
+    p_d = torch.zeros(g.shape, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision, precond=args.precond,
+                          stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def step():
+        solver.set_density(F_d)
+        p_d.zero_()
+        rc, st = solver.solve(s_d, p_d, case.tol)
+        if rc != capi.OK:
+            raise RuntimeError("solve failed: %s" % capi.strerror(rc))
+        return st
+
+    for _ in range(args.warmup):
+        step()
+    solver.profile(True)
+    clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    iters, outer, rels = 0, 0, []
+    barrier()
+    if clocks:
+        clocks.start()
+    l0 = capi.kernel_launches()
+    for q in range(args.steps):
+        flush.fill_(q & 0xFF)
+        evs[q][0].record(stream)
+        st = step()
+        evs[q][1].record(stream)
+        iters += st["inner_iters"]
+        outer += st["outer_iters"]
+        rels.append(st["rel_residual"])
+    barrier()
+    launches = capi.kernel_launches() - l0
+    clk = clocks.stop() if clocks else None
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    prof = solver.profile_read()
+    solver.profile(False)
+    units = float(g.n) * iters                     # cell-iterations of this rank
+    t_max = dev_ms
+    if world > 1:
+        tt = torch.tensor([dev_ms, units], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.SUM)
+        t_max, units = float(mx[0]), float(tt[1])
+    value = units / (t_max * 1e-3) / 1e9
+
+    # dominant CG kernel and its roofline
+    bpc = BYTES_PER_CELL[args.precision]
+    dom = max(("cg_phase_a", "cg_phase_b"), key=lambda k: prof[k]["ms"])
+    per_launch_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
+    alg_bytes = bpc[dom] * g.n
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = ncu_traffic(dom, args.precision)
+    hbm_alg = value * (bpc["cg_phase_a"] + bpc["cg_phase_b"])  # GB/s of CG-pass algorithmic traffic
+
+    # end to end through the C ABI with pinned host arrays
+    e2e = None
+    if not args.no_e2e:
+        F_h = torch.from_numpy(case.F).pin_memory()
+        s_h = torch.from_numpy(case.s).pin_memory()
+        p_h = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+        solver_h = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision,
+                                precond=args.precond, stream=stream.cuda_stream)
+
+        def step_e2e():
+            p_h.zero_()
+            solver_h.set_density(F_h)
+            rc, st = solver_h.solve(s_h, p_h, case.tol)
+            if rc != capi.OK:
+                raise RuntimeError("e2e solve failed: %s" % capi.strerror(rc))
+            return st
+
+        for _ in range(min(2, args.warmup)):
+            step_e2e()
+        barrier()
+        its_e, t0 = 0, time.perf_counter()
+        for _ in range(args.steps):
+            its_e += step_e2e()["inner_iters"]
+        barrier()
+        te = time.perf_counter() - t0
+        ue = float(g.n) * its_e
+        if world > 1:
+            tt = torch.tensor([te, ue], dtype=torch.float64, device=dev)
+            mx = tt.clone()
+            tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+            tdist.all_reduce(tt, op=tdist.ReduceOp.SUM)
+            te, ue = float(mx[0]), float(tt[1])
+        e2e = {"value": ue / te / 1e9, "unit": "Gcell-iters/s",
+               "h2d_bytes_per_step": 3 * 8 * g.n, "d2h_bytes_per_step": 8 * g.n,
+               "ms_per_step": 1e3 * te / args.steps}
+        solver_h.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(case, args.cpu_seconds, "ssor" if args.precond == "rbssor" else "jacobi")
+
+    if rank == 0:
+        line = {
+            "metric": "Poisson PCG Gcell-iters/s", "value": value, "unit": "Gcell-iters/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cells": g.n, "precision": args.precision,
+                       "precond": args.precond, "tol": case.tol,
+                       "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "cg_iters_per_step": iters / args.steps,
+                       "outer_iters_per_step": outer / args.steps,
+                       "max_rel_residual": max(rels)},
+            "hbm_gbs_algorithmic": hbm_alg,
+            "solves_per_s": world * args.steps / (t_max * 1e-3),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                         "ms_per_launch": per_launch_ms},
+            "kernel_times": prof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        tdist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

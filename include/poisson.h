@@ -1,0 +1,171 @@
+/*
+ * poisson.h -- C ABI of libpoisson, a GB300 (sm_103a) solver for the variable-coefficient pressure
+ * Poisson equation of a Cartesian-grid two-phase ship-wave method.
+ *
+ * The equation (Formulation, eq. (pois); the two stage solves of Numerical Time Integration) is
+ *
+ *     div( (1/rho) grad p ) = s,        s = div(u*) / dt,
+ *
+ * on a uniform grid of nx x ny x nz cells of spacing h, cell-centred p, with
+ *   rho = rho_air + F (rho_water - rho_air)        (eq. (density); F = water fraction of the cell)
+ *   face coefficient = 2 / (rho_c + rho_n)          (harmonic mean of 1/rho over the two cells)
+ *   zero normal gradient on the walls x = 0, x = nx h, y = 0, y = ny h, z = 0;
+ *   p = 0 on the top face z = nz h (second order: ghost value -p_c).
+ * The Introduction states that this second-order variable-coefficient Poisson equation is solved by
+ * preconditioned conjugate gradients; the preconditioner is Jacobi or red-black SSOR.
+ *
+ * Conventions for every call:
+ *   - 3-D arrays are float64, nx*ny*nz elements, x fastest: element (i, j, k) at i + nx*(j + ny*k).
+ *   - A pointer argument may be host memory or device memory of the current CUDA device; the
+ *     library tells them apart with cudaPointerGetAttributes (pageable, pinned and device memory
+ *     are all accepted).  The caller owns every array it passes; the library never frees them.
+ *   - Device pointers are read or written on the handle's stream (poisson_opts.stream); calls that
+ *     return results on the host synchronise that stream before returning.
+ *   - Every call returns POISSON_OK (0) or a negative status; poisson_strerror names it.
+ *   - A handle is not thread-safe: do not call into one handle from two threads at once.
+ */
+#ifndef POISSON_H
+#define POISSON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define POISSON_OK 0
+#define POISSON_PENDING 1            /* poisson_poll: solve still running */
+#define POISSON_EINVAL (-1)          /* bad argument: size <= 0, h <= 0, tol <= 0, NULL, ...  */
+#define POISSON_ENOMEM (-2)          /* device or host allocation failed */
+#define POISSON_ENOTCONV (-3)        /* iteration cap reached; p holds the best iterate */
+#define POISSON_EBREAKDOWN (-4)      /* CG breakdown: p.Ap <= 0 or a non-finite scalar */
+#define POISSON_ETIMEOUT (-5)        /* a device-side wait exceeded its deadline */
+#define POISSON_ENOTREADY (-6)       /* solve before set_density */
+#define POISSON_ECUDA (-7)           /* a CUDA runtime call failed */
+#define POISSON_ENOMEM_BUDGET (-8)   /* admission refused: over the device-memory budget */
+#define POISSON_ENOTICKET (-9)       /* poisson_poll: unknown or already collected ticket */
+
+/* ------------------------------------------------------------------ options */
+#define POISSON_FP64 0           /* plain FP64 PCG on the GPU */
+#define POISSON_FP32 1           /* FP32 inner PCG inside FP64 iterative refinement */
+#define POISSON_FP32_BF16COEF 2  /* as POISSON_FP32, inner densities stored as bfloat16 */
+
+#define POISSON_JACOBI 0
+#define POISSON_RBSSOR 1
+
+#define POISSON_MEM_HOST 0
+#define POISSON_MEM_DEVICE 1
+
+typedef struct poisson_s poisson_t; /* opaque; the library owns all device state of a handle */
+
+typedef struct {
+    int precision;     /* POISSON_FP64 | POISSON_FP32 | POISSON_FP32_BF16COEF (default FP32)     */
+    int precond;       /* POISSON_JACOBI | POISSON_RBSSOR (default JACOBI)                        */
+    double omega;      /* SSOR relaxation factor in (0, 2) (default 1.0)                           */
+    int max_iters;     /* cap on total CG iterations of one solve (default 20000)                  */
+    double inner_tol;  /* FP32 inner solve: relative residual reduction per refinement step
+                          (default 1e-4; ignored by POISSON_FP64)                                  */
+    int tile;          /* stencil tile variant; 0 = the library's choice (autotuned per shape)     */
+    void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream                 */
+} poisson_opts;
+
+typedef struct {
+    int outer_iters;      /* FP64 refinement steps (1 for POISSON_FP64)                           */
+    int inner_iters;      /* CG iterations in total                                                */
+    double rel_residual;  /* ||b - A p||_2 / ||b||_2 of the returned p, in FP64 on the device      */
+    double seconds;       /* wall time of the call                                                 */
+} poisson_stats;
+
+/* Fill *opts with the defaults above. */
+void poisson_default_opts(poisson_opts* opts);
+
+/* Create a handle for an nx x ny x nz grid of spacing h (Formulation; uniform grid).  opts may be
+ * NULL (defaults).  Allocates the handle's device state.  Errors: EINVAL (a size <= 0, h <= 0,
+ * bad option), ENOMEM, ECUDA.  *out is set only on success. */
+int poisson_create(int nx, int ny, int nz, double h, const poisson_opts* opts, poisson_t** out);
+
+/* Release the handle and its device memory (after synchronising its stream).  NULL is a no-op. */
+int poisson_destroy(poisson_t* h);
+
+/* Set the density from the water fraction F (eq. (density), rho = rho_air + F (rho_water -
+ * rho_air)) and build the operator: face coefficients (harmonic means), diagonal, and the
+ * reduced-precision copies.  F: nx*ny*nz doubles; mem = POISSON_MEM_HOST or POISSON_MEM_DEVICE
+ * says where F lives (checked against the pointer).  F is read during the call only.
+ * Errors: EINVAL (NULL, rho <= 0, mem mismatch), ECUDA. */
+int poisson_set_density(poisson_t* h, const double* F, double rho_air, double rho_water, int mem);
+
+/* Solve div((1/rho) grad p) = rhs (eq. (pois)) to relative residual ||b - A p|| / ||b|| <= tol,
+ * where A is the FP64 operator and b = -h^2 rhs.  rhs: the source s = div(u*)/dt, nx*ny*nz
+ * doubles.  p: on entry the initial guess (warm start; zeros for none), on exit the solution.
+ * stats may be NULL.  An all-zero rhs returns p = 0 and OK.  Errors: ENOTREADY (no density set),
+ * EINVAL (NULL, tol <= 0), ENOTCONV (cap reached: p = best iterate, stats = its residual),
+ * EBREAKDOWN, ECUDA. */
+int poisson_solve(poisson_t* h, const double* rhs, double* p, double tol, poisson_stats* stats);
+
+/* y = A x with the handle's operator at the given precision (A = -h^2 div_h((1/rho) grad_h)).
+ * POISSON_FP64 uses the FP64 face coefficients; POISSON_FP32 / _BF16COEF apply the inner
+ * reduced-precision operator with FP32 vectors (x is rounded to float, y widened back).
+ * x, y: nx*ny*nz doubles, distinct.  Errors: ENOTREADY, EINVAL, ECUDA. */
+int poisson_apply(poisson_t* h, const double* x, double* y, int precision);
+
+/* z = M^{-1} r for the preconditioner kind (POISSON_JACOBI, POISSON_RBSSOR with the handle's
+ * omega) at the given precision, with M built from the operator of that precision:
+ * Jacobi M = D; SSOR M = (D - wE) D^{-1} (D - wE^T) / (w (2 - w)) in red-black order (red =
+ * (i+j+k) even first, A = D - E - E^T).  Errors: ENOTREADY, EINVAL, ECUDA. */
+int poisson_precond_apply(poisson_t* h, const double* r, double* z, int kind, int precision);
+
+/* Copy out the FP64 operator: low-side face coefficients bx, by, bz (bx[c] couples cell c with
+ * its -x neighbour, 0 on the wall) and the diagonal.  Any pointer may be NULL to skip it.
+ * Errors: ENOTREADY, ECUDA. */
+int poisson_get_operator(poisson_t* h, double* bx, double* by, double* bz, double* diag);
+
+/* ------------------------------------------------------------------ batched solves
+ * Many independent solves of uneven size in one persistent launch captured in a CUDA graph.
+ * poisson_batch_submit enqueues n solves (handles[i] with its density already set, rhs[i],
+ * p[i] in/out as in poisson_solve, tol[i]) and returns a ticket per solve.  The arrays must stay
+ * valid until poisson_poll reports the ticket finished.  Handles in one batch must be distinct.
+ * Errors: EINVAL, ENOTREADY, ENOMEM, ECUDA. */
+int poisson_batch_submit(poisson_t* const* handles, const double* const* rhs, double* const* p,
+                         const double* tol, int n, uint64_t* tickets);
+
+/* POISSON_PENDING while the ticket's solve runs; then its final status (OK, ENOTCONV, ...),
+ * with *stats filled (may be NULL); a finished ticket is forgotten after it is reported once.
+ * Polling drives the batch: it launches the next chunk of iterations when none is in flight. */
+int poisson_poll(uint64_t ticket, poisson_stats* stats);
+
+/* ------------------------------------------------------------------ instrumentation */
+/* Kernel classes timed by poisson_profile (indices into poisson_kernel_times). */
+#define POISSON_K_CG_A 0      /* CG phase A: p = z + beta p, sum p.Ap                      */
+#define POISSON_K_CG_B 1      /* CG phase B: x, r, z updates, sums r.z and r.r             */
+#define POISSON_K_RESIDUAL 2  /* FP64 residual b - A x and its norm                        */
+#define POISSON_K_OTHER 3     /* set-up, scaling, refinement update, CG init               */
+#define POISSON_K_CLASSES 4
+
+typedef struct {
+    long long launches[POISSON_K_CLASSES]; /* kernel launches per class                     */
+    double ms[POISSON_K_CLASSES];          /* summed CUDA-event time per class, ms           */
+} poisson_kernel_times;
+
+/* Total CUDA kernel launches issued by this library (all handles) since it was loaded. */
+uint64_t poisson_kernel_launches(void);
+
+/* enable != 0: record a CUDA event pair on the handle's stream around every CG phase and
+ * residual kernel of later solves, and zero the accumulated times; 0 turns recording off.
+ * The events add no device work; their host-side cost is a few microseconds per launch. */
+int poisson_profile(poisson_t* h, int enable);
+
+/* Copy out the accumulated per-class launch counts and event times (since poisson_profile). */
+int poisson_profile_read(poisson_t* h, poisson_kernel_times* out);
+
+/* Human-readable name of a status code. */
+const char* poisson_strerror(int status);
+
+/* Library version string. */
+const char* poisson_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POISSON_H */

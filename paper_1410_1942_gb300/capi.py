@@ -1,0 +1,230 @@
+"""Thin ctypes binding to ``libpoisson.so`` (the C ABI of ``include/poisson.h``).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA kernels.  Arrays
+may be numpy float64 arrays (host memory) or CUDA torch tensors (device memory, passed by
+``data_ptr()``); the library tells the two apart.  The library must have been built
+(``paper_1410_1942_gb300.build.build()``); loading raises if it is missing -- there is no other
+implementation behind these names.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, PENDING = 0, 1
+EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN, ETIMEOUT, ENOTREADY, ECUDA, ENOMEM_BUDGET, ENOTICKET = \
+    -1, -2, -3, -4, -5, -6, -7, -8, -9
+FP64, FP32, FP32_BF16COEF = 0, 1, 2
+JACOBI, RBSSOR = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+
+PRECISION = {"fp64": FP64, "fp32": FP32, "bf16": FP32_BF16COEF}
+PRECOND = {"jacobi": JACOBI, "rbssor": RBSSOR, "ssor": RBSSOR}
+
+# every symbol include/poisson.h declares
+EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson_set_density",
+           "poisson_solve", "poisson_apply", "poisson_precond_apply", "poisson_get_operator",
+           "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
+           "poisson_profile_read", "poisson_strerror", "poisson_version"]
+K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER = 0, 1, 2, 3
+K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other"]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("omega", ctypes.c_double),
+                ("max_iters", ctypes.c_int), ("inner_tol", ctypes.c_double), ("tile", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("outer_iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("rel_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4)]
+
+    def as_dict(self):
+        return {K_NAMES[q]: {"launches": int(self.launches[q]), "ms": float(self.ms[q])}
+                for q in range(4)}
+
+
+class PoissonError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s: %s (%d)" % (what, strerror(status), status))
+        self.status = status
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load the library (built in-tree); raises OSError if it is not there."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise OSError("libpoisson.so not built (%s); run paper_1410_1942_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.poisson_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    lib.poisson_default_opts.restype = None
+    lib.poisson_create.argtypes = [i, i, i, d, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+    lib.poisson_destroy.argtypes = [vp]
+    lib.poisson_set_density.argtypes = [vp, vp, d, d, i]
+    lib.poisson_solve.argtypes = [vp, vp, vp, d, ctypes.POINTER(Stats)]
+    lib.poisson_apply.argtypes = [vp, vp, vp, i]
+    lib.poisson_precond_apply.argtypes = [vp, vp, vp, i, i]
+    lib.poisson_get_operator.argtypes = [vp, vp, vp, vp, vp]
+    lib.poisson_batch_submit.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(d), i, ctypes.POINTER(ctypes.c_uint64)]
+    lib.poisson_poll.argtypes = [ctypes.c_uint64, ctypes.POINTER(Stats)]
+    lib.poisson_strerror.argtypes = [i]
+    lib.poisson_strerror.restype = ctypes.c_char_p
+    lib.poisson_version.argtypes = []
+    lib.poisson_version.restype = ctypes.c_char_p
+    lib.poisson_kernel_launches.argtypes = []
+    lib.poisson_kernel_launches.restype = ctypes.c_uint64
+    lib.poisson_profile.argtypes = [vp, i]
+    lib.poisson_profile_read.argtypes = [vp, ctypes.POINTER(KernelTimes)]
+    for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read"]:
+        getattr(lib, name).restype = i
+    _lib = lib
+    return lib
+
+
+def strerror(status):
+    try:
+        return load().poisson_strerror(int(status)).decode()
+    except OSError:
+        return "status %d" % status
+
+
+def _addr(a):
+    """Address of a float64 array: numpy (host) or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError("arrays must be C-contiguous float64")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError("tensors must be contiguous float64")
+        return a.data_ptr()
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def _check(rc, what, ok=(OK,)):
+    if rc not in ok:
+        raise PoissonError(rc, what)
+    return rc
+
+
+def default_opts():
+    o = Opts()
+    load().poisson_default_opts(ctypes.byref(o))
+    return o
+
+
+class Poisson:
+    """One grid: ``poisson_create`` ... ``poisson_destroy``."""
+
+    def __init__(self, nx, ny, nz, h, precision="fp32", precond="jacobi", omega=1.0,
+                 max_iters=20000, inner_tol=1e-4, tile=0, stream=None):
+        lib = load()
+        o = default_opts()
+        o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        o.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
+        o.omega, o.max_iters, o.inner_tol, o.tile = omega, max_iters, inner_tol, tile
+        o.stream = stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream
+        self.shape = (nz, ny, nx)
+        self.h = h
+        self.opts = o
+        hnd = ctypes.c_void_p()
+        _check(lib.poisson_create(nx, ny, nz, h, ctypes.byref(o), ctypes.byref(hnd)), "poisson_create")
+        self._h = hnd
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            load().poisson_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_density(self, F, rho_air=1.0, rho_water=1000.0):
+        mem = MEM_HOST if isinstance(F, np.ndarray) or not getattr(F, "is_cuda", False) else MEM_DEVICE
+        _check(load().poisson_set_density(self._h, _addr(F), rho_air, rho_water, mem),
+               "poisson_set_density")
+
+    def solve(self, rhs, p, tol, allow=(OK,)):
+        """Solves in place into ``p``; returns (status, stats dict)."""
+        st = Stats()
+        rc = load().poisson_solve(self._h, _addr(rhs), _addr(p), tol, ctypes.byref(st))
+        _check(rc, "poisson_solve", ok=allow)
+        return rc, st.as_dict()
+
+    def apply(self, x, y, precision="fp64"):
+        _check(load().poisson_apply(self._h, _addr(x), _addr(y), PRECISION[precision]), "poisson_apply")
+
+    def precond_apply(self, r, z, kind="jacobi", precision="fp64"):
+        _check(load().poisson_precond_apply(self._h, _addr(r), _addr(z), PRECOND[kind],
+                                            PRECISION[precision]), "poisson_precond_apply")
+
+    def profile(self, enable=True):
+        _check(load().poisson_profile(self._h, 1 if enable else 0), "poisson_profile")
+
+    def profile_read(self):
+        t = KernelTimes()
+        _check(load().poisson_profile_read(self._h, ctypes.byref(t)), "poisson_profile_read")
+        return t.as_dict()
+
+    def get_operator(self, bx=None, by=None, bz=None, diag=None):
+        _check(load().poisson_get_operator(self._h, _addr(bx), _addr(by), _addr(bz), _addr(diag)),
+               "poisson_get_operator")
+
+
+def kernel_launches():
+    """CUDA kernels launched by the library since it was loaded."""
+    return int(load().poisson_kernel_launches())
+
+
+def batch_submit(solvers, rhs, p, tol):
+    n = len(solvers)
+    H = (ctypes.c_void_p * n)(*[s.handle.value for s in solvers])
+    R = (ctypes.c_void_p * n)(*[_addr(a) for a in rhs])
+    P = (ctypes.c_void_p * n)(*[_addr(a) for a in p])
+    T = (ctypes.c_double * n)(*([tol] * n if np.isscalar(tol) else list(tol)))
+    tickets = (ctypes.c_uint64 * n)()
+    _check(load().poisson_batch_submit(H, R, P, T, n, tickets), "poisson_batch_submit")
+    return list(tickets)
+
+
+def poll(ticket):
+    """Returns (status, stats dict or None); status PENDING while running."""
+    st = Stats()
+    rc = load().poisson_poll(ctypes.c_uint64(ticket), ctypes.byref(st))
+    return rc, (st.as_dict() if rc != PENDING else None)

@@ -1,0 +1,549 @@
+// capi.cu -- the C ABI of libpoisson (declared in include/poisson.h): handles, operator set-up,
+// the single-solve drivers (plain FP64 PCG; FP32 inner PCG inside FP64 iterative refinement)
+// and the operator / preconditioner entry points used to check the kernels one by one.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "poisson.h"
+#include "kernels.h"
+#include "capi_internal.h"
+
+using namespace pcg;
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) {                                   \
+            last_cuda_error() = e_;                                \
+            return POISSON_ECUDA;                                  \
+        }                                                          \
+    } while (0)
+
+cudaError_t& last_cuda_error() {
+    static thread_local cudaError_t e = cudaSuccess;
+    return e;
+}
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static int dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return POISSON_OK;
+    if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return POISSON_ENOMEM;
+    }
+    return POISSON_OK;
+}
+
+static void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+extern "C" void poisson_default_opts(poisson_opts* o) {
+    if (!o) return;
+    o->precision = POISSON_FP32;
+    o->precond = POISSON_JACOBI;
+    o->omega = 1.0;
+    o->max_iters = 20000;
+    o->inner_tol = 1e-4;
+    o->tile = 0;
+    o->stream = nullptr;
+}
+
+// z-chunk per thread: about 2048 blocks per launch, at least one plane per thread.
+static int choose_kc(const Dims& d) {
+    const long long tiles = (long long)((d.nx + TX - 1) / TX) * ((d.ny + TY - 1) / TY);
+    long long kc = (tiles * d.nz) / 2048;
+    if (kc < 1) kc = 1;
+    if (kc > d.nz) kc = d.nz;
+    return (int)kc;
+}
+
+static void free_state(poisson_t* H) {
+    void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->eta32, H->eta16, H->x64,
+                    H->b64, H->r64, H->z64, H->p64a, H->p64b, H->d32, H->r32, H->z32,
+                    H->p32a, H->p32b, H->sc, H->partials, H->io_a, H->io_b};
+    for (void* p : ptrs) dfree(p);
+    if (H->sc_host) cudaFreeHost(H->sc_host);
+    for (auto& e : H->ev) if (e) cudaEventDestroy(e);
+    for (auto& e : H->prof_ev) if (e) cudaEventDestroy(e);
+}
+
+extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_opts* opts,
+                              poisson_t** out) {
+    if (!out || nx <= 0 || ny <= 0 || nz <= 0 || !(h > 0.0) || !std::isfinite(h))
+        return POISSON_EINVAL;
+    const long long n = (long long)nx * ny * nz;
+    if (n >= (1LL << 31)) return POISSON_EINVAL;
+    poisson_opts o;
+    poisson_default_opts(&o);
+    if (opts) o = *opts;
+    if (o.precision < POISSON_FP64 || o.precision > POISSON_FP32_BF16COEF) return POISSON_EINVAL;
+    if (o.precond != POISSON_JACOBI && o.precond != POISSON_RBSSOR) return POISSON_EINVAL;
+    if (!(o.omega > 0.0 && o.omega < 2.0)) return POISSON_EINVAL;
+    if (o.max_iters <= 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return POISSON_EINVAL;
+
+    poisson_t* H = new (std::nothrow) poisson_t();
+    if (!H) return POISSON_ENOMEM;
+    H->d = Dims{nx, ny, nz, nx * ny, (int)n};
+    H->h = h;
+    H->opts = o;
+    H->st = (cudaStream_t)o.stream;
+    H->kc = choose_kc(H->d);
+    cudaGetDevice(&H->device);
+    const dim3 g((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + H->kc - 1) / H->kc);
+    H->nblocks = (size_t)g.x * g.y * g.z;
+
+    int rc = POISSON_OK;
+    auto A = [&](int r) { if (rc == POISSON_OK) rc = r; };
+    const size_t N = (size_t)n;
+    A(dalloc(&H->bx, N)); A(dalloc(&H->by, N)); A(dalloc(&H->bz, N)); A(dalloc(&H->diag, N));
+    A(dalloc(&H->eta32, N)); A(dalloc(&H->eta16, N));
+    A(dalloc(&H->x64, N)); A(dalloc(&H->b64, N));
+    if (o.precision == POISSON_FP64) {
+        A(dalloc(&H->dinv, N));
+        A(dalloc(&H->r64, N)); A(dalloc(&H->z64, N)); A(dalloc(&H->p64a, N)); A(dalloc(&H->p64b, N));
+    } else {
+        A(dalloc(&H->d32, N)); A(dalloc(&H->r32, N)); A(dalloc(&H->z32, N));
+        A(dalloc(&H->p32a, N)); A(dalloc(&H->p32b, N));
+    }
+    A(dalloc(&H->sc, 1));
+    A(dalloc(&H->partials, 2 * H->nblocks + 64));
+    if (rc == POISSON_OK && cudaMallocHost((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
+        cudaGetLastError();
+        H->sc_host = nullptr;
+        rc = POISSON_ENOMEM;
+    }
+    for (auto& e : H->ev)
+        if (rc == POISSON_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            rc = POISSON_ECUDA;
+    if (rc == POISSON_OK && cudaMemsetAsync(H->sc, 0, sizeof(Scalars), H->st) != cudaSuccess)
+        rc = POISSON_ECUDA;
+    if (rc != POISSON_OK) {
+        free_state(H);
+        delete H;
+        return rc;
+    }
+    *out = H;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_destroy(poisson_t* H) {
+    if (!H) return POISSON_OK;
+    cudaStreamSynchronize(H->st);
+    free_state(H);
+    delete H;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air,
+                                   double rho_water, int mem) {
+    if (!H || !F || !(rho_air > 0.0) || !(rho_water > 0.0)) return POISSON_EINVAL;
+    if (mem != POISSON_MEM_HOST && mem != POISSON_MEM_DEVICE) return POISSON_EINVAL;
+    const bool dev = is_device_ptr(F);
+    if (dev != (mem == POISSON_MEM_DEVICE)) return POISSON_EINVAL;
+    const size_t bytes = sizeof(double) * (size_t)H->d.n;
+    const double* Fd = F;
+    if (!dev) {
+        // stage F through b64 (overwritten by every solve)
+        CK(cudaMemcpyAsync(H->b64, F, bytes, cudaMemcpyHostToDevice, H->st));
+        Fd = H->b64;
+    }
+    launch_setup(H->d, Fd, rho_air, rho_water, H->bx, H->by, H->bz, H->diag, H->dinv, H->eta32,
+                 H->eta16, H->st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(H->st));
+    H->ready = true;
+    return POISSON_OK;
+}
+
+// ------------------------------------------------------------------ profiling events
+// Event pairs around CG phase / residual kernels (poisson_profile).  Slot q of a chunk owns
+// events [q * PROF_PER_CHUNK, (q + 1) * PROF_PER_CHUNK).
+static int prof_events(poisson_t* H) {
+    if (!H->prof_ev.empty()) return POISSON_OK;
+    H->prof_ev.resize(2 * PROF_PER_CHUNK + 2);
+    for (auto& e : H->prof_ev) CK(cudaEventCreate(&e));
+    return POISSON_OK;
+}
+
+static void prof_add(poisson_t* H, int cls, cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, a, b) == cudaSuccess) {
+        H->prof.ms[cls] += ms;
+        H->prof.launches[cls] += 1;
+    } else {
+        cudaGetLastError();
+    }
+}
+
+// ------------------------------------------------------------------ inner CG loop
+// Queues chunks of CG_CHUNK iterations; reads the scalars of chunk n while chunk n+1 runs.
+template <typename V, typename Coef>
+static int cg_loop(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* pa, V* pb, double tol2,
+                   int rel_to_b, int max_iter, Scalars* result) {
+    const int K = CG_CHUNK;
+    cudaStream_t st = H->st;
+    const bool prof = H->prof_on;
+    launch_cg_init<V, Coef>(H->d, H->kc, coef, r, z, H->sc, H->partials, tol2, rel_to_b, max_iter,
+                            st);
+    V* p_in = pa;
+    V* p_out = pb;
+    auto enqueue_chunk = [&](int slot) -> int {
+        cudaEvent_t* ev = prof ? &H->prof_ev[slot * PROF_PER_CHUNK] : nullptr;
+        for (int q = 0; q < K; ++q) {
+            if (prof) CK(cudaEventRecord(ev[3 * q], st));
+            launch_cg_a<V, Coef>(H->d, H->kc, coef, z, p_in, p_out, H->sc, H->partials, st);
+            if (prof) CK(cudaEventRecord(ev[3 * q + 1], st));
+            launch_cg_b<V, Coef>(H->d, H->kc, coef, p_out, x, r, z, H->sc, H->partials, st);
+            if (prof) CK(cudaEventRecord(ev[3 * q + 2], st));
+            std::swap(p_in, p_out);
+        }
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&H->sc_host[slot], H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
+        CK(cudaEventRecord(H->ev[slot], st));
+        return POISSON_OK;
+    };
+    // Scalars copied back with a chunk tell how many of its iterations did work.
+    int it_seen = 0;
+    auto harvest = [&](int slot) {
+        if (!prof) return;
+        const int it_now = H->sc_host[slot].iter;
+        // iterations of this chunk that did work (later ones returned at once)
+        const int live = std::max(0, std::min(K, it_now - it_seen));
+        cudaEvent_t* ev = &H->prof_ev[slot * PROF_PER_CHUNK];
+        for (int q = 0; q < live; ++q) {
+            prof_add(H, POISSON_K_CG_A, ev[3 * q], ev[3 * q + 1]);
+            prof_add(H, POISSON_K_CG_B, ev[3 * q + 1], ev[3 * q + 2]);
+        }
+        it_seen = it_now;
+    };
+    int rc = enqueue_chunk(0);
+    if (rc) return rc;
+    int slot = 0;
+    long long launched = K;
+    for (;;) {
+        const bool more = launched < (long long)max_iter + K;
+        if (more) {
+            rc = enqueue_chunk(slot ^ 1);
+            if (rc) return rc;
+            launched += K;
+        }
+        CK(cudaEventSynchronize(H->ev[slot]));
+        const Scalars s = H->sc_host[slot];
+        harvest(slot);
+        if (s.done != RUNNING || !more) {
+            CK(cudaStreamSynchronize(st));
+            CK(cudaMemcpy(result, H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost));
+            return POISSON_OK;
+        }
+        slot ^= 1;
+    }
+}
+
+// Reads the scalars after a residual kernel (and books its time when profiling).
+static int read_scalars(poisson_t* H, Scalars* s) {
+    CK(cudaMemcpyAsync(&H->sc_host[0], H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    *s = H->sc_host[0];
+    if (H->prof_on)
+        prof_add(H, POISSON_K_RESIDUAL, H->prof_ev[2 * PROF_PER_CHUNK],
+                 H->prof_ev[2 * PROF_PER_CHUNK + 1]);
+    return POISSON_OK;
+}
+
+// Plain FP64 PCG on A64 x = b; restarts from the recomputed residual if the recurrence drifts.
+static int solve_fp64(poisson_t* H, double tol, int* outer, int* inner, double* rel_out) {
+    const CoefFaces64 c{H->bx, H->by, H->bz, H->diag, H->dinv};
+    const size_t bytes = sizeof(double) * (size_t)H->d.n;
+    int total = 0, status = POISSON_ENOTCONV;
+    double rel = INFINITY;
+    int restarts = 0;
+    for (;; ++restarts) {
+        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[2 * PROF_PER_CHUNK], H->st));
+        launch_residual64(H->d, H->kc, c, H->b64, H->x64, H->r64, H->sc, H->partials, H->st);
+        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[2 * PROF_PER_CHUNK + 1], H->st));
+        CK(cudaGetLastError());
+        Scalars s;
+        int rc = read_scalars(H, &s);
+        if (rc) return rc;
+        if (s.bb == 0.0) {
+            CK(cudaMemsetAsync(H->x64, 0, bytes, H->st));
+            rel = 0.0;
+            status = POISSON_OK;
+            break;
+        }
+        rel = std::sqrt(s.rr / s.bb);
+        if (!std::isfinite(rel)) { status = POISSON_EBREAKDOWN; break; }
+        if (rel <= tol) { status = POISSON_OK; break; }
+        if (total >= H->opts.max_iters || restarts >= 8) { status = POISSON_ENOTCONV; break; }
+        CK(cudaMemsetAsync(H->p64a, 0, bytes, H->st));
+        Scalars res;
+        rc = cg_loop<double, CoefFaces64>(H, c, H->x64, H->r64, H->z64, H->p64a, H->p64b,
+                                          tol * tol, 1, H->opts.max_iters - total, &res);
+        if (rc) return rc;
+        total += res.iter;
+        if (res.done == BREAKDOWN && res.iter == 0) { status = POISSON_EBREAKDOWN; break; }
+    }
+    *outer = restarts + 1;
+    *inner = total;
+    *rel_out = rel;
+    return status;
+}
+
+// FP32 inner PCG on the reduced-precision operator inside FP64 iterative refinement:
+//   r = b - A64 x (FP64); stop when ||r||/||b|| <= tol; solve A32 d = r (FP32 PCG, relative
+//   reduction inner_tol); x += d.
+template <typename E>
+static int solve_mixed(poisson_t* H, const E* eta, double tol, int* outer, int* inner,
+                       double* rel_out) {
+    const CoefFaces64 c64{H->bx, H->by, H->bz, H->diag, nullptr};
+    const CoefEta<E> c32{eta};
+    const size_t bytes32 = sizeof(float) * (size_t)H->d.n;
+    int total = 0, status = POISSON_ENOTCONV, k = 0;
+    double rel = INFINITY, prev = INFINITY;
+    int stalls = 0;
+    for (k = 0;; ++k) {
+        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[2 * PROF_PER_CHUNK], H->st));
+        launch_residual64_f32(H->d, H->kc, c64, H->b64, H->x64, H->r32, H->sc, H->partials, H->st);
+        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[2 * PROF_PER_CHUNK + 1], H->st));
+        CK(cudaGetLastError());
+        Scalars s;
+        int rc = read_scalars(H, &s);
+        if (rc) return rc;
+        if (s.bb == 0.0) {
+            CK(cudaMemsetAsync(H->x64, 0, sizeof(double) * (size_t)H->d.n, H->st));
+            rel = 0.0;
+            status = POISSON_OK;
+            break;
+        }
+        rel = std::sqrt(s.rr / s.bb);
+        if (!std::isfinite(rel)) { status = POISSON_EBREAKDOWN; break; }
+        if (rel <= tol) { status = POISSON_OK; break; }
+        if (rel > 0.5 * prev) ++stalls; else stalls = 0;
+        if (total >= H->opts.max_iters || stalls >= 3 || k >= 60) { status = POISSON_ENOTCONV; break; }
+        prev = rel;
+        double target = std::max(H->opts.inner_tol, 0.3 * tol / rel);
+        target = std::min(target, 0.5);
+        CK(cudaMemsetAsync(H->d32, 0, bytes32, H->st));
+        CK(cudaMemsetAsync(H->p32a, 0, bytes32, H->st));
+        Scalars res;
+        rc = cg_loop<float, CoefEta<E>>(H, c32, H->d32, H->r32, H->z32, H->p32a, H->p32b,
+                                        target * target, 0, H->opts.max_iters - total, &res);
+        if (rc) return rc;
+        total += res.iter;
+        if (res.iter > 0) launch_update64(H->d.n, H->x64, H->d32, H->st);
+        CK(cudaGetLastError());
+        if (res.done == BREAKDOWN && res.iter == 0) { status = POISSON_EBREAKDOWN; break; }
+    }
+    *outer = k + 1;
+    *inner = total;
+    *rel_out = rel;
+    return status;
+}
+
+extern "C" int poisson_solve(poisson_t* H, const double* rhs, double* p, double tol,
+                             poisson_stats* stats) {
+    if (!H || !rhs || !p || !(tol > 0.0)) return POISSON_EINVAL;
+    if (!H->ready) return POISSON_ENOTREADY;
+    const double t0 = now_s();
+    const size_t n = (size_t)H->d.n, bytes = sizeof(double) * n;
+    const bool drhs = is_device_ptr(rhs), dp = is_device_ptr(p);
+    const double a = -(H->h * H->h);
+    if (drhs) {
+        launch_scale((long long)n, rhs, a, H->b64, H->st);
+    } else {
+        CK(cudaMemcpyAsync(H->b64, rhs, bytes, cudaMemcpyHostToDevice, H->st));
+        launch_scale((long long)n, H->b64, a, H->b64, H->st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(H->x64, p, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       H->st));
+    int outer = 0, inner = 0;
+    double rel = 0.0;
+    int status;
+    switch (H->opts.precision) {
+        case POISSON_FP64: status = solve_fp64(H, tol, &outer, &inner, &rel); break;
+        case POISSON_FP32: status = solve_mixed<float>(H, H->eta32, tol, &outer, &inner, &rel); break;
+        default: status = solve_mixed<__nv_bfloat16>(H, H->eta16, tol, &outer, &inner, &rel); break;
+    }
+    if (status == POISSON_ECUDA) return status;
+    CK(cudaMemcpyAsync(p, H->x64, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       H->st));
+    CK(cudaStreamSynchronize(H->st));
+    if (stats) {
+        stats->outer_iters = outer;
+        stats->inner_iters = inner;
+        stats->rel_residual = rel;
+        stats->seconds = now_s() - t0;
+    }
+    return status;
+}
+
+// ------------------------------------------------------------------ checking entry points
+static int io_buffers(poisson_t* H) {
+    if (H->io_a) return POISSON_OK;
+    int rc = dalloc(&H->io_a, (size_t)H->d.n);
+    if (rc == POISSON_OK) rc = dalloc(&H->io_b, (size_t)H->d.n);
+    return rc;
+}
+
+// Runs `fn(in_dev, out_dev)` on device copies of host arrays when needed.
+template <typename Fn>
+static int with_io(poisson_t* H, const double* in, double* out, Fn fn) {
+    const size_t bytes = sizeof(double) * (size_t)H->d.n;
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    if (!din || !dout) {
+        int rc = io_buffers(H);
+        if (rc) return rc;
+    }
+    const double* xi = in;
+    double* yo = out;
+    if (!din) {
+        CK(cudaMemcpyAsync(H->io_a, in, bytes, cudaMemcpyHostToDevice, H->st));
+        xi = H->io_a;
+    }
+    if (!dout) yo = H->io_b;
+    fn(xi, yo);
+    CK(cudaGetLastError());
+    if (!dout) CK(cudaMemcpyAsync(out, yo, bytes, cudaMemcpyDeviceToHost, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    return POISSON_OK;
+}
+
+extern "C" int poisson_apply(poisson_t* H, const double* x, double* y, int precision) {
+    if (!H || !x || !y || x == y) return POISSON_EINVAL;
+    if (!H->ready) return POISSON_ENOTREADY;
+    const Dims d = H->d;
+    const int kc = H->kc;
+    cudaStream_t st = H->st;
+    switch (precision) {
+        case POISSON_FP64: {
+            const CoefFaces64 c{H->bx, H->by, H->bz, H->diag, nullptr};
+            return with_io(H, x, y, [&](const double* a, double* b) {
+                launch_apply<double, CoefFaces64>(d, kc, c, a, b, st);
+            });
+        }
+        case POISSON_FP32: {
+            const CoefEta<float> c{H->eta32};
+            return with_io(H, x, y, [&](const double* a, double* b) {
+                launch_apply<float, CoefEta<float>>(d, kc, c, a, b, st);
+            });
+        }
+        case POISSON_FP32_BF16COEF: {
+            const CoefEta<__nv_bfloat16> c{H->eta16};
+            return with_io(H, x, y, [&](const double* a, double* b) {
+                launch_apply<float, CoefEta<__nv_bfloat16>>(d, kc, c, a, b, st);
+            });
+        }
+        default: return POISSON_EINVAL;
+    }
+}
+
+extern "C" int poisson_precond_apply(poisson_t* H, const double* r, double* z, int kind,
+                                     int precision) {
+    if (!H || !r || !z || r == z) return POISSON_EINVAL;
+    if (!H->ready) return POISSON_ENOTREADY;
+    if (kind != POISSON_JACOBI) return POISSON_EINVAL;
+    const Dims d = H->d;
+    const int kc = H->kc;
+    cudaStream_t st = H->st;
+    switch (precision) {
+        case POISSON_FP64: {
+            const CoefFaces64 c{H->bx, H->by, H->bz, H->diag, nullptr};
+            return with_io(H, r, z, [&](const double* a, double* b) {
+                launch_jacobi<double, CoefFaces64>(d, kc, c, a, b, st);
+            });
+        }
+        case POISSON_FP32: {
+            const CoefEta<float> c{H->eta32};
+            return with_io(H, r, z, [&](const double* a, double* b) {
+                launch_jacobi<float, CoefEta<float>>(d, kc, c, a, b, st);
+            });
+        }
+        case POISSON_FP32_BF16COEF: {
+            const CoefEta<__nv_bfloat16> c{H->eta16};
+            return with_io(H, r, z, [&](const double* a, double* b) {
+                launch_jacobi<float, CoefEta<__nv_bfloat16>>(d, kc, c, a, b, st);
+            });
+        }
+        default: return POISSON_EINVAL;
+    }
+}
+
+extern "C" int poisson_get_operator(poisson_t* H, double* bx, double* by, double* bz,
+                                    double* diag) {
+    if (!H) return POISSON_EINVAL;
+    if (!H->ready) return POISSON_ENOTREADY;
+    const size_t bytes = sizeof(double) * (size_t)H->d.n;
+    const double* src[4] = {H->bx, H->by, H->bz, H->diag};
+    double* dst[4] = {bx, by, bz, diag};
+    for (int q = 0; q < 4; ++q) {
+        if (!dst[q]) continue;
+        CK(cudaMemcpyAsync(dst[q], src[q], bytes,
+                           is_device_ptr(dst[q]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           H->st));
+    }
+    CK(cudaStreamSynchronize(H->st));
+    return POISSON_OK;
+}
+
+extern "C" uint64_t poisson_kernel_launches(void) {
+    return (uint64_t)g_kernel_launches.load(std::memory_order_relaxed);
+}
+
+extern "C" int poisson_profile(poisson_t* H, int enable) {
+    if (!H) return POISSON_EINVAL;
+    if (enable) {
+        int rc = prof_events(H);
+        if (rc) return rc;
+    }
+    H->prof_on = enable != 0;
+    H->prof = poisson_kernel_times{};
+    return POISSON_OK;
+}
+
+extern "C" int poisson_profile_read(poisson_t* H, poisson_kernel_times* out) {
+    if (!H || !out) return POISSON_EINVAL;
+    *out = H->prof;
+    return POISSON_OK;
+}
+
+extern "C" const char* poisson_strerror(int s) {
+    switch (s) {
+        case POISSON_OK: return "ok";
+        case POISSON_PENDING: return "pending";
+        case POISSON_EINVAL: return "invalid argument";
+        case POISSON_ENOMEM: return "out of memory";
+        case POISSON_ENOTCONV: return "not converged (iteration cap)";
+        case POISSON_EBREAKDOWN: return "CG breakdown (p.Ap <= 0 or non-finite)";
+        case POISSON_ETIMEOUT: return "device wait timed out";
+        case POISSON_ENOTREADY: return "density not set";
+        case POISSON_ECUDA: return "CUDA runtime error";
+        case POISSON_ENOMEM_BUDGET: return "over the device-memory budget";
+        case POISSON_ENOTICKET: return "unknown ticket";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* poisson_version(void) { return "libpoisson 0.1 (sm_103a)"; }

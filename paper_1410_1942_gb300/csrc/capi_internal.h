@@ -1,0 +1,50 @@
+// capi_internal.h -- the handle behind the opaque poisson_t of include/poisson.h.
+#pragma once
+
+#include <vector>
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "poisson.h"
+#include "internal.cuh"
+
+struct poisson_s {
+    pcg::Dims d{};
+    double h = 0.0;
+    poisson_opts opts{};
+    cudaStream_t st = nullptr;
+    int kc = 1;          // z-planes per thread in the column kernels
+    int device = 0;
+    size_t nblocks = 0;  // blocks of one column-kernel launch (= reduction partials)
+    bool ready = false;  // density set
+
+    // FP64 operator: low-side face coefficients, diagonal, 1/diagonal (FP64 Jacobi only)
+    double *bx = nullptr, *by = nullptr, *bz = nullptr, *diag = nullptr, *dinv = nullptr;
+    // rho / 2 per cell for the reduced-precision inner operator
+    float* eta32 = nullptr;
+    __nv_bfloat16* eta16 = nullptr;
+    // FP64 solution and right side (b = -h^2 s)
+    double *x64 = nullptr, *b64 = nullptr;
+    // plain FP64 PCG vectors
+    double *r64 = nullptr, *z64 = nullptr, *p64a = nullptr, *p64b = nullptr;
+    // FP32 inner PCG vectors (d = correction)
+    float *d32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32a = nullptr, *p32b = nullptr;
+    // device scalars, reduction partials, pinned host mirror (2 slots), chunk events
+    pcg::Scalars* sc = nullptr;
+    double* partials = nullptr;
+    pcg::Scalars* sc_host = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // staging for the checking entry points when given host arrays
+    double *io_a = nullptr, *io_b = nullptr;
+    // poisson_profile: event pairs around the timed kernels, accumulated times
+    bool prof_on = false;
+    poisson_kernel_times prof{};
+    std::vector<cudaEvent_t> prof_ev;
+};
+
+constexpr int CG_CHUNK = 8;                    // CG iterations queued per host check
+constexpr int PROF_PER_CHUNK = 3 * CG_CHUNK;   // events per chunk slot when profiling
+
+cudaError_t& last_cuda_error();
+bool is_device_ptr(const void* p);

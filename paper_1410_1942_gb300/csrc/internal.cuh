@@ -1,0 +1,178 @@
+// internal.cuh -- device-side building blocks shared by the libpoisson kernels.
+//
+// Operator (Formulation, eqs. (density) and (pois)): for cell c with neighbours n,
+//   (A v)_c = D_c v_c - sum_n w_cn v_n,   D_c = sum_n w_cn + w_top,
+// w_cn = 2 / (rho_c + rho_n) on interior faces, 0 on the Neumann walls, and w_top = 2 / rho_c on
+// the top face (Dirichlet p = 0, ghost -v_c).  A = -h^2 div_h((1/rho) grad_h).
+//
+// Two coefficient sources implement it:
+//   * FP64 face arrays (bx, by, bz = coefficient of the low face of each cell, diag) built once
+//     per density -- the exact operator of the FP64 residual and of the plain FP64 PCG;
+//   * eta = rho / 2 per cell in FP32 or BF16, from which the inner solver forms each face on the
+//     fly as 1 / (eta_c + eta_n) (and the top term as 1 / eta_c).  The sum is commutative, so
+//     both cells of a face see the same coefficient: the reduced-precision operator stays a
+//     symmetric weighted graph Laplacian whose diagonal is the sum of its own faces.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace pcg {
+
+struct Dims {
+    int nx, ny, nz;
+    int sxy;  // nx * ny
+    int n;    // nx * ny * nz (< 2^31, checked at create)
+};
+
+// Per-solve CG scalars, updated on the device by the last block of each reduction.
+struct Scalars {
+    double rz;      // (r, z) of the current iterate
+    double pq;      // (p, A p)
+    double alpha;
+    double beta;
+    double rr;      // (r, r)
+    double rr0;     // (r, r) at the start of the (inner) solve
+    double stop2;   // stop when rr <= stop2
+    double bb;      // (b, b) -- written by the residual reduction
+    int iter;       // CG iterations done in this solve
+    int max_iter;   // cap
+    int done;       // 0 running, 1 converged, 2 breakdown, 3 iteration cap
+    unsigned int ticket;  // arrivals of the current reduction
+};
+
+enum Done { RUNNING = 0, CONVERGED = 1, BREAKDOWN = 2, CAPPED = 3 };
+
+// Hardware reciprocal (MUFU), flush-to-zero: deterministic for a given input.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ------------------------------------------------------------------ block reductions (FP64)
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sums NV doubles over the block; the result is valid in thread 0.  smem: 32 * NV doubles.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* smem) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = (nthreads + 31) >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) smem[warp * NV + q] = v[q];
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = (lane < nwarps) ? smem[lane * NV + q] : 0.0;
+            v[q] = warp_sum(t);
+        }
+    }
+    __syncthreads();
+}
+
+// Grid-wide deterministic reduction: every block stores its NV partial sums to
+// partials[block * NV + q]; the last block to arrive adds them in block order and returns true
+// in all of its threads with the totals in `tot` (valid in every thread of that block).
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, unsigned int* ticket,
+                                         double (&tot)[NV], double* smem) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const unsigned int nblocks = gridDim.x * gridDim.y * gridDim.z;
+    const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    __shared__ unsigned int s_last;
+    block_sum<NV>(v, smem);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) partials[(size_t)bid * NV + q] = v[q];
+        __threadfence();
+        unsigned int t = atomicAdd(ticket, 1u);
+        s_last = (t == nblocks - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    for (unsigned int b = tid; b < nblocks; b += nthreads) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&partials[(size_t)b * NV + q]);
+    }
+    block_sum<NV>(acc, smem);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) smem[q] = acc[q];
+        *ticket = 0u;  // ready for the next reduction (stream-ordered)
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = smem[q];
+    __syncthreads();
+    return true;
+}
+
+// ------------------------------------------------------------------ coefficient policies
+// weights(): the six face coefficients and the diagonal of cell (i, j, k).
+template <typename T>
+struct Stencil {
+    T xm, xp, ym, yp, zm, zp, D;
+};
+
+struct CoefFaces64 {
+    const double* bx;
+    const double* by;
+    const double* bz;
+    const double* diag;
+    const double* dinv;  // 1/diag (FP64 Jacobi); may be null
+    __device__ __forceinline__ void weights(const Dims& d, int c, int i, int j, int k,
+                                            Stencil<double>& w) const {
+        w.xm = bx[c];
+        w.xp = (i + 1 < d.nx) ? bx[c + 1] : 0.0;
+        w.ym = by[c];
+        w.yp = (j + 1 < d.ny) ? by[c + d.nx] : 0.0;
+        w.zm = bz[c];
+        w.zp = (k + 1 < d.nz) ? bz[c + d.sxy] : 0.0;
+        w.D = diag[c];
+    }
+};
+
+template <typename E>
+__device__ __forceinline__ float eta_load(const E* p, int c);
+template <>
+__device__ __forceinline__ float eta_load<float>(const float* p, int c) { return __ldg(p + c); }
+template <>
+__device__ __forceinline__ float eta_load<__nv_bfloat16>(const __nv_bfloat16* p, int c) {
+    return __bfloat162float(p[c]);
+}
+
+template <typename E>
+struct CoefEta {
+    const E* eta;
+    __device__ __forceinline__ void weights(const Dims& d, int c, int i, int j, int k,
+                                            Stencil<float>& w) const {
+        const float ec = eta_load(eta, c);
+        w.xm = (i > 0) ? rcp_approx(ec + eta_load(eta, c - 1)) : 0.f;
+        w.xp = (i + 1 < d.nx) ? rcp_approx(ec + eta_load(eta, c + 1)) : 0.f;
+        w.ym = (j > 0) ? rcp_approx(ec + eta_load(eta, c - d.nx)) : 0.f;
+        w.yp = (j + 1 < d.ny) ? rcp_approx(ec + eta_load(eta, c + d.nx)) : 0.f;
+        w.zm = (k > 0) ? rcp_approx(ec + eta_load(eta, c - d.sxy)) : 0.f;
+        const bool top = (k + 1 == d.nz);
+        const float wzp = top ? rcp_approx(ec) : rcp_approx(ec + eta_load(eta, c + d.sxy));
+        w.zp = top ? 0.f : wzp;
+        w.D = w.xm + w.xp + w.ym + w.yp + w.zm + wzp;
+    }
+};
+
+}  // namespace pcg

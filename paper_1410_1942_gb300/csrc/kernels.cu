@@ -1,0 +1,392 @@
+// kernels.cu -- operator setup, FP64 residual/refinement and the PCG phase kernels.
+//
+// PCG (Introduction: preconditioned conjugate gradients on the second-order variable-coefficient
+// Poisson equation) is split at its two global reductions into two fused passes per iteration:
+//
+//   phase A:  p = z + beta p_old;  q = A p (not stored);  sum p.q          -> alpha = rz / pq
+//   phase B:  q = A p (recomputed); x += alpha p;  r -= alpha q;  z = M^{-1} r;
+//             sum r.z and r.r                                            -> beta, convergence
+//
+// Recomputing q in phase B costs one more stencil evaluation but saves writing and re-reading q.
+// p is double-buffered (phase A reads neighbours of p_old while writing p).  All CG scalars live
+// in device memory (struct Scalars); the last block of each reduction updates them, and every
+// kernel returns at once when the solve is finished, so chunks of iterations can be queued
+// without host round trips.
+#include "internal.cuh"
+#include "kernels.h"
+
+#include <atomic>
+
+namespace pcg {
+
+// ------------------------------------------------------------------ operator setup (FP64)
+// rho = rho_air + F (rho_water - rho_air) with explicit rounding (no contraction) so the FP64
+// face arrays are reproducible bit for bit.
+__device__ __forceinline__ double rho_of(double F, double ra, double rw) {
+    return __dadd_rn(ra, __dmul_rn(F, __dadd_rn(rw, -ra)));
+}
+
+__global__ void k_setup_faces(Dims d, const double* __restrict__ F, double ra, double rw,
+                              double* __restrict__ bx, double* __restrict__ by,
+                              double* __restrict__ bz, float* __restrict__ eta32,
+                              __nv_bfloat16* __restrict__ eta16) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= d.n) return;
+    const int c = (int)tid;
+    const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
+    const double rc = rho_of(F[c], ra, rw);
+    bx[c] = (i > 0) ? 2.0 / __dadd_rn(rc, rho_of(F[c - 1], ra, rw)) : 0.0;
+    by[c] = (j > 0) ? 2.0 / __dadd_rn(rc, rho_of(F[c - d.nx], ra, rw)) : 0.0;
+    bz[c] = (k > 0) ? 2.0 / __dadd_rn(rc, rho_of(F[c - d.sxy], ra, rw)) : 0.0;
+    const double e = 0.5 * rc;
+    if (eta32) eta32[c] = (float)e;
+    if (eta16) eta16[c] = __float2bfloat16_rn((float)e);
+}
+
+// diag = bx[c] + by[c] + bz[c] + high faces (+ 2/rho_c on the top layer), summed in that order.
+__global__ void k_setup_diag(Dims d, const double* __restrict__ F, double ra, double rw,
+                             const double* __restrict__ bx, const double* __restrict__ by,
+                             const double* __restrict__ bz, double* __restrict__ diag,
+                             double* __restrict__ dinv) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= d.n) return;
+    const int c = (int)tid;
+    const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
+    double s = __dadd_rn(__dadd_rn(bx[c], by[c]), bz[c]);
+    if (i + 1 < d.nx) s = __dadd_rn(s, bx[c + 1]);
+    if (j + 1 < d.ny) s = __dadd_rn(s, by[c + d.nx]);
+    if (k + 1 < d.nz) s = __dadd_rn(s, bz[c + d.sxy]);
+    else s = __dadd_rn(s, 2.0 / rho_of(F[c], ra, rw));
+    diag[c] = s;
+    if (dinv) dinv[c] = 1.0 / s;
+}
+
+__global__ void k_scale(long long n, const double* __restrict__ s, double a, double* __restrict__ b) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = __dmul_rn(a, s[t]);
+}
+
+__global__ void k_update64(long long n, double* __restrict__ x, const float* __restrict__ dlt) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) x[t] += (double)dlt[t];
+}
+
+template <typename T>
+__global__ void k_narrow(long long n, const double* __restrict__ a, T* __restrict__ b) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (T)a[t];
+}
+
+template <typename T>
+__global__ void k_widen(long long n, const T* __restrict__ a, double* __restrict__ b) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (double)a[t];
+}
+
+// ------------------------------------------------------------------ stencil helpers
+#define COL_LOOP_BEGIN                                                         \
+    const int i = blockIdx.x * TX + threadIdx.x;                               \
+    const int j = blockIdx.y * TY + threadIdx.y;                               \
+    const int k0 = blockIdx.z * kc;                                            \
+    const int k1 = min(d.nz, k0 + kc);                                         \
+    if (i < d.nx && j < d.ny)                                                  \
+        for (int k = k0; k < k1; ++k) {                                        \
+            const int c = i + d.nx * (j + d.ny * k);
+
+#define COL_LOOP_END }
+
+template <typename V, typename Coef>
+__device__ __forceinline__ V inv_diag(const Coef& coef, int c, const Stencil<V>& w);
+
+template <>
+__device__ __forceinline__ double inv_diag<double, CoefFaces64>(const CoefFaces64& coef, int c,
+                                                                const Stencil<double>& w) {
+    return coef.dinv ? coef.dinv[c] : 1.0 / w.D;
+}
+template <>
+__device__ __forceinline__ float inv_diag<float, CoefEta<float>>(const CoefEta<float>&, int,
+                                                                 const Stencil<float>& w) {
+    return rcp_approx(w.D);
+}
+template <>
+__device__ __forceinline__ float inv_diag<float, CoefEta<__nv_bfloat16>>(
+    const CoefEta<__nv_bfloat16>&, int, const Stencil<float>& w) {
+    return rcp_approx(w.D);
+}
+
+// sum_n w_cn v_n with v = load(e)
+template <typename V, typename L>
+__device__ __forceinline__ V nb_sum(const Dims& d, const Stencil<V>& w, int c, int i, int j,
+                                    int k, L load) {
+    V s = 0;
+    if (i > 0) s += w.xm * load(c - 1);
+    if (i + 1 < d.nx) s += w.xp * load(c + 1);
+    if (j > 0) s += w.ym * load(c - d.nx);
+    if (j + 1 < d.ny) s += w.yp * load(c + d.nx);
+    if (k > 0) s += w.zm * load(c - d.sxy);
+    if (k + 1 < d.nz) s += w.zp * load(c + d.sxy);
+    return s;
+}
+
+// ------------------------------------------------------------------ FP64 residual
+// r = b - A x with the FP64 operator; writes r (as R) and reduces (r.r, b.b) into sc->rr, sc->bb.
+template <typename R>
+__global__ void __launch_bounds__(TX * TY) k_residual64(Dims d, CoefFaces64 coef, int kc,
+                                                       const double* __restrict__ b,
+                                                       const double* __restrict__ x,
+                                                       R* __restrict__ r, Scalars* sc,
+                                                       double* partials) {
+    __shared__ double smem[64];
+    double rr = 0.0, bb = 0.0;
+    auto ld = [&](int e) { return x[e]; };
+    COL_LOOP_BEGIN
+        Stencil<double> w;
+        coef.weights(d, c, i, j, k, w);
+        const double ax = w.D * x[c] - nb_sum(d, w, c, i, j, k, ld);
+        const double bc = b[c];
+        const double rc = bc - ax;
+        r[c] = (R)rc;
+        rr += rc * rc;
+        bb += bc * bc;
+    COL_LOOP_END
+    double v[2] = {rr, bb}, tot[2];
+    if (grid_sum<2>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            sc->rr = tot[0];
+            sc->bb = tot[1];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ y = A x, z = D^{-1} r
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_apply(Dims d, Coef coef, int kc,
+                                                  const double* __restrict__ x,
+                                                  double* __restrict__ y) {
+    auto ld = [&](int e) { return (V)x[e]; };
+    COL_LOOP_BEGIN
+        Stencil<V> w;
+        coef.weights(d, c, i, j, k, w);
+        y[c] = (double)(w.D * ld(c) - nb_sum(d, w, c, i, j, k, ld));
+    COL_LOOP_END
+}
+
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_jacobi(Dims d, Coef coef, int kc,
+                                                   const double* __restrict__ r,
+                                                   double* __restrict__ z) {
+    COL_LOOP_BEGIN
+        Stencil<V> w;
+        coef.weights(d, c, i, j, k, w);
+        z[c] = (double)((V)r[c] * inv_diag<V, Coef>(coef, c, w));
+    COL_LOOP_END
+}
+
+// ------------------------------------------------------------------ PCG passes
+// init: z = D^{-1} r, rz = r.z, rr0 = r.r; stop2 = tol2 * (rel_to_b ? bb : rr0).
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_cg_init(Dims d, Coef coef, int kc,
+                                                    const V* __restrict__ r, V* __restrict__ z,
+                                                    Scalars* sc, double* partials, double tol2,
+                                                    int rel_to_b, int max_iter) {
+    __shared__ double smem[64];
+    V rz = 0, rr = 0;
+    COL_LOOP_BEGIN
+        Stencil<V> w;
+        coef.weights(d, c, i, j, k, w);
+        const V rc = r[c];
+        const V zc = rc * inv_diag<V, Coef>(coef, c, w);
+        z[c] = zc;
+        rz += rc * zc;
+        rr += rc * rc;
+    COL_LOOP_END
+    double v[2] = {(double)rz, (double)rr}, tot[2];
+    if (grid_sum<2>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            sc->rz = tot[0];
+            sc->rr = tot[1];
+            sc->rr0 = tot[1];
+            sc->beta = 0.0;
+            sc->alpha = 0.0;
+            sc->iter = 0;
+            sc->max_iter = max_iter;
+            sc->stop2 = tol2 * (rel_to_b ? sc->bb : tot[1]);
+            sc->done = (tot[1] <= sc->stop2) ? CONVERGED : RUNNING;
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) sc->done = BREAKDOWN;
+        }
+    }
+}
+
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_cg_a(Dims d, Coef coef, int kc,
+                                                 const V* __restrict__ z,
+                                                 const V* __restrict__ p_in,
+                                                 V* __restrict__ p_out, Scalars* sc,
+                                                 double* partials) {
+    __shared__ double smem[64];
+    if (sc->done) return;
+    const V beta = (V)sc->beta;
+    auto pn = [&](int e) { return z[e] + beta * p_in[e]; };
+    V acc = 0;
+    COL_LOOP_BEGIN
+        Stencil<V> w;
+        coef.weights(d, c, i, j, k, w);
+        const V pc = pn(c);
+        const V q = w.D * pc - nb_sum(d, w, c, i, j, k, pn);
+        acc += pc * q;
+        p_out[c] = pc;
+    COL_LOOP_END
+    double v[1] = {(double)acc}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double pq = tot[0];
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                sc->done = BREAKDOWN;
+            } else {
+                sc->pq = pq;
+                sc->alpha = sc->rz / pq;
+            }
+        }
+    }
+}
+
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_cg_b(Dims d, Coef coef, int kc,
+                                                 const V* __restrict__ p, V* __restrict__ x,
+                                                 V* __restrict__ r, V* __restrict__ z,
+                                                 Scalars* sc, double* partials) {
+    __shared__ double smem[64];
+    if (sc->done) return;
+    const V alpha = (V)sc->alpha;
+    auto ld = [&](int e) { return p[e]; };
+    V rz = 0, rr = 0;
+    COL_LOOP_BEGIN
+        Stencil<V> w;
+        coef.weights(d, c, i, j, k, w);
+        const V pc = p[c];
+        const V q = w.D * pc - nb_sum(d, w, c, i, j, k, ld);
+        x[c] += alpha * pc;
+        const V rn = r[c] - alpha * q;
+        const V zn = rn * inv_diag<V, Coef>(coef, c, w);
+        r[c] = rn;
+        z[c] = zn;
+        rz += rn * zn;
+        rr += rn * rn;
+    COL_LOOP_END
+    double v[2] = {(double)rz, (double)rr}, tot[2];
+    if (grid_sum<2>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double rz_new = tot[0], rr_new = tot[1];
+            sc->iter += 1;
+            sc->rr = rr_new;
+            if (!isfinite(rz_new) || !isfinite(rr_new) || rz_new < 0.0) {
+                sc->done = BREAKDOWN;
+            } else if (rr_new <= sc->stop2) {
+                sc->done = CONVERGED;
+            } else if (sc->iter >= sc->max_iter) {
+                sc->done = CAPPED;
+            } else {
+                sc->beta = rz_new / sc->rz;
+                sc->rz = rz_new;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host launchers
+std::atomic<unsigned long long> g_kernel_launches{0};
+static inline void counted(int k) { g_kernel_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
+static inline dim3 grid_of(const Dims& d, int kc) {
+    return dim3((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, (d.nz + kc - 1) / kc);
+}
+static inline unsigned blocks1d(long long n) { return (unsigned)((n + 255) / 256); }
+
+void launch_setup(const Dims& d, const double* F, double ra, double rw, double* bx, double* by,
+                  double* bz, double* diag, double* dinv, float* eta32, __nv_bfloat16* eta16,
+                  cudaStream_t st) {
+    k_setup_faces<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, eta32, eta16);
+    k_setup_diag<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, diag, dinv);
+    counted(2);
+}
+
+void launch_scale(long long n, const double* s, double a, double* b, cudaStream_t st) {
+    k_scale<<<blocks1d(n), 256, 0, st>>>(n, s, a, b);
+    counted(1);
+}
+
+void launch_update64(long long n, double* x, const float* dlt, cudaStream_t st) {
+    k_update64<<<blocks1d(n), 256, 0, st>>>(n, x, dlt);
+    counted(1);
+}
+
+void launch_narrow_f32(long long n, const double* a, float* b, cudaStream_t st) {
+    k_narrow<float><<<blocks1d(n), 256, 0, st>>>(n, a, b);
+    counted(1);
+}
+
+void launch_residual64(const Dims& d, int kc, const CoefFaces64& c, const double* b,
+                       const double* x, double* r, Scalars* sc, double* part, cudaStream_t st) {
+    k_residual64<double><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, b, x, r, sc, part);
+    counted(1);
+}
+
+void launch_residual64_f32(const Dims& d, int kc, const CoefFaces64& c, const double* b,
+                           const double* x, float* r, Scalars* sc, double* part, cudaStream_t st) {
+    k_residual64<float><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, b, x, r, sc, part);
+    counted(1);
+}
+
+template <typename V, typename Coef>
+void launch_apply(const Dims& d, int kc, const Coef& c, const double* x, double* y,
+                  cudaStream_t st) {
+    k_apply<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, x, y);
+    counted(1);
+}
+
+template <typename V, typename Coef>
+void launch_jacobi(const Dims& d, int kc, const Coef& c, const double* r, double* z,
+                   cudaStream_t st) {
+    k_jacobi<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, r, z);
+    counted(1);
+}
+
+template <typename V, typename Coef>
+void launch_cg_init(const Dims& d, int kc, const Coef& c, const V* r, V* z, Scalars* sc,
+                    double* part, double tol2, int rel_to_b, int max_iter, cudaStream_t st) {
+    k_cg_init<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, r, z, sc, part, tol2,
+                                                                rel_to_b, max_iter);
+    counted(1);
+}
+
+template <typename V, typename Coef>
+void launch_cg_a(const Dims& d, int kc, const Coef& c, const V* z, const V* p_in, V* p_out,
+                 Scalars* sc, double* part, cudaStream_t st) {
+    k_cg_a<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
+    counted(1);
+}
+
+template <typename V, typename Coef>
+void launch_cg_b(const Dims& d, int kc, const Coef& c, const V* p, V* x, V* r, V* z,
+                 Scalars* sc, double* part, cudaStream_t st) {
+    k_cg_b<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, p, x, r, z, sc, part);
+    counted(1);
+}
+
+#define INSTANTIATE(V, C)                                                                   \
+    template void launch_apply<V, C>(const Dims&, int, const C&, const double*, double*,     \
+                                     cudaStream_t);                                         \
+    template void launch_jacobi<V, C>(const Dims&, int, const C&, const double*, double*,    \
+                                      cudaStream_t);                                        \
+    template void launch_cg_init<V, C>(const Dims&, int, const C&, const V*, V*, Scalars*,   \
+                                       double*, double, int, int, cudaStream_t);            \
+    template void launch_cg_a<V, C>(const Dims&, int, const C&, const V*, const V*, V*,     \
+                                    Scalars*, double*, cudaStream_t);                       \
+    template void launch_cg_b<V, C>(const Dims&, int, const C&, const V*, V*, V*, V*,       \
+                                    Scalars*, double*, cudaStream_t);
+
+INSTANTIATE(double, CoefFaces64)
+INSTANTIATE(float, CoefEta<float>)
+INSTANTIATE(float, CoefEta<__nv_bfloat16>)
+
+}  // namespace pcg

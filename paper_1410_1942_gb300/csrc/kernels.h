@@ -1,0 +1,42 @@
+// kernels.h -- host-side launchers of the libpoisson kernels (see kernels.cu).
+#pragma once
+
+#include "internal.cuh"
+
+#include <atomic>
+
+namespace pcg {
+
+constexpr int TX = 32;  // threads (cells) per tile along x
+constexpr int TY = 8;   // ... along y
+
+void launch_setup(const Dims& d, const double* F, double ra, double rw, double* bx, double* by,
+                  double* bz, double* diag, double* dinv, float* eta32, __nv_bfloat16* eta16,
+                  cudaStream_t st);
+void launch_scale(long long n, const double* s, double a, double* b, cudaStream_t st);
+void launch_update64(long long n, double* x, const float* dlt, cudaStream_t st);
+void launch_narrow_f32(long long n, const double* a, float* b, cudaStream_t st);
+void launch_residual64(const Dims& d, int kc, const CoefFaces64& c, const double* b,
+                       const double* x, double* r, Scalars* sc, double* part, cudaStream_t st);
+void launch_residual64_f32(const Dims& d, int kc, const CoefFaces64& c, const double* b,
+                           const double* x, float* r, Scalars* sc, double* part, cudaStream_t st);
+
+template <typename V, typename Coef>
+void launch_apply(const Dims& d, int kc, const Coef& c, const double* x, double* y,
+                  cudaStream_t st);
+template <typename V, typename Coef>
+void launch_jacobi(const Dims& d, int kc, const Coef& c, const double* r, double* z,
+                   cudaStream_t st);
+template <typename V, typename Coef>
+void launch_cg_init(const Dims& d, int kc, const Coef& c, const V* r, V* z, Scalars* sc,
+                    double* part, double tol2, int rel_to_b, int max_iter, cudaStream_t st);
+template <typename V, typename Coef>
+void launch_cg_a(const Dims& d, int kc, const Coef& c, const V* z, const V* p_in, V* p_out,
+                 Scalars* sc, double* part, cudaStream_t st);
+template <typename V, typename Coef>
+void launch_cg_b(const Dims& d, int kc, const Coef& c, const V* p, V* x, V* r, V* z,
+                 Scalars* sc, double* part, cudaStream_t st);
+
+extern std::atomic<unsigned long long> g_kernel_launches;
+
+}  // namespace pcg
