@@ -66,7 +66,10 @@ typedef struct {
     int max_iters;     /* cap on total CG iterations of one solve (default 20000)                  */
     double inner_tol;  /* FP32 inner solve: relative residual reduction per refinement step
                           (default 1e-4; ignored by POISSON_FP64)                                  */
-    int tile;          /* stencil tile variant; 0 = the library's choice (autotuned per shape)     */
+    int tile;          /* FP32 inner-solve kernels: 0 = TMA plane-marching kernels with the tile
+                          height and z-chunk autotuned per shape (when nx % 8 == 0, else the
+                          column kernels); 4, 8, 16 = marching kernels with that tile height;
+                          -1 = column kernels (plain loads) (default 0)                         */
     void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream                 */
 } poisson_opts;
 

@@ -1,7 +1,10 @@
 // capi.cu -- the C ABI of libpoisson (declared in include/poisson.h): handles, operator set-up,
 // the single-solve drivers (plain FP64 PCG; FP32 inner PCG inside FP64 iterative refinement)
 // and the operator / preconditioner entry points used to check the kernels one by one.
+#include <algorithm>
 #include <chrono>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -12,6 +15,7 @@
 #include "poisson.h"
 #include "kernels.h"
 #include "capi_internal.h"
+#include "march.h"
 
 using namespace pcg;
 
@@ -79,6 +83,123 @@ static int choose_kc(const Dims& d) {
     return (int)kc;
 }
 
+// ------------------------------------------------------------------ march kernel tuning
+// Candidate (tile height, z-chunk) pairs: chunks sized for one or two full waves of resident
+// CTAs, and whole columns.  Each candidate's phase A and phase B are timed on the handle's own
+// buffers (zeroed; the scalars reset before every launch) and the fastest pair is kept; the
+// choice is cached per shape and coefficient type.
+struct TuneKey {
+    int nx, ny, nz, bf16;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(nx, ny, nz, bf16) < std::tie(o.nx, o.ny, o.nz, o.bf16);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tuned;
+
+static int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+static int kc_for(const Dims& d, int ty, int waves, bool bf16) {
+    const long long tiles = (long long)((d.nx + 31) / 32) * ((d.ny + ty - 1) / ty);
+    const int occ = std::min(march_occupancy(ty, bf16, true), march_occupancy(ty, bf16, false));
+    long long target = (long long)waves * occ * num_sms();
+    long long chunks = std::max(1LL, (target + tiles - 1) / tiles);
+    int kc = (int)((d.nz + chunks - 1) / chunks);
+    return std::max(2, std::min(kc, d.nz));
+}
+
+static int setup_march(poisson_t* H) {
+    const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
+    const void* eta = bf16 ? (const void*)H->eta16 : (const void*)H->eta32;
+    const Dims d = H->d;
+    auto maps_for = [&](int ty) {
+        return march_maps(&H->maps, d, ty, H->z32, H->p32a, H->p32b, eta, bf16, H->d32, H->r32);
+    };
+    const int forced = H->opts.tile;
+    if (forced == 4 || forced == 8 || forced == 16) {
+        if (!maps_for(forced)) return POISSON_OK;  // stay on the column kernels
+        H->march = true;
+        H->march_ty = forced;
+        H->march_kc = kc_for(d, forced, 1, bf16);
+        return POISSON_OK;
+    }
+    const TuneKey key{d.nx, d.ny, d.nz, bf16 ? 1 : 0};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            if (!maps_for(it->second.first)) return POISSON_OK;
+            H->march = true;
+            H->march_ty = it->second.first;
+            H->march_kc = it->second.second;
+            return POISSON_OK;
+        }
+    }
+    // scratch partials big enough for every candidate
+    double* part = nullptr;
+    if (dalloc(&part, 2 * march_blocks(d, 4, 2) + 64) != POISSON_OK) return POISSON_ENOMEM;
+    const size_t b32 = sizeof(float) * (size_t)d.n;
+    cudaStream_t st = H->st;
+    float* vecs[] = {H->z32, H->p32a, H->p32b, H->d32, H->r32};
+    for (float* v : vecs) cudaMemsetAsync(v, 0, b32, st);
+    cudaMemsetAsync(bf16 ? (void*)H->eta16 : (void*)H->eta32, 0, bf16 ? b32 / 2 : b32, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_ty = 0, best_kc = 0;
+    for (int ty : {4, 8, 16}) {
+        if (!maps_for(ty)) continue;
+        int kcs[3] = {kc_for(d, ty, 1, bf16), kc_for(d, ty, 2, bf16), d.nz};
+        for (int kc : kcs) {
+            float tot = 0.f;
+            for (int side = 0; side < 2; ++side) {
+                float t[3];
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaMemsetAsync(H->sc, 0, sizeof(Scalars), st);
+                    cudaEventRecord(e0, st);
+                    if (side == 0)
+                        launch_march_a(d, kc, H->maps, true, H->p32b, H->sc, part, st);
+                    else
+                        launch_march_b(d, kc, H->maps, true, H->d32, H->r32, H->z32, H->sc, part, st);
+                    cudaEventRecord(e1, st);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&t[rep], e0, e1);
+                }
+                std::sort(t, t + 3);
+                tot += t[1];
+            }
+            if (cudaGetLastError() != cudaSuccess) continue;
+            if (tot < best) {
+                best = tot;
+                best_ty = ty;
+                best_kc = kc;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    dfree(part);
+    cudaMemsetAsync(H->sc, 0, sizeof(Scalars), st);
+    if (!best_ty || !maps_for(best_ty)) return POISSON_OK;
+    H->march = true;
+    H->march_ty = best_ty;
+    H->march_kc = best_kc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = {best_ty, best_kc};
+    return POISSON_OK;
+}
+
 static void free_state(poisson_t* H) {
     void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->eta32, H->eta16, H->x64,
                     H->b64, H->r64, H->z64, H->p64a, H->p64b, H->d32, H->r32, H->z32,
@@ -102,6 +223,8 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (o.precond != POISSON_JACOBI && o.precond != POISSON_RBSSOR) return POISSON_EINVAL;
     if (!(o.omega > 0.0 && o.omega < 2.0)) return POISSON_EINVAL;
     if (o.max_iters <= 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return POISSON_EINVAL;
+    if (o.tile != 0 && o.tile != -1 && o.tile != 4 && o.tile != 8 && o.tile != 16)
+        return POISSON_EINVAL;
 
     poisson_t* H = new (std::nothrow) poisson_t();
     if (!H) return POISSON_ENOMEM;
@@ -128,6 +251,10 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
         A(dalloc(&H->p32a, N)); A(dalloc(&H->p32b, N));
     }
     A(dalloc(&H->sc, 1));
+    if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.tile != -1 && march_supported(H->d))
+        A(setup_march(H));
+    if (rc == POISSON_OK && H->march)
+        H->nblocks = std::max(H->nblocks, march_blocks(H->d, H->march_ty, H->march_kc));
     A(dalloc(&H->partials, 2 * H->nblocks + 64));
     if (rc == POISSON_OK && cudaMallocHost((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
         cudaGetLastError();
@@ -199,25 +326,25 @@ static void prof_add(poisson_t* H, int cls, cudaEvent_t a, cudaEvent_t b) {
 
 // ------------------------------------------------------------------ inner CG loop
 // Queues chunks of CG_CHUNK iterations; reads the scalars of chunk n while chunk n+1 runs.
-template <typename V, typename Coef>
-static int cg_loop(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* pa, V* pb, double tol2,
-                   int rel_to_b, int max_iter, Scalars* result) {
+// pass_a(p_in_is_a) and pass_b(p_is_a) launch one CG phase each on the handle's stream.
+template <typename V, typename Coef, typename PassA, typename PassB>
+static int cg_loop(poisson_t* H, const Coef& coef, V* r, V* z, double tol2, int rel_to_b,
+                   int max_iter, Scalars* result, PassA pass_a, PassB pass_b) {
     const int K = CG_CHUNK;
     cudaStream_t st = H->st;
     const bool prof = H->prof_on;
     launch_cg_init<V, Coef>(H->d, H->kc, coef, r, z, H->sc, H->partials, tol2, rel_to_b, max_iter,
                             st);
-    V* p_in = pa;
-    V* p_out = pb;
+    bool in_is_a = true;
     auto enqueue_chunk = [&](int slot) -> int {
         cudaEvent_t* ev = prof ? &H->prof_ev[slot * PROF_PER_CHUNK] : nullptr;
         for (int q = 0; q < K; ++q) {
             if (prof) CK(cudaEventRecord(ev[3 * q], st));
-            launch_cg_a<V, Coef>(H->d, H->kc, coef, z, p_in, p_out, H->sc, H->partials, st);
+            pass_a(in_is_a);
             if (prof) CK(cudaEventRecord(ev[3 * q + 1], st));
-            launch_cg_b<V, Coef>(H->d, H->kc, coef, p_out, x, r, z, H->sc, H->partials, st);
+            pass_b(!in_is_a);
             if (prof) CK(cudaEventRecord(ev[3 * q + 2], st));
-            std::swap(p_in, p_out);
+            in_is_a = !in_is_a;
         }
         CK(cudaGetLastError());
         CK(cudaMemcpyAsync(&H->sc_host[slot], H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, st));
@@ -261,6 +388,38 @@ static int cg_loop(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* pa, V* p
     }
 }
 
+// Column-kernel passes (any shape, any precision).
+template <typename V, typename Coef>
+static int cg_loop_columns(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* pa, V* pb,
+                           double tol2, int rel_to_b, int max_iter, Scalars* result) {
+    const Dims d = H->d;
+    const int kc = H->kc;
+    cudaStream_t st = H->st;
+    auto A = [=](bool in_a) {
+        launch_cg_a<V, Coef>(d, kc, coef, z, in_a ? pa : pb, in_a ? pb : pa, H->sc, H->partials, st);
+    };
+    auto B = [=](bool p_a) {
+        launch_cg_b<V, Coef>(d, kc, coef, p_a ? pa : pb, x, r, z, H->sc, H->partials, st);
+    };
+    return cg_loop<V, Coef>(H, coef, r, z, tol2, rel_to_b, max_iter, result, A, B);
+}
+
+// TMA plane-marching passes (FP32 inner solve).
+template <typename Coef>
+static int cg_loop_march(poisson_t* H, const Coef& coef, double tol2, int max_iter,
+                         Scalars* result) {
+    const Dims d = H->d;
+    const int kc = H->march_kc;
+    cudaStream_t st = H->st;
+    const MarchMaps* mm = &H->maps;
+    float *pa = H->p32a, *pb = H->p32b, *x = H->d32, *r = H->r32, *z = H->z32;
+    auto A = [=](bool in_a) {
+        launch_march_a(d, kc, *mm, in_a, in_a ? pb : pa, H->sc, H->partials, st);
+    };
+    auto B = [=](bool p_a) { launch_march_b(d, kc, *mm, p_a, x, r, z, H->sc, H->partials, st); };
+    return cg_loop<float, Coef>(H, coef, r, z, tol2, 0, max_iter, result, A, B);
+}
+
 // Reads the scalars after a residual kernel (and books its time when profiling).
 static int read_scalars(poisson_t* H, Scalars* s) {
     CK(cudaMemcpyAsync(&H->sc_host[0], H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, H->st));
@@ -299,10 +458,11 @@ static int solve_fp64(poisson_t* H, double tol, int* outer, int* inner, double* 
         if (total >= H->opts.max_iters || restarts >= 8) { status = POISSON_ENOTCONV; break; }
         CK(cudaMemsetAsync(H->p64a, 0, bytes, H->st));
         Scalars res;
-        rc = cg_loop<double, CoefFaces64>(H, c, H->x64, H->r64, H->z64, H->p64a, H->p64b,
-                                          tol * tol, 1, H->opts.max_iters - total, &res);
+        rc = cg_loop_columns<double, CoefFaces64>(H, c, H->x64, H->r64, H->z64, H->p64a, H->p64b,
+                                                  tol * tol, 1, H->opts.max_iters - total, &res);
         if (rc) return rc;
         total += res.iter;
+        if (res.done == TIMEDOUT) { status = POISSON_ETIMEOUT; break; }
         if (res.done == BREAKDOWN && res.iter == 0) { status = POISSON_EBREAKDOWN; break; }
     }
     *outer = restarts + 1;
@@ -348,12 +508,17 @@ static int solve_mixed(poisson_t* H, const E* eta, double tol, int* outer, int* 
         CK(cudaMemsetAsync(H->d32, 0, bytes32, H->st));
         CK(cudaMemsetAsync(H->p32a, 0, bytes32, H->st));
         Scalars res;
-        rc = cg_loop<float, CoefEta<E>>(H, c32, H->d32, H->r32, H->z32, H->p32a, H->p32b,
-                                        target * target, 0, H->opts.max_iters - total, &res);
+        if (H->march)
+            rc = cg_loop_march<CoefEta<E>>(H, c32, target * target, H->opts.max_iters - total, &res);
+        else
+            rc = cg_loop_columns<float, CoefEta<E>>(H, c32, H->d32, H->r32, H->z32, H->p32a,
+                                                    H->p32b, target * target, 0,
+                                                    H->opts.max_iters - total, &res);
         if (rc) return rc;
         total += res.iter;
         if (res.iter > 0) launch_update64(H->d.n, H->x64, H->d32, H->st);
         CK(cudaGetLastError());
+        if (res.done == TIMEDOUT) { status = POISSON_ETIMEOUT; break; }
         if (res.done == BREAKDOWN && res.iter == 0) { status = POISSON_EBREAKDOWN; break; }
     }
     *outer = k + 1;

@@ -8,6 +8,7 @@
 
 #include "poisson.h"
 #include "internal.cuh"
+#include "march.h"
 
 struct poisson_s {
     pcg::Dims d{};
@@ -37,6 +38,11 @@ struct poisson_s {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // staging for the checking entry points when given host arrays
     double *io_a = nullptr, *io_b = nullptr;
+    // TMA plane-marching kernels for the FP32 inner solve (when the shape allows them)
+    bool march = false;
+    int march_ty = 8;
+    int march_kc = 8;
+    pcg::MarchMaps maps{};
     // poisson_profile: event pairs around the timed kernels, accumulated times
     bool prof_on = false;
     poisson_kernel_times prof{};

@@ -38,11 +38,11 @@ struct Scalars {
     double bb;      // (b, b) -- written by the residual reduction
     int iter;       // CG iterations done in this solve
     int max_iter;   // cap
-    int done;       // 0 running, 1 converged, 2 breakdown, 3 iteration cap
+    int done;       // 0 running, 1 converged, 2 breakdown, 3 iteration cap, 4 wait timed out
     unsigned int ticket;  // arrivals of the current reduction
 };
 
-enum Done { RUNNING = 0, CONVERGED = 1, BREAKDOWN = 2, CAPPED = 3 };
+enum Done { RUNNING = 0, CONVERGED = 1, BREAKDOWN = 2, CAPPED = 3, TIMEDOUT = 4 };
 
 // Hardware reciprocal (MUFU), flush-to-zero: deterministic for a given input.
 __device__ __forceinline__ float rcp_approx(float x) {

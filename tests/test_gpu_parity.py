@@ -114,6 +114,23 @@ def test_solve_matches_oracle(name, prec):
         assert st["outer_iters"] >= 2
 
 
+@pytest.mark.parametrize("tile", [-1, 0, 4, 8, 16])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("shape", [(96, 48, 40), (40, 23, 19), (64, 16, 1), (8, 9, 33)])
+def test_kernel_variants_match_oracle(tile, prec, shape):
+    """Every inner-solve kernel family and tile height, on shapes with ragged x and y tiles,
+    a single plane and a thin column, against both acceptance criteria."""
+    c = inputs.flat_case(*shape, seed=9, tol=1e-10)
+    op = oracle.operator(c.F)
+    b = oracle.rhs(c.s, c.grid.h)
+    xref = oracle.pcg(op, b, tol=REF_TOL, precond="ssor").x
+    with solver(c, prec, tile=tile) as s:
+        p = np.zeros(c.grid.shape)
+        rc, st = s.solve(c.s, p, c.tol)
+    assert rc == capi.OK
+    _check_solution(c, op, b, xref, p, st, c.tol)
+
+
 def test_device_and_host_arrays_give_identical_results():
     import torch
     c, _, _, _ = case("ragged")
