@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shape", type=int, nargs=3, default=(256, 128, 128),
+                    help="grid of the strut workload (profiling of smaller cases)")
+    ap.add_argument("--tile", type=int, default=0, help="FP32 kernel tile option (0 = autotuned)")
     return ap.parse_args()
 
 
@@ -237,14 +240,14 @@ def main():
     _build.build()
     capi.load()
 
-    case = inputs.strut_case(256, 128, 128, seed=args.seed + rank)
+    case = inputs.strut_case(*args.shape, seed=args.seed + rank)
     g = case.grid
     F_d = torch.from_numpy(case.F).to(dev)
     s_d = torch.from_numpy(case.s).to(dev)
     p_d = torch.zeros(g.shape, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision, precond=args.precond,
-                          stream=stream.cuda_stream)
+                          stream=stream.cuda_stream, tile=args.tile)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -312,7 +315,7 @@ def main():
         s_h = torch.from_numpy(case.s).pin_memory()
         p_h = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
         solver_h = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision,
-                                precond=args.precond, stream=stream.cuda_stream)
+                                precond=args.precond, stream=stream.cuda_stream, tile=args.tile)
 
         def step_e2e():
             p_h.zero_()
@@ -353,7 +356,8 @@ def main():
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "cells": g.n, "precision": args.precision,
+            "config": {"workload": WORKLOAD if tuple(args.shape) == (256, 128, 128)
+                        else "strut %dx%dx%d (profiling case)" % tuple(args.shape), "cells": g.n, "precision": args.precision,
                        "precond": args.precond, "tol": case.tol,
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
