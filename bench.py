@@ -361,6 +361,7 @@ def main():
                        "precond": args.precond, "tol": case.tol,
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "kernels": solver.describe(),
                        "cg_iters_per_step": iters / args.steps,
                        "outer_iters_per_step": outer / args.steps,
                        "max_rel_residual": max(rels)},

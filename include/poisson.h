@@ -66,10 +66,12 @@ typedef struct {
     int max_iters;     /* cap on total CG iterations of one solve (default 20000)                  */
     double inner_tol;  /* FP32 inner solve: relative residual reduction per refinement step
                           (default 1e-4; ignored by POISSON_FP64)                                  */
-    int tile;          /* FP32 inner-solve kernels: 0 = TMA plane-marching kernels with the tile
-                          height and z-chunk autotuned per shape (when nx % 8 == 0, else the
-                          column kernels); 4, 8, 16 = marching kernels with that tile height;
-                          -1 = column kernels (plain loads) (default 0)                         */
+    int tile;          /* FP32 inner-solve kernels.  0 = TMA plane-marching kernels, variant and
+                          z-chunk autotuned per shape (when nx % 8 == 0, else the column
+                          kernels); -1 = column kernels (plain loads); 1000 CX + 100 CY + T =
+                          marching kernels with T rows of 32 threads, each thread owning CX x CY
+                          cells (tile 32 CX x CY T): 1104, 1108, 1116, 2202, 2204, 2208, 2108,
+                          1208 (default 0)                                                       */
     void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream                 */
 } poisson_opts;
 
@@ -160,6 +162,10 @@ int poisson_profile(poisson_t* h, int enable);
 
 /* Copy out the accumulated per-class launch counts and event times (since poisson_profile). */
 int poisson_profile_read(poisson_t* h, poisson_kernel_times* out);
+
+/* Write a one-line description of the handle's kernel choice (family, tile, z-chunk) into buf
+ * (NUL-terminated, at most len bytes). */
+int poisson_describe(poisson_t* h, char* buf, int len);
 
 /* Human-readable name of a status code. */
 const char* poisson_strerror(int status);

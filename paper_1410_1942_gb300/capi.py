@@ -29,7 +29,7 @@ PRECOND = {"jacobi": JACOBI, "rbssor": RBSSOR, "ssor": RBSSOR}
 EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson_set_density",
            "poisson_solve", "poisson_apply", "poisson_precond_apply", "poisson_get_operator",
            "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
-           "poisson_profile_read", "poisson_strerror", "poisson_version"]
+           "poisson_profile_read", "poisson_describe", "poisson_strerror", "poisson_version"]
 K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER = 0, 1, 2, 3
 K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other"]
 
@@ -95,7 +95,8 @@ def load(path=None):
     lib.poisson_kernel_launches.restype = ctypes.c_uint64
     lib.poisson_profile.argtypes = [vp, i]
     lib.poisson_profile_read.argtypes = [vp, ctypes.POINTER(KernelTimes)]
-    for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read"]:
+    lib.poisson_describe.argtypes = [vp, ctypes.c_char_p, i]
+    for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read", "poisson_describe"]:
         getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -201,6 +202,11 @@ class Poisson:
         t = KernelTimes()
         _check(load().poisson_profile_read(self._h, ctypes.byref(t)), "poisson_profile_read")
         return t.as_dict()
+
+    def describe(self):
+        buf = ctypes.create_string_buffer(256)
+        _check(load().poisson_describe(self._h, buf, 256), "poisson_describe")
+        return buf.value.decode()
 
     def get_operator(self, bx=None, by=None, bz=None, diag=None):
         _check(load().poisson_get_operator(self._h, _addr(bx), _addr(by), _addr(bz), _addr(diag)),

@@ -108,9 +108,11 @@ static int num_sms() {
     return n;
 }
 
-static int kc_for(const Dims& d, int ty, int waves, bool bf16) {
-    const long long tiles = (long long)((d.nx + 31) / 32) * ((d.ny + ty - 1) / ty);
-    const int occ = std::min(march_occupancy(ty, bf16, true), march_occupancy(ty, bf16, false));
+static int kc_for(const Dims& d, int variant, int waves, bool bf16) {
+    const MarchVariant v = march_variant(variant);
+    const long long tiles = (long long)((d.nx + v.width - 1) / v.width) *
+                            ((d.ny + v.height - 1) / v.height);
+    const int occ = march_occupancy(variant, bf16);
     long long target = (long long)waves * occ * num_sms();
     long long chunks = std::max(1LL, (target + tiles - 1) / tiles);
     int kc = (int)((d.nz + chunks - 1) / chunks);
@@ -121,15 +123,16 @@ static int setup_march(poisson_t* H) {
     const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
     const void* eta = bf16 ? (const void*)H->eta16 : (const void*)H->eta32;
     const Dims d = H->d;
-    auto maps_for = [&](int ty) {
-        return march_maps(&H->maps, d, ty, H->z32, H->p32a, H->p32b, eta, bf16, H->d32, H->r32);
+    auto maps_for = [&](int var) {
+        return march_maps(&H->maps, d, var, H->z32, H->p32a, H->p32b, eta, bf16, H->d32, H->r32);
     };
     const int forced = H->opts.tile;
-    if (forced == 4 || forced == 8 || forced == 16) {
-        if (!maps_for(forced)) return POISSON_OK;  // stay on the column kernels
+    if (forced > 0) {
+        const int var = march_find_variant(forced / 1000, (forced / 100) % 10, forced % 100);
+        if (var < 0 || !maps_for(var)) return POISSON_OK;  // stay on the column kernels
         H->march = true;
-        H->march_ty = forced;
-        H->march_kc = kc_for(d, forced, 1, bf16);
+        H->march_variant = var;
+        H->march_kc = kc_for(d, var, 1, bf16);
         return POISSON_OK;
     }
     const TuneKey key{d.nx, d.ny, d.nz, bf16 ? 1 : 0};
@@ -139,14 +142,14 @@ static int setup_march(poisson_t* H) {
         if (it != g_tuned.end()) {
             if (!maps_for(it->second.first)) return POISSON_OK;
             H->march = true;
-            H->march_ty = it->second.first;
+            H->march_variant = it->second.first;
             H->march_kc = it->second.second;
             return POISSON_OK;
         }
     }
-    // scratch partials big enough for every candidate
+    // scratch partials big enough for every candidate (chunks of at least 2 planes)
     double* part = nullptr;
-    if (dalloc(&part, 2 * march_blocks(d, 4, 2) + 64) != POISSON_OK) return POISSON_ENOMEM;
+    if (dalloc(&part, 2 * march_max_blocks(d, 2) + 64) != POISSON_OK) return POISSON_ENOMEM;
     const size_t b32 = sizeof(float) * (size_t)d.n;
     cudaStream_t st = H->st;
     float* vecs[] = {H->z32, H->p32a, H->p32b, H->d32, H->r32};
@@ -156,10 +159,10 @@ static int setup_march(poisson_t* H) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int best_ty = 0, best_kc = 0;
-    for (int ty : {4, 8, 16}) {
-        if (!maps_for(ty)) continue;
-        int kcs[3] = {kc_for(d, ty, 1, bf16), kc_for(d, ty, 2, bf16), d.nz};
+    int best_var = -1, best_kc = 0;
+    for (int var = 0; var < march_variant_count(); ++var) {
+        if (!maps_for(var)) continue;
+        int kcs[3] = {kc_for(d, var, 1, bf16), kc_for(d, var, 2, bf16), d.nz};
         for (int kc : kcs) {
             float tot = 0.f;
             for (int side = 0; side < 2; ++side) {
@@ -181,7 +184,7 @@ static int setup_march(poisson_t* H) {
             if (cudaGetLastError() != cudaSuccess) continue;
             if (tot < best) {
                 best = tot;
-                best_ty = ty;
+                best_var = var;
                 best_kc = kc;
             }
         }
@@ -191,12 +194,12 @@ static int setup_march(poisson_t* H) {
     cudaStreamSynchronize(st);
     dfree(part);
     cudaMemsetAsync(H->sc, 0, sizeof(Scalars), st);
-    if (!best_ty || !maps_for(best_ty)) return POISSON_OK;
+    if (best_var < 0 || !maps_for(best_var)) return POISSON_OK;
     H->march = true;
-    H->march_ty = best_ty;
+    H->march_variant = best_var;
     H->march_kc = best_kc;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = {best_ty, best_kc};
+    g_tuned[key] = {best_var, best_kc};
     return POISSON_OK;
 }
 
@@ -223,7 +226,8 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (o.precond != POISSON_JACOBI && o.precond != POISSON_RBSSOR) return POISSON_EINVAL;
     if (!(o.omega > 0.0 && o.omega < 2.0)) return POISSON_EINVAL;
     if (o.max_iters <= 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return POISSON_EINVAL;
-    if (o.tile != 0 && o.tile != -1 && o.tile != 4 && o.tile != 8 && o.tile != 16)
+    if (o.tile < -1 || (o.tile > 0 && march_find_variant(o.tile / 1000, (o.tile / 100) % 10,
+                                                          o.tile % 100) < 0))
         return POISSON_EINVAL;
 
     poisson_t* H = new (std::nothrow) poisson_t();
@@ -254,7 +258,7 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.tile != -1 && march_supported(H->d))
         A(setup_march(H));
     if (rc == POISSON_OK && H->march)
-        H->nblocks = std::max(H->nblocks, march_blocks(H->d, H->march_ty, H->march_kc));
+        H->nblocks = std::max(H->nblocks, march_blocks(H->d, H->march_variant, H->march_kc));
     A(dalloc(&H->partials, 2 * H->nblocks + 64));
     if (rc == POISSON_OK && cudaMallocHost((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
         cudaGetLastError();
@@ -691,6 +695,20 @@ extern "C" int poisson_profile(poisson_t* H, int enable) {
 extern "C" int poisson_profile_read(poisson_t* H, poisson_kernel_times* out) {
     if (!H || !out) return POISSON_EINVAL;
     *out = H->prof;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
+    if (!H || !buf || len <= 0) return POISSON_EINVAL;
+    const char* prec = H->opts.precision == POISSON_FP64 ? "fp64"
+                       : H->opts.precision == POISSON_FP32 ? "fp32" : "fp32/bf16-coef";
+    if (H->march) {
+        const MarchVariant v = march_variant(H->march_variant);
+        snprintf(buf, (size_t)len, "%s march tile=%d (%dx%d cells, %dx%d per thread) zchunk=%d",
+                 prec, 1000 * v.cx + 100 * v.cy + v.tyt, v.width, v.height, v.cx, v.cy, H->march_kc);
+    } else {
+        snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d", prec, TX, TY, H->kc);
+    }
     return POISSON_OK;
 }
 

@@ -40,7 +40,7 @@ struct poisson_s {
     double *io_a = nullptr, *io_b = nullptr;
     // TMA plane-marching kernels for the FP32 inner solve (when the shape allows them)
     bool march = false;
-    int march_ty = 8;
+    int march_variant = 0;
     int march_kc = 8;
     pcg::MarchMaps maps{};
     // poisson_profile: event pairs around the timed kernels, accumulated times

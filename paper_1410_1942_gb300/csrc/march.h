@@ -8,21 +8,29 @@
 
 namespace pcg {
 
-// Tensor maps of one FP32 inner solve: halo boxes (32+8) x (ty+2) x 1 for z, both p buffers and
-// eta (BF16: (32+16) x (ty+2)), centre boxes 32 x ty x 1 for x and r.
+// One kernel variant: 32 x tyt threads, each owning cx x cy cells; tile width x height cells.
+struct MarchVariant {
+    int id, cx, cy, tyt, width, height;
+};
+
+// Tensor maps of one FP32 inner solve for one variant: halo boxes (width+8) x (height+2) x 1
+// for z and both p buffers, (width+8 or +16 for BF16) x (height+2) for eta, centre boxes
+// width x height x 1 for x and r.
 struct MarchMaps {
     CUtensorMap z, pa, pb, eta, x, r;
-    int ty = 8;
+    int variant = 0;
     bool bf16 = false;
 };
 
 bool march_supported(const Dims& d);
-bool march_maps(MarchMaps* mm, const Dims& d, int ty, const float* z, const float* pa,
+int march_variant_count();
+MarchVariant march_variant(int id);
+int march_find_variant(int cx, int cy, int tyt);  // -1 if there is none
+bool march_maps(MarchMaps* mm, const Dims& d, int variant, const float* z, const float* pa,
                 const float* pb, const void* eta, bool bf16, const float* x, const float* r);
-int march_smem_a(int ty, bool bf16);
-int march_smem_b(int ty, bool bf16);
-int march_occupancy(int ty, bool bf16, bool a_side);
-size_t march_blocks(const Dims& d, int ty, int kchunk);
+int march_occupancy(int variant, bool bf16);       // resident CTAs per SM (min of both phases)
+size_t march_blocks(const Dims& d, int variant, int kchunk);
+size_t march_max_blocks(const Dims& d, int kchunk);
 
 // phase A: reads z and p_in (pa if pin_is_a else pb) with eta, writes p_out.
 void launch_march_a(const Dims& d, int kchunk, const MarchMaps& mm, bool pin_is_a, float* p_out,
