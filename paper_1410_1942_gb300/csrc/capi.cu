@@ -84,10 +84,9 @@ static int choose_kc(const Dims& d) {
 }
 
 // ------------------------------------------------------------------ march kernel tuning
-// Candidate (tile height, z-chunk) pairs: chunks sized for one or two full waves of resident
-// CTAs, and whole columns.  Each candidate's phase A and phase B are timed on the handle's own
-// buffers (zeroed; the scalars reset before every launch) and the fastest pair is kept; the
-// choice is cached per shape and coefficient type.
+// Every variant is tried on the handle's own buffers (zeroed; the scalars reset before every
+// launch) with a persistent grid of (resident CTAs per SM) x (SMs) CTAs, its phases A and B
+// timed with events, and the fastest kept; the choice is cached per shape and coefficient type.
 struct TuneKey {
     int nx, ny, nz, bf16;
     bool operator<(const TuneKey& o) const {
@@ -95,7 +94,7 @@ struct TuneKey {
     }
 };
 static std::mutex g_tune_mu;
-static std::map<TuneKey, std::pair<int, int>> g_tuned;
+static std::map<TuneKey, int> g_tuned;
 
 static int num_sms() {
     static int n = 0;
@@ -108,62 +107,43 @@ static int num_sms() {
     return n;
 }
 
-static int kc_for(const Dims& d, int variant, int waves, bool bf16) {
-    const MarchVariant v = march_variant(variant);
-    const long long tiles = (long long)((d.nx + v.width - 1) / v.width) *
-                            ((d.ny + v.height - 1) / v.height);
-    const int occ = march_occupancy(variant, bf16);
-    long long target = (long long)waves * occ * num_sms();
-    long long chunks = std::max(1LL, (target + tiles - 1) / tiles);
-    int kc = (int)((d.nz + chunks - 1) / chunks);
-    return std::max(2, std::min(kc, d.nz));
+static MarchSolve march_solve_of(poisson_t* H) {
+    const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
+    return MarchSolve{H->d, H->d32, H->r32, H->z32, H->p32a, H->p32b,
+                      bf16 ? (const void*)H->eta16 : (const void*)H->eta32, H->sc};
+}
+
+static int build_plan(poisson_t* H, int var) {
+    const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
+    const MarchSolve s = march_solve_of(H);
+    const int nctas = march_occupancy(var, bf16) * num_sms();
+    return march_plan_build(&H->plan, &s, 1, var, bf16, nctas, H->st);
 }
 
 static int setup_march(poisson_t* H) {
     const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
-    const void* eta = bf16 ? (const void*)H->eta16 : (const void*)H->eta32;
     const Dims d = H->d;
-    auto maps_for = [&](int var) {
-        return march_maps(&H->maps, d, var, H->z32, H->p32a, H->p32b, eta, bf16, H->d32, H->r32);
-    };
     const int forced = H->opts.tile;
+    int var = -1;
     if (forced > 0) {
-        const int var = march_find_variant(forced / 1000, (forced / 100) % 10, forced % 100);
-        if (var < 0 || !maps_for(var)) return POISSON_OK;  // stay on the column kernels
-        H->march = true;
-        H->march_variant = var;
-        H->march_kc = kc_for(d, var, 1, bf16);
-        return POISSON_OK;
-    }
-    const TuneKey key{d.nx, d.ny, d.nz, bf16 ? 1 : 0};
-    {
+        var = march_find_variant(forced / 1000, (forced / 100) % 10, forced % 100);
+    } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) {
-            if (!maps_for(it->second.first)) return POISSON_OK;
-            H->march = true;
-            H->march_variant = it->second.first;
-            H->march_kc = it->second.second;
-            return POISSON_OK;
-        }
+        auto it = g_tuned.find(TuneKey{d.nx, d.ny, d.nz, bf16 ? 1 : 0});
+        if (it != g_tuned.end()) var = it->second;
     }
-    // scratch partials big enough for every candidate (chunks of at least 2 planes)
-    double* part = nullptr;
-    if (dalloc(&part, 2 * march_max_blocks(d, 2) + 64) != POISSON_OK) return POISSON_ENOMEM;
-    const size_t b32 = sizeof(float) * (size_t)d.n;
-    cudaStream_t st = H->st;
-    float* vecs[] = {H->z32, H->p32a, H->p32b, H->d32, H->r32};
-    for (float* v : vecs) cudaMemsetAsync(v, 0, b32, st);
-    cudaMemsetAsync(bf16 ? (void*)H->eta16 : (void*)H->eta32, 0, bf16 ? b32 / 2 : b32, st);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best = 1e30f;
-    int best_var = -1, best_kc = 0;
-    for (int var = 0; var < march_variant_count(); ++var) {
-        if (!maps_for(var)) continue;
-        int kcs[3] = {kc_for(d, var, 1, bf16), kc_for(d, var, 2, bf16), d.nz};
-        for (int kc : kcs) {
+    if (var < 0 && forced <= 0) {
+        const size_t b32 = sizeof(float) * (size_t)d.n;
+        cudaStream_t st = H->st;
+        float* vecs[] = {H->z32, H->p32a, H->p32b, H->d32, H->r32};
+        for (float* v : vecs) cudaMemsetAsync(v, 0, b32, st);
+        cudaMemsetAsync(bf16 ? (void*)H->eta16 : (void*)H->eta32, 0, bf16 ? b32 / 2 : b32, st);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (int cand = 0; cand < march_variant_count(); ++cand) {
+            if (build_plan(H, cand) != 0) continue;
             float tot = 0.f;
             for (int side = 0; side < 2; ++side) {
                 float t[3];
@@ -171,9 +151,9 @@ static int setup_march(poisson_t* H) {
                     cudaMemsetAsync(H->sc, 0, sizeof(Scalars), st);
                     cudaEventRecord(e0, st);
                     if (side == 0)
-                        launch_march_a(d, kc, H->maps, true, H->p32b, H->sc, part, st);
+                        launch_march_a(H->plan, true, st);
                     else
-                        launch_march_b(d, kc, H->maps, true, H->d32, H->r32, H->z32, H->sc, part, st);
+                        launch_march_b(H->plan, true, st);
                     cudaEventRecord(e1, st);
                     cudaEventSynchronize(e1);
                     cudaEventElapsedTime(&t[rep], e0, e1);
@@ -184,22 +164,22 @@ static int setup_march(poisson_t* H) {
             if (cudaGetLastError() != cudaSuccess) continue;
             if (tot < best) {
                 best = tot;
-                best_var = var;
-                best_kc = kc;
+                var = cand;
             }
         }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaMemsetAsync(H->sc, 0, sizeof(Scalars), st);
+        cudaStreamSynchronize(st);
+        if (var >= 0) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[TuneKey{d.nx, d.ny, d.nz, bf16 ? 1 : 0}] = var;
+        }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaStreamSynchronize(st);
-    dfree(part);
-    cudaMemsetAsync(H->sc, 0, sizeof(Scalars), st);
-    if (best_var < 0 || !maps_for(best_var)) return POISSON_OK;
-    H->march = true;
-    H->march_variant = best_var;
-    H->march_kc = best_kc;
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[key] = {best_var, best_kc};
+    if (var < 0) return POISSON_OK;  // stay on the column kernels
+    const int rc = build_plan(H, var);
+    if (rc == -2) return POISSON_ENOMEM;
+    H->march = (rc == 0);
     return POISSON_OK;
 }
 
@@ -211,6 +191,7 @@ static void free_state(poisson_t* H) {
     if (H->sc_host) cudaFreeHost(H->sc_host);
     for (auto& e : H->ev) if (e) cudaEventDestroy(e);
     for (auto& e : H->prof_ev) if (e) cudaEventDestroy(e);
+    march_plan_free(&H->plan);
 }
 
 extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_opts* opts,
@@ -257,8 +238,6 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     A(dalloc(&H->sc, 1));
     if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.tile != -1 && march_supported(H->d))
         A(setup_march(H));
-    if (rc == POISSON_OK && H->march)
-        H->nblocks = std::max(H->nblocks, march_blocks(H->d, H->march_variant, H->march_kc));
     A(dalloc(&H->partials, 2 * H->nblocks + 64));
     if (rc == POISSON_OK && cudaMallocHost((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
         cudaGetLastError();
@@ -408,20 +387,15 @@ static int cg_loop_columns(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* 
     return cg_loop<V, Coef>(H, coef, r, z, tol2, rel_to_b, max_iter, result, A, B);
 }
 
-// TMA plane-marching passes (FP32 inner solve).
+// TMA plane-marching passes (FP32 inner solve), persistent work-list launches.
 template <typename Coef>
 static int cg_loop_march(poisson_t* H, const Coef& coef, double tol2, int max_iter,
                          Scalars* result) {
-    const Dims d = H->d;
-    const int kc = H->march_kc;
     cudaStream_t st = H->st;
-    const MarchMaps* mm = &H->maps;
-    float *pa = H->p32a, *pb = H->p32b, *x = H->d32, *r = H->r32, *z = H->z32;
-    auto A = [=](bool in_a) {
-        launch_march_a(d, kc, *mm, in_a, in_a ? pb : pa, H->sc, H->partials, st);
-    };
-    auto B = [=](bool p_a) { launch_march_b(d, kc, *mm, p_a, x, r, z, H->sc, H->partials, st); };
-    return cg_loop<float, Coef>(H, coef, r, z, tol2, 0, max_iter, result, A, B);
+    const MarchPlan* plan = &H->plan;
+    auto A = [=](bool in_a) { launch_march_a(*plan, in_a, st); };
+    auto B = [=](bool p_a) { launch_march_b(*plan, p_a, st); };
+    return cg_loop<float, Coef>(H, coef, H->r32, H->z32, tol2, 0, max_iter, result, A, B);
 }
 
 // Reads the scalars after a residual kernel (and books its time when profiling).
@@ -703,9 +677,11 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
     const char* prec = H->opts.precision == POISSON_FP64 ? "fp64"
                        : H->opts.precision == POISSON_FP32 ? "fp32" : "fp32/bf16-coef";
     if (H->march) {
-        const MarchVariant v = march_variant(H->march_variant);
-        snprintf(buf, (size_t)len, "%s march tile=%d (%dx%d cells, %dx%d per thread) zchunk=%d",
-                 prec, 1000 * v.cx + 100 * v.cy + v.tyt, v.width, v.height, v.cx, v.cy, H->march_kc);
+        const MarchVariant v = march_variant(H->plan.variant);
+        snprintf(buf, (size_t)len,
+                 "%s march tile=%d (%dx%d cells, %dx%d per thread) persistent ctas=%d segments=%d",
+                 prec, 1000 * v.cx + 100 * v.cy + v.tyt, v.width, v.height, v.cx, v.cy,
+                 H->plan.nctas, H->plan.nsegs);
     } else {
         snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d", prec, TX, TY, H->kc);
     }

@@ -40,9 +40,7 @@ struct poisson_s {
     double *io_a = nullptr, *io_b = nullptr;
     // TMA plane-marching kernels for the FP32 inner solve (when the shape allows them)
     bool march = false;
-    int march_variant = 0;
-    int march_kc = 8;
-    pcg::MarchMaps maps{};
+    pcg::MarchPlan plan{};  // persistent work-list launch over this handle's grid
     // poisson_profile: event pairs around the timed kernels, accumulated times
     bool prof_on = false;
     poisson_kernel_times prof{};

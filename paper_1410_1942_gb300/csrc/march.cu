@@ -1,7 +1,11 @@
 // march.cu -- the FP32 CG passes as 2.5-D plane-marching kernels with TMA-staged x-y planes.
 //
-// A CTA of 32 x TYT threads owns an x-y tile of W x HT cells (W = 32 CX, HT = TYT CY; each
-// thread owns a CX x CY block of cells) and walks a chunk of z-planes.  Each plane of the inputs
+// A CTA of 32 x TYT threads works on x-y tiles of W x HT cells (W = 32 CX, HT = TYT CY; each
+// thread owns a CX x CY block of cells) and walks them along z.  The grid is persistent (as many
+// CTAs as fit on the GPU at once) and driven by a work list of z-segments, so every CTA gets the
+// same number of tile-planes whatever the grid shape, and one launch can serve many solves of
+// different sizes (each segment names its solve; per-solve tensor maps, vectors and scalars
+// live in device memory).  Each plane of the inputs
 // that need neighbours (p, or z and p_old; and rho/2) is copied into a ring of NS shared-memory
 // stages by one TMA box load with a one-cell halo in y and an aligned halo in x (the box starts
 // at x0 - 4 for FP32 and x0 - 8 for BF16 so its first coordinate stays on a 16-byte boundary);
@@ -26,6 +30,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <vector>
 
 namespace pcg {
 
@@ -185,272 +190,377 @@ __device__ __forceinline__ void load_centre(const T* t, int pitch, int r0, int c
     for (int a = 0; a < CY; ++a) ld_row<CX>(t + (r0 + a) * pitch + c0, cen[a]);
 }
 
+// ------------------------------------------------------------------ work-list kernels
+// The grid is persistent: CTA c walks the segments [cta_seg[c], cta_seg[c+1]) of the work list.
+// A segment is one tile column of one solve over planes [k0, k1); its plane stream is k0-1 .. k1
+// (one halo plane at each end).  The planes of all of a CTA's segments form one stream through
+// the NS-stage ring, so the TMA lookahead runs on across segment boundaries.  Each segment
+// leaves its partial sums in seg_part; the CTA that completes the last segment of a solve (the
+// solve's ticket) adds that solve's partials in segment order and updates its scalars.
+//
+// A solve whose scalars say it is finished is skipped.  That flag only changes once every
+// segment of the solve has been processed in the current launch, so every reader of a pending
+// segment sees the value it had at launch.
+
+__device__ __forceinline__ bool seg_active(const SolveDev* solves, const Seg& s) {
+    return *(volatile const int*)&solves[s.solve].sc->done == RUNNING;
+}
+
+// Thread 0's issue cursor over the plane stream of this CTA.
+struct Cursor {
+    int seg;  // current segment
+    int off;  // plane offset within it (0 .. L+1)
+    int n;    // stream positions issued
+};
+
+template <int NV>
+__device__ __forceinline__ bool segment_done(const SolveDev& sv, int s, double (&v)[NV],
+                                             double* seg_part, double (&tot)[NV], double* red,
+                                             int tid, int nthreads) {
+    __shared__ int s_last;
+    block_sum<NV>(v, red);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) seg_part[(size_t)s * NV + q] = v[q];
+        __threadfence();
+        const unsigned t = atomicAdd(&sv.sc->ticket, 1u);
+        s_last = (t + 1 == (unsigned)(sv.seg_end - sv.seg_begin)) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
+    for (int b = sv.seg_begin + tid; b < sv.seg_end; b += nthreads)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&seg_part[(size_t)b * NV + q]);
+    block_sum<NV>(acc, red);
+    if (tid == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[q] = acc[q];
+        sv.sc->ticket = 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) tot[q] = red[q];
+    __syncthreads();
+    return true;
+}
+
 template <int CX, int CY, int TYT, typename E>
-__global__ void __launch_bounds__(32 * TYT) k_march_a(Dims d, int kchunk,
-                                                     const __grid_constant__ CUtensorMap mz,
-                                                     const __grid_constant__ CUtensorMap mp,
-                                                     const __grid_constant__ CUtensorMap me,
-                                                     float* __restrict__ p_out, Scalars* sc,
-                                                     double* partials) {
+__global__ void __launch_bounds__(32 * TYT) k_march_a(const SolveDev* __restrict__ solves,
+                                                     const Seg* __restrict__ segs,
+                                                     const int* __restrict__ cta_seg,
+                                                     const CUtensorMap* __restrict__ maps,
+                                                     double* seg_part, int pin_is_a) {
     using G = Geo<CX, CY, TYT, E>;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ double red[64];
-    if (sc->done) return;
+    const int sb = cta_seg[blockIdx.x], se = cta_seg[blockIdx.x + 1];
+    if (sb >= se) return;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-    const int x0 = blockIdx.x * G::W, y0 = blockIdx.y * G::HT;
-    const int k0 = blockIdx.z * kchunk, k1 = min(d.nz, k0 + kchunk);
-    const int nplanes = k1 - k0 + 2;  // k0-1 .. k1
-    const float beta = (float)sc->beta;
-
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int q) {
-        const int s = q % NS, kk = k0 - 1 + q;
-        unsigned char* st = sm + s * G::A_STAGE;
-        mbar_arrive_expect_tx(&bars[s], G::A_TX);
-        tma_load_3d(st + G::A_Z, &mz, &bars[s], x0 - G::VOFF, y0 - 1, kk);
-        tma_load_3d(st + G::A_P, &mp, &bars[s], x0 - G::VOFF, y0 - 1, kk);
-        tma_load_3d(st + G::A_E, &me, &bars[s], x0 - G::EOFF, y0 - 1, kk);
+
+    Cursor cur{sb, 0, 0};
+    auto issue_next = [&]() {  // thread 0
+        while (cur.seg < se && cur.off == 0 && !seg_active(solves, segs[cur.seg])) ++cur.seg;
+        if (cur.seg >= se) return;
+        const Seg sg = segs[cur.seg];
+        const int st = cur.n % NS, kk = sg.k0 - 1 + cur.off;
+        unsigned char* dst = sm + st * G::A_STAGE;
+        const CUtensorMap* m = maps + 6 * sg.solve;
+        const int pm = pin_is_a ? MAP_PA : MAP_PB;
+        mbar_arrive_expect_tx(&bars[st], G::A_TX);
+        tma_load_3d(dst + G::A_Z, m + MAP_Z, &bars[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
+        tma_load_3d(dst + G::A_P, m + pm, &bars[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
+        tma_load_3d(dst + G::A_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+        ++cur.n;
+        if (++cur.off == sg.k1 - sg.k0 + 2) {
+            cur.off = 0;
+            ++cur.seg;
+        }
     };
     if (tid == 0)
-        for (int q = 0; q < NS && q < nplanes; ++q) issue(q);
-    int issued = min(NS, nplanes);
+        for (int q = 0; q < NS; ++q) issue_next();
 
-    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx;
-    const int i0 = x0 + CX * tx, j0 = y0 + CY * ty;
+    int g = 0;  // next stream position to acquire
+    bool ok = true, failed = false;
+    auto acquire = [&]() -> bool {
+        ok = ok && mbar_wait(&bars[g % NS], (g / NS) & 1);
+        if (__syncthreads_or(!ok)) return false;  // also: every thread is done with plane g-2
+        if (tid == 0 && g >= 2) issue_next();
+        ++g;
+        return true;
+    };
     auto Zs = [&](int q) { return (const float*)(sm + (q % NS) * G::A_STAGE + G::A_Z); };
     auto Ps = [&](int q) { return (const float*)(sm + (q % NS) * G::A_STAGE + G::A_P); };
     auto Es = [&](int q) { return (const E*)(sm + (q % NS) * G::A_STAGE + G::A_E); };
-    // p = z + beta p_old of a centre block
-    auto centre_pn = [&](int q, float (&o)[CY][CX]) {
-        float zz[CY][CX], pp[CY][CX];
-        load_centre<CX, CY>(Zs(q), G::VW, r0, cv, zz);
-        load_centre<CX, CY>(Ps(q), G::VW, r0, cv, pp);
+    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx;
+
+    for (int s = sb; s < se; ++s) {
+        const Seg sg = segs[s];
+        if (!seg_active(solves, sg)) continue;
+        const SolveDev& sv = solves[sg.solve];
+        const Dims d = sv.d;
+        const float beta = (float)sv.sc->beta;
+        float* p_out = pin_is_a ? sv.pb : sv.pa;
+        const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * ty;
+        auto centre_pn = [&](int q, float (&o)[CY][CX]) {
+            float zz[CY][CX], pp[CY][CX];
+            load_centre<CX, CY>(Zs(q), G::VW, r0, cv, zz);
+            load_centre<CX, CY>(Ps(q), G::VW, r0, cv, pp);
+#pragma unroll
+            for (int a = 0; a < CY; ++a)
+#pragma unroll
+                for (int b = 0; b < CX; ++b) o[a][b] = zz[a][b] + beta * pp[a][b];
+        };
+        float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
+        if (!acquire()) { failed = true; break; }  // plane k0-1
+        centre_pn(g - 1, vm);
+        load_centre<CX, CY>(Es(g - 1), G::EW, r0, ce, em);
+        if (!acquire()) { failed = true; break; }  // plane k0
+        centre_pn(g - 1, vc);
+        load_centre<CX, CY>(Es(g - 1), G::EW, r0, ce, ec);
 #pragma unroll
         for (int a = 0; a < CY; ++a)
 #pragma unroll
-            for (int b = 0; b < CX; ++b) o[a][b] = zz[a][b] + beta * pp[a][b];
-    };
-
-    bool ok = mbar_wait(&bars[0], 0);
-    ok = ok && mbar_wait(&bars[1], 0);
-    float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
-    centre_pn(0, vm);
-    centre_pn(1, vc);
-    load_centre<CX, CY>(Es(0), G::EW, r0, ce, em);
-    load_centre<CX, CY>(Es(1), G::EW, r0, ce, ec);
-#pragma unroll
-    for (int a = 0; a < CY; ++a)
-#pragma unroll
-        for (int b = 0; b < CX; ++b) wzl[a][b] = (k0 > 0) ? rcp_approx(ec[a][b] + em[a][b]) : 0.f;
-    float acc = 0.f;
-    int waited = 2;
-    bool failed = false;
-    for (int k = k0; k < k1; ++k) {
-        const int q = k - k0 + 1;
-        ok = ok && mbar_wait(&bars[(q + 1) % NS], ((q + 1) / NS) & 1);
-        if (__syncthreads_or(!ok)) {  // also: every thread is done with plane q-1
-            failed = true;
-            break;
-        }
-        waited = q + 2;
-        if (tid == 0 && q - 1 + NS < nplanes) issue(q - 1 + NS);
-        if (q - 1 + NS < nplanes) issued = q + NS;
-        float vp[CY][CX], ep[CY][CX];
-        centre_pn(q + 1, vp);
-        load_centre<CX, CY>(Es(q + 1), G::EW, r0, ce, ep);
-        // neighbour strips of p = z + beta p_old in plane q
-        float zxm[CY], zxp[CY], zym[CX], zyp[CX];
-        float pxm[CY], pxp[CY], pym[CX], pyp[CX];
-        load_halo<CX, CY>(Zs(q), G::VW, r0, cv, zxm, zxp, zym, zyp);
-        load_halo<CX, CY>(Ps(q), G::VW, r0, cv, pxm, pxp, pym, pyp);
-        float vxm[CY], vxp[CY], vym[CX], vyp[CX];
-#pragma unroll
-        for (int a = 0; a < CY; ++a) {
-            vxm[a] = zxm[a] + beta * pxm[a];
-            vxp[a] = zxp[a] + beta * pxp[a];
-        }
-#pragma unroll
-        for (int b = 0; b < CX; ++b) {
-            vym[b] = zym[b] + beta * pym[b];
-            vyp[b] = zyp[b] + beta * pyp[b];
-        }
-        float exm[CY], exp_[CY], eym[CX], eyp[CX];
-        load_halo<CX, CY>(Es(q), G::EW, r0, ce, exm, exp_, eym, eyp);
-        float qv[CY][CX], D[CY][CX];
-        stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exp_, eym, eyp, ep,
-                        wzl, qv, D);
-        if (i0 < d.nx) {
+            for (int b = 0; b < CX; ++b)
+                wzl[a][b] = (sg.k0 > 0) ? rcp_approx(ec[a][b] + em[a][b]) : 0.f;
+        float acc = 0.f;
+        for (int k = sg.k0; k < sg.k1; ++k) {
+            if (!acquire()) { failed = true; break; }  // plane k+1 (lookahead)
+            const int qc = g - 2, qn = g - 1;
+            float vp[CY][CX], ep[CY][CX];
+            centre_pn(qn, vp);
+            load_centre<CX, CY>(Es(qn), G::EW, r0, ce, ep);
+            float zxm[CY], zxp[CY], zym[CX], zyp[CX];
+            float pxm[CY], pxp[CY], pym[CX], pyp[CX];
+            load_halo<CX, CY>(Zs(qc), G::VW, r0, cv, zxm, zxp, zym, zyp);
+            load_halo<CX, CY>(Ps(qc), G::VW, r0, cv, pxm, pxp, pym, pyp);
+            float vxm[CY], vxp[CY], vym[CX], vyp[CX];
 #pragma unroll
             for (int a = 0; a < CY; ++a) {
-                if (j0 + a < d.ny) {
+                vxm[a] = zxm[a] + beta * pxm[a];
+                vxp[a] = zxp[a] + beta * pxp[a];
+            }
 #pragma unroll
-                    for (int b = 0; b < CX; ++b) acc += vc[a][b] * qv[a][b];
-                    st_row<CX>(p_out + (size_t)i0 + (size_t)d.nx * (j0 + a + (size_t)d.ny * k), vc[a]);
+            for (int b = 0; b < CX; ++b) {
+                vym[b] = zym[b] + beta * pym[b];
+                vyp[b] = zyp[b] + beta * pyp[b];
+            }
+            float exm[CY], exq[CY], eym[CX], eyp[CX];
+            load_halo<CX, CY>(Es(qc), G::EW, r0, ce, exm, exq, eym, eyp);
+            float qv[CY][CX], D[CY][CX];
+            stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym, eyp,
+                            ep, wzl, qv, D);
+            if (i0 < d.nx) {
+#pragma unroll
+                for (int a = 0; a < CY; ++a) {
+                    if (j0 + a < d.ny) {
+#pragma unroll
+                        for (int b = 0; b < CX; ++b) acc += vc[a][b] * qv[a][b];
+                        st_row<CX>(p_out + (size_t)i0 + (size_t)d.nx * (j0 + a + (size_t)d.ny * k),
+                                   vc[a]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < CY; ++a)
+#pragma unroll
+                for (int b = 0; b < CX; ++b) {
+                    vm[a][b] = vc[a][b];
+                    vc[a][b] = vp[a][b];
+                    ec[a][b] = ep[a][b];
+                }
+        }
+        if (failed) break;
+        double v[1] = {(double)acc}, tot[1];
+        if (segment_done<1>(sv, s, v, seg_part, tot, red, tid, 32 * TYT)) {
+            if (tid == 0 && sv.sc->done == RUNNING) {
+                const double pq = tot[0];
+                if (!(pq > 0.0) || !isfinite(pq)) {
+                    sv.sc->done = BREAKDOWN;
+                } else {
+                    sv.sc->pq = pq;
+                    sv.sc->alpha = sv.sc->rz / pq;
                 }
             }
         }
-#pragma unroll
-        for (int a = 0; a < CY; ++a)
-#pragma unroll
-            for (int b = 0; b < CX; ++b) {
-                vm[a][b] = vc[a][b];
-                vc[a][b] = vp[a][b];
-                ec[a][b] = ep[a][b];
-            }
     }
-    if (failed) march_abort(sc, bars, waited, issued, tid);
-    double v[1] = {(double)acc}, tot[1];
-    if (grid_sum<1>(v, partials, &sc->ticket, tot, red)) {
-        if (tid == 0 && sc->done == RUNNING) {
-            const double pq = tot[0];
-            if (!(pq > 0.0) || !isfinite(pq)) {
-                sc->done = BREAKDOWN;
-            } else {
-                sc->pq = pq;
-                sc->alpha = sc->rz / pq;
-            }
+    if (failed) {
+        if (tid == 0) {
+            for (int s = sb; s < se; ++s) atomicExch(&solves[segs[s].solve].sc->done, (int)TIMEDOUT);
+            for (int q = g; q < cur.n; ++q) (void)mbar_wait(&bars[q % NS], (q / NS) & 1);
+            __threadfence();
         }
+        __syncthreads();
     }
 }
 
 template <int CX, int CY, int TYT, typename E>
-__global__ void __launch_bounds__(32 * TYT) k_march_b(Dims d, int kchunk,
-                                                     const __grid_constant__ CUtensorMap mp,
-                                                     const __grid_constant__ CUtensorMap me,
-                                                     const __grid_constant__ CUtensorMap mx,
-                                                     const __grid_constant__ CUtensorMap mr,
-                                                     float* __restrict__ x, float* __restrict__ r,
-                                                     float* __restrict__ z, Scalars* sc,
-                                                     double* partials) {
+__global__ void __launch_bounds__(32 * TYT) k_march_b(const SolveDev* __restrict__ solves,
+                                                     const Seg* __restrict__ segs,
+                                                     const int* __restrict__ cta_seg,
+                                                     const CUtensorMap* __restrict__ maps,
+                                                     double* seg_part, int p_is_a) {
     using G = Geo<CX, CY, TYT, E>;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ double red[64];
-    if (sc->done) return;
+    const int sb = cta_seg[blockIdx.x], se = cta_seg[blockIdx.x + 1];
+    if (sb >= se) return;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-    const int x0 = blockIdx.x * G::W, y0 = blockIdx.y * G::HT;
-    const int k0 = blockIdx.z * kchunk, k1 = min(d.nz, k0 + kchunk);
-    const int nplanes = k1 - k0 + 2;
-    const float alpha = (float)sc->alpha;
-
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    auto issue = [&](int q) {
-        const int s = q % NS, kk = k0 - 1 + q;
-        unsigned char* st = sm + s * G::B_STAGE;
-        const bool centre = (q > 0) && (q < nplanes - 1);
-        mbar_arrive_expect_tx(&bars[s], centre ? G::B_TX : G::B_TX_HALO);
-        tma_load_3d(st + G::B_P, &mp, &bars[s], x0 - G::VOFF, y0 - 1, kk);
-        tma_load_3d(st + G::B_E, &me, &bars[s], x0 - G::EOFF, y0 - 1, kk);
+
+    Cursor cur{sb, 0, 0};
+    auto issue_next = [&]() {  // thread 0
+        while (cur.seg < se && cur.off == 0 && !seg_active(solves, segs[cur.seg])) ++cur.seg;
+        if (cur.seg >= se) return;
+        const Seg sg = segs[cur.seg];
+        const int L = sg.k1 - sg.k0;
+        const int st = cur.n % NS, kk = sg.k0 - 1 + cur.off;
+        unsigned char* dst = sm + st * G::B_STAGE;
+        const CUtensorMap* m = maps + 6 * sg.solve;
+        const bool centre = cur.off > 0 && cur.off <= L;
+        mbar_arrive_expect_tx(&bars[st], centre ? G::B_TX : G::B_TX_HALO);
+        tma_load_3d(dst + G::B_P, m + (p_is_a ? MAP_PA : MAP_PB), &bars[st], sg.x0 - G::VOFF,
+                    sg.y0 - 1, kk);
+        tma_load_3d(dst + G::B_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
         if (centre) {
-            tma_load_3d(st + G::B_X, &mx, &bars[s], x0, y0, kk);
-            tma_load_3d(st + G::B_R, &mr, &bars[s], x0, y0, kk);
+            tma_load_3d(dst + G::B_X, m + MAP_X, &bars[st], sg.x0, sg.y0, kk);
+            tma_load_3d(dst + G::B_R, m + MAP_R, &bars[st], sg.x0, sg.y0, kk);
+        }
+        ++cur.n;
+        if (++cur.off == L + 2) {
+            cur.off = 0;
+            ++cur.seg;
         }
     };
     if (tid == 0)
-        for (int q = 0; q < NS && q < nplanes; ++q) issue(q);
-    int issued = min(NS, nplanes);
+        for (int q = 0; q < NS; ++q) issue_next();
 
-    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx;
-    const int cc = CX * tx;  // column in the centre boxes
-    const int i0 = x0 + CX * tx, j0 = y0 + CY * ty;
+    int g = 0;
+    bool ok = true, failed = false;
+    auto acquire = [&]() -> bool {
+        ok = ok && mbar_wait(&bars[g % NS], (g / NS) & 1);
+        if (__syncthreads_or(!ok)) return false;
+        if (tid == 0 && g >= 2) issue_next();
+        ++g;
+        return true;
+    };
     auto Ps = [&](int q) { return (const float*)(sm + (q % NS) * G::B_STAGE + G::B_P); };
     auto Es = [&](int q) { return (const E*)(sm + (q % NS) * G::B_STAGE + G::B_E); };
     auto Xs = [&](int q) { return (const float*)(sm + (q % NS) * G::B_STAGE + G::B_X); };
     auto Rs = [&](int q) { return (const float*)(sm + (q % NS) * G::B_STAGE + G::B_R); };
+    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx;
+    const int cc = CX * tx;
 
-    bool ok = mbar_wait(&bars[0], 0);
-    ok = ok && mbar_wait(&bars[1], 0);
-    float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
-    load_centre<CX, CY>(Ps(0), G::VW, r0, cv, vm);
-    load_centre<CX, CY>(Ps(1), G::VW, r0, cv, vc);
-    load_centre<CX, CY>(Es(0), G::EW, r0, ce, em);
-    load_centre<CX, CY>(Es(1), G::EW, r0, ce, ec);
-#pragma unroll
-    for (int a = 0; a < CY; ++a)
-#pragma unroll
-        for (int b = 0; b < CX; ++b) wzl[a][b] = (k0 > 0) ? rcp_approx(ec[a][b] + em[a][b]) : 0.f;
-    float arz = 0.f, arr = 0.f;
-    int waited = 2;
-    bool failed = false;
-    for (int k = k0; k < k1; ++k) {
-        const int q = k - k0 + 1;
-        ok = ok && mbar_wait(&bars[(q + 1) % NS], ((q + 1) / NS) & 1);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        waited = q + 2;
-        if (tid == 0 && q - 1 + NS < nplanes) issue(q - 1 + NS);
-        if (q - 1 + NS < nplanes) issued = q + NS;
-        float vp[CY][CX], ep[CY][CX];
-        load_centre<CX, CY>(Ps(q + 1), G::VW, r0, cv, vp);
-        load_centre<CX, CY>(Es(q + 1), G::EW, r0, ce, ep);
-        float vxm[CY], vxp[CY], vym[CX], vyp[CX];
-        load_halo<CX, CY>(Ps(q), G::VW, r0, cv, vxm, vxp, vym, vyp);
-        float exm[CY], exp_[CY], eym[CX], eyp[CX];
-        load_halo<CX, CY>(Es(q), G::EW, r0, ce, exm, exp_, eym, eyp);
-        float qv[CY][CX], D[CY][CX];
-        stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exp_, eym, eyp, ep,
-                        wzl, qv, D);
-        float xo[CY][CX], ro[CY][CX];
-        load_centre<CX, CY>(Xs(q), G::W, CY * ty, cc, xo);
-        load_centre<CX, CY>(Rs(q), G::W, CY * ty, cc, ro);
-        if (i0 < d.nx) {
-#pragma unroll
-            for (int a = 0; a < CY; ++a) {
-                if (j0 + a < d.ny) {
-                    float xn[CX], rn[CX], zn[CX];
-#pragma unroll
-                    for (int b = 0; b < CX; ++b) {
-                        xn[b] = xo[a][b] + alpha * vc[a][b];
-                        rn[b] = ro[a][b] - alpha * qv[a][b];
-                        zn[b] = rn[b] * rcp_approx(D[a][b]);
-                        arz += rn[b] * zn[b];
-                        arr += rn[b] * rn[b];
-                    }
-                    const size_t c = (size_t)i0 + (size_t)d.nx * (j0 + a + (size_t)d.ny * k);
-                    st_row<CX>(x + c, xn);
-                    st_row<CX>(r + c, rn);
-                    st_row<CX>(z + c, zn);
-                }
-            }
-        }
+    for (int s = sb; s < se; ++s) {
+        const Seg sg = segs[s];
+        if (!seg_active(solves, sg)) continue;
+        const SolveDev& sv = solves[sg.solve];
+        const Dims d = sv.d;
+        const float alpha = (float)sv.sc->alpha;
+        float* x = sv.x;
+        float* r = sv.r;
+        float* z = sv.z;
+        const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * ty;
+        float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
+        if (!acquire()) { failed = true; break; }
+        load_centre<CX, CY>(Ps(g - 1), G::VW, r0, cv, vm);
+        load_centre<CX, CY>(Es(g - 1), G::EW, r0, ce, em);
+        if (!acquire()) { failed = true; break; }
+        load_centre<CX, CY>(Ps(g - 1), G::VW, r0, cv, vc);
+        load_centre<CX, CY>(Es(g - 1), G::EW, r0, ce, ec);
 #pragma unroll
         for (int a = 0; a < CY; ++a)
 #pragma unroll
-            for (int b = 0; b < CX; ++b) {
-                vm[a][b] = vc[a][b];
-                vc[a][b] = vp[a][b];
-                ec[a][b] = ep[a][b];
+            for (int b = 0; b < CX; ++b)
+                wzl[a][b] = (sg.k0 > 0) ? rcp_approx(ec[a][b] + em[a][b]) : 0.f;
+        float arz = 0.f, arr = 0.f;
+        for (int k = sg.k0; k < sg.k1; ++k) {
+            if (!acquire()) { failed = true; break; }
+            const int qc = g - 2, qn = g - 1;
+            float vp[CY][CX], ep[CY][CX];
+            load_centre<CX, CY>(Ps(qn), G::VW, r0, cv, vp);
+            load_centre<CX, CY>(Es(qn), G::EW, r0, ce, ep);
+            float vxm[CY], vxp[CY], vym[CX], vyp[CX];
+            load_halo<CX, CY>(Ps(qc), G::VW, r0, cv, vxm, vxp, vym, vyp);
+            float exm[CY], exq[CY], eym[CX], eyp[CX];
+            load_halo<CX, CY>(Es(qc), G::EW, r0, ce, exm, exq, eym, eyp);
+            float qv[CY][CX], D[CY][CX];
+            stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym, eyp,
+                            ep, wzl, qv, D);
+            float xo[CY][CX], ro[CY][CX];
+            load_centre<CX, CY>(Xs(qc), G::W, CY * ty, cc, xo);
+            load_centre<CX, CY>(Rs(qc), G::W, CY * ty, cc, ro);
+            if (i0 < d.nx) {
+#pragma unroll
+                for (int a = 0; a < CY; ++a) {
+                    if (j0 + a < d.ny) {
+                        float xn[CX], rn[CX], zn[CX];
+#pragma unroll
+                        for (int b = 0; b < CX; ++b) {
+                            xn[b] = xo[a][b] + alpha * vc[a][b];
+                            rn[b] = ro[a][b] - alpha * qv[a][b];
+                            zn[b] = rn[b] * rcp_approx(D[a][b]);
+                            arz += rn[b] * zn[b];
+                            arr += rn[b] * rn[b];
+                        }
+                        const size_t c = (size_t)i0 + (size_t)d.nx * (j0 + a + (size_t)d.ny * k);
+                        st_row<CX>(x + c, xn);
+                        st_row<CX>(r + c, rn);
+                        st_row<CX>(z + c, zn);
+                    }
+                }
             }
-    }
-    if (failed) march_abort(sc, bars, waited, issued, tid);
-    double v[2] = {(double)arz, (double)arr}, tot[2];
-    if (grid_sum<2>(v, partials, &sc->ticket, tot, red)) {
-        if (tid == 0 && sc->done == RUNNING) {
-            const double rz_new = tot[0], rr_new = tot[1];
-            sc->iter += 1;
-            sc->rr = rr_new;
-            if (!isfinite(rz_new) || !isfinite(rr_new) || rz_new < 0.0) {
-                sc->done = BREAKDOWN;
-            } else if (rr_new <= sc->stop2) {
-                sc->done = CONVERGED;
-            } else if (sc->iter >= sc->max_iter) {
-                sc->done = CAPPED;
-            } else {
-                sc->beta = rz_new / sc->rz;
-                sc->rz = rz_new;
+#pragma unroll
+            for (int a = 0; a < CY; ++a)
+#pragma unroll
+                for (int b = 0; b < CX; ++b) {
+                    vm[a][b] = vc[a][b];
+                    vc[a][b] = vp[a][b];
+                    ec[a][b] = ep[a][b];
+                }
+        }
+        if (failed) break;
+        double v[2] = {(double)arz, (double)arr}, tot[2];
+        if (segment_done<2>(sv, s, v, seg_part, tot, red, tid, 32 * TYT)) {
+            Scalars* sc = sv.sc;
+            if (tid == 0 && sc->done == RUNNING) {
+                const double rz_new = tot[0], rr_new = tot[1];
+                sc->iter += 1;
+                sc->rr = rr_new;
+                if (!isfinite(rz_new) || !isfinite(rr_new) || rz_new < 0.0) {
+                    sc->done = BREAKDOWN;
+                } else if (rr_new <= sc->stop2) {
+                    sc->done = CONVERGED;
+                } else if (sc->iter >= sc->max_iter) {
+                    sc->done = CAPPED;
+                } else {
+                    sc->beta = rz_new / sc->rz;
+                    sc->rz = rz_new;
+                }
             }
         }
+    }
+    if (failed) {
+        if (tid == 0) {
+            for (int s = sb; s < se; ++s) atomicExch(&solves[segs[s].solve].sc->done, (int)TIMEDOUT);
+            for (int q = g; q < cur.n; ++q) (void)mbar_wait(&bars[q % NS], (q / NS) & 1);
+            __threadfence();
+        }
+        __syncthreads();
     }
 }
 
@@ -509,12 +619,13 @@ static VariantOps make_ops() {
                       (const void*)k_march_b<CX, CY, TYT, __nv_bfloat16>};
 }
 
+#define MARCH_VARIANTS(X) X(0, 1, 1, 4) X(1, 1, 1, 8) X(2, 1, 1, 16) X(3, 2, 2, 2) \
+    X(4, 2, 2, 4) X(5, 2, 2, 8) X(6, 2, 1, 8) X(7, 1, 2, 8)
+
 static const VariantOps* variants(int* count) {
-    static const VariantOps table[] = {
-        make_ops<1, 1, 4>(), make_ops<1, 1, 8>(), make_ops<1, 1, 16>(),
-        make_ops<2, 2, 2>(), make_ops<2, 2, 4>(), make_ops<2, 2, 8>(),
-        make_ops<2, 1, 8>(), make_ops<1, 2, 8>(),
-    };
+#define ROW(ID, CX, CY, TYT) make_ops<CX, CY, TYT>(),
+    static const VariantOps table[] = {MARCH_VARIANTS(ROW)};
+#undef ROW
     static std::once_flag once;
     std::call_once(once, [] {
         for (const auto& v : table) {
@@ -550,36 +661,6 @@ int march_find_variant(int cx, int cy, int tyt) {
     return -1;
 }
 
-bool march_maps(MarchMaps* mm, const Dims& d, int variant, const float* z, const float* pa,
-                const float* pb, const void* eta, bool bf16, const float* x, const float* r) {
-    const MarchVariant v = march_variant(variant);
-    const int eoff = bf16 ? 8 : 4;
-    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const CUtensorMapDataType edt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : f32;
-    bool ok = true;
-    ok = ok && encode3d(&mm->z, z, f32, 4, d, v.width + 8, v.height + 2);
-    ok = ok && encode3d(&mm->pa, pa, f32, 4, d, v.width + 8, v.height + 2);
-    ok = ok && encode3d(&mm->pb, pb, f32, 4, d, v.width + 8, v.height + 2);
-    ok = ok && encode3d(&mm->eta, eta, edt, bf16 ? 2 : 4, d, v.width + 2 * eoff, v.height + 2);
-    ok = ok && encode3d(&mm->x, x, f32, 4, d, v.width, v.height);
-    ok = ok && encode3d(&mm->r, r, f32, 4, d, v.width, v.height);
-    mm->variant = variant;
-    mm->bf16 = bf16;
-    return ok;
-}
-
-size_t march_blocks(const Dims& d, int variant, int kchunk) {
-    const MarchVariant v = march_variant(variant);
-    return (size_t)((d.nx + v.width - 1) / v.width) * ((d.ny + v.height - 1) / v.height) *
-           ((d.nz + kchunk - 1) / kchunk);
-}
-
-size_t march_max_blocks(const Dims& d, int kchunk) {
-    size_t m = 0;
-    for (int q = 0; q < march_variant_count(); ++q) m = std::max(m, march_blocks(d, q, kchunk));
-    return m;
-}
-
 int march_occupancy(int variant, bool bf16) {
     int n;
     const VariantOps& v = variants(&n)[variant];
@@ -595,63 +676,162 @@ int march_occupancy(int variant, bool bf16) {
     return std::max(1, std::min(oa, ob));
 }
 
+// ------------------------------------------------------------------ plans
+bool march_encode_solve(CUtensorMap (&m)[6], const MarchSolve& s, int variant, bool bf16) {
+    const MarchVariant v = march_variant(variant);
+    const int eoff = bf16 ? 8 : 4;
+    const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUtensorMapDataType edt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : f32;
+    const Dims& d = s.d;
+    bool ok = true;
+    ok = ok && encode3d(&m[MAP_Z], s.z, f32, 4, d, v.width + 8, v.height + 2);
+    ok = ok && encode3d(&m[MAP_PA], s.pa, f32, 4, d, v.width + 8, v.height + 2);
+    ok = ok && encode3d(&m[MAP_PB], s.pb, f32, 4, d, v.width + 8, v.height + 2);
+    ok = ok && encode3d(&m[MAP_ETA], s.eta, edt, bf16 ? 2 : 4, d, v.width + 2 * eoff, v.height + 2);
+    ok = ok && encode3d(&m[MAP_X], s.x, f32, 4, d, v.width, v.height);
+    ok = ok && encode3d(&m[MAP_R], s.r, f32, 4, d, v.width, v.height);
+    return ok;
+}
+
+void march_plan_free(MarchPlan* p) {
+    void* ptrs[] = {p->solves, p->segs, p->cta_seg, p->maps, p->seg_part};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    *p = MarchPlan{};
+}
+
+// Splits the solves' tile columns into segments and gives every CTA an equal share of the
+// linearised (solve, tile, plane) space: CTA c owns planes [c W / G, (c + 1) W / G), cut into
+// one segment per tile column it touches.  Segments come out ordered by solve.
+int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int variant, bool bf16,
+                     int nctas, cudaStream_t st) {
+    march_plan_free(p);
+    const MarchVariant v = march_variant(variant);
+    std::vector<long long> base(nsolves + 1, 0);  // first plane unit of each solve
+    std::vector<int> tiles_x(nsolves), tiles_y(nsolves);
+    for (int s = 0; s < nsolves; ++s) {
+        tiles_x[s] = (solves[s].d.nx + v.width - 1) / v.width;
+        tiles_y[s] = (solves[s].d.ny + v.height - 1) / v.height;
+        base[s + 1] = base[s] + (long long)tiles_x[s] * tiles_y[s] * solves[s].d.nz;
+    }
+    const long long W = base[nsolves];
+    if (W <= 0) return -1;
+    if (nctas > W) nctas = (int)W;
+    std::vector<Seg> segs;
+    std::vector<int> cta_seg(nctas + 1, 0);
+    std::vector<SolveDev> sd(nsolves);
+    int sol = 0;
+    for (int c = 0; c < nctas; ++c) {
+        cta_seg[c] = (int)segs.size();
+        long long u = W * c / nctas;
+        const long long u1 = W * (c + 1) / nctas;
+        while (u < u1) {
+            while (base[sol + 1] <= u) ++sol;
+            const Dims& d = solves[sol].d;
+            const long long local = u - base[sol];
+            const int tile = (int)(local / d.nz);
+            const int k0 = (int)(local % d.nz);
+            const int k1 = (int)std::min<long long>(d.nz, k0 + (u1 - u));
+            Seg g{};
+            g.solve = sol;
+            g.x0 = (tile % tiles_x[sol]) * v.width;
+            g.y0 = (tile / tiles_x[sol]) * v.height;
+            g.k0 = k0;
+            g.k1 = k1;
+            segs.push_back(g);
+            u += k1 - k0;
+        }
+    }
+    cta_seg[nctas] = (int)segs.size();
+    for (int s = 0; s < nsolves; ++s) {
+        sd[s].d = solves[s].d;
+        sd[s].x = solves[s].x;
+        sd[s].r = solves[s].r;
+        sd[s].z = solves[s].z;
+        sd[s].pa = solves[s].pa;
+        sd[s].pb = solves[s].pb;
+        sd[s].sc = solves[s].sc;
+        sd[s].seg_begin = (int)segs.size();
+        sd[s].seg_end = 0;
+    }
+    for (int q = 0; q < (int)segs.size(); ++q) {
+        SolveDev& t = sd[segs[q].solve];
+        t.seg_begin = std::min(t.seg_begin, q);
+        t.seg_end = std::max(t.seg_end, q + 1);
+    }
+    std::vector<CUtensorMap> maps(6 * (size_t)nsolves);
+    for (int s = 0; s < nsolves; ++s) {
+        CUtensorMap m[6];
+        if (!march_encode_solve(m, solves[s], variant, bf16)) return -1;
+        for (int q = 0; q < 6; ++q) maps[6 * (size_t)s + q] = m[q];
+    }
+    p->variant = variant;
+    p->bf16 = bf16;
+    p->nctas = nctas;
+    p->nsolves = nsolves;
+    p->nsegs = (int)segs.size();
+    auto up = [&](void** dst, const void* src, size_t bytes) -> bool {
+        if (cudaMalloc(dst, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *dst = nullptr;
+            return false;
+        }
+        return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    };
+    bool ok = up((void**)&p->solves, sd.data(), sizeof(SolveDev) * sd.size()) &&
+              up((void**)&p->segs, segs.data(), sizeof(Seg) * segs.size()) &&
+              up((void**)&p->cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size()) &&
+              up((void**)&p->maps, maps.data(), sizeof(CUtensorMap) * maps.size());
+    if (ok && cudaMalloc((void**)&p->seg_part, sizeof(double) * 2 * segs.size()) != cudaSuccess) {
+        cudaGetLastError();
+        ok = false;
+    }
+    if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;  // host vectors go out of scope
+    if (!ok) {
+        march_plan_free(p);
+        return -2;
+    }
+    return 0;
+}
+
 template <int CX, int CY, int TYT, typename E>
-static void launch_ab(const Dims& d, int kchunk, const MarchMaps& mm, bool a_side, bool p_is_a,
-                      float* p_out, float* x, float* r, float* z, Scalars* sc, double* part,
-                      cudaStream_t st) {
+static void launch_ab(const MarchPlan& p, bool a_side, int flag, cudaStream_t st) {
     using G = Geo<CX, CY, TYT, E>;
-    const dim3 grid((d.nx + G::W - 1) / G::W, (d.ny + G::HT - 1) / G::HT,
-                    (d.nz + kchunk - 1) / kchunk);
     const dim3 block(32, TYT);
     if (a_side)
-        k_march_a<CX, CY, TYT, E><<<grid, block, NS * G::A_STAGE, st>>>(
-            d, kchunk, mm.z, p_is_a ? mm.pa : mm.pb, mm.eta, p_out, sc, part);
+        k_march_a<CX, CY, TYT, E><<<p.nctas, block, NS * G::A_STAGE, st>>>(
+            p.solves, p.segs, p.cta_seg, p.maps, p.seg_part, flag);
     else
-        k_march_b<CX, CY, TYT, E><<<grid, block, NS * G::B_STAGE, st>>>(
-            d, kchunk, p_is_a ? mm.pa : mm.pb, mm.eta, mm.x, mm.r, x, r, z, sc, part);
+        k_march_b<CX, CY, TYT, E><<<p.nctas, block, NS * G::B_STAGE, st>>>(
+            p.solves, p.segs, p.cta_seg, p.maps, p.seg_part, flag);
     g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
 }
 
 template <typename E>
-static void dispatch(const Dims& d, int kchunk, const MarchMaps& mm, bool a_side, bool p_is_a,
-                     float* p_out, float* x, float* r, float* z, Scalars* sc, double* part,
-                     cudaStream_t st) {
+static void dispatch(const MarchPlan& p, bool a_side, int flag, cudaStream_t st) {
     int n;
     variants(&n);  // function attributes set
-    switch (mm.variant) {
-#define CASE(ID, CX, CY, TYT)                                                                \
-    case ID:                                                                                 \
-        launch_ab<CX, CY, TYT, E>(d, kchunk, mm, a_side, p_is_a, p_out, x, r, z, sc, part, st); \
-        break;
-        CASE(0, 1, 1, 4)
-        CASE(1, 1, 1, 8)
-        CASE(2, 1, 1, 16)
-        CASE(3, 2, 2, 2)
-        CASE(4, 2, 2, 4)
-        CASE(5, 2, 2, 8)
-        CASE(6, 2, 1, 8)
-        CASE(7, 1, 2, 8)
+    switch (p.variant) {
+#define CASE(ID, CX, CY, TYT) \
+    case ID: launch_ab<CX, CY, TYT, E>(p, a_side, flag, st); break;
+        MARCH_VARIANTS(CASE)
 #undef CASE
         default: break;
     }
 }
 
-void launch_march_a(const Dims& d, int kchunk, const MarchMaps& mm, bool pin_is_a, float* p_out,
-                    Scalars* sc, double* part, cudaStream_t st) {
-    if (mm.bf16)
-        dispatch<__nv_bfloat16>(d, kchunk, mm, true, pin_is_a, p_out, nullptr, nullptr, nullptr,
-                                sc, part, st);
+void launch_march_a(const MarchPlan& p, bool pin_is_a, cudaStream_t st) {
+    if (p.bf16)
+        dispatch<__nv_bfloat16>(p, true, pin_is_a ? 1 : 0, st);
     else
-        dispatch<float>(d, kchunk, mm, true, pin_is_a, p_out, nullptr, nullptr, nullptr, sc, part,
-                        st);
+        dispatch<float>(p, true, pin_is_a ? 1 : 0, st);
 }
 
-void launch_march_b(const Dims& d, int kchunk, const MarchMaps& mm, bool p_is_a, float* x,
-                    float* r, float* z, Scalars* sc, double* part, cudaStream_t st) {
-    if (mm.bf16)
-        dispatch<__nv_bfloat16>(d, kchunk, mm, false, p_is_a, nullptr, x, r, z, sc, part, st);
+void launch_march_b(const MarchPlan& p, bool p_is_a, cudaStream_t st) {
+    if (p.bf16)
+        dispatch<__nv_bfloat16>(p, false, p_is_a ? 1 : 0, st);
     else
-        dispatch<float>(d, kchunk, mm, false, p_is_a, nullptr, x, r, z, sc, part, st);
+        dispatch<float>(p, false, p_is_a ? 1 : 0, st);
 }
 
 }  // namespace pcg
