@@ -300,9 +300,14 @@ def main():
 
     # dominant CG kernel and its roofline
     bpc = BYTES_PER_CELL[args.precision]
-    dom = max(("cg_phase_a", "cg_phase_b"), key=lambda k: prof[k]["ms"])
-    per_launch_ms = prof[dom]["ms"] / max(1, prof[dom]["launches"])
-    alg_bytes = bpc[dom] * g.n
+    cands = [k for k in ("pcg_persistent", "cg_phase_a", "cg_phase_b") if prof[k]["launches"]]
+    dom = max(cands, key=lambda k: prof[k]["ms"])
+    per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
+    if dom == "pcg_persistent":
+        # one launch runs every CG iteration of one inner solve: both passes per iteration
+        alg_bytes = (bpc["cg_phase_a"] + bpc["cg_phase_b"]) * g.n * iters / prof[dom]["launches"]
+    else:
+        alg_bytes = bpc[dom] * g.n
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     traffic = ncu_traffic(dom, args.precision)

@@ -145,7 +145,8 @@ int poisson_poll(uint64_t ticket, poisson_stats* stats);
 #define POISSON_K_CG_B 1      /* CG phase B: x, r, z updates, sums r.z and r.r             */
 #define POISSON_K_RESIDUAL 2  /* FP64 residual b - A x and its norm                        */
 #define POISSON_K_OTHER 3     /* set-up, scaling, refinement update, CG init               */
-#define POISSON_K_CLASSES 4
+#define POISSON_K_PCG 4       /* persistent PCG: every iteration of one inner solve         */
+#define POISSON_K_CLASSES 5
 
 typedef struct {
     long long launches[POISSON_K_CLASSES]; /* kernel launches per class                     */

@@ -30,8 +30,8 @@ EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson
            "poisson_solve", "poisson_apply", "poisson_precond_apply", "poisson_get_operator",
            "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
            "poisson_profile_read", "poisson_describe", "poisson_strerror", "poisson_version"]
-K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER = 0, 1, 2, 3
-K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other"]
+K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER, K_PCG = 0, 1, 2, 3, 4
+K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 
 
 class Opts(ctypes.Structure):
@@ -49,11 +49,11 @@ class Stats(ctypes.Structure):
 
 
 class KernelTimes(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong * 4), ("ms", ctypes.c_double * 4)]
+    _fields_ = [("launches", ctypes.c_longlong * 5), ("ms", ctypes.c_double * 5)]
 
     def as_dict(self):
         return {K_NAMES[q]: {"launches": int(self.launches[q]), "ms": float(self.ms[q])}
-                for q in range(4)}
+                for q in range(5)}
 
 
 class PoissonError(RuntimeError):

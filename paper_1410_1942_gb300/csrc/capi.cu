@@ -83,6 +83,8 @@ static int choose_kc(const Dims& d) {
     return (int)kc;
 }
 
+static void prof_add(poisson_t* H, int cls, cudaEvent_t a, cudaEvent_t b);
+
 // ------------------------------------------------------------------ march kernel tuning
 // Every variant is tried on the handle's own buffers (zeroed; the scalars reset before every
 // launch) with a persistent grid of (resident CTAs per SM) x (SMs) CTAs, its phases A and B
@@ -120,6 +122,33 @@ static int build_plan(poisson_t* H, int var) {
     return march_plan_build(&H->plan, &s, 1, var, bf16, nctas, H->st);
 }
 
+// One FP32 inner PCG through the persistent kernel: init (z = D^{-1} r, scalars), p_in = 0,
+// control words, cooperative launch, then wait.  r32 holds the right side, d32 the (zeroed)
+// correction.  POISSON_ECUDA if the launch is refused.
+static int march_run(poisson_t* H, bool bf16, double tol2, int max_iter, Scalars* result = nullptr) {
+    cudaStream_t st = H->st;
+    const Dims d = H->d;
+    cudaMemsetAsync(H->d32, 0, sizeof(float) * (size_t)d.n, st);
+    cudaMemsetAsync(H->p32a, 0, sizeof(float) * (size_t)d.n, st);
+    if (bf16)
+        launch_cg_init<float, CoefEta<__nv_bfloat16>>(d, H->kc, CoefEta<__nv_bfloat16>{H->eta16},
+                                                      H->r32, H->z32, H->sc, H->partials, tol2, 0,
+                                                      max_iter, st);
+    else
+        launch_cg_init<float, CoefEta<float>>(d, H->kc, CoefEta<float>{H->eta32}, H->r32, H->z32,
+                                              H->sc, H->partials, tol2, 0, max_iter, st);
+    *H->ctl_host = MarchCtl{0u, 1, 0, 0};
+    CK(cudaMemcpyAsync(H->plan.ctl, H->ctl_host, sizeof(MarchCtl), cudaMemcpyHostToDevice, st));
+    const bool prof = H->prof_on && result;
+    if (prof) CK(cudaEventRecord(H->prof_ev[PROF_PCG], st));
+    if (launch_march_pcg(H->plan, st) != 0) return POISSON_ECUDA;
+    if (prof) CK(cudaEventRecord(H->prof_ev[PROF_PCG + 1], st));
+    CK(cudaStreamSynchronize(st));
+    if (prof) prof_add(H, POISSON_K_PCG, H->prof_ev[PROF_PCG], H->prof_ev[PROF_PCG + 1]);
+    if (result) CK(cudaMemcpy(result, H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost));
+    return POISSON_OK;
+}
+
 static int setup_march(poisson_t* H) {
     const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
     const Dims d = H->d;
@@ -133,37 +162,32 @@ static int setup_march(poisson_t* H) {
         if (it != g_tuned.end()) var = it->second;
     }
     if (var < 0 && forced <= 0) {
-        const size_t b32 = sizeof(float) * (size_t)d.n;
+        // a constant-density model problem (rho = 1) with r = 1, TUNE_ITERS iterations per try
+        constexpr int TUNE_ITERS = 6;
+        const long long n = d.n;
         cudaStream_t st = H->st;
-        float* vecs[] = {H->z32, H->p32a, H->p32b, H->d32, H->r32};
-        for (float* v : vecs) cudaMemsetAsync(v, 0, b32, st);
-        cudaMemsetAsync(bf16 ? (void*)H->eta16 : (void*)H->eta32, 0, bf16 ? b32 / 2 : b32, st);
+        if (bf16) launch_fill_bf16(n, H->eta16, 0.5f, st);
+        else launch_fill_f32(n, H->eta32, 0.5f, st);
+        launch_fill_f32(n, H->r32, 1.0f, st);
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
         for (int cand = 0; cand < march_variant_count(); ++cand) {
-            if (build_plan(H, cand) != 0) continue;
-            float tot = 0.f;
-            for (int side = 0; side < 2; ++side) {
-                float t[3];
-                for (int rep = 0; rep < 3; ++rep) {
-                    cudaMemsetAsync(H->sc, 0, sizeof(Scalars), st);
-                    cudaEventRecord(e0, st);
-                    if (side == 0)
-                        launch_march_a(H->plan, true, st);
-                    else
-                        launch_march_b(H->plan, true, st);
-                    cudaEventRecord(e1, st);
-                    cudaEventSynchronize(e1);
-                    cudaEventElapsedTime(&t[rep], e0, e1);
-                }
-                std::sort(t, t + 3);
-                tot += t[1];
+            if (march_occupancy(cand, bf16) <= 0 || build_plan(H, cand) != 0) continue;
+            float t[2];
+            bool good = true;
+            for (int rep = 0; rep < 2 && good; ++rep) {
+                cudaEventRecord(e0, st);
+                good = march_run(H, bf16, 0.0, TUNE_ITERS) == POISSON_OK;
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&t[rep], e0, e1);
             }
-            if (cudaGetLastError() != cudaSuccess) continue;
-            if (tot < best) {
-                best = tot;
+            if (!good || cudaGetLastError() != cudaSuccess) continue;
+            const float tt = std::min(t[0], t[1]);
+            if (tt < best) {
+                best = tt;
                 var = cand;
             }
         }
@@ -189,6 +213,7 @@ static void free_state(poisson_t* H) {
                     H->p32a, H->p32b, H->sc, H->partials, H->io_a, H->io_b};
     for (void* p : ptrs) dfree(p);
     if (H->sc_host) cudaFreeHost(H->sc_host);
+    if (H->ctl_host) cudaFreeHost(H->ctl_host);
     for (auto& e : H->ev) if (e) cudaEventDestroy(e);
     for (auto& e : H->prof_ev) if (e) cudaEventDestroy(e);
     march_plan_free(&H->plan);
@@ -236,12 +261,15 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
         A(dalloc(&H->p32a, N)); A(dalloc(&H->p32b, N));
     }
     A(dalloc(&H->sc, 1));
-    if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.tile != -1 && march_supported(H->d))
-        A(setup_march(H));
     A(dalloc(&H->partials, 2 * H->nblocks + 64));
     if (rc == POISSON_OK && cudaMallocHost((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
         cudaGetLastError();
         H->sc_host = nullptr;
+        rc = POISSON_ENOMEM;
+    }
+    if (rc == POISSON_OK && cudaMallocHost((void**)&H->ctl_host, sizeof(MarchCtl)) != cudaSuccess) {
+        cudaGetLastError();
+        H->ctl_host = nullptr;
         rc = POISSON_ENOMEM;
     }
     for (auto& e : H->ev)
@@ -249,6 +277,8 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
             rc = POISSON_ECUDA;
     if (rc == POISSON_OK && cudaMemsetAsync(H->sc, 0, sizeof(Scalars), H->st) != cudaSuccess)
         rc = POISSON_ECUDA;
+    if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.tile != -1 && march_supported(H->d))
+        A(setup_march(H));
     if (rc != POISSON_OK) {
         free_state(H);
         delete H;
@@ -292,7 +322,7 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
 // events [q * PROF_PER_CHUNK, (q + 1) * PROF_PER_CHUNK).
 static int prof_events(poisson_t* H) {
     if (!H->prof_ev.empty()) return POISSON_OK;
-    H->prof_ev.resize(2 * PROF_PER_CHUNK + 2);
+    H->prof_ev.resize(PROF_EVENTS);
     for (auto& e : H->prof_ev) CK(cudaEventCreate(&e));
     return POISSON_OK;
 }
@@ -387,25 +417,14 @@ static int cg_loop_columns(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* 
     return cg_loop<V, Coef>(H, coef, r, z, tol2, rel_to_b, max_iter, result, A, B);
 }
 
-// TMA plane-marching passes (FP32 inner solve), persistent work-list launches.
-template <typename Coef>
-static int cg_loop_march(poisson_t* H, const Coef& coef, double tol2, int max_iter,
-                         Scalars* result) {
-    cudaStream_t st = H->st;
-    const MarchPlan* plan = &H->plan;
-    auto A = [=](bool in_a) { launch_march_a(*plan, in_a, st); };
-    auto B = [=](bool p_a) { launch_march_b(*plan, p_a, st); };
-    return cg_loop<float, Coef>(H, coef, H->r32, H->z32, tol2, 0, max_iter, result, A, B);
-}
-
 // Reads the scalars after a residual kernel (and books its time when profiling).
 static int read_scalars(poisson_t* H, Scalars* s) {
     CK(cudaMemcpyAsync(&H->sc_host[0], H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, H->st));
     CK(cudaStreamSynchronize(H->st));
     *s = H->sc_host[0];
     if (H->prof_on)
-        prof_add(H, POISSON_K_RESIDUAL, H->prof_ev[2 * PROF_PER_CHUNK],
-                 H->prof_ev[2 * PROF_PER_CHUNK + 1]);
+        prof_add(H, POISSON_K_RESIDUAL, H->prof_ev[PROF_RES],
+                 H->prof_ev[PROF_RES + 1]);
     return POISSON_OK;
 }
 
@@ -417,9 +436,9 @@ static int solve_fp64(poisson_t* H, double tol, int* outer, int* inner, double* 
     double rel = INFINITY;
     int restarts = 0;
     for (;; ++restarts) {
-        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[2 * PROF_PER_CHUNK], H->st));
+        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[PROF_RES], H->st));
         launch_residual64(H->d, H->kc, c, H->b64, H->x64, H->r64, H->sc, H->partials, H->st);
-        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[2 * PROF_PER_CHUNK + 1], H->st));
+        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[PROF_RES + 1], H->st));
         CK(cudaGetLastError());
         Scalars s;
         int rc = read_scalars(H, &s);
@@ -462,9 +481,9 @@ static int solve_mixed(poisson_t* H, const E* eta, double tol, int* outer, int* 
     double rel = INFINITY, prev = INFINITY;
     int stalls = 0;
     for (k = 0;; ++k) {
-        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[2 * PROF_PER_CHUNK], H->st));
+        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[PROF_RES], H->st));
         launch_residual64_f32(H->d, H->kc, c64, H->b64, H->x64, H->r32, H->sc, H->partials, H->st);
-        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[2 * PROF_PER_CHUNK + 1], H->st));
+        if (H->prof_on) CK(cudaEventRecord(H->prof_ev[PROF_RES + 1], H->st));
         CK(cudaGetLastError());
         Scalars s;
         int rc = read_scalars(H, &s);
@@ -486,9 +505,12 @@ static int solve_mixed(poisson_t* H, const E* eta, double tol, int* outer, int* 
         CK(cudaMemsetAsync(H->d32, 0, bytes32, H->st));
         CK(cudaMemsetAsync(H->p32a, 0, bytes32, H->st));
         Scalars res;
-        if (H->march)
-            rc = cg_loop_march<CoefEta<E>>(H, c32, target * target, H->opts.max_iters - total, &res);
-        else
+        rc = POISSON_ECUDA;
+        if (H->march) {
+            rc = march_run(H, sizeof(E) == 2, target * target, H->opts.max_iters - total, &res);
+            if (rc == POISSON_ECUDA) H->march = false;  // launch refused: use the column kernels
+        }
+        if (!H->march)
             rc = cg_loop_columns<float, CoefEta<E>>(H, c32, H->d32, H->r32, H->z32, H->p32a,
                                                     H->p32b, target * target, 0,
                                                     H->opts.max_iters - total, &res);

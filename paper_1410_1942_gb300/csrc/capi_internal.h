@@ -41,6 +41,7 @@ struct poisson_s {
     // TMA plane-marching kernels for the FP32 inner solve (when the shape allows them)
     bool march = false;
     pcg::MarchPlan plan{};  // persistent work-list launch over this handle's grid
+    pcg::MarchCtl* ctl_host = nullptr;  // pinned staging of plan.ctl
     // poisson_profile: event pairs around the timed kernels, accumulated times
     bool prof_on = false;
     poisson_kernel_times prof{};
@@ -49,6 +50,9 @@ struct poisson_s {
 
 constexpr int CG_CHUNK = 8;                    // CG iterations queued per host check
 constexpr int PROF_PER_CHUNK = 3 * CG_CHUNK;   // events per chunk slot when profiling
+constexpr int PROF_RES = 2 * PROF_PER_CHUNK;   // event pair around a residual kernel
+constexpr int PROF_PCG = PROF_RES + 2;         // event pair around a persistent PCG launch
+constexpr int PROF_EVENTS = PROF_PCG + 2;
 
 cudaError_t& last_cuda_error();
 bool is_device_ptr(const void* p);

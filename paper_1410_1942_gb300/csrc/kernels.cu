@@ -83,6 +83,12 @@ __global__ void k_widen(long long n, const T* __restrict__ a, double* __restrict
     if (t < n) b[t] = (double)a[t];
 }
 
+template <typename T>
+__global__ void k_fill(long long n, T* __restrict__ p, float v) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) p[t] = (T)v;
+}
+
 // ------------------------------------------------------------------ stencil helpers
 #define COL_LOOP_BEGIN                                                         \
     const int i = blockIdx.x * TX + threadIdx.x;                               \
@@ -317,6 +323,16 @@ void launch_scale(long long n, const double* s, double a, double* b, cudaStream_
 
 void launch_update64(long long n, double* x, const float* dlt, cudaStream_t st) {
     k_update64<<<blocks1d(n), 256, 0, st>>>(n, x, dlt);
+    counted(1);
+}
+
+void launch_fill_f32(long long n, float* p, float v, cudaStream_t st) {
+    k_fill<float><<<blocks1d(n), 256, 0, st>>>(n, p, v);
+    counted(1);
+}
+
+void launch_fill_bf16(long long n, __nv_bfloat16* p, float v, cudaStream_t st) {
+    k_fill<__nv_bfloat16><<<blocks1d(n), 256, 0, st>>>(n, p, v);
     counted(1);
 }
 

@@ -16,6 +16,8 @@ void launch_setup(const Dims& d, const double* F, double ra, double rw, double* 
 void launch_scale(long long n, const double* s, double a, double* b, cudaStream_t st);
 void launch_update64(long long n, double* x, const float* dlt, cudaStream_t st);
 void launch_narrow_f32(long long n, const double* a, float* b, cudaStream_t st);
+void launch_fill_f32(long long n, float* p, float v, cudaStream_t st);
+void launch_fill_bf16(long long n, __nv_bfloat16* p, float v, cudaStream_t st);
 void launch_residual64(const Dims& d, int kc, const CoefFaces64& c, const double* b,
                        const double* x, double* r, Scalars* sc, double* part, cudaStream_t st);
 void launch_residual64_f32(const Dims& d, int kc, const CoefFaces64& c, const double* b,

@@ -2,10 +2,11 @@
 //
 // A CTA of 32 x TYT threads works on x-y tiles of W x HT cells (W = 32 CX, HT = TYT CY; each
 // thread owns a CX x CY block of cells) and walks them along z.  The grid is persistent (as many
-// CTAs as fit on the GPU at once) and driven by a work list of z-segments, so every CTA gets the
-// same number of tile-planes whatever the grid shape, and one launch can serve many solves of
-// different sizes (each segment names its solve; per-solve tensor maps, vectors and scalars
-// live in device memory).  Each plane of the inputs
+// CTAs as fit on the GPU at once, launched cooperatively) and runs every CG iteration of the
+// inner solve; it is driven by a work list of z-segments, so every CTA gets the same number of
+// tile-planes whatever the grid shape, and one launch serves many solves of different sizes
+// (each segment names its solve; per-solve tensor maps, vectors and scalars live in device
+// memory).  Each plane of the inputs
 // that need neighbours (p, or z and p_old; and rho/2) is copied into a ring of NS shared-memory
 // stages by one TMA box load with a one-cell halo in y and an aligned halo in x (the box starts
 // at x0 - 4 for FP32 and x0 - 8 for BF16 so its first coordinate stays on a 16-byte boundary);
@@ -65,6 +66,7 @@ struct Geo {
     static constexpr int B_STAGE = B_R + align128(CB);
     static constexpr int B_TX_HALO = VB + EB;  // planes k0-1 and k1: p, eta only
     static constexpr int B_TX = VB + EB + 2 * CB;
+    static constexpr int STAGE = A_STAGE > B_STAGE ? A_STAGE : B_STAGE;
 };
 
 // CX consecutive values of a shared-memory row (CX = 1 or 2), widened to float.
@@ -190,374 +192,377 @@ __device__ __forceinline__ void load_centre(const T* t, int pitch, int r0, int c
     for (int a = 0; a < CY; ++a) ld_row<CX>(t + (r0 + a) * pitch + c0, cen[a]);
 }
 
-// ------------------------------------------------------------------ work-list kernels
-// The grid is persistent: CTA c walks the segments [cta_seg[c], cta_seg[c+1]) of the work list.
-// A segment is one tile column of one solve over planes [k0, k1); its plane stream is k0-1 .. k1
-// (one halo plane at each end).  The planes of all of a CTA's segments form one stream through
-// the NS-stage ring, so the TMA lookahead runs on across segment boundaries.  Each segment
-// leaves its partial sums in seg_part; the CTA that completes the last segment of a solve (the
-// solve's ticket) adds that solve's partials in segment order and updates its scalars.
+// ------------------------------------------------------------------ persistent PCG kernel
+// One cooperative launch runs the whole FP32 inner PCG of one or many solves.  CTA c walks the
+// segments [cta_seg[c], cta_seg[c+1]) of the work list (a segment is one tile column of one
+// solve over planes [k0, k1); its plane stream is k0-1 .. k1), phase A then phase B, with a grid
+// barrier after each phase.  Each segment leaves its partial sums in part_a / part_b; after the
+// barrier every CTA adds, in segment order, the partials of the solves it works on and derives
+// alpha, beta and the stopping decision itself -- the same numbers in every CTA.  The CTA that
+// owns a solve's first segment publishes its final state and counts it off ctl->running; the
+// loop ends, in every CTA at once, when no solve is left running.
 //
-// A solve whose scalars say it is finished is skipped.  That flag only changes once every
-// segment of the solve has been processed in the current launch, so every reader of a pending
-// segment sees the value it had at launch.
+// Barrier waits spin on a global counter with a deadline (BAR_NS); a wait that runs out sets
+// ctl->error, marks the CTA's solves TIMEDOUT, waits (bounded) for its TMA copies in flight
+// and leaves the loop.
 
-__device__ __forceinline__ bool seg_active(const SolveDev* solves, const Seg& s) {
-    return *(volatile const int*)&solves[s.solve].sc->done == RUNNING;
+constexpr int MAXSEG = 16;                                           // segments per CTA
+constexpr unsigned long long BAR_NS = 1000ull * 1000ull * 1000ull;   // 1 s per barrier
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
 }
 
-// Thread 0's issue cursor over the plane stream of this CTA.
-struct Cursor {
-    int seg;  // current segment
-    int off;  // plane offset within it (0 .. L+1)
-    int n;    // stream positions issued
-};
-
-template <int NV>
-__device__ __forceinline__ bool segment_done(const SolveDev& sv, int s, double (&v)[NV],
-                                             double* seg_part, double (&tot)[NV], double* red,
-                                             int tid, int nthreads) {
-    __shared__ int s_last;
-    block_sum<NV>(v, red);
+__device__ __forceinline__ bool grid_barrier(MarchCtl* ctl, unsigned target, int tid) {
+    __shared__ int s_ok;
+    // generic-proxy stores of this phase must be ordered before the next phase's TMA reads
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
     if (tid == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) seg_part[(size_t)s * NV + q] = v[q];
         __threadfence();
-        const unsigned t = atomicAdd(&sv.sc->ticket, 1u);
-        s_last = (t + 1 == (unsigned)(sv.seg_end - sv.seg_begin)) ? 1 : 0;
+        atomicAdd(&ctl->bar, 1u);
+        int ok = 1;
+        unsigned long long t0 = 0;
+        while (ld_acquire(&ctl->bar) < target) {
+            if (*(volatile int*)&ctl->error) { ok = 0; break; }
+            const unsigned long long t = globaltimer();
+            if (!t0) t0 = t;
+            else if (t - t0 > BAR_NS) { ok = 0; atomicExch(&ctl->error, 1); break; }
+        }
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        s_ok = ok;
     }
     __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
+    return s_ok != 0;
+}
+
+// Sum over segments [b, e) of part[seg * NV + q], in a fixed order (the result is the same in
+// every CTA); valid in all threads.
+template <int NV>
+__device__ __forceinline__ void range_sum(const double* part, int b, int e, double (&out)[NV],
+                                          double* red, int tid, int nthreads) {
     double acc[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-    for (int b = sv.seg_begin + tid; b < sv.seg_end; b += nthreads)
+    for (int s = b + tid; s < e; s += nthreads)
 #pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&seg_part[(size_t)b * NV + q]);
+        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&part[(size_t)s * NV + q]);
     block_sum<NV>(acc, red);
-    if (tid == 0) {
+    if (tid == 0)
 #pragma unroll
         for (int q = 0; q < NV; ++q) red[q] = acc[q];
-        sv.sc->ticket = 0u;
-    }
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < NV; ++q) tot[q] = red[q];
+    for (int q = 0; q < NV; ++q) out[q] = red[q];
     __syncthreads();
-    return true;
 }
 
+struct LocalSolve {
+    Dims d;
+    float *x, *r, *z, *pa, *pb;
+    Scalars* sc;
+    int seg_begin, seg_end;
+    double rz, alpha, beta, rr, stop2;
+    int done, iter, max_iter, finished, owner;
+};
+
 template <int CX, int CY, int TYT, typename E>
-__global__ void __launch_bounds__(32 * TYT) k_march_a(const SolveDev* __restrict__ solves,
-                                                     const Seg* __restrict__ segs,
-                                                     const int* __restrict__ cta_seg,
-                                                     const CUtensorMap* __restrict__ maps,
-                                                     double* seg_part, int pin_is_a) {
+__global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     using G = Geo<CX, CY, TYT, E>;
+    constexpr int NT = 32 * TYT;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ double red[64];
-    const int sb = cta_seg[blockIdx.x], se = cta_seg[blockIdx.x + 1];
-    if (sb >= se) return;
+    __shared__ Seg s_seg[MAXSEG];
+    __shared__ LocalSolve s_sol[MAXSEG];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
+    const int sb = a.cta_seg[blockIdx.x];
+    const int nseg = min(MAXSEG, a.cta_seg[blockIdx.x + 1] - sb);
+    if (tid < nseg) s_seg[tid] = a.segs[sb + tid];
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         fence_mbar_init();
     }
     __syncthreads();
+    const int first = nseg ? s_seg[0].solve : 0;
+    const int nloc = nseg ? s_seg[nseg - 1].solve - first + 1 : 0;
+    if (tid < nloc) {
+        const SolveDev& sv = a.solves[first + tid];
+        LocalSolve& L = s_sol[tid];
+        L.d = sv.d;
+        L.x = sv.x; L.r = sv.r; L.z = sv.z; L.pa = sv.pa; L.pb = sv.pb;
+        L.sc = sv.sc;
+        L.seg_begin = sv.seg_begin;
+        L.seg_end = sv.seg_end;
+        L.rz = sv.sc->rz;
+        L.rr = sv.sc->rr;
+        L.stop2 = sv.sc->stop2;
+        L.alpha = 0.0;
+        L.beta = 0.0;
+        L.done = sv.sc->done;
+        L.iter = 0;
+        L.max_iter = sv.sc->max_iter;
+        L.finished = 0;
+        L.owner = (sv.seg_begin >= sb && sv.seg_begin < sb + nseg) ? 1 : 0;
+        if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
+    }
+    __syncthreads();
 
-    Cursor cur{sb, 0, 0};
-    auto issue_next = [&]() {  // thread 0
-        while (cur.seg < se && cur.off == 0 && !seg_active(solves, segs[cur.seg])) ++cur.seg;
-        if (cur.seg >= se) return;
-        const Seg sg = segs[cur.seg];
-        const int st = cur.n % NS, kk = sg.k0 - 1 + cur.off;
-        unsigned char* dst = sm + st * G::A_STAGE;
-        const CUtensorMap* m = maps + 6 * sg.solve;
-        const int pm = pin_is_a ? MAP_PA : MAP_PB;
-        mbar_arrive_expect_tx(&bars[st], G::A_TX);
-        tma_load_3d(dst + G::A_Z, m + MAP_Z, &bars[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
-        tma_load_3d(dst + G::A_P, m + pm, &bars[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
-        tma_load_3d(dst + G::A_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
-        ++cur.n;
-        if (++cur.off == sg.k1 - sg.k0 + 2) {
-            cur.off = 0;
-            ++cur.seg;
-        }
-    };
-    if (tid == 0)
-        for (int q = 0; q < NS; ++q) issue_next();
+    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx, cc = CX * tx;
+    auto stage = [&](int q) { return sm + (q % NS) * G::STAGE; };
+    int g = 0;        // stream positions acquired (all threads)
+    int nissued = 0;  // stream positions issued (thread 0)
+    bool ok = true;
 
-    int g = 0;  // next stream position to acquire
-    bool ok = true, failed = false;
-    auto acquire = [&]() -> bool {
-        ok = ok && mbar_wait(&bars[g % NS], (g / NS) & 1);
-        if (__syncthreads_or(!ok)) return false;  // also: every thread is done with plane g-2
-        if (tid == 0 && g >= 2) issue_next();
-        ++g;
-        return true;
-    };
-    auto Zs = [&](int q) { return (const float*)(sm + (q % NS) * G::A_STAGE + G::A_Z); };
-    auto Ps = [&](int q) { return (const float*)(sm + (q % NS) * G::A_STAGE + G::A_P); };
-    auto Es = [&](int q) { return (const E*)(sm + (q % NS) * G::A_STAGE + G::A_E); };
-    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx;
-
-    for (int s = sb; s < se; ++s) {
-        const Seg sg = segs[s];
-        if (!seg_active(solves, sg)) continue;
-        const SolveDev& sv = solves[sg.solve];
-        const Dims d = sv.d;
-        const float beta = (float)sv.sc->beta;
-        float* p_out = pin_is_a ? sv.pb : sv.pa;
-        const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * ty;
-        auto centre_pn = [&](int q, float (&o)[CY][CX]) {
-            float zz[CY][CX], pp[CY][CX];
-            load_centre<CX, CY>(Zs(q), G::VW, r0, cv, zz);
-            load_centre<CX, CY>(Ps(q), G::VW, r0, cv, pp);
-#pragma unroll
-            for (int a = 0; a < CY; ++a)
-#pragma unroll
-                for (int b = 0; b < CX; ++b) o[a][b] = zz[a][b] + beta * pp[a][b];
+    // ---------------------------------------------------------------- one phase over the segments
+    // a_side: phase A (p = z + beta p_in, sum p.Ap) else phase B.  p_in_a: phase A reads pa.
+    auto run_phase = [&](bool a_side, bool p_in_a) -> bool {
+        int cs = 0, coff = 0;  // issue cursor (thread 0)
+        auto issue_next = [&]() {
+            while (cs < nseg && coff == 0 && s_sol[s_seg[cs].solve - first].done != RUNNING) ++cs;
+            if (cs >= nseg) return;
+            const Seg& sg = s_seg[cs];
+            const int L = sg.k1 - sg.k0, kk = sg.k0 - 1 + coff;
+            const int st = nissued % NS;
+            unsigned char* dst = sm + st * G::STAGE;
+            const CUtensorMap* m = a.maps + 6 * sg.solve;
+            if (a_side) {
+                mbar_arrive_expect_tx(&bars[st], G::A_TX);
+                tma_load_3d(dst + G::A_Z, m + MAP_Z, &bars[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
+                tma_load_3d(dst + G::A_P, m + (p_in_a ? MAP_PA : MAP_PB), &bars[st],
+                            sg.x0 - G::VOFF, sg.y0 - 1, kk);
+                tma_load_3d(dst + G::A_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+            } else {
+                const bool centre = coff > 0 && coff <= L;
+                mbar_arrive_expect_tx(&bars[st], centre ? G::B_TX : G::B_TX_HALO);
+                tma_load_3d(dst + G::B_P, m + (p_in_a ? MAP_PB : MAP_PA), &bars[st],
+                            sg.x0 - G::VOFF, sg.y0 - 1, kk);
+                tma_load_3d(dst + G::B_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+                if (centre) {
+                    tma_load_3d(dst + G::B_X, m + MAP_X, &bars[st], sg.x0, sg.y0, kk);
+                    tma_load_3d(dst + G::B_R, m + MAP_R, &bars[st], sg.x0, sg.y0, kk);
+                }
+            }
+            ++nissued;
+            if (++coff == L + 2) {
+                coff = 0;
+                ++cs;
+            }
         };
-        float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
-        if (!acquire()) { failed = true; break; }  // plane k0-1
-        centre_pn(g - 1, vm);
-        load_centre<CX, CY>(Es(g - 1), G::EW, r0, ce, em);
-        if (!acquire()) { failed = true; break; }  // plane k0
-        centre_pn(g - 1, vc);
-        load_centre<CX, CY>(Es(g - 1), G::EW, r0, ce, ec);
+        const int g0 = g;
+        if (tid == 0)
+            for (int q = 0; q < NS; ++q) issue_next();
+        auto acquire = [&]() -> bool {
+            ok = ok && mbar_wait(&bars[g % NS], (g / NS) & 1);
+            if (__syncthreads_or(!ok)) return false;  // also: every thread is done with g-2
+            if (tid == 0 && g - g0 >= 2) issue_next();
+            ++g;
+            return true;
+        };
+        for (int ls = 0; ls < nseg; ++ls) {
+            const Seg sg = s_seg[ls];
+            const int l = sg.solve - first;
+            if (s_sol[l].done != RUNNING) continue;
+            const Dims d = s_sol[l].d;
+            const float coefv = (float)(a_side ? s_sol[l].beta : s_sol[l].alpha);
+            const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * ty;
+            // centre values of a plane: p (phase B) or z + beta p_in (phase A)
+            auto centre = [&](int q, float (&o)[CY][CX]) {
+                const unsigned char* S = stage(q);
+                if (a_side) {
+                    float zz[CY][CX];
+                    load_centre<CX, CY>((const float*)(S + G::A_Z), G::VW, r0, cv, zz);
+                    load_centre<CX, CY>((const float*)(S + G::A_P), G::VW, r0, cv, o);
 #pragma unroll
-        for (int a = 0; a < CY; ++a)
+                    for (int y = 0; y < CY; ++y)
 #pragma unroll
-            for (int b = 0; b < CX; ++b)
-                wzl[a][b] = (sg.k0 > 0) ? rcp_approx(ec[a][b] + em[a][b]) : 0.f;
-        float acc = 0.f;
-        for (int k = sg.k0; k < sg.k1; ++k) {
-            if (!acquire()) { failed = true; break; }  // plane k+1 (lookahead)
-            const int qc = g - 2, qn = g - 1;
-            float vp[CY][CX], ep[CY][CX];
-            centre_pn(qn, vp);
-            load_centre<CX, CY>(Es(qn), G::EW, r0, ce, ep);
-            float zxm[CY], zxp[CY], zym[CX], zyp[CX];
-            float pxm[CY], pxp[CY], pym[CX], pyp[CX];
-            load_halo<CX, CY>(Zs(qc), G::VW, r0, cv, zxm, zxp, zym, zyp);
-            load_halo<CX, CY>(Ps(qc), G::VW, r0, cv, pxm, pxp, pym, pyp);
-            float vxm[CY], vxp[CY], vym[CX], vyp[CX];
+                        for (int x = 0; x < CX; ++x) o[y][x] = zz[y][x] + coefv * o[y][x];
+                } else {
+                    load_centre<CX, CY>((const float*)(S + G::B_P), G::VW, r0, cv, o);
+                }
+            };
+            auto eta_of = [&](int q) { return (const E*)(stage(q) + (a_side ? G::A_E : G::B_E)); };
+            float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
+            if (!acquire()) return false;  // plane k0-1
+            centre(g - 1, vm);
+            load_centre<CX, CY>(eta_of(g - 1), G::EW, r0, ce, em);
+            if (!acquire()) return false;  // plane k0
+            centre(g - 1, vc);
+            load_centre<CX, CY>(eta_of(g - 1), G::EW, r0, ce, ec);
 #pragma unroll
-            for (int a = 0; a < CY; ++a) {
-                vxm[a] = zxm[a] + beta * pxm[a];
-                vxp[a] = zxp[a] + beta * pxp[a];
-            }
+            for (int y = 0; y < CY; ++y)
 #pragma unroll
-            for (int b = 0; b < CX; ++b) {
-                vym[b] = zym[b] + beta * pym[b];
-                vyp[b] = zyp[b] + beta * pyp[b];
-            }
-            float exm[CY], exq[CY], eym[CX], eyp[CX];
-            load_halo<CX, CY>(Es(qc), G::EW, r0, ce, exm, exq, eym, eyp);
-            float qv[CY][CX], D[CY][CX];
-            stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym, eyp,
-                            ep, wzl, qv, D);
-            if (i0 < d.nx) {
+                for (int x = 0; x < CX; ++x)
+                    wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
+            float acc0 = 0.f, acc1 = 0.f;
+            for (int k = sg.k0; k < sg.k1; ++k) {
+                if (!acquire()) return false;  // plane k+1
+                const int qc = g - 2, qn = g - 1;
+                const unsigned char* S = stage(qc);
+                float vp[CY][CX], ep[CY][CX];
+                centre(qn, vp);
+                load_centre<CX, CY>(eta_of(qn), G::EW, r0, ce, ep);
+                float vxm[CY], vxp[CY], vym[CX], vyp[CX];
+                if (a_side) {
+                    float zxm[CY], zxp[CY], zym[CX], zyp[CX];
+                    load_halo<CX, CY>((const float*)(S + G::A_Z), G::VW, r0, cv, zxm, zxp, zym, zyp);
+                    load_halo<CX, CY>((const float*)(S + G::A_P), G::VW, r0, cv, vxm, vxp, vym, vyp);
 #pragma unroll
-                for (int a = 0; a < CY; ++a) {
-                    if (j0 + a < d.ny) {
+                    for (int y = 0; y < CY; ++y) {
+                        vxm[y] = zxm[y] + coefv * vxm[y];
+                        vxp[y] = zxp[y] + coefv * vxp[y];
+                    }
 #pragma unroll
-                        for (int b = 0; b < CX; ++b) acc += vc[a][b] * qv[a][b];
-                        st_row<CX>(p_out + (size_t)i0 + (size_t)d.nx * (j0 + a + (size_t)d.ny * k),
-                                   vc[a]);
+                    for (int x = 0; x < CX; ++x) {
+                        vym[x] = zym[x] + coefv * vym[x];
+                        vyp[x] = zyp[x] + coefv * vyp[x];
+                    }
+                } else {
+                    load_halo<CX, CY>((const float*)(S + G::B_P), G::VW, r0, cv, vxm, vxp, vym, vyp);
+                }
+                float exm[CY], exq[CY], eym[CX], eyp[CX];
+                load_halo<CX, CY>(eta_of(qc), G::EW, r0, ce, exm, exq, eym, eyp);
+                float qv[CY][CX], D[CY][CX];
+                stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym,
+                                eyp, ep, wzl, qv, D);
+                if (a_side) {
+                    float* p_out = p_in_a ? s_sol[l].pb : s_sol[l].pa;
+                    if (i0 < d.nx) {
+#pragma unroll
+                        for (int y = 0; y < CY; ++y) {
+                            if (j0 + y < d.ny) {
+#pragma unroll
+                                for (int x = 0; x < CX; ++x) acc0 += vc[y][x] * qv[y][x];
+                                st_row<CX>(p_out + (size_t)i0 +
+                                               (size_t)d.nx * (j0 + y + (size_t)d.ny * k), vc[y]);
+                            }
+                        }
+                    }
+                } else {
+                    float xo[CY][CX], ro[CY][CX];
+                    load_centre<CX, CY>((const float*)(S + G::B_X), G::W, CY * ty, cc, xo);
+                    load_centre<CX, CY>((const float*)(S + G::B_R), G::W, CY * ty, cc, ro);
+                    if (i0 < d.nx) {
+#pragma unroll
+                        for (int y = 0; y < CY; ++y) {
+                            if (j0 + y < d.ny) {
+                                float xn[CX], rn[CX], zn[CX];
+#pragma unroll
+                                for (int x = 0; x < CX; ++x) {
+                                    xn[x] = xo[y][x] + coefv * vc[y][x];
+                                    rn[x] = ro[y][x] - coefv * qv[y][x];
+                                    zn[x] = rn[x] * rcp_approx(D[y][x]);
+                                    acc0 += rn[x] * zn[x];
+                                    acc1 += rn[x] * rn[x];
+                                }
+                                const size_t c =
+                                    (size_t)i0 + (size_t)d.nx * (j0 + y + (size_t)d.ny * k);
+                                st_row<CX>(s_sol[l].x + c, xn);
+                                st_row<CX>(s_sol[l].r + c, rn);
+                                st_row<CX>(s_sol[l].z + c, zn);
+                            }
+                        }
                     }
                 }
+#pragma unroll
+                for (int y = 0; y < CY; ++y)
+#pragma unroll
+                    for (int x = 0; x < CX; ++x) {
+                        vm[y][x] = vc[y][x];
+                        vc[y][x] = vp[y][x];
+                        ec[y][x] = ep[y][x];
+                    }
             }
-#pragma unroll
-            for (int a = 0; a < CY; ++a)
-#pragma unroll
-                for (int b = 0; b < CX; ++b) {
-                    vm[a][b] = vc[a][b];
-                    vc[a][b] = vp[a][b];
-                    ec[a][b] = ep[a][b];
+            // the segment's partial sums
+            double v[2] = {(double)acc0, (double)acc1};
+            block_sum<2>(v, red);
+            if (tid == 0) {
+                if (a_side)
+                    a.part_a[sb + ls] = v[0];
+                else {
+                    a.part_b[2 * (size_t)(sb + ls)] = v[0];
+                    a.part_b[2 * (size_t)(sb + ls) + 1] = v[1];
                 }
+            }
         }
-        if (failed) break;
-        double v[1] = {(double)acc}, tot[1];
-        if (segment_done<1>(sv, s, v, seg_part, tot, red, tid, 32 * TYT)) {
-            if (tid == 0 && sv.sc->done == RUNNING) {
-                const double pq = tot[0];
-                if (!(pq > 0.0) || !isfinite(pq)) {
-                    sv.sc->done = BREAKDOWN;
+        return true;
+    };
+
+    unsigned nbar = 0;
+    bool p_in_a = true;
+    bool failed = false;
+    for (;;) {
+        if (!run_phase(true, p_in_a)) { failed = true; break; }
+        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (*(volatile int*)&a.ctl->running == 0) break;
+        for (int l = 0; l < nloc; ++l) {
+            if (s_sol[l].done != RUNNING) continue;
+            double t[1];
+            range_sum<1>(a.part_a, s_sol[l].seg_begin, s_sol[l].seg_end, t, red, tid, NT);
+            if (tid == 0) {
+                if (!(t[0] > 0.0) || !isfinite(t[0])) {
+                    s_sol[l].done = BREAKDOWN;
+                    s_sol[l].finished = 1;
                 } else {
-                    sv.sc->pq = pq;
-                    sv.sc->alpha = sv.sc->rz / pq;
+                    s_sol[l].alpha = s_sol[l].rz / t[0];
                 }
             }
+            __syncthreads();
         }
-    }
-    if (failed) {
-        if (tid == 0) {
-            for (int s = sb; s < se; ++s) atomicExch(&solves[segs[s].solve].sc->done, (int)TIMEDOUT);
-            for (int q = g; q < cur.n; ++q) (void)mbar_wait(&bars[q % NS], (q / NS) & 1);
-            __threadfence();
+        if (!run_phase(false, p_in_a)) { failed = true; break; }
+        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        for (int l = 0; l < nloc; ++l) {
+            if (s_sol[l].done != RUNNING) continue;
+            double t[2];
+            range_sum<2>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, red, tid, NT);
+            if (tid == 0) {
+                LocalSolve& L = s_sol[l];
+                L.iter += 1;
+                L.rr = t[1];
+                if (!isfinite(t[0]) || !isfinite(t[1]) || t[0] < 0.0) {
+                    L.done = BREAKDOWN;
+                } else if (t[1] <= L.stop2) {
+                    L.done = CONVERGED;
+                } else if (L.iter >= L.max_iter) {
+                    L.done = CAPPED;
+                } else {
+                    L.beta = t[0] / L.rz;
+                    L.rz = t[0];
+                }
+                if (L.done != RUNNING) L.finished = 1;
+            }
+            __syncthreads();
+        }
+        // owners publish the solves that finished in this iteration (the only window in which
+        // ctl->running changes: between the phase-B barrier and the next phase-A barrier)
+        if (tid < nloc) {
+            LocalSolve& L = s_sol[tid];
+            if (L.finished) {
+                L.finished = 0;
+                if (L.owner) {
+                    L.sc->iter = L.iter;
+                    L.sc->rr = L.rr;
+                    L.sc->rz = L.rz;
+                    L.sc->done = L.done;
+                    __threadfence();
+                    atomicSub(&a.ctl->running, 1);
+                }
+            }
         }
         __syncthreads();
-    }
-}
-
-template <int CX, int CY, int TYT, typename E>
-__global__ void __launch_bounds__(32 * TYT) k_march_b(const SolveDev* __restrict__ solves,
-                                                     const Seg* __restrict__ segs,
-                                                     const int* __restrict__ cta_seg,
-                                                     const CUtensorMap* __restrict__ maps,
-                                                     double* seg_part, int p_is_a) {
-    using G = Geo<CX, CY, TYT, E>;
-    extern __shared__ __align__(128) unsigned char sm[];
-    __shared__ __align__(8) uint64_t bars[NS];
-    __shared__ double red[64];
-    const int sb = cta_seg[blockIdx.x], se = cta_seg[blockIdx.x + 1];
-    if (sb >= se) return;
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
-    if (tid == 0) {
-        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    Cursor cur{sb, 0, 0};
-    auto issue_next = [&]() {  // thread 0
-        while (cur.seg < se && cur.off == 0 && !seg_active(solves, segs[cur.seg])) ++cur.seg;
-        if (cur.seg >= se) return;
-        const Seg sg = segs[cur.seg];
-        const int L = sg.k1 - sg.k0;
-        const int st = cur.n % NS, kk = sg.k0 - 1 + cur.off;
-        unsigned char* dst = sm + st * G::B_STAGE;
-        const CUtensorMap* m = maps + 6 * sg.solve;
-        const bool centre = cur.off > 0 && cur.off <= L;
-        mbar_arrive_expect_tx(&bars[st], centre ? G::B_TX : G::B_TX_HALO);
-        tma_load_3d(dst + G::B_P, m + (p_is_a ? MAP_PA : MAP_PB), &bars[st], sg.x0 - G::VOFF,
-                    sg.y0 - 1, kk);
-        tma_load_3d(dst + G::B_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
-        if (centre) {
-            tma_load_3d(dst + G::B_X, m + MAP_X, &bars[st], sg.x0, sg.y0, kk);
-            tma_load_3d(dst + G::B_R, m + MAP_R, &bars[st], sg.x0, sg.y0, kk);
-        }
-        ++cur.n;
-        if (++cur.off == L + 2) {
-            cur.off = 0;
-            ++cur.seg;
-        }
-    };
-    if (tid == 0)
-        for (int q = 0; q < NS; ++q) issue_next();
-
-    int g = 0;
-    bool ok = true, failed = false;
-    auto acquire = [&]() -> bool {
-        ok = ok && mbar_wait(&bars[g % NS], (g / NS) & 1);
-        if (__syncthreads_or(!ok)) return false;
-        if (tid == 0 && g >= 2) issue_next();
-        ++g;
-        return true;
-    };
-    auto Ps = [&](int q) { return (const float*)(sm + (q % NS) * G::B_STAGE + G::B_P); };
-    auto Es = [&](int q) { return (const E*)(sm + (q % NS) * G::B_STAGE + G::B_E); };
-    auto Xs = [&](int q) { return (const float*)(sm + (q % NS) * G::B_STAGE + G::B_X); };
-    auto Rs = [&](int q) { return (const float*)(sm + (q % NS) * G::B_STAGE + G::B_R); };
-    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx;
-    const int cc = CX * tx;
-
-    for (int s = sb; s < se; ++s) {
-        const Seg sg = segs[s];
-        if (!seg_active(solves, sg)) continue;
-        const SolveDev& sv = solves[sg.solve];
-        const Dims d = sv.d;
-        const float alpha = (float)sv.sc->alpha;
-        float* x = sv.x;
-        float* r = sv.r;
-        float* z = sv.z;
-        const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * ty;
-        float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
-        if (!acquire()) { failed = true; break; }
-        load_centre<CX, CY>(Ps(g - 1), G::VW, r0, cv, vm);
-        load_centre<CX, CY>(Es(g - 1), G::EW, r0, ce, em);
-        if (!acquire()) { failed = true; break; }
-        load_centre<CX, CY>(Ps(g - 1), G::VW, r0, cv, vc);
-        load_centre<CX, CY>(Es(g - 1), G::EW, r0, ce, ec);
-#pragma unroll
-        for (int a = 0; a < CY; ++a)
-#pragma unroll
-            for (int b = 0; b < CX; ++b)
-                wzl[a][b] = (sg.k0 > 0) ? rcp_approx(ec[a][b] + em[a][b]) : 0.f;
-        float arz = 0.f, arr = 0.f;
-        for (int k = sg.k0; k < sg.k1; ++k) {
-            if (!acquire()) { failed = true; break; }
-            const int qc = g - 2, qn = g - 1;
-            float vp[CY][CX], ep[CY][CX];
-            load_centre<CX, CY>(Ps(qn), G::VW, r0, cv, vp);
-            load_centre<CX, CY>(Es(qn), G::EW, r0, ce, ep);
-            float vxm[CY], vxp[CY], vym[CX], vyp[CX];
-            load_halo<CX, CY>(Ps(qc), G::VW, r0, cv, vxm, vxp, vym, vyp);
-            float exm[CY], exq[CY], eym[CX], eyp[CX];
-            load_halo<CX, CY>(Es(qc), G::EW, r0, ce, exm, exq, eym, eyp);
-            float qv[CY][CX], D[CY][CX];
-            stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym, eyp,
-                            ep, wzl, qv, D);
-            float xo[CY][CX], ro[CY][CX];
-            load_centre<CX, CY>(Xs(qc), G::W, CY * ty, cc, xo);
-            load_centre<CX, CY>(Rs(qc), G::W, CY * ty, cc, ro);
-            if (i0 < d.nx) {
-#pragma unroll
-                for (int a = 0; a < CY; ++a) {
-                    if (j0 + a < d.ny) {
-                        float xn[CX], rn[CX], zn[CX];
-#pragma unroll
-                        for (int b = 0; b < CX; ++b) {
-                            xn[b] = xo[a][b] + alpha * vc[a][b];
-                            rn[b] = ro[a][b] - alpha * qv[a][b];
-                            zn[b] = rn[b] * rcp_approx(D[a][b]);
-                            arz += rn[b] * zn[b];
-                            arr += rn[b] * rn[b];
-                        }
-                        const size_t c = (size_t)i0 + (size_t)d.nx * (j0 + a + (size_t)d.ny * k);
-                        st_row<CX>(x + c, xn);
-                        st_row<CX>(r + c, rn);
-                        st_row<CX>(z + c, zn);
-                    }
-                }
-            }
-#pragma unroll
-            for (int a = 0; a < CY; ++a)
-#pragma unroll
-                for (int b = 0; b < CX; ++b) {
-                    vm[a][b] = vc[a][b];
-                    vc[a][b] = vp[a][b];
-                    ec[a][b] = ep[a][b];
-                }
-        }
-        if (failed) break;
-        double v[2] = {(double)arz, (double)arr}, tot[2];
-        if (segment_done<2>(sv, s, v, seg_part, tot, red, tid, 32 * TYT)) {
-            Scalars* sc = sv.sc;
-            if (tid == 0 && sc->done == RUNNING) {
-                const double rz_new = tot[0], rr_new = tot[1];
-                sc->iter += 1;
-                sc->rr = rr_new;
-                if (!isfinite(rz_new) || !isfinite(rr_new) || rz_new < 0.0) {
-                    sc->done = BREAKDOWN;
-                } else if (rr_new <= sc->stop2) {
-                    sc->done = CONVERGED;
-                } else if (sc->iter >= sc->max_iter) {
-                    sc->done = CAPPED;
-                } else {
-                    sc->beta = rz_new / sc->rz;
-                    sc->rz = rz_new;
-                }
-            }
-        }
+        p_in_a = !p_in_a;
     }
     if (failed) {
         if (tid == 0) {
-            for (int s = sb; s < se; ++s) atomicExch(&solves[segs[s].solve].sc->done, (int)TIMEDOUT);
-            for (int q = g; q < cur.n; ++q) (void)mbar_wait(&bars[q % NS], (q / NS) & 1);
+            atomicExch(&a.ctl->error, 1);
+            for (int l = 0; l < nloc; ++l) {
+                s_sol[l].sc->iter = s_sol[l].iter;
+                atomicExch(&s_sol[l].sc->done, (int)TIMEDOUT);
+            }
+            for (int q = g; q < nissued; ++q) (void)mbar_wait(&bars[q % NS], (q / NS) & 1);
             __threadfence();
         }
         __syncthreads();
@@ -603,20 +608,16 @@ bool march_supported(const Dims& d) {
 // A variant is (CX, CY, TYT); its tile is 32 CX wide and CY TYT high.
 struct VariantOps {
     int cx, cy, tyt;
-    int smem_a32, smem_b32, smem_a16, smem_b16;
-    const void *ka32, *kb32, *ka16, *kb16;
+    int smem32, smem16;
+    const void *k32, *k16;
 };
 
 template <int CX, int CY, int TYT>
 static VariantOps make_ops() {
-    using G32 = Geo<CX, CY, TYT, float>;
-    using G16 = Geo<CX, CY, TYT, __nv_bfloat16>;
-    return VariantOps{CX, CY, TYT,
-                      NS * G32::A_STAGE, NS * G32::B_STAGE, NS * G16::A_STAGE, NS * G16::B_STAGE,
-                      (const void*)k_march_a<CX, CY, TYT, float>,
-                      (const void*)k_march_b<CX, CY, TYT, float>,
-                      (const void*)k_march_a<CX, CY, TYT, __nv_bfloat16>,
-                      (const void*)k_march_b<CX, CY, TYT, __nv_bfloat16>};
+    return VariantOps{CX, CY, TYT, NS * Geo<CX, CY, TYT, float>::STAGE,
+                      NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
+                      (const void*)k_pcg<CX, CY, TYT, float>,
+                      (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16>};
 }
 
 #define MARCH_VARIANTS(X) X(0, 1, 1, 4) X(1, 1, 1, 8) X(2, 1, 1, 16) X(3, 2, 2, 2) \
@@ -629,10 +630,8 @@ static const VariantOps* variants(int* count) {
     static std::once_flag once;
     std::call_once(once, [] {
         for (const auto& v : table) {
-            cudaFuncSetAttribute(v.ka32, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem_a32);
-            cudaFuncSetAttribute(v.kb32, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem_b32);
-            cudaFuncSetAttribute(v.ka16, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem_a16);
-            cudaFuncSetAttribute(v.kb16, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem_b16);
+            cudaFuncSetAttribute(v.k32, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem32);
+            cudaFuncSetAttribute(v.k16, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem16);
         }
         cudaGetLastError();
     });
@@ -664,16 +663,13 @@ int march_find_variant(int cx, int cy, int tyt) {
 int march_occupancy(int variant, bool bf16) {
     int n;
     const VariantOps& v = variants(&n)[variant];
-    int oa = 0, ob = 0;
-    const int threads = 32 * v.tyt;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oa, bf16 ? v.ka16 : v.ka32, threads,
-                                                      bf16 ? v.smem_a16 : v.smem_a32) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ob, bf16 ? v.kb16 : v.kb32, threads,
-                                                      bf16 ? v.smem_b16 : v.smem_b32) != cudaSuccess) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, bf16 ? v.k16 : v.k32, 32 * v.tyt,
+                                                      bf16 ? v.smem16 : v.smem32) != cudaSuccess) {
         cudaGetLastError();
-        return 1;
+        return 0;
     }
-    return std::max(1, std::min(oa, ob));
+    return o;
 }
 
 // ------------------------------------------------------------------ plans
@@ -694,7 +690,7 @@ bool march_encode_solve(CUtensorMap (&m)[6], const MarchSolve& s, int variant, b
 }
 
 void march_plan_free(MarchPlan* p) {
-    void* ptrs[] = {p->solves, p->segs, p->cta_seg, p->maps, p->seg_part};
+    void* ptrs[] = {p->solves, p->segs, p->cta_seg, p->maps, p->part_a, p->part_b, p->ctl};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     *p = MarchPlan{};
@@ -702,7 +698,8 @@ void march_plan_free(MarchPlan* p) {
 
 // Splits the solves' tile columns into segments and gives every CTA an equal share of the
 // linearised (solve, tile, plane) space: CTA c owns planes [c W / G, (c + 1) W / G), cut into
-// one segment per tile column it touches.  Segments come out ordered by solve.
+// one segment per tile column it touches.  Segments come out ordered by solve.  Fails (-1) if a
+// CTA would hold more than MAXSEG segments or a tensor map cannot be encoded.
 int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int variant, bool bf16,
                      int nctas, cudaStream_t st) {
     march_plan_free(p);
@@ -743,6 +740,8 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
         }
     }
     cta_seg[nctas] = (int)segs.size();
+    for (int c = 0; c < nctas; ++c)
+        if (cta_seg[c + 1] - cta_seg[c] > MAXSEG) return -1;
     for (int s = 0; s < nsolves; ++s) {
         sd[s].d = solves[s].d;
         sd[s].x = solves[s].x;
@@ -782,7 +781,9 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
               up((void**)&p->segs, segs.data(), sizeof(Seg) * segs.size()) &&
               up((void**)&p->cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size()) &&
               up((void**)&p->maps, maps.data(), sizeof(CUtensorMap) * maps.size());
-    if (ok && cudaMalloc((void**)&p->seg_part, sizeof(double) * 2 * segs.size()) != cudaSuccess) {
+    if (ok && (cudaMalloc((void**)&p->part_a, sizeof(double) * segs.size()) != cudaSuccess ||
+               cudaMalloc((void**)&p->part_b, sizeof(double) * 2 * segs.size()) != cudaSuccess ||
+               cudaMalloc((void**)&p->ctl, sizeof(MarchCtl)) != cudaSuccess)) {
         cudaGetLastError();
         ok = false;
     }
@@ -794,44 +795,20 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
     return 0;
 }
 
-template <int CX, int CY, int TYT, typename E>
-static void launch_ab(const MarchPlan& p, bool a_side, int flag, cudaStream_t st) {
-    using G = Geo<CX, CY, TYT, E>;
-    const dim3 block(32, TYT);
-    if (a_side)
-        k_march_a<CX, CY, TYT, E><<<p.nctas, block, NS * G::A_STAGE, st>>>(
-            p.solves, p.segs, p.cta_seg, p.maps, p.seg_part, flag);
-    else
-        k_march_b<CX, CY, TYT, E><<<p.nctas, block, NS * G::B_STAGE, st>>>(
-            p.solves, p.segs, p.cta_seg, p.maps, p.seg_part, flag);
-    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-}
-
-template <typename E>
-static void dispatch(const MarchPlan& p, bool a_side, int flag, cudaStream_t st) {
+int launch_march_pcg(const MarchPlan& p, cudaStream_t st) {
     int n;
-    variants(&n);  // function attributes set
-    switch (p.variant) {
-#define CASE(ID, CX, CY, TYT) \
-    case ID: launch_ab<CX, CY, TYT, E>(p, a_side, flag, st); break;
-        MARCH_VARIANTS(CASE)
-#undef CASE
-        default: break;
+    const VariantOps& v = variants(&n)[p.variant];
+    PcgArgs args{p.solves, p.segs, p.cta_seg, p.maps, p.part_a, p.part_b, p.ctl, p.nctas};
+    void* params[] = {&args};
+    const cudaError_t e = cudaLaunchCooperativeKernel(p.bf16 ? v.k16 : v.k32, dim3(p.nctas),
+                                                      dim3(32, v.tyt), params,
+                                                      (size_t)(p.bf16 ? v.smem16 : v.smem32), st);
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
     }
-}
-
-void launch_march_a(const MarchPlan& p, bool pin_is_a, cudaStream_t st) {
-    if (p.bf16)
-        dispatch<__nv_bfloat16>(p, true, pin_is_a ? 1 : 0, st);
-    else
-        dispatch<float>(p, true, pin_is_a ? 1 : 0, st);
-}
-
-void launch_march_b(const MarchPlan& p, bool p_is_a, cudaStream_t st) {
-    if (p.bf16)
-        dispatch<__nv_bfloat16>(p, false, p_is_a ? 1 : 0, st);
-    else
-        dispatch<float>(p, false, p_is_a ? 1 : 0, st);
+    return 0;
 }
 
 }  // namespace pcg

@@ -39,6 +39,14 @@ struct Seg {
     int solve, x0, y0, k0, k1, pad0, pad1, pad2;
 };
 
+// Control words of one persistent launch (set by the host before the launch).
+struct MarchCtl {
+    unsigned bar;  // grid-barrier arrivals (0 at launch)
+    int running;   // solves not finished (the number of solves at launch)
+    int error;     // 1 once a wait has timed out
+    int pad;
+};
+
 // A persistent launch: nctas CTAs, CTA c owns segments [cta_seg[c], cta_seg[c+1]).
 struct MarchPlan {
     int variant = 0;
@@ -48,14 +56,28 @@ struct MarchPlan {
     Seg* segs = nullptr;
     int* cta_seg = nullptr;
     CUtensorMap* maps = nullptr;
-    double* seg_part = nullptr;
+    double* part_a = nullptr;  // per segment: p.Ap
+    double* part_b = nullptr;  // per segment: r.z, r.r
+    MarchCtl* ctl = nullptr;
+};
+
+// Kernel parameters of the persistent PCG launch.
+struct PcgArgs {
+    const SolveDev* solves;
+    const Seg* segs;
+    const int* cta_seg;
+    const CUtensorMap* maps;
+    double* part_a;
+    double* part_b;
+    MarchCtl* ctl;
+    int nctas;
 };
 
 bool march_supported(const Dims& d);
 int march_variant_count();
 MarchVariant march_variant(int id);
 int march_find_variant(int cx, int cy, int tyt);  // -1 if there is none
-int march_occupancy(int variant, bool bf16);       // resident CTAs per SM (min of both phases)
+int march_occupancy(int variant, bool bf16);       // resident CTAs per SM (0 if unknown)
 
 // Builds (device arrays allocated, copied on st, synchronised) / frees a plan.  0 on success,
 // -1 if a tensor map cannot be encoded, -2 on allocation failure.
@@ -63,9 +85,8 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
                      int nctas, cudaStream_t st);
 void march_plan_free(MarchPlan* p);
 
-// phase A: p = z + beta p_in (p_in = pa if pin_is_a else pb; p written to the other buffer).
-void launch_march_a(const MarchPlan& p, bool pin_is_a, cudaStream_t st);
-// phase B: reads p (pa if p_is_a else pb), eta, x, r; writes x, r, z.
-void launch_march_b(const MarchPlan& p, bool p_is_a, cudaStream_t st);
+// Cooperative launch of the persistent PCG over the plan (every solve's r, z, scalars
+// initialised, pa zeroed, *ctl set).  0 on success, -1 if the launch was refused.
+int launch_march_pcg(const MarchPlan& p, cudaStream_t st);
 
 }  // namespace pcg
