@@ -155,7 +155,8 @@ static int setup_march(poisson_t* H) {
     const int forced = H->opts.tile;
     int var = -1;
     if (forced > 0) {
-        var = march_find_variant(forced / 1000, (forced / 100) % 10, forced % 100);
+        var = march_find_variant((forced / 1000) % 10, (forced / 100) % 10, forced % 100,
+                                 forced / 10000);
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(TuneKey{d.nx, d.ny, d.nz, bf16 ? 1 : 0});
@@ -232,8 +233,8 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (o.precond != POISSON_JACOBI && o.precond != POISSON_RBSSOR) return POISSON_EINVAL;
     if (!(o.omega > 0.0 && o.omega < 2.0)) return POISSON_EINVAL;
     if (o.max_iters <= 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return POISSON_EINVAL;
-    if (o.tile < -1 || (o.tile > 0 && march_find_variant(o.tile / 1000, (o.tile / 100) % 10,
-                                                          o.tile % 100) < 0))
+    if (o.tile < -1 || (o.tile > 0 && march_find_variant((o.tile / 1000) % 10, (o.tile / 100) % 10,
+                                                          o.tile % 100, o.tile / 10000) < 0))
         return POISSON_EINVAL;
 
     poisson_t* H = new (std::nothrow) poisson_t();
@@ -701,9 +702,9 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
     if (H->march) {
         const MarchVariant v = march_variant(H->plan.variant);
         snprintf(buf, (size_t)len,
-                 "%s march tile=%d (%dx%d cells, %dx%d per thread) persistent ctas=%d segments=%d",
-                 prec, 1000 * v.cx + 100 * v.cy + v.tyt, v.width, v.height, v.cx, v.cy,
-                 H->plan.nctas, H->plan.nsegs);
+                 "%s march tile=%d (%dx%d cells, %dx%d per thread%s) persistent ctas=%d segments=%d",
+                 prec, 10000 * v.ws + 1000 * v.cx + 100 * v.cy + v.tyt, v.width, v.height, v.cx,
+                 v.cy, v.ws ? ", producer warp" : "", H->plan.nctas, H->plan.nsegs);
     } else {
         snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d", prec, TX, TY, H->kc);
     }

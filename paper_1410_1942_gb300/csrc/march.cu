@@ -569,6 +569,364 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     }
 }
 
+// ------------------------------------------------------------------ warp-specialised variant
+// Same work list, phases, grid barriers and reductions as k_pcg, but with a producer warp: its
+// lane 0 walks the plane stream issuing TMA loads into the NS-stage ring, waiting on an "empty"
+// mbarrier per stage (one arrival per consumer warp) before refilling it.  The TYT consumer
+// warps wait on the "full" barriers, compute, and release each plane after its last use, so no
+// block-wide barrier is taken per plane.  A timed-out wait sets s_fail; from then on every wait
+// returns at once, so all warps still pass the same named barriers and leave together.
+template <int CX, int CY, int TYT, typename E>
+__global__ void __launch_bounds__(32 * (TYT + 1)) k_pcg_ws(PcgArgs a) {
+    using G = Geo<CX, CY, TYT, E>;
+    constexpr int NT = 32 * (TYT + 1);  // all threads
+    constexpr int NC = 32 * TYT;        // consumer threads
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ __align__(8) uint64_t full[NS];
+    __shared__ __align__(8) uint64_t empty[NS];
+    __shared__ double red[64];
+    __shared__ Seg s_seg[MAXSEG];
+    __shared__ LocalSolve s_sol[MAXSEG];
+    __shared__ int s_member[MAXSEG];  // solve streamed in this iteration
+    __shared__ volatile int s_fail;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
+    const bool producer = (ty == TYT);
+    const int sb = a.cta_seg[blockIdx.x];
+    const int nseg = min(MAXSEG, a.cta_seg[blockIdx.x + 1] - sb);
+    if (tid < nseg) s_seg[tid] = a.segs[sb + tid];
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TYT);
+        }
+        fence_mbar_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+    const int first = nseg ? s_seg[0].solve : 0;
+    const int nloc = nseg ? s_seg[nseg - 1].solve - first + 1 : 0;
+    if (tid < nloc) {
+        const SolveDev& sv = a.solves[first + tid];
+        LocalSolve& L = s_sol[tid];
+        L.d = sv.d;
+        L.x = sv.x; L.r = sv.r; L.z = sv.z; L.pa = sv.pa; L.pb = sv.pb;
+        L.sc = sv.sc;
+        L.seg_begin = sv.seg_begin;
+        L.seg_end = sv.seg_end;
+        L.rz = sv.sc->rz;
+        L.rr = sv.sc->rr;
+        L.stop2 = sv.sc->stop2;
+        L.alpha = 0.0;
+        L.beta = 0.0;
+        L.done = sv.sc->done;
+        L.iter = 0;
+        L.max_iter = sv.sc->max_iter;
+        L.finished = 0;
+        L.owner = (sv.seg_begin >= sb && sv.seg_begin < sb + nseg) ? 1 : 0;
+        s_member[tid] = (L.done == RUNNING);
+        if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
+    }
+    __syncthreads();
+
+    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx, cc = CX * tx;
+    const int warp = ty, lane = tx;
+    auto stage = [&](int q) { return sm + (q % NS) * G::STAGE; };
+    int np = 0;  // planes issued (producer lane 0)
+    int nc = 0;  // planes acquired (each consumer warp)
+
+    auto produce = [&](bool a_side, bool p_in_a) {
+        for (int ls = 0; ls < nseg; ++ls) {
+            const Seg& sg = s_seg[ls];
+            if (!s_member[sg.solve - first]) continue;
+            const int L = sg.k1 - sg.k0;
+            const CUtensorMap* m = a.maps + 6 * sg.solve;
+            for (int off = 0; off < L + 2; ++off) {
+                if (s_fail) return;
+                const int st = np % NS, kk = sg.k0 - 1 + off;
+                if (np >= NS && !mbar_wait_or(&empty[st], ((np / NS) - 1) & 1, &s_fail)) {
+                    s_fail = 1;
+                    return;
+                }
+                unsigned char* dst = sm + st * G::STAGE;
+                if (a_side) {
+                    mbar_arrive_expect_tx(&full[st], G::A_TX);
+                    tma_load_3d(dst + G::A_Z, m + MAP_Z, &full[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
+                    tma_load_3d(dst + G::A_P, m + (p_in_a ? MAP_PA : MAP_PB), &full[st],
+                                sg.x0 - G::VOFF, sg.y0 - 1, kk);
+                    tma_load_3d(dst + G::A_E, m + MAP_ETA, &full[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+                } else {
+                    const bool centre = off > 0 && off <= L;
+                    mbar_arrive_expect_tx(&full[st], centre ? G::B_TX : G::B_TX_HALO);
+                    tma_load_3d(dst + G::B_P, m + (p_in_a ? MAP_PB : MAP_PA), &full[st],
+                                sg.x0 - G::VOFF, sg.y0 - 1, kk);
+                    tma_load_3d(dst + G::B_E, m + MAP_ETA, &full[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+                    if (centre) {
+                        tma_load_3d(dst + G::B_X, m + MAP_X, &full[st], sg.x0, sg.y0, kk);
+                        tma_load_3d(dst + G::B_R, m + MAP_R, &full[st], sg.x0, sg.y0, kk);
+                    }
+                }
+                ++np;
+            }
+        }
+    };
+
+    auto consume = [&](bool a_side, bool p_in_a) {
+        auto acquire = [&]() -> bool {
+            const int q = nc++;
+            if (s_fail) return false;
+            if (!mbar_wait_or(&full[q % NS], (q / NS) & 1, &s_fail)) {
+                s_fail = 1;
+                return false;
+            }
+            return true;
+        };
+        auto release = [&](int q) {
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[q % NS]);
+        };
+        for (int ls = 0; ls < nseg; ++ls) {
+            const Seg sg = s_seg[ls];
+            const int l = sg.solve - first;
+            if (!s_member[l]) continue;
+            const bool work = s_sol[l].done == RUNNING;
+            const Dims d = s_sol[l].d;
+            const float coefv = (float)(a_side ? s_sol[l].beta : s_sol[l].alpha);
+            const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * warp;
+            auto centre = [&](int q, float (&o)[CY][CX]) {
+                const unsigned char* S = stage(q);
+                if (a_side) {
+                    float zz[CY][CX];
+                    load_centre<CX, CY>((const float*)(S + G::A_Z), G::VW, r0, cv, zz);
+                    load_centre<CX, CY>((const float*)(S + G::A_P), G::VW, r0, cv, o);
+#pragma unroll
+                    for (int y = 0; y < CY; ++y)
+#pragma unroll
+                        for (int x = 0; x < CX; ++x) o[y][x] = zz[y][x] + coefv * o[y][x];
+                } else {
+                    load_centre<CX, CY>((const float*)(S + G::B_P), G::VW, r0, cv, o);
+                }
+            };
+            auto eta_of = [&](int q) { return (const E*)(stage(q) + (a_side ? G::A_E : G::B_E)); };
+            float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
+            const int p0 = nc;
+            bool ok = acquire();  // plane k0-1
+            if (ok && work) {
+                centre(p0, vm);
+                load_centre<CX, CY>(eta_of(p0), G::EW, r0, ce, em);
+            }
+            release(p0);
+            ok = acquire();  // plane k0
+            if (ok && work) {
+                centre(p0 + 1, vc);
+                load_centre<CX, CY>(eta_of(p0 + 1), G::EW, r0, ce, ec);
+#pragma unroll
+                for (int y = 0; y < CY; ++y)
+#pragma unroll
+                    for (int x = 0; x < CX; ++x)
+                        wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
+            }
+            float acc0 = 0.f, acc1 = 0.f;
+            for (int k = sg.k0; k < sg.k1; ++k) {
+                const int qc = p0 + 1 + (k - sg.k0), qn = qc + 1;
+                ok = acquire();  // plane k+1
+                if (ok && work) {
+                    const unsigned char* S = stage(qc);
+                    float vp[CY][CX], ep[CY][CX];
+                    centre(qn, vp);
+                    load_centre<CX, CY>(eta_of(qn), G::EW, r0, ce, ep);
+                    float vxm[CY], vxp[CY], vym[CX], vyp[CX];
+                    if (a_side) {
+                        float zxm[CY], zxp[CY], zym[CX], zyp[CX];
+                        load_halo<CX, CY>((const float*)(S + G::A_Z), G::VW, r0, cv, zxm, zxp, zym, zyp);
+                        load_halo<CX, CY>((const float*)(S + G::A_P), G::VW, r0, cv, vxm, vxp, vym, vyp);
+#pragma unroll
+                        for (int y = 0; y < CY; ++y) {
+                            vxm[y] = zxm[y] + coefv * vxm[y];
+                            vxp[y] = zxp[y] + coefv * vxp[y];
+                        }
+#pragma unroll
+                        for (int x = 0; x < CX; ++x) {
+                            vym[x] = zym[x] + coefv * vym[x];
+                            vyp[x] = zyp[x] + coefv * vyp[x];
+                        }
+                    } else {
+                        load_halo<CX, CY>((const float*)(S + G::B_P), G::VW, r0, cv, vxm, vxp, vym, vyp);
+                    }
+                    float exm[CY], exq[CY], eym[CX], eyp[CX];
+                    load_halo<CX, CY>(eta_of(qc), G::EW, r0, ce, exm, exq, eym, eyp);
+                    float qv[CY][CX], D[CY][CX];
+                    stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym,
+                                    eyp, ep, wzl, qv, D);
+                    if (a_side) {
+                        float* p_out = p_in_a ? s_sol[l].pb : s_sol[l].pa;
+                        if (i0 < d.nx) {
+#pragma unroll
+                            for (int y = 0; y < CY; ++y) {
+                                if (j0 + y < d.ny) {
+#pragma unroll
+                                    for (int x = 0; x < CX; ++x) acc0 += vc[y][x] * qv[y][x];
+                                    st_row<CX>(p_out + (size_t)i0 +
+                                                   (size_t)d.nx * (j0 + y + (size_t)d.ny * k), vc[y]);
+                                }
+                            }
+                        }
+                    } else {
+                        float xo[CY][CX], ro[CY][CX];
+                        load_centre<CX, CY>((const float*)(S + G::B_X), G::W, CY * warp, cc, xo);
+                        load_centre<CX, CY>((const float*)(S + G::B_R), G::W, CY * warp, cc, ro);
+                        if (i0 < d.nx) {
+#pragma unroll
+                            for (int y = 0; y < CY; ++y) {
+                                if (j0 + y < d.ny) {
+                                    float xn[CX], rn[CX], zn[CX];
+#pragma unroll
+                                    for (int x = 0; x < CX; ++x) {
+                                        xn[x] = xo[y][x] + coefv * vc[y][x];
+                                        rn[x] = ro[y][x] - coefv * qv[y][x];
+                                        zn[x] = rn[x] * rcp_approx(D[y][x]);
+                                        acc0 += rn[x] * zn[x];
+                                        acc1 += rn[x] * rn[x];
+                                    }
+                                    const size_t c =
+                                        (size_t)i0 + (size_t)d.nx * (j0 + y + (size_t)d.ny * k);
+                                    st_row<CX>(s_sol[l].x + c, xn);
+                                    st_row<CX>(s_sol[l].r + c, rn);
+                                    st_row<CX>(s_sol[l].z + c, zn);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int y = 0; y < CY; ++y)
+#pragma unroll
+                        for (int x = 0; x < CX; ++x) {
+                            vm[y][x] = vc[y][x];
+                            vc[y][x] = vp[y][x];
+                            ec[y][x] = ep[y][x];
+                        }
+                }
+                release(qc);
+                if (k + 1 == sg.k1) release(qn);
+            }
+            // the segment's partial sums, over the consumer warps
+            double v0 = warp_sum((double)acc0), v1 = warp_sum((double)acc1);
+            if (lane == 0) {
+                red[2 * warp] = v0;
+                red[2 * warp + 1] = v1;
+            }
+            named_sync(1, NC);
+            if (warp == 0) {
+                double t0 = lane < TYT ? red[2 * lane] : 0.0;
+                double t1 = lane < TYT ? red[2 * lane + 1] : 0.0;
+                t0 = warp_sum(t0);
+                t1 = warp_sum(t1);
+                if (lane == 0) {
+                    if (a_side)
+                        a.part_a[sb + ls] = t0;
+                    else {
+                        a.part_b[2 * (size_t)(sb + ls)] = t0;
+                        a.part_b[2 * (size_t)(sb + ls) + 1] = t1;
+                    }
+                }
+            }
+            named_sync(1, NC);
+        }
+    };
+
+    unsigned nbar = 0;
+    bool p_in_a = true;
+    bool failed = false;
+    for (;;) {
+        if (producer) {
+            if (lane == 0) produce(true, p_in_a);
+            __syncwarp();
+        } else {
+            consume(true, p_in_a);
+        }
+        __syncthreads();
+        if (s_fail) { failed = true; break; }
+        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (*(volatile int*)&a.ctl->running == 0) break;
+        for (int l = 0; l < nloc; ++l) {
+            if (s_sol[l].done != RUNNING) continue;
+            double t[1];
+            range_sum<1>(a.part_a, s_sol[l].seg_begin, s_sol[l].seg_end, t, red, tid, NT);
+            if (tid == 0) {
+                if (!(t[0] > 0.0) || !isfinite(t[0])) {
+                    s_sol[l].done = BREAKDOWN;
+                    s_sol[l].finished = 1;
+                } else {
+                    s_sol[l].alpha = s_sol[l].rz / t[0];
+                }
+            }
+            __syncthreads();
+        }
+        if (producer) {
+            if (lane == 0) produce(false, p_in_a);
+            __syncwarp();
+        } else {
+            consume(false, p_in_a);
+        }
+        __syncthreads();
+        if (s_fail) { failed = true; break; }
+        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        for (int l = 0; l < nloc; ++l) {
+            if (s_sol[l].done != RUNNING) continue;
+            double t[2];
+            range_sum<2>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, red, tid, NT);
+            if (tid == 0) {
+                LocalSolve& L = s_sol[l];
+                L.iter += 1;
+                L.rr = t[1];
+                if (!isfinite(t[0]) || !isfinite(t[1]) || t[0] < 0.0) {
+                    L.done = BREAKDOWN;
+                } else if (t[1] <= L.stop2) {
+                    L.done = CONVERGED;
+                } else if (L.iter >= L.max_iter) {
+                    L.done = CAPPED;
+                } else {
+                    L.beta = t[0] / L.rz;
+                    L.rz = t[0];
+                }
+                if (L.done != RUNNING) L.finished = 1;
+            }
+            __syncthreads();
+        }
+        if (tid < nloc) {
+            LocalSolve& L = s_sol[tid];
+            if (L.finished) {
+                L.finished = 0;
+                if (L.owner) {
+                    L.sc->iter = L.iter;
+                    L.sc->rr = L.rr;
+                    L.sc->rz = L.rz;
+                    L.sc->done = L.done;
+                    __threadfence();
+                    atomicSub(&a.ctl->running, 1);
+                }
+            }
+            s_member[tid] = (L.done == RUNNING);
+        }
+        __syncthreads();
+        p_in_a = !p_in_a;
+    }
+    if (failed) {
+        if (tid == 0) {
+            atomicExch(&a.ctl->error, 1);
+            for (int l = 0; l < nloc; ++l) {
+                s_sol[l].sc->iter = s_sol[l].iter;
+                atomicExch(&s_sol[l].sc->done, (int)TIMEDOUT);
+            }
+        }
+        if (producer && lane == 0) {
+            // only the last NS planes can still be in flight
+            for (int q = max(0, np - NS); q < np; ++q) (void)mbar_wait(&full[q % NS], (q / NS) & 1);
+        }
+        __threadfence();
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ host side
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -607,24 +965,32 @@ bool march_supported(const Dims& d) {
 // ------------------------------------------------------------------ variant table
 // A variant is (CX, CY, TYT); its tile is 32 CX wide and CY TYT high.
 struct VariantOps {
-    int cx, cy, tyt;
+    int cx, cy, tyt, ws;
     int smem32, smem16;
     const void *k32, *k16;
 };
 
-template <int CX, int CY, int TYT>
+template <int CX, int CY, int TYT, int WS>
 static VariantOps make_ops() {
-    return VariantOps{CX, CY, TYT, NS * Geo<CX, CY, TYT, float>::STAGE,
-                      NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
-                      (const void*)k_pcg<CX, CY, TYT, float>,
-                      (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16>};
+    if constexpr (WS)
+        return VariantOps{CX, CY, TYT, 1, NS * Geo<CX, CY, TYT, float>::STAGE,
+                          NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
+                          (const void*)k_pcg_ws<CX, CY, TYT, float>,
+                          (const void*)k_pcg_ws<CX, CY, TYT, __nv_bfloat16>};
+    else
+        return VariantOps{CX, CY, TYT, 0, NS * Geo<CX, CY, TYT, float>::STAGE,
+                          NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
+                          (const void*)k_pcg<CX, CY, TYT, float>,
+                          (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16>};
 }
 
-#define MARCH_VARIANTS(X) X(0, 1, 1, 4) X(1, 1, 1, 8) X(2, 1, 1, 16) X(3, 2, 2, 2) \
-    X(4, 2, 2, 4) X(5, 2, 2, 8) X(6, 2, 1, 8) X(7, 1, 2, 8)
+// (CX, CY, TYT, warp-specialised)
+#define MARCH_VARIANTS(X) X(1, 1, 4, 0) X(1, 1, 8, 0) X(1, 1, 16, 0) X(2, 2, 2, 0) \
+    X(2, 2, 4, 0) X(2, 2, 8, 0) X(2, 1, 8, 0) X(1, 2, 8, 0)                        \
+    X(2, 2, 4, 1) X(2, 2, 8, 1) X(1, 1, 8, 1) X(2, 1, 8, 1) X(1, 2, 8, 1) X(2, 2, 2, 1)
 
 static const VariantOps* variants(int* count) {
-#define ROW(ID, CX, CY, TYT) make_ops<CX, CY, TYT>(),
+#define ROW(CX, CY, TYT, WS) make_ops<CX, CY, TYT, WS>(),
     static const VariantOps table[] = {MARCH_VARIANTS(ROW)};
 #undef ROW
     static std::once_flag once;
@@ -639,6 +1005,8 @@ static const VariantOps* variants(int* count) {
     return table;
 }
 
+static int threads_of(const VariantOps& v) { return 32 * (v.tyt + v.ws); }
+
 int march_variant_count() {
     int n;
     variants(&n);
@@ -649,14 +1017,14 @@ MarchVariant march_variant(int id) {
     int n;
     const VariantOps* t = variants(&n);
     const VariantOps& v = t[id < 0 || id >= n ? 0 : id];
-    return MarchVariant{id, v.cx, v.cy, v.tyt, 32 * v.cx, v.cy * v.tyt};
+    return MarchVariant{id, v.cx, v.cy, v.tyt, v.ws, 32 * v.cx, v.cy * v.tyt};
 }
 
-int march_find_variant(int cx, int cy, int tyt) {
+int march_find_variant(int cx, int cy, int tyt, int ws) {
     int n;
     const VariantOps* t = variants(&n);
     for (int q = 0; q < n; ++q)
-        if (t[q].cx == cx && t[q].cy == cy && t[q].tyt == tyt) return q;
+        if (t[q].cx == cx && t[q].cy == cy && t[q].tyt == tyt && t[q].ws == ws) return q;
     return -1;
 }
 
@@ -664,7 +1032,7 @@ int march_occupancy(int variant, bool bf16) {
     int n;
     const VariantOps& v = variants(&n)[variant];
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, bf16 ? v.k16 : v.k32, 32 * v.tyt,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, bf16 ? v.k16 : v.k32, threads_of(v),
                                                       bf16 ? v.smem16 : v.smem32) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -801,7 +1169,7 @@ int launch_march_pcg(const MarchPlan& p, cudaStream_t st) {
     PcgArgs args{p.solves, p.segs, p.cta_seg, p.maps, p.part_a, p.part_b, p.ctl, p.nctas};
     void* params[] = {&args};
     const cudaError_t e = cudaLaunchCooperativeKernel(p.bf16 ? v.k16 : v.k32, dim3(p.nctas),
-                                                      dim3(32, v.tyt), params,
+                                                      dim3(32, v.tyt + v.ws), params,
                                                       (size_t)(p.bf16 ? v.smem16 : v.smem32), st);
     g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     if (e != cudaSuccess) {

@@ -8,9 +8,10 @@
 
 namespace pcg {
 
-// One kernel variant: 32 x tyt threads, each owning cx x cy cells; tile width x height cells.
+// One kernel variant: 32 x tyt compute threads, each owning cx x cy cells, plus one TMA
+// producer warp when ws; tile width x height cells.
 struct MarchVariant {
-    int id, cx, cy, tyt, width, height;
+    int id, cx, cy, tyt, ws, width, height;
 };
 
 // Tensor maps of one solve, in this order: halo boxes (width+8) x (height+2) x 1 for z and both
@@ -76,7 +77,7 @@ struct PcgArgs {
 bool march_supported(const Dims& d);
 int march_variant_count();
 MarchVariant march_variant(int id);
-int march_find_variant(int cx, int cy, int tyt);  // -1 if there is none
+int march_find_variant(int cx, int cy, int tyt, int ws);  // -1 if there is none
 int march_occupancy(int variant, bool bf16);       // resident CTAs per SM (0 if unknown)
 
 // Builds (device arrays allocated, copied on st, synchronised) / frees a plan.  0 on success,
