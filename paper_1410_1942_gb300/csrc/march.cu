@@ -60,10 +60,12 @@ struct Geo {
     static constexpr int A_Z = 0, A_P = align128(VB), A_E = A_P + align128(VB);
     static constexpr int A_STAGE = A_E + align128(EB);
     static constexpr int A_TX = 2 * VB + EB;
-    // phase B stage: p | eta  (x and r, needed at the centre only, go straight to registers)
-    static constexpr int B_P = 0, B_E = align128(VB);
-    static constexpr int B_STAGE = B_E + align128(EB);
-    static constexpr int B_TX = VB + EB;
+    // phase B stage: p | eta | x | r
+    static constexpr int B_P = 0, B_E = align128(VB), B_X = B_E + align128(EB);
+    static constexpr int B_R = B_X + align128(CB);
+    static constexpr int B_STAGE = B_R + align128(CB);
+    static constexpr int B_TX_HALO = VB + EB;  // planes k0-1 and k1: p, eta only
+    static constexpr int B_TX = VB + EB + 2 * CB;
     static constexpr int STAGE = A_STAGE > B_STAGE ? A_STAGE : B_STAGE;
 };
 
@@ -90,18 +92,6 @@ __device__ __forceinline__ void ld_row(const __nv_bfloat16* p, float (&v)[CX]) {
 }
 __device__ __forceinline__ float ld1(const float* p) { return *p; }
 __device__ __forceinline__ float ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-
-// CX consecutive values of a global row through L2 (the same thread wrote them last time).
-template <int CX>
-__device__ __forceinline__ void ldg_row(const float* g, float (&v)[CX]) {
-    if constexpr (CX == 2) {
-        const float2 t = __ldcg(reinterpret_cast<const float2*>(g));
-        v[0] = t.x;
-        v[1] = t.y;
-    } else {
-        v[0] = __ldcg(g);
-    }
-}
 
 template <int CX>
 __device__ __forceinline__ void st_row(float* g, const float (&v)[CX]) {
@@ -321,7 +311,7 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     }
     __syncthreads();
 
-    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx;
+    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx, cc = CX * tx;
     auto stage = [&](int q) { return sm + (q % NS) * G::STAGE; };
     int g = 0;        // stream positions acquired (all threads)
     int nissued = 0;  // stream positions issued (thread 0)
@@ -346,10 +336,15 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
                             sg.x0 - G::VOFF, sg.y0 - 1, kk);
                 tma_load_3d(dst + G::A_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
             } else {
-                mbar_arrive_expect_tx(&bars[st], G::B_TX);
+                const bool centre = coff > 0 && coff <= L;
+                mbar_arrive_expect_tx(&bars[st], centre ? G::B_TX : G::B_TX_HALO);
                 tma_load_3d(dst + G::B_P, m + (p_in_a ? MAP_PB : MAP_PA), &bars[st],
                             sg.x0 - G::VOFF, sg.y0 - 1, kk);
                 tma_load_3d(dst + G::B_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+                if (centre) {
+                    tma_load_3d(dst + G::B_X, m + MAP_X, &bars[st], sg.x0, sg.y0, kk);
+                    tma_load_3d(dst + G::B_R, m + MAP_R, &bars[st], sg.x0, sg.y0, kk);
+                }
             }
             ++nissued;
             if (++coff == L + 2) {
@@ -402,21 +397,6 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
 #pragma unroll
                 for (int x = 0; x < CX; ++x)
                     wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
-            // x and r of the next plane, loaded one plane ahead (phase B)
-            float xnx[CY][CX], rnx[CY][CX];
-            auto load_xr = [&](int kk) {
-                if (i0 < d.nx) {
-#pragma unroll
-                    for (int y = 0; y < CY; ++y) {
-                        if (j0 + y < d.ny) {
-                            const size_t c = (size_t)i0 + (size_t)d.nx * (j0 + y + (size_t)d.ny * kk);
-                            ldg_row<CX>(s_sol[l].x + c, xnx[y]);
-                            ldg_row<CX>(s_sol[l].r + c, rnx[y]);
-                        }
-                    }
-                }
-            };
-            if (!a_side) load_xr(sg.k0);
             float acc0 = 0.f, acc1 = 0.f;
             for (int k = sg.k0; k < sg.k1; ++k) {
                 if (!acquire()) return false;  // plane k+1
@@ -463,14 +443,8 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
                     }
                 } else {
                     float xo[CY][CX], ro[CY][CX];
-#pragma unroll
-                    for (int y = 0; y < CY; ++y)
-#pragma unroll
-                        for (int x = 0; x < CX; ++x) {
-                            xo[y][x] = xnx[y][x];
-                            ro[y][x] = rnx[y][x];
-                        }
-                    if (k + 1 < sg.k1) load_xr(k + 1);
+                    load_centre<CX, CY>((const float*)(S + G::B_X), G::W, CY * ty, cc, xo);
+                    load_centre<CX, CY>((const float*)(S + G::B_R), G::W, CY * ty, cc, ro);
                     if (i0 < d.nx) {
 #pragma unroll
                         for (int y = 0; y < CY; ++y) {
@@ -659,7 +633,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
     }
     __syncthreads();
 
-    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx;
+    const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx, cc = CX * tx;
     const int warp = ty, lane = tx;
     auto stage = [&](int q) { return sm + (q % NS) * G::STAGE; };
     int np = 0;  // planes issued (producer lane 0)
@@ -686,10 +660,15 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
                                 sg.x0 - G::VOFF, sg.y0 - 1, kk);
                     tma_load_3d(dst + G::A_E, m + MAP_ETA, &full[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
                 } else {
-                    mbar_arrive_expect_tx(&full[st], G::B_TX);
+                    const bool centre = off > 0 && off <= L;
+                    mbar_arrive_expect_tx(&full[st], centre ? G::B_TX : G::B_TX_HALO);
                     tma_load_3d(dst + G::B_P, m + (p_in_a ? MAP_PB : MAP_PA), &full[st],
                                 sg.x0 - G::VOFF, sg.y0 - 1, kk);
                     tma_load_3d(dst + G::B_E, m + MAP_ETA, &full[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+                    if (centre) {
+                        tma_load_3d(dst + G::B_X, m + MAP_X, &full[st], sg.x0, sg.y0, kk);
+                        tma_load_3d(dst + G::B_R, m + MAP_R, &full[st], sg.x0, sg.y0, kk);
+                    }
                 }
                 ++np;
             }
@@ -751,21 +730,6 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
                     for (int x = 0; x < CX; ++x)
                         wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
             }
-            // x and r of the next plane, loaded one plane ahead (phase B)
-            float xnx[CY][CX], rnx[CY][CX];
-            auto load_xr = [&](int kk) {
-                if (i0 < d.nx) {
-#pragma unroll
-                    for (int y = 0; y < CY; ++y) {
-                        if (j0 + y < d.ny) {
-                            const size_t c = (size_t)i0 + (size_t)d.nx * (j0 + y + (size_t)d.ny * kk);
-                            ldg_row<CX>(s_sol[l].x + c, xnx[y]);
-                            ldg_row<CX>(s_sol[l].r + c, rnx[y]);
-                        }
-                    }
-                }
-            };
-            if (!a_side) load_xr(sg.k0);
             float acc0 = 0.f, acc1 = 0.f;
             for (int k = sg.k0; k < sg.k1; ++k) {
                 const int qc = p0 + 1 + (k - sg.k0), qn = qc + 1;
@@ -813,14 +777,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
                         }
                     } else {
                         float xo[CY][CX], ro[CY][CX];
-#pragma unroll
-                        for (int y = 0; y < CY; ++y)
-#pragma unroll
-                            for (int x = 0; x < CX; ++x) {
-                                xo[y][x] = xnx[y][x];
-                                ro[y][x] = rnx[y][x];
-                            }
-                        if (k + 1 < sg.k1) load_xr(k + 1);
+                        load_centre<CX, CY>((const float*)(S + G::B_X), G::W, CY * warp, cc, xo);
+                        load_centre<CX, CY>((const float*)(S + G::B_R), G::W, CY * warp, cc, ro);
                         if (i0 < d.nx) {
 #pragma unroll
                             for (int y = 0; y < CY; ++y) {
