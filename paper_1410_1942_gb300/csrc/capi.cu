@@ -217,6 +217,19 @@ static void free_state(poisson_t* H) {
     if (H->ctl_host) cudaFreeHost(H->ctl_host);
     for (auto& e : H->ev) if (e) cudaEventDestroy(e);
     for (auto& e : H->prof_ev) if (e) cudaEventDestroy(e);
+    if (H->plan.trace) {
+        // development aid (POISSON_TRACE set): CTA 0's time per part of a PCG iteration
+        unsigned long long t[TRACE_PARTS] = {};
+        if (cudaMemcpy(t, H->plan.trace, sizeof(t), cudaMemcpyDeviceToHost) == cudaSuccess && t[TR_ITERS]) {
+            const char* names[] = {"phaseA", "bar1", "alpha", "phaseB", "bar2", "beta"};
+            fprintf(stderr, "[poisson trace] %dx%dx%d %llu iterations, us/iteration:", H->d.nx,
+                    H->d.ny, H->d.nz, t[TR_ITERS]);
+            for (int q = 0; q < TR_ITERS; ++q)
+                fprintf(stderr, " %s=%.2f", names[q], 1e-3 * (double)t[q] / (double)t[TR_ITERS]);
+            fprintf(stderr, "\n");
+        }
+        cudaGetLastError();
+    }
     march_plan_free(&H->plan);
 }
 

@@ -29,6 +29,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <atomic>
 #include <mutex>
 #include <vector>
@@ -494,9 +495,21 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     unsigned nbar = 0;
     bool p_in_a = true;
     bool failed = false;
+    const bool tr = a.trace && blockIdx.x == 0 && tid == 0;
+    unsigned long long tt[TRACE_PARTS] = {};
+    unsigned long long tprev = tr ? globaltimer() : 0;
+    auto mark = [&](int part) {
+        if (tr) {
+            const unsigned long long t = globaltimer();
+            tt[part] += t - tprev;
+            tprev = t;
+        }
+    };
     for (;;) {
         if (!run_phase(true, p_in_a)) { failed = true; break; }
+        mark(TR_A);
         if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        mark(TR_BAR1);
         if (*(volatile int*)&a.ctl->running == 0) break;
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
@@ -512,8 +525,11 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
             }
             __syncthreads();
         }
+        mark(TR_ALPHA);
         if (!run_phase(false, p_in_a)) { failed = true; break; }
+        mark(TR_B);
         if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        mark(TR_BAR2);
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[2];
@@ -553,8 +569,12 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
             }
         }
         __syncthreads();
+        mark(TR_BETA);
+        if (tr) tt[TR_ITERS] += 1;
         p_in_a = !p_in_a;
     }
+    if (tr)
+        for (int q = 0; q < TRACE_PARTS; ++q) a.trace[q] += tt[q];
     if (failed) {
         if (tid == 0) {
             atomicExch(&a.ctl->error, 1);
@@ -841,6 +861,16 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
     unsigned nbar = 0;
     bool p_in_a = true;
     bool failed = false;
+    const bool tr = a.trace && blockIdx.x == 0 && tid == 0;
+    unsigned long long tt[TRACE_PARTS] = {};
+    unsigned long long tprev = tr ? globaltimer() : 0;
+    auto mark = [&](int part) {
+        if (tr) {
+            const unsigned long long t = globaltimer();
+            tt[part] += t - tprev;
+            tprev = t;
+        }
+    };
     for (;;) {
         if (producer) {
             if (lane == 0) produce(true, p_in_a);
@@ -849,8 +879,10 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
             consume(true, p_in_a);
         }
         __syncthreads();
+        mark(TR_A);
         if (s_fail) { failed = true; break; }
         if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        mark(TR_BAR1);
         if (*(volatile int*)&a.ctl->running == 0) break;
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
@@ -866,6 +898,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
             }
             __syncthreads();
         }
+        mark(TR_ALPHA);
         if (producer) {
             if (lane == 0) produce(false, p_in_a);
             __syncwarp();
@@ -873,8 +906,10 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
             consume(false, p_in_a);
         }
         __syncthreads();
+        mark(TR_B);
         if (s_fail) { failed = true; break; }
         if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        mark(TR_BAR2);
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[2];
@@ -913,8 +948,12 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
             s_member[tid] = (L.done == RUNNING);
         }
         __syncthreads();
+        mark(TR_BETA);
+        if (tr) tt[TR_ITERS] += 1;
         p_in_a = !p_in_a;
     }
+    if (tr)
+        for (int q = 0; q < TRACE_PARTS; ++q) a.trace[q] += tt[q];
     if (failed) {
         if (tid == 0) {
             atomicExch(&a.ctl->error, 1);
@@ -1063,7 +1102,8 @@ bool march_encode_solve(CUtensorMap (&m)[6], const MarchSolve& s, int variant, b
 }
 
 void march_plan_free(MarchPlan* p) {
-    void* ptrs[] = {p->solves, p->segs, p->cta_seg, p->maps, p->part_a, p->part_b, p->ctl};
+    void* ptrs[] = {p->solves, p->segs, p->cta_seg, p->maps, p->part_a, p->part_b, p->ctl,
+                    p->trace};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     *p = MarchPlan{};
@@ -1160,6 +1200,13 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
         cudaGetLastError();
         ok = false;
     }
+    if (ok && getenv("POISSON_TRACE")) {
+        if (cudaMalloc((void**)&p->trace, sizeof(unsigned long long) * TRACE_PARTS) != cudaSuccess ||
+            cudaMemsetAsync(p->trace, 0, sizeof(unsigned long long) * TRACE_PARTS, st) != cudaSuccess) {
+            cudaGetLastError();
+            p->trace = nullptr;
+        }
+    }
     if (ok) ok = cudaStreamSynchronize(st) == cudaSuccess;  // host vectors go out of scope
     if (!ok) {
         march_plan_free(p);
@@ -1171,7 +1218,7 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
 int launch_march_pcg(const MarchPlan& p, cudaStream_t st) {
     int n;
     const VariantOps& v = variants(&n)[p.variant];
-    PcgArgs args{p.solves, p.segs, p.cta_seg, p.maps, p.part_a, p.part_b, p.ctl, p.nctas};
+    PcgArgs args{p.solves, p.segs, p.cta_seg, p.maps, p.part_a, p.part_b, p.ctl, p.nctas, p.trace};
     void* params[] = {&args};
     const cudaError_t e = cudaLaunchCooperativeKernel(p.bf16 ? v.k16 : v.k32, dim3(p.nctas),
                                                       dim3(32, v.tyt + v.ws), params,

@@ -60,6 +60,7 @@ struct MarchPlan {
     double* part_a = nullptr;  // per segment: p.Ap
     double* part_b = nullptr;  // per segment: r.z, r.r
     MarchCtl* ctl = nullptr;
+    unsigned long long* trace = nullptr;  // TRACE_PARTS counters when tracing is on
 };
 
 // Kernel parameters of the persistent PCG launch.
@@ -72,7 +73,11 @@ struct PcgArgs {
     double* part_b;
     MarchCtl* ctl;
     int nctas;
+    unsigned long long* trace;  // optional: CTA 0 adds its per-part times (ns), TRACE_PARTS slots
 };
+
+// Parts of a persistent-PCG iteration timed by the optional trace (CTA 0's view).
+enum { TR_A = 0, TR_BAR1, TR_ALPHA, TR_B, TR_BAR2, TR_BETA, TR_ITERS, TRACE_PARTS };
 
 bool march_supported(const Dims& d);
 int march_variant_count();
