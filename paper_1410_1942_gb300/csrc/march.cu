@@ -270,15 +270,34 @@ struct LocalSolve {
     int done, iter, max_iter, finished, owner;
 };
 
+// Sum of part[seg * NV + q] over segments [b, e) by one warp, in a fixed order; the result is
+// exact-same in every CTA and valid in every lane.
+template <int NV>
+__device__ __forceinline__ void warp_range_sum(const double* part, int b, int e, int lane,
+                                               double (&out)[NV]) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = 0.0;
+    for (int s = b + lane; s < e; s += 32)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) out[q] += __ldcg(&part[(size_t)s * NV + q]);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = warp_sum(out[q]);
+}
+
+// Stream membership: the planes of a solve's segments are streamed in a phase iff s_member was
+// set for it when the phase's stream began (right after the preceding grid barrier, before that
+// barrier's decisions), so the first planes of a phase are already in flight while the partial
+// sums of the previous one are being added.  A solve that finished at that barrier is walked
+// once more without arithmetic (its work flag is off).
 template <int CX, int CY, int TYT, typename E>
 __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     using G = Geo<CX, CY, TYT, E>;
-    constexpr int NT = 32 * TYT;
     extern __shared__ __align__(128) unsigned char sm[];
     __shared__ __align__(8) uint64_t bars[NS];
     __shared__ double red[64];
     __shared__ Seg s_seg[MAXSEG];
     __shared__ LocalSolve s_sol[MAXSEG];
+    __shared__ int s_member[MAXSEG];
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
     const int sb = a.cta_seg[blockIdx.x];
     const int nseg = min(MAXSEG, a.cta_seg[blockIdx.x + 1] - sb);
@@ -308,69 +327,82 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         L.max_iter = sv.sc->max_iter;
         L.finished = 0;
         L.owner = (sv.seg_begin >= sb && sv.seg_begin < sb + nseg) ? 1 : 0;
+        s_member[tid] = (L.done == RUNNING);
         if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
     }
     __syncthreads();
 
     const int r0 = 1 + CY * ty, cv = G::VOFF + CX * tx, ce = G::EOFF + CX * tx, cc = CX * tx;
+    const int lane = tx, warp = ty;
     auto stage = [&](int q) { return sm + (q % NS) * G::STAGE; };
     int g = 0;        // stream positions acquired (all threads)
     int nissued = 0;  // stream positions issued (thread 0)
+    int g0 = 0;       // first position of the current phase
     bool ok = true;
 
-    // ---------------------------------------------------------------- one phase over the segments
-    // a_side: phase A (p = z + beta p_in, sum p.Ap) else phase B.  p_in_a: phase A reads pa.
-    auto run_phase = [&](bool a_side, bool p_in_a) -> bool {
-        int cs = 0, coff = 0;  // issue cursor (thread 0)
-        auto issue_next = [&]() {
-            while (cs < nseg && coff == 0 && s_sol[s_seg[cs].solve - first].done != RUNNING) ++cs;
-            if (cs >= nseg) return;
-            const Seg& sg = s_seg[cs];
-            const int L = sg.k1 - sg.k0, kk = sg.k0 - 1 + coff;
-            const int st = nissued % NS;
-            unsigned char* dst = sm + st * G::STAGE;
-            const CUtensorMap* m = a.maps + 6 * sg.solve;
-            if (a_side) {
-                mbar_arrive_expect_tx(&bars[st], G::A_TX);
-                tma_load_3d(dst + G::A_Z, m + MAP_Z, &bars[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
-                tma_load_3d(dst + G::A_P, m + (p_in_a ? MAP_PA : MAP_PB), &bars[st],
-                            sg.x0 - G::VOFF, sg.y0 - 1, kk);
-                tma_load_3d(dst + G::A_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
-            } else {
-                const bool centre = coff > 0 && coff <= L;
-                mbar_arrive_expect_tx(&bars[st], centre ? G::B_TX : G::B_TX_HALO);
-                tma_load_3d(dst + G::B_P, m + (p_in_a ? MAP_PB : MAP_PA), &bars[st],
-                            sg.x0 - G::VOFF, sg.y0 - 1, kk);
-                tma_load_3d(dst + G::B_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
-                if (centre) {
-                    tma_load_3d(dst + G::B_X, m + MAP_X, &bars[st], sg.x0, sg.y0, kk);
-                    tma_load_3d(dst + G::B_R, m + MAP_R, &bars[st], sg.x0, sg.y0, kk);
-                }
+    // ---------------------------------------------------------------- the plane stream (thread 0)
+    int cs = 0, coff = 0;           // issue cursor
+    bool st_a = true, st_pa = true;  // phase of the stream being issued, p_in is pa
+    auto issue_next = [&]() {
+        while (cs < nseg && coff == 0 && !s_member[s_seg[cs].solve - first]) ++cs;
+        if (cs >= nseg) return;
+        const Seg& sg = s_seg[cs];
+        const int L = sg.k1 - sg.k0, kk = sg.k0 - 1 + coff;
+        const int st = nissued % NS;
+        unsigned char* dst = sm + st * G::STAGE;
+        const CUtensorMap* m = a.maps + 6 * sg.solve;
+        if (st_a) {
+            mbar_arrive_expect_tx(&bars[st], G::A_TX);
+            tma_load_3d(dst + G::A_Z, m + MAP_Z, &bars[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
+            tma_load_3d(dst + G::A_P, m + (st_pa ? MAP_PA : MAP_PB), &bars[st], sg.x0 - G::VOFF,
+                        sg.y0 - 1, kk);
+            tma_load_3d(dst + G::A_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+        } else {
+            const bool centre = coff > 0 && coff <= L;
+            mbar_arrive_expect_tx(&bars[st], centre ? G::B_TX : G::B_TX_HALO);
+            tma_load_3d(dst + G::B_P, m + (st_pa ? MAP_PB : MAP_PA), &bars[st], sg.x0 - G::VOFF,
+                        sg.y0 - 1, kk);
+            tma_load_3d(dst + G::B_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
+            if (centre) {
+                tma_load_3d(dst + G::B_X, m + MAP_X, &bars[st], sg.x0, sg.y0, kk);
+                tma_load_3d(dst + G::B_R, m + MAP_R, &bars[st], sg.x0, sg.y0, kk);
             }
-            ++nissued;
-            if (++coff == L + 2) {
-                coff = 0;
-                ++cs;
-            }
-        };
-        const int g0 = g;
-        if (tid == 0)
+        }
+        ++nissued;
+        if (++coff == L + 2) {
+            coff = 0;
+            ++cs;
+        }
+    };
+    // Starts the stream of a phase: the first NS planes are issued at once.
+    auto begin_stream = [&](bool a_side, bool p_in_a) {
+        g0 = g;
+        if (tid == 0) {
+            cs = 0;
+            coff = 0;
+            st_a = a_side;
+            st_pa = p_in_a;
             for (int q = 0; q < NS; ++q) issue_next();
-        auto acquire = [&]() -> bool {
-            ok = ok && mbar_wait(&bars[g % NS], (g / NS) & 1);
-            if (__syncthreads_or(!ok)) return false;  // also: every thread is done with g-2
-            if (tid == 0 && g - g0 >= 2) issue_next();
-            ++g;
-            return true;
-        };
+        }
+    };
+    auto acquire = [&]() -> bool {
+        ok = ok && mbar_wait(&bars[g % NS], (g / NS) & 1);
+        if (__syncthreads_or(!ok)) return false;  // also: every thread is done with g-2
+        if (tid == 0 && g - g0 >= 2) issue_next();
+        ++g;
+        return true;
+    };
+
+    // ---------------------------------------------------------------- one phase over the segments
+    auto run_phase = [&](bool a_side, bool p_in_a) -> bool {
         for (int ls = 0; ls < nseg; ++ls) {
             const Seg sg = s_seg[ls];
             const int l = sg.solve - first;
-            if (s_sol[l].done != RUNNING) continue;
+            if (!s_member[l]) continue;
+            const bool work = s_sol[l].done == RUNNING;
             const Dims d = s_sol[l].d;
             const float coefv = (float)(a_side ? s_sol[l].beta : s_sol[l].alpha);
             const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * ty;
-            // centre values of a plane: p (phase B) or z + beta p_in (phase A)
             auto centre = [&](int q, float (&o)[CY][CX]) {
                 const unsigned char* S = stage(q);
                 if (a_side) {
@@ -388,19 +420,24 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
             auto eta_of = [&](int q) { return (const E*)(stage(q) + (a_side ? G::A_E : G::B_E)); };
             float vm[CY][CX], vc[CY][CX], em[CY][CX], ec[CY][CX], wzl[CY][CX];
             if (!acquire()) return false;  // plane k0-1
-            centre(g - 1, vm);
-            load_centre<CX, CY>(eta_of(g - 1), G::EW, r0, ce, em);
+            if (work) {
+                centre(g - 1, vm);
+                load_centre<CX, CY>(eta_of(g - 1), G::EW, r0, ce, em);
+            }
             if (!acquire()) return false;  // plane k0
-            centre(g - 1, vc);
-            load_centre<CX, CY>(eta_of(g - 1), G::EW, r0, ce, ec);
+            if (work) {
+                centre(g - 1, vc);
+                load_centre<CX, CY>(eta_of(g - 1), G::EW, r0, ce, ec);
 #pragma unroll
-            for (int y = 0; y < CY; ++y)
+                for (int y = 0; y < CY; ++y)
 #pragma unroll
-                for (int x = 0; x < CX; ++x)
-                    wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
+                    for (int x = 0; x < CX; ++x)
+                        wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
+            }
             float acc0 = 0.f, acc1 = 0.f;
             for (int k = sg.k0; k < sg.k1; ++k) {
                 if (!acquire()) return false;  // plane k+1
+                if (!work) continue;
                 const int qc = g - 2, qn = g - 1;
                 const unsigned char* S = stage(qc);
                 float vp[CY][CX], ep[CY][CX];
@@ -505,66 +542,80 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
             tprev = t;
         }
     };
+    auto snapshot_members = [&]() {
+        if (tid < nloc) s_member[tid] = (s_sol[tid].done == RUNNING);
+        __syncthreads();
+    };
+    begin_stream(true, p_in_a);
     for (;;) {
         if (!run_phase(true, p_in_a)) { failed = true; break; }
         mark(TR_A);
         if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
         mark(TR_BAR1);
+        snapshot_members();
+        begin_stream(false, p_in_a);
         if (*(volatile int*)&a.ctl->running == 0) break;
-        for (int l = 0; l < nloc; ++l) {
-            if (s_sol[l].done != RUNNING) continue;
-            double t[1];
-            range_sum<1>(a.part_a, s_sol[l].seg_begin, s_sol[l].seg_end, t, red, tid, NT);
-            if (tid == 0) {
-                if (!(t[0] > 0.0) || !isfinite(t[0])) {
-                    s_sol[l].done = BREAKDOWN;
-                    s_sol[l].finished = 1;
-                } else {
-                    s_sol[l].alpha = s_sol[l].rz / t[0];
+        if (warp == 0) {
+            for (int l = 0; l < nloc; ++l) {
+                if (s_sol[l].done != RUNNING) continue;
+                double t[1];
+                warp_range_sum<1>(a.part_a, s_sol[l].seg_begin, s_sol[l].seg_end, lane, t);
+                if (lane == 0) {
+                    if (!(t[0] > 0.0) || !isfinite(t[0])) {
+                        s_sol[l].done = BREAKDOWN;
+                        s_sol[l].finished = 1;
+                    } else {
+                        s_sol[l].alpha = s_sol[l].rz / t[0];
+                    }
                 }
+                __syncwarp();
             }
-            __syncthreads();
         }
+        __syncthreads();
         mark(TR_ALPHA);
         if (!run_phase(false, p_in_a)) { failed = true; break; }
         mark(TR_B);
         if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
         mark(TR_BAR2);
-        for (int l = 0; l < nloc; ++l) {
-            if (s_sol[l].done != RUNNING) continue;
-            double t[2];
-            range_sum<2>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, red, tid, NT);
-            if (tid == 0) {
-                LocalSolve& L = s_sol[l];
-                L.iter += 1;
-                L.rr = t[1];
-                if (!isfinite(t[0]) || !isfinite(t[1]) || t[0] < 0.0) {
-                    L.done = BREAKDOWN;
-                } else if (t[1] <= L.stop2) {
-                    L.done = CONVERGED;
-                } else if (L.iter >= L.max_iter) {
-                    L.done = CAPPED;
-                } else {
-                    L.beta = t[0] / L.rz;
-                    L.rz = t[0];
+        snapshot_members();
+        begin_stream(true, !p_in_a);
+        if (warp == 0) {
+            for (int l = 0; l < nloc; ++l) {
+                if (s_sol[l].done != RUNNING) continue;
+                double t[2];
+                warp_range_sum<2>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, lane, t);
+                if (lane == 0) {
+                    LocalSolve& L = s_sol[l];
+                    L.iter += 1;
+                    L.rr = t[1];
+                    if (!isfinite(t[0]) || !isfinite(t[1]) || t[0] < 0.0) {
+                        L.done = BREAKDOWN;
+                    } else if (t[1] <= L.stop2) {
+                        L.done = CONVERGED;
+                    } else if (L.iter >= L.max_iter) {
+                        L.done = CAPPED;
+                    } else {
+                        L.beta = t[0] / L.rz;
+                        L.rz = t[0];
+                    }
+                    if (L.done != RUNNING) L.finished = 1;
                 }
-                if (L.done != RUNNING) L.finished = 1;
+                __syncwarp();
             }
-            __syncthreads();
-        }
-        // owners publish the solves that finished in this iteration (the only window in which
-        // ctl->running changes: between the phase-B barrier and the next phase-A barrier)
-        if (tid < nloc) {
-            LocalSolve& L = s_sol[tid];
-            if (L.finished) {
-                L.finished = 0;
-                if (L.owner) {
-                    L.sc->iter = L.iter;
-                    L.sc->rr = L.rr;
-                    L.sc->rz = L.rz;
-                    L.sc->done = L.done;
-                    __threadfence();
-                    atomicSub(&a.ctl->running, 1);
+            // owners publish the solves that finished in this iteration (the only window in
+            // which ctl->running changes: between the phase-B barrier and the next phase-A one)
+            if (lane < nloc) {
+                LocalSolve& L = s_sol[lane];
+                if (L.finished) {
+                    L.finished = 0;
+                    if (L.owner) {
+                        L.sc->iter = L.iter;
+                        L.sc->rr = L.rr;
+                        L.sc->rz = L.rz;
+                        L.sc->done = L.done;
+                        __threadfence();
+                        atomicSub(&a.ctl->running, 1);
+                    }
                 }
             }
         }
@@ -575,18 +626,20 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     }
     if (tr)
         for (int q = 0; q < TRACE_PARTS; ++q) a.trace[q] += tt[q];
-    if (failed) {
-        if (tid == 0) {
+    // Planes issued but not consumed (the stream begun after the last barrier, or the rest of
+    // a failed phase): wait for them so no copy lands after the CTA has gone.
+    if (tid == 0) {
+        if (failed) {
             atomicExch(&a.ctl->error, 1);
             for (int l = 0; l < nloc; ++l) {
                 s_sol[l].sc->iter = s_sol[l].iter;
                 atomicExch(&s_sol[l].sc->done, (int)TIMEDOUT);
             }
-            for (int q = g; q < nissued; ++q) (void)mbar_wait(&bars[q % NS], (q / NS) & 1);
-            __threadfence();
         }
-        __syncthreads();
+        for (int q = g; q < nissued; ++q) (void)mbar_wait(&bars[q % NS], (q / NS) & 1);
+        __threadfence();
     }
+    __syncthreads();
 }
 
 // ------------------------------------------------------------------ warp-specialised variant
@@ -1128,30 +1181,70 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
     if (W <= 0) return -1;
     if (nctas > W) nctas = (int)W;
     std::vector<Seg> segs;
-    std::vector<int> cta_seg(nctas + 1, 0);
-    std::vector<SolveDev> sd(nsolves);
-    int sol = 0;
-    for (int c = 0; c < nctas; ++c) {
-        cta_seg[c] = (int)segs.size();
-        long long u = W * c / nctas;
-        const long long u1 = W * (c + 1) / nctas;
-        while (u < u1) {
-            while (base[sol + 1] <= u) ++sol;
-            const Dims& d = solves[sol].d;
-            const long long local = u - base[sol];
-            const int tile = (int)(local / d.nz);
-            const int k0 = (int)(local % d.nz);
-            const int k1 = (int)std::min<long long>(d.nz, k0 + (u1 - u));
-            Seg g{};
-            g.solve = sol;
-            g.x0 = (tile % tiles_x[sol]) * v.width;
-            g.y0 = (tile / tiles_x[sol]) * v.height;
-            g.k0 = k0;
-            g.k1 = k1;
-            segs.push_back(g);
-            u += k1 - k0;
+    std::vector<int> cta_seg;
+    long long ntiles = 0;
+    for (int s = 0; s < nsolves; ++s) ntiles += (long long)tiles_x[s] * tiles_y[s];
+    if (ntiles <= nctas) {
+        // One segment per CTA: every tile column gets chunks, one CTA each, handed out one at a
+        // time to the column whose longest chunk is longest (this minimises the longest chunk,
+        // hence the slowest CTA).
+        struct Col { int solve, tile, nz, chunks; };
+        std::vector<Col> cols;
+        for (int s = 0; s < nsolves; ++s)
+            for (int t = 0; t < tiles_x[s] * tiles_y[s]; ++t) cols.push_back({s, t, solves[s].d.nz, 1});
+        auto longest = [](const Col& c) { return (c.nz + c.chunks - 1) / c.chunks; };
+        long long used = (long long)cols.size();
+        while (used < nctas) {
+            size_t best = 0;
+            for (size_t q = 1; q < cols.size(); ++q)
+                if (longest(cols[q]) > longest(cols[best])) best = q;
+            if (cols[best].chunks >= cols[best].nz) break;
+            ++cols[best].chunks;
+            ++used;
+        }
+        for (const Col& c : cols) {
+            const Dims& d = solves[c.solve].d;
+            for (int q = 0; q < c.chunks; ++q) {
+                Seg g{};
+                g.solve = c.solve;
+                g.x0 = (c.tile % tiles_x[c.solve]) * v.width;
+                g.y0 = (c.tile / tiles_x[c.solve]) * v.height;
+                g.k0 = (int)((long long)d.nz * q / c.chunks);
+                g.k1 = (int)((long long)d.nz * (q + 1) / c.chunks);
+                if (g.k1 <= g.k0) continue;
+                cta_seg.push_back((int)segs.size());
+                segs.push_back(g);
+            }
+        }
+        nctas = (int)segs.size();
+        cta_seg.push_back((int)segs.size());
+    } else {
+        // More tile columns than CTAs: an equal share of the linearised plane space per CTA.
+        cta_seg.assign(nctas + 1, 0);
+        int sol = 0;
+        for (int c = 0; c < nctas; ++c) {
+            cta_seg[c] = (int)segs.size();
+            long long u = W * c / nctas;
+            const long long u1 = W * (c + 1) / nctas;
+            while (u < u1) {
+                while (base[sol + 1] <= u) ++sol;
+                const Dims& d = solves[sol].d;
+                const long long local = u - base[sol];
+                const int tile = (int)(local / d.nz);
+                const int k0 = (int)(local % d.nz);
+                const int k1 = (int)std::min<long long>(d.nz, k0 + (u1 - u));
+                Seg g{};
+                g.solve = sol;
+                g.x0 = (tile % tiles_x[sol]) * v.width;
+                g.y0 = (tile / tiles_x[sol]) * v.height;
+                g.k0 = k0;
+                g.k1 = k1;
+                segs.push_back(g);
+                u += k1 - k0;
+            }
         }
     }
+    std::vector<SolveDev> sd(nsolves);
     cta_seg[nctas] = (int)segs.size();
     for (int c = 0; c < nctas; ++c)
         if (cta_seg[c + 1] - cta_seg[c] > MAXSEG) return -1;
