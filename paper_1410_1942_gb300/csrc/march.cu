@@ -240,6 +240,35 @@ __device__ __forceinline__ bool grid_barrier(MarchCtl* ctl, unsigned target, int
     return s_ok != 0;
 }
 
+// Split-phase form of grid_barrier: arrive (after the CTA's stores), do independent work, wait.
+__device__ __forceinline__ void grid_arrive(MarchCtl* ctl, int tid) {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        atomicAdd(&ctl->bar, 1u);
+    }
+}
+
+__device__ __forceinline__ bool grid_wait(MarchCtl* ctl, unsigned target, int tid) {
+    __shared__ int s_ok2;
+    if (tid == 0) {
+        int ok = 1;
+        unsigned long long t0 = 0;
+        while (ld_acquire(&ctl->bar) < target) {
+            if (*(volatile int*)&ctl->error) { ok = 0; break; }
+            const unsigned long long t = globaltimer();
+            if (!t0) t0 = t;
+            else if (t - t0 > BAR_NS) { ok = 0; atomicExch(&ctl->error, 1); break; }
+        }
+        __threadfence();
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        s_ok2 = ok;
+    }
+    __syncthreads();
+    return s_ok2 != 0;
+}
+
 // Sum over segments [b, e) of part[seg * NV + q], in a fixed order (the result is the same in
 // every CTA); valid in all threads.
 template <int NV>
@@ -275,11 +304,22 @@ struct LocalSolve {
 template <int NV>
 __device__ __forceinline__ void warp_range_sum(const double* part, int b, int e, int lane,
                                                double (&out)[NV]) {
+    constexpr int U = 8;  // loads in flight per lane
 #pragma unroll
     for (int q = 0; q < NV; ++q) out[q] = 0.0;
-    for (int s = b + lane; s < e; s += 32)
+    for (int s0 = b; s0 < e; s0 += 32 * U) {
+        double v[U][NV];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) out[q] += __ldcg(&part[(size_t)s * NV + q]);
+        for (int u = 0; u < U; ++u) {
+            const int s = s0 + 32 * u + lane;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) v[u][q] = (s < e) ? __ldcg(&part[(size_t)s * NV + q]) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int q = 0; q < NV; ++q) out[q] += v[u][q];
+    }
 #pragma unroll
     for (int q = 0; q < NV; ++q) out[q] = warp_sum(out[q]);
 }
@@ -343,46 +383,82 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     // ---------------------------------------------------------------- the plane stream (thread 0)
     int cs = 0, coff = 0;           // issue cursor
     bool st_a = true, st_pa = true;  // phase of the stream being issued, p_in is pa
-    auto issue_next = [&]() {
-        while (cs < nseg && coff == 0 && !s_member[s_seg[cs].solve - first]) ++cs;
-        if (cs >= nseg) return;
-        const Seg& sg = s_seg[cs];
-        const int L = sg.k1 - sg.k0, kk = sg.k0 - 1 + coff;
-        const int st = nissued % NS;
+    // Planes whose independent boxes went out before a grid barrier, waiting for the rest.
+    int pend_n = 0, pend_seg[NS], pend_off[NS], pend_st[NS];
+    // part: 0 = the whole plane, 1 = boxes not written by other CTAs since the last barrier
+    // (eta; x and r; p_in of phase A), with the plane's full byte count expected but no
+    // arrival, 2 = the remaining box (p of phase B, z of phase A) and the arrival.
+    auto issue_boxes = [&](int seg, int off, int st, int part) {
+        const Seg& sg = s_seg[seg];
+        const int L = sg.k1 - sg.k0, kk = sg.k0 - 1 + off;
         unsigned char* dst = sm + st * G::STAGE;
         const CUtensorMap* m = a.maps + 6 * sg.solve;
+        uint64_t* bar = &bars[st];
         if (st_a) {
-            mbar_arrive_expect_tx(&bars[st], G::A_TX);
-            tma_load_3d(dst + G::A_Z, m + MAP_Z, &bars[st], sg.x0 - G::VOFF, sg.y0 - 1, kk);
-            tma_load_3d(dst + G::A_P, m + (st_pa ? MAP_PA : MAP_PB), &bars[st], sg.x0 - G::VOFF,
-                        sg.y0 - 1, kk);
-            tma_load_3d(dst + G::A_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
-        } else {
-            const bool centre = coff > 0 && coff <= L;
-            mbar_arrive_expect_tx(&bars[st], centre ? G::B_TX : G::B_TX_HALO);
-            tma_load_3d(dst + G::B_P, m + (st_pa ? MAP_PB : MAP_PA), &bars[st], sg.x0 - G::VOFF,
-                        sg.y0 - 1, kk);
-            tma_load_3d(dst + G::B_E, m + MAP_ETA, &bars[st], sg.x0 - G::EOFF, sg.y0 - 1, kk);
-            if (centre) {
-                tma_load_3d(dst + G::B_X, m + MAP_X, &bars[st], sg.x0, sg.y0, kk);
-                tma_load_3d(dst + G::B_R, m + MAP_R, &bars[st], sg.x0, sg.y0, kk);
+            if (part == 0) mbar_arrive_expect_tx(bar, G::A_TX);
+            if (part == 1) mbar_expect_tx(bar, G::A_TX);
+            if (part != 2) {
+                tma_load_3d(dst + G::A_P, m + (st_pa ? MAP_PA : MAP_PB), bar, sg.x0 - G::VOFF,
+                            sg.y0 - 1, kk);
+                tma_load_3d(dst + G::A_E, m + MAP_ETA, bar, sg.x0 - G::EOFF, sg.y0 - 1, kk);
             }
+            if (part != 1)
+                tma_load_3d(dst + G::A_Z, m + MAP_Z, bar, sg.x0 - G::VOFF, sg.y0 - 1, kk);
+        } else {
+            const bool centre = off > 0 && off <= L;
+            const uint32_t tx = centre ? G::B_TX : G::B_TX_HALO;
+            if (part == 0) mbar_arrive_expect_tx(bar, tx);
+            if (part == 1) mbar_expect_tx(bar, tx);
+            if (part != 2) {
+                tma_load_3d(dst + G::B_E, m + MAP_ETA, bar, sg.x0 - G::EOFF, sg.y0 - 1, kk);
+                if (centre) {
+                    tma_load_3d(dst + G::B_X, m + MAP_X, bar, sg.x0, sg.y0, kk);
+                    tma_load_3d(dst + G::B_R, m + MAP_R, bar, sg.x0, sg.y0, kk);
+                }
+            }
+            if (part != 1)
+                tma_load_3d(dst + G::B_P, m + (st_pa ? MAP_PB : MAP_PA), bar, sg.x0 - G::VOFF,
+                            sg.y0 - 1, kk);
+        }
+        if (part == 2) mbar_arrive(bar);
+    };
+    // Issues the next plane of the stream (or, with pre, only its independent boxes).
+    auto issue_next = [&](bool pre = false) {
+        while (cs < nseg && coff == 0 && !s_member[s_seg[cs].solve - first]) ++cs;
+        if (cs >= nseg) return;
+        const int st = nissued % NS;
+        if (pre) {
+            issue_boxes(cs, coff, st, 1);
+            pend_seg[pend_n] = cs;
+            pend_off[pend_n] = coff;
+            pend_st[pend_n] = st;
+            ++pend_n;
+        } else {
+            issue_boxes(cs, coff, st, 0);
         }
         ++nissued;
-        if (++coff == L + 2) {
+        if (++coff == s_seg[cs].k1 - s_seg[cs].k0 + 2) {
             coff = 0;
             ++cs;
         }
     };
-    // Starts the stream of a phase: the first NS planes are issued at once.
-    auto begin_stream = [&](bool a_side, bool p_in_a) {
+    // Starts the stream of a phase.  With pre, only the first NS planes' independent boxes go
+    // out (before a grid barrier completes); finish_stream() then adds the rest.
+    auto begin_stream = [&](bool a_side, bool p_in_a, bool pre) {
         g0 = g;
         if (tid == 0) {
             cs = 0;
             coff = 0;
             st_a = a_side;
             st_pa = p_in_a;
-            for (int q = 0; q < NS; ++q) issue_next();
+            pend_n = 0;
+            for (int q = 0; q < NS; ++q) issue_next(pre);
+        }
+    };
+    auto finish_stream = [&]() {
+        if (tid == 0) {
+            for (int q = 0; q < pend_n; ++q) issue_boxes(pend_seg[q], pend_off[q], pend_st[q], 2);
+            pend_n = 0;
         }
     };
     auto acquire = [&]() -> bool {
@@ -546,14 +622,16 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         if (tid < nloc) s_member[tid] = (s_sol[tid].done == RUNNING);
         __syncthreads();
     };
-    begin_stream(true, p_in_a);
+    begin_stream(true, p_in_a, false);
     for (;;) {
         if (!run_phase(true, p_in_a)) { failed = true; break; }
         mark(TR_A);
-        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
-        mark(TR_BAR1);
         snapshot_members();
-        begin_stream(false, p_in_a);
+        grid_arrive(a.ctl, tid);
+        begin_stream(false, p_in_a, true);
+        if (!grid_wait(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        finish_stream();
+        mark(TR_BAR1);
         if (*(volatile int*)&a.ctl->running == 0) break;
         if (warp == 0) {
             for (int l = 0; l < nloc; ++l) {
@@ -575,10 +653,12 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         mark(TR_ALPHA);
         if (!run_phase(false, p_in_a)) { failed = true; break; }
         mark(TR_B);
-        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
-        mark(TR_BAR2);
         snapshot_members();
-        begin_stream(true, !p_in_a);
+        grid_arrive(a.ctl, tid);
+        begin_stream(true, !p_in_a, true);
+        if (!grid_wait(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        finish_stream();
+        mark(TR_BAR2);
         if (warp == 0) {
             for (int l = 0; l < nloc; ++l) {
                 if (s_sol[l].done != RUNNING) continue;
@@ -626,8 +706,10 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     }
     if (tr)
         for (int q = 0; q < TRACE_PARTS; ++q) a.trace[q] += tt[q];
-    // Planes issued but not consumed (the stream begun after the last barrier, or the rest of
-    // a failed phase): wait for them so no copy lands after the CTA has gone.
+    // Planes issued but not consumed (the stream begun at the last barrier, or the rest of a
+    // failed phase): complete any half-issued plane, then wait for them so no copy lands after
+    // the CTA has gone.
+    finish_stream();
     if (tid == 0) {
         if (failed) {
             atomicExch(&a.ctl->error, 1);
