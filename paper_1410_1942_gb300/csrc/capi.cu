@@ -137,7 +137,7 @@ static int march_run(poisson_t* H, bool bf16, double tol2, int max_iter, Scalars
     else
         launch_cg_init<float, CoefEta<float>>(d, H->kc, CoefEta<float>{H->eta32}, H->r32, H->z32,
                                               H->sc, H->partials, tol2, 0, max_iter, st);
-    *H->ctl_host = MarchCtl{0u, 1, 0, 0};
+    *H->ctl_host = MarchCtl{0u, 1, 0, 0, 0ull};
     CK(cudaMemcpyAsync(H->plan.ctl, H->ctl_host, sizeof(MarchCtl), cudaMemcpyHostToDevice, st));
     const bool prof = H->prof_on && result;
     if (prof) CK(cudaEventRecord(H->prof_ev[PROF_PCG], st));
@@ -221,11 +221,13 @@ static void free_state(poisson_t* H) {
         // development aid (POISSON_TRACE set): CTA 0's time per part of a PCG iteration
         unsigned long long t[TRACE_PARTS] = {};
         if (cudaMemcpy(t, H->plan.trace, sizeof(t), cudaMemcpyDeviceToHost) == cudaSuccess && t[TR_ITERS]) {
-            const char* names[] = {"phaseA", "bar1", "alpha", "phaseB", "bar2", "beta"};
+            const char* names[] = {"phaseA", "bar1", "alpha", "phaseB", "bar2", "beta", "iters",
+                                   "wait_slowest", "release"};
             fprintf(stderr, "[poisson trace] %dx%dx%d %llu iterations, us/iteration:", H->d.nx,
                     H->d.ny, H->d.nz, t[TR_ITERS]);
-            for (int q = 0; q < TR_ITERS; ++q)
-                fprintf(stderr, " %s=%.2f", names[q], 1e-3 * (double)t[q] / (double)t[TR_ITERS]);
+            for (int q = 0; q < TRACE_PARTS; ++q)
+                if (q != TR_ITERS)
+                    fprintf(stderr, " %s=%.2f", names[q], 1e-3 * (double)t[q] / (double)t[TR_ITERS]);
             fprintf(stderr, "\n");
         }
         cudaGetLastError();

@@ -241,12 +241,15 @@ __device__ __forceinline__ bool grid_barrier(MarchCtl* ctl, unsigned target, int
 }
 
 // Split-phase form of grid_barrier: arrive (after the CTA's stores), do independent work, wait.
-__device__ __forceinline__ void grid_arrive(MarchCtl* ctl, int tid) {
+// With a trace, the last CTA to arrive stamps the time of its arrival.
+__device__ __forceinline__ void grid_arrive(MarchCtl* ctl, int tid, unsigned target = 0,
+                                            bool stamp = false) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
         __threadfence();
-        atomicAdd(&ctl->bar, 1u);
+        const unsigned old = atomicAdd(&ctl->bar, 1u);
+        if (stamp && old + 1 == target) *(volatile unsigned long long*)&ctl->t_last = globaltimer();
     }
 }
 
@@ -627,9 +630,17 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         if (!run_phase(true, p_in_a)) { failed = true; break; }
         mark(TR_A);
         snapshot_members();
-        grid_arrive(a.ctl, tid);
+        ++nbar;
+        grid_arrive(a.ctl, tid, nbar * (unsigned)a.nctas, a.trace != nullptr);
+        const unsigned long long t_arr1 = tr ? globaltimer() : 0;
         begin_stream(false, p_in_a, true);
-        if (!grid_wait(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (!grid_wait(a.ctl, nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (tr) {
+            const unsigned long long tl = *(volatile unsigned long long*)&a.ctl->t_last;
+            const unsigned long long tn = globaltimer();
+            if (tl > t_arr1) tt[TR_IMB] += tl - t_arr1;
+            if (tn > tl) tt[TR_REL] += tn - tl;
+        }
         finish_stream();
         mark(TR_BAR1);
         if (*(volatile int*)&a.ctl->running == 0) break;
@@ -654,9 +665,17 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         if (!run_phase(false, p_in_a)) { failed = true; break; }
         mark(TR_B);
         snapshot_members();
-        grid_arrive(a.ctl, tid);
+        ++nbar;
+        grid_arrive(a.ctl, tid, nbar * (unsigned)a.nctas, a.trace != nullptr);
+        const unsigned long long t_arr2 = tr ? globaltimer() : 0;
         begin_stream(true, !p_in_a, true);
-        if (!grid_wait(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (!grid_wait(a.ctl, nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (tr) {
+            const unsigned long long tl = *(volatile unsigned long long*)&a.ctl->t_last;
+            const unsigned long long tn = globaltimer();
+            if (tl > t_arr2) tt[TR_IMB] += tl - t_arr2;
+            if (tn > tl) tt[TR_REL] += tn - tl;
+        }
         finish_stream();
         mark(TR_BAR2);
         if (warp == 0) {

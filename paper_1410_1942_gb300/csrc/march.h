@@ -46,6 +46,7 @@ struct MarchCtl {
     int running;   // solves not finished (the number of solves at launch)
     int error;     // 1 once a wait has timed out
     int pad;
+    unsigned long long t_last;  // trace only: global time of the last arrival at a barrier
 };
 
 // A persistent launch: nctas CTAs, CTA c owns segments [cta_seg[c], cta_seg[c+1]).
@@ -77,7 +78,8 @@ struct PcgArgs {
 };
 
 // Parts of a persistent-PCG iteration timed by the optional trace (CTA 0's view).
-enum { TR_A = 0, TR_BAR1, TR_ALPHA, TR_B, TR_BAR2, TR_BETA, TR_ITERS, TRACE_PARTS };
+// TR_IMB: CTA 0's arrival to the last CTA's arrival; TR_REL: last arrival to CTA 0's release.
+enum { TR_A = 0, TR_BAR1, TR_ALPHA, TR_B, TR_BAR2, TR_BETA, TR_ITERS, TR_IMB, TR_REL, TRACE_PARTS };
 
 bool march_supported(const Dims& d);
 int march_variant_count();
