@@ -1263,10 +1263,10 @@ void march_plan_free(MarchPlan* p) {
     *p = MarchPlan{};
 }
 
-// Splits the solves' tile columns into segments and gives every CTA an equal share of the
-// linearised (solve, tile, plane) space: CTA c owns planes [c W / G, (c + 1) W / G), cut into
-// one segment per tile column it touches.  Segments come out ordered by solve.  Fails (-1) if a
-// CTA would hold more than MAXSEG segments or a tensor map cannot be encoded.
+// Splits the solves' tile columns into z-segments and packs them into at most nctas CTAs so
+// that the largest per-CTA cost (planes + a fixed cost per segment) is as small as possible.
+// Segments come out ordered by solve.  Fails (-1) if a CTA would hold more than MAXSEG
+// segments or a tensor map cannot be encoded.
 int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int variant, bool bf16,
                      int nctas, cudaStream_t st) {
     march_plan_free(p);
@@ -1283,70 +1283,60 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
     if (nctas > W) nctas = (int)W;
     std::vector<Seg> segs;
     std::vector<int> cta_seg;
-    long long ntiles = 0;
-    for (int s = 0; s < nsolves; ++s) ntiles += (long long)tiles_x[s] * tiles_y[s];
-    if (ntiles <= nctas) {
-        // One segment per CTA: every tile column gets chunks, one CTA each, handed out one at a
-        // time to the column whose longest chunk is longest (this minimises the longest chunk,
-        // hence the slowest CTA).
-        struct Col { int solve, tile, nz, chunks; };
+    {
+        // Balanced split.  A CTA's cost is its planes plus SEG_COST per segment (the two halo
+        // planes of a segment and its pipeline start).  The smallest capacity T for which a
+        // greedy walk over the tile columns (in solve, tile order) fits in nctas CTAs is found
+        // by bisection; the walk then cuts the work list, taking a new segment only when the
+        // current CTA has room for at least MIN_PLANES more planes.
+        constexpr double SEG_COST = 2.0;
+        constexpr int MIN_PLANES = 2;
+        struct Col { int solve, tile, nz; };
         std::vector<Col> cols;
         for (int s = 0; s < nsolves; ++s)
-            for (int t = 0; t < tiles_x[s] * tiles_y[s]; ++t) cols.push_back({s, t, solves[s].d.nz, 1});
-        auto longest = [](const Col& c) { return (c.nz + c.chunks - 1) / c.chunks; };
-        long long used = (long long)cols.size();
-        while (used < nctas) {
-            size_t best = 0;
-            for (size_t q = 1; q < cols.size(); ++q)
-                if (longest(cols[q]) > longest(cols[best])) best = q;
-            if (cols[best].chunks >= cols[best].nz) break;
-            ++cols[best].chunks;
-            ++used;
-        }
-        for (const Col& c : cols) {
-            const Dims& d = solves[c.solve].d;
-            for (int q = 0; q < c.chunks; ++q) {
-                Seg g{};
-                g.solve = c.solve;
-                g.x0 = (c.tile % tiles_x[c.solve]) * v.width;
-                g.y0 = (c.tile / tiles_x[c.solve]) * v.height;
-                g.k0 = (int)((long long)d.nz * q / c.chunks);
-                g.k1 = (int)((long long)d.nz * (q + 1) / c.chunks);
-                if (g.k1 <= g.k0) continue;
-                cta_seg.push_back((int)segs.size());
-                segs.push_back(g);
+            for (int t = 0; t < tiles_x[s] * tiles_y[s]; ++t) cols.push_back({s, t, solves[s].d.nz});
+        auto walk = [&](double T, bool emit) -> long long {
+            long long ctas = 1;
+            double cost = 0.0;
+            if (emit) cta_seg.push_back(0);
+            for (const Col& c : cols) {
+                int k = 0;
+                while (k < c.nz) {
+                    int room = (int)(T - cost - SEG_COST + 1e-9);
+                    if (room < MIN_PLANES && cost > 0.0) {
+                        ++ctas;
+                        cost = 0.0;
+                        if (emit) cta_seg.push_back((int)segs.size());
+                        continue;
+                    }
+                    if (room < 1) room = 1;
+                    const int take = std::min(room, c.nz - k);
+                    if (emit) {
+                        Seg g{};
+                        g.solve = c.solve;
+                        g.x0 = (c.tile % tiles_x[c.solve]) * v.width;
+                        g.y0 = (c.tile / tiles_x[c.solve]) * v.height;
+                        g.k0 = k;
+                        g.k1 = k + take;
+                        segs.push_back(g);
+                    }
+                    cost += SEG_COST + take;
+                    k += take;
+                }
             }
+            return ctas;
+        };
+        double lo = (double)W / nctas + SEG_COST - 1.0, hi = (double)W / nctas * 2.0 + 4.0 * SEG_COST;
+        while (walk(hi, false) > nctas) hi *= 2.0;
+        for (int it = 0; it < 40; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (walk(mid, false) <= nctas) hi = mid; else lo = mid;
         }
-        nctas = (int)segs.size();
+        walk(hi, true);
+        nctas = (int)cta_seg.size();
         cta_seg.push_back((int)segs.size());
-    } else {
-        // More tile columns than CTAs: an equal share of the linearised plane space per CTA.
-        cta_seg.assign(nctas + 1, 0);
-        int sol = 0;
-        for (int c = 0; c < nctas; ++c) {
-            cta_seg[c] = (int)segs.size();
-            long long u = W * c / nctas;
-            const long long u1 = W * (c + 1) / nctas;
-            while (u < u1) {
-                while (base[sol + 1] <= u) ++sol;
-                const Dims& d = solves[sol].d;
-                const long long local = u - base[sol];
-                const int tile = (int)(local / d.nz);
-                const int k0 = (int)(local % d.nz);
-                const int k1 = (int)std::min<long long>(d.nz, k0 + (u1 - u));
-                Seg g{};
-                g.solve = sol;
-                g.x0 = (tile % tiles_x[sol]) * v.width;
-                g.y0 = (tile / tiles_x[sol]) * v.height;
-                g.k0 = k0;
-                g.k1 = k1;
-                segs.push_back(g);
-                u += k1 - k0;
-            }
-        }
     }
     std::vector<SolveDev> sd(nsolves);
-    cta_seg[nctas] = (int)segs.size();
     for (int c = 0; c < nctas; ++c)
         if (cta_seg[c + 1] - cta_seg[c] > MAXSEG) return -1;
     for (int s = 0; s < nsolves; ++s) {
