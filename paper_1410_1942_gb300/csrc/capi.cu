@@ -96,7 +96,7 @@ struct TuneKey {
     }
 };
 static std::mutex g_tune_mu;
-static std::map<TuneKey, int> g_tuned;
+static std::map<TuneKey, std::pair<int, int>> g_tuned;  // (variant, split strategy)
 
 static int num_sms() {
     static int n = 0;
@@ -115,11 +115,11 @@ static MarchSolve march_solve_of(poisson_t* H) {
                       bf16 ? (const void*)H->eta16 : (const void*)H->eta32, H->sc};
 }
 
-static int build_plan(poisson_t* H, int var) {
+static int build_plan(poisson_t* H, int var, int strategy) {
     const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
     const MarchSolve s = march_solve_of(H);
     const int nctas = march_occupancy(var, bf16) * num_sms();
-    return march_plan_build(&H->plan, &s, 1, var, bf16, nctas, H->st);
+    return march_plan_build(&H->plan, &s, 1, var, bf16, nctas, strategy, H->st);
 }
 
 // One FP32 inner PCG through the persistent kernel: init (z = D^{-1} r, scalars), p_in = 0,
@@ -153,14 +153,17 @@ static int setup_march(poisson_t* H) {
     const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
     const Dims d = H->d;
     const int forced = H->opts.tile;
-    int var = -1;
+    int var = -1, strategy = MARCH_SPLIT_EQUAL;
     if (forced > 0) {
         var = march_find_variant((forced / 1000) % 10, (forced / 100) % 10, forced % 100,
                                  forced / 10000);
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(TuneKey{d.nx, d.ny, d.nz, bf16 ? 1 : 0});
-        if (it != g_tuned.end()) var = it->second;
+        if (it != g_tuned.end()) {
+            var = it->second.first;
+            strategy = it->second.second;
+        }
     }
     if (var < 0 && forced <= 0) {
         // a constant-density model problem (rho = 1) with r = 1, TUNE_ITERS iterations per try
@@ -175,21 +178,25 @@ static int setup_march(poisson_t* H) {
         cudaEventCreate(&e1);
         float best = 1e30f;
         for (int cand = 0; cand < march_variant_count(); ++cand) {
-            if (march_occupancy(cand, bf16) <= 0 || build_plan(H, cand) != 0) continue;
-            float t[2];
-            bool good = true;
-            for (int rep = 0; rep < 2 && good; ++rep) {
-                cudaEventRecord(e0, st);
-                good = march_run(H, bf16, 0.0, TUNE_ITERS) == POISSON_OK;
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&t[rep], e0, e1);
-            }
-            if (!good || cudaGetLastError() != cudaSuccess) continue;
-            const float tt = std::min(t[0], t[1]);
-            if (tt < best) {
-                best = tt;
-                var = cand;
+            if (march_occupancy(cand, bf16) <= 0) continue;
+            for (int strat = 0; strat < MARCH_SPLITS; ++strat) {
+                if (build_plan(H, cand, strat) != 0) continue;
+                float t[2];
+                bool good = true;
+                for (int rep = 0; rep < 2 && good; ++rep) {
+                    cudaEventRecord(e0, st);
+                    good = march_run(H, bf16, 0.0, TUNE_ITERS) == POISSON_OK;
+                    cudaEventRecord(e1, st);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&t[rep], e0, e1);
+                }
+                if (!good || cudaGetLastError() != cudaSuccess) continue;
+                const float tt = std::min(t[0], t[1]);
+                if (tt < best) {
+                    best = tt;
+                    var = cand;
+                    strategy = strat;
+                }
             }
         }
         cudaEventDestroy(e0);
@@ -198,11 +205,11 @@ static int setup_march(poisson_t* H) {
         cudaStreamSynchronize(st);
         if (var >= 0) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tuned[TuneKey{d.nx, d.ny, d.nz, bf16 ? 1 : 0}] = var;
+            g_tuned[TuneKey{d.nx, d.ny, d.nz, bf16 ? 1 : 0}] = {var, strategy};
         }
     }
     if (var < 0) return POISSON_OK;  // stay on the column kernels
-    const int rc = build_plan(H, var);
+    const int rc = build_plan(H, var, strategy);
     if (rc == -2) return POISSON_ENOMEM;
     H->march = (rc == 0);
     return POISSON_OK;
@@ -717,9 +724,11 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
     if (H->march) {
         const MarchVariant v = march_variant(H->plan.variant);
         snprintf(buf, (size_t)len,
-                 "%s march tile=%d (%dx%d cells, %dx%d per thread%s) persistent ctas=%d segments=%d",
+                 "%s march tile=%d (%dx%d cells, %dx%d per thread%s) persistent ctas=%d segments=%d "
+                 "split=%s",
                  prec, 10000 * v.ws + 1000 * v.cx + 100 * v.cy + v.tyt, v.width, v.height, v.cx,
-                 v.cy, v.ws ? ", producer warp" : "", H->plan.nctas, H->plan.nsegs);
+                 v.cy, v.ws ? ", producer warp" : "", H->plan.nctas, H->plan.nsegs,
+                 H->plan.strategy == MARCH_SPLIT_BALANCED ? "balanced" : "equal");
     } else {
         snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d", prec, TX, TY, H->kc);
     }

@@ -1268,7 +1268,7 @@ void march_plan_free(MarchPlan* p) {
 // Segments come out ordered by solve.  Fails (-1) if a CTA would hold more than MAXSEG
 // segments or a tensor map cannot be encoded.
 int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int variant, bool bf16,
-                     int nctas, cudaStream_t st) {
+                     int nctas, int strategy, cudaStream_t st) {
     march_plan_free(p);
     const MarchVariant v = march_variant(variant);
     std::vector<long long> base(nsolves + 1, 0);  // first plane unit of each solve
@@ -1284,13 +1284,13 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
     std::vector<Seg> segs;
     std::vector<int> cta_seg;
     {
-        // Balanced split.  A CTA's cost is its planes plus SEG_COST per segment (the two halo
-        // planes of a segment and its pipeline start).  The smallest capacity T for which a
-        // greedy walk over the tile columns (in solve, tile order) fits in nctas CTAs is found
-        // by bisection; the walk then cuts the work list, taking a new segment only when the
-        // current CTA has room for at least MIN_PLANES more planes.
-        constexpr double SEG_COST = 2.0;
-        constexpr int MIN_PLANES = 2;
+        // A CTA's cost is its planes plus SEG_COST per segment (the two halo planes of a
+        // segment and its pipeline start; 0 for the plain equal-planes split).  The smallest
+        // capacity T for which a greedy walk over the tile columns (in solve, tile order) fits
+        // in nctas CTAs is found by bisection; the walk then cuts the work list, taking a new
+        // segment only when the current CTA has room for at least MIN_PLANES more planes.
+        const double SEG_COST = strategy == MARCH_SPLIT_BALANCED ? 2.0 : 0.0;
+        const int MIN_PLANES = strategy == MARCH_SPLIT_BALANCED ? 2 : 1;
         struct Col { int solve, tile, nz; };
         std::vector<Col> cols;
         for (int s = 0; s < nsolves; ++s)
@@ -1362,6 +1362,7 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
         for (int q = 0; q < 6; ++q) maps[6 * (size_t)s + q] = m[q];
     }
     p->variant = variant;
+    p->strategy = strategy;
     p->bf16 = bf16;
     p->nctas = nctas;
     p->nsolves = nsolves;

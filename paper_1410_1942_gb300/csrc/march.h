@@ -49,9 +49,13 @@ struct MarchCtl {
     unsigned long long t_last;  // trace only: global time of the last arrival at a barrier
 };
 
+// Work-split strategies of march_plan_build.
+enum { MARCH_SPLIT_EQUAL = 0, MARCH_SPLIT_BALANCED = 1, MARCH_SPLITS = 2 };
+
 // A persistent launch: nctas CTAs, CTA c owns segments [cta_seg[c], cta_seg[c+1]).
 struct MarchPlan {
     int variant = 0;
+    int strategy = 0;
     bool bf16 = false;
     int nctas = 0, nsolves = 0, nsegs = 0;
     SolveDev* solves = nullptr;
@@ -89,8 +93,10 @@ int march_occupancy(int variant, bool bf16);       // resident CTAs per SM (0 if
 
 // Builds (device arrays allocated, copied on st, synchronised) / frees a plan.  0 on success,
 // -1 if a tensor map cannot be encoded, -2 on allocation failure.
+// strategy: MARCH_SPLIT_EQUAL (equal planes per CTA) or MARCH_SPLIT_BALANCED (planes plus a
+// per-segment cost).
 int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int variant, bool bf16,
-                     int nctas, cudaStream_t st);
+                     int nctas, int strategy, cudaStream_t st);
 void march_plan_free(MarchPlan* p);
 
 // Cooperative launch of the persistent PCG over the plan (every solve's r, z, scalars
