@@ -45,6 +45,7 @@ extern "C" {
 #define POISSON_ECUDA (-7)           /* a CUDA runtime call failed */
 #define POISSON_ENOMEM_BUDGET (-8)   /* admission refused: over the device-memory budget */
 #define POISSON_ENOTICKET (-9)       /* poisson_poll: unknown or already collected ticket */
+#define POISSON_ETOOLARGE (-10)      /* poisson_residual_noalloc: grid beyond its static scratch */
 
 /* ------------------------------------------------------------------ options */
 #define POISSON_FP64 0           /* plain FP64 PCG on the GPU */
@@ -164,6 +165,29 @@ int poisson_profile(poisson_t* h, int enable);
 
 /* Copy out the accumulated per-class launch counts and event times (since poisson_profile). */
 int poisson_profile_read(poisson_t* h, poisson_kernel_times* out);
+
+/* ------------------------------------------------------------------ allocation-free check
+ * The paper has no counterpart to this entry point.  It is for callers that cannot allocate
+ * device memory when they check a pressure field: a step loop that must not pay cudaMalloc's
+ * latency or cudaFree's implicit device synchronisation, a process whose device memory belongs
+ * to another allocator under a fixed budget, or code that forbids dynamic allocation after
+ * initialisation.  It computes the FP64 relative residual ||b - A p||_2 / ||b||_2 (b = -h^2 rhs,
+ * A the FP64 operator of eq. (pois) built on the fly from F, rho_air, rho_water as in
+ * poisson_set_density) -- the figure poisson_solve reports in stats->rel_residual -- without any
+ * handle and without allocating: its only scratch is a 64 KiB static device array of the
+ * library, which every GPU that loads the library holds until the process exits.
+ *   F, rhs, p: device arrays of nx*ny*nz doubles (x fastest); host arrays give EINVAL.
+ *   rel_residual: one double, host or device memory (a device output is written on the stream
+ *     without waiting; a host output waits for the stream).  0 for an all-zero rhs.
+ *   stream: cudaStream_t to run on (NULL = legacy default stream).
+ * Limit: the x-y plane may span at most 4096 tiles of 32 x 8 cells (e.g. 2048 x 512 cells);
+ * larger grids give POISSON_ETOOLARGE.  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any stream capture.  All
+ * calls on a device share the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Errors: EINVAL, ETOOLARGE, ECUDA. */
+int poisson_residual_noalloc(int nx, int ny, int nz, double h, const double* F, double rho_air,
+                             double rho_water, const double* rhs, const double* p,
+                             double* rel_residual, void* stream);
 
 /* Write a one-line description of the handle's kernel choice (family, tile, z-chunk) into buf
  * (NUL-terminated, at most len bytes). */

@@ -18,6 +18,7 @@ from . import build as _build
 OK, PENDING = 0, 1
 EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN, ETIMEOUT, ENOTREADY, ECUDA, ENOMEM_BUDGET, ENOTICKET = \
     -1, -2, -3, -4, -5, -6, -7, -8, -9
+ETOOLARGE = -10
 FP64, FP32, FP32_BF16COEF = 0, 1, 2
 JACOBI, RBSSOR = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -29,7 +30,8 @@ PRECOND = {"jacobi": JACOBI, "rbssor": RBSSOR, "ssor": RBSSOR}
 EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson_set_density",
            "poisson_solve", "poisson_apply", "poisson_precond_apply", "poisson_get_operator",
            "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
-           "poisson_profile_read", "poisson_describe", "poisson_strerror", "poisson_version"]
+           "poisson_profile_read", "poisson_describe", "poisson_residual_noalloc",
+           "poisson_strerror", "poisson_version"]
 K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER, K_PCG = 0, 1, 2, 3, 4
 K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 
@@ -96,6 +98,8 @@ def load(path=None):
     lib.poisson_profile.argtypes = [vp, i]
     lib.poisson_profile_read.argtypes = [vp, ctypes.POINTER(KernelTimes)]
     lib.poisson_describe.argtypes = [vp, ctypes.c_char_p, i]
+    lib.poisson_residual_noalloc.argtypes = [i, i, i, d, vp, d, d, vp, vp, vp, vp]
+    lib.poisson_residual_noalloc.restype = i
     for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read", "poisson_describe"]:
         getattr(lib, name).restype = i
     _lib = lib
@@ -211,6 +215,24 @@ class Poisson:
     def get_operator(self, bx=None, by=None, bz=None, diag=None):
         _check(load().poisson_get_operator(self._h, _addr(bx), _addr(by), _addr(bz), _addr(diag)),
                "poisson_get_operator")
+
+
+def residual_noalloc(nx, ny, nz, h, F, rho_air, rho_water, rhs, p, out=None, stream=None):
+    """FP64 relative residual of ``p`` through ``poisson_residual_noalloc`` (no device allocation
+    in the library during the call; for callers that cannot allocate).  ``F``, ``rhs``, ``p`` are
+    CUDA float64 tensors; with ``out`` (a one-element CUDA float64 tensor) the result is written
+    there on the stream and None is returned, else the value is returned."""
+    st = stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream
+    if out is not None:
+        rc = load().poisson_residual_noalloc(nx, ny, nz, h, _addr(F), rho_air, rho_water,
+                                             _addr(rhs), _addr(p), _addr(out), st)
+        _check(rc, "poisson_residual_noalloc")
+        return None
+    v = ctypes.c_double(0.0)
+    rc = load().poisson_residual_noalloc(nx, ny, nz, h, _addr(F), rho_air, rho_water, _addr(rhs),
+                                         _addr(p), ctypes.addressof(v), st)
+    _check(rc, "poisson_residual_noalloc")
+    return v.value
 
 
 def kernel_launches():

@@ -748,6 +748,7 @@ extern "C" const char* poisson_strerror(int s) {
         case POISSON_ECUDA: return "CUDA runtime error";
         case POISSON_ENOMEM_BUDGET: return "over the device-memory budget";
         case POISSON_ENOTICKET: return "unknown ticket";
+        case POISSON_ETOOLARGE: return "grid too large for the allocation-free entry point";
         default: return "unknown status";
     }
 }
