@@ -218,7 +218,8 @@ static int setup_march(poisson_t* H) {
 static void free_state(poisson_t* H) {
     void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->eta32, H->eta16, H->x64,
                     H->b64, H->r64, H->z64, H->p64a, H->p64b, H->d32, H->r32, H->z32,
-                    H->p32a, H->p32b, H->sc, H->partials, H->io_a, H->io_b};
+                    H->p32a, H->p32b, H->sc, H->partials, H->io_a, H->io_b, H->io_c,
+                    H->io_c32};
     for (void* p : ptrs) dfree(p);
     if (H->sc_host) cudaFreeHost(H->sc_host);
     if (H->ctl_host) cudaFreeHost(H->ctl_host);
@@ -300,7 +301,8 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
             rc = POISSON_ECUDA;
     if (rc == POISSON_OK && cudaMemsetAsync(H->sc, 0, sizeof(Scalars), H->st) != cudaSuccess)
         rc = POISSON_ECUDA;
-    if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.tile != -1 && march_supported(H->d))
+    if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.precond == POISSON_JACOBI &&
+        o.tile != -1 && march_supported(H->d))
         A(setup_march(H));
     if (rc != POISSON_OK) {
         free_state(H);
@@ -369,8 +371,12 @@ static int cg_loop(poisson_t* H, const Coef& coef, V* r, V* z, double tol2, int 
     const int K = CG_CHUNK;
     cudaStream_t st = H->st;
     const bool prof = H->prof_on;
-    launch_cg_init<V, Coef>(H->d, H->kc, coef, r, z, H->sc, H->partials, tol2, rel_to_b, max_iter,
-                            st);
+    if (H->opts.precond == POISSON_RBSSOR)
+        launch_ssor_init<V, Coef>(H->d, H->kc, coef, r, z, H->opts.omega, H->sc, H->partials, tol2,
+                                  rel_to_b, max_iter, st);
+    else
+        launch_cg_init<V, Coef>(H->d, H->kc, coef, r, z, H->sc, H->partials, tol2, rel_to_b,
+                                max_iter, st);
     bool in_is_a = true;
     auto enqueue_chunk = [&](int slot) -> int {
         cudaEvent_t* ev = prof ? &H->prof_ev[slot * PROF_PER_CHUNK] : nullptr;
@@ -424,7 +430,7 @@ static int cg_loop(poisson_t* H, const Coef& coef, V* r, V* z, double tol2, int 
     }
 }
 
-// Column-kernel passes (any shape, any precision).
+// Column-kernel passes (any shape, any precision; Jacobi or red-black SSOR).
 template <typename V, typename Coef>
 static int cg_loop_columns(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* pa, V* pb,
                            double tol2, int rel_to_b, int max_iter, Scalars* result) {
@@ -434,8 +440,14 @@ static int cg_loop_columns(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* 
     auto A = [=](bool in_a) {
         launch_cg_a<V, Coef>(d, kc, coef, z, in_a ? pa : pb, in_a ? pb : pa, H->sc, H->partials, st);
     };
+    const bool ssor = H->opts.precond == POISSON_RBSSOR;
+    const double omega = H->opts.omega;
     auto B = [=](bool p_a) {
-        launch_cg_b<V, Coef>(d, kc, coef, p_a ? pa : pb, x, r, z, H->sc, H->partials, st);
+        if (ssor)
+            launch_cg_b_ssor<V, Coef>(d, kc, coef, p_a ? pa : pb, x, r, z, omega, H->sc,
+                                      H->partials, st);
+        else
+            launch_cg_b<V, Coef>(d, kc, coef, p_a ? pa : pb, x, r, z, H->sc, H->partials, st);
     };
     return cg_loop<V, Coef>(H, coef, r, z, tol2, rel_to_b, max_iter, result, A, B);
 }
@@ -529,11 +541,11 @@ static int solve_mixed(poisson_t* H, const E* eta, double tol, int* outer, int* 
         CK(cudaMemsetAsync(H->p32a, 0, bytes32, H->st));
         Scalars res;
         rc = POISSON_ECUDA;
-        if (H->march) {
+        if (H->march && H->opts.precond == POISSON_JACOBI) {
             rc = march_run(H, sizeof(E) == 2, target * target, H->opts.max_iters - total, &res);
             if (rc == POISSON_ECUDA) H->march = false;  // launch refused: use the column kernels
         }
-        if (!H->march)
+        if (!H->march || H->opts.precond != POISSON_JACOBI)
             rc = cg_loop_columns<float, CoefEta<E>>(H, c32, H->d32, H->r32, H->z32, H->p32a,
                                                     H->p32b, target * target, 0,
                                                     H->opts.max_iters - total, &res);
@@ -652,30 +664,53 @@ extern "C" int poisson_precond_apply(poisson_t* H, const double* r, double* z, i
                                      int precision) {
     if (!H || !r || !z || r == z) return POISSON_EINVAL;
     if (!H->ready) return POISSON_ENOTREADY;
-    if (kind != POISSON_JACOBI) return POISSON_EINVAL;
+    if (kind != POISSON_JACOBI && kind != POISSON_RBSSOR) return POISSON_EINVAL;
+    if (precision < POISSON_FP64 || precision > POISSON_FP32_BF16COEF) return POISSON_EINVAL;
     const Dims d = H->d;
     const int kc = H->kc;
     cudaStream_t st = H->st;
+    const double om = H->opts.omega;
+    if (kind == POISSON_RBSSOR) {
+        // sweeps in the precision's arithmetic on a scratch vector of that type
+        if (precision == POISSON_FP64) {
+            if (!H->io_c) {
+                int rc = dalloc(&H->io_c, (size_t)d.n);
+                if (rc) return rc;
+            }
+        } else if (!H->io_c32) {
+            int rc = dalloc(&H->io_c32, (size_t)d.n);
+            if (rc) return rc;
+        }
+    }
     switch (precision) {
         case POISSON_FP64: {
             const CoefFaces64 c{H->bx, H->by, H->bz, H->diag, nullptr};
             return with_io(H, r, z, [&](const double* a, double* b) {
-                launch_jacobi<double, CoefFaces64>(d, kc, c, a, b, st);
+                if (kind == POISSON_RBSSOR)
+                    launch_ssor_apply<double, CoefFaces64>(d, kc, c, a, H->io_c, om, b, st);
+                else
+                    launch_jacobi<double, CoefFaces64>(d, kc, c, a, b, st);
             });
         }
         case POISSON_FP32: {
             const CoefEta<float> c{H->eta32};
             return with_io(H, r, z, [&](const double* a, double* b) {
-                launch_jacobi<float, CoefEta<float>>(d, kc, c, a, b, st);
+                if (kind == POISSON_RBSSOR)
+                    launch_ssor_apply<float, CoefEta<float>>(d, kc, c, a, H->io_c32, om, b, st);
+                else
+                    launch_jacobi<float, CoefEta<float>>(d, kc, c, a, b, st);
             });
         }
-        case POISSON_FP32_BF16COEF: {
+        default: {
             const CoefEta<__nv_bfloat16> c{H->eta16};
             return with_io(H, r, z, [&](const double* a, double* b) {
-                launch_jacobi<float, CoefEta<__nv_bfloat16>>(d, kc, c, a, b, st);
+                if (kind == POISSON_RBSSOR)
+                    launch_ssor_apply<float, CoefEta<__nv_bfloat16>>(d, kc, c, a, H->io_c32, om, b,
+                                                                    st);
+                else
+                    launch_jacobi<float, CoefEta<__nv_bfloat16>>(d, kc, c, a, b, st);
             });
         }
-        default: return POISSON_EINVAL;
     }
 }
 

@@ -38,6 +38,8 @@ struct poisson_s {
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // staging for the checking entry points when given host arrays
     double *io_a = nullptr, *io_b = nullptr;
+    double* io_c = nullptr;   // SSOR apply scratch (FP64)
+    float* io_c32 = nullptr;  // SSOR apply scratch (FP32)
     // TMA plane-marching kernels for the FP32 inner solve (when the shape allows them)
     bool march = false;
     pcg::MarchPlan plan{};  // persistent work-list launch over this handle's grid

@@ -299,6 +299,164 @@ __global__ void __launch_bounds__(TX * TY) k_cg_b(Dims d, Coef coef, int kc,
     }
 }
 
+// ------------------------------------------------------------------ red-black SSOR
+// M = (D - wE) D^-1 (D - wE^T) / (w (2 - w)) in red-black order (red = (i+j+k) even first),
+// applied as: y_R = r_R / D_R; y_B = (r_B + w sum_{red nbrs} w_f y_R) / D_B;
+// t_R = y_R + w (sum_{black nbrs} w_f y_B) / D_R, t_B = y_B; z = w (2 - w) t.  Inside PCG the
+// constant factor w (2 - w) is left out (it rescales the search directions, not the iterates);
+// poisson_precond_apply applies it.  Each sweep updates one colour and reads only the other.
+__device__ __forceinline__ bool is_red(int i, int j, int k) { return ((i + j + k) & 1) == 0; }
+
+// phase B of SSOR-PCG: q = A p (recomputed), x += alpha p, r -= alpha q, z_R = r_R / D_R; sums r.r
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_cg_b_ssor(Dims d, Coef coef, int kc,
+                                                      const V* __restrict__ p, V* __restrict__ x,
+                                                      V* __restrict__ r, V* __restrict__ z,
+                                                      Scalars* sc, double* partials) {
+    __shared__ double smem[64];
+    if (sc->done) return;
+    const V alpha = (V)sc->alpha;
+    auto ld = [&](int e) { return p[e]; };
+    V rr = 0;
+    COL_LOOP_BEGIN
+        Stencil<V> w;
+        coef.weights(d, c, i, j, k, w);
+        const V pc = p[c];
+        const V q = w.D * pc - nb_sum(d, w, c, i, j, k, ld);
+        x[c] += alpha * pc;
+        const V rn = r[c] - alpha * q;
+        r[c] = rn;
+        if (is_red(i, j, k)) z[c] = rn * inv_diag<V, Coef>(coef, c, w);
+        rr += rn * rn;
+    COL_LOOP_END
+    double v[1] = {(double)rr}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sc->rr = tot[0];
+    }
+}
+
+// SSOR start from r: z_R = r_R / D_R (the black sweep and k_ssor_red follow); sums r.r and sets
+// the solve's scalars like k_cg_init.  R is the type r is read as (V, or double for the
+// checking entry point).
+template <typename V, typename Coef, typename R>
+__global__ void __launch_bounds__(TX * TY) k_ssor_first(Dims d, Coef coef, int kc,
+                                                       const R* __restrict__ r, V* __restrict__ z,
+                                                       Scalars* sc, double* partials, double tol2,
+                                                       int rel_to_b, int max_iter) {
+    __shared__ double smem[64];
+    V rr = 0;
+    COL_LOOP_BEGIN
+        const V rc = (V)r[c];
+        if (is_red(i, j, k)) {
+            Stencil<V> w;
+            coef.weights(d, c, i, j, k, w);
+            z[c] = rc * inv_diag<V, Coef>(coef, c, w);
+        }
+        rr += rc * rc;
+    COL_LOOP_END
+    if (!sc) return;
+    double v[1] = {(double)rr}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            sc->rr = tot[0];
+            sc->rr0 = tot[0];
+            sc->beta = 0.0;
+            sc->alpha = 0.0;
+            sc->iter = 0;
+            sc->max_iter = max_iter;
+            sc->stop2 = tol2 * (rel_to_b ? sc->bb : tot[0]);
+            sc->done = (tot[0] <= sc->stop2) ? CONVERGED : RUNNING;
+            if (!isfinite(tot[0])) sc->done = BREAKDOWN;
+            sc->rz = 0.0;
+        }
+    }
+}
+
+// black sweep: z_B = (r_B + w sum_{red nbrs} w_f z) / D_B
+template <typename V, typename Coef, typename R>
+__global__ void __launch_bounds__(TX * TY) k_ssor_black(Dims d, Coef coef, int kc,
+                                                       const R* __restrict__ r,
+                                                       V* __restrict__ z, double omega,
+                                                       const Scalars* sc) {
+    if (sc && sc->done) return;
+    const V om = (V)omega;
+    auto ld = [&](int e) { return z[e]; };
+    COL_LOOP_BEGIN
+        if (!is_red(i, j, k)) {
+            Stencil<V> w;
+            coef.weights(d, c, i, j, k, w);
+            z[c] = ((V)r[c] + om * nb_sum(d, w, c, i, j, k, ld)) * inv_diag<V, Coef>(coef, c, w);
+        }
+    COL_LOOP_END
+}
+
+// red sweep: z_R += w (sum_{black nbrs} w_f z) / D_R; then, inside PCG, sums r.z and updates
+// beta and the stopping state (mode 1), or only stores rz after the start (mode 0).
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_ssor_red(Dims d, Coef coef, int kc,
+                                                     const V* __restrict__ r, V* __restrict__ z,
+                                                     double omega, Scalars* sc, double* partials,
+                                                     int mode) {
+    __shared__ double smem[64];
+    if (sc->done) return;
+    const V om = (V)omega;
+    auto ld = [&](int e) { return z[e]; };
+    V rz = 0;
+    COL_LOOP_BEGIN
+        V zc = z[c];
+        if (is_red(i, j, k)) {
+            Stencil<V> w;
+            coef.weights(d, c, i, j, k, w);
+            zc += om * nb_sum(d, w, c, i, j, k, ld) * inv_diag<V, Coef>(coef, c, w);
+            z[c] = zc;
+        }
+        rz += r[c] * zc;
+    COL_LOOP_END
+    double v[1] = {(double)rz}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double rz_new = tot[0];
+            if (mode == 0) {
+                sc->rz = rz_new;
+                if (!isfinite(rz_new) || !(rz_new > 0.0)) sc->done = BREAKDOWN;
+            } else {
+                sc->iter += 1;
+                if (!isfinite(rz_new) || rz_new < 0.0 || !isfinite(sc->rr)) {
+                    sc->done = BREAKDOWN;
+                } else if (sc->rr <= sc->stop2) {
+                    sc->done = CONVERGED;
+                } else if (sc->iter >= sc->max_iter) {
+                    sc->done = CAPPED;
+                } else {
+                    sc->beta = rz_new / sc->rz;
+                    sc->rz = rz_new;
+                }
+            }
+        }
+    }
+}
+
+// red sweep of the checking entry point: z_R += w (sum w_f z_B) / D_R (no reduction)
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_ssor_red_plain(Dims d, Coef coef, int kc,
+                                                           V* __restrict__ z, double omega) {
+    const V om = (V)omega;
+    auto ld = [&](int e) { return z[e]; };
+    COL_LOOP_BEGIN
+        if (is_red(i, j, k)) {
+            Stencil<V> w;
+            coef.weights(d, c, i, j, k, w);
+            z[c] += om * nb_sum(d, w, c, i, j, k, ld) * inv_diag<V, Coef>(coef, c, w);
+        }
+    COL_LOOP_END
+}
+
+template <typename V>
+__global__ void k_scale_out(long long n, const V* __restrict__ z, double a, double* __restrict__ o) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t < n) o[t] = a * (double)z[t];
+}
+
 // ------------------------------------------------------------------ host launchers
 std::atomic<unsigned long long> g_kernel_launches{0};
 static inline void counted(int k) { g_kernel_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
@@ -389,6 +547,38 @@ void launch_cg_b(const Dims& d, int kc, const Coef& c, const V* p, V* x, V* r, V
     counted(1);
 }
 
+template <typename V, typename Coef>
+void launch_ssor_init(const Dims& d, int kc, const Coef& c, const V* r, V* z, double omega,
+                      Scalars* sc, double* part, double tol2, int rel_to_b, int max_iter,
+                      cudaStream_t st) {
+    k_ssor_first<V, Coef, V><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, r, z, sc, part,
+                                                                      tol2, rel_to_b, max_iter);
+    k_ssor_black<V, Coef, V><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, r, z, omega, sc);
+    k_ssor_red<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, r, z, omega, sc, part, 0);
+    counted(3);
+}
+
+template <typename V, typename Coef>
+void launch_cg_b_ssor(const Dims& d, int kc, const Coef& c, const V* p, V* x, V* r, V* z,
+                      double omega, Scalars* sc, double* part, cudaStream_t st) {
+    k_cg_b_ssor<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, p, x, r, z, sc, part);
+    k_ssor_black<V, Coef, V><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, r, z, omega, sc);
+    k_ssor_red<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, r, z, omega, sc, part, 1);
+    counted(3);
+}
+
+template <typename V, typename Coef>
+void launch_ssor_apply(const Dims& d, int kc, const Coef& c, const double* r, V* zbuf,
+                       double omega, double* out, cudaStream_t st) {
+    k_ssor_first<V, Coef, double><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(
+        d, c, kc, r, zbuf, nullptr, nullptr, 0.0, 0, 0);
+    k_ssor_black<V, Coef, double><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, r, zbuf,
+                                                                           omega, nullptr);
+    k_ssor_red_plain<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, zbuf, omega);
+    k_scale_out<V><<<blocks1d(d.n), 256, 0, st>>>(d.n, zbuf, omega * (2.0 - omega), out);
+    counted(4);
+}
+
 #define INSTANTIATE(V, C)                                                                   \
     template void launch_apply<V, C>(const Dims&, int, const C&, const double*, double*,     \
                                      cudaStream_t);                                         \
@@ -399,7 +589,13 @@ void launch_cg_b(const Dims& d, int kc, const Coef& c, const V* p, V* x, V* r, V
     template void launch_cg_a<V, C>(const Dims&, int, const C&, const V*, const V*, V*,     \
                                     Scalars*, double*, cudaStream_t);                       \
     template void launch_cg_b<V, C>(const Dims&, int, const C&, const V*, V*, V*, V*,       \
-                                    Scalars*, double*, cudaStream_t);
+                                    Scalars*, double*, cudaStream_t);                       \
+    template void launch_ssor_init<V, C>(const Dims&, int, const C&, const V*, V*, double,  \
+                                         Scalars*, double*, double, int, int, cudaStream_t); \
+    template void launch_cg_b_ssor<V, C>(const Dims&, int, const C&, const V*, V*, V*, V*,  \
+                                         double, Scalars*, double*, cudaStream_t);          \
+    template void launch_ssor_apply<V, C>(const Dims&, int, const C&, const double*, V*,    \
+                                          double, double*, cudaStream_t);
 
 INSTANTIATE(double, CoefFaces64)
 INSTANTIATE(float, CoefEta<float>)

@@ -39,6 +39,20 @@ template <typename V, typename Coef>
 void launch_cg_b(const Dims& d, int kc, const Coef& c, const V* p, V* x, V* r, V* z,
                  Scalars* sc, double* part, cudaStream_t st);
 
+// red-black SSOR (see kernels.cu): start (z = M^-1 r without the w(2-w) factor, scalars set),
+// phase B with the two sweeps and the beta/stopping update, and the checking apply
+// (out = M^-1 r including the factor; zbuf: n values of type V).
+template <typename V, typename Coef>
+void launch_ssor_init(const Dims& d, int kc, const Coef& c, const V* r, V* z, double omega,
+                      Scalars* sc, double* part, double tol2, int rel_to_b, int max_iter,
+                      cudaStream_t st);
+template <typename V, typename Coef>
+void launch_cg_b_ssor(const Dims& d, int kc, const Coef& c, const V* p, V* x, V* r, V* z,
+                      double omega, Scalars* sc, double* part, cudaStream_t st);
+template <typename V, typename Coef>
+void launch_ssor_apply(const Dims& d, int kc, const Coef& c, const double* r, V* zbuf,
+                       double omega, double* out, cudaStream_t st);
+
 extern std::atomic<unsigned long long> g_kernel_launches;
 
 }  // namespace pcg

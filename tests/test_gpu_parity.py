@@ -92,6 +92,26 @@ def test_jacobi_apply(name, prec):
     np.testing.assert_allclose(z, ref, rtol=APPLY_TOL[prec], atol=0)
 
 
+# SSOR sweeps accumulate up to 13 terms per cell in the precision's arithmetic; compared with the
+# oracle's FP64 sweep relative to max|z|.
+SSOR_TOL = {"fp64": 1e-13, "fp32": 1e-5, "bf16": 3e-2}
+
+
+@pytest.mark.parametrize("name", ["flat32", "ragged", "column"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("omega", [1.0, 1.3])
+def test_rbssor_apply(name, prec, omega):
+    """z = M^-1 r for the red-black SSOR preconditioner, against the oracle's sweep (itself
+    pinned to the literal dense splitting)."""
+    c, op, _, _ = case(name)
+    r = np.random.default_rng(10).standard_normal(c.grid.shape)
+    with solver(c, "fp64" if prec == "fp64" else "fp32", precond="rbssor", omega=omega) as s:
+        z = np.empty_like(r)
+        s.precond_apply(r, z, "rbssor", prec)
+    ref = oracle.precond(op, r, "ssor", omega)
+    assert np.max(np.abs(z - ref)) <= SSOR_TOL[prec] * np.abs(ref).max()
+
+
 def _check_solution(c, op, b, xref, p, stats, tol):
     rel = oracle.rel_residual(op, b, p)
     assert rel <= tol * (1 + 1e-6), rel
@@ -103,9 +123,10 @@ def _check_solution(c, op, b, xref, p, stats, tol):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
-def test_solve_matches_oracle(name, prec):
+@pytest.mark.parametrize("precond", ["jacobi", "rbssor"])
+def test_solve_matches_oracle(name, prec, precond):
     c, op, b, xref = case(name)
-    with solver(c, prec) as s:
+    with solver(c, prec, precond=precond) as s:
         p = np.zeros(c.grid.shape)
         rc, st = s.solve(c.s, p, c.tol)
     assert rc == capi.OK
@@ -130,6 +151,18 @@ def test_kernel_variants_match_oracle(tile, prec, shape):
         rc, st = s.solve(c.s, p, c.tol)
     assert rc == capi.OK
     _check_solution(c, op, b, xref, p, st, c.tol)
+
+
+def test_rbssor_needs_fewer_iterations_than_jacobi():
+    c, op, b, xref = case("strut")
+    its = {}
+    for pc in ("jacobi", "rbssor"):
+        with solver(c, "fp64", precond=pc) as s:
+            p = np.zeros(c.grid.shape)
+            rc, st = s.solve(c.s, p, 1e-9)
+        assert rc == capi.OK
+        its[pc] = st["inner_iters"]
+    assert its["rbssor"] < 0.75 * its["jacobi"], its
 
 
 def test_device_and_host_arrays_give_identical_results():
@@ -241,11 +274,13 @@ def strut_full():
     return c, op, b, ref.x
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp64", "bf16"])
-def test_full_size_strut_solve(strut_full, prec):
+@pytest.mark.parametrize("prec,precond", [("fp32", "jacobi"), ("fp64", "jacobi"),
+                                          ("bf16", "jacobi"), ("fp32", "rbssor"),
+                                          ("fp64", "rbssor")])
+def test_full_size_strut_solve(strut_full, prec, precond):
     """The 256 x 128 x 128 strut workload at 1e-9, as the benchmark runs it."""
     c, op, b, xref = strut_full
-    with solver(c, prec) as s:
+    with solver(c, prec, precond=precond) as s:
         p = np.zeros(c.grid.shape)
         rc, st = s.solve(c.s, p, c.tol)
     assert rc == capi.OK
