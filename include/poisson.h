@@ -128,17 +128,23 @@ int poisson_precond_apply(poisson_t* h, const double* r, double* z, int kind, in
 int poisson_get_operator(poisson_t* h, double* bx, double* by, double* bz, double* diag);
 
 /* ------------------------------------------------------------------ batched solves
- * Many independent solves of uneven size in one persistent launch captured in a CUDA graph.
+ * Many independent solves of uneven size driven together.  Every FP64 refinement step of the
+ * batch is one batched residual kernel, one batched CG start and ONE cooperative persistent
+ * PCG launch over all unfinished solves (captured in CUDA graphs, rebuilt when the batch
+ * changes).  Solves submitted while a batch runs join it at its next refinement step
+ * (continuous batching).  Handles with POISSON_FP64, POISSON_RBSSOR or nx % 8 != 0 are solved
+ * one by one with poisson_solve when polled.
  * poisson_batch_submit enqueues n solves (handles[i] with its density already set, rhs[i],
  * p[i] in/out as in poisson_solve, tol[i]) and returns a ticket per solve.  The arrays must stay
- * valid until poisson_poll reports the ticket finished.  Handles in one batch must be distinct.
- * Errors: EINVAL, ENOTREADY, ENOMEM, ECUDA. */
+ * valid, and the handles must not be used or destroyed, until poisson_poll reports the ticket.
+ * A handle may belong to one unreported ticket at a time.  Errors: EINVAL, ENOTREADY. */
 int poisson_batch_submit(poisson_t* const* handles, const double* const* rhs, double* const* p,
                          const double* tol, int n, uint64_t* tickets);
 
 /* POISSON_PENDING while the ticket's solve runs; then its final status (OK, ENOTCONV, ...),
  * with *stats filled (may be NULL); a finished ticket is forgotten after it is reported once.
- * Polling drives the batch: it launches the next chunk of iterations when none is in flight. */
+ * Polling drives the batch: a poll of an unfinished ticket runs one refinement step of its
+ * batch (or, for a one-by-one solve, the solve) before it returns. */
 int poisson_poll(uint64_t ticket, poisson_stats* stats);
 
 /* ------------------------------------------------------------------ instrumentation */

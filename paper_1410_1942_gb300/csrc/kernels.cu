@@ -14,6 +14,7 @@
 // without host round trips.
 #include "internal.cuh"
 #include "kernels.h"
+#include "jobs.cuh"
 
 #include <atomic>
 
@@ -457,6 +458,113 @@ __global__ void k_scale_out(long long n, const V* __restrict__ z, double a, doub
     if (t < n) o[t] = a * (double)z[t];
 }
 
+// ------------------------------------------------------------------ batched jobs
+// One launch over every job of a batch; block -> job by bisection over the job table.
+#define JOB_LOOP_BEGIN(J)                                                          \
+    const int jb_ = job_of_block(jobs, njobs, blockIdx.x);                        \
+    const JobDev& J = jobs[jb_];                                                   \
+    const unsigned local_ = blockIdx.x - J.blk_off;                                \
+    const Dims d = J.d;                                                            \
+    const int kc = J.kc;                                                           \
+    const int bx_ = local_ % J.gx, by_ = (local_ / J.gx) % J.gy, bz_ = local_ / (J.gx * J.gy); \
+    const int i = bx_ * TX + threadIdx.x;                                          \
+    const int j = by_ * TY + threadIdx.y;                                          \
+    const int k0 = bz_ * kc;                                                       \
+    const int k1 = min(d.nz, k0 + kc);
+
+// x64 += d; d = 0; p_a = 0 (the inner solve of the next refinement step starts from zero).
+__global__ void __launch_bounds__(TX * TY) k_batch_update(const JobDev* jobs, int njobs) {
+    JOB_LOOP_BEGIN(J)
+    if (!J.active || i >= d.nx || j >= d.ny) return;
+    for (int k = k0; k < k1; ++k) {
+        const int c = i + d.nx * (j + d.ny * k);
+        J.x64[c] += (double)J.d32[c];
+        J.d32[c] = 0.f;
+        J.pa32[c] = 0.f;
+    }
+}
+
+// r32 = (float)(b - A64 x64); (r.r, b.b) -> the job's scalars rr, bb.
+__global__ void __launch_bounds__(TX * TY) k_batch_residual(const JobDev* jobs, int njobs) {
+    __shared__ double smem[64];
+    JOB_LOOP_BEGIN(J)
+    if (!J.active) return;  // whole job skipped: its blocks never reach the reduction
+    const CoefFaces64 coef{J.bx, J.by, J.bz, J.diag, nullptr};
+    const double* x = J.x64;
+    auto ld = [&](int e) { return x[e]; };
+    double rr = 0.0, bb = 0.0;
+    if (i < d.nx && j < d.ny)
+        for (int k = k0; k < k1; ++k) {
+            const int c = i + d.nx * (j + d.ny * k);
+            Stencil<double> w;
+            coef.weights(d, c, i, j, k, w);
+            const double ax = w.D * x[c] - nb_sum(d, w, c, i, j, k, ld);
+            const double bc = J.b64[c];
+            const double rc = bc - ax;
+            J.r32[c] = (float)rc;
+            rr += rc * rc;
+            bb += bc * bc;
+        }
+    double v[2] = {rr, bb}, tot[2];
+    if (job_sum<2>(v, J.partials, &J.sc->ticket, (unsigned)J.blocks, local_, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            J.sc->rr = tot[0];
+            J.sc->bb = tot[1];
+        }
+    }
+}
+
+// z = D^-1 r (Jacobi start of the inner FP32 PCG), rz, rr0, stop2 = tol2 rr0; an inactive job
+// is marked CONVERGED so the persistent PCG skips it.
+template <typename E>
+__device__ __forceinline__ void batch_init_body(const JobDev& J, const Dims& d, int i, int j,
+                                                int k0, int k1, const E* eta, float& rz,
+                                                float& rr) {
+    const CoefEta<E> coef{eta};
+    if (i < d.nx && j < d.ny)
+        for (int k = k0; k < k1; ++k) {
+            const int c = i + d.nx * (j + d.ny * k);
+            Stencil<float> w;
+            coef.weights(d, c, i, j, k, w);
+            const float rc = J.r32[c];
+            const float zc = rc * rcp_approx(w.D);
+            J.z32[c] = zc;
+            rz += rc * zc;
+            rr += rc * rc;
+        }
+}
+
+__global__ void __launch_bounds__(TX * TY) k_batch_init(const JobDev* jobs, int njobs) {
+    __shared__ double smem[64];
+    JOB_LOOP_BEGIN(J)
+    if (!J.active) {
+        if (local_ == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+            J.sc->done = CONVERGED;
+            J.sc->iter = 0;
+        }
+        return;
+    }
+    float rz = 0.f, rr = 0.f;
+    if (J.bf16) batch_init_body(J, d, i, j, k0, k1, J.eta16, rz, rr);
+    else batch_init_body(J, d, i, j, k0, k1, J.eta32, rz, rr);
+    double v[2] = {(double)rz, (double)rr}, tot[2];
+    if (job_sum<2>(v, J.partials, &J.sc->ticket, (unsigned)J.blocks, local_, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            Scalars* sc = J.sc;
+            sc->rz = tot[0];
+            sc->rr = tot[1];
+            sc->rr0 = tot[1];
+            sc->beta = 0.0;
+            sc->alpha = 0.0;
+            sc->iter = 0;
+            sc->max_iter = J.max_iter;
+            sc->stop2 = J.tol2 * tot[1];
+            sc->done = (tot[1] <= sc->stop2) ? CONVERGED : RUNNING;
+            if (!isfinite(tot[0]) || !isfinite(tot[1])) sc->done = BREAKDOWN;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host launchers
 std::atomic<unsigned long long> g_kernel_launches{0};
 static inline void counted(int k) { g_kernel_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
@@ -577,6 +685,21 @@ void launch_ssor_apply(const Dims& d, int kc, const Coef& c, const double* r, V*
     k_ssor_red_plain<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, zbuf, omega);
     k_scale_out<V><<<blocks1d(d.n), 256, 0, st>>>(d.n, zbuf, omega * (2.0 - omega), out);
     counted(4);
+}
+
+void launch_batch_update(const JobDev* jobs, int njobs, int blocks, cudaStream_t st) {
+    k_batch_update<<<blocks, dim3(TX, TY), 0, st>>>(jobs, njobs);
+    counted(1);
+}
+
+void launch_batch_residual(const JobDev* jobs, int njobs, int blocks, cudaStream_t st) {
+    k_batch_residual<<<blocks, dim3(TX, TY), 0, st>>>(jobs, njobs);
+    counted(1);
+}
+
+void launch_batch_init(const JobDev* jobs, int njobs, int blocks, cudaStream_t st) {
+    k_batch_init<<<blocks, dim3(TX, TY), 0, st>>>(jobs, njobs);
+    counted(1);
 }
 
 #define INSTANTIATE(V, C)                                                                   \

@@ -53,6 +53,12 @@ template <typename V, typename Coef>
 void launch_ssor_apply(const Dims& d, int kc, const Coef& c, const double* r, V* zbuf,
                        double omega, double* out, cudaStream_t st);
 
+// Batched column kernels over a job table (jobs.cuh); blocks = total blocks of all jobs.
+struct JobDev;
+void launch_batch_update(const JobDev* jobs, int njobs, int blocks, cudaStream_t st);
+void launch_batch_residual(const JobDev* jobs, int njobs, int blocks, cudaStream_t st);
+void launch_batch_init(const JobDev* jobs, int njobs, int blocks, cudaStream_t st);
+
 extern std::atomic<unsigned long long> g_kernel_launches;
 
 }  // namespace pcg

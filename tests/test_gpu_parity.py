@@ -243,24 +243,95 @@ def test_iteration_cap_reports_notconv_with_best_iterate():
     assert rel < 1.0 and abs(st["rel_residual"] - rel) <= 1e-3 * rel
 
 
-def test_batch_submit_poll_matches_single_solves():
-    cases = inputs.batch_cases(4, seed=3, hi=(64, 48, 48))
-    solvers, ps = [], []
-    for c in cases:
-        solvers.append(solver(c, "fp32"))
-        ps.append(np.zeros(c.grid.shape))
-    tickets = capi.batch_submit(solvers, [c.s for c in cases], ps, 1e-9)
-    for t, c, p in zip(tickets, cases, ps):
-        while True:
+def _poll_all(tickets):
+    out = {}
+    pending = list(tickets)
+    while pending:
+        nxt = []
+        for t in pending:
             rc, st = capi.poll(t)
-            if rc != capi.PENDING:
-                break
+            if rc == capi.PENDING:
+                nxt.append(t)
+            else:
+                out[t] = (rc, st)
+        pending = nxt
+    return out
+
+
+def _oracle_ref(c):
+    op = oracle.operator(c.F)
+    b = oracle.rhs(c.s, c.grid.h)
+    return op, b, oracle.pcg(op, b, tol=REF_TOL, precond="ssor").x
+
+
+def test_batch_of_uneven_solves_matches_oracle():
+    """A batch of solves of uneven size, FP32 and BF16 coefficients, plus handles that run one
+    by one (FP64, SSOR): every result meets both acceptance criteria."""
+    cases = inputs.batch_cases(12, seed=3, hi=(96, 64, 48))
+    precs = ["fp32"] * 8 + ["bf16"] * 2 + ["fp64", "fp32"]
+    pcs = ["jacobi"] * 11 + ["rbssor"]
+    solvers = [solver(c, pr, precond=pc) for c, pr, pc in zip(cases, precs, pcs)]
+    ps = [np.zeros(c.grid.shape) for c in cases]
+    tickets = capi.batch_submit(solvers, [c.s for c in cases], ps, 1e-9)
+    res = _poll_all(tickets)
+    for t, c, p in zip(tickets, cases, ps):
+        rc, st = res[t]
         assert rc == capi.OK
-        op = oracle.operator(c.F)
-        assert oracle.rel_residual(op, oracle.rhs(c.s, c.grid.h), p) <= 1e-9 * (1 + 1e-6)
+        op, b, xref = _oracle_ref(c)
+        _check_solution(c, op, b, xref, p, st, 1e-9)
     assert capi.poll(tickets[0])[0] == capi.ENOTICKET
     for s in solvers:
         s.close()
+
+
+def test_solve_alone_and_in_the_mix_agree():
+    """The same solve run alone and inside a batch of others gives the same pressure within the
+    acceptance tolerance (both meet it against the oracle)."""
+    cases = inputs.batch_cases(6, seed=11, hi=(96, 64, 48))
+    target = cases[2]
+    alone = np.zeros(target.grid.shape)
+    with solver(target) as s:
+        t = capi.batch_submit([s], [target.s], [alone], 1e-9)
+        rc, _ = _poll_all(t)[t[0]]
+        assert rc == capi.OK
+    solvers = [solver(c) for c in cases]
+    ps = [np.zeros(c.grid.shape) for c in cases]
+    tickets = capi.batch_submit(solvers, [c.s for c in cases], ps, 1e-9)
+    res = _poll_all(tickets)
+    assert all(r[0] == capi.OK for r in res.values())
+    mixed = ps[2]
+    assert np.linalg.norm(mixed - alone) / np.linalg.norm(alone) <= L2_TOL
+    op, b, xref = _oracle_ref(target)
+    assert oracle.rel_residual(op, b, mixed) <= 1e-9 * (1 + 1e-6)
+    for s in solvers:
+        s.close()
+
+
+def test_solves_join_a_running_batch():
+    """Solves submitted after a batch has started join it at its next refinement step."""
+    cases = inputs.batch_cases(8, seed=21, hi=(80, 64, 48))
+    solvers = [solver(c) for c in cases]
+    ps = [np.zeros(c.grid.shape) for c in cases]
+    first = capi.batch_submit(solvers[:4], [c.s for c in cases[:4]], ps[:4], 1e-9)
+    for t in first[:1]:
+        assert capi.poll(t)[0] == capi.PENDING  # one refinement step of the first four
+    second = capi.batch_submit(solvers[4:], [c.s for c in cases[4:]], ps[4:], 1e-9)
+    res = _poll_all(first + second)
+    for t, c, p in zip(first + second, cases, ps):
+        rc, st = res[t]
+        assert rc == capi.OK
+        op, b, xref = _oracle_ref(c)
+        _check_solution(c, op, b, xref, p, st, 1e-9)
+    for s in solvers:
+        s.close()
+
+
+def test_batch_rejects_a_handle_twice():
+    c = inputs.flat_case(32, 32, 32, seed=1)
+    with solver(c) as s:
+        p = np.zeros(c.grid.shape)
+        with pytest.raises(capi.PoissonError):
+            capi.batch_submit([s, s], [c.s, c.s], [p, p.copy()], 1e-9)
 
 
 # ----------------------------------------------------------------------------- full size
