@@ -313,3 +313,96 @@ def batch_cases(n=64, seed=0, lo=(32, 32, 32), hi=(128, 64, 64), tol=1e-9):
     rng = np.random.default_rng(seed)
     shapes = [draw_shape(rng, lo, hi) for _ in range(n)]
     return [mixed_case(sh, seed * 100003 + 17 * i + 1, tol) for i, sh in enumerate(shapes)]
+
+
+# ----------------------------------------------------------------------------- torch twins
+# The same fields computed with torch (float64) on any device, for workloads that generate
+# inputs inside a running loop (the served request stream).  Same formulas as the numpy
+# versions above; tests check the two agree.
+def _torch():
+    import torch
+    return torch
+
+
+def smoothed_step_t(d, eps):
+    torch = _torch()
+    dr = d / eps
+    ramp = 0.5 * (1.0 + dr + torch.sin(math.pi * dr) / math.pi)
+    return torch.where(d > eps, torch.ones_like(d), torch.where(d < -eps, torch.zeros_like(d), ramp))
+
+
+def water_fraction_t(grid: Grid, eta_fn, psi_fn=None, z0=None, eps_cells=1.5, device="cpu"):
+    """:func:`water_fraction` (without breaking patches) in torch, shape (nz, ny, nx)."""
+    torch = _torch()
+    h = grid.h
+    eps = eps_cells * h
+    if z0 is None:
+        z0 = 0.5 * grid.lengths[2]
+    f64 = torch.float64
+    x = (torch.arange(grid.nx, dtype=f64, device=device) + 0.5) * h
+    y = (torch.arange(grid.ny, dtype=f64, device=device) + 0.5) * h
+    z = (torch.arange(grid.nz, dtype=f64, device=device) + 0.5) * h
+    surf = z0 + eta_fn(x[None, :], y[:, None])
+    F = smoothed_step_t(surf[None, :, :] - z[:, None, None], eps)
+    if psi_fn is not None:
+        F = torch.maximum(F, smoothed_step_t(-psi_fn(x[None, :], y[:, None]), eps)[None, :, :])
+    return F
+
+
+def divergence_source_t(grid: Grid, modes, dt=DT, amp=MODE_AMPLITUDE, device="cpu"):
+    """:func:`divergence_source` in torch (complex128 outer products), shape (nz, ny, nx)."""
+    torch = _torch()
+    nx, ny, nz, h = grid.nx, grid.ny, grid.nz, grid.h
+    L = grid.lengths
+    c128, f64 = torch.complex128, torch.float64
+    acc = torch.zeros(grid.shape, dtype=f64, device=device)
+
+    def e(kk, pos, Ld):
+        return torch.exp(1j * (2 * math.pi * kk / Ld) * pos.to(c128))
+
+    def mask(n, open_top):
+        m = torch.ones(n + 1, dtype=c128, device=device)
+        m[0] = 0
+        if not open_top:
+            m[n] = 0
+        return m
+
+    cx = (torch.arange(nx, dtype=f64, device=device) + 0.5) * h
+    cy = (torch.arange(ny, dtype=f64, device=device) + 0.5) * h
+    cz = (torch.arange(nz, dtype=f64, device=device) + 0.5) * h
+    fx = torch.arange(nx + 1, dtype=f64, device=device) * h
+    fy = torch.arange(ny + 1, dtype=f64, device=device) * h
+    fz = torch.arange(nz + 1, dtype=f64, device=device) * h
+    for m in modes:
+        ex_c, ey_c, ez_c = e(m.k[0], cx, L[0]), e(m.k[1], cy, L[1]), e(m.k[2], cz, L[2])
+        dx = torch.diff(e(m.k[0], fx, L[0]) * mask(nx, False))
+        dy = torch.diff(e(m.k[1], fy, L[1]) * mask(ny, False))
+        dz = torch.diff(e(m.k[2], fz, L[2]) * mask(nz, True))
+        c = amp * complex(math.cos(m.phase), math.sin(m.phase))
+        P = c * m.a[0] * (ez_c[:, None] * ey_c[None, :])
+        Q = c * (m.a[1] * ez_c[:, None] * dy[None, :] + m.a[2] * dz[:, None] * ey_c[None, :])
+        acc += (P[:, :, None] * dx[None, None, :] + Q[:, :, None] * ex_c[None, None, :]).imag
+    return acc / (h * dt)
+
+
+def mixed_fields_t(shape, seed, device="cpu"):
+    """The density field and first source of :func:`mixed_case` computed with torch, plus the
+    modes (for drifting the source step by step).  Returns (grid, F, s, modes)."""
+    nx, ny, nz = shape
+    grid = Grid(nx, ny, nz, 1.0 / nz)
+    rng = np.random.default_rng(seed)
+    Lx, Ly, _ = grid.lengths
+    px, py = rng.uniform(0.0, 2 * math.pi, size=2)
+    torch = _torch()
+    eta = lambda x, y: 0.02 * torch.sin(2 * math.pi * x / Lx + px) * torch.cos(2 * math.pi * y / Ly + py)
+    xc = rng.uniform(0.3, 0.7) * Lx
+    yc = rng.uniform(0.3, 0.7) * Ly
+
+    def psi(x, y):
+        r = torch.sqrt(((x - xc) / 0.1) ** 2 + ((y - yc) / 0.02) ** 2)
+        return (r - 1.0) * 0.02
+
+    F = water_fraction_t(grid, eta, psi, device=device)
+    modes = fourier_modes(rng)
+    s = divergence_source_t(grid, modes, device=device)
+    return grid, F, s, modes

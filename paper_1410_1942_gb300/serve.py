@@ -1,0 +1,164 @@
+"""Served pressure solves: a request stream over the batch executor (continuous batching).
+
+A request is one grid of its own size, density field and source, solved for ``steps``
+consecutive projection steps (the two-stage time integration of a ship-wave run solves the
+pressure Poisson equation at every stage); between steps the source drifts (the velocity modes
+are advected by the free stream for one ``dt``) and the previous pressure, kept on the device,
+is the next step's initial guess.
+
+The loop admits arriving requests first come first served while their device memory fits the
+budget, submits each request's current step to the library's batch executor
+(``poisson_batch_submit``), and polls: every poll of an unfinished solve runs one refinement step
+of the whole batch, and a request whose step finished submits its next step at once, so
+requests that arrive while others run join the batch at its next refinement step.  Reported:
+solves/s, per-solve latency percentiles (from submission, or arrival for a request's first
+step, to completion), the residual of every solve.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import math
+import time
+
+import numpy as np
+
+from . import capi, inputs
+
+# device bytes per cell of a handle (capi.cu allocations) plus the request's own F, s, p arrays
+HANDLE_BYTES_PER_CELL = {"fp32": 32 + 16 + 6 + 20, "bf16": 32 + 16 + 6 + 20, "fp64": 32 + 16 + 6 + 8 + 32}
+REQUEST_BYTES_PER_CELL = 3 * 8
+
+
+def request_bytes(shape, precision):
+    n = shape[0] * shape[1] * shape[2]
+    return n * (HANDLE_BYTES_PER_CELL[precision] + REQUEST_BYTES_PER_CELL) + (1 << 20)
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float        # seconds after the start of the run
+    shape: tuple          # (nx, ny, nz)
+    seed: int
+    # runtime state
+    step: int = 0
+    solver: object = None
+    grid: object = None
+    modes: list = None
+    F: object = None
+    s: object = None
+    p: object = None
+    ticket: int = 0
+    t_submit: float = 0.0
+    latencies: list = dataclasses.field(default_factory=list)
+    residuals: list = dataclasses.field(default_factory=list)
+    iters: list = dataclasses.field(default_factory=list)
+    statuses: list = dataclasses.field(default_factory=list)
+    admitted_at: float = -1.0
+    done_at: float = -1.0
+
+
+def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
+    """``n`` requests with Poisson arrivals of ``rate`` per second (rate = inf: all at t = 0) and
+    grid sizes drawn as in the batched workload (dims multiples of 16, aspect <= 4)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        if math.isfinite(rate):
+            t += rng.exponential(1.0 / rate)
+        out.append(Request(i, t if math.isfinite(rate) else 0.0, inputs.draw_shape(rng, lo, hi),
+                           int(seed * 7919 + 31 * i + 5)))
+    return out
+
+
+class Server:
+    def __init__(self, budget_bytes, precision="fp32", tol=1e-9, steps=20, device="cuda",
+                 keep_results=False):
+        self.budget = int(budget_bytes)
+        self.precision = precision
+        self.tol = tol
+        self.steps = steps
+        self.device = device
+        self.keep = keep_results
+        self.results = {}
+
+    def _admit(self, r, now):
+        g, F, s, modes = inputs.mixed_fields_t(r.shape, r.seed, device=self.device)
+        r.grid, r.F, r.s, r.modes = g, F, s, modes
+        import torch
+        r.p = torch.zeros(g.shape, dtype=torch.float64, device=self.device)
+        r.solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=self.precision)
+        r.solver.set_density(F)
+        r.admitted_at = now
+        self._submit(r, r.arrival)
+
+    def _submit(self, r, t_from):
+        import torch
+        torch.cuda.synchronize()  # the source is written on torch's stream
+        r.ticket = capi.batch_submit([r.solver], [r.s], [r.p], self.tol)[0]
+        r.t_submit = t_from
+
+    def _advance(self, r):
+        r.modes = inputs.advect_modes(r.modes, r.grid, inputs.DT)
+        r.s = inputs.divergence_source_t(r.grid, r.modes, device=self.device)
+
+    def serve(self, requests):
+        """Runs the stream to completion (wall clock); returns the statistics."""
+        pending = collections.deque(sorted(requests, key=lambda q: q.arrival))
+        active = []
+        used = 0
+        t0 = time.perf_counter()
+        lat = []
+        peak_active = 0
+        while pending or active:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                need = request_bytes(pending[0].shape, self.precision)
+                if used + need > self.budget and active:
+                    break  # wait for memory to free up
+                r = pending.popleft()
+                used += need
+                self._admit(r, now)
+                active.append(r)
+            peak_active = max(peak_active, len(active))
+            if not active:
+                time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
+                continue
+            for r in list(active):
+                rc, st = capi.poll(r.ticket)
+                if rc == capi.PENDING:
+                    continue
+                t = time.perf_counter() - t0
+                r.latencies.append(t - r.t_submit)
+                r.statuses.append(rc)
+                r.residuals.append(st["rel_residual"] if st else float("nan"))
+                r.iters.append(st["inner_iters"] if st else 0)
+                lat.append(t - r.t_submit)
+                r.step += 1
+                if r.step < self.steps and rc == capi.OK:
+                    self._advance(r)
+                    self._submit(r, t)
+                else:
+                    r.done_at = t
+                    if self.keep:
+                        self.results[r.rid] = r.p.cpu().numpy()
+                    r.solver.close()
+                    r.solver = None
+                    r.F = r.s = r.p = None
+                    used -= request_bytes(r.shape, self.precision)
+                    active.remove(r)
+        wall = time.perf_counter() - t0
+        lat = np.array(lat) if lat else np.zeros(1)
+        nsolves = sum(len(r.latencies) for r in requests)
+        cells = sum(r.shape[0] * r.shape[1] * r.shape[2] * len(r.latencies) for r in requests)
+        return {
+            "requests": len(requests), "solves": nsolves, "wall_s": wall,
+            "solves_per_s": nsolves / wall, "cell_solves_per_s": cells / wall,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "max_rel_residual": max((max(r.residuals) for r in requests if r.residuals), default=0.0),
+            "all_ok": all(all(s == capi.OK for s in r.statuses) and len(r.statuses) == self.steps
+                          for r in requests),
+            "peak_active": peak_active, "budget_bytes": self.budget, "precision": self.precision,
+        }

@@ -349,3 +349,16 @@ def test_oracle_reproduces_golden_fixture():
     got = [res.x[k, j, i] for i, j, k in g["samples_ijk"]]
     np.testing.assert_allclose(got, g["jacobi"]["p"], rtol=1e-8)
     assert abs(res.iters - g["jacobi"]["iters"]) <= 5
+
+
+def test_torch_input_twins_match_numpy():
+    """The torch generators used inside the served request loop give the numpy fields."""
+    torch = pytest.importorskip("torch")
+    c = inputs.mixed_case((48, 32, 32), seed=7)
+    grid, F, s, modes = inputs.mixed_fields_t((48, 32, 32), seed=7)
+    np.testing.assert_allclose(F.numpy(), c.F, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(s.numpy(), c.s, rtol=0, atol=1e-9 * np.abs(c.s).max())
+    drift = inputs.advect_modes(modes, grid, inputs.DT)
+    np.testing.assert_allclose(inputs.divergence_source_t(grid, drift).numpy(),
+                               inputs.divergence_source(grid, drift), rtol=0,
+                               atol=1e-9 * np.abs(c.s).max())

@@ -1,0 +1,55 @@
+"""The served request loop: continuous batching, admission by device-memory budget, warm starts,
+and the same result alone and in the mix."""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+from paper_1410_1942_gb300 import build, capi, inputs, serve
+
+pytestmark = pytest.mark.gpu
+
+L2_TOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available()
+    build.build()
+    capi.load()
+
+
+def _stream(n, rate, seed, hi=(96, 64, 64)):
+    return serve.request_stream(n, rate, seed=seed, hi=hi)
+
+
+def test_stream_of_requests_all_converge():
+    reqs = _stream(6, math.inf, seed=1)
+    st = serve.Server(budget_bytes=8 << 30, steps=4).serve(reqs)
+    assert st["all_ok"] and st["solves"] == 24
+    assert st["max_rel_residual"] <= 1e-9 * (1 + 1e-6)
+    # warm starts: later steps of a request need fewer CG iterations than its first
+    for r in reqs:
+        assert min(r.iters[1:]) < r.iters[0]
+
+
+def test_admission_respects_the_memory_budget():
+    reqs = _stream(5, math.inf, seed=2)
+    need = max(serve.request_bytes(r.shape, "fp32") for r in reqs)
+    st = serve.Server(budget_bytes=2 * need, steps=2).serve(reqs)
+    assert st["all_ok"] and st["peak_active"] <= 2
+
+
+def test_result_alone_equals_result_in_the_mix():
+    mix = _stream(6, 200.0, seed=3)
+    target = copy.deepcopy(mix[2])
+    target.arrival = 0.0
+    alone = serve.Server(budget_bytes=8 << 30, steps=5, keep_results=True)
+    alone.serve([target])
+    mixed = serve.Server(budget_bytes=8 << 30, steps=5, keep_results=True)
+    st = mixed.serve(mix)
+    assert st["all_ok"] and st["peak_active"] >= 2
+    a, m = alone.results[target.rid], mixed.results[mix[2].rid]
+    assert np.linalg.norm(a - m) / np.linalg.norm(a) <= L2_TOL
