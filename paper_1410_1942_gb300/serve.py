@@ -112,6 +112,7 @@ class Server:
         t0 = time.perf_counter()
         lat = []
         peak_active = 0
+        peak_used = 0
         while pending or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
@@ -123,6 +124,7 @@ class Server:
                 self._admit(r, now)
                 active.append(r)
             peak_active = max(peak_active, len(active))
+            peak_used = max(peak_used, used)
             if not active:
                 time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                 continue
@@ -160,5 +162,6 @@ class Server:
             "max_rel_residual": max((max(r.residuals) for r in requests if r.residuals), default=0.0),
             "all_ok": all(all(s == capi.OK for s in r.statuses) and len(r.statuses) == self.steps
                           for r in requests),
-            "peak_active": peak_active, "budget_bytes": self.budget, "precision": self.precision,
+            "peak_active": peak_active, "peak_used_bytes": peak_used, "budget_bytes": self.budget,
+            "precision": self.precision,
         }

@@ -39,7 +39,9 @@ def test_admission_respects_the_memory_budget():
     reqs = _stream(5, math.inf, seed=2)
     need = max(serve.request_bytes(r.shape, "fp32") for r in reqs)
     st = serve.Server(budget_bytes=2 * need, steps=2).serve(reqs)
-    assert st["all_ok"] and st["peak_active"] <= 2
+    assert st["all_ok"]
+    assert st["peak_used_bytes"] <= 2 * need
+    assert st["peak_active"] < len(reqs)  # some requests waited for memory
 
 
 def test_result_alone_equals_result_in_the_mix():
