@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--shape", type=int, nargs=3, default=(256, 128, 128),
                     help="grid of the strut workload (profiling of smaller cases)")
     ap.add_argument("--tile", type=int, default=0, help="FP32 kernel tile option (0 = autotuned)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 comparison, batched and served measurements")
+    ap.add_argument("--serve-requests", type=int, default=24)
     return ap.parse_args()
 
 
@@ -197,6 +200,99 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def fp64_baseline(case, steps, stream):
+    """Plain FP64 GPU PCG (Jacobi) on the same workload: solves/s at the same tolerance."""
+    import torch
+    from paper_1410_1942_gb300 import capi
+    g = case.grid
+    F = torch.from_numpy(case.F).cuda()
+    s = torch.from_numpy(case.s).cuda()
+    p = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp64", stream=stream.cuda_stream) as sv:
+        sv.set_density(F)
+        sv.solve(s, p, case.tol)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rel = 0, 0.0
+        for _ in range(steps):
+            sv.set_density(F)
+            p.zero_()
+            rc, st = sv.solve(s, p, case.tol)
+            its += st["inner_iters"]
+            rel = max(rel, st["rel_residual"])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+    return {"solves_per_s": steps / dt, "ms_per_solve": 1e3 * dt / steps,
+            "gcell_iters_per_s": g.n * its / dt / 1e9, "cg_iters_per_solve": its / steps,
+            "max_rel_residual": rel}
+
+
+def batched(n=64, seed=0):
+    """64 independent solves of uneven size (32^3 .. 128x64x64) submitted together and driven
+    by the batch executor (one persistent PCG launch per refinement step)."""
+    import torch
+    from paper_1410_1942_gb300 import capi, inputs
+    cases = inputs.batch_cases(n, seed=seed)
+    solvers, ps, rhs = [], [], []
+    for c in cases:
+        g = c.grid
+        sv = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32")
+        sv.set_density(torch.from_numpy(c.F).cuda())
+        solvers.append(sv)
+        rhs.append(torch.from_numpy(c.s).cuda())
+        ps.append(torch.zeros(g.shape, dtype=torch.float64, device="cuda"))
+
+    def run():
+        for p in ps:
+            p.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tickets = capi.batch_submit(solvers, rhs, ps, 1e-9)
+        res, pending = {}, list(tickets)
+        while pending:
+            nxt = []
+            for t in pending:
+                rc, st = capi.poll(t)
+                if rc == capi.PENDING:
+                    nxt.append(t)
+                else:
+                    res[t] = (rc, st)
+            pending = nxt
+        return time.perf_counter() - t0, [res[t] for t in tickets]
+
+    run()  # warm-up (graphs, plans)
+    dt, res = run()
+    cells_it = sum(c.grid.n * r[1]["inner_iters"] for c, r in zip(cases, res))
+    out = {"solves": n, "wall_s": dt, "solves_per_s": n / dt, "gcell_iters_per_s": cells_it / dt / 1e9,
+           "all_ok": all(r[0] == capi.OK for r in res),
+           "max_rel_residual": max(r[1]["rel_residual"] for r in res),
+           "cells": sum(c.grid.n for c in cases)}
+    for sv in solvers:
+        sv.close()
+    return out
+
+
+def served(nreq, seed=0):
+    """The request stream: capacity with every request waiting at t = 0 (6 steps each), then
+    Poisson arrivals at 70 % of that capacity, 20 steps per request; FP32 inner solve, and the
+    plain FP64 PCG's capacity on the same stream for comparison."""
+    import math as _m
+    from paper_1410_1942_gb300 import serve
+    budget = 48 << 30
+    cap = serve.Server(budget, steps=6).serve(serve.request_stream(max(4, nreq // 2), _m.inf, seed=seed + 1))
+    rate = 0.7 * cap["solves_per_s"] / 20.0
+    st = serve.Server(budget, steps=20).serve(serve.request_stream(nreq, rate, seed=seed))
+    cap64 = serve.Server(budget, precision="fp64", steps=3).serve(
+        serve.request_stream(max(4, nreq // 4), _m.inf, seed=seed + 2))
+    return {"capacity_solves_per_s": cap["solves_per_s"], "arrival_rate_per_s": rate,
+            "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "solves": st["solves"], "requests": nreq, "steps_per_request": 20,
+            "max_rel_residual": st["max_rel_residual"], "all_ok": st["all_ok"],
+            "peak_active": st["peak_active"],
+            "fp64_capacity_solves_per_s": cap64["solves_per_s"],
+            "fp64_p50_ms": cap64["p50_ms"], "fp64_p99_ms": cap64["p99_ms"]}
 
 
 def cpu_baseline(case, seconds, precond):
@@ -350,6 +446,14 @@ def main():
                "ms_per_step": 1e3 * te / args.steps}
         solver_h.close()
 
+    extras = {}
+    if rank == 0 and not args.no_extras and tuple(args.shape) == (256, 128, 128):
+        fb = fp64_baseline(case, 2, stream)
+        extras["fp64_baseline"] = fb
+        extras["mixed_vs_fp64_solves_ratio"] = (world * args.steps / (t_max * 1e-3)) / fb["solves_per_s"]
+        extras["batched"] = batched()
+        extras["served"] = served(args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(case, args.cpu_seconds, "ssor" if args.precond == "rbssor" else "jacobi")
@@ -377,6 +481,7 @@ def main():
                          "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
                          "ms_per_launch": per_launch_ms},
             "kernel_times": prof,
+            **extras,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
