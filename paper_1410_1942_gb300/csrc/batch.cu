@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -72,8 +74,24 @@ struct Executor {
     MarchPlan plan{};
     cudaGraphExec_t gR = nullptr, gS = nullptr;
     bool dirty = true;
+    // development trace (POISSON_TRACE): rebuilds and refinement steps, with their host time
+    bool trace = getenv("POISSON_TRACE") != nullptr;
+    long long n_rebuild = 0, n_step = 0;
+    double t_rebuild = 0.0, t_step = 0.0;
 
-    ~Executor() { release(); }
+    void report() const {
+        if (trace && (n_rebuild || n_step))
+            fprintf(stderr,
+                    "[poisson batch] %lld rebuilds (%.2f ms each), %lld refinement steps "
+                    "(%.2f ms each), graphs %s\n",
+                    n_rebuild, n_rebuild ? 1e3 * t_rebuild / n_rebuild : 0.0, n_step,
+                    n_step ? 1e3 * t_step / n_step : 0.0, gR ? "on" : "off");
+    }
+
+    ~Executor() {
+        report();
+        release();
+    }
 
     void release_graphs() {
         if (gR) cudaGraphExecDestroy(gR);
@@ -309,8 +327,12 @@ struct Executor {
     int step() {
         int rc = ensure_stream();
         if (rc) return rc;
+        const double ts = now_s();
         if (dirty || !waiting.empty()) {
             rc = rebuild();
+            ++n_rebuild;
+            t_rebuild += now_s() - ts;
+            if (trace && (n_rebuild % 64) == 1) report();
             if (rc) {
                 for (Job* j : table)
                     if (!j->finished) { j->finished = true; j->status = rc; }
@@ -368,6 +390,8 @@ struct Executor {
         }
         if (running == 0) {
             dirty = true;  // drop the finished jobs at the next rebuild
+            ++n_step;
+            t_step += now_s() - ts;
             return POISSON_OK;
         }
         *h_ctl = MarchCtl{0u, nj, 0, 0, 0ull};
@@ -389,6 +413,8 @@ struct Executor {
                 finish(j, POISSON_EBREAKDOWN);
             }
         }
+        ++n_step;
+        t_step += now_s() - ts;
         return POISSON_OK;
     }
 };

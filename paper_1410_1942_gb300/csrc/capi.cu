@@ -89,12 +89,21 @@ static void prof_add(poisson_t* H, int cls, cudaEvent_t a, cudaEvent_t b);
 // Every variant is tried on the handle's own buffers (zeroed; the scalars reset before every
 // launch) with a persistent grid of (resident CTAs per SM) x (SMs) CTAs, its phases A and B
 // timed with events, and the fastest kept; the choice is cached per shape and coefficient type.
+// Shapes are tuned per size class: each dimension rounded up to a power of two (at least 16).
 struct TuneKey {
     int nx, ny, nz, bf16;
     bool operator<(const TuneKey& o) const {
         return std::tie(nx, ny, nz, bf16) < std::tie(o.nx, o.ny, o.nz, o.bf16);
     }
 };
+static int size_class(int v) {
+    int c = 16;
+    while (c < v) c <<= 1;
+    return c;
+}
+static TuneKey tune_key(const Dims& d, bool bf16) {
+    return TuneKey{size_class(d.nx), size_class(d.ny), size_class(d.nz), bf16 ? 1 : 0};
+}
 static std::mutex g_tune_mu;
 static std::map<TuneKey, std::pair<int, int>> g_tuned;  // (variant, split strategy)
 
@@ -159,7 +168,7 @@ static int setup_march(poisson_t* H) {
                                  forced / 10000);
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tuned.find(TuneKey{d.nx, d.ny, d.nz, bf16 ? 1 : 0});
+        auto it = g_tuned.find(tune_key(d, bf16));
         if (it != g_tuned.end()) {
             var = it->second.first;
             strategy = it->second.second;
@@ -205,7 +214,7 @@ static int setup_march(poisson_t* H) {
         cudaStreamSynchronize(st);
         if (var >= 0) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            g_tuned[TuneKey{d.nx, d.ny, d.nz, bf16 ? 1 : 0}] = {var, strategy};
+            g_tuned[tune_key(d, bf16)] = {var, strategy};
         }
     }
     if (var < 0) return POISSON_OK;  // stay on the column kernels

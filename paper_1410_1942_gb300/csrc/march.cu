@@ -1263,13 +1263,27 @@ void march_plan_free(MarchPlan* p) {
     *p = MarchPlan{};
 }
 
+// Device buffer of at least `bytes`, reallocated only when it must grow.
+static bool plan_buffer(void** buf, size_t* cap, size_t bytes) {
+    if (*buf && *cap >= bytes) return true;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    if (cudaMalloc(buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *buf = nullptr;
+        return false;
+    }
+    *cap = bytes;
+    return true;
+}
+
 // Splits the solves' tile columns into z-segments and packs them into at most nctas CTAs so
 // that the largest per-CTA cost (planes + a fixed cost per segment) is as small as possible.
 // Segments come out ordered by solve.  Fails (-1) if a CTA would hold more than MAXSEG
 // segments or a tensor map cannot be encoded.
 int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int variant, bool bf16,
                      int nctas, int strategy, cudaStream_t st) {
-    march_plan_free(p);
     const MarchVariant v = march_variant(variant);
     std::vector<long long> base(nsolves + 1, 0);  // first plane unit of each solve
     std::vector<int> tiles_x(nsolves), tiles_y(nsolves);
@@ -1367,25 +1381,18 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
     p->nctas = nctas;
     p->nsolves = nsolves;
     p->nsegs = (int)segs.size();
-    auto up = [&](void** dst, const void* src, size_t bytes) -> bool {
-        if (cudaMalloc(dst, bytes) != cudaSuccess) {
-            cudaGetLastError();
-            *dst = nullptr;
-            return false;
-        }
-        return cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    auto up = [&](void** dst, size_t* cap, const void* src, size_t bytes) -> bool {
+        return plan_buffer(dst, cap, bytes) &&
+               cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, st) == cudaSuccess;
     };
-    bool ok = up((void**)&p->solves, sd.data(), sizeof(SolveDev) * sd.size()) &&
-              up((void**)&p->segs, segs.data(), sizeof(Seg) * segs.size()) &&
-              up((void**)&p->cta_seg, cta_seg.data(), sizeof(int) * cta_seg.size()) &&
-              up((void**)&p->maps, maps.data(), sizeof(CUtensorMap) * maps.size());
-    if (ok && (cudaMalloc((void**)&p->part_a, sizeof(double) * segs.size()) != cudaSuccess ||
-               cudaMalloc((void**)&p->part_b, sizeof(double) * 2 * segs.size()) != cudaSuccess ||
-               cudaMalloc((void**)&p->ctl, sizeof(MarchCtl)) != cudaSuccess)) {
-        cudaGetLastError();
-        ok = false;
-    }
-    if (ok && getenv("POISSON_TRACE")) {
+    bool ok = up((void**)&p->solves, &p->cap_solves, sd.data(), sizeof(SolveDev) * sd.size()) &&
+              up((void**)&p->segs, &p->cap_segs, segs.data(), sizeof(Seg) * segs.size()) &&
+              up((void**)&p->cta_seg, &p->cap_cta, cta_seg.data(), sizeof(int) * cta_seg.size()) &&
+              up((void**)&p->maps, &p->cap_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
+    ok = ok && plan_buffer((void**)&p->part_a, &p->cap_pa, sizeof(double) * segs.size()) &&
+         plan_buffer((void**)&p->part_b, &p->cap_pb, sizeof(double) * 2 * segs.size()) &&
+         plan_buffer((void**)&p->ctl, &p->cap_ctl, sizeof(MarchCtl));
+    if (ok && getenv("POISSON_TRACE") && !p->trace) {
         if (cudaMalloc((void**)&p->trace, sizeof(unsigned long long) * TRACE_PARTS) != cudaSuccess ||
             cudaMemsetAsync(p->trace, 0, sizeof(unsigned long long) * TRACE_PARTS, st) != cudaSuccess) {
             cudaGetLastError();

@@ -66,6 +66,9 @@ struct MarchPlan {
     double* part_b = nullptr;  // per segment: r.z, r.r
     MarchCtl* ctl = nullptr;
     unsigned long long* trace = nullptr;  // TRACE_PARTS counters when tracing is on
+    // allocated bytes of the buffers above (a rebuild reuses them when they suffice)
+    size_t cap_solves = 0, cap_segs = 0, cap_cta = 0, cap_maps = 0, cap_pa = 0, cap_pb = 0,
+           cap_ctl = 0;
 };
 
 // Kernel parameters of the persistent PCG launch.
@@ -91,8 +94,9 @@ MarchVariant march_variant(int id);
 int march_find_variant(int cx, int cy, int tyt, int ws);  // -1 if there is none
 int march_occupancy(int variant, bool bf16);       // resident CTAs per SM (0 if unknown)
 
-// Builds (device arrays allocated, copied on st, synchronised) / frees a plan.  0 on success,
-// -1 if a tensor map cannot be encoded, -2 on allocation failure.
+// Builds a plan (device arrays allocated, or reused when large enough, copied on st,
+// synchronised) / frees it.  0 on success, -1 if a tensor map cannot be encoded or a CTA would
+// hold too many segments, -2 on allocation failure.
 // strategy: MARCH_SPLIT_EQUAL (equal planes per CTA) or MARCH_SPLIT_BALANCED (planes plus a
 // per-segment cost).
 int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int variant, bool bf16,
