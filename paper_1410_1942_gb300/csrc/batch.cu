@@ -392,6 +392,7 @@ struct Executor {
             dirty = true;  // drop the finished jobs at the next rebuild
             ++n_step;
             t_step += now_s() - ts;
+            if (waiting.empty()) report();  // the batch has drained
             return POISSON_OK;
         }
         *h_ctl = MarchCtl{0u, nj, 0, 0, 0ull};
