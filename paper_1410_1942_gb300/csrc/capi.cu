@@ -186,8 +186,12 @@ static int setup_march(poisson_t* H) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
-        for (int cand = 0; cand < march_variant_count(); ++cand) {
-            if (march_occupancy(cand, bf16) <= 0) continue;
+        // candidates: the 2 x 2-cells-per-thread variants (64-wide tiles, 8 or 16 rows, with or
+        // without a producer warp); on the workloads measured the others never won
+        const int cands[] = {march_find_variant(2, 2, 8, 0), march_find_variant(2, 2, 4, 0),
+                             march_find_variant(2, 2, 8, 1), march_find_variant(2, 2, 4, 1)};
+        for (int cand : cands) {
+            if (cand < 0 || march_occupancy(cand, bf16) <= 0) continue;
             for (int strat = 0; strat < MARCH_SPLITS; ++strat) {
                 if (build_plan(H, cand, strat) != 0) continue;
                 float t[2];

@@ -75,7 +75,10 @@ def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
 
 class Server:
     def __init__(self, budget_bytes, precision="fp32", tol=1e-9, steps=20, device="cuda",
-                 keep_results=False):
+                 keep_results=False, tile=12204):
+        # tile: kernel variant of every request's handle (fixed, so admission does not run the
+        # autotuner; the batch executor uses the variant of its largest solve)
+        self.tile = tile
         self.budget = int(budget_bytes)
         self.precision = precision
         self.tol = tol
@@ -89,7 +92,8 @@ class Server:
         r.grid, r.F, r.s, r.modes = g, F, s, modes
         import torch
         r.p = torch.zeros(g.shape, dtype=torch.float64, device=self.device)
-        r.solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=self.precision)
+        r.solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=self.precision,
+                                tile=self.tile if self.precision != "fp64" else 0)
         r.solver.set_density(F)
         r.admitted_at = now
         self._submit(r, r.arrival)
