@@ -279,7 +279,9 @@ def served(nreq, seed=0):
     Poisson arrivals at 70 % of that capacity, 20 steps per request; FP32 inner solve, and the
     plain FP64 PCG's capacity on the same stream for comparison."""
     import math as _m
-    from paper_1410_1942_gb300 import serve
+    from paper_1410_1942_gb300 import inputs, serve
+    # warm the device-side input generators (torch compiles its complex kernels on first use)
+    inputs.mixed_fields_t((32, 32, 32), 1, device="cuda")
     budget = 48 << 30
     cap = serve.Server(budget, steps=6).serve(serve.request_stream(max(4, nreq // 2), _m.inf, seed=seed + 1))
     rate = 0.7 * cap["solves_per_s"] / 20.0

@@ -19,6 +19,7 @@ def _lib():
     assert torch.cuda.is_available()
     build.build()
     capi.load()
+    inputs.mixed_fields_t((32, 32, 32), 1, device="cuda")  # first-use compilation outside tests
 
 
 def _stream(n, rate, seed, hi=(96, 64, 64)):
