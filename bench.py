@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, batched and served measurements")
     ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--case", default="strut", choices=["strut", "wedge"],
+                    help="strut 256x128x128 (default) or the 1024x512x256 wedge (fields made on "
+                         "the device)")
     return ap.parse_args()
 
 
@@ -338,10 +341,18 @@ def main():
     _build.build()
     capi.load()
 
-    case = inputs.strut_case(*args.shape, seed=args.seed + rank)
-    g = case.grid
-    F_d = torch.from_numpy(case.F).to(dev)
-    s_d = torch.from_numpy(case.s).to(dev)
+    if args.case == "wedge":
+        shape = (1024, 512, 256) if tuple(args.shape) == (256, 128, 128) else tuple(args.shape)
+        g, F_d, s_d, _ = inputs.wedge_fields_t(shape, seed=args.seed + rank, device=dev)
+        case = inputs.Case("wedge", g, None, None, 1e-9, {})
+        args.no_extras = True
+        args.no_cpu_baseline = True
+        args.no_e2e = True
+    else:
+        case = inputs.strut_case(*args.shape, seed=args.seed + rank)
+        g = case.grid
+        F_d = torch.from_numpy(case.F).to(dev)
+        s_d = torch.from_numpy(case.s).to(dev)
     p_d = torch.zeros(g.shape, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision, precond=args.precond,
@@ -467,8 +478,10 @@ def main():
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if tuple(args.shape) == (256, 128, 128)
-                        else "strut %dx%dx%d (profiling case)" % tuple(args.shape), "cells": g.n, "precision": args.precision,
+            "config": {"workload": ("wedge %dx%dx%d (hull half-plane pair, breaking patches)"
+                                    % (g.nx, g.ny, g.nz)) if args.case == "wedge" else
+                        (WORKLOAD if tuple(args.shape) == (256, 128, 128)
+                         else "strut %dx%dx%d (profiling case)" % tuple(args.shape)), "cells": g.n, "precision": args.precision,
                        "precond": args.precond, "tol": case.tol,
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",

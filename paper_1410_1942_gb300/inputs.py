@@ -406,3 +406,41 @@ def mixed_fields_t(shape, seed, device="cpu"):
     modes = fourier_modes(rng)
     s = divergence_source_t(grid, modes, device=device)
     return grid, F, s, modes
+
+
+def wedge_fields_t(shape=(1024, 512, 256), seed=0, device="cpu"):
+    """The wedge workload of :func:`wedge_case` computed with torch on ``device``: same hull,
+    surface and source; the breaking patches are drawn with a seeded torch generator (so they
+    differ from the numpy version's).  Returns (grid, F, s, meta)."""
+    torch = _torch()
+    nx, ny, nz = shape
+    grid = Grid(nx, ny, nz, 1.0 / nz)
+    rng = np.random.default_rng(seed)
+    Lx, Ly, _ = grid.lengths
+    xa, yc = 0.25 * Lx, 0.5 * Ly
+    theta = math.radians(rng.uniform(10.0, 30.0))
+    kw = rng.uniform(8.0, 16.0)
+    sn, cs = math.sin(theta), math.cos(theta)
+    eta = lambda x, y: 0.01 * torch.sin(kw * (x - xa)) * torch.exp(-torch.abs(y - yc) / 0.2)
+    psi = lambda x, y: torch.maximum((y - yc) * cs - (x - xa) * sn, -(y - yc) * cs - (x - xa) * sn)
+    F = water_fraction_t(grid, eta, psi, device=device)
+    # breaking-like patches: 5 % of the cells within 2h of the surface set to a sharp 0 or 1
+    h = grid.h
+    f64 = torch.float64
+    x = (torch.arange(nx, dtype=f64, device=device) + 0.5) * h
+    y = (torch.arange(ny, dtype=f64, device=device) + 0.5) * h
+    z = (torch.arange(nz, dtype=f64, device=device) + 0.5) * h
+    surf = 0.5 * grid.lengths[2] + eta(x[None, :], y[:, None])
+    body = smoothed_step_t(-psi(x[None, :], y[:, None]), 1.5 * h)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) + 12345)
+    for k0 in range(0, nz, 32):
+        k1 = min(nz, k0 + 32)
+        d = surf[None, :, :] - z[k0:k1, None, None]
+        near = torch.abs(d) <= 2.0 * h
+        flip = near & (torch.rand(d.shape, generator=gen, device=device) < 0.05)
+        vals = (torch.rand(d.shape, generator=gen, device=device) < 0.5).to(f64)
+        F[k0:k1] = torch.maximum(torch.where(flip, vals, F[k0:k1]), body[None, :, :])
+    modes = fourier_modes(rng)
+    s = divergence_source_t(grid, modes, device=device)
+    return grid, F, s, {"seed": seed, "theta_deg": math.degrees(theta), "k": kw}
