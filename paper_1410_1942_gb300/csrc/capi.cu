@@ -164,8 +164,7 @@ static int setup_march(poisson_t* H) {
     const int forced = H->opts.tile;
     int var = -1, strategy = MARCH_SPLIT_EQUAL;
     if (forced > 0) {
-        var = march_find_variant((forced / 1000) % 10, (forced / 100) % 10, forced % 100,
-                                 forced / 10000);
+        var = march_variant_of_tile(forced);
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(tune_key(d, bf16));
@@ -187,11 +186,9 @@ static int setup_march(poisson_t* H) {
         cudaEventCreate(&e1);
         float best = 1e30f;
         // candidates: the 2 x 2-cells-per-thread variants (64-wide tiles, 8 or 16 rows, with or
-        // without a producer warp); on the workloads measured the others never won
-        const int cands[] = {march_find_variant(2, 2, 8, 0), march_find_variant(2, 2, 4, 0),
-                             march_find_variant(2, 2, 8, 1), march_find_variant(2, 2, 4, 1)};
-        for (int cand : cands) {
-            if (cand < 0 || march_occupancy(cand, bf16) <= 0) continue;
+        // without a producer warp, 3-, 4- or 6-stage rings); the 1 x 1 one never won
+        for (int cand = 0; cand < march_variant_count(); ++cand) {
+            if (march_variant(cand).cx != 2 || march_occupancy(cand, bf16) <= 0) continue;
             for (int strat = 0; strat < MARCH_SPLITS; ++strat) {
                 if (build_plan(H, cand, strat) != 0) continue;
                 float t[2];
@@ -269,8 +266,7 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (o.precond != POISSON_JACOBI && o.precond != POISSON_RBSSOR) return POISSON_EINVAL;
     if (!(o.omega > 0.0 && o.omega < 2.0)) return POISSON_EINVAL;
     if (o.max_iters <= 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return POISSON_EINVAL;
-    if (o.tile < -1 || (o.tile > 0 && march_find_variant((o.tile / 1000) % 10, (o.tile / 100) % 10,
-                                                          o.tile % 100, o.tile / 10000) < 0))
+    if (o.tile < -1 || (o.tile > 0 && march_variant_of_tile(o.tile) < 0))
         return POISSON_EINVAL;
 
     poisson_t* H = new (std::nothrow) poisson_t();
@@ -772,10 +768,10 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
     if (H->march) {
         const MarchVariant v = march_variant(H->plan.variant);
         snprintf(buf, (size_t)len,
-                 "%s march tile=%d (%dx%d cells, %dx%d per thread%s) persistent ctas=%d segments=%d "
-                 "split=%s",
-                 prec, 10000 * v.ws + 1000 * v.cx + 100 * v.cy + v.tyt, v.width, v.height, v.cx,
-                 v.cy, v.ws ? ", producer warp" : "", H->plan.nctas, H->plan.nsegs,
+                 "%s march tile=%d (%dx%d cells, %dx%d per thread%s, %d stages) persistent "
+                 "ctas=%d segments=%d split=%s",
+                 prec, march_tile_of(H->plan.variant), v.width, v.height, v.cx, v.cy,
+                 v.ws ? ", producer warp" : "", v.ns, H->plan.nctas, H->plan.nsegs,
                  H->plan.strategy == MARCH_SPLIT_BALANCED ? "balanced" : "equal");
     } else {
         snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d", prec, TX, TY, H->kc);

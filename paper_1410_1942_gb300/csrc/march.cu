@@ -36,7 +36,8 @@
 
 namespace pcg {
 
-constexpr int NS = 4;  // shared-memory stages (planes) in the ring
+// Shared-memory stages (planes) in a kernel's ring: a template parameter of each kernel
+// (3, 4 or 6 in the variant table).
 
 __host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
 
@@ -100,18 +101,6 @@ __device__ __forceinline__ void st_row(float* g, const float (&v)[CX]) {
         *reinterpret_cast<float2*>(g) = make_float2(v[0], v[1]);
     else
         *g = v[0];
-}
-
-// Gives up on a failed wait: records the timeout, then (thread 0) waits, bounded, for the
-// stages still in flight so no copy lands in shared memory after the CTA has gone.
-__device__ __forceinline__ void march_abort(Scalars* sc, uint64_t* bars, int waited, int issued,
-                                            int tid) {
-    if (tid == 0) {
-        atomicExch(&sc->done, (int)TIMEDOUT);
-        for (int q = waited; q < issued; ++q) (void)mbar_wait(&bars[q % NS], (q / NS) & 1);
-        __threadfence();
-    }
-    __syncthreads();
 }
 
 // The stencil of one plane for the CX x CY block of a thread.
@@ -332,7 +321,7 @@ __device__ __forceinline__ void warp_range_sum(const double* part, int b, int e,
 // barrier's decisions), so the first planes of a phase are already in flight while the partial
 // sums of the previous one are being added.  A solve that finished at that barrier is walked
 // once more without arithmetic (its work flag is off).
-template <int CX, int CY, int TYT, typename E>
+template <int CX, int CY, int TYT, typename E, int NS>
 __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     using G = Geo<CX, CY, TYT, E>;
     extern __shared__ __align__(128) unsigned char sm[];
@@ -755,7 +744,7 @@ struct WsMinBlocks {
     static constexpr int value = TYT >= 8 ? 2 : (TYT >= 4 ? 3 : 4);
 };
 
-template <int CX, int CY, int TYT, typename E>
+template <int CX, int CY, int TYT, typename E, int NS>
 __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg_ws(PcgArgs a) {
     using G = Geo<CX, CY, TYT, E>;
     constexpr int NT = 32 * (TYT + 1);  // all threads
@@ -1163,32 +1152,32 @@ bool march_supported(const Dims& d) {
 // ------------------------------------------------------------------ variant table
 // A variant is (CX, CY, TYT); its tile is 32 CX wide and CY TYT high.
 struct VariantOps {
-    int cx, cy, tyt, ws;
+    int cx, cy, tyt, ws, ns;
     int smem32, smem16;
     const void *k32, *k16;
 };
 
-template <int CX, int CY, int TYT, int WS>
+template <int CX, int CY, int TYT, int WS, int NS>
 static VariantOps make_ops() {
     if constexpr (WS)
-        return VariantOps{CX, CY, TYT, 1, NS * Geo<CX, CY, TYT, float>::STAGE,
+        return VariantOps{CX, CY, TYT, 1, NS, NS * Geo<CX, CY, TYT, float>::STAGE,
                           NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
-                          (const void*)k_pcg_ws<CX, CY, TYT, float>,
-                          (const void*)k_pcg_ws<CX, CY, TYT, __nv_bfloat16>};
+                          (const void*)k_pcg_ws<CX, CY, TYT, float, NS>,
+                          (const void*)k_pcg_ws<CX, CY, TYT, __nv_bfloat16, NS>};
     else
-        return VariantOps{CX, CY, TYT, 0, NS * Geo<CX, CY, TYT, float>::STAGE,
+        return VariantOps{CX, CY, TYT, 0, NS, NS * Geo<CX, CY, TYT, float>::STAGE,
                           NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
-                          (const void*)k_pcg<CX, CY, TYT, float>,
-                          (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16>};
+                          (const void*)k_pcg<CX, CY, TYT, float, NS>,
+                          (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16, NS>};
 }
 
-// (CX, CY, TYT, warp-specialised)
-#define MARCH_VARIANTS(X) X(1, 1, 4, 0) X(1, 1, 8, 0) X(1, 1, 16, 0) X(2, 2, 2, 0) \
-    X(2, 2, 4, 0) X(2, 2, 8, 0) X(2, 1, 8, 0) X(1, 2, 8, 0)                        \
-    X(2, 2, 4, 1) X(2, 2, 8, 1) X(1, 1, 8, 1) X(2, 1, 8, 1) X(1, 2, 8, 1) X(2, 2, 2, 1)
+// (CX, CY, TYT, warp-specialised, ring stages)
+#define MARCH_VARIANTS(X) X(1, 1, 8, 0, 4) X(2, 2, 4, 0, 4) X(2, 2, 8, 0, 4) X(2, 2, 4, 1, 4) \
+    X(2, 2, 8, 1, 4) X(2, 2, 4, 0, 3) X(2, 2, 8, 0, 3) X(2, 2, 8, 1, 3) X(2, 2, 4, 0, 6)        \
+    X(2, 2, 8, 1, 6)
 
 static const VariantOps* variants(int* count) {
-#define ROW(CX, CY, TYT, WS) make_ops<CX, CY, TYT, WS>(),
+#define ROW(CX, CY, TYT, WS, NS) make_ops<CX, CY, TYT, WS, NS>(),
     static const VariantOps table[] = {MARCH_VARIANTS(ROW)};
 #undef ROW
     static std::once_flag once;
@@ -1215,15 +1204,27 @@ MarchVariant march_variant(int id) {
     int n;
     const VariantOps* t = variants(&n);
     const VariantOps& v = t[id < 0 || id >= n ? 0 : id];
-    return MarchVariant{id, v.cx, v.cy, v.tyt, v.ws, 32 * v.cx, v.cy * v.tyt};
+    return MarchVariant{id, v.cx, v.cy, v.tyt, v.ws, v.ns, 32 * v.cx, v.cy * v.tyt};
 }
 
-int march_find_variant(int cx, int cy, int tyt, int ws) {
+int march_find_variant(int cx, int cy, int tyt, int ws, int ns) {
     int n;
     const VariantOps* t = variants(&n);
     for (int q = 0; q < n; ++q)
-        if (t[q].cx == cx && t[q].cy == cy && t[q].tyt == tyt && t[q].ws == ws) return q;
+        if (t[q].cx == cx && t[q].cy == cy && t[q].tyt == tyt && t[q].ws == ws && t[q].ns == ns)
+            return q;
     return -1;
+}
+
+int march_variant_of_tile(int tile) {
+    const int ns = tile / 100000 ? tile / 100000 : 4;
+    return march_find_variant((tile / 1000) % 10, (tile / 100) % 10, tile % 100,
+                              (tile / 10000) % 10, ns);
+}
+
+int march_tile_of(int variant) {
+    const MarchVariant v = march_variant(variant);
+    return (v.ns == 4 ? 0 : 100000 * v.ns) + 10000 * v.ws + 1000 * v.cx + 100 * v.cy + v.tyt;
 }
 
 int march_occupancy(int variant, bool bf16) {

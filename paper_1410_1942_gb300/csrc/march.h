@@ -9,9 +9,9 @@
 namespace pcg {
 
 // One kernel variant: 32 x tyt compute threads, each owning cx x cy cells, plus one TMA
-// producer warp when ws; tile width x height cells.
+// producer warp when ws, an ns-stage plane ring; tile width x height cells.
 struct MarchVariant {
-    int id, cx, cy, tyt, ws, width, height;
+    int id, cx, cy, tyt, ws, ns, width, height;
 };
 
 // Tensor maps of one solve, in this order: halo boxes (width+8) x (height+2) x 1 for z and both
@@ -91,7 +91,10 @@ enum { TR_A = 0, TR_BAR1, TR_ALPHA, TR_B, TR_BAR2, TR_BETA, TR_ITERS, TR_IMB, TR
 bool march_supported(const Dims& d);
 int march_variant_count();
 MarchVariant march_variant(int id);
-int march_find_variant(int cx, int cy, int tyt, int ws);  // -1 if there is none
+int march_find_variant(int cx, int cy, int tyt, int ws, int ns);  // -1 if there is none
+// poisson_opts.tile codes: 100000 NS (omitted for NS = 4) + 10000 WS + 1000 CX + 100 CY + T
+int march_variant_of_tile(int tile);  // -1 if there is none
+int march_tile_of(int variant);
 int march_occupancy(int variant, bool bf16);       // resident CTAs per SM (0 if unknown)
 
 // Builds a plan (device arrays allocated, or reused when large enough, copied on st,
