@@ -277,6 +277,9 @@ struct Executor {
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         const int nctas = std::max(1, march_occupancy(var, bf16)) * std::max(1, nsm);
         int rc = march_plan_build(&plan, ms.data(), nj, var, bf16, nctas, strat, st);
+        // a lockstep deal can spread one CTA over too many solves: fall back to the equal split
+        if (rc == -1 && strat != MARCH_SPLIT_EQUAL)
+            rc = march_plan_build(&plan, ms.data(), nj, var, bf16, nctas, MARCH_SPLIT_EQUAL, st);
         if (rc == -2) return POISSON_ENOMEM;
         if (rc != 0) return POISSON_EINVAL;
         return capture();

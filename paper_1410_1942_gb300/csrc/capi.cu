@@ -165,6 +165,7 @@ static int setup_march(poisson_t* H) {
     int var = -1, strategy = MARCH_SPLIT_EQUAL;
     if (forced > 0) {
         var = march_variant_of_tile(forced);
+        strategy = march_split_of_tile(forced);
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(tune_key(d, bf16));
@@ -770,9 +771,11 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
         snprintf(buf, (size_t)len,
                  "%s march tile=%d (%dx%d cells, %dx%d per thread%s, %d stages) persistent "
                  "ctas=%d segments=%d split=%s",
-                 prec, march_tile_of(H->plan.variant), v.width, v.height, v.cx, v.cy,
+                 prec, march_tile_of(H->plan.variant) + 1000000 * H->plan.strategy, v.width, v.height, v.cx, v.cy,
                  v.ws ? ", producer warp" : "", v.ns, H->plan.nctas, H->plan.nsegs,
-                 H->plan.strategy == MARCH_SPLIT_BALANCED ? "balanced" : "equal");
+                 H->plan.strategy == MARCH_SPLIT_BALANCED   ? "balanced"
+                 : H->plan.strategy == MARCH_SPLIT_LOCKSTEP ? "lockstep"
+                                                            : "equal");
     } else {
         snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d", prec, TX, TY, H->kc);
     }

@@ -358,7 +358,9 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         L.iter = 0;
         L.max_iter = sv.sc->max_iter;
         L.finished = 0;
-        L.owner = (sv.seg_begin >= sb && sv.seg_begin < sb + nseg) ? 1 : 0;
+        L.owner = 0;
+        for (int q = 0; q < nseg; ++q)
+            if (s_seg[q].slot == sv.seg_begin) L.owner = 1;
         s_member[tid] = (L.done == RUNNING);
         if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
     }
@@ -587,10 +589,10 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
             block_sum<2>(v, red);
             if (tid == 0) {
                 if (a_side)
-                    a.part_a[sb + ls] = v[0];
+                    a.part_a[s_seg[ls].slot] = v[0];
                 else {
-                    a.part_b[2 * (size_t)(sb + ls)] = v[0];
-                    a.part_b[2 * (size_t)(sb + ls) + 1] = v[1];
+                    a.part_b[2 * (size_t)s_seg[ls].slot] = v[0];
+                    a.part_b[2 * (size_t)s_seg[ls].slot + 1] = v[1];
                 }
             }
         }
@@ -790,7 +792,9 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
         L.iter = 0;
         L.max_iter = sv.sc->max_iter;
         L.finished = 0;
-        L.owner = (sv.seg_begin >= sb && sv.seg_begin < sb + nseg) ? 1 : 0;
+        L.owner = 0;
+        for (int q = 0; q < nseg; ++q)
+            if (s_seg[q].slot == sv.seg_begin) L.owner = 1;
         s_member[tid] = (L.done == RUNNING);
         if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
     }
@@ -990,10 +994,10 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
                 t1 = warp_sum(t1);
                 if (lane == 0) {
                     if (a_side)
-                        a.part_a[sb + ls] = t0;
+                        a.part_a[s_seg[ls].slot] = t0;
                     else {
-                        a.part_b[2 * (size_t)(sb + ls)] = t0;
-                        a.part_b[2 * (size_t)(sb + ls) + 1] = t1;
+                        a.part_b[2 * (size_t)s_seg[ls].slot] = t0;
+                        a.part_b[2 * (size_t)s_seg[ls].slot + 1] = t1;
                     }
                 }
             }
@@ -1217,10 +1221,14 @@ int march_find_variant(int cx, int cy, int tyt, int ws, int ns) {
 }
 
 int march_variant_of_tile(int tile) {
+    if (tile / 1000000 >= MARCH_SPLITS) return -1;
+    tile %= 1000000;
     const int ns = tile / 100000 ? tile / 100000 : 4;
     return march_find_variant((tile / 1000) % 10, (tile / 100) % 10, tile % 100,
                               (tile / 10000) % 10, ns);
 }
+
+int march_split_of_tile(int tile) { return tile / 1000000; }
 
 int march_tile_of(int variant) {
     const MarchVariant v = march_variant(variant);
@@ -1279,10 +1287,11 @@ static bool plan_buffer(void** buf, size_t* cap, size_t bytes) {
     return true;
 }
 
-// Splits the solves' tile columns into z-segments and packs them into at most nctas CTAs so
-// that the largest per-CTA cost (planes + a fixed cost per segment) is as small as possible.
-// Segments come out ordered by solve.  Fails (-1) if a CTA would hold more than MAXSEG
-// segments or a tensor map cannot be encoded.
+// Splits the solves' tile columns into z-segments and packs them into at most nctas CTAs:
+// EQUAL and BALANCED make the largest per-CTA cost (planes + a fixed cost per segment) as
+// small as possible, LOCKSTEP keeps neighbouring tiles on the same planes.  A CTA's segments
+// come out ordered by solve.  Fails (-1) if a CTA would hold more than MAXSEG segments or span
+// more than MAXSEG solves, or a tensor map cannot be encoded.
 int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int variant, bool bf16,
                      int nctas, int strategy, cudaStream_t st) {
     const MarchVariant v = march_variant(variant);
@@ -1298,7 +1307,53 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
     if (nctas > W) nctas = (int)W;
     std::vector<Seg> segs;
     std::vector<int> cta_seg;
-    {
+    long long ntiles = 0;
+    for (int s = 0; s < nsolves; ++s) ntiles += (long long)tiles_x[s] * tiles_y[s];
+    if (strategy == MARCH_SPLIT_LOCKSTEP) {
+        // Whole columns dealt round-robin when there are at least as many tile columns as CTAs
+        // (CTA c: tiles c, c + G, c + 2G, ... of the (solve, tile) list); otherwise every column
+        // is cut into q equal z-chunks and CTA c * ntiles + t takes chunk c of tile t.  Either
+        // way the CTAs holding neighbouring tiles march the same planes at the same time.
+        if (ntiles < 1) return -1;
+        std::vector<std::pair<int, int>> tl;  // (solve, tile)
+        for (int s = 0; s < nsolves; ++s)
+            for (int t = 0; t < tiles_x[s] * tiles_y[s]; ++t) tl.push_back({s, t});
+        auto seg_of = [&](long long t, int k0, int k1, int slot) {
+            Seg g{};
+            g.solve = tl[t].first;
+            g.x0 = (tl[t].second % tiles_x[g.solve]) * v.width;
+            g.y0 = (tl[t].second / tiles_x[g.solve]) * v.height;
+            g.k0 = k0;
+            g.k1 = k1;
+            g.slot = slot;
+            return g;
+        };
+        if (ntiles >= nctas) {
+            const long long m = (ntiles + nctas - 1) / nctas;
+            const int G = (int)((ntiles + m - 1) / m);
+            for (int c = 0; c < G; ++c) {
+                cta_seg.push_back((int)segs.size());
+                for (long long t = c; t < ntiles; t += G) {
+                    const int nz = solves[tl[t].first].d.nz;
+                    segs.push_back(seg_of(t, 0, nz, (int)t));  // slots in (solve, tile) order
+                }
+            }
+            nctas = G;
+        } else {
+            int q = (int)(nctas / ntiles);
+            for (int s = 0; s < nsolves; ++s) q = std::min(q, solves[s].d.nz);
+            for (int c = 0; c < q; ++c)
+                for (long long t = 0; t < ntiles; ++t) {
+                    const int nz = solves[tl[t].first].d.nz;
+                    cta_seg.push_back((int)segs.size());
+                    // slots in (solve, tile, chunk) order
+                    segs.push_back(seg_of(t, (int)((long long)c * nz / q),
+                                          (int)((long long)(c + 1) * nz / q), (int)(t * q + c)));
+                }
+            nctas = (int)cta_seg.size();
+        }
+        cta_seg.push_back((int)segs.size());
+    } else {
         // A CTA's cost is its planes plus SEG_COST per segment (the two halo planes of a
         // segment and its pipeline start; 0 for the plain equal-planes split).  The smallest
         // capacity T for which a greedy walk over the tile columns (in solve, tile order) fits
@@ -1333,6 +1388,7 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
                         g.y0 = (c.tile / tiles_x[c.solve]) * v.height;
                         g.k0 = k;
                         g.k1 = k + take;
+                        g.slot = (int)segs.size();
                         segs.push_back(g);
                     }
                     cost += SEG_COST + take;
@@ -1352,8 +1408,12 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
         cta_seg.push_back((int)segs.size());
     }
     std::vector<SolveDev> sd(nsolves);
-    for (int c = 0; c < nctas; ++c)
-        if (cta_seg[c + 1] - cta_seg[c] > MAXSEG) return -1;
+    for (int c = 0; c < nctas; ++c) {
+        const int b = cta_seg[c], e = cta_seg[c + 1];
+        if (e - b > MAXSEG) return -1;
+        // the kernel keeps one local record per solve from the CTA's first to its last
+        if (e > b && segs[e - 1].solve - segs[b].solve + 1 > MAXSEG) return -1;
+    }
     for (int s = 0; s < nsolves; ++s) {
         sd[s].d = solves[s].d;
         sd[s].x = solves[s].x;
@@ -1367,8 +1427,8 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
     }
     for (int q = 0; q < (int)segs.size(); ++q) {
         SolveDev& t = sd[segs[q].solve];
-        t.seg_begin = std::min(t.seg_begin, q);
-        t.seg_end = std::max(t.seg_end, q + 1);
+        t.seg_begin = std::min(t.seg_begin, segs[q].slot);
+        t.seg_end = std::max(t.seg_end, segs[q].slot + 1);
     }
     std::vector<CUtensorMap> maps(6 * (size_t)nsolves);
     for (int s = 0; s < nsolves; ++s) {

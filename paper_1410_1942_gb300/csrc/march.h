@@ -27,7 +27,7 @@ struct MarchSolve {
     Scalars* sc;
 };
 
-// Device-side copy: the segment range [seg_begin, seg_end) of the solve in the work list.
+// Device-side copy: the partial-sum slots [seg_begin, seg_end) of the solve.
 struct SolveDev {
     Dims d;
     int seg_begin, seg_end;
@@ -35,9 +35,10 @@ struct SolveDev {
     Scalars* sc;
 };
 
-// One tile column of one solve over planes [k0, k1).
+// One tile column of one solve over planes [k0, k1); its partial sums go to slot `slot` of the
+// partial arrays (slots are contiguous per solve, in solve order).
 struct Seg {
-    int solve, x0, y0, k0, k1, pad0, pad1, pad2;
+    int solve, x0, y0, k0, k1, slot, pad1, pad2;
 };
 
 // Control words of one persistent launch (set by the host before the launch).
@@ -50,7 +51,9 @@ struct MarchCtl {
 };
 
 // Work-split strategies of march_plan_build.
-enum { MARCH_SPLIT_EQUAL = 0, MARCH_SPLIT_BALANCED = 1, MARCH_SPLITS = 2 };
+// LOCKSTEP deals whole tile columns round-robin (CTA c: tiles c, c + G, ...) so that all CTAs
+// march the same planes at the same time (halo rows of neighbouring tiles stay in L2).
+enum { MARCH_SPLIT_EQUAL = 0, MARCH_SPLIT_BALANCED = 1, MARCH_SPLIT_LOCKSTEP = 2, MARCH_SPLITS = 3 };
 
 // A persistent launch: nctas CTAs, CTA c owns segments [cta_seg[c], cta_seg[c+1]).
 struct MarchPlan {
@@ -95,6 +98,7 @@ int march_find_variant(int cx, int cy, int tyt, int ws, int ns);  // -1 if there
 // poisson_opts.tile codes: 100000 NS (omitted for NS = 4) + 10000 WS + 1000 CX + 100 CY + T
 int march_variant_of_tile(int tile);  // -1 if there is none
 int march_tile_of(int variant);
+int march_split_of_tile(int tile);  // the 1000000s digit: the split strategy
 int march_occupancy(int variant, bool bf16);       // resident CTAs per SM (0 if unknown)
 
 // Builds a plan (device arrays allocated, or reused when large enough, copied on st,

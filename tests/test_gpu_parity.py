@@ -136,7 +136,7 @@ def test_solve_matches_oracle(name, prec, precond):
 
 
 @pytest.mark.parametrize("tile", [-1, 0, 1108, 2204, 2208, 12204, 12208, 302204, 302208,
-                                  312208, 602204, 612208])
+                                  312208, 602204, 612208, 1012204, 2002204, 2012208, 2302204])
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("shape", [(96, 48, 40), (40, 23, 19), (64, 16, 1), (8, 9, 33)])
 def test_kernel_variants_match_oracle(tile, prec, shape):
@@ -332,6 +332,27 @@ def test_batch_rejects_a_handle_twice():
         p = np.zeros(c.grid.shape)
         with pytest.raises(capi.PoissonError):
             capi.batch_submit([s, s], [c.s, c.s], [p, p.copy()], 1e-9)
+
+
+@pytest.mark.parametrize("tile", [2002204, 2012208])
+def test_lockstep_round_robin_split(tile):
+    """More tile columns than CTAs (1024 x 512 planes): the lockstep split deals whole columns
+    round-robin.  Checked by the oracle's FP64 residual (a property at any size) and against the
+    equal split's solution."""
+    c = inputs.flat_case(1024, 512, 6, seed=3, tol=1e-9)
+    op = oracle.operator(c.F)
+    b = oracle.rhs(c.s, c.grid.h)
+    sols = []
+    for t in (tile, tile % 1000000):
+        with solver(c, "fp32", tile=t) as s:
+            assert ("split=lockstep" in s.describe()) == (t == tile)
+            p = np.zeros(c.grid.shape)
+            rc, st = s.solve(c.s, p, c.tol)
+        assert rc == capi.OK
+        rel = oracle.rel_residual(op, b, p)
+        assert rel <= c.tol * (1 + 1e-6), rel
+        sols.append(p)
+    assert np.linalg.norm(sols[0] - sols[1]) <= 2e-6 * np.linalg.norm(sols[1])
 
 
 # ----------------------------------------------------------------------------- full size
