@@ -217,6 +217,7 @@ struct Executor {
             J.bx = H->bx; J.by = H->by; J.bz = H->bz; J.diag = H->diag;
             J.b64 = H->b64; J.x64 = H->x64;
             J.d32 = H->d32; J.r32 = H->r32; J.z32 = H->z32; J.pa32 = H->p32a;
+            J.sa32 = H->s32a; J.wa32 = H->w32a;
             J.eta32 = H->eta32; J.eta16 = H->eta16;
             part += 2 * (size_t)J.blocks;
             J.tol2 = 0.25;
@@ -266,7 +267,8 @@ struct Executor {
         for (int q = 0; q < nj; ++q) {
             poisson_t* H = table[q]->h;
             ms[q] = MarchSolve{H->d, H->d32, H->r32, H->z32, H->p32a, H->p32b,
-                               bf16 ? (const void*)H->eta16 : (const void*)H->eta32, d_sc + q};
+                               bf16 ? (const void*)H->eta16 : (const void*)H->eta32, d_sc + q,
+                               H->s32a, H->s32b, H->w32a, H->w32b};
             if (H->d.n > table[big]->h->d.n) big = q;
         }
         const poisson_t* HB = table[big]->h;

@@ -121,7 +121,8 @@ static int num_sms() {
 static MarchSolve march_solve_of(poisson_t* H) {
     const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
     return MarchSolve{H->d, H->d32, H->r32, H->z32, H->p32a, H->p32b,
-                      bf16 ? (const void*)H->eta16 : (const void*)H->eta32, H->sc};
+                      bf16 ? (const void*)H->eta16 : (const void*)H->eta32, H->sc,
+                      H->s32a, H->s32b, H->w32a, H->w32b};
 }
 
 static int build_plan(poisson_t* H, int var, int strategy) {
@@ -139,6 +140,11 @@ static int march_run(poisson_t* H, bool bf16, double tol2, int max_iter, Scalars
     const Dims d = H->d;
     cudaMemsetAsync(H->d32, 0, sizeof(float) * (size_t)d.n, st);
     cudaMemsetAsync(H->p32a, 0, sizeof(float) * (size_t)d.n, st);
+    if (march_variant(H->plan.variant).family == 1) {
+        // the start-up sweep reads s^ and w^ (times alpha = beta = 0): they must be finite
+        cudaMemsetAsync(H->s32a, 0, sizeof(float) * (size_t)d.n, st);
+        cudaMemsetAsync(H->w32a, 0, sizeof(float) * (size_t)d.n, st);
+    }
     if (bf16)
         launch_cg_init<float, CoefEta<__nv_bfloat16>>(d, H->kc, CoefEta<__nv_bfloat16>{H->eta16},
                                                       H->r32, H->z32, H->sc, H->partials, tol2, 0,
@@ -176,7 +182,7 @@ static int setup_march(poisson_t* H) {
     }
     if (var < 0 && forced <= 0) {
         // a constant-density model problem (rho = 1) with r = 1, TUNE_ITERS iterations per try
-        constexpr int TUNE_ITERS = 6;
+        constexpr int TUNE_ITERS = 16;
         const long long n = d.n;
         cudaStream_t st = H->st;
         if (bf16) launch_fill_bf16(n, H->eta16, 0.5f, st);
@@ -229,8 +235,8 @@ static int setup_march(poisson_t* H) {
 static void free_state(poisson_t* H) {
     void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->eta32, H->eta16, H->x64,
                     H->b64, H->r64, H->z64, H->p64a, H->p64b, H->d32, H->r32, H->z32,
-                    H->p32a, H->p32b, H->sc, H->partials, H->io_a, H->io_b, H->io_c,
-                    H->io_c32};
+                    H->p32a, H->p32b, H->s32a, H->s32b, H->w32a, H->w32b, H->sc,
+                    H->partials, H->io_a, H->io_b, H->io_c, H->io_c32};
     for (void* p : ptrs) dfree(p);
     if (H->sc_host) cudaFreeHost(H->sc_host);
     if (H->ctl_host) cudaFreeHost(H->ctl_host);
@@ -293,6 +299,7 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     } else {
         A(dalloc(&H->d32, N)); A(dalloc(&H->r32, N)); A(dalloc(&H->z32, N));
         A(dalloc(&H->p32a, N)); A(dalloc(&H->p32b, N));
+        A(dalloc(&H->s32a, N)); A(dalloc(&H->s32b, N)); A(dalloc(&H->w32a, N)); A(dalloc(&H->w32b, N));
     }
     A(dalloc(&H->sc, 1));
     A(dalloc(&H->partials, 2 * H->nblocks + 64));
@@ -769,10 +776,11 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
     if (H->march) {
         const MarchVariant v = march_variant(H->plan.variant);
         snprintf(buf, (size_t)len,
-                 "%s march tile=%d (%dx%d cells, %dx%d per thread%s, %d stages) persistent "
+                 "%s march tile=%d (%dx%d cells, %dx%d per thread%s, %d stages) persistent %s "
                  "ctas=%d segments=%d split=%s",
-                 prec, march_tile_of(H->plan.variant) + 1000000 * H->plan.strategy, v.width, v.height, v.cx, v.cy,
-                 v.ws ? ", producer warp" : "", v.ns, H->plan.nctas, H->plan.nsegs,
+                 prec, march_tile_of(H->plan.variant) + 1000000 * H->plan.strategy, v.width,
+                 v.height, v.cx, v.cy, v.ws ? ", producer warp" : "", v.ns,
+                 v.family == 1 ? "one-sweep" : "two-sweep", H->plan.nctas, H->plan.nsegs,
                  H->plan.strategy == MARCH_SPLIT_BALANCED   ? "balanced"
                  : H->plan.strategy == MARCH_SPLIT_LOCKSTEP ? "lockstep"
                                                             : "equal");

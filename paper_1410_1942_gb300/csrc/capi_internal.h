@@ -31,6 +31,8 @@ struct poisson_s {
     double *r64 = nullptr, *z64 = nullptr, *p64a = nullptr, *p64b = nullptr;
     // FP32 inner PCG vectors (d = correction)
     float *d32 = nullptr, *r32 = nullptr, *z32 = nullptr, *p32a = nullptr, *p32b = nullptr;
+    // the one-sweep kernels' s^ and w^ (both buffers); u is z32 / p32b, p is p32a
+    float *s32a = nullptr, *s32b = nullptr, *w32a = nullptr, *w32b = nullptr;
     // device scalars, reduction partials, pinned host mirror (2 slots), chunk events
     pcg::Scalars* sc = nullptr;
     double* partials = nullptr;

@@ -23,6 +23,7 @@ struct JobDev {
     double* x64;
     // FP32 inner vectors
     float *d32, *r32, *z32, *pa32;
+    float *sa32, *wa32;  // zeroed by the init (read, times zero, by the one-sweep kernels)
     const float* eta32;
     const __nv_bfloat16* eta16;
     Scalars* sc;       // this job's scalars (contiguous array of the batch)

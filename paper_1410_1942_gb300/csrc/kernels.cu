@@ -529,6 +529,8 @@ __device__ __forceinline__ void batch_init_body(const JobDev& J, const Dims& d, 
             const float rc = J.r32[c];
             const float zc = rc * rcp_approx(w.D);
             J.z32[c] = zc;
+            J.sa32[c] = 0.f;
+            J.wa32[c] = 0.f;
             rz += rc * zc;
             rr += rc * rc;
         }

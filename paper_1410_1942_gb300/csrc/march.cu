@@ -24,6 +24,7 @@
 #include "internal.cuh"
 #include "kernels.h"
 #include "march.h"
+#include "march_dev.cuh"
 #include "tma.cuh"
 
 #include <cudaTypedefs.h>
@@ -35,152 +36,6 @@
 #include <vector>
 
 namespace pcg {
-
-// Shared-memory stages (planes) in a kernel's ring: a template parameter of each kernel
-// (3, 4 or 6 in the variant table).
-
-__host__ __device__ constexpr int align128(int b) { return (b + 127) & ~127; }
-
-template <typename E>
-struct EtaX {
-    static constexpr int OFF = 16 / (int)sizeof(E);  // 16 bytes of halo in x
-};
-
-template <int CX, int CY, int TYT, typename E>
-struct Geo {
-    static constexpr int W = 32 * CX;               // tile width (cells)
-    static constexpr int HT = CY * TYT;             // tile height (cells)
-    static constexpr int VOFF = 4;                  // FP32 halo in x
-    static constexpr int VW = W + 2 * VOFF;
-    static constexpr int EOFF = EtaX<E>::OFF;
-    static constexpr int EW = W + 2 * EOFF;
-    static constexpr int H = HT + 2;
-    static constexpr int VB = VW * H * 4;
-    static constexpr int EB = EW * H * (int)sizeof(E);
-    static constexpr int CB = W * HT * 4;
-    // phase A stage: z | p_old | eta
-    static constexpr int A_Z = 0, A_P = align128(VB), A_E = A_P + align128(VB);
-    static constexpr int A_STAGE = A_E + align128(EB);
-    static constexpr int A_TX = 2 * VB + EB;
-    // phase B stage: p | eta | x | r
-    static constexpr int B_P = 0, B_E = align128(VB), B_X = B_E + align128(EB);
-    static constexpr int B_R = B_X + align128(CB);
-    static constexpr int B_STAGE = B_R + align128(CB);
-    static constexpr int B_TX_HALO = VB + EB;  // planes k0-1 and k1: p, eta only
-    static constexpr int B_TX = VB + EB + 2 * CB;
-    static constexpr int STAGE = A_STAGE > B_STAGE ? A_STAGE : B_STAGE;
-};
-
-// CX consecutive values of a shared-memory row (CX = 1 or 2), widened to float.
-template <int CX>
-__device__ __forceinline__ void ld_row(const float* p, float (&v)[CX]) {
-    if constexpr (CX == 2) {
-        const float2 t = *reinterpret_cast<const float2*>(p);
-        v[0] = t.x;
-        v[1] = t.y;
-    } else {
-        v[0] = *p;
-    }
-}
-template <int CX>
-__device__ __forceinline__ void ld_row(const __nv_bfloat16* p, float (&v)[CX]) {
-    if constexpr (CX == 2) {
-        const __nv_bfloat162 t = *reinterpret_cast<const __nv_bfloat162*>(p);
-        v[0] = __low2float(t);
-        v[1] = __high2float(t);
-    } else {
-        v[0] = __bfloat162float(*p);
-    }
-}
-__device__ __forceinline__ float ld1(const float* p) { return *p; }
-__device__ __forceinline__ float ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-
-template <int CX>
-__device__ __forceinline__ void st_row(float* g, const float (&v)[CX]) {
-    if constexpr (CX == 2)
-        *reinterpret_cast<float2*>(g) = make_float2(v[0], v[1]);
-    else
-        *g = v[0];
-}
-
-// The stencil of one plane for the CX x CY block of a thread.
-//   cen: centre values of plane k (registers); vxm/vxp/vym/vyp: the block's neighbour strips in
-//   plane k; vm/vp: centre values of planes k-1 and k+1; e*: the same for eta; wzl: face to
-//   plane k-1 (0 on the floor).  Returns q = A v and the diagonal per cell, and moves wzl to the
-//   face between k and k+1 (0 at the top layer, whose Dirichlet term goes into D).
-template <int CX, int CY>
-__device__ __forceinline__ void stencil(const Dims& d, int i0, int j0, int k,
-                                        const float (&cen)[CY][CX], const float (&vxm)[CY],
-                                        const float (&vxp)[CY], const float (&vym)[CX],
-                                        const float (&vyp)[CX], const float (&vm)[CY][CX],
-                                        const float (&vp)[CY][CX], const float (&ec)[CY][CX],
-                                        const float (&exm)[CY], const float (&exq)[CY],
-                                        const float (&eym)[CX], const float (&eyp)[CX],
-                                        const float (&ep)[CY][CX], float (&wzl)[CY][CX],
-                                        float (&q)[CY][CX], float (&D)[CY][CX]) {
-    const bool top = (k + 1 == d.nz);
-    // x faces of each row: fx[a][b] couples cells b-1 and b (b = 0: the -x neighbour)
-    float fx[CY][CX + 1];
-#pragma unroll
-    for (int a = 0; a < CY; ++a) {
-        fx[a][0] = (i0 > 0) ? rcp_approx(ec[a][0] + exm[a]) : 0.f;
-#pragma unroll
-        for (int b = 1; b < CX; ++b)
-            fx[a][b] = (i0 + b < d.nx) ? rcp_approx(ec[a][b - 1] + ec[a][b]) : 0.f;
-        fx[a][CX] = (i0 + CX < d.nx) ? rcp_approx(ec[a][CX - 1] + exq[a]) : 0.f;
-    }
-    float fy[CY + 1][CX];
-#pragma unroll
-    for (int b = 0; b < CX; ++b) {
-        fy[0][b] = (j0 > 0) ? rcp_approx(ec[0][b] + eym[b]) : 0.f;
-#pragma unroll
-        for (int a = 1; a < CY; ++a)
-            fy[a][b] = (j0 + a < d.ny) ? rcp_approx(ec[a - 1][b] + ec[a][b]) : 0.f;
-        fy[CY][b] = (j0 + CY < d.ny) ? rcp_approx(ec[CY - 1][b] + eyp[b]) : 0.f;
-    }
-#pragma unroll
-    for (int a = 0; a < CY; ++a)
-#pragma unroll
-        for (int b = 0; b < CX; ++b) {
-            const float wzt = top ? rcp_approx(ec[a][b]) : rcp_approx(ec[a][b] + ep[a][b]);
-            const float wzp = top ? 0.f : wzt;
-            const float wxm = fx[a][b], wxp = fx[a][b + 1];
-            const float wym = fy[a][b], wyp = fy[a + 1][b];
-            D[a][b] = wxm + wxp + wym + wyp + wzl[a][b] + wzt;
-            const float pxm = (b == 0) ? vxm[a] : cen[a][b > 0 ? b - 1 : 0];
-            const float pxp = (b == CX - 1) ? vxp[a] : cen[a][b < CX - 1 ? b + 1 : b];
-            const float pym = (a == 0) ? vym[b] : cen[a > 0 ? a - 1 : 0][b];
-            const float pyp = (a == CY - 1) ? vyp[b] : cen[a < CY - 1 ? a + 1 : a][b];
-            float s = wxm * pxm;
-            s += wxp * pxp;
-            s += wym * pym;
-            s += wyp * pyp;
-            s += wzl[a][b] * vm[a][b];
-            s += wzp * vp[a][b];
-            q[a][b] = D[a][b] * cen[a][b] - s;
-            wzl[a][b] = wzp;
-        }
-}
-
-// Loads the four halo strips around a thread's CX x CY block from one plane tile.
-template <int CX, int CY, typename T>
-__device__ __forceinline__ void load_halo(const T* t, int pitch, int r0, int c0, float (&xm)[CY],
-                                          float (&xp)[CY], float (&ym)[CX], float (&yp)[CX]) {
-#pragma unroll
-    for (int a = 0; a < CY; ++a) {
-        xm[a] = ld1(t + (r0 + a) * pitch + c0 - 1);
-        xp[a] = ld1(t + (r0 + a) * pitch + c0 + CX);
-    }
-    ld_row<CX>(t + (r0 - 1) * pitch + c0, ym);
-    ld_row<CX>(t + (r0 + CY) * pitch + c0, yp);
-}
-
-template <int CX, int CY, typename T>
-__device__ __forceinline__ void load_centre(const T* t, int pitch, int r0, int c0,
-                                            float (&cen)[CY][CX]) {
-#pragma unroll
-    for (int a = 0; a < CY; ++a) ld_row<CX>(t + (r0 + a) * pitch + c0, cen[a]);
-}
 
 // ------------------------------------------------------------------ persistent PCG kernel
 // One cooperative launch runs the whole FP32 inner PCG of one or many solves.  CTA c walks the
@@ -195,126 +50,6 @@ __device__ __forceinline__ void load_centre(const T* t, int pitch, int r0, int c
 // Barrier waits spin on a global counter with a deadline (BAR_NS); a wait that runs out sets
 // ctl->error, marks the CTA's solves TIMEDOUT, waits (bounded) for its TMA copies in flight
 // and leaves the loop.
-
-constexpr int MAXSEG = 16;                                           // segments per CTA
-constexpr unsigned long long BAR_NS = 1000ull * 1000ull * 1000ull;   // 1 s per barrier
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ bool grid_barrier(MarchCtl* ctl, unsigned target, int tid) {
-    __shared__ int s_ok;
-    // generic-proxy stores of this phase must be ordered before the next phase's TMA reads
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        atomicAdd(&ctl->bar, 1u);
-        int ok = 1;
-        unsigned long long t0 = 0;
-        while (ld_acquire(&ctl->bar) < target) {
-            if (*(volatile int*)&ctl->error) { ok = 0; break; }
-            const unsigned long long t = globaltimer();
-            if (!t0) t0 = t;
-            else if (t - t0 > BAR_NS) { ok = 0; atomicExch(&ctl->error, 1); break; }
-        }
-        __threadfence();
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-// Split-phase form of grid_barrier: arrive (after the CTA's stores), do independent work, wait.
-// With a trace, the last CTA to arrive stamps the time of its arrival.
-__device__ __forceinline__ void grid_arrive(MarchCtl* ctl, int tid, unsigned target = 0,
-                                            bool stamp = false) {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        const unsigned old = atomicAdd(&ctl->bar, 1u);
-        if (stamp && old + 1 == target) *(volatile unsigned long long*)&ctl->t_last = globaltimer();
-    }
-}
-
-__device__ __forceinline__ bool grid_wait(MarchCtl* ctl, unsigned target, int tid) {
-    __shared__ int s_ok2;
-    if (tid == 0) {
-        int ok = 1;
-        unsigned long long t0 = 0;
-        while (ld_acquire(&ctl->bar) < target) {
-            if (*(volatile int*)&ctl->error) { ok = 0; break; }
-            const unsigned long long t = globaltimer();
-            if (!t0) t0 = t;
-            else if (t - t0 > BAR_NS) { ok = 0; atomicExch(&ctl->error, 1); break; }
-        }
-        __threadfence();
-        asm volatile("fence.proxy.async.global;" ::: "memory");
-        s_ok2 = ok;
-    }
-    __syncthreads();
-    return s_ok2 != 0;
-}
-
-// Sum over segments [b, e) of part[seg * NV + q], in a fixed order (the result is the same in
-// every CTA); valid in all threads.
-template <int NV>
-__device__ __forceinline__ void range_sum(const double* part, int b, int e, double (&out)[NV],
-                                          double* red, int tid, int nthreads) {
-    double acc[NV];
-#pragma unroll
-    for (int q = 0; q < NV; ++q) acc[q] = 0.0;
-    for (int s = b + tid; s < e; s += nthreads)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) acc[q] += __ldcg(&part[(size_t)s * NV + q]);
-    block_sum<NV>(acc, red);
-    if (tid == 0)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) red[q] = acc[q];
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < NV; ++q) out[q] = red[q];
-    __syncthreads();
-}
-
-struct LocalSolve {
-    Dims d;
-    float *x, *r, *z, *pa, *pb;
-    Scalars* sc;
-    int seg_begin, seg_end;
-    double rz, alpha, beta, rr, stop2;
-    int done, iter, max_iter, finished, owner;
-};
-
-// Sum of part[seg * NV + q] over segments [b, e) by one warp, in a fixed order; the result is
-// exact-same in every CTA and valid in every lane.
-template <int NV>
-__device__ __forceinline__ void warp_range_sum(const double* part, int b, int e, int lane,
-                                               double (&out)[NV]) {
-    constexpr int U = 8;  // loads in flight per lane
-#pragma unroll
-    for (int q = 0; q < NV; ++q) out[q] = 0.0;
-    for (int s0 = b; s0 < e; s0 += 32 * U) {
-        double v[U][NV];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int s = s0 + 32 * u + lane;
-#pragma unroll
-            for (int q = 0; q < NV; ++q) v[u][q] = (s < e) ? __ldcg(&part[(size_t)s * NV + q]) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int q = 0; q < NV; ++q) out[q] += v[u][q];
-    }
-#pragma unroll
-    for (int q = 0; q < NV; ++q) out[q] = warp_sum(out[q]);
-}
 
 // Stream membership: the planes of a solve's segments are streamed in a phase iff s_member was
 // set for it when the phase's stream began (right after the preceding grid barrier, before that
@@ -386,7 +121,7 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         const Seg& sg = s_seg[seg];
         const int L = sg.k1 - sg.k0, kk = sg.k0 - 1 + off;
         unsigned char* dst = sm + st * G::STAGE;
-        const CUtensorMap* m = a.maps + 6 * sg.solve;
+        const CUtensorMap* m = a.maps + MAPS_PER_SOLVE * sg.solve;
         uint64_t* bar = &bars[st];
         if (st_a) {
             if (part == 0) mbar_arrive_expect_tx(bar, G::A_TX);
@@ -585,15 +320,14 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
                     }
             }
             // the segment's partial sums
-            double v[2] = {(double)acc0, (double)acc1};
-            block_sum<2>(v, red);
-            if (tid == 0) {
-                if (a_side)
-                    a.part_a[s_seg[ls].slot] = v[0];
-                else {
-                    a.part_b[2 * (size_t)s_seg[ls].slot] = v[0];
-                    a.part_b[2 * (size_t)s_seg[ls].slot + 1] = v[1];
-                }
+            if (a_side) {
+                const float v[1] = {acc0};
+                segment_partials<1>(v, a.part_a + s_seg[ls].slot, reinterpret_cast<ff*>(red), tid,
+                                    32 * TYT, 1);
+            } else {
+                const float v[2] = {acc0, acc1};
+                segment_partials<2>(v, a.part_b + 2 * (size_t)s_seg[ls].slot,
+                                    reinterpret_cast<ff*>(red), tid, 32 * TYT, 1);
             }
         }
         return true;
@@ -741,10 +475,6 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
 // warps wait on the "full" barriers, compute, and release each plane after its last use, so no
 // block-wide barrier is taken per plane.  A timed-out wait sets s_fail; from then on every wait
 // returns at once, so all warps still pass the same named barriers and leave together.
-template <int TYT>
-struct WsMinBlocks {
-    static constexpr int value = TYT >= 8 ? 2 : (TYT >= 4 ? 3 : 4);
-};
 
 template <int CX, int CY, int TYT, typename E, int NS>
 __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg_ws(PcgArgs a) {
@@ -811,7 +541,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
             const Seg& sg = s_seg[ls];
             if (!s_member[sg.solve - first]) continue;
             const int L = sg.k1 - sg.k0;
-            const CUtensorMap* m = a.maps + 6 * sg.solve;
+            const CUtensorMap* m = a.maps + MAPS_PER_SOLVE * sg.solve;
             for (int off = 0; off < L + 2; ++off) {
                 if (s_fail) return;
                 const int st = np % NS, kk = sg.k0 - 1 + off;
@@ -981,27 +711,15 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
                 if (k + 1 == sg.k1) release(qn);
             }
             // the segment's partial sums, over the consumer warps
-            double v0 = warp_sum((double)acc0), v1 = warp_sum((double)acc1);
-            if (lane == 0) {
-                red[2 * warp] = v0;
-                red[2 * warp + 1] = v1;
+            if (a_side) {
+                const float v[1] = {acc0};
+                segment_partials<1>(v, a.part_a + s_seg[ls].slot, reinterpret_cast<ff*>(red), tid,
+                                    NC, 1);
+            } else {
+                const float v[2] = {acc0, acc1};
+                segment_partials<2>(v, a.part_b + 2 * (size_t)s_seg[ls].slot,
+                                    reinterpret_cast<ff*>(red), tid, NC, 1);
             }
-            named_sync(1, NC);
-            if (warp == 0) {
-                double t0 = lane < TYT ? red[2 * lane] : 0.0;
-                double t1 = lane < TYT ? red[2 * lane + 1] : 0.0;
-                t0 = warp_sum(t0);
-                t1 = warp_sum(t1);
-                if (lane == 0) {
-                    if (a_side)
-                        a.part_a[s_seg[ls].slot] = t0;
-                    else {
-                        a.part_b[2 * (size_t)s_seg[ls].slot] = t0;
-                        a.part_b[2 * (size_t)s_seg[ls].slot + 1] = t1;
-                    }
-                }
-            }
-            named_sync(1, NC);
         }
     };
 
@@ -1034,7 +752,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[1];
-            range_sum<1>(a.part_a, s_sol[l].seg_begin, s_sol[l].seg_end, t, red, tid, NT);
+            range_sum<1>(a.part_a, s_sol[l].seg_begin, s_sol[l].seg_end, t, reinterpret_cast<ff*>(red),
+                         tid, NT);
             if (tid == 0) {
                 if (!(t[0] > 0.0) || !isfinite(t[0])) {
                     s_sol[l].done = BREAKDOWN;
@@ -1060,7 +779,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[2];
-            range_sum<2>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, red, tid, NT);
+            range_sum<2>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, reinterpret_cast<ff*>(red),
+                         tid, NT);
             if (tid == 0) {
                 LocalSolve& L = s_sol[l];
                 L.iter += 1;
@@ -1159,29 +879,36 @@ struct VariantOps {
     int cx, cy, tyt, ws, ns;
     int smem32, smem16;
     const void *k32, *k16;
+    int family;
 };
 
-template <int CX, int CY, int TYT, int WS, int NS>
+template <int CX, int CY, int TYT, int WS, int NS, int F>
 static VariantOps make_ops() {
-    if constexpr (WS)
+    if constexpr (F == 1) {
+        static_assert(WS == 1, "the one-sweep kernels have a producer warp");
+        const Cg1Kernel k = cg1_kernel(CX, CY, TYT, NS);
+        return VariantOps{CX, CY, TYT, 1, NS, k.smem32, k.smem16, k.k32, k.k16, 1};
+    } else if constexpr (WS)
         return VariantOps{CX, CY, TYT, 1, NS, NS * Geo<CX, CY, TYT, float>::STAGE,
                           NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
                           (const void*)k_pcg_ws<CX, CY, TYT, float, NS>,
-                          (const void*)k_pcg_ws<CX, CY, TYT, __nv_bfloat16, NS>};
+                          (const void*)k_pcg_ws<CX, CY, TYT, __nv_bfloat16, NS>, 0};
     else
         return VariantOps{CX, CY, TYT, 0, NS, NS * Geo<CX, CY, TYT, float>::STAGE,
                           NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
                           (const void*)k_pcg<CX, CY, TYT, float, NS>,
-                          (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16, NS>};
+                          (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16, NS>, 0};
 }
 
-// (CX, CY, TYT, warp-specialised, ring stages)
-#define MARCH_VARIANTS(X) X(1, 1, 8, 0, 4) X(2, 2, 4, 0, 4) X(2, 2, 8, 0, 4) X(2, 2, 4, 1, 4) \
-    X(2, 2, 8, 1, 4) X(2, 2, 4, 0, 3) X(2, 2, 8, 0, 3) X(2, 2, 8, 1, 3) X(2, 2, 4, 0, 6)        \
-    X(2, 2, 8, 1, 6)
+// (CX, CY, TYT, warp-specialised, ring stages, family); family 1 rows must be in CG1_CONFIGS
+#define MARCH_VARIANTS(X)                                                                       \
+    X(1, 1, 8, 0, 4, 0) X(2, 2, 4, 0, 4, 0) X(2, 2, 8, 0, 4, 0) X(2, 2, 4, 1, 4, 0)             \
+    X(2, 2, 8, 1, 4, 0) X(2, 2, 4, 0, 3, 0) X(2, 2, 8, 0, 3, 0) X(2, 2, 8, 1, 3, 0)             \
+    X(2, 2, 4, 0, 6, 0) X(2, 2, 8, 1, 6, 0) X(2, 2, 4, 1, 4, 1) X(2, 2, 4, 1, 3, 1)             \
+    X(2, 2, 8, 1, 3, 1)
 
 static const VariantOps* variants(int* count) {
-#define ROW(CX, CY, TYT, WS, NS) make_ops<CX, CY, TYT, WS, NS>(),
+#define ROW(CX, CY, TYT, WS, NS, F) make_ops<CX, CY, TYT, WS, NS, F>(),
     static const VariantOps table[] = {MARCH_VARIANTS(ROW)};
 #undef ROW
     static std::once_flag once;
@@ -1208,31 +935,34 @@ MarchVariant march_variant(int id) {
     int n;
     const VariantOps* t = variants(&n);
     const VariantOps& v = t[id < 0 || id >= n ? 0 : id];
-    return MarchVariant{id, v.cx, v.cy, v.tyt, v.ws, v.ns, 32 * v.cx, v.cy * v.tyt};
+    return MarchVariant{id, v.cx, v.cy, v.tyt, v.ws, v.ns, 32 * v.cx, v.cy * v.tyt, v.family};
 }
 
-int march_find_variant(int cx, int cy, int tyt, int ws, int ns) {
+int march_find_variant(int cx, int cy, int tyt, int ws, int ns, int family) {
     int n;
     const VariantOps* t = variants(&n);
     for (int q = 0; q < n; ++q)
-        if (t[q].cx == cx && t[q].cy == cy && t[q].tyt == tyt && t[q].ws == ws && t[q].ns == ns)
+        if (t[q].cx == cx && t[q].cy == cy && t[q].tyt == tyt && t[q].ws == ws && t[q].ns == ns &&
+            t[q].family == family && t[q].k32)
             return q;
     return -1;
 }
 
 int march_variant_of_tile(int tile) {
-    if (tile / 1000000 >= MARCH_SPLITS) return -1;
+    if (tile < 0 || tile / 10000000 > 1 || (tile / 1000000) % 10 >= MARCH_SPLITS) return -1;
+    const int family = tile / 10000000;
     tile %= 1000000;
     const int ns = tile / 100000 ? tile / 100000 : 4;
     return march_find_variant((tile / 1000) % 10, (tile / 100) % 10, tile % 100,
-                              (tile / 10000) % 10, ns);
+                              (tile / 10000) % 10, ns, family);
 }
 
-int march_split_of_tile(int tile) { return tile / 1000000; }
+int march_split_of_tile(int tile) { return (tile / 1000000) % 10; }
 
 int march_tile_of(int variant) {
     const MarchVariant v = march_variant(variant);
-    return (v.ns == 4 ? 0 : 100000 * v.ns) + 10000 * v.ws + 1000 * v.cx + 100 * v.cy + v.tyt;
+    return 10000000 * v.family + (v.ns == 4 ? 0 : 100000 * v.ns) + 10000 * v.ws + 1000 * v.cx +
+           100 * v.cy + v.tyt;
 }
 
 int march_occupancy(int variant, bool bf16) {
@@ -1248,13 +978,28 @@ int march_occupancy(int variant, bool bf16) {
 }
 
 // ------------------------------------------------------------------ plans
-bool march_encode_solve(CUtensorMap (&m)[6], const MarchSolve& s, int variant, bool bf16) {
+bool march_encode_solve(CUtensorMap (&m)[MAPS_PER_SOLVE], const MarchSolve& s, int variant,
+                        bool bf16) {
     const MarchVariant v = march_variant(variant);
     const int eoff = bf16 ? 8 : 4;
     const CUtensorMapDataType f32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const CUtensorMapDataType edt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : f32;
     const Dims& d = s.d;
     bool ok = true;
+    if (v.family == 1) {
+        const int bw = v.width + 8, bh = v.height + 2;
+        ok = ok && s.sa && s.sb && s.wa && s.wb;
+        ok = ok && encode3d(&m[MAP1_U0], s.z, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP1_U1], s.pb, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP1_S0], s.sa, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP1_S1], s.sb, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP1_W0], s.wa, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP1_W1], s.wb, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP1_ETA], s.eta, edt, bf16 ? 2 : 4, d, v.width + 2 * eoff, bh);
+        ok = ok && encode3d(&m[MAP1_X], s.x, f32, 4, d, v.width, v.height);
+        ok = ok && encode3d(&m[MAP1_P], s.pa, f32, 4, d, v.width, v.height);
+        return ok;
+    }
     ok = ok && encode3d(&m[MAP_Z], s.z, f32, 4, d, v.width + 8, v.height + 2);
     ok = ok && encode3d(&m[MAP_PA], s.pa, f32, 4, d, v.width + 8, v.height + 2);
     ok = ok && encode3d(&m[MAP_PB], s.pb, f32, 4, d, v.width + 8, v.height + 2);
@@ -1422,6 +1167,10 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
         sd[s].pa = solves[s].pa;
         sd[s].pb = solves[s].pb;
         sd[s].sc = solves[s].sc;
+        sd[s].sa = solves[s].sa;
+        sd[s].sb = solves[s].sb;
+        sd[s].wa = solves[s].wa;
+        sd[s].wb = solves[s].wb;
         sd[s].seg_begin = (int)segs.size();
         sd[s].seg_end = 0;
     }
@@ -1430,11 +1179,11 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
         t.seg_begin = std::min(t.seg_begin, segs[q].slot);
         t.seg_end = std::max(t.seg_end, segs[q].slot + 1);
     }
-    std::vector<CUtensorMap> maps(6 * (size_t)nsolves);
+    std::vector<CUtensorMap> maps(MAPS_PER_SOLVE * (size_t)nsolves);
     for (int s = 0; s < nsolves; ++s) {
-        CUtensorMap m[6];
+        CUtensorMap m[MAPS_PER_SOLVE] = {};
         if (!march_encode_solve(m, solves[s], variant, bf16)) return -1;
-        for (int q = 0; q < 6; ++q) maps[6 * (size_t)s + q] = m[q];
+        for (int q = 0; q < MAPS_PER_SOLVE; ++q) maps[MAPS_PER_SOLVE * (size_t)s + q] = m[q];
     }
     p->variant = variant;
     p->strategy = strategy;
@@ -1450,8 +1199,8 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
               up((void**)&p->segs, &p->cap_segs, segs.data(), sizeof(Seg) * segs.size()) &&
               up((void**)&p->cta_seg, &p->cap_cta, cta_seg.data(), sizeof(int) * cta_seg.size()) &&
               up((void**)&p->maps, &p->cap_maps, maps.data(), sizeof(CUtensorMap) * maps.size());
-    ok = ok && plan_buffer((void**)&p->part_a, &p->cap_pa, sizeof(double) * segs.size()) &&
-         plan_buffer((void**)&p->part_b, &p->cap_pb, sizeof(double) * 2 * segs.size()) &&
+    ok = ok && plan_buffer((void**)&p->part_a, &p->cap_pa, sizeof(float2) * segs.size()) &&
+         plan_buffer((void**)&p->part_b, &p->cap_pb, sizeof(float2) * 3 * segs.size()) &&
          plan_buffer((void**)&p->ctl, &p->cap_ctl, sizeof(MarchCtl));
     if (ok && getenv("POISSON_TRACE") && !p->trace) {
         if (cudaMalloc((void**)&p->trace, sizeof(unsigned long long) * TRACE_PARTS) != cudaSuccess ||

@@ -9,15 +9,22 @@
 namespace pcg {
 
 // One kernel variant: 32 x tyt compute threads, each owning cx x cy cells, plus one TMA
-// producer warp when ws, an ns-stage plane ring; tile width x height cells.
+// producer warp when ws, an ns-stage plane ring; tile width x height cells.  family 0: two
+// sweeps (and two grid barriers) per CG iteration; family 1: one sweep per iteration (the
+// Chronopoulos-Gear recurrences, march1.cu).
 struct MarchVariant {
-    int id, cx, cy, tyt, ws, ns, width, height;
+    int id, cx, cy, tyt, ws, ns, width, height, family;
 };
 
 // Tensor maps of one solve, in this order: halo boxes (width+8) x (height+2) x 1 for z and both
 // p buffers, (width+8, or +16 for BF16) x (height+2) for eta, centre boxes width x height x 1
 // for x and r.
 enum { MAP_Z = 0, MAP_PA = 1, MAP_PB = 2, MAP_ETA = 3, MAP_X = 4, MAP_R = 5 };
+// Family 1: halo boxes for both buffers of u (z, pb), s-hat (sa, sb) and w-hat (wa, wb), eta as
+// above, centre boxes for x and p (pa).
+enum { MAP1_U0 = 0, MAP1_U1 = 1, MAP1_S0 = 2, MAP1_S1 = 3, MAP1_W0 = 4, MAP1_W1 = 5,
+       MAP1_ETA = 6, MAP1_X = 7, MAP1_P = 8 };
+constexpr int MAPS_PER_SOLVE = 9;
 
 // One solve of a plan as the host describes it.
 struct MarchSolve {
@@ -25,6 +32,7 @@ struct MarchSolve {
     float *x, *r, *z, *pa, *pb;
     const void* eta;  // float or bf16, rho/2 per cell
     Scalars* sc;
+    float *sa, *sb, *wa, *wb;  // family 1 only
 };
 
 // Device-side copy: the partial-sum slots [seg_begin, seg_end) of the solve.
@@ -33,6 +41,7 @@ struct SolveDev {
     int seg_begin, seg_end;
     float *x, *r, *z, *pa, *pb;
     Scalars* sc;
+    float *sa, *sb, *wa, *wb;
 };
 
 // One tile column of one solve over planes [k0, k1); its partial sums go to slot `slot` of the
@@ -65,8 +74,9 @@ struct MarchPlan {
     Seg* segs = nullptr;
     int* cta_seg = nullptr;
     CUtensorMap* maps = nullptr;
-    double* part_a = nullptr;  // per segment: p.Ap
-    double* part_b = nullptr;  // per segment: r.z, r.r
+    // per-segment partial sums as float-float pairs (hi, lo)
+    float2* part_a = nullptr;  // per segment: p.Ap
+    float2* part_b = nullptr;  // per segment: r.z, r.r (family 1: gamma, delta, r.r)
     MarchCtl* ctl = nullptr;
     unsigned long long* trace = nullptr;  // TRACE_PARTS counters when tracing is on
     // allocated bytes of the buffers above (a rebuild reuses them when they suffice)
@@ -80,8 +90,8 @@ struct PcgArgs {
     const Seg* segs;
     const int* cta_seg;
     const CUtensorMap* maps;
-    double* part_a;
-    double* part_b;
+    float2* part_a;
+    float2* part_b;
     MarchCtl* ctl;
     int nctas;
     unsigned long long* trace;  // optional: CTA 0 adds its per-part times (ns), TRACE_PARTS slots
@@ -94,8 +104,9 @@ enum { TR_A = 0, TR_BAR1, TR_ALPHA, TR_B, TR_BAR2, TR_BETA, TR_ITERS, TR_IMB, TR
 bool march_supported(const Dims& d);
 int march_variant_count();
 MarchVariant march_variant(int id);
-int march_find_variant(int cx, int cy, int tyt, int ws, int ns);  // -1 if there is none
-// poisson_opts.tile codes: 100000 NS (omitted for NS = 4) + 10000 WS + 1000 CX + 100 CY + T
+int march_find_variant(int cx, int cy, int tyt, int ws, int ns, int family = 0);  // -1: none
+// poisson_opts.tile codes: 10000000 family + 1000000 split + 100000 NS (omitted for NS = 4) +
+// 10000 WS + 1000 CX + 100 CY + T
 int march_variant_of_tile(int tile);  // -1 if there is none
 int march_tile_of(int variant);
 int march_split_of_tile(int tile);  // the 1000000s digit: the split strategy

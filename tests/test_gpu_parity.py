@@ -136,7 +136,8 @@ def test_solve_matches_oracle(name, prec, precond):
 
 
 @pytest.mark.parametrize("tile", [-1, 0, 1108, 2204, 2208, 12204, 12208, 302204, 302208,
-                                  312208, 602204, 612208, 1012204, 2002204, 2012208, 2302204])
+                                  312208, 602204, 612208, 1012204, 2002204, 2012208, 2302204,
+                                  10012204, 12012204, 10312204, 10312208, 12312208])
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("shape", [(96, 48, 40), (40, 23, 19), (64, 16, 1), (8, 9, 33)])
 def test_kernel_variants_match_oracle(tile, prec, shape):
@@ -264,13 +265,16 @@ def _oracle_ref(c):
     return op, b, oracle.pcg(op, b, tol=REF_TOL, precond="ssor").x
 
 
-def test_batch_of_uneven_solves_matches_oracle():
+@pytest.mark.parametrize("tile", [0, 2012204, 10012204, 12012204])
+def test_batch_of_uneven_solves_matches_oracle(tile):
     """A batch of solves of uneven size, FP32 and BF16 coefficients, plus handles that run one
-    by one (FP64, SSOR): every result meets both acceptance criteria."""
+    by one (FP64, SSOR): every result meets both acceptance criteria, with the persistent
+    kernel of either family and split."""
     cases = inputs.batch_cases(12, seed=3, hi=(96, 64, 48))
     precs = ["fp32"] * 8 + ["bf16"] * 2 + ["fp64", "fp32"]
     pcs = ["jacobi"] * 11 + ["rbssor"]
-    solvers = [solver(c, pr, precond=pc) for c, pr, pc in zip(cases, precs, pcs)]
+    solvers = [solver(c, pr, precond=pc, tile=tile if pr != "fp64" else 0)
+               for c, pr, pc in zip(cases, precs, pcs)]
     ps = [np.zeros(c.grid.shape) for c in cases]
     tickets = capi.batch_submit(solvers, [c.s for c in cases], ps, 1e-9)
     res = _poll_all(tickets)
@@ -334,7 +338,7 @@ def test_batch_rejects_a_handle_twice():
             capi.batch_submit([s, s], [c.s, c.s], [p, p.copy()], 1e-9)
 
 
-@pytest.mark.parametrize("tile", [2002204, 2012208])
+@pytest.mark.parametrize("tile", [2002204, 2012208, 12012204])
 def test_lockstep_round_robin_split(tile):
     """More tile columns than CTAs (1024 x 512 planes): the lockstep split deals whole columns
     round-robin.  Checked by the oracle's FP64 residual (a property at any size) and against the
@@ -353,6 +357,23 @@ def test_lockstep_round_robin_split(tile):
         assert rel <= c.tol * (1 + 1e-6), rel
         sols.append(p)
     assert np.linalg.norm(sols[0] - sols[1]) <= 2e-6 * np.linalg.norm(sols[1])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_one_sweep_kernel_takes_the_iterations_of_standard_pcg(prec):
+    """The one-sweep kernels run the Chronopoulos-Gear recurrences, which have the iterates of
+    standard PCG: the inner iteration count stays within a few percent of the two-sweep
+    kernel's."""
+    c, op, b, xref = case("strut")
+    its = {}
+    for t in (12204, 10012204):
+        with solver(c, prec, tile=t) as s:
+            p = np.zeros(c.grid.shape)
+            rc, st = s.solve(c.s, p, c.tol)
+        assert rc == capi.OK
+        _check_solution(c, op, b, xref, p, st, c.tol)
+        its[t] = st["inner_iters"]
+    assert abs(its[10012204] - its[12204]) <= 0.1 * its[12204] + 5, its
 
 
 # ----------------------------------------------------------------------------- full size
