@@ -90,18 +90,18 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, precision):
-    """DRAM bytes per launch for `kernel` from the committed ncu summary, if it was taken on the
-    current kernel sources; else None."""
+def ncu_traffic(kernel, precision, workload):
+    """DRAM bytes per cell-iteration of `kernel` on `workload` from the committed ncu summary, if
+    it was taken on the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    e = d.get("%s/%s" % (precision, kernel))
+    e = d.get("%s/%s/%s" % (precision, kernel, workload))
     if not e or e.get("source_hash") != source_hash():
         return None
-    return e.get("bytes_per_launch_full")
+    return e.get("dram_bytes_per_cell_iter")
 
 
 class Clocks:
@@ -419,7 +419,12 @@ def main():
         alg_bytes = bpc[dom] * g.n
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = ncu_traffic(dom, args.precision)
+    wl_key = "%s%dx%dx%d" % (args.case, g.nx, g.ny, g.nz)
+    bpci = ncu_traffic(dom, args.precision, wl_key)
+    # DRAM bytes per launch, like alg_bytes: the measured bytes per cell-iteration times the
+    # cell-iterations of an average launch
+    traffic = (bpci * g.n * iters / prof[dom]["launches"]
+               if bpci is not None and dom == "pcg_persistent" else None)
     hbm_alg = value * (bpc["cg_phase_a"] + bpc["cg_phase_b"])  # GB/s of CG-pass algorithmic traffic
 
     # end to end through the C ABI with pinned host arrays
