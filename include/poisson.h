@@ -69,14 +69,16 @@ typedef struct {
                           (default 1e-4; ignored by POISSON_FP64)                                  */
     int tile;          /* FP32 inner-solve kernels.  0 = TMA plane-marching kernels, variant and
                           z-chunk autotuned per shape (when nx % 8 == 0, else the column
-                          kernels); -1 = column kernels (plain loads); 1000000 P + 100000 S +
-                          10000 WS + 1000 CX + 100 CY + T = persistent marching kernel with T
-                          rows of 32 threads, each owning CX x CY cells (tile 32 CX x CY T), a
-                          TMA producer warp when WS = 1 and an S-stage plane ring (S omitted =
-                          4): 1108, 2204, 2208, 12204, 12208, 302204, 302208, 312208, 602204,
-                          612208; P = split of the tile columns over the CTAs: 0 equal planes
-                          per CTA, 1 balanced (segment start cost counted), 2 lockstep
-                          (neighbouring tiles on the same planes) (default 0)                   */
+                          kernels); -1 = column kernels (plain loads); 10000000 F + 1000000 P +
+                          100000 S + 10000 WS + 1000 CX + 100 CY + T = persistent marching
+                          kernel with T rows of 32 threads, each owning CX x CY cells (tile
+                          32 CX x CY T), a TMA producer warp when WS = 1 and an S-stage plane
+                          ring (S omitted = 4).  F = 0, two sweeps per CG iteration: 1108, 2204,
+                          2208, 12204, 12208, 302204, 302208, 312208, 602204, 612208; F = 1, one
+                          sweep per iteration (Chronopoulos-Gear recurrences): 12204, 312204,
+                          312208 (plus 10000000).  P = split of the tile columns over the CTAs:
+                          0 equal planes per CTA, 1 balanced (segment start cost counted), 2
+                          lockstep (neighbouring tiles on the same planes) (default 0)          */
     void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream                 */
 } poisson_opts;
 

@@ -26,7 +26,7 @@ import numpy as np
 from . import capi, inputs
 
 # device bytes per cell of a handle (capi.cu allocations) plus the request's own F, s, p arrays
-HANDLE_BYTES_PER_CELL = {"fp32": 32 + 16 + 6 + 20, "bf16": 32 + 16 + 6 + 20, "fp64": 32 + 16 + 6 + 8 + 32}
+HANDLE_BYTES_PER_CELL = {"fp32": 32 + 16 + 6 + 36, "bf16": 32 + 16 + 6 + 36, "fp64": 32 + 16 + 6 + 8 + 32}
 REQUEST_BYTES_PER_CELL = 3 * 8
 
 
