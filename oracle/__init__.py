@@ -76,6 +76,10 @@ def _load():
         lib.oracle_pcg.argtypes = [i, i, i, P, P, P, P, P, P, d, i, d, i,
                                    ctypes.POINTER(ctypes.c_int), P, P]
         lib.oracle_pcg.restype = i
+        lib.oracle_divergence.argtypes = [i, i, i, d, d, P, P, P, P]
+        lib.oracle_divergence.restype = None
+        lib.oracle_project.argtypes = [i, i, i, d, d, P, d, d, P, P, P, P, P, P, P]
+        lib.oracle_project.restype = None
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = i
         lib.oracle_set_threads.argtypes = [i]
@@ -244,6 +248,38 @@ def pcg_single_reduction(op: Operator, b, tol=1e-12, max_iters=100000):
         gamma = g_new
     st = OK if (tol <= 0 or rr <= stop2) else ENOTCONV
     return PCGResult(x, it, float(np.sqrt(rr / rr0)), st)
+
+
+def _faces_shapes(nx, ny, nz):
+    return (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)
+
+
+def divergence(u, v, w, h, dt):
+    """``s = div_h(u) / dt`` at cell centres from MAC face velocities ``u`` ``(nz, ny, nx+1)``,
+    ``v`` ``(nz, ny+1, nx)``, ``w`` ``(nz+1, ny, nx)`` (w's last plane is the top boundary):
+    the flux difference of each cell divided by ``h dt`` (Numerical Time Integration: the
+    pressure equation's source)."""
+    u, v, w = _f64(u), _f64(v), _f64(w)
+    nz, ny, nx1 = u.shape
+    nx = nx1 - 1
+    assert (v.shape, w.shape) == _faces_shapes(nx, ny, nz)[1:]
+    s = np.empty((nz, ny, nx))
+    _load().oracle_divergence(nx, ny, nz, float(h), float(dt), _ptr(u), _ptr(v), _ptr(w), _ptr(s))
+    return s
+
+
+def project(op: Operator, F, u, v, w, p, h, dt, rho_air=1.0, rho_water=1000.0):
+    """The velocity correction ``u - dt beta_f grad_h p`` on every face (new arrays): interior
+    faces use the operator's face coefficients and ``(p_n - p_c)/h``; the top face, where
+    ``p = 0``, uses ``1/rho_c`` and ``(0 - p_c)/(h/2)``; wall faces are unchanged.  Then
+    ``divergence(u_new) = (A p - b)/h^2`` for ``b = rhs(divergence(u), h)``."""
+    u, v, w = _f64(u).copy(), _f64(v).copy(), _f64(w).copy()
+    p, F = _f64(p).reshape(op.shape), _f64(F).reshape(op.shape)
+    assert (u.shape, v.shape, w.shape) == _faces_shapes(op.nx, op.ny, op.nz)
+    _load().oracle_project(op.nx, op.ny, op.nz, float(h), float(dt), _ptr(F), float(rho_air),
+                           float(rho_water), _ptr(op.bx), _ptr(op.by), _ptr(op.bz), _ptr(p),
+                           _ptr(u), _ptr(v), _ptr(w))
+    return u, v, w
 
 
 def rhs(s, h):

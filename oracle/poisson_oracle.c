@@ -297,3 +297,63 @@ done:
     free(r); free(z); free(p); free(q);
     return status;
 }
+
+/*
+ * The projection around the solve (Numerical Time Integration: each stage forms a provisional
+ * velocity u*, solves the pressure Poisson equation whose source is div(u*)/dt, and corrects the
+ * velocity by the pressure gradient divided by the density).  Velocities live on the faces of the
+ * cells (MAC grid), x fastest:
+ *   u: (nx+1) x ny x nz, u[i + (nx+1)(j + ny k)] on the face between cells i-1 and i
+ *      (i = 0 and i = nx are the walls x = 0, x = Lx);
+ *   v: nx x (ny+1) x nz, likewise in y;  w: nx x ny x (nz+1), w at k = nz on the top boundary.
+ *
+ * Divergence:  s_c = ((u_{i+1} - u_i) + (v_{j+1} - v_j) + (w_{k+1} - w_k)) / (h dt).
+ *
+ * Correction:  u_f <- u_f - dt (beta_f ((p_n - p_c) / h)) on every interior face, with the face
+ * coefficient beta_f = 2/(rho_c + rho_n) of the operator (bx, by, bz); on the top face, where
+ * p = 0, the gradient is (0 - p_c)/(h/2) and the coefficient 1/rho_c, written as
+ * (2/rho_c) ((0 - p_c)/h); wall faces keep their value (beta = 0 there).  With these faces
+ * div_h(u_new)/dt = div_h(u*)/dt - L p, i.e. divergence(u_new) = (A p - b) / h^2 for b = -h^2 s.
+ */
+void oracle_divergence(int nx, int ny, int nz, double h, double dt, const double* u,
+                       const double* v, const double* w, double* s) {
+    const double hd = h * dt;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const idx_t fu = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                const idx_t fv = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
+                const idx_t fw = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)ny * k);
+                const double du = u[fu + 1] - u[fu];
+                const double dv = v[fv + nx] - v[fv];
+                const double dw = w[fw + (idx_t)nx * ny] - w[fw];
+                s[fw] = ((du + dv) + dw) / hd;
+            }
+}
+
+void oracle_project(int nx, int ny, int nz, double h, double dt, const double* F, double rho_air,
+                    double rho_water, const double* bx, const double* by, const double* bz,
+                    const double* p, double* u, double* v, double* w) {
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const idx_t c = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)ny * k);
+                const idx_t sxy = (idx_t)nx * ny;
+                if (i > 0) {
+                    const idx_t f = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                    u[f] = u[f] - dt * (bx[c] * ((p[c] - p[c - 1]) / h));
+                }
+                if (j > 0) {
+                    const idx_t f = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
+                    v[f] = v[f] - dt * (by[c] * ((p[c] - p[c - nx]) / h));
+                }
+                if (k > 0) w[c] = w[c] - dt * (bz[c] * ((p[c] - p[c - sxy]) / h));
+                if (k == nz - 1) {
+                    const double rho = rho_air + F[c] * (rho_water - rho_air);
+                    const idx_t f = c + sxy;
+                    w[f] = w[f] - dt * ((2.0 / rho) * ((0.0 - p[c]) / h));
+                }
+            }
+}

@@ -345,6 +345,74 @@ def test_warm_start_from_solution_takes_no_iterations():
     assert again.iters == 0
 
 
+# ------------------------------------------------------------------------------- projection
+def _faces(shape, seed):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((nz, ny, nx + 1)), rng.standard_normal((nz, ny + 1, nx)),
+            rng.standard_normal((nz + 1, ny, nx)))
+
+
+@pytest.mark.parametrize("shape", [(5, 6, 7), (1, 4, 9), (6, 1, 5), (3, 5, 1)])
+def test_projection_leaves_the_residual_as_divergence(shape):
+    """u_new = u* - dt beta grad p has div_h(u_new)/dt = s - L p, i.e. divergence(u_new) =
+    (A p - b)/h^2 with b = -h^2 div(u*)/dt, for ANY p: the projection's faces, gradients and top
+    boundary are those of the operator (a wrong face, sign or top factor breaks it)."""
+    h, dt = 1.0 / 8, 2e-3
+    F = _rand_F(shape, 91)
+    op = oracle.operator(F, RHO_A, RHO_W)
+    u, v, w = _faces(shape, 92)
+    p = np.random.default_rng(93).standard_normal(shape)
+    b = oracle.rhs(oracle.divergence(u, v, w, h, dt), h)
+    un, vn, wn = oracle.project(op, F, u, v, w, p, h, dt, RHO_A, RHO_W)
+    r, _ = oracle.residual(op, b, p)
+    div = oracle.divergence(un, vn, wn, h, dt)
+    scale = (np.abs(b) + np.abs(oracle.apply(op, p))).max() / h ** 2
+    assert np.abs(div + r / h ** 2).max() <= 1e-13 * scale
+    # wall faces are untouched, the others move
+    assert np.array_equal(un[:, :, 0], u[:, :, 0]) and np.array_equal(un[:, :, -1], u[:, :, -1])
+    assert np.array_equal(vn[:, 0, :], v[:, 0, :]) and np.array_equal(wn[0], w[0])
+    assert not np.array_equal(wn[-1], w[-1])
+
+
+def test_projection_removes_an_eigenmode_gradient():
+    """Constant density: u* = dt grad_h v for a closed-form eigenvector v of A (Neumann walls,
+    p = 0 on the top face) has divergence/dt = L v = -(lambda/h^2) v, the solve of A p = -h^2 s
+    returns p = v, and the projection leaves zero velocity."""
+    nx, ny, nz, h, dt = 6, 5, 4, 0.25, 1e-3
+    v, lam = _cosine_mode(nx, ny, nz, 2, 1, 1)
+    # gradient of v on the faces: centred differences, p = 0 on the top face (half-cell distance)
+    gu = np.zeros((nz, ny, nx + 1)); gu[:, :, 1:nx] = np.diff(v, axis=2) / h
+    gv = np.zeros((nz, ny + 1, nx)); gv[:, 1:ny, :] = np.diff(v, axis=1) / h
+    gw = np.zeros((nz + 1, ny, nx)); gw[1:nz] = np.diff(v, axis=0) / h
+    gw[nz] = (0.0 - v[-1]) / (h / 2)
+    u0, v0, w0 = dt * gu, dt * gv, dt * gw
+    s = oracle.divergence(u0, v0, w0, h, dt)
+    assert np.abs(s + lam / h ** 2 * v).max() <= 1e-12 * lam / h ** 2
+    F = np.zeros((nz, ny, nx))  # rho = rho_air = 1 everywhere
+    op = oracle.operator(F, RHO_A, RHO_W)
+    res = oracle.pcg(op, oracle.rhs(s, h), tol=1e-14)
+    assert np.abs(res.x - v).max() <= 1e-11
+    un, vn, wn = oracle.project(op, F, u0, v0, w0, res.x, h, dt, RHO_A, RHO_W)
+    top = max(np.abs(u0).max(), np.abs(v0).max(), np.abs(w0).max())
+    assert max(np.abs(un).max(), np.abs(vn).max(), np.abs(wn).max()) <= 1e-10 * top
+
+
+def test_projection_after_a_solve_is_divergence_free_to_the_tolerance():
+    c = inputs.flat_case(16, 12, 10, seed=5)
+    g = c.grid
+    modes = inputs.fourier_modes(np.random.default_rng(5))
+    u, v, w = inputs.face_velocity(g, modes)
+    op = oracle.operator(c.F)
+    b = oracle.rhs(oracle.divergence(u, v, w, g.h, inputs.DT), g.h)
+    res = oracle.pcg(op, b, tol=1e-12, precond="ssor")
+    un, vn, wn = oracle.project(op, c.F, u, v, w, res.x, g.h, inputs.DT)
+    div = oracle.divergence(un, vn, wn, g.h, inputs.DT)
+    # |div(u_new)| h^2 is the residual: <= 1e-12 |b| in the 2-norm
+    assert np.linalg.norm(div) * g.h ** 2 <= 1.01e-12 * np.linalg.norm(b)
+    assert np.linalg.norm(div) < 1e-9 * np.linalg.norm(oracle.divergence(u, v, w, g.h, inputs.DT))
+
+
 # ------------------------------------------------------------------------------- inputs
 def test_source_is_discrete_divergence_of_face_velocity():
     g = inputs.Grid(12, 10, 8, 1.0 / 8)
