@@ -177,6 +177,32 @@ int poisson_profile(poisson_t* h, int enable);
 /* Copy out the accumulated per-class launch counts and event times (since poisson_profile). */
 int poisson_profile_read(poisson_t* h, poisson_kernel_times* out);
 
+/* ------------------------------------------------------------------ projection
+ * Numerical Time Integration: each stage forms a provisional velocity u* on the cell faces
+ * (MAC grid), solves div((1/rho) grad p) = div(u*)/dt, and corrects u = u* - dt (1/rho) grad p.
+ * Face arrays are doubles, x fastest:
+ *   u: (nx+1) x ny x nz -- u[i + (nx+1)(j + ny k)] is on the face between cells i-1 and i;
+ *      faces i = 0 and i = nx are the walls x = 0, x = Lx;
+ *   v: nx x (ny+1) x nz, likewise in y (walls at j = 0, ny);
+ *   w: nx x ny x (nz+1), likewise in z; the bottom k = 0 is a wall, k = nz the top boundary.
+ * Host or device pointers (each detected; host arrays are staged through temporary device
+ * buffers); the caller owns them.  Both calls wait for the handle's stream before returning. */
+
+/* s_c = [(u_{i+1} - u_i) + (v_{j+1} - v_j) + (w_{k+1} - w_k)] / (h dt), in that order: the
+ * source of the pressure equation for poisson_solve.  s: nx*ny*nz doubles.  Needs only the
+ * handle's grid.  Errors: EINVAL (NULL, dt <= 0 or not finite), ENOMEM, ECUDA. */
+int poisson_divergence(poisson_t* h, const double* u, const double* v, const double* w,
+                       double dt, double* s);
+
+/* In place, on every face: u_f <- u_f - dt (beta_f ((p_n - p_c) / h)) with the face coefficients
+ * of the last poisson_set_density (beta_f = 2/(rho_c + rho_n); (p_n - p_c) across the face in
+ * the +axis direction); on the top face, where p = 0, u_f <- u_f - dt ((2/rho_c)((0 - p_c)/h)),
+ * i.e. 1/rho_c times the gradient over the half cell; wall faces are left as they are.  Then
+ * div_h(u)/dt = div_h(u*)/dt - div_h((1/rho) grad_h p): with p from poisson_solve for
+ * s = div(u*)/dt, the divergence left is the solve's residual, (A p - b)/h^2.  p: nx*ny*nz
+ * doubles.  Errors: EINVAL, ENOTREADY (before set_density), ENOMEM, ECUDA. */
+int poisson_project(poisson_t* h, double* u, double* v, double* w, const double* p, double dt);
+
 /* ------------------------------------------------------------------ allocation-free check
  * The paper has no counterpart to this entry point.  It is for callers that cannot allocate
  * device memory when they check a pressure field: a step loop that must not pay cudaMalloc's

@@ -31,7 +31,7 @@ EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson
            "poisson_solve", "poisson_apply", "poisson_precond_apply", "poisson_get_operator",
            "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
            "poisson_profile_read", "poisson_describe", "poisson_residual_noalloc",
-           "poisson_strerror", "poisson_version"]
+           "poisson_divergence", "poisson_project", "poisson_strerror", "poisson_version"]
 K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER, K_PCG = 0, 1, 2, 3, 4
 K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 
@@ -100,6 +100,10 @@ def load(path=None):
     lib.poisson_describe.argtypes = [vp, ctypes.c_char_p, i]
     lib.poisson_residual_noalloc.argtypes = [i, i, i, d, vp, d, d, vp, vp, vp, vp]
     lib.poisson_residual_noalloc.restype = i
+    lib.poisson_divergence.argtypes = [vp, vp, vp, vp, d, vp]
+    lib.poisson_divergence.restype = i
+    lib.poisson_project.argtypes = [vp, vp, vp, vp, vp, d]
+    lib.poisson_project.restype = i
     for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read", "poisson_describe"]:
         getattr(lib, name).restype = i
     _lib = lib
@@ -211,6 +215,29 @@ class Poisson:
         buf = ctypes.create_string_buffer(256)
         _check(load().poisson_describe(self._h, buf, 256), "poisson_describe")
         return buf.value.decode()
+
+    def divergence(self, u, v, w, dt, s):
+        """``s = div_h(u) / dt`` from face velocities ``u`` ``(nz, ny, nx+1)``, ``v``
+        ``(nz, ny+1, nx)``, ``w`` ``(nz+1, ny, nx)`` (numpy or CUDA float64) into ``s``."""
+        _check(load().poisson_divergence(self._h, _addr(u), _addr(v), _addr(w), dt, _addr(s)),
+               "poisson_divergence")
+
+    def project(self, u, v, w, p, dt):
+        """In place: ``u -= dt beta_f grad_h p`` on every face (walls unchanged)."""
+        _check(load().poisson_project(self._h, _addr(u), _addr(v), _addr(w), _addr(p), dt),
+               "poisson_project")
+
+    def projection_step(self, u, v, w, dt, p, tol, s=None):
+        """One pressure projection of a provisional face velocity, in place: ``s =
+        div(u)/dt``, ``p`` solves the pressure equation (``p`` is the warm start on entry), then
+        ``u -= dt beta grad p``.  ``s``: optional scratch of the cell shape (same kind of array
+        as ``p``).  Returns the solve's (status, stats)."""
+        if s is None:
+            s = np.empty(self.shape) if isinstance(p, np.ndarray) else p.new_empty(self.shape)
+        self.divergence(u, v, w, dt, s)
+        rc, st = self.solve(s, p, tol)
+        self.project(u, v, w, p, dt)
+        return rc, st
 
     def get_operator(self, bx=None, by=None, bz=None, diag=None):
         _check(load().poisson_get_operator(self._h, _addr(bx), _addr(by), _addr(bz), _addr(diag)),

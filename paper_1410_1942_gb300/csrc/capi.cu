@@ -233,7 +233,7 @@ static int setup_march(poisson_t* H) {
 }
 
 static void free_state(poisson_t* H) {
-    void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->eta32, H->eta16, H->x64,
+    void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->top64, H->eta32, H->eta16, H->x64,
                     H->b64, H->r64, H->z64, H->p64a, H->p64b, H->d32, H->r32, H->z32,
                     H->p32a, H->p32b, H->s32a, H->s32b, H->w32a, H->w32b, H->sc,
                     H->partials, H->io_a, H->io_b, H->io_c, H->io_c32};
@@ -291,6 +291,7 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     auto A = [&](int r) { if (rc == POISSON_OK) rc = r; };
     const size_t N = (size_t)n;
     A(dalloc(&H->bx, N)); A(dalloc(&H->by, N)); A(dalloc(&H->bz, N)); A(dalloc(&H->diag, N));
+    A(dalloc(&H->top64, (size_t)nx * ny));
     A(dalloc(&H->eta32, N)); A(dalloc(&H->eta16, N));
     A(dalloc(&H->x64, N)); A(dalloc(&H->b64, N));
     if (o.precision == POISSON_FP64) {
@@ -351,8 +352,8 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
         CK(cudaMemcpyAsync(H->b64, F, bytes, cudaMemcpyHostToDevice, H->st));
         Fd = H->b64;
     }
-    launch_setup(H->d, Fd, rho_air, rho_water, H->bx, H->by, H->bz, H->diag, H->dinv, H->eta32,
-                 H->eta16, H->st);
+    launch_setup(H->d, Fd, rho_air, rho_water, H->bx, H->by, H->bz, H->diag, H->dinv, H->top64,
+                 H->eta32, H->eta16, H->st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(H->st));
     H->ready = true;

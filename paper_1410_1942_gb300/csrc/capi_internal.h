@@ -22,6 +22,9 @@ struct poisson_s {
 
     // FP64 operator: low-side face coefficients, diagonal, 1/diagonal (FP64 Jacobi only)
     double *bx = nullptr, *by = nullptr, *bz = nullptr, *diag = nullptr, *dinv = nullptr;
+    // 2/rho_c of the top layer (nx*ny): the coefficient of the Dirichlet top face, for the
+    // velocity correction of poisson_project
+    double* top64 = nullptr;
     // rho / 2 per cell for the reduced-precision inner operator
     float* eta32 = nullptr;
     __nv_bfloat16* eta16 = nullptr;

@@ -44,11 +44,12 @@ __global__ void k_setup_faces(Dims d, const double* __restrict__ F, double ra, d
     if (eta16) eta16[c] = __float2bfloat16_rn((float)e);
 }
 
-// diag = bx[c] + by[c] + bz[c] + high faces (+ 2/rho_c on the top layer), summed in that order.
+// diag = bx[c] + by[c] + bz[c] + high faces (+ 2/rho_c on the top layer), summed in that order;
+// top[i + nx j] = 2/rho_c of the top layer.
 __global__ void k_setup_diag(Dims d, const double* __restrict__ F, double ra, double rw,
                              const double* __restrict__ bx, const double* __restrict__ by,
                              const double* __restrict__ bz, double* __restrict__ diag,
-                             double* __restrict__ dinv) {
+                             double* __restrict__ dinv, double* __restrict__ top) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= d.n) return;
     const int c = (int)tid;
@@ -56,8 +57,13 @@ __global__ void k_setup_diag(Dims d, const double* __restrict__ F, double ra, do
     double s = __dadd_rn(__dadd_rn(bx[c], by[c]), bz[c]);
     if (i + 1 < d.nx) s = __dadd_rn(s, bx[c + 1]);
     if (j + 1 < d.ny) s = __dadd_rn(s, by[c + d.nx]);
-    if (k + 1 < d.nz) s = __dadd_rn(s, bz[c + d.sxy]);
-    else s = __dadd_rn(s, 2.0 / rho_of(F[c], ra, rw));
+    if (k + 1 < d.nz) {
+        s = __dadd_rn(s, bz[c + d.sxy]);
+    } else {
+        const double t = 2.0 / rho_of(F[c], ra, rw);
+        s = __dadd_rn(s, t);
+        if (top) top[c - k * d.sxy] = t;
+    }
     diag[c] = s;
     if (dinv) dinv[c] = 1.0 / s;
 }
@@ -577,10 +583,10 @@ static inline dim3 grid_of(const Dims& d, int kc) {
 static inline unsigned blocks1d(long long n) { return (unsigned)((n + 255) / 256); }
 
 void launch_setup(const Dims& d, const double* F, double ra, double rw, double* bx, double* by,
-                  double* bz, double* diag, double* dinv, float* eta32, __nv_bfloat16* eta16,
-                  cudaStream_t st) {
+                  double* bz, double* diag, double* dinv, double* top, float* eta32,
+                  __nv_bfloat16* eta16, cudaStream_t st) {
     k_setup_faces<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, eta32, eta16);
-    k_setup_diag<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, diag, dinv);
+    k_setup_diag<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, diag, dinv, top);
     counted(2);
 }
 

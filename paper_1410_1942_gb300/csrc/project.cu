@@ -1,0 +1,179 @@
+// project.cu -- the projection around the pressure solve: the divergence of a face velocity
+// (the solve's source) and the velocity correction by the pressure gradient.
+//
+// Numerical Time Integration: each stage forms a provisional velocity u* on the faces of the
+// cells (MAC grid), solves div((1/rho) grad p) = div(u*)/dt, and corrects
+// u = u* - dt (1/rho) grad p.  The correction uses the operator's own face coefficients
+// (2/(rho_c + rho_n) on interior faces; 1/rho_c with p = 0 on the top face, at half a cell from
+// the centre), so div_h(u) / dt = div_h(u*) / dt - L p exactly: the divergence left behind is the
+// solve's residual, (A p - b) / h^2.
+//
+// Both passes are elementwise over cells (one thread per cell, its three low faces plus the top
+// face on the last layer): HBM-bound, a few tens of bytes per cell, once per solve.  They are FP64
+// throughout and evaluate every expression in one fixed order with rounded intrinsics, so the
+// results do not depend on FMA contraction.
+#include <cmath>
+
+#include "poisson.h"
+#include "capi_internal.h"
+#include "internal.cuh"
+#include "kernels.h"
+
+namespace {
+
+using pcg::Dims;
+
+constexpr int PT = 256;
+
+inline unsigned blocks_of(long long n) { return (unsigned)((n + PT - 1) / PT); }
+
+// s_c = ((u_{i+1} - u_i) + (v_{j+1} - v_j) + (w_{k+1} - w_k)) / (h dt)
+__global__ void __launch_bounds__(PT) k_divergence(Dims d, double hd, const double* __restrict__ u,
+                                                   const double* __restrict__ v,
+                                                   const double* __restrict__ w,
+                                                   double* __restrict__ s) {
+    const long long t = blockIdx.x * (long long)PT + threadIdx.x;
+    if (t >= d.n) return;
+    const int c = (int)t;
+    const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
+    const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+    const long long fv = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+    const double du = __dsub_rn(u[fu + 1], u[fu]);
+    const double dv = __dsub_rn(v[fv + d.nx], v[fv]);
+    const double dw = __dsub_rn(w[c + (long long)d.sxy], w[c]);
+    s[c] = __ddiv_rn(__dadd_rn(__dadd_rn(du, dv), dw), hd);
+}
+
+// q - dt (beta ((p_hi - p_lo) / h)), in that order
+__device__ __forceinline__ double corrected(double q, double dt, double beta, double p_hi,
+                                            double p_lo, double h) {
+    return __dsub_rn(q, __dmul_rn(dt, __dmul_rn(beta, __ddiv_rn(__dsub_rn(p_hi, p_lo), h))));
+}
+
+__global__ void __launch_bounds__(PT) k_project(Dims d, double h, double dt,
+                                                const double* __restrict__ bx,
+                                                const double* __restrict__ by,
+                                                const double* __restrict__ bz,
+                                                const double* __restrict__ top,
+                                                const double* __restrict__ p, double* __restrict__ u,
+                                                double* __restrict__ v, double* __restrict__ w) {
+    const long long t = blockIdx.x * (long long)PT + threadIdx.x;
+    if (t >= d.n) return;
+    const int c = (int)t;
+    const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
+    const double pc = p[c];
+    if (i > 0) {
+        const long long f = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+        u[f] = corrected(u[f], dt, bx[c], pc, p[c - 1], h);
+    }
+    if (j > 0) {
+        const long long f = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+        v[f] = corrected(v[f], dt, by[c], pc, p[c - d.nx], h);
+    }
+    if (k > 0) w[c] = corrected(w[c], dt, bz[c], pc, p[c - d.sxy], h);
+    if (k + 1 == d.nz) {
+        // top face: p = 0 there; (1/rho_c) (0 - p_c) / (h/2) = (2/rho_c) ((0 - p_c) / h)
+        const long long f = c + (long long)d.sxy;
+        w[f] = corrected(w[f], dt, top[c - k * d.sxy], 0.0, pc, h);
+    }
+}
+
+// Device copies of caller arrays: the caller's pointer if it is device memory, else a temporary
+// filled from the host (and, for outputs, copied back by flush()).
+struct Staged {
+    double* dev = nullptr;
+    double* host = nullptr;
+    size_t bytes = 0;
+    bool owned = false;
+    int stage(const double* p, size_t n, bool load, cudaStream_t st) {
+        bytes = n * sizeof(double);
+        if (is_device_ptr(p)) {
+            dev = const_cast<double*>(p);
+            return POISSON_OK;
+        }
+        host = const_cast<double*>(p);
+        if (cudaMalloc((void**)&dev, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            dev = nullptr;
+            return POISSON_ENOMEM;
+        }
+        owned = true;
+        if (load && cudaMemcpyAsync(dev, p, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            return POISSON_ECUDA;
+        }
+        return POISSON_OK;
+    }
+    int flush(cudaStream_t st) {
+        if (!owned) return POISSON_OK;
+        if (cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+            cudaGetLastError();
+            return POISSON_ECUDA;
+        }
+        return POISSON_OK;
+    }
+    ~Staged() {
+        if (owned && dev) cudaFree(dev);
+    }
+};
+
+int finish(cudaStream_t st) {
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return POISSON_ECUDA;
+    }
+    return POISSON_OK;
+}
+
+}  // namespace
+
+extern "C" int poisson_divergence(poisson_t* H, const double* u, const double* v, const double* w,
+                                  double dt, double* s) {
+    if (!H || !u || !v || !w || !s || !(dt > 0.0) || !std::isfinite(dt)) return POISSON_EINVAL;
+    const Dims d = H->d;
+    const size_t nu = (size_t)(d.nx + 1) * d.ny * d.nz, nv = (size_t)d.nx * (d.ny + 1) * d.nz,
+                 nw = (size_t)d.sxy * (d.nz + 1);
+    Staged U, V, W, S;
+    int rc = U.stage(u, nu, true, H->st);
+    if (rc == POISSON_OK) rc = V.stage(v, nv, true, H->st);
+    if (rc == POISSON_OK) rc = W.stage(w, nw, true, H->st);
+    if (rc == POISSON_OK) rc = S.stage(s, (size_t)d.n, false, H->st);
+    if (rc != POISSON_OK) {
+        finish(H->st);
+        return rc;
+    }
+    k_divergence<<<blocks_of(d.n), PT, 0, H->st>>>(d, H->h * dt, U.dev, V.dev, W.dev, S.dev);
+    pcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    if (cudaGetLastError() != cudaSuccess) rc = POISSON_ECUDA;
+    if (rc == POISSON_OK) rc = S.flush(H->st);
+    const int rs = finish(H->st);
+    return rc != POISSON_OK ? rc : rs;
+}
+
+extern "C" int poisson_project(poisson_t* H, double* u, double* v, double* w, const double* p,
+                               double dt) {
+    if (!H || !u || !v || !w || !p || !(dt > 0.0) || !std::isfinite(dt)) return POISSON_EINVAL;
+    if (!H->ready) return POISSON_ENOTREADY;
+    const Dims d = H->d;
+    const size_t nu = (size_t)(d.nx + 1) * d.ny * d.nz, nv = (size_t)d.nx * (d.ny + 1) * d.nz,
+                 nw = (size_t)d.sxy * (d.nz + 1);
+    Staged U, V, W, P;
+    int rc = U.stage(u, nu, true, H->st);
+    if (rc == POISSON_OK) rc = V.stage(v, nv, true, H->st);
+    if (rc == POISSON_OK) rc = W.stage(w, nw, true, H->st);
+    if (rc == POISSON_OK) rc = P.stage(p, (size_t)d.n, true, H->st);
+    if (rc != POISSON_OK) {
+        finish(H->st);
+        return rc;
+    }
+    k_project<<<blocks_of(d.n), PT, 0, H->st>>>(d, H->h, dt, H->bx, H->by, H->bz, H->top64,
+                                                P.dev, U.dev, V.dev, W.dev);
+    pcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    if (cudaGetLastError() != cudaSuccess) rc = POISSON_ECUDA;
+    if (rc == POISSON_OK) rc = U.flush(H->st);
+    if (rc == POISSON_OK) rc = V.flush(H->st);
+    if (rc == POISSON_OK) rc = W.flush(H->st);
+    const int rs = finish(H->st);
+    return rc != POISSON_OK ? rc : rs;
+}

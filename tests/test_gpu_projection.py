@@ -1,0 +1,129 @@
+"""Parity of the projection around the solve (divergence of u*, velocity correction) with the FP64
+oracle, through the C ABI: both passes bit for bit, and the full projection step (divergence,
+mixed-precision solve, correction) leaving a divergence equal to the solve's residual."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_1942_gb300 import build, capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(37, 23, 19), (64, 16, 1), (8, 9, 33), (1, 5, 7), (16, 1, 4)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    capi.load()
+
+
+def _faces(shape, seed):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((nz, ny, nx + 1)), rng.standard_normal((nz, ny + 1, nx)),
+            rng.standard_normal((nz + 1, ny, nx)))
+
+
+def _rand_F(shape, seed):
+    rng = np.random.default_rng(seed)
+    F = rng.random(shape)
+    F[rng.random(shape) < 0.3] = 0.0
+    F[rng.random(shape) < 0.3] = 1.0
+    return F
+
+
+@pytest.mark.parametrize("dev", [False, True])
+@pytest.mark.parametrize("nx,ny,nz", SHAPES)
+def test_divergence_bit_exact(nx, ny, nz, dev):
+    import torch
+    shape = (nz, ny, nx)
+    u, v, w = _faces(shape, 1)
+    h, dt = 1.0 / 16, 1.3e-3
+    ref = oracle.divergence(u, v, w, h, dt)
+    with capi.Poisson(nx, ny, nz, h) as s:
+        if dev:
+            ud, vd, wd = (torch.from_numpy(a).cuda() for a in (u, v, w))
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+            s.divergence(ud, vd, wd, dt, out)
+            got = out.cpu().numpy()
+        else:
+            got = np.empty(shape)
+            s.divergence(u, v, w, dt, got)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("dev", [False, True])
+@pytest.mark.parametrize("nx,ny,nz", SHAPES)
+def test_project_bit_exact(nx, ny, nz, dev):
+    import torch
+    shape = (nz, ny, nx)
+    F = _rand_F(shape, 2)
+    u, v, w = _faces(shape, 3)
+    p = np.random.default_rng(4).standard_normal(shape)
+    h, dt = 1.0 / 16, 1.3e-3
+    op = oracle.operator(F)
+    ru, rv, rw = oracle.project(op, F, u, v, w, p, h, dt)
+    with capi.Poisson(nx, ny, nz, h) as s:
+        s.set_density(F)
+        if dev:
+            ud, vd, wd, pd = (torch.from_numpy(a.copy()).cuda() for a in (u, v, w, p))
+            s.project(ud, vd, wd, pd, dt)
+            gu, gv, gw = (a.cpu().numpy() for a in (ud, vd, wd))
+        else:
+            gu, gv, gw = u.copy(), v.copy(), w.copy()
+            s.project(gu, gv, gw, p, dt)
+    assert np.array_equal(gu, ru) and np.array_equal(gv, rv) and np.array_equal(gw, rw)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["flat", "strut"])
+def test_projection_step_leaves_the_solve_residual(prec, case):
+    """divergence -> solve -> correction on the device: div_h(u_new) h^2 is the residual of the
+    solve (<= tol |b|), and the corrected velocity matches the oracle's projection of its own
+    1e-12 pressure to the solve's accuracy."""
+    c = (inputs.flat_case(40, 24, 20, seed=6, tol=1e-9) if case == "flat"
+         else inputs.strut_case(96, 48, 40, seed=2))
+    g = c.grid
+    modes = inputs.fourier_modes(np.random.default_rng(7))
+    u, v, w = inputs.face_velocity(g, modes)
+    op = oracle.operator(c.F)
+    s_ref = oracle.divergence(u, v, w, g.h, inputs.DT)
+    b = oracle.rhs(s_ref, g.h)
+    p = np.zeros(g.shape)
+    un, vn, wn = u.copy(), v.copy(), w.copy()
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec) as s:
+        s.set_density(c.F)
+        rc, st = s.projection_step(un, vn, wn, inputs.DT, p, 1e-9)
+    assert rc == capi.OK
+    div = oracle.divergence(un, vn, wn, g.h, inputs.DT)
+    r, _ = oracle.residual(op, b, p)
+    scale = (np.abs(b).max() + np.abs(oracle.apply(op, p)).max()) / g.h ** 2
+    assert np.abs(div + r / g.h ** 2).max() <= 1e-12 * scale
+    assert np.linalg.norm(div) * g.h ** 2 <= 1e-9 * (1 + 1e-6) * np.linalg.norm(b)
+    ref = oracle.pcg(op, b, tol=1e-12, precond="ssor")
+    ru, rv, rw = oracle.project(op, c.F, u, v, w, ref.x, g.h, inputs.DT)
+    # the correction differs by dt beta grad(p - p_ref): |p - p_ref| <= 1e-6 |p_ref| (the solve's
+    # parity bound), and the CG error is smooth, so its gradient stays within a few times that
+    for got, want, orig in ((un, ru, u), (vn, rv, v), (wn, rw, w)):
+        assert np.linalg.norm(got - want) <= 2e-5 * np.linalg.norm(orig - want) + 1e-15
+
+
+def test_projection_errors():
+    c = inputs.flat_case(16, 8, 8, seed=1)
+    g = c.grid
+    u, v, w = _faces(g.shape, 5)
+    p = np.zeros(g.shape)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h) as s:
+        with pytest.raises(capi.PoissonError) as e:
+            s.project(u, v, w, p, 1e-3)
+        assert e.value.status == capi.ENOTREADY
+        s.set_density(c.F)
+        with pytest.raises(capi.PoissonError) as e:
+            s.project(u, v, w, p, 0.0)
+        assert e.value.status == capi.EINVAL
+        with pytest.raises(capi.PoissonError) as e:
+            s.divergence(u, v, w, -1.0, p)
+        assert e.value.status == capi.EINVAL
