@@ -45,6 +45,9 @@ BYTES_PER_CELL = {
     # FP64 PCG: vectors 8 B, stored FP64 faces bx, by, bz + diag (+ dinv in phase B)
     "fp64": {"cg_phase_a": 8 * 3 + 8 * 4, "cg_phase_b": 8 * 6 + 8 * 5},
 }
+# one-sweep persistent kernels (Chronopoulos-Gear): reads p, u, s^, w^ (16 B) + eta, writes p,
+# u, s^, w^ (16 B) every iteration; x read and written every other iteration (4 B on average)
+BYTES_PER_CELL_ONE_SWEEP = {"fp32": 16 + 4 + 16 + 4, "bf16": 16 + 2 + 16 + 4}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -412,9 +415,12 @@ def main():
     cands = [k for k in ("pcg_persistent", "cg_phase_a", "cg_phase_b") if prof[k]["launches"]]
     dom = max(cands, key=lambda k: prof[k]["ms"])
     per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
+    one_sweep = "one-sweep" in solver.describe()
+    bpi = (BYTES_PER_CELL_ONE_SWEEP[args.precision] if one_sweep
+           else bpc["cg_phase_a"] + bpc["cg_phase_b"])  # algorithmic bytes per cell-iteration
     if dom == "pcg_persistent":
-        # one launch runs every CG iteration of one inner solve: both passes per iteration
-        alg_bytes = (bpc["cg_phase_a"] + bpc["cg_phase_b"]) * g.n * iters / prof[dom]["launches"]
+        # one launch runs every CG iteration of one inner solve
+        alg_bytes = bpi * g.n * iters / prof[dom]["launches"]
     else:
         alg_bytes = bpc[dom] * g.n
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
@@ -425,7 +431,7 @@ def main():
     # cell-iterations of an average launch
     traffic = (bpci * g.n * iters / prof[dom]["launches"]
                if bpci is not None and dom == "pcg_persistent" else None)
-    hbm_alg = value * (bpc["cg_phase_a"] + bpc["cg_phase_b"])  # GB/s of CG-pass algorithmic traffic
+    hbm_alg = value * bpi  # GB/s of CG-pass algorithmic traffic
 
     # end to end through the C ABI with pinned host arrays
     e2e = None
@@ -499,6 +505,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
+                         "alg_bytes_per_cell_iter": bpi,
                          "ms_per_launch": per_launch_ms},
             "kernel_times": prof,
             **extras,

@@ -14,8 +14,12 @@
 //   gamma' = (D u', u'),  delta' = (A u', u'),  rho' = |D u'|^2     (one reduction)
 //   beta'  = gamma' / gamma,  alpha' = gamma' / (delta' - beta' gamma' / alpha)
 //
-// A sweep reads x, p, u, s^, w^ and eta and writes x, p, u', s^, w^': 44 bytes per cell, the
-// same as the two passes of the standard form, in one pass.  The neighbours of a cell's u' are
+// A sweep reads p, u, s^, w^ and eta and writes p, u', s^, w^' (36 bytes per cell); x is read
+// and written every other iteration only: an even iteration i leaves x_i in memory and an odd one
+// stores x_{i+1} = x_{i-1} + alpha_{i-1} p_{i-1} + alpha_i p_i from the p it reads and the p it
+// forms, so x costs 4 bytes per cell-iteration and a sweep 40 on average (44 for the two passes
+// of the standard form).  A solve that stops after an even iteration adds alpha_i p_i to x in a
+// short pass over its own cells.  The neighbours of a cell's u' are
 // formed from the neighbours' u, s^, w^ (halo boxes of the plane), so u, s^ and w^ are double
 // buffered (a CTA writes u' while its neighbours still read u).  The first sweep of a launch has
 // alpha = beta = 0 (u = M^-1 r from the init kernel, s^ = w^ = p = 0): it only forms w^ = M^-1 A u
@@ -56,13 +60,19 @@ struct LocalSolve1 {
     Scalars* sc;
     int seg_begin, seg_end;
     double gamma, alpha, beta, rr, stop2;
+    double alpha_prev;  // alpha of the previous iteration (odd iterations update x with it)
     int done, iter, max_iter, finished, owner, first;
+    int xfix;           // stopped after an even iteration: x still lacks alpha p
 };
 
 // u' = u - alpha (w^ + beta s^), rounded the same way everywhere
 __device__ __forceinline__ float u_next(float u, float s, float w, float al, float be) {
     return __fmaf_rn(-al, __fmaf_rn(be, s, w), u);
 }
+
+// Whether the coming sweep updates x: odd iterations (the start-up sweep and even iterations
+// leave x as it is).
+__device__ __forceinline__ bool x_sweep(const LocalSolve1& L) { return !L.first && (L.iter & 1); }
 
 template <int CX, int CY, int TYT, typename E, int NS>
 __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1_ws(PcgArgs a) {
@@ -112,12 +122,14 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
         L.rr = sv.sc->rr;
         L.stop2 = sv.sc->stop2;
         L.alpha = 0.0;
+        L.alpha_prev = 0.0;
         L.beta = 0.0;
         L.done = sv.sc->done;
         L.iter = 0;
         L.max_iter = sv.sc->max_iter;
         L.finished = 0;
         L.first = 1;
+        L.xfix = 0;
         L.owner = 0;
         for (int q = 0; q < nseg; ++q)
             if (s_seg[q].slot == sv.seg_begin) L.owner = 1;
@@ -139,6 +151,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             if (!s_member[sg.solve - first]) continue;
             const int L = sg.k1 - sg.k0;
             const CUtensorMap* m = a.maps + MAPS_PER_SOLVE * sg.solve;
+            const bool xs = x_sweep(s_sol[sg.solve - first]);
             for (int off = 0; off < L + 2; ++off) {
                 if (s_fail) return;
                 const int st = np % NS, kk = sg.k0 - 1 + off;
@@ -149,13 +162,13 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                 unsigned char* dst = sm + st * G::STAGE;
                 const bool centre = off > 0 && off <= L;
                 uint64_t* bar = &full[st];
-                mbar_arrive_expect_tx(bar, centre ? G::TX : G::TX_HALO);
+                mbar_arrive_expect_tx(bar, centre ? (xs ? G::TX : G::TX - G::CB) : G::TX_HALO);
                 tma_load_3d(dst + G::U, m + MAP1_U0 + in, bar, sg.x0 - G::VOFF, sg.y0 - 1, kk);
                 tma_load_3d(dst + G::S, m + MAP1_S0 + in, bar, sg.x0 - G::VOFF, sg.y0 - 1, kk);
                 tma_load_3d(dst + G::WV, m + MAP1_W0 + in, bar, sg.x0 - G::VOFF, sg.y0 - 1, kk);
                 tma_load_3d(dst + G::ETA, m + MAP1_ETA, bar, sg.x0 - G::EOFF, sg.y0 - 1, kk);
                 if (centre) {
-                    tma_load_3d(dst + G::X, m + MAP1_X, bar, sg.x0, sg.y0, kk);
+                    if (xs) tma_load_3d(dst + G::X, m + MAP1_X, bar, sg.x0, sg.y0, kk);
                     tma_load_3d(dst + G::P, m + MAP1_P, bar, sg.x0, sg.y0, kk);
                 }
                 ++np;
@@ -185,6 +198,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             const bool work = s_sol[l].done == RUNNING;
             const Dims d = s_sol[l].d;
             const float al = (float)s_sol[l].alpha, be = (float)s_sol[l].beta;
+            const float alp = (float)s_sol[l].alpha_prev;
+            const bool xs = x_sweep(s_sol[l]);
             const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * warp;
             // u' of the thread's own block in plane q
             auto u_centre = [&](int q, float (&o)[CY][CX]) {
@@ -255,7 +270,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                         load_centre<CX, CY>((const float*)(S + G::U), G::VW, r0, cv, u0);
                         load_centre<CX, CY>((const float*)(S + G::S), G::VW, r0, cv, s0);
                         load_centre<CX, CY>((const float*)(S + G::WV), G::VW, r0, cv, w0);
-                        load_centre<CX, CY>((const float*)(S + G::X), G::W, CY * warp, cc, xo);
+                        if (xs) load_centre<CX, CY>((const float*)(S + G::X), G::W, CY * warp, cc, xo);
                         load_centre<CX, CY>((const float*)(S + G::P), G::W, CY * warp, cc, po);
 #pragma unroll
                         for (int y = 0; y < CY; ++y) {
@@ -265,7 +280,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                                 for (int x = 0; x < CX; ++x) {
                                     pn[x] = __fmaf_rn(be, po[y][x], u0[y][x]);
                                     sn[x] = __fmaf_rn(be, s0[y][x], w0[y][x]);
-                                    xn[x] = __fmaf_rn(al, pn[x], xo[y][x]);
+                                    if (xs)
+                                        xn[x] = __fmaf_rn(al, pn[x], __fmaf_rn(alp, po[y][x], xo[y][x]));
                                     wn[x] = qv[y][x] * rcp_approx(D[y][x]);
                                     const float du = D[y][x] * uc[y][x];
                                     ag += du * uc[y][x];
@@ -274,7 +290,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                                 }
                                 const size_t c =
                                     (size_t)i0 + (size_t)d.nx * (j0 + y + (size_t)d.ny * k);
-                                st_row<CX>(s_sol[l].x + c, xn);
+                                if (xs) st_row<CX>(s_sol[l].x + c, xn);
                                 st_row<CX>(s_sol[l].p + c, pn);
                                 st_row<CX>(s_sol[l].u[out] + c, uc[y]);
                                 st_row<CX>(s_sol[l].s[out] + c, sn);
@@ -349,6 +365,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                         L.beta = 0.0;
                     }
                 } else {
+                    const bool x_updated = (L.iter & 1) != 0;  // this sweep wrote x_{i+1}
                     L.iter += 1;
                     if (rn <= L.stop2) {
                         L.done = CONVERGED;
@@ -361,14 +378,40 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                             L.done = BREAKDOWN;
                         } else {
                             L.beta = be;
+                            L.alpha_prev = L.alpha;
                             L.alpha = gn / den;
                             L.gamma = gn;
                         }
                     }
+                    if (L.done != RUNNING && !x_updated) L.xfix = 1;
                 }
                 if (L.done != RUNNING) L.finished = 1;
             }
             __syncthreads();
+        }
+        // Solves that stopped after an even iteration: x_{i+1} = x_i + alpha_i p_i over this CTA's
+        // cells of the solve (p_i is what this CTA stored in the sweep just done).
+        bool any_fix = false;
+        for (int l = 0; l < nloc; ++l) any_fix = any_fix || s_sol[l].xfix;
+        if (any_fix) {
+            for (int ls = 0; ls < nseg; ++ls) {
+                const Seg sg = s_seg[ls];
+                const LocalSolve1& L = s_sol[sg.solve - first];
+                if (!L.xfix) continue;
+                const int nx = L.d.nx, ny = L.d.ny;
+                const int wd = min(G::W, nx - sg.x0), ht = min(G::HT, ny - sg.y0);
+                const int per = wd * ht;
+                const long long cnt = (long long)per * (sg.k1 - sg.k0);
+                const float al = (float)L.alpha;
+                for (long long q = tid; q < cnt; q += NT) {
+                    const int k = sg.k0 + (int)(q / per), r = (int)(q % per);
+                    const size_t c = (size_t)(sg.x0 + r % wd) +
+                                     (size_t)nx * ((size_t)(sg.y0 + r / wd) + (size_t)ny * k);
+                    L.x[c] = __fmaf_rn(al, L.p[c], L.x[c]);
+                }
+            }
+            __syncthreads();
+            if (tid < nloc) s_sol[tid].xfix = 0;
         }
         mark(TR_ALPHA);
         if (tid < nloc) {

@@ -376,6 +376,22 @@ def test_one_sweep_kernel_takes_the_iterations_of_standard_pcg(prec):
     assert abs(its[10012204] - its[12204]) <= 0.1 * its[12204] + 5, its
 
 
+@pytest.mark.parametrize("tile", [12204, 10012204])
+@pytest.mark.parametrize("k", [7, 8])
+def test_capped_solve_returns_the_k_th_iterate(tile, k):
+    """With the iteration cap at k, the FP32 inner solve stops after k CG iterations and p holds
+    the k-th iterate: the FP64 oracle's k-th iterate to FP32 accuracy.  An odd k ends the
+    one-sweep kernel on an iteration that leaves x to a closing pass (x is stored every other
+    iteration), an even k on one that stores it."""
+    c, op, b, _ = case("strut")
+    with solver(c, "fp32", tile=tile, max_iters=k) as s:
+        p = np.zeros(c.grid.shape)
+        rc, st = s.solve(c.s, p, 1e-9, allow=(capi.OK, capi.ENOTCONV))
+    assert rc == capi.ENOTCONV and st["inner_iters"] == k
+    ref = oracle.pcg_single_reduction(op, b, tol=0.0, max_iters=k).x
+    assert np.linalg.norm(p - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
 # ----------------------------------------------------------------------------- full size
 @pytest.fixture(scope="module")
 def strut_full():
