@@ -48,6 +48,9 @@ BYTES_PER_CELL = {
 # one-sweep persistent kernels (Chronopoulos-Gear): reads p, u, s^, w^ (16 B) + eta, writes p,
 # u, s^, w^ (16 B) every iteration; x read and written every other iteration (4 B on average)
 BYTES_PER_CELL_ONE_SWEEP = {"fp32": 16 + 4 + 16 + 4, "bf16": 16 + 2 + 16 + 4}
+# one-sweep kernels that form A p in the sweep: read u, p (8 B) + eta, write u, p (8 B), x every
+# other iteration (4 B on average)
+BYTES_PER_CELL_AP_FORMED = {"fp32": 8 + 4 + 8 + 4, "bf16": 8 + 2 + 8 + 4}
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -415,9 +418,13 @@ def main():
     cands = [k for k in ("pcg_persistent", "cg_phase_a", "cg_phase_b") if prof[k]["launches"]]
     dom = max(cands, key=lambda k: prof[k]["ms"])
     per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
-    one_sweep = "one-sweep" in solver.describe()
-    bpi = (BYTES_PER_CELL_ONE_SWEEP[args.precision] if one_sweep
-           else bpc["cg_phase_a"] + bpc["cg_phase_b"])  # algorithmic bytes per cell-iteration
+    desc = solver.describe()
+    if "A p formed" in desc:
+        bpi = BYTES_PER_CELL_AP_FORMED[args.precision]
+    elif "one-sweep" in desc:
+        bpi = BYTES_PER_CELL_ONE_SWEEP[args.precision]
+    else:
+        bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]  # algorithmic bytes per cell-iteration
     if dom == "pcg_persistent":
         # one launch runs every CG iteration of one inner solve
         alg_bytes = bpi * g.n * iters / prof[dom]["launches"]

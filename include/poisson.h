@@ -76,7 +76,9 @@ typedef struct {
                           ring (S omitted = 4).  F = 0, two sweeps per CG iteration: 1108, 2204,
                           2208, 12204, 12208, 302204, 302208, 312208, 602204, 612208; F = 1, one
                           sweep per iteration (Chronopoulos-Gear recurrences): 12204, 312204,
-                          312208 (plus 10000000).  P = split of the tile columns over the CTAs:
+                          312208 (plus 10000000); F = 2, one sweep with A p formed in it (2-cell
+                          halos, u, p, x and eta in memory): 12204, 512204, 12208 (plus
+                          20000000).  P = split of the tile columns over the CTAs:
                           0 equal planes per CTA, 1 balanced (segment start cost counted), 2
                           lockstep (neighbouring tiles on the same planes) (default 0)          */
     void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream                 */

@@ -781,7 +781,10 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
                  "ctas=%d segments=%d split=%s",
                  prec, march_tile_of(H->plan.variant) + 1000000 * H->plan.strategy, v.width,
                  v.height, v.cx, v.cy, v.ws ? ", producer warp" : "", v.ns,
-                 v.family == 1 ? "one-sweep" : "two-sweep", H->plan.nctas, H->plan.nsegs,
+                 v.family == 2   ? "one-sweep (A p formed)"
+                 : v.family == 1 ? "one-sweep"
+                                 : "two-sweep",
+                 H->plan.nctas, H->plan.nsegs,
                  H->plan.strategy == MARCH_SPLIT_BALANCED   ? "balanced"
                  : H->plan.strategy == MARCH_SPLIT_LOCKSTEP ? "lockstep"
                                                             : "equal");

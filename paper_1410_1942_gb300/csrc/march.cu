@@ -884,10 +884,10 @@ struct VariantOps {
 
 template <int CX, int CY, int TYT, int WS, int NS, int F>
 static VariantOps make_ops() {
-    if constexpr (F == 1) {
+    if constexpr (F == 1 || F == 2) {
         static_assert(WS == 1, "the one-sweep kernels have a producer warp");
-        const Cg1Kernel k = cg1_kernel(CX, CY, TYT, NS);
-        return VariantOps{CX, CY, TYT, 1, NS, k.smem32, k.smem16, k.k32, k.k16, 1};
+        const Cg1Kernel k = F == 1 ? cg1_kernel(CX, CY, TYT, NS) : cg2_kernel(CX, CY, TYT, NS);
+        return VariantOps{CX, CY, TYT, 1, NS, k.smem32, k.smem16, k.k32, k.k16, F};
     } else if constexpr (WS)
         return VariantOps{CX, CY, TYT, 1, NS, NS * Geo<CX, CY, TYT, float>::STAGE,
                           NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
@@ -900,12 +900,13 @@ static VariantOps make_ops() {
                           (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16, NS>, 0};
 }
 
-// (CX, CY, TYT, warp-specialised, ring stages, family); family 1 rows must be in CG1_CONFIGS
+// (CX, CY, TYT, warp-specialised, ring stages, family); family 1 and 2 rows must be in
+// CG1_CONFIGS and CG2_CONFIGS
 #define MARCH_VARIANTS(X)                                                                       \
     X(1, 1, 8, 0, 4, 0) X(2, 2, 4, 0, 4, 0) X(2, 2, 8, 0, 4, 0) X(2, 2, 4, 1, 4, 0)             \
     X(2, 2, 8, 1, 4, 0) X(2, 2, 4, 0, 3, 0) X(2, 2, 8, 0, 3, 0) X(2, 2, 8, 1, 3, 0)             \
     X(2, 2, 4, 0, 6, 0) X(2, 2, 8, 1, 6, 0) X(2, 2, 4, 1, 4, 1) X(2, 2, 4, 1, 3, 1)             \
-    X(2, 2, 8, 1, 3, 1)
+    X(2, 2, 8, 1, 3, 1) X(2, 2, 4, 1, 4, 2) X(2, 2, 4, 1, 5, 2) X(2, 2, 8, 1, 4, 2)
 
 static const VariantOps* variants(int* count) {
 #define ROW(CX, CY, TYT, WS, NS, F) make_ops<CX, CY, TYT, WS, NS, F>(),
@@ -949,7 +950,7 @@ int march_find_variant(int cx, int cy, int tyt, int ws, int ns, int family) {
 }
 
 int march_variant_of_tile(int tile) {
-    if (tile < 0 || tile / 10000000 > 1 || (tile / 1000000) % 10 >= MARCH_SPLITS) return -1;
+    if (tile < 0 || tile / 10000000 > 2 || (tile / 1000000) % 10 >= MARCH_SPLITS) return -1;
     const int family = tile / 10000000;
     tile %= 1000000;
     const int ns = tile / 100000 ? tile / 100000 : 4;
@@ -986,6 +987,17 @@ bool march_encode_solve(CUtensorMap (&m)[MAPS_PER_SOLVE], const MarchSolve& s, i
     const CUtensorMapDataType edt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : f32;
     const Dims& d = s.d;
     bool ok = true;
+    if (v.family == 2) {
+        const int bw = v.width + 8, bh = v.height + 4;
+        ok = ok && s.sa;
+        ok = ok && encode3d(&m[MAP2_U0], s.z, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP2_U1], s.sa, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP2_P0], s.pa, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP2_P1], s.pb, f32, 4, d, bw, bh);
+        ok = ok && encode3d(&m[MAP2_ETA], s.eta, edt, bf16 ? 2 : 4, d, v.width + 2 * eoff, bh);
+        ok = ok && encode3d(&m[MAP2_X], s.x, f32, 4, d, v.width, v.height);
+        return ok;
+    }
     if (v.family == 1) {
         const int bw = v.width + 8, bh = v.height + 2;
         ok = ok && s.sa && s.sb && s.wa && s.wb;

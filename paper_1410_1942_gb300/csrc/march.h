@@ -11,7 +11,8 @@ namespace pcg {
 // One kernel variant: 32 x tyt compute threads, each owning cx x cy cells, plus one TMA
 // producer warp when ws, an ns-stage plane ring; tile width x height cells.  family 0: two
 // sweeps (and two grid barriers) per CG iteration; family 1: one sweep per iteration (the
-// Chronopoulos-Gear recurrences, march1.cu).
+// Chronopoulos-Gear recurrences, march1.cu); family 2: one sweep per iteration with A p formed
+// in the sweep (march2.cu).
 struct MarchVariant {
     int id, cx, cy, tyt, ws, ns, width, height, family;
 };
@@ -24,6 +25,9 @@ enum { MAP_Z = 0, MAP_PA = 1, MAP_PB = 2, MAP_ETA = 3, MAP_X = 4, MAP_R = 5 };
 // above, centre boxes for x and p (pa).
 enum { MAP1_U0 = 0, MAP1_U1 = 1, MAP1_S0 = 2, MAP1_S1 = 3, MAP1_W0 = 4, MAP1_W1 = 5,
        MAP1_ETA = 6, MAP1_X = 7, MAP1_P = 8 };
+// Family 2: 2-cell halo boxes for both buffers of u (z, sa) and p (pa, pb) and for eta, a centre
+// box for x.
+enum { MAP2_U0 = 0, MAP2_U1 = 1, MAP2_P0 = 2, MAP2_P1 = 3, MAP2_ETA = 4, MAP2_X = 5 };
 constexpr int MAPS_PER_SOLVE = 9;
 
 // One solve of a plan as the host describes it.

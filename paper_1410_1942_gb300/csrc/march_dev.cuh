@@ -375,6 +375,9 @@ struct Cg1Kernel {
     int smem32, smem16;
 };
 Cg1Kernel cg1_kernel(int cx, int cy, int tyt, int ns);  // null kernels if not instantiated
+// Kernels of the one-sweep family with A p formed in the sweep (march2.cu).
+#define CG2_CONFIGS(X) X(2, 2, 4, 4) X(2, 2, 4, 5) X(2, 2, 8, 4)
+Cg1Kernel cg2_kernel(int cx, int cy, int tyt, int ns);  // null kernels if not instantiated
 
 template <int TYT>
 struct WsMinBlocks {

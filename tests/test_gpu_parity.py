@@ -137,7 +137,8 @@ def test_solve_matches_oracle(name, prec, precond):
 
 @pytest.mark.parametrize("tile", [-1, 0, 1108, 2204, 2208, 12204, 12208, 302204, 302208,
                                   312208, 602204, 612208, 1012204, 2002204, 2012208, 2302204,
-                                  10012204, 12012204, 10312204, 10312208, 12312208])
+                                  10012204, 12012204, 10312204, 10312208, 12312208, 20012204,
+                                  22012204, 20512204, 20012208, 22012208])
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("shape", [(96, 48, 40), (40, 23, 19), (64, 16, 1), (8, 9, 33)])
 def test_kernel_variants_match_oracle(tile, prec, shape):
@@ -265,7 +266,7 @@ def _oracle_ref(c):
     return op, b, oracle.pcg(op, b, tol=REF_TOL, precond="ssor").x
 
 
-@pytest.mark.parametrize("tile", [0, 2012204, 10012204, 12012204])
+@pytest.mark.parametrize("tile", [0, 2012204, 10012204, 12012204, 22012204])
 def test_batch_of_uneven_solves_matches_oracle(tile):
     """A batch of solves of uneven size, FP32 and BF16 coefficients, plus handles that run one
     by one (FP64, SSOR): every result meets both acceptance criteria, with the persistent
@@ -338,7 +339,7 @@ def test_batch_rejects_a_handle_twice():
             capi.batch_submit([s, s], [c.s, c.s], [p, p.copy()], 1e-9)
 
 
-@pytest.mark.parametrize("tile", [2002204, 2012208, 12012204])
+@pytest.mark.parametrize("tile", [2002204, 2012208, 12012204, 22012204])
 def test_lockstep_round_robin_split(tile):
     """More tile columns than CTAs (1024 x 512 planes): the lockstep split deals whole columns
     round-robin.  Checked by the oracle's FP64 residual (a property at any size) and against the
@@ -366,7 +367,7 @@ def test_one_sweep_kernel_takes_the_iterations_of_standard_pcg(prec):
     kernel's."""
     c, op, b, xref = case("strut")
     its = {}
-    for t in (12204, 10012204):
+    for t in (12204, 10012204, 20012204):
         with solver(c, prec, tile=t) as s:
             p = np.zeros(c.grid.shape)
             rc, st = s.solve(c.s, p, c.tol)
@@ -374,9 +375,10 @@ def test_one_sweep_kernel_takes_the_iterations_of_standard_pcg(prec):
         _check_solution(c, op, b, xref, p, st, c.tol)
         its[t] = st["inner_iters"]
     assert abs(its[10012204] - its[12204]) <= 0.1 * its[12204] + 5, its
+    assert abs(its[20012204] - its[12204]) <= 0.1 * its[12204] + 5, its
 
 
-@pytest.mark.parametrize("tile", [12204, 10012204])
+@pytest.mark.parametrize("tile", [12204, 10012204, 20012204])
 @pytest.mark.parametrize("k", [7, 8])
 def test_capped_solve_returns_the_k_th_iterate(tile, k):
     """With the iteration cap at k, the FP32 inner solve stops after k CG iterations and p holds
