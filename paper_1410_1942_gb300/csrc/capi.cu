@@ -192,10 +192,12 @@ static int setup_march(poisson_t* H) {
         cudaEventCreate(&e0);
         cudaEventCreate(&e1);
         float best = 1e30f;
-        // candidates: the 2 x 2-cells-per-thread variants (64-wide tiles, 8 or 16 rows, with or
-        // without a producer warp, 3-, 4- or 6-stage rings); the 1 x 1 one never won
+        // candidates: the 2 x 2-cells-per-thread variants of families 0 and 1 (64-wide tiles, 8
+        // or 16 rows, with or without a producer warp, 3-, 4- or 6-stage rings); the 1 x 1
+        // variant and family 2 (A p formed in the sweep, bound by its arithmetic) never won
         for (int cand = 0; cand < march_variant_count(); ++cand) {
-            if (march_variant(cand).cx != 2 || march_occupancy(cand, bf16) <= 0) continue;
+            const MarchVariant mv = march_variant(cand);
+            if (mv.cx != 2 || mv.family == 2 || march_occupancy(cand, bf16) <= 0) continue;
             for (int strat = 0; strat < MARCH_SPLITS; ++strat) {
                 if (build_plan(H, cand, strat) != 0) continue;
                 float t[2];
