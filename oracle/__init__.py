@@ -67,6 +67,8 @@ def _load():
         i, d = ctypes.c_int, ctypes.c_double
         lib.oracle_faces.argtypes = [i, i, i, P, d, d, i, P, P, P, P]
         lib.oracle_faces.restype = i
+        lib.oracle_faces_bc.argtypes = [i, i, i, P, d, d, i, i, P, P, P, P]
+        lib.oracle_faces_bc.restype = i
         lib.oracle_apply.argtypes = [i, i, i, P, P, P, P, P, P]
         lib.oracle_apply.restype = None
         lib.oracle_precond.argtypes = [i, i, i, P, P, P, P, i, d, P, P]
@@ -80,6 +82,8 @@ def _load():
         lib.oracle_divergence.restype = None
         lib.oracle_project.argtypes = [i, i, i, d, d, P, d, d, P, P, P, P, P, P, P]
         lib.oracle_project.restype = None
+        lib.oracle_project_bc.argtypes = [i, i, i, d, d, P, d, d, i, P, P, P, P, P, P, P]
+        lib.oracle_project_bc.restype = None
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = i
         lib.oracle_set_threads.argtypes = [i]
@@ -116,6 +120,7 @@ class Operator:
     by: np.ndarray
     bz: np.ndarray
     diag: np.ndarray
+    walls: int = 0
 
     @property
     def shape(self):
@@ -127,17 +132,22 @@ class Operator:
                 _ptr(self.diag))
 
 
-def operator(F, rho_air=1.0, rho_water=1000.0, mean="harmonic"):
-    """Assemble the operator from the water fraction ``F`` (shape ``(nz, ny, nx)``)."""
+WALL_XM, WALL_XP, WALL_YM, WALL_YP, WALL_ZM = 1, 2, 4, 8, 16
+
+
+def operator(F, rho_air=1.0, rho_water=1000.0, mean="harmonic", walls=0):
+    """Assemble the operator from the water fraction ``F`` (shape ``(nz, ny, nx)``).  ``walls``:
+    bitmask of side/bottom walls with p = 0 on the wall face (WALL_XM | ...); the others, as in
+    the paper's configuration, have a zero normal gradient; the top face always has p = 0."""
     F = _f64(F)
     nz, ny, nx = F.shape
     bx, by, bz, dg = (np.empty_like(F) for _ in range(4))
     m = MEAN_HARMONIC if mean == "harmonic" else MEAN_ARITHMETIC
-    rc = _load().oracle_faces(nx, ny, nz, _ptr(F), float(rho_air), float(rho_water), m,
-                              _ptr(bx), _ptr(by), _ptr(bz), _ptr(dg))
+    rc = _load().oracle_faces_bc(nx, ny, nz, _ptr(F), float(rho_air), float(rho_water), m,
+                                 int(walls), _ptr(bx), _ptr(by), _ptr(bz), _ptr(dg))
     if rc != OK:
         raise RuntimeError("oracle_faces failed: %d" % rc)
-    return Operator(nx, ny, nz, bx, by, bz, dg)
+    return Operator(nx, ny, nz, bx, by, bz, dg, int(walls))
 
 
 def apply(op: Operator, x):
@@ -270,15 +280,16 @@ def divergence(u, v, w, h, dt):
 
 def project(op: Operator, F, u, v, w, p, h, dt, rho_air=1.0, rho_water=1000.0):
     """The velocity correction ``u - dt beta_f grad_h p`` on every face (new arrays): interior
-    faces use the operator's face coefficients and ``(p_n - p_c)/h``; the top face, where
-    ``p = 0``, uses ``1/rho_c`` and ``(0 - p_c)/(h/2)``; wall faces are unchanged.  Then
+    faces use the operator's face coefficients and ``(p_n - p_c)/h``; the top face and the
+    operator's Dirichlet walls, where ``p = 0``, use ``1/rho_c`` and the difference to 0 over
+    ``h/2``; zero-gradient wall faces are unchanged.  Then
     ``divergence(u_new) = (A p - b)/h^2`` for ``b = rhs(divergence(u), h)``."""
     u, v, w = _f64(u).copy(), _f64(v).copy(), _f64(w).copy()
     p, F = _f64(p).reshape(op.shape), _f64(F).reshape(op.shape)
     assert (u.shape, v.shape, w.shape) == _faces_shapes(op.nx, op.ny, op.nz)
-    _load().oracle_project(op.nx, op.ny, op.nz, float(h), float(dt), _ptr(F), float(rho_air),
-                           float(rho_water), _ptr(op.bx), _ptr(op.by), _ptr(op.bz), _ptr(p),
-                           _ptr(u), _ptr(v), _ptr(w))
+    _load().oracle_project_bc(op.nx, op.ny, op.nz, float(h), float(dt), _ptr(F), float(rho_air),
+                              float(rho_water), op.walls, _ptr(op.bx), _ptr(op.by), _ptr(op.bz),
+                              _ptr(p), _ptr(u), _ptr(v), _ptr(w))
     return u, v, w
 
 

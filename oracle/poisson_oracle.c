@@ -77,8 +77,17 @@ void oracle_set_threads(int n) {
 }
 
 /* ---------------------------------------------------------------------------- operator setup */
-int oracle_faces(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
-                 int mean, double* bx, double* by, double* bz, double* diag) {
+/* walls: bitmask of the side and bottom walls that carry p = 0 instead of a zero normal gradient
+ * (1 x = 0, 2 x = Lx, 4 y = 0, 8 y = Ly, 16 z = 0); like the top face, such a wall adds
+ * 2 (1/rho_c) to the diagonal of the cells that touch it and couples them to nothing. */
+#define OR_WALL_XM 1
+#define OR_WALL_XP 2
+#define OR_WALL_YM 4
+#define OR_WALL_YP 8
+#define OR_WALL_ZM 16
+
+int oracle_faces_bc(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
+                    int mean, int walls, double* bx, double* by, double* bz, double* diag) {
     if (nx <= 0 || ny <= 0 || nz <= 0 || !F || !bx || !by || !bz || !diag) return OR_EINVAL;
     const idx_t n = (idx_t)nx * ny * nz;
     double* rho = (double*)malloc(sizeof(double) * (size_t)n);
@@ -120,10 +129,20 @@ int oracle_faces(int nx, int ny, int nz, const double* F, double rho_air, double
                 if (j + 1 < ny) d += by[c + nx];
                 if (k + 1 < nz) d += bz[c + (idx_t)nx * ny];
                 else d += 2.0 / rho[c];
+                if ((walls & OR_WALL_XM) && i == 0) d += 2.0 / rho[c];
+                if ((walls & OR_WALL_XP) && i == nx - 1) d += 2.0 / rho[c];
+                if ((walls & OR_WALL_YM) && j == 0) d += 2.0 / rho[c];
+                if ((walls & OR_WALL_YP) && j == ny - 1) d += 2.0 / rho[c];
+                if ((walls & OR_WALL_ZM) && k == 0) d += 2.0 / rho[c];
                 diag[c] = d;
             }
     free(rho);
     return OR_OK;
+}
+
+int oracle_faces(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
+                 int mean, double* bx, double* by, double* bz, double* diag) {
+    return oracle_faces_bc(nx, ny, nz, F, rho_air, rho_water, mean, 0, bx, by, bz, diag);
 }
 
 /* ---------------------------------------------------------------------------- y = A x */
@@ -332,9 +351,10 @@ void oracle_divergence(int nx, int ny, int nz, double h, double dt, const double
             }
 }
 
-void oracle_project(int nx, int ny, int nz, double h, double dt, const double* F, double rho_air,
-                    double rho_water, const double* bx, const double* by, const double* bz,
-                    const double* p, double* u, double* v, double* w) {
+void oracle_project_bc(int nx, int ny, int nz, double h, double dt, const double* F,
+                       double rho_air, double rho_water, int walls, const double* bx,
+                       const double* by, const double* bz, const double* p, double* u, double* v,
+                       double* w) {
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
@@ -350,10 +370,29 @@ void oracle_project(int nx, int ny, int nz, double h, double dt, const double* F
                     v[f] = v[f] - dt * (by[c] * ((p[c] - p[c - nx]) / h));
                 }
                 if (k > 0) w[c] = w[c] - dt * (bz[c] * ((p[c] - p[c - sxy]) / h));
+                const double rho = rho_air + F[c] * (rho_water - rho_air);
                 if (k == nz - 1) {
-                    const double rho = rho_air + F[c] * (rho_water - rho_air);
                     const idx_t f = c + sxy;
                     w[f] = w[f] - dt * ((2.0 / rho) * ((0.0 - p[c]) / h));
                 }
+                /* Dirichlet walls: p = 0 on the wall face, half a cell from the centre */
+                const idx_t fu = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                const idx_t fv = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
+                if ((walls & OR_WALL_XM) && i == 0)
+                    u[fu] = u[fu] - dt * ((2.0 / rho) * ((p[c] - 0.0) / h));
+                if ((walls & OR_WALL_XP) && i == nx - 1)
+                    u[fu + 1] = u[fu + 1] - dt * ((2.0 / rho) * ((0.0 - p[c]) / h));
+                if ((walls & OR_WALL_YM) && j == 0)
+                    v[fv] = v[fv] - dt * ((2.0 / rho) * ((p[c] - 0.0) / h));
+                if ((walls & OR_WALL_YP) && j == ny - 1)
+                    v[fv + nx] = v[fv + nx] - dt * ((2.0 / rho) * ((0.0 - p[c]) / h));
+                if ((walls & OR_WALL_ZM) && k == 0)
+                    w[c] = w[c] - dt * ((2.0 / rho) * ((p[c] - 0.0) / h));
             }
+}
+
+void oracle_project(int nx, int ny, int nz, double h, double dt, const double* F, double rho_air,
+                    double rho_water, const double* bx, const double* by, const double* bz,
+                    const double* p, double* u, double* v, double* w) {
+    oracle_project_bc(nx, ny, nz, h, dt, F, rho_air, rho_water, 0, bx, by, bz, p, u, v, w);
 }

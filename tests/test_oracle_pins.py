@@ -345,6 +345,71 @@ def test_warm_start_from_solution_takes_no_iterations():
     assert again.iters == 0
 
 
+# ------------------------------------------------------------------------------- wall variants
+def _mode_1d(n, a, low_dirichlet, high_dirichlet):
+    """Closed-form eigenvector of the 1-D cell-centred second difference with the given wall
+    conditions (p = 0 on a Dirichlet wall face, zero gradient on the others) and its eigenvalue:
+    N-N cos(pi a (i+1/2)/n), lambda 4 sin^2(pi a/2n); N-D cos(pi (a+1/2)(i+1/2)/n) and D-N
+    sin(pi (a+1/2)(i+1/2)/n), lambda 4 sin^2(pi (2a+1)/4n); D-D sin(pi (a+1)(i+1/2)/n),
+    lambda 4 sin^2(pi (a+1)/2n)."""
+    i = np.arange(n) + 0.5
+    if not low_dirichlet and not high_dirichlet:
+        th = math.pi * a / n
+        return np.cos(th * i), 4 * math.sin(th / 2) ** 2
+    if low_dirichlet and high_dirichlet:
+        th = math.pi * (a + 1) / n
+        return np.sin(th * i), 4 * math.sin(th / 2) ** 2
+    th = math.pi * (a + 0.5) / n
+    return (np.sin(th * i) if low_dirichlet else np.cos(th * i)), 4 * math.sin(th / 2) ** 2
+
+
+@pytest.mark.parametrize("walls", [1, 2, 3, 4 | 8, 16, 1 | 8 | 16, 31])
+@pytest.mark.parametrize("shape,modes", [((6, 5, 7), (1, 2, 0)), ((4, 8, 3), (0, 3, 2))])
+def test_dirichlet_wall_eigenvectors(walls, shape, modes):
+    """At constant density every wall mask has separable closed-form eigenvectors: products of
+    the 1-D modes of each axis under its pair of wall conditions (the top face is always
+    Dirichlet).  A v = lambda v to rounding pins each wall's diagonal term."""
+    nz, ny, nx = shape
+    vx, lx = _mode_1d(nx, modes[0], walls & 1, walls & 2)
+    vy, ly = _mode_1d(ny, modes[1], walls & 4, walls & 8)
+    vz, lz = _mode_1d(nz, modes[2], walls & 16, True)
+    v = vz[:, None, None] * vy[None, :, None] * vx[None, None, :]
+    op = oracle.operator(np.zeros(shape), RHO_A, RHO_W, walls=walls)
+    lam = lx + ly + lz
+    assert np.abs(oracle.apply(op, v) - lam * v).max() <= 1e-12 * max(1.0, lam)
+
+
+@pytest.mark.parametrize("walls", [3, 16, 31])
+def test_dirichlet_walls_pcg_matches_dense_lu(walls):
+    shape = (5, 4, 6)
+    op = oracle.operator(_rand_F(shape, 17), RHO_A, RHO_W, walls=walls)
+    A = _dense(op)
+    assert np.allclose(A, A.T, rtol=0, atol=1e-12)
+    b = np.random.default_rng(18).standard_normal(shape)
+    ref = scipy.linalg.solve(A, b.ravel(), assume_a="sym").reshape(shape)
+    res = oracle.pcg(op, b, tol=1e-14)
+    assert res.status == oracle.OK
+    assert np.linalg.norm(res.x - ref) / np.linalg.norm(ref) <= 1e-11
+
+
+@pytest.mark.parametrize("walls", [1, 2, 4, 8, 16, 31])
+def test_projection_with_dirichlet_walls_leaves_the_residual(walls):
+    shape, h, dt = (5, 6, 7), 1.0 / 8, 2e-3
+    F = _rand_F(shape, 94)
+    op = oracle.operator(F, RHO_A, RHO_W, walls=walls)
+    u, v, w = _faces(shape, 95)
+    p = np.random.default_rng(96).standard_normal(shape)
+    b = oracle.rhs(oracle.divergence(u, v, w, h, dt), h)
+    un, vn, wn = oracle.project(op, F, u, v, w, p, h, dt, RHO_A, RHO_W)
+    r, _ = oracle.residual(op, b, p)
+    div = oracle.divergence(un, vn, wn, h, dt)
+    scale = (np.abs(b) + np.abs(oracle.apply(op, p))).max() / h ** 2
+    assert np.abs(div + r / h ** 2).max() <= 1e-13 * scale
+    # a Dirichlet wall's faces move, a zero-gradient wall's do not
+    assert np.array_equal(un[:, :, 0], u[:, :, 0]) == (not walls & 1)
+    assert np.array_equal(wn[0], w[0]) == (not walls & 16)
+
+
 # ------------------------------------------------------------------------------- projection
 def _faces(shape, seed):
     nz, ny, nx = shape
