@@ -34,6 +34,14 @@ extern "C" {
 #endif
 
 /* ------------------------------------------------------------------ status codes */
+/* Walls of poisson_opts.dirichlet_walls */
+#define POISSON_WALL_XM 1   /* x = 0  */
+#define POISSON_WALL_XP 2   /* x = Lx */
+#define POISSON_WALL_YM 4   /* y = 0  */
+#define POISSON_WALL_YP 8   /* y = Ly */
+#define POISSON_WALL_ZM 16  /* z = 0 (the bottom) */
+#define POISSON_WALLS_ALL 31
+
 #define POISSON_OK 0
 #define POISSON_PENDING 1            /* poisson_poll: solve still running */
 #define POISSON_EINVAL (-1)          /* bad argument: size <= 0, h <= 0, tol <= 0, NULL, ...  */
@@ -82,6 +90,11 @@ typedef struct {
                           0 equal planes per CTA, 1 balanced (segment start cost counted), 2
                           lockstep (neighbouring tiles on the same planes) (default 0)          */
     void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream                 */
+    int dirichlet_walls; /* side/bottom walls with p = 0 on the wall face instead of a zero normal
+                          gradient: a bitmask of POISSON_WALL_* (default 0, the paper's walls);
+                          the top face z = Lz always has p = 0.  Each such wall adds 2/rho_c to
+                          the diagonal of the cells that touch it and, in poisson_project, its
+                          face is corrected with 1/rho_c over the half cell.                    */
 } poisson_opts;
 
 typedef struct {
@@ -199,7 +212,9 @@ int poisson_divergence(poisson_t* h, const double* u, const double* v, const dou
 /* In place, on every face: u_f <- u_f - dt (beta_f ((p_n - p_c) / h)) with the face coefficients
  * of the last poisson_set_density (beta_f = 2/(rho_c + rho_n); (p_n - p_c) across the face in
  * the +axis direction); on the top face, where p = 0, u_f <- u_f - dt ((2/rho_c)((0 - p_c)/h)),
- * i.e. 1/rho_c times the gradient over the half cell; wall faces are left as they are.  Then
+ * i.e. 1/rho_c times the gradient over the half cell, and the same on the faces of the handle's
+ * Dirichlet walls (poisson_opts.dirichlet_walls); zero-gradient wall faces are left as they are.
+ * Then
  * div_h(u)/dt = div_h(u*)/dt - div_h((1/rho) grad_h p): with p from poisson_solve for
  * s = div(u*)/dt, the divergence left is the solve's residual, (A p - b)/h^2.  p: nx*ny*nz
  * doubles.  Errors: EINVAL, ENOTREADY (before set_density), ENOMEM, ECUDA. */
@@ -212,7 +227,7 @@ int poisson_project(poisson_t* h, double* u, double* v, double* w, const double*
  * to another allocator under a fixed budget, or code that forbids dynamic allocation after
  * initialisation.  It computes the FP64 relative residual ||b - A p||_2 / ||b||_2 (b = -h^2 rhs,
  * A the FP64 operator of eq. (pois) built on the fly from F, rho_air, rho_water as in
- * poisson_set_density) -- the figure poisson_solve reports in stats->rel_residual -- without any
+ * poisson_set_density, with the paper's walls: zero normal gradient on the sides and bottom) -- the figure poisson_solve reports in stats->rel_residual -- without any
  * handle and without allocating: its only scratch is a 64 KiB static device array of the
  * library, which every GPU that loads the library holds until the process exits.
  *   F, rhs, p: device arrays of nx*ny*nz doubles (x fastest); host arrays give EINVAL.

@@ -72,6 +72,7 @@ extern "C" void poisson_default_opts(poisson_opts* o) {
     o->inner_tol = 1e-4;
     o->tile = 0;
     o->stream = nullptr;
+    o->dirichlet_walls = 0;
 }
 
 // z-chunk per thread: about 2048 blocks per launch, at least one plane per thread.
@@ -235,7 +236,7 @@ static int setup_march(poisson_t* H) {
 }
 
 static void free_state(poisson_t* H) {
-    void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->top64, H->eta32, H->eta16, H->x64,
+    void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->top64, H->rinv2, H->eta32, H->eta16, H->x64,
                     H->b64, H->r64, H->z64, H->p64a, H->p64b, H->d32, H->r32, H->z32,
                     H->p32a, H->p32b, H->s32a, H->s32b, H->w32a, H->w32b, H->sc,
                     H->partials, H->io_a, H->io_b, H->io_c, H->io_c32};
@@ -277,10 +278,11 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (o.max_iters <= 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return POISSON_EINVAL;
     if (o.tile < -1 || (o.tile > 0 && march_variant_of_tile(o.tile) < 0))
         return POISSON_EINVAL;
+    if (o.dirichlet_walls < 0 || o.dirichlet_walls > POISSON_WALLS_ALL) return POISSON_EINVAL;
 
     poisson_t* H = new (std::nothrow) poisson_t();
     if (!H) return POISSON_ENOMEM;
-    H->d = Dims{nx, ny, nz, nx * ny, (int)n};
+    H->d = Dims{nx, ny, nz, nx * ny, (int)n, o.dirichlet_walls};
     H->h = h;
     H->opts = o;
     H->st = (cudaStream_t)o.stream;
@@ -294,6 +296,7 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     const size_t N = (size_t)n;
     A(dalloc(&H->bx, N)); A(dalloc(&H->by, N)); A(dalloc(&H->bz, N)); A(dalloc(&H->diag, N));
     A(dalloc(&H->top64, (size_t)nx * ny));
+    if (o.dirichlet_walls) A(dalloc(&H->rinv2, N));
     A(dalloc(&H->eta32, N)); A(dalloc(&H->eta16, N));
     A(dalloc(&H->x64, N)); A(dalloc(&H->b64, N));
     if (o.precision == POISSON_FP64) {
@@ -355,7 +358,7 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
         Fd = H->b64;
     }
     launch_setup(H->d, Fd, rho_air, rho_water, H->bx, H->by, H->bz, H->diag, H->dinv, H->top64,
-                 H->eta32, H->eta16, H->st);
+                 H->rinv2, H->eta32, H->eta16, H->st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(H->st));
     H->ready = true;

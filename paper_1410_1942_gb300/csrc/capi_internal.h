@@ -25,6 +25,9 @@ struct poisson_s {
     // 2/rho_c of the top layer (nx*ny): the coefficient of the Dirichlet top face, for the
     // velocity correction of poisson_project
     double* top64 = nullptr;
+    // 2/rho_c per cell, only when the handle has Dirichlet side/bottom walls (their faces in
+    // poisson_project)
+    double* rinv2 = nullptr;
     // rho / 2 per cell for the reduced-precision inner operator
     float* eta32 = nullptr;
     __nv_bfloat16* eta16 = nullptr;

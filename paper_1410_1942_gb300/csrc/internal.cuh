@@ -22,9 +22,19 @@ namespace pcg {
 
 struct Dims {
     int nx, ny, nz;
-    int sxy;  // nx * ny
-    int n;    // nx * ny * nz (< 2^31, checked at create)
+    int sxy;        // nx * ny
+    int n;          // nx * ny * nz (< 2^31, checked at create)
+    int walls = 0;  // side/bottom walls with p = 0 (POISSON_WALL_* bits); the top always has p = 0
 };
+
+// The number of Dirichlet side/bottom walls cell (i, j, k) touches: each adds 2/rho_c (1/eta_c)
+// to its diagonal, like the top face of the last layer.
+__host__ __device__ __forceinline__ int dirichlet_walls(const Dims& d, int i, int j, int k) {
+    if (!d.walls) return 0;
+    return ((d.walls & 1) && i == 0) + ((d.walls & 2) && i == d.nx - 1) +
+           ((d.walls & 4) && j == 0) + ((d.walls & 8) && j == d.ny - 1) +
+           ((d.walls & 16) && k == 0);
+}
 
 // Per-solve CG scalars, updated on the device by the last block of each reduction.
 struct Scalars {
@@ -172,6 +182,7 @@ struct CoefEta {
         const float wzp = top ? rcp_approx(ec) : rcp_approx(ec + eta_load(eta, c + d.sxy));
         w.zp = top ? 0.f : wzp;
         w.D = w.xm + w.xp + w.ym + w.yp + w.zm + wzp;
+        for (int q = dirichlet_walls(d, i, j, k); q > 0; --q) w.D += rcp_approx(ec);
     }
 };
 

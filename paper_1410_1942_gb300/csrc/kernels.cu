@@ -44,12 +44,14 @@ __global__ void k_setup_faces(Dims d, const double* __restrict__ F, double ra, d
     if (eta16) eta16[c] = __float2bfloat16_rn((float)e);
 }
 
-// diag = bx[c] + by[c] + bz[c] + high faces (+ 2/rho_c on the top layer), summed in that order;
-// top[i + nx j] = 2/rho_c of the top layer.
+// diag = bx[c] + by[c] + bz[c] + high faces (+ 2/rho_c on the top layer) (+ 2/rho_c for each
+// Dirichlet side/bottom wall the cell touches, x-, x+, y-, y+, z-), summed in that order;
+// top[i + nx j] = 2/rho_c of the top layer; rinv2[c] = 2/rho_c (only with Dirichlet walls).
 __global__ void k_setup_diag(Dims d, const double* __restrict__ F, double ra, double rw,
                              const double* __restrict__ bx, const double* __restrict__ by,
                              const double* __restrict__ bz, double* __restrict__ diag,
-                             double* __restrict__ dinv, double* __restrict__ top) {
+                             double* __restrict__ dinv, double* __restrict__ top,
+                             double* __restrict__ rinv2) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= d.n) return;
     const int c = (int)tid;
@@ -63,6 +65,15 @@ __global__ void k_setup_diag(Dims d, const double* __restrict__ F, double ra, do
         const double t = 2.0 / rho_of(F[c], ra, rw);
         s = __dadd_rn(s, t);
         if (top) top[c - k * d.sxy] = t;
+    }
+    if (d.walls) {
+        const double t = 2.0 / rho_of(F[c], ra, rw);
+        if ((d.walls & 1) && i == 0) s = __dadd_rn(s, t);
+        if ((d.walls & 2) && i == d.nx - 1) s = __dadd_rn(s, t);
+        if ((d.walls & 4) && j == 0) s = __dadd_rn(s, t);
+        if ((d.walls & 8) && j == d.ny - 1) s = __dadd_rn(s, t);
+        if ((d.walls & 16) && k == 0) s = __dadd_rn(s, t);
+        if (rinv2) rinv2[c] = t;
     }
     diag[c] = s;
     if (dinv) dinv[c] = 1.0 / s;
@@ -583,10 +594,10 @@ static inline dim3 grid_of(const Dims& d, int kc) {
 static inline unsigned blocks1d(long long n) { return (unsigned)((n + 255) / 256); }
 
 void launch_setup(const Dims& d, const double* F, double ra, double rw, double* bx, double* by,
-                  double* bz, double* diag, double* dinv, double* top, float* eta32,
-                  __nv_bfloat16* eta16, cudaStream_t st) {
+                  double* bz, double* diag, double* dinv, double* top, double* rinv2,
+                  float* eta32, __nv_bfloat16* eta16, cudaStream_t st) {
     k_setup_faces<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, eta32, eta16);
-    k_setup_diag<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, diag, dinv, top);
+    k_setup_diag<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, diag, dinv, top, rinv2);
     counted(2);
 }
 

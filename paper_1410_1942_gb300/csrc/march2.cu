@@ -243,7 +243,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
                 f.zm = face(m > 0, ec, ev(q - 1, xx, yy));
                 f.zp = face(m + 1 < d.nz, ec, ev(q + 1, xx, yy));
                 f.zt = (m + 1 == d.nz) ? rcp_approx(ec) : f.zp;
-                const float D = diag_of(f);
+                float D = diag_of(f);
+                for (int w = dirichlet_walls(d, i, j, m); w > 0; --w) D = __fadd_rn(D, rcp_approx(ec));
                 const float Ap = apply_cell(f, D, pv(q, xx, yy), pv(q, xx - 1, yy), pv(q, xx + 1, yy),
                                             pv(q, xx, yy - 1), pv(q, xx, yy + 1), pv(q - 1, xx, yy),
                                             pv(q + 1, xx, yy));
@@ -301,7 +302,9 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
                         f.zp = face(k + 1 < d.nz, ec, ev(q + 1, xx, yy));
                         f.zt = (k + 1 == d.nz) ? rcp_approx(ec) : f.zp;
                         wzl[y][x] = f.zp;
-                        const float D = diag_of(f);
+                        float D = diag_of(f);
+                        for (int w = dirichlet_walls(d, i, j, k); w > 0; --w)
+                            D = __fadd_rn(D, rcp_approx(ec));
                         const float c = uk[y][x];
                         const float Au = apply_cell(f, D, c, B[bidx(xx - 1, yy)], B[bidx(xx + 1, yy)],
                                                     B[bidx(xx, yy - 1)], B[bidx(xx, yy + 1)],

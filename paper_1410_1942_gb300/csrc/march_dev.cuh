@@ -120,6 +120,8 @@ __device__ __forceinline__ void stencil(const Dims& d, int i0, int j0, int k,
             const float wxm = fx[a][b], wxp = fx[a][b + 1];
             const float wym = fy[a][b], wyp = fy[a + 1][b];
             D[a][b] = wxm + wxp + wym + wyp + wzl[a][b] + wzt;
+            for (int w = dirichlet_walls(d, i0 + b, j0 + a, k); w > 0; --w)
+                D[a][b] += rcp_approx(ec[a][b]);
             const float pxm = (b == 0) ? vxm[a] : cen[a][b > 0 ? b - 1 : 0];
             const float pxp = (b == CX - 1) ? vxp[a] : cen[a][b < CX - 1 ? b + 1 : b];
             const float pym = (a == 0) ? vym[b] : cen[a > 0 ? a - 1 : 0][b];

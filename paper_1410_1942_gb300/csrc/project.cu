@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(PT) k_project(Dims d, double h, double dt,
                                                 const double* __restrict__ by,
                                                 const double* __restrict__ bz,
                                                 const double* __restrict__ top,
+                                                const double* __restrict__ rinv2,
                                                 const double* __restrict__ p, double* __restrict__ u,
                                                 double* __restrict__ v, double* __restrict__ w) {
     const long long t = blockIdx.x * (long long)PT + threadIdx.x;
@@ -75,6 +76,17 @@ __global__ void __launch_bounds__(PT) k_project(Dims d, double h, double dt,
         // top face: p = 0 there; (1/rho_c) (0 - p_c) / (h/2) = (2/rho_c) ((0 - p_c) / h)
         const long long f = c + (long long)d.sxy;
         w[f] = corrected(w[f], dt, top[c - k * d.sxy], 0.0, pc, h);
+    }
+    if (d.walls) {
+        // Dirichlet walls: p = 0 on the wall face, (2/rho_c) times the difference to 0 over h
+        const double t = rinv2[c];
+        const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+        const long long fv = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+        if ((d.walls & 1) && i == 0) u[fu] = corrected(u[fu], dt, t, pc, 0.0, h);
+        if ((d.walls & 2) && i == d.nx - 1) u[fu + 1] = corrected(u[fu + 1], dt, t, 0.0, pc, h);
+        if ((d.walls & 4) && j == 0) v[fv] = corrected(v[fv], dt, t, pc, 0.0, h);
+        if ((d.walls & 8) && j == d.ny - 1) v[fv + d.nx] = corrected(v[fv + d.nx], dt, t, 0.0, pc, h);
+        if ((d.walls & 16) && k == 0) w[c] = corrected(w[c], dt, t, pc, 0.0, h);
     }
 }
 
@@ -168,7 +180,7 @@ extern "C" int poisson_project(poisson_t* H, double* u, double* v, double* w, co
         return rc;
     }
     k_project<<<blocks_of(d.n), PT, 0, H->st>>>(d, H->h, dt, H->bx, H->by, H->bz, H->top64,
-                                                P.dev, U.dev, V.dev, W.dev);
+                                                H->rinv2, P.dev, U.dev, V.dev, W.dev);
     pcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     if (cudaGetLastError() != cudaSuccess) rc = POISSON_ECUDA;
     if (rc == POISSON_OK) rc = U.flush(H->st);

@@ -60,3 +60,26 @@ def test_create_rejects_bad_sizes_before_touching_the_gpu(lib):
     o = capi.default_opts()
     o.omega = 2.0
     assert lib.poisson_create(4, 4, 4, 0.1, ctypes.byref(o), ctypes.byref(h)) == capi.EINVAL
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of poisson_opts, poisson_stats and poisson_kernel_times have the C
+    structs' sizes and field offsets (compiled from the header with the host compiler)."""
+    checks = {"poisson_opts": capi.Opts, "poisson_stats": capi.Stats,
+              "poisson_kernel_times": capi.KernelTimes}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "poisson.h"', "int main(void) {"]
+    for cname, cls in checks.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for field, _ in cls._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, field, cname, field))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True,
+                                                        text=True).stdout.splitlines())
+    for cname, cls in checks.items():
+        assert int(got[cname]) == ctypes.sizeof(cls), cname
+        for field, _ in cls._fields_:
+            assert int(got["%s.%s" % (cname, field)]) == getattr(cls, field).offset, (cname, field)

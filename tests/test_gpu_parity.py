@@ -394,6 +394,52 @@ def test_capped_solve_returns_the_k_th_iterate(tile, k):
     assert np.linalg.norm(p - ref) <= 1e-4 * np.linalg.norm(ref)
 
 
+# ----------------------------------------------------------------------------- wall variants
+WALL_CASES = [1 | 2, 4 | 8 | 16, 31]
+
+
+@pytest.mark.parametrize("walls", WALL_CASES)
+def test_dirichlet_walls_operator_bit_exact(walls):
+    c = inputs.flat_case(37, 23, 19, seed=2, tol=1e-10)
+    op = oracle.operator(c.F, walls=walls)
+    with solver(c, "fp64", dirichlet_walls=walls) as s:
+        arrs = [np.empty(c.grid.shape) for _ in range(4)]
+        s.get_operator(*arrs)
+        x = np.random.default_rng(3).standard_normal(c.grid.shape)
+        y = np.empty_like(x)
+        s.apply(x, y, "fp64")
+    for got, ref in zip(arrs, (op.bx, op.by, op.bz, op.diag)):
+        assert np.array_equal(got, ref)
+    assert np.all(np.abs(y - oracle.apply(op, x)) <= APPLY_TOL["fp64"] * op.diag * np.abs(x).max())
+
+
+@pytest.mark.parametrize("walls", WALL_CASES)
+@pytest.mark.parametrize("prec,tile,precond", [("fp64", 0, "jacobi"), ("fp64", 0, "rbssor"),
+                                               ("fp32", -1, "jacobi"), ("fp32", 0, "rbssor"),
+                                               ("fp32", 2204, "jacobi"), ("fp32", 12204, "jacobi"),
+                                               ("fp32", 12012204, "jacobi"),
+                                               ("fp32", 22012204, "jacobi"),
+                                               ("bf16", 12312208, "jacobi")])
+def test_dirichlet_walls_solve_matches_oracle(walls, prec, tile, precond):
+    """Side/bottom walls with p = 0 through every kernel family, against both criteria with the
+    oracle's operator for the same walls."""
+    c = inputs.flat_case(64, 40, 24, seed=5, tol=1e-9)
+    op = oracle.operator(c.F, walls=walls)
+    b = oracle.rhs(c.s, c.grid.h)
+    xref = oracle.pcg(op, b, tol=REF_TOL, precond="ssor").x
+    with solver(c, prec, tile=tile, precond=precond, dirichlet_walls=walls) as s:
+        p = np.zeros(c.grid.shape)
+        rc, st = s.solve(c.s, p, c.tol)
+    assert rc == capi.OK
+    _check_solution(c, op, b, xref, p, st, c.tol)
+
+
+def test_dirichlet_walls_rejects_unknown_bits():
+    with pytest.raises(capi.PoissonError) as e:
+        capi.Poisson(16, 16, 16, 1.0 / 16, dirichlet_walls=32)
+    assert e.value.status == capi.EINVAL
+
+
 # ----------------------------------------------------------------------------- full size
 @pytest.fixture(scope="module")
 def strut_full():

@@ -111,6 +111,23 @@ def test_projection_step_leaves_the_solve_residual(prec, case):
         assert np.linalg.norm(got - want) <= 2e-5 * np.linalg.norm(orig - want) + 1e-15
 
 
+@pytest.mark.parametrize("walls", [1, 2, 4, 8, 16, 31])
+def test_project_with_dirichlet_walls_bit_exact(walls):
+    nx, ny, nz = 13, 9, 7
+    shape = (nz, ny, nx)
+    F = _rand_F(shape, 8)
+    u, v, w = _faces(shape, 9)
+    p = np.random.default_rng(10).standard_normal(shape)
+    h, dt = 1.0 / 16, 1.3e-3
+    op = oracle.operator(F, walls=walls)
+    ru, rv, rw = oracle.project(op, F, u, v, w, p, h, dt)
+    with capi.Poisson(nx, ny, nz, h, dirichlet_walls=walls) as s:
+        s.set_density(F)
+        gu, gv, gw = u.copy(), v.copy(), w.copy()
+        s.project(gu, gv, gw, p, dt)
+    assert np.array_equal(gu, ru) and np.array_equal(gv, rv) and np.array_equal(gw, rw)
+
+
 def test_projection_errors():
     c = inputs.flat_case(16, 8, 8, seed=1)
     g = c.grid
