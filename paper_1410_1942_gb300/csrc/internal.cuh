@@ -27,15 +27,9 @@ struct Dims {
     int walls = 0;  // side/bottom walls with p = 0 (POISSON_WALL_* bits); the top always has p = 0
 };
 
-// The number of Dirichlet side/bottom walls cell (i, j, k) touches: each adds 2/rho_c (1/eta_c)
-// to its diagonal, like the top face of the last layer.
-__host__ __device__ __forceinline__ int dirichlet_walls(const Dims& d, int i, int j, int k) {
-    if (!d.walls) return 0;
-    return ((d.walls & 1) && i == 0) + ((d.walls & 2) && i == d.nx - 1) +
-           ((d.walls & 4) && j == 0) + ((d.walls & 8) && j == d.ny - 1) +
-           ((d.walls & 16) && k == 0);
-}
-
+// A Dirichlet side/bottom wall (Dims::walls bit) puts p = 0 on its face: the wall face gets the
+// coefficient 2/rho_c = 1/eta_c, which counts in the diagonal, while the value beyond the wall
+// contributes nothing (the kernels read it as 0: zero-filled halo, or no neighbour term).
 // Per-solve CG scalars, updated on the device by the last block of each reduction.
 struct Scalars {
     double rz;      // (r, z) of the current iterate
@@ -173,16 +167,17 @@ struct CoefEta {
     __device__ __forceinline__ void weights(const Dims& d, int c, int i, int j, int k,
                                             Stencil<float>& w) const {
         const float ec = eta_load(eta, c);
-        w.xm = (i > 0) ? rcp_approx(ec + eta_load(eta, c - 1)) : 0.f;
-        w.xp = (i + 1 < d.nx) ? rcp_approx(ec + eta_load(eta, c + 1)) : 0.f;
-        w.ym = (j > 0) ? rcp_approx(ec + eta_load(eta, c - d.nx)) : 0.f;
-        w.yp = (j + 1 < d.ny) ? rcp_approx(ec + eta_load(eta, c + d.nx)) : 0.f;
-        w.zm = (k > 0) ? rcp_approx(ec + eta_load(eta, c - d.sxy)) : 0.f;
+        // at a Dirichlet wall the face coefficient is 1/eta_c (nb_sum never reads past the wall)
+        const float ew = rcp_approx(ec);
+        w.xm = (i > 0) ? rcp_approx(ec + eta_load(eta, c - 1)) : ((d.walls & 1) ? ew : 0.f);
+        w.xp = (i + 1 < d.nx) ? rcp_approx(ec + eta_load(eta, c + 1)) : ((d.walls & 2) ? ew : 0.f);
+        w.ym = (j > 0) ? rcp_approx(ec + eta_load(eta, c - d.nx)) : ((d.walls & 4) ? ew : 0.f);
+        w.yp = (j + 1 < d.ny) ? rcp_approx(ec + eta_load(eta, c + d.nx)) : ((d.walls & 8) ? ew : 0.f);
+        w.zm = (k > 0) ? rcp_approx(ec + eta_load(eta, c - d.sxy)) : ((d.walls & 16) ? ew : 0.f);
         const bool top = (k + 1 == d.nz);
         const float wzp = top ? rcp_approx(ec) : rcp_approx(ec + eta_load(eta, c + d.sxy));
         w.zp = top ? 0.f : wzp;
         w.D = w.xm + w.xp + w.ym + w.yp + w.zm + wzp;
-        for (int q = dirichlet_walls(d, i, j, k); q > 0; --q) w.D += rcp_approx(ec);
     }
 };
 

@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
             const Dims d = s_sol[l].d;
             const float coefv = (float)(a_side ? s_sol[l].beta : s_sol[l].alpha);
             const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * ty;
+            const unsigned edges = block_edges<CX, CY>(d, i0, j0);
             auto centre = [&](int q, float (&o)[CY][CX]) {
                 const unsigned char* S = stage(q);
                 if (a_side) {
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
                 for (int y = 0; y < CY; ++y)
 #pragma unroll
                     for (int x = 0; x < CX; ++x)
-                        wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
+                        wzl[y][x] = (sg.k0 > 0 || (d.walls & 16)) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
             }
             float acc0 = 0.f, acc1 = 0.f;
             for (int k = sg.k0; k < sg.k1; ++k) {
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
                 float exm[CY], exq[CY], eym[CX], eyp[CX];
                 load_halo<CX, CY>(eta_of(qc), G::EW, r0, ce, exm, exq, eym, eyp);
                 float qv[CY][CX], D[CY][CX];
-                stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym,
+                stencil<CX, CY>(d, edges, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym,
                                 eyp, ep, wzl, qv, D);
                 if (a_side) {
                     float* p_out = p_in_a ? s_sol[l].pb : s_sol[l].pa;
@@ -594,6 +595,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
             const Dims d = s_sol[l].d;
             const float coefv = (float)(a_side ? s_sol[l].beta : s_sol[l].alpha);
             const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * warp;
+            const unsigned edges = block_edges<CX, CY>(d, i0, j0);
             auto centre = [&](int q, float (&o)[CY][CX]) {
                 const unsigned char* S = stage(q);
                 if (a_side) {
@@ -625,7 +627,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
                 for (int y = 0; y < CY; ++y)
 #pragma unroll
                     for (int x = 0; x < CX; ++x)
-                        wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
+                        wzl[y][x] = (sg.k0 > 0 || (d.walls & 16)) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
             }
             float acc0 = 0.f, acc1 = 0.f;
             for (int k = sg.k0; k < sg.k1; ++k) {
@@ -657,7 +659,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
                     float exm[CY], exq[CY], eym[CX], eyp[CX];
                     load_halo<CX, CY>(eta_of(qc), G::EW, r0, ce, exm, exq, eym, eyp);
                     float qv[CY][CX], D[CY][CX];
-                    stencil<CX, CY>(d, i0, j0, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym,
+                    stencil<CX, CY>(d, edges, k, vc, vxm, vxp, vym, vyp, vm, vp, ec, exm, exq, eym,
                                     eyp, ep, wzl, qv, D);
                     if (a_side) {
                         float* p_out = p_in_a ? s_sol[l].pb : s_sol[l].pa;

@@ -103,7 +103,10 @@ struct PcgArgs {
 
 // Parts of a persistent-PCG iteration timed by the optional trace (CTA 0's view).
 // TR_IMB: CTA 0's arrival to the last CTA's arrival; TR_REL: last arrival to CTA 0's release.
-enum { TR_A = 0, TR_BAR1, TR_ALPHA, TR_B, TR_BAR2, TR_BETA, TR_ITERS, TR_IMB, TR_REL, TRACE_PARTS };
+// One-sweep kernels: TR_SUM the cross-CTA sums, TR_DECIDE the scalar recurrences (both inside
+// TR_ALPHA).
+enum { TR_A = 0, TR_BAR1, TR_ALPHA, TR_B, TR_BAR2, TR_BETA, TR_ITERS, TR_IMB, TR_REL, TR_SUM,
+       TR_DECIDE, TRACE_PARTS };
 
 bool march_supported(const Dims& d);
 int march_variant_count();

@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             const float alp = (float)s_sol[l].alpha_prev;
             const bool xs = x_sweep(s_sol[l]);
             const int i0 = sg.x0 + CX * tx, j0 = sg.y0 + CY * warp;
+            const unsigned edges = block_edges<CX, CY>(d, i0, j0);
             // u' of the thread's own block in plane q
             auto u_centre = [&](int q, float (&o)[CY][CX]) {
                 const unsigned char* S = stage(q);
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                 for (int y = 0; y < CY; ++y)
 #pragma unroll
                     for (int x = 0; x < CX; ++x)
-                        wzl[y][x] = (sg.k0 > 0) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
+                        wzl[y][x] = (sg.k0 > 0 || (d.walls & 16)) ? rcp_approx(ec[y][x] + em[y][x]) : 0.f;
             }
             float ag = 0.f, ad = 0.f, ar = 0.f;
             for (int k = sg.k0; k < sg.k1; ++k) {
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                     float exm[CY], exq[CY], eym[CX], eyp[CX];
                     load_halo<CX, CY>(eta_of(qc), G::EW, r0, ce, exm, exq, eym, eyp);
                     float qv[CY][CX], D[CY][CX];
-                    stencil<CX, CY>(d, i0, j0, k, uc, vxm, vxp, vym, vyp, um, up, ec, exm, exq, eym,
+                    stencil<CX, CY>(d, edges, k, uc, vxm, vxp, vym, vyp, um, up, ec, exm, exq, eym,
                                     eyp, ep, wzl, qv, D);
                     if (i0 < d.nx) {
                         float u0[CY][CX], s0[CY][CX], w0[CY][CX], xo[CY][CX], po[CY][CX];
@@ -346,8 +347,10 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[3];
+            unsigned long long t_s0 = tr ? globaltimer() : 0;
             range_sum<3>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, reinterpret_cast<ff*>(red),
                          tid, NT);
+            unsigned long long t_s1 = tr ? globaltimer() : 0;
             if (tid == 0) {
                 LocalSolve1& L = s_sol[l];
                 const double gn = t[0], dn = t[1], rn = t[2];
@@ -386,6 +389,11 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                     if (L.done != RUNNING && !x_updated) L.xfix = 1;
                 }
                 if (L.done != RUNNING) L.finished = 1;
+            }
+            if (tr) {
+                const unsigned long long t_s2 = globaltimer();
+                tt[TR_SUM] += t_s1 - t_s0;
+                tt[TR_DECIDE] += t_s2 - t_s1;
             }
             __syncthreads();
         }

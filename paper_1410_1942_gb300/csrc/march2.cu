@@ -236,15 +236,15 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
                 const int i = sg.x0 + xx, j = sg.y0 + yy;
                 const float ec = ev(q, xx, yy);
                 Faces f;
-                f.xm = face(i > 0, ec, ev(q, xx - 1, yy));
-                f.xp = face(i + 1 < d.nx, ec, ev(q, xx + 1, yy));
-                f.ym = face(j > 0, ec, ev(q, xx, yy - 1));
-                f.yp = face(j + 1 < d.ny, ec, ev(q, xx, yy + 1));
-                f.zm = face(m > 0, ec, ev(q - 1, xx, yy));
+                // a Dirichlet wall's face: the halo beyond the grid is zero-filled (eta = 0)
+                f.xm = face(i > 0 || (d.walls & 1), ec, ev(q, xx - 1, yy));
+                f.xp = face(i + 1 < d.nx || (d.walls & 2), ec, ev(q, xx + 1, yy));
+                f.ym = face(j > 0 || (d.walls & 4), ec, ev(q, xx, yy - 1));
+                f.yp = face(j + 1 < d.ny || (d.walls & 8), ec, ev(q, xx, yy + 1));
+                f.zm = face(m > 0 || (d.walls & 16), ec, ev(q - 1, xx, yy));
                 f.zp = face(m + 1 < d.nz, ec, ev(q + 1, xx, yy));
                 f.zt = (m + 1 == d.nz) ? rcp_approx(ec) : f.zp;
-                float D = diag_of(f);
-                for (int w = dirichlet_walls(d, i, j, m); w > 0; --w) D = __fadd_rn(D, rcp_approx(ec));
+                const float D = diag_of(f);
                 const float Ap = apply_cell(f, D, pv(q, xx, yy), pv(q, xx - 1, yy), pv(q, xx + 1, yy),
                                             pv(q, xx, yy - 1), pv(q, xx, yy + 1), pv(q - 1, xx, yy),
                                             pv(q + 1, xx, yy));
@@ -294,17 +294,15 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
                         const int i = sg.x0 + xx;
                         const float ec = ev(q, xx, yy);
                         Faces f;
-                        f.xm = face(i > 0, ec, ev(q, xx - 1, yy));
-                        f.xp = face(i + 1 < d.nx, ec, ev(q, xx + 1, yy));
-                        f.ym = face(j > 0, ec, ev(q, xx, yy - 1));
-                        f.yp = face(j + 1 < d.ny, ec, ev(q, xx, yy + 1));
+                        f.xm = face(i > 0 || (d.walls & 1), ec, ev(q, xx - 1, yy));
+                        f.xp = face(i + 1 < d.nx || (d.walls & 2), ec, ev(q, xx + 1, yy));
+                        f.ym = face(j > 0 || (d.walls & 4), ec, ev(q, xx, yy - 1));
+                        f.yp = face(j + 1 < d.ny || (d.walls & 8), ec, ev(q, xx, yy + 1));
                         f.zm = wzl[y][x];
                         f.zp = face(k + 1 < d.nz, ec, ev(q + 1, xx, yy));
                         f.zt = (k + 1 == d.nz) ? rcp_approx(ec) : f.zp;
                         wzl[y][x] = f.zp;
-                        float D = diag_of(f);
-                        for (int w = dirichlet_walls(d, i, j, k); w > 0; --w)
-                            D = __fadd_rn(D, rcp_approx(ec));
+                        const float D = diag_of(f);
                         const float c = uk[y][x];
                         const float Au = apply_cell(f, D, c, B[bidx(xx - 1, yy)], B[bidx(xx + 1, yy)],
                                                     B[bidx(xx, yy - 1)], B[bidx(xx, yy + 1)],
@@ -350,7 +348,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
                         for (int y = 0; y < CY; ++y)
 #pragma unroll
                             for (int x = 0; x < CX; ++x)
-                                wzl[y][x] = face(sg.k0 > 0, ev(q, ox + x, oy + y),
+                                wzl[y][x] = face(sg.k0 > 0 || (d.walls & 16), ev(q, ox + x, oy + y),
                                                  ev(q - 1, ox + x, oy + y));
                     }
                     stage1(q, m, ukp1);
@@ -406,8 +404,10 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[3];
+            unsigned long long t_s0 = tr ? globaltimer() : 0;
             range_sum<3>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, reinterpret_cast<ff*>(red),
                          tid, NT);
+            unsigned long long t_s1 = tr ? globaltimer() : 0;
             if (tid == 0) {
                 LocalSolve2& L = s_sol[l];
                 const double gn = t[0], dn = t[1], rn = t[2];
@@ -446,6 +446,11 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
                     if (L.done != RUNNING && !x_updated) L.xfix = 1;
                 }
                 if (L.done != RUNNING) L.finished = 1;
+            }
+            if (tr) {
+                const unsigned long long t_s2 = globaltimer();
+                tt[TR_SUM] += t_s1 - t_s0;
+                tt[TR_DECIDE] += t_s2 - t_s1;
             }
             __syncthreads();
         }

@@ -76,13 +76,32 @@ __device__ __forceinline__ void st_row(float* g, const float (&v)[CX]) {
         *g = v[0];
 }
 
+// Which faces of a thread's CX x CY block at the block's edges are open (have a coefficient):
+// bit 0 the -x faces (column i0), bit 1 the +x faces (after column i0+CX-1), bit 2 the -y faces
+// (row j0), bit 2+a the faces between rows j0+a-1 and j0+a for a = 1..CY (a = CY: the +y faces).
+// Open means inside the grid or on a Dirichlet wall (Dims::walls): a Dirichlet wall's face has
+// the coefficient 1/eta_c, which the shared expression gives because the zero-filled halo beyond
+// the grid holds eta = 0 and value 0.  Interior x faces of the block are always open (nx is a
+// multiple of 8 for these kernels).  Computed once per segment.
+template <int CX, int CY>
+__device__ __forceinline__ unsigned block_edges(const Dims& d, int i0, int j0) {
+    unsigned e = 0;
+    if (i0 > 0 || (d.walls & 1)) e |= 1u;
+    if (i0 + CX < d.nx || (d.walls & 2)) e |= 2u;
+    if (j0 > 0 || (d.walls & 4)) e |= 4u;
+#pragma unroll
+    for (int a = 1; a <= CY; ++a)
+        if (j0 + a < d.ny || (d.walls & 8)) e |= 4u << a;
+    return e;
+}
+
 // The stencil of one plane for the CX x CY block of a thread.
 //   cen: centre values of plane k (registers); vxm/vxp/vym/vyp: the block's neighbour strips in
 //   plane k; vm/vp: centre values of planes k-1 and k+1; e*: the same for eta; wzl: face to
 //   plane k-1 (0 on the floor).  Returns q = A v and the diagonal per cell, and moves wzl to the
 //   face between k and k+1 (0 at the top layer, whose Dirichlet term goes into D).
 template <int CX, int CY>
-__device__ __forceinline__ void stencil(const Dims& d, int i0, int j0, int k,
+__device__ __forceinline__ void stencil(const Dims& d, unsigned edges, int k,
                                         const float (&cen)[CY][CX], const float (&vxm)[CY],
                                         const float (&vxp)[CY], const float (&vym)[CX],
                                         const float (&vyp)[CX], const float (&vm)[CY][CX],
@@ -96,20 +115,19 @@ __device__ __forceinline__ void stencil(const Dims& d, int i0, int j0, int k,
     float fx[CY][CX + 1];
 #pragma unroll
     for (int a = 0; a < CY; ++a) {
-        fx[a][0] = (i0 > 0) ? rcp_approx(ec[a][0] + exm[a]) : 0.f;
+        fx[a][0] = (edges & 1u) ? rcp_approx(ec[a][0] + exm[a]) : 0.f;
 #pragma unroll
-        for (int b = 1; b < CX; ++b)
-            fx[a][b] = (i0 + b < d.nx) ? rcp_approx(ec[a][b - 1] + ec[a][b]) : 0.f;
-        fx[a][CX] = (i0 + CX < d.nx) ? rcp_approx(ec[a][CX - 1] + exq[a]) : 0.f;
+        for (int b = 1; b < CX; ++b) fx[a][b] = rcp_approx(ec[a][b - 1] + ec[a][b]);
+        fx[a][CX] = (edges & 2u) ? rcp_approx(ec[a][CX - 1] + exq[a]) : 0.f;
     }
     float fy[CY + 1][CX];
 #pragma unroll
     for (int b = 0; b < CX; ++b) {
-        fy[0][b] = (j0 > 0) ? rcp_approx(ec[0][b] + eym[b]) : 0.f;
+        fy[0][b] = (edges & 4u) ? rcp_approx(ec[0][b] + eym[b]) : 0.f;
 #pragma unroll
         for (int a = 1; a < CY; ++a)
-            fy[a][b] = (j0 + a < d.ny) ? rcp_approx(ec[a - 1][b] + ec[a][b]) : 0.f;
-        fy[CY][b] = (j0 + CY < d.ny) ? rcp_approx(ec[CY - 1][b] + eyp[b]) : 0.f;
+            fy[a][b] = (edges & (4u << a)) ? rcp_approx(ec[a - 1][b] + ec[a][b]) : 0.f;
+        fy[CY][b] = (edges & (4u << CY)) ? rcp_approx(ec[CY - 1][b] + eyp[b]) : 0.f;
     }
 #pragma unroll
     for (int a = 0; a < CY; ++a)
@@ -120,8 +138,6 @@ __device__ __forceinline__ void stencil(const Dims& d, int i0, int j0, int k,
             const float wxm = fx[a][b], wxp = fx[a][b + 1];
             const float wym = fy[a][b], wyp = fy[a + 1][b];
             D[a][b] = wxm + wxp + wym + wyp + wzl[a][b] + wzt;
-            for (int w = dirichlet_walls(d, i0 + b, j0 + a, k); w > 0; --w)
-                D[a][b] += rcp_approx(ec[a][b]);
             const float pxm = (b == 0) ? vxm[a] : cen[a][b > 0 ? b - 1 : 0];
             const float pxp = (b == CX - 1) ? vxp[a] : cen[a][b < CX - 1 ? b + 1 : b];
             const float pym = (a == 0) ? vym[b] : cen[a > 0 ? a - 1 : 0][b];
