@@ -133,12 +133,17 @@ class Operator:
 
 
 WALL_XM, WALL_XP, WALL_YM, WALL_YP, WALL_ZM = 1, 2, 4, 8, 16
+PERIODIC_X = 32  # in ``walls``: x periodic (no x walls)
 
 
 def operator(F, rho_air=1.0, rho_water=1000.0, mean="harmonic", walls=0):
     """Assemble the operator from the water fraction ``F`` (shape ``(nz, ny, nx)``).  ``walls``:
     bitmask of side/bottom walls with p = 0 on the wall face (WALL_XM | ...); the others, as in
-    the paper's configuration, have a zero normal gradient; the top face always has p = 0."""
+    the paper's configuration, have a zero normal gradient; the top face always has p = 0.
+    ``PERIODIC_X`` in ``walls`` makes x periodic (the strut run of the Results), with no x
+    walls; red-black SSOR then needs an even nx."""
+    if walls & PERIODIC_X and walls & (WALL_XM | WALL_XP):
+        raise ValueError("periodic x has no x walls")
     F = _f64(F)
     nz, ny, nx = F.shape
     bx, by, bz, dg = (np.empty_like(F) for _ in range(4))

@@ -85,6 +85,10 @@ void oracle_set_threads(int n) {
 #define OR_WALL_YM 4
 #define OR_WALL_YP 8
 #define OR_WALL_ZM 16
+/* periodic x: the low face of cell (0, j, k) couples it to (nx-1, j, k); no x walls.  The
+ * operator functions recognise it by that face's nonzero coefficient (it is 0 without
+ * periodicity). */
+#define OR_PERIODIC_X 32
 
 int oracle_faces_bc(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
                     int mean, int walls, double* bx, double* by, double* bz, double* diag) {
@@ -101,8 +105,8 @@ int oracle_faces_bc(int nx, int ny, int nz, const double* F, double rho_air, dou
                 idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
                 double rc = rho[c];
                 double fx = 0.0, fy = 0.0, fz = 0.0;
-                if (i > 0) {
-                    double rn = rho[c - 1];
+                if (i > 0 || (walls & OR_PERIODIC_X)) {
+                    double rn = rho[i > 0 ? c - 1 : c + nx - 1];
                     fx = (mean == OR_MEAN_HARMONIC) ? 2.0 / (rc + rn) : 0.5 * (1.0 / rc + 1.0 / rn);
                 }
                 if (j > 0) {
@@ -126,6 +130,7 @@ int oracle_faces_bc(int nx, int ny, int nz, const double* F, double rho_air, dou
                 idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
                 double d = bx[c] + by[c] + bz[c];
                 if (i + 1 < nx) d += bx[c + 1];
+                else if (walls & OR_PERIODIC_X) d += bx[c + 1 - nx];
                 if (j + 1 < ny) d += by[c + nx];
                 if (k + 1 < nz) d += bz[c + (idx_t)nx * ny];
                 else d += 2.0 / rho[c];
@@ -156,7 +161,9 @@ void oracle_apply(int nx, int ny, int nz, const double* bx, const double* by, co
                 idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
                 double v = diag[c] * x[c];
                 if (i > 0) v -= bx[c] * x[c - sx];
+                else if (bx[c] != 0.0) v -= bx[c] * x[c + nx - 1];            /* periodic x */
                 if (i + 1 < nx) v -= bx[c + sx] * x[c + sx];
+                else if (bx[c + 1 - nx] != 0.0) v -= bx[c + 1 - nx] * x[c + 1 - nx];
                 if (j > 0) v -= by[c] * x[c - sy];
                 if (j + 1 < ny) v -= by[c + sy] * x[c + sy];
                 if (k > 0) v -= bz[c] * x[c - sz];
@@ -173,7 +180,9 @@ static double nb_sum(int nx, int ny, int nz, const double* bx, const double* by,
     idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
     double s = 0.0;
     if (i > 0) s += bx[c] * v[c - sx];
+    else if (bx[c] != 0.0) s += bx[c] * v[c + nx - 1];                      /* periodic x */
     if (i + 1 < nx) s += bx[c + sx] * v[c + sx];
+    else if (bx[c + 1 - nx] != 0.0) s += bx[c + 1 - nx] * v[c + 1 - nx];
     if (j > 0) s += by[c] * v[c - sy];
     if (j + 1 < ny) s += by[c + sy] * v[c + sy];
     if (k > 0) s += bz[c] * v[c - sz];
@@ -364,6 +373,11 @@ void oracle_project_bc(int nx, int ny, int nz, double h, double dt, const double
                 if (i > 0) {
                     const idx_t f = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
                     u[f] = u[f] - dt * (bx[c] * ((p[c] - p[c - 1]) / h));
+                } else if (walls & OR_PERIODIC_X) {
+                    /* faces 0 and nx are one face: corrected from face 0, written to both */
+                    const idx_t f = (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                    u[f] = u[f] - dt * (bx[c] * ((p[c] - p[c + nx - 1]) / h));
+                    u[f + nx] = u[f];
                 }
                 if (j > 0) {
                     const idx_t f = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);

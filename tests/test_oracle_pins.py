@@ -410,6 +410,73 @@ def test_projection_with_dirichlet_walls_leaves_the_residual(walls):
     assert np.array_equal(wn[0], w[0]) == (not walls & 16)
 
 
+@pytest.mark.parametrize("walls", [oracle.PERIODIC_X, oracle.PERIODIC_X | 4 | 16])
+@pytest.mark.parametrize("shape,a", [((5, 4, 8), 3), ((3, 6, 7), 2), ((4, 2, 1), 0)])
+def test_periodic_x_eigenvectors(walls, shape, a):
+    """Periodic x: cos(2 pi a (i+1/2)/nx) and sin(...) are eigenvectors of the x second difference
+    with lambda 4 sin^2(pi a/nx); combined with the other axes' closed-form modes."""
+    nz, ny, nx = shape
+    i = np.arange(nx) + 0.5
+    lx = 4 * math.sin(math.pi * a / nx) ** 2
+    vy, ly = _mode_1d(ny, 1 if ny > 1 else 0, walls & 4, walls & 8)
+    vz, lz = _mode_1d(nz, 1, walls & 16, True)
+    op = oracle.operator(np.zeros(shape), RHO_A, RHO_W, walls=walls)
+    for vx in (np.cos(2 * math.pi * a * i / nx), np.sin(2 * math.pi * a * i / nx)):
+        v = vz[:, None, None] * vy[None, :, None] * vx[None, None, :]
+        if not np.abs(v).max():
+            continue
+        lam = lx + ly + lz
+        assert np.abs(oracle.apply(op, v) - lam * v).max() <= 1e-12 * max(1.0, lam)
+
+
+def test_periodic_x_dense_lu_and_ssor_splitting():
+    shape = (4, 3, 6)  # nx even: red-black colouring survives the wrap
+    F = _rand_F(shape, 19)
+    op = oracle.operator(F, RHO_A, RHO_W, walls=oracle.PERIODIC_X)
+    A = _dense(op)
+    assert np.allclose(A, A.T, rtol=0, atol=1e-12)
+    # the wrap couples i = 0 and i = nx-1 with the harmonic face of their densities
+    c0, c1 = 0, shape[2] - 1
+    rho = RHO_A + F.ravel() * (RHO_W - RHO_A)
+    assert A[c0, c1] == -2.0 / (rho[c0] + rho[c1])
+    b = np.random.default_rng(20).standard_normal(shape)
+    ref = scipy.linalg.solve(A, b.ravel(), assume_a="sym").reshape(shape)
+    for pc in ("jacobi", "ssor"):
+        res = oracle.pcg(op, b, tol=1e-14, precond=pc)
+        assert res.status == oracle.OK
+        assert np.linalg.norm(res.x - ref) / np.linalg.norm(ref) <= 1e-11
+    nz, ny, nx = shape
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    colour = ((ii + jj + kk) % 2).ravel()
+    perm = np.concatenate([np.flatnonzero(colour == 0), np.flatnonzero(colour == 1)])
+    Ap = A[np.ix_(perm, perm)]
+    D = np.diag(np.diag(Ap))
+    E = -np.tril(Ap, -1)
+    M = (D - E) @ np.linalg.inv(D) @ (D - E.T)
+    r = np.random.default_rng(21).standard_normal(shape)
+    zp = np.linalg.solve(M, r.ravel()[perm])
+    expect = np.empty_like(zp)
+    expect[perm] = zp
+    got = oracle.precond(op, r, "ssor", 1.0).ravel()
+    np.testing.assert_allclose(got, expect, rtol=1e-12, atol=1e-14 * np.abs(expect).max())
+
+
+def test_projection_with_periodic_x_leaves_the_residual():
+    shape, h, dt = (5, 6, 8), 1.0 / 8, 2e-3
+    F = _rand_F(shape, 97)
+    op = oracle.operator(F, RHO_A, RHO_W, walls=oracle.PERIODIC_X | 16)
+    u, v, w = _faces(shape, 98)
+    u[:, :, -1] = u[:, :, 0]  # faces 0 and nx are one face
+    p = np.random.default_rng(99).standard_normal(shape)
+    b = oracle.rhs(oracle.divergence(u, v, w, h, dt), h)
+    un, vn, wn = oracle.project(op, F, u, v, w, p, h, dt, RHO_A, RHO_W)
+    assert np.array_equal(un[:, :, 0], un[:, :, -1]) and not np.array_equal(un[:, :, 0], u[:, :, 0])
+    r, _ = oracle.residual(op, b, p)
+    div = oracle.divergence(un, vn, wn, h, dt)
+    scale = (np.abs(b) + np.abs(oracle.apply(op, p))).max() / h ** 2
+    assert np.abs(div + r / h ** 2).max() <= 1e-13 * scale
+
+
 # ------------------------------------------------------------------------------- projection
 def _faces(shape, seed):
     nz, ny, nx = shape
