@@ -95,6 +95,12 @@ typedef struct {
                           the top face z = Lz always has p = 0.  Each such wall adds 2/rho_c to
                           the diagonal of the cells that touch it and, in poisson_project, its
                           face is corrected with 1/rho_c over the half cell.                    */
+    int periodic_x;    /* 1: x periodic (the cells i = 0 and i = nx-1 of a row are neighbours
+                          through the face x = 0 = Lx, as in the paper's strut run); no x walls
+                          then (EINVAL with POISSON_WALL_XM/XP), red-black SSOR needs an even nx,
+                          and the inner solve runs on the column kernels.  Face arrays of
+                          poisson_divergence / poisson_project keep nx+1 x-faces; faces 0 and nx
+                          are the same face (poisson_project writes both).  Default 0.         */
 } poisson_opts;
 
 typedef struct {

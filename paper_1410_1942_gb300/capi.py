@@ -39,7 +39,8 @@ K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("precond", ctypes.c_int), ("omega", ctypes.c_double),
                 ("max_iters", ctypes.c_int), ("inner_tol", ctypes.c_double), ("tile", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("dirichlet_walls", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("dirichlet_walls", ctypes.c_int),
+                ("periodic_x", ctypes.c_int)]
 
 
 # poisson_opts.dirichlet_walls bits: side/bottom walls with p = 0 on the wall face
@@ -153,7 +154,8 @@ class Poisson:
     """One grid: ``poisson_create`` ... ``poisson_destroy``."""
 
     def __init__(self, nx, ny, nz, h, precision="fp32", precond="jacobi", omega=1.0,
-                 max_iters=20000, inner_tol=1e-4, tile=0, stream=None, dirichlet_walls=0):
+                 max_iters=20000, inner_tol=1e-4, tile=0, stream=None, dirichlet_walls=0,
+                 periodic_x=False):
         lib = load()
         o = default_opts()
         o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
@@ -161,6 +163,7 @@ class Poisson:
         o.omega, o.max_iters, o.inner_tol, o.tile = omega, max_iters, inner_tol, tile
         o.stream = stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream
         o.dirichlet_walls = dirichlet_walls
+        o.periodic_x = 1 if periodic_x else 0
         self.shape = (nz, ny, nx)
         self.h = h
         self.opts = o

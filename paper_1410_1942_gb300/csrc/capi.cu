@@ -73,6 +73,7 @@ extern "C" void poisson_default_opts(poisson_opts* o) {
     o->tile = 0;
     o->stream = nullptr;
     o->dirichlet_walls = 0;
+    o->periodic_x = 0;
 }
 
 // z-chunk per thread: about 2048 blocks per launch, at least one plane per thread.
@@ -279,10 +280,13 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (o.tile < -1 || (o.tile > 0 && march_variant_of_tile(o.tile) < 0))
         return POISSON_EINVAL;
     if (o.dirichlet_walls < 0 || o.dirichlet_walls > POISSON_WALLS_ALL) return POISSON_EINVAL;
+    if (o.periodic_x != 0 && o.periodic_x != 1) return POISSON_EINVAL;
+    if (o.periodic_x && (o.dirichlet_walls & (POISSON_WALL_XM | POISSON_WALL_XP))) return POISSON_EINVAL;
+    if (o.periodic_x && o.precond == POISSON_RBSSOR && nx % 2) return POISSON_EINVAL;
 
     poisson_t* H = new (std::nothrow) poisson_t();
     if (!H) return POISSON_ENOMEM;
-    H->d = Dims{nx, ny, nz, nx * ny, (int)n, o.dirichlet_walls};
+    H->d = Dims{nx, ny, nz, nx * ny, (int)n, o.dirichlet_walls | (o.periodic_x ? PERIODIC_X : 0)};
     H->h = h;
     H->opts = o;
     H->st = (cudaStream_t)o.stream;
@@ -296,7 +300,7 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     const size_t N = (size_t)n;
     A(dalloc(&H->bx, N)); A(dalloc(&H->by, N)); A(dalloc(&H->bz, N)); A(dalloc(&H->diag, N));
     A(dalloc(&H->top64, (size_t)nx * ny));
-    if (o.dirichlet_walls) A(dalloc(&H->rinv2, N));
+    if (o.dirichlet_walls) A(dalloc(&H->rinv2, N));  // (not needed for periodic x)
     A(dalloc(&H->eta32, N)); A(dalloc(&H->eta16, N));
     A(dalloc(&H->x64, N)); A(dalloc(&H->b64, N));
     if (o.precision == POISSON_FP64) {

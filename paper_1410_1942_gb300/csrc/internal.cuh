@@ -24,8 +24,11 @@ struct Dims {
     int nx, ny, nz;
     int sxy;        // nx * ny
     int n;          // nx * ny * nz (< 2^31, checked at create)
-    int walls = 0;  // side/bottom walls with p = 0 (POISSON_WALL_* bits); the top always has p = 0
+    int walls = 0;  // side/bottom walls with p = 0 (POISSON_WALL_* bits); the top always has p = 0;
+                    // bit PERIODIC_X: x periodic (cell 0 and cell nx-1 of a row are neighbours)
 };
+
+constexpr int PERIODIC_X = 32;
 
 // A Dirichlet side/bottom wall (Dims::walls bit) puts p = 0 on its face: the wall face gets the
 // coefficient 2/rho_c = 1/eta_c, which counts in the diagonal, while the value beyond the wall
@@ -142,8 +145,8 @@ struct CoefFaces64 {
     const double* dinv;  // 1/diag (FP64 Jacobi); may be null
     __device__ __forceinline__ void weights(const Dims& d, int c, int i, int j, int k,
                                             Stencil<double>& w) const {
-        w.xm = bx[c];
-        w.xp = (i + 1 < d.nx) ? bx[c + 1] : 0.0;
+        w.xm = bx[c];  // periodic x: the wrap face of cell 0, else 0 at i = 0
+        w.xp = (i + 1 < d.nx) ? bx[c + 1] : ((d.walls & PERIODIC_X) ? bx[c + 1 - d.nx] : 0.0);
         w.ym = by[c];
         w.yp = (j + 1 < d.ny) ? by[c + d.nx] : 0.0;
         w.zm = bz[c];
@@ -169,8 +172,12 @@ struct CoefEta {
         const float ec = eta_load(eta, c);
         // at a Dirichlet wall the face coefficient is 1/eta_c (nb_sum never reads past the wall)
         const float ew = rcp_approx(ec);
-        w.xm = (i > 0) ? rcp_approx(ec + eta_load(eta, c - 1)) : ((d.walls & 1) ? ew : 0.f);
-        w.xp = (i + 1 < d.nx) ? rcp_approx(ec + eta_load(eta, c + 1)) : ((d.walls & 2) ? ew : 0.f);
+        const bool per = d.walls & PERIODIC_X;
+        w.xm = (i > 0 || per) ? rcp_approx(ec + eta_load(eta, i > 0 ? c - 1 : c + d.nx - 1))
+                              : ((d.walls & 1) ? ew : 0.f);
+        w.xp = (i + 1 < d.nx || per)
+                   ? rcp_approx(ec + eta_load(eta, i + 1 < d.nx ? c + 1 : c + 1 - d.nx))
+                   : ((d.walls & 2) ? ew : 0.f);
         w.ym = (j > 0) ? rcp_approx(ec + eta_load(eta, c - d.nx)) : ((d.walls & 4) ? ew : 0.f);
         w.yp = (j + 1 < d.ny) ? rcp_approx(ec + eta_load(eta, c + d.nx)) : ((d.walls & 8) ? ew : 0.f);
         w.zm = (k > 0) ? rcp_approx(ec + eta_load(eta, c - d.sxy)) : ((d.walls & 16) ? ew : 0.f);

@@ -36,7 +36,10 @@ __global__ void k_setup_faces(Dims d, const double* __restrict__ F, double ra, d
     const int c = (int)tid;
     const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
     const double rc = rho_of(F[c], ra, rw);
-    bx[c] = (i > 0) ? 2.0 / __dadd_rn(rc, rho_of(F[c - 1], ra, rw)) : 0.0;
+    // periodic x: the low face of cell 0 couples it to cell nx-1 of its row
+    bx[c] = (i > 0 || (d.walls & PERIODIC_X))
+                ? 2.0 / __dadd_rn(rc, rho_of(F[i > 0 ? c - 1 : c + d.nx - 1], ra, rw))
+                : 0.0;
     by[c] = (j > 0) ? 2.0 / __dadd_rn(rc, rho_of(F[c - d.nx], ra, rw)) : 0.0;
     bz[c] = (k > 0) ? 2.0 / __dadd_rn(rc, rho_of(F[c - d.sxy], ra, rw)) : 0.0;
     const double e = 0.5 * rc;
@@ -58,6 +61,7 @@ __global__ void k_setup_diag(Dims d, const double* __restrict__ F, double ra, do
     const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
     double s = __dadd_rn(__dadd_rn(bx[c], by[c]), bz[c]);
     if (i + 1 < d.nx) s = __dadd_rn(s, bx[c + 1]);
+    else if (d.walls & PERIODIC_X) s = __dadd_rn(s, bx[c + 1 - d.nx]);
     if (j + 1 < d.ny) s = __dadd_rn(s, by[c + d.nx]);
     if (k + 1 < d.nz) {
         s = __dadd_rn(s, bz[c + d.sxy]);
@@ -143,8 +147,11 @@ template <typename V, typename L>
 __device__ __forceinline__ V nb_sum(const Dims& d, const Stencil<V>& w, int c, int i, int j,
                                     int k, L load) {
     V s = 0;
+    const bool per = d.walls & PERIODIC_X;
     if (i > 0) s += w.xm * load(c - 1);
+    else if (per) s += w.xm * load(c + d.nx - 1);
     if (i + 1 < d.nx) s += w.xp * load(c + 1);
+    else if (per) s += w.xp * load(c + 1 - d.nx);
     if (j > 0) s += w.ym * load(c - d.nx);
     if (j + 1 < d.ny) s += w.yp * load(c + d.nx);
     if (k > 0) s += w.zm * load(c - d.sxy);

@@ -66,6 +66,12 @@ __global__ void __launch_bounds__(PT) k_project(Dims d, double h, double dt,
     if (i > 0) {
         const long long f = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
         u[f] = corrected(u[f], dt, bx[c], pc, p[c - 1], h);
+    } else if (d.walls & pcg::PERIODIC_X) {
+        // periodic x: faces 0 and nx are one face, corrected from face 0 and written to both
+        const long long f = (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+        const double q = corrected(u[f], dt, bx[c], pc, p[c + d.nx - 1], h);
+        u[f] = q;
+        u[f + d.nx] = q;
     }
     if (j > 0) {
         const long long f = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
@@ -77,7 +83,7 @@ __global__ void __launch_bounds__(PT) k_project(Dims d, double h, double dt,
         const long long f = c + (long long)d.sxy;
         w[f] = corrected(w[f], dt, top[c - k * d.sxy], 0.0, pc, h);
     }
-    if (d.walls) {
+    if (d.walls & POISSON_WALLS_ALL) {
         // Dirichlet walls: p = 0 on the wall face, (2/rho_c) times the difference to 0 over h
         const double t = rinv2[c];
         const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);

@@ -434,6 +434,47 @@ def test_dirichlet_walls_solve_matches_oracle(walls, prec, tile, precond):
     _check_solution(c, op, b, xref, p, st, c.tol)
 
 
+PERIODIC_CASES = [0, capi.WALL_YM | capi.WALL_ZM]
+
+
+@pytest.mark.parametrize("walls", PERIODIC_CASES)
+def test_periodic_x_operator_bit_exact(walls):
+    c = inputs.flat_case(36, 23, 19, seed=4, tol=1e-10)
+    op = oracle.operator(c.F, walls=walls | oracle.PERIODIC_X)
+    with solver(c, "fp64", dirichlet_walls=walls, periodic_x=True) as s:
+        arrs = [np.empty(c.grid.shape) for _ in range(4)]
+        s.get_operator(*arrs)
+        x = np.random.default_rng(5).standard_normal(c.grid.shape)
+        y = np.empty_like(x)
+        s.apply(x, y, "fp64")
+        assert "columns" in s.describe()
+    for got, ref in zip(arrs, (op.bx, op.by, op.bz, op.diag)):
+        assert np.array_equal(got, ref)
+    assert np.all(np.abs(y - oracle.apply(op, x)) <= APPLY_TOL["fp64"] * op.diag * np.abs(x).max())
+
+
+@pytest.mark.parametrize("walls", PERIODIC_CASES)
+@pytest.mark.parametrize("prec,precond", [("fp64", "jacobi"), ("fp64", "rbssor"), ("fp32", "jacobi"),
+                                          ("fp32", "rbssor"), ("bf16", "jacobi")])
+def test_periodic_x_solve_matches_oracle(walls, prec, precond):
+    c = inputs.flat_case(48, 24, 20, seed=6, tol=1e-9)
+    op = oracle.operator(c.F, walls=walls | oracle.PERIODIC_X)
+    b = oracle.rhs(c.s, c.grid.h)
+    xref = oracle.pcg(op, b, tol=REF_TOL, precond="ssor").x
+    with solver(c, prec, precond=precond, dirichlet_walls=walls, periodic_x=True) as s:
+        p = np.zeros(c.grid.shape)
+        rc, st = s.solve(c.s, p, c.tol)
+    assert rc == capi.OK
+    _check_solution(c, op, b, xref, p, st, c.tol)
+
+
+def test_periodic_x_rejects_x_walls_and_odd_ssor():
+    for kw in ({"dirichlet_walls": capi.WALL_XM}, {"precond": "rbssor"}):
+        with pytest.raises(capi.PoissonError) as e:
+            capi.Poisson(15, 16, 16, 1.0 / 16, periodic_x=True, **kw)
+        assert e.value.status == capi.EINVAL
+
+
 def test_dirichlet_walls_rejects_unknown_bits():
     with pytest.raises(capi.PoissonError) as e:
         capi.Poisson(16, 16, 16, 1.0 / 16, dirichlet_walls=32)

@@ -128,6 +128,23 @@ def test_project_with_dirichlet_walls_bit_exact(walls):
     assert np.array_equal(gu, ru) and np.array_equal(gv, rv) and np.array_equal(gw, rw)
 
 
+def test_project_with_periodic_x_bit_exact():
+    nx, ny, nz = 12, 9, 7
+    shape = (nz, ny, nx)
+    F = _rand_F(shape, 11)
+    u, v, w = _faces(shape, 12)
+    u[:, :, -1] = u[:, :, 0]
+    p = np.random.default_rng(13).standard_normal(shape)
+    h, dt = 1.0 / 16, 1.3e-3
+    op = oracle.operator(F, walls=oracle.PERIODIC_X | oracle.WALL_ZM)
+    ru, rv, rw = oracle.project(op, F, u, v, w, p, h, dt)
+    with capi.Poisson(nx, ny, nz, h, dirichlet_walls=capi.WALL_ZM, periodic_x=True) as s:
+        s.set_density(F)
+        gu, gv, gw = u.copy(), v.copy(), w.copy()
+        s.project(gu, gv, gw, p, dt)
+    assert np.array_equal(gu, ru) and np.array_equal(gv, rv) and np.array_equal(gw, rw)
+
+
 def test_projection_errors():
     c = inputs.flat_case(16, 8, 8, seed=1)
     g = c.grid
