@@ -251,7 +251,8 @@ static void free_state(poisson_t* H) {
         unsigned long long t[TRACE_PARTS] = {};
         if (cudaMemcpy(t, H->plan.trace, sizeof(t), cudaMemcpyDeviceToHost) == cudaSuccess && t[TR_ITERS]) {
             const char* names[] = {"phaseA", "bar1", "alpha", "phaseB", "bar2", "beta", "iters",
-                                   "wait_slowest", "release", "(sums", "decide)"};
+                                   "wait_slowest", "release", "(sums_kcycles",
+                                   "decide_kcycles)"};
             fprintf(stderr, "[poisson trace] %dx%dx%d %llu iterations, us/iteration:", H->d.nx,
                     H->d.ny, H->d.nz, t[TR_ITERS]);
             for (int q = 0; q < TRACE_PARTS; ++q)

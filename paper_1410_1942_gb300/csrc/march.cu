@@ -44,8 +44,9 @@ namespace pcg {
 // barrier after each phase.  Each segment leaves its partial sums in part_a / part_b; after the
 // barrier every CTA adds, in segment order, the partials of the solves it works on and derives
 // alpha, beta and the stopping decision itself -- the same numbers in every CTA.  The CTA that
-// owns a solve's first segment publishes its final state and counts it off ctl->running; the
-// loop ends, in every CTA at once, when no solve is left running.
+// owns a solve's first segment publishes its final state; at every grid barrier each CTA adds
+// the unfinished solves it owns to the barrier's count (MarchCtl::alive), and the loop ends, in
+// every CTA at once, when a barrier's count is zero.
 //
 // Barrier waits spin on a global counter with a deadline (BAR_NS); a wait that runs out sets
 // ctl->error, marks the CTA's solves TIMEDOUT, waits (bounded) for its TMA copies in flight
@@ -97,7 +98,6 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         for (int q = 0; q < nseg; ++q)
             if (s_seg[q].slot == sv.seg_begin) L.owner = 1;
         s_member[tid] = (L.done == RUNNING);
-        if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
     }
     __syncthreads();
 
@@ -335,6 +335,13 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
     };
 
     unsigned nbar = 0;
+    int alive = 0;  // unfinished solves of the launch as of the last grid barrier
+    // unfinished solves this CTA owns (thread 0 adds them at every grid barrier)
+    auto owned_running = [&]() {
+        int c = 0;
+        for (int l = 0; l < nloc; ++l) c += (s_sol[l].owner && s_sol[l].done == RUNNING) ? 1 : 0;
+        return c;
+    };
     bool p_in_a = true;
     bool failed = false;
     const bool tr = a.trace && blockIdx.x == 0 && tid == 0;
@@ -357,10 +364,10 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         mark(TR_A);
         snapshot_members();
         ++nbar;
-        grid_arrive(a.ctl, tid, nbar * (unsigned)a.nctas, a.trace != nullptr);
+        grid_arrive(a.ctl, tid, nbar, nbar * (unsigned)a.nctas, owned_running(), a.trace != nullptr);
         const unsigned long long t_arr1 = tr ? globaltimer() : 0;
         begin_stream(false, p_in_a, true);
-        if (!grid_wait(a.ctl, nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (!grid_wait(a.ctl, nbar, nbar * (unsigned)a.nctas, tid, &alive)) { failed = true; break; }
         if (tr) {
             const unsigned long long tl = *(volatile unsigned long long*)&a.ctl->t_last;
             const unsigned long long tn = globaltimer();
@@ -369,7 +376,7 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         }
         finish_stream();
         mark(TR_BAR1);
-        if (*(volatile int*)&a.ctl->running == 0) break;
+        if (alive == 0) break;
         if (warp == 0) {
             for (int l = 0; l < nloc; ++l) {
                 if (s_sol[l].done != RUNNING) continue;
@@ -392,10 +399,10 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
         mark(TR_B);
         snapshot_members();
         ++nbar;
-        grid_arrive(a.ctl, tid, nbar * (unsigned)a.nctas, a.trace != nullptr);
+        grid_arrive(a.ctl, tid, nbar, nbar * (unsigned)a.nctas, owned_running(), a.trace != nullptr);
         const unsigned long long t_arr2 = tr ? globaltimer() : 0;
         begin_stream(true, !p_in_a, true);
-        if (!grid_wait(a.ctl, nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (!grid_wait(a.ctl, nbar, nbar * (unsigned)a.nctas, tid, &alive)) { failed = true; break; }
         if (tr) {
             const unsigned long long tl = *(volatile unsigned long long*)&a.ctl->t_last;
             const unsigned long long tn = globaltimer();
@@ -427,8 +434,8 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
                 }
                 __syncwarp();
             }
-            // owners publish the solves that finished in this iteration (the only window in
-            // which ctl->running changes: between the phase-B barrier and the next phase-A one)
+            // owners publish the solves that finished in this iteration (counted out at the next
+            // phase-A barrier)
             if (lane < nloc) {
                 LocalSolve& L = s_sol[lane];
                 if (L.finished) {
@@ -439,7 +446,6 @@ __global__ void __launch_bounds__(32 * TYT) k_pcg(PcgArgs a) {
                         L.sc->rz = L.rz;
                         L.sc->done = L.done;
                         __threadfence();
-                        atomicSub(&a.ctl->running, 1);
                     }
                 }
             }
@@ -527,7 +533,6 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
         for (int q = 0; q < nseg; ++q)
             if (s_seg[q].slot == sv.seg_begin) L.owner = 1;
         s_member[tid] = (L.done == RUNNING);
-        if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
     }
     __syncthreads();
 
@@ -726,6 +731,13 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
     };
 
     unsigned nbar = 0;
+    int alive = 0;  // unfinished solves of the launch as of the last grid barrier
+    // unfinished solves this CTA owns (thread 0 adds them at every grid barrier)
+    auto owned_running = [&]() {
+        int c = 0;
+        for (int l = 0; l < nloc; ++l) c += (s_sol[l].owner && s_sol[l].done == RUNNING) ? 1 : 0;
+        return c;
+    };
     bool p_in_a = true;
     bool failed = false;
     const bool tr = a.trace && blockIdx.x == 0 && tid == 0;
@@ -748,9 +760,13 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
         __syncthreads();
         mark(TR_A);
         if (s_fail) { failed = true; break; }
-        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        ++nbar;
+        if (!grid_barrier(a.ctl, nbar, nbar * (unsigned)a.nctas, tid, owned_running(), &alive)) {
+            failed = true;
+            break;
+        }
         mark(TR_BAR1);
-        if (*(volatile int*)&a.ctl->running == 0) break;
+        if (alive == 0) break;
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[1];
@@ -776,7 +792,11 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
         __syncthreads();
         mark(TR_B);
         if (s_fail) { failed = true; break; }
-        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        ++nbar;
+        if (!grid_barrier(a.ctl, nbar, nbar * (unsigned)a.nctas, tid, owned_running(), &alive)) {
+            failed = true;
+            break;
+        }
         mark(TR_BAR2);
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
@@ -811,7 +831,6 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_pcg
                     L.sc->rz = L.rz;
                     L.sc->done = L.done;
                     __threadfence();
-                    atomicSub(&a.ctl->running, 1);
                 }
             }
             s_member[tid] = (L.done == RUNNING);

@@ -55,12 +55,19 @@ struct Seg {
 };
 
 // Control words of one persistent launch (set by the host before the launch).
+// alive[m % 3]: at grid barrier m every CTA adds, before it arrives, the number of unfinished
+// solves it owns; once the barrier is passed the sum is complete and no CTA changes it until all
+// have left, so every CTA reads the same count and takes the same decision to stop.  CTA 0
+// clears alive[(m + 1) % 3] before it arrives at barrier m (its readers left at barrier m - 1,
+// its writers come after barrier m).
 struct MarchCtl {
     unsigned bar;  // grid-barrier arrivals (0 at launch)
-    int running;   // solves not finished (the number of solves at launch)
+    int running;   // solves at launch (informational)
     int error;     // 1 once a wait has timed out
     int pad;
     unsigned long long t_last;  // trace only: global time of the last arrival at a barrier
+    int alive[3];  // 0 at launch
+    int pad2;
 };
 
 // Work-split strategies of march_plan_build.
@@ -104,7 +111,7 @@ struct PcgArgs {
 // Parts of a persistent-PCG iteration timed by the optional trace (CTA 0's view).
 // TR_IMB: CTA 0's arrival to the last CTA's arrival; TR_REL: last arrival to CTA 0's release.
 // One-sweep kernels: TR_SUM the cross-CTA sums, TR_DECIDE the scalar recurrences (both inside
-// TR_ALPHA).
+// TR_ALPHA; in SM cycles, not ns).
 enum { TR_A = 0, TR_BAR1, TR_ALPHA, TR_B, TR_BAR2, TR_BETA, TR_ITERS, TR_IMB, TR_REL, TR_SUM,
        TR_DECIDE, TRACE_PARTS };
 

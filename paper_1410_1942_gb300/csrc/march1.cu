@@ -85,7 +85,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
     __shared__ double red[64];
     __shared__ Seg s_seg[MAXSEG];
     __shared__ LocalSolve1 s_sol[MAXSEG];
-    __shared__ int s_member[MAXSEG];
+    __shared__ int s_member[MAXSEG];  // solve streamed in the coming sweep
+    __shared__ int s_nextxs[MAXSEG];  // the coming sweep updates x (producer's copy)
     __shared__ volatile int s_fail;
     const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + 32 * ty;
     const bool producer = (ty == TYT);
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
         for (int q = 0; q < nseg; ++q)
             if (s_seg[q].slot == sv.seg_begin) L.owner = 1;
         s_member[tid] = (L.done == RUNNING);
-        if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
+        s_nextxs[tid] = 0;  // the start-up sweep leaves x alone
     }
     __syncthreads();
 
@@ -151,7 +152,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             if (!s_member[sg.solve - first]) continue;
             const int L = sg.k1 - sg.k0;
             const CUtensorMap* m = a.maps + MAPS_PER_SOLVE * sg.solve;
-            const bool xs = x_sweep(s_sol[sg.solve - first]);
+            const bool xs = s_nextxs[sg.solve - first] != 0;
             for (int off = 0; off < L + 2; ++off) {
                 if (s_fail) return;
                 const int st = np % NS, kk = sg.k0 - 1 + off;
@@ -319,6 +320,13 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
     };
 
     unsigned nbar = 0;
+    int alive = 0;  // unfinished solves of the launch as of the last grid barrier
+    // unfinished solves this CTA owns (thread 0 adds them at every grid barrier)
+    auto owned_running = [&]() {
+        int c = 0;
+        for (int l = 0; l < nloc; ++l) c += (s_sol[l].owner && s_sol[l].done == RUNNING) ? 1 : 0;
+        return c;
+    };
     int in = 0;
     bool failed = false;
     const bool tr = a.trace && blockIdx.x == 0 && tid == 0;
@@ -331,26 +339,43 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             tprev = t;
         }
     };
+    // The producer streams the next sweep as soon as a grid barrier has passed, while the
+    // consumers add the partial sums and decide; the next sweep's membership and x parity are
+    // therefore fixed just before the barrier (a solve that stops at the coming decisions is
+    // walked once more without arithmetic).
+    if (producer && lane == 0) produce(in);
     for (;;) {
-        if (producer) {
-            if (lane == 0) produce(in);
-            __syncwarp();
-        } else {
-            consume(in);
-        }
-        __syncthreads();
+        if (!producer) consume(in);
+        __syncthreads();  // the sweep is issued and consumed
         mark(TR_A);
         if (s_fail) { failed = true; break; }
-        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        if (tid < nloc) {
+            const LocalSolve1& L = s_sol[tid];
+            s_member[tid] = (L.done == RUNNING);
+            s_nextxs[tid] = L.first ? 0 : ((L.iter + 1) & 1);
+        }
+        ++nbar;
+        if (!grid_barrier(a.ctl, nbar, nbar * (unsigned)a.nctas, tid, owned_running(), &alive)) {
+            failed = true;
+            break;
+        }
         mark(TR_BAR1);
-        if (*(volatile int*)&a.ctl->running == 0) break;
+        if (alive == 0) break;
+        if (producer) {
+            if (lane == 0) produce(in ^ 1);
+            __syncwarp();
+            in ^= 1;
+            continue;
+        }
+        // consumers only from here on (named barrier 1 over NC threads)
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[3];
-            unsigned long long t_s0 = tr ? globaltimer() : 0;
+            // SM cycles (the globaltimer's granularity is too coarse for these parts)
+            const long long t_s0 = tr ? clock64() : 0;
             range_sum<3>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, reinterpret_cast<ff*>(red),
-                         tid, NT);
-            unsigned long long t_s1 = tr ? globaltimer() : 0;
+                         tid, NC, 1);
+            const long long t_s1 = tr ? clock64() : 0;
             if (tid == 0) {
                 LocalSolve1& L = s_sol[l];
                 const double gn = t[0], dn = t[1], rn = t[2];
@@ -391,11 +416,11 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                 if (L.done != RUNNING) L.finished = 1;
             }
             if (tr) {
-                const unsigned long long t_s2 = globaltimer();
-                tt[TR_SUM] += t_s1 - t_s0;
-                tt[TR_DECIDE] += t_s2 - t_s1;
+                const long long t_s2 = clock64();
+                tt[TR_SUM] += (unsigned long long)(t_s1 - t_s0);
+                tt[TR_DECIDE] += (unsigned long long)(t_s2 - t_s1);
             }
-            __syncthreads();
+            named_sync(1, NC);
         }
         // Solves that stopped after an even iteration: x_{i+1} = x_i + alpha_i p_i over this CTA's
         // cells of the solve (p_i is what this CTA stored in the sweep just done).
@@ -411,14 +436,14 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                 const int per = wd * ht;
                 const long long cnt = (long long)per * (sg.k1 - sg.k0);
                 const float al = (float)L.alpha;
-                for (long long q = tid; q < cnt; q += NT) {
+                for (long long q = tid; q < cnt; q += NC) {
                     const int k = sg.k0 + (int)(q / per), r = (int)(q % per);
                     const size_t c = (size_t)(sg.x0 + r % wd) +
                                      (size_t)nx * ((size_t)(sg.y0 + r / wd) + (size_t)ny * k);
                     L.x[c] = __fmaf_rn(al, L.p[c], L.x[c]);
                 }
             }
-            __syncthreads();
+            named_sync(1, NC);
             if (tid < nloc) s_sol[tid].xfix = 0;
         }
         mark(TR_ALPHA);
@@ -432,12 +457,10 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                     L.sc->rz = L.gamma;
                     L.sc->done = L.done;
                     __threadfence();
-                    atomicSub(&a.ctl->running, 1);
                 }
             }
-            s_member[tid] = (L.done == RUNNING);
         }
-        __syncthreads();
+        named_sync(1, NC);
         mark(TR_BETA);
         if (tr) tt[TR_ITERS] += 1;
         in ^= 1;

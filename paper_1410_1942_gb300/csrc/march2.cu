@@ -148,7 +148,6 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
         for (int q = 0; q < nseg; ++q)
             if (s_seg[q].slot == sv.seg_begin) L.owner = 1;
         s_member[tid] = (L.done == RUNNING);
-        if (L.owner && L.done != RUNNING) atomicSub(&a.ctl->running, 1);
     }
     __syncthreads();
 
@@ -376,6 +375,13 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
     };
 
     unsigned nbar = 0;
+    int alive = 0;  // unfinished solves of the launch as of the last grid barrier
+    // unfinished solves this CTA owns (thread 0 adds them at every grid barrier)
+    auto owned_running = [&]() {
+        int c = 0;
+        for (int l = 0; l < nloc; ++l) c += (s_sol[l].owner && s_sol[l].done == RUNNING) ? 1 : 0;
+        return c;
+    };
     int in = 0;
     bool failed = false;
     const bool tr = a.trace && blockIdx.x == 0 && tid == 0;
@@ -398,16 +404,21 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
         __syncthreads();
         mark(TR_A);
         if (s_fail) { failed = true; break; }
-        if (!grid_barrier(a.ctl, ++nbar * (unsigned)a.nctas, tid)) { failed = true; break; }
+        ++nbar;
+        if (!grid_barrier(a.ctl, nbar, nbar * (unsigned)a.nctas, tid, owned_running(), &alive)) {
+            failed = true;
+            break;
+        }
         mark(TR_BAR1);
-        if (*(volatile int*)&a.ctl->running == 0) break;
+        if (alive == 0) break;
         for (int l = 0; l < nloc; ++l) {
             if (s_sol[l].done != RUNNING) continue;
             double t[3];
-            unsigned long long t_s0 = tr ? globaltimer() : 0;
+            // SM cycles (the globaltimer's granularity is too coarse for these parts)
+            const long long t_s0 = tr ? clock64() : 0;
             range_sum<3>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, reinterpret_cast<ff*>(red),
                          tid, NT);
-            unsigned long long t_s1 = tr ? globaltimer() : 0;
+            const long long t_s1 = tr ? clock64() : 0;
             if (tid == 0) {
                 LocalSolve2& L = s_sol[l];
                 const double gn = t[0], dn = t[1], rn = t[2];
@@ -448,9 +459,9 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
                 if (L.done != RUNNING) L.finished = 1;
             }
             if (tr) {
-                const unsigned long long t_s2 = globaltimer();
-                tt[TR_SUM] += t_s1 - t_s0;
-                tt[TR_DECIDE] += t_s2 - t_s1;
+                const long long t_s2 = clock64();
+                tt[TR_SUM] += (unsigned long long)(t_s1 - t_s0);
+                tt[TR_DECIDE] += (unsigned long long)(t_s2 - t_s1);
             }
             __syncthreads();
         }
@@ -490,7 +501,6 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg2
                     L.sc->rz = L.gamma;
                     L.sc->done = L.done;
                     __threadfence();
-                    atomicSub(&a.ctl->running, 1);
                 }
             }
             s_member[tid] = (L.done == RUNNING);

@@ -183,59 +183,76 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-__device__ __forceinline__ bool grid_barrier(MarchCtl* ctl, unsigned target, int tid) {
-    __shared__ int s_ok;
+// Arrival at grid barrier m (thread 0): CTA 0 clears the count slot of barrier m + 1, the CTA adds
+// its unfinished owned solves to the slot of barrier m, then the arrival itself.
+__device__ __forceinline__ void barrier_arrive(MarchCtl* ctl, unsigned m, int add) {
+    if (blockIdx.x == 0) *(volatile int*)&ctl->alive[(m + 1) % 3] = 0;
+    if (add) atomicAdd(&ctl->alive[m % 3], add);
+    __threadfence();
+}
+
+// Thread 0's bounded wait for `target` arrivals; false after a timeout or another CTA's error.
+__device__ __forceinline__ bool barrier_spin(MarchCtl* ctl, unsigned target) {
+    unsigned long long t0 = 0;
+    while (ld_acquire(&ctl->bar) < target) {
+        if (*(volatile int*)&ctl->error) return false;
+        const unsigned long long t = globaltimer();
+        if (!t0) t0 = t;
+        else if (t - t0 > BAR_NS) {
+            atomicExch(&ctl->error, 1);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Grid barrier m (target = m * nctas arrivals).  add: this CTA's unfinished owned solves; *alive
+// (every thread): the unfinished solves of the whole launch as of this barrier.
+__device__ __forceinline__ bool grid_barrier(MarchCtl* ctl, unsigned m, unsigned target, int tid,
+                                             int add, int* alive) {
+    __shared__ int s_ok, s_alive;
     // generic-proxy stores of this phase must be ordered before the next phase's TMA reads
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
-        __threadfence();
+        barrier_arrive(ctl, m, add);
         atomicAdd(&ctl->bar, 1u);
-        int ok = 1;
-        unsigned long long t0 = 0;
-        while (ld_acquire(&ctl->bar) < target) {
-            if (*(volatile int*)&ctl->error) { ok = 0; break; }
-            const unsigned long long t = globaltimer();
-            if (!t0) t0 = t;
-            else if (t - t0 > BAR_NS) { ok = 0; atomicExch(&ctl->error, 1); break; }
-        }
+        const int ok = barrier_spin(ctl, target) ? 1 : 0;
         __threadfence();
         asm volatile("fence.proxy.async.global;" ::: "memory");
+        s_alive = *(volatile int*)&ctl->alive[m % 3];
         s_ok = ok;
     }
     __syncthreads();
+    *alive = s_alive;
     return s_ok != 0;
 }
 
 // Split-phase form of grid_barrier: arrive (after the CTA's stores), do independent work, wait.
 // With a trace, the last CTA to arrive stamps the time of its arrival.
-__device__ __forceinline__ void grid_arrive(MarchCtl* ctl, int tid, unsigned target = 0,
-                                            bool stamp = false) {
+__device__ __forceinline__ void grid_arrive(MarchCtl* ctl, int tid, unsigned m, unsigned target,
+                                            int add, bool stamp = false) {
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
-        __threadfence();
+        barrier_arrive(ctl, m, add);
         const unsigned old = atomicAdd(&ctl->bar, 1u);
         if (stamp && old + 1 == target) *(volatile unsigned long long*)&ctl->t_last = globaltimer();
     }
 }
 
-__device__ __forceinline__ bool grid_wait(MarchCtl* ctl, unsigned target, int tid) {
-    __shared__ int s_ok2;
+__device__ __forceinline__ bool grid_wait(MarchCtl* ctl, unsigned m, unsigned target, int tid,
+                                          int* alive) {
+    __shared__ int s_ok2, s_alive2;
     if (tid == 0) {
-        int ok = 1;
-        unsigned long long t0 = 0;
-        while (ld_acquire(&ctl->bar) < target) {
-            if (*(volatile int*)&ctl->error) { ok = 0; break; }
-            const unsigned long long t = globaltimer();
-            if (!t0) t0 = t;
-            else if (t - t0 > BAR_NS) { ok = 0; atomicExch(&ctl->error, 1); break; }
-        }
+        const int ok = barrier_spin(ctl, target) ? 1 : 0;
         __threadfence();
         asm volatile("fence.proxy.async.global;" ::: "memory");
+        s_alive2 = *(volatile int*)&ctl->alive[m % 3];
         s_ok2 = ok;
     }
     __syncthreads();
+    *alive = s_alive2;
     return s_ok2 != 0;
 }
 
@@ -280,7 +297,9 @@ __device__ __forceinline__ double ff_value(ff v) { return (double)v.hi + (double
 // by every thread in warp order.  red: at least NV * nwarps entries.
 template <int NV>
 __device__ __forceinline__ void range_sum(const float2* part, int b, int e, double (&out)[NV],
-                                          ff* red, int tid, int nthreads) {
+                                          ff* red, int tid, int nthreads, int bar_id = 0) {
+    // threads [0, nthreads) take part; bar_id 0: the whole CTA (__syncthreads), else that named
+    // barrier over nthreads threads
     constexpr int U = 4;
     ff acc[NV];
 #pragma unroll
@@ -311,14 +330,14 @@ __device__ __forceinline__ void range_sum(const float2* part, int b, int e, doub
     if ((tid & 31) == 0)
 #pragma unroll
         for (int q = 0; q < NV; ++q) red[(tid >> 5) * NV + q] = acc[q];
-    __syncthreads();
+    if (bar_id) named_sync(bar_id, nthreads); else __syncthreads();
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         ff t{0.f, 0.f};
         for (int w = 0; w < nw; ++w) t = ff_add(t, red[w * NV + q]);
         out[q] = ff_value(t);
     }
-    __syncthreads();
+    if (bar_id) named_sync(bar_id, nthreads); else __syncthreads();
 }
 
 // The same sum by one warp (valid in every lane).
