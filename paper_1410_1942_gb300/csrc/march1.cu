@@ -61,6 +61,8 @@ struct LocalSolve1 {
     int seg_begin, seg_end;
     double gamma, alpha, beta, rr, stop2;
     double alpha_prev;  // alpha of the previous iteration (odd iterations update x with it)
+    double den;         // delta - beta gamma / alpha of the last iteration: (p, A p)
+    double ginv[2];     // 1/gamma, by the parity of the grid barrier it was formed at
     int done, iter, max_iter, finished, owner, first;
     int xfix;           // stopped after an even iteration: x still lacks alpha p
 };
@@ -376,6 +378,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             range_sum<3>(a.part_b, s_sol[l].seg_begin, s_sol[l].seg_end, t, reinterpret_cast<ff*>(red),
                          tid, NC, 1);
             const long long t_s1 = tr ? clock64() : 0;
+            // 1/gamma for the next decision, off thread 0's path (another warp)
+            if (tid == 32) s_sol[l].ginv[nbar & 1] = 1.0 / t[0];
             if (tid == 0) {
                 LocalSolve1& L = s_sol[l];
                 const double gn = t[0], dn = t[1], rn = t[2];
@@ -389,6 +393,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                     if (rn <= L.stop2) L.done = CONVERGED;
                     else if (!(dn > 0.0)) L.done = BREAKDOWN;
                     else {
+                        L.den = dn;
                         L.alpha = gn / dn;
                         L.beta = 0.0;
                     }
@@ -400,8 +405,10 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                     } else if (L.iter >= L.max_iter) {
                         L.done = CAPPED;
                     } else {
-                        const double be = gn / L.gamma;
-                        const double den = dn - be * gn / L.alpha;
+                        // beta = gamma'/gamma; delta' - beta gamma'/alpha = delta' - beta^2 den
+                        // (alpha = gamma/den): one division on this thread's path
+                        const double be = gn * L.ginv[(nbar - 1) & 1];
+                        const double den = fma(-be * be, L.den, dn);
                         if (!(den > 0.0) || !isfinite(den)) {
                             L.done = BREAKDOWN;
                         } else {
@@ -409,6 +416,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                             L.alpha_prev = L.alpha;
                             L.alpha = gn / den;
                             L.gamma = gn;
+                            L.den = den;
                         }
                     }
                     if (L.done != RUNNING && !x_updated) L.xfix = 1;
