@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             s_nextxs[tid] = L.first ? 0 : ((L.iter + 1) & 1);
         }
         ++nbar;
-        if (!grid_barrier(a.ctl, nbar, nbar * (unsigned)a.nctas, tid, owned_running(), &alive)) {
+        if (!grid_barrier(a.ctl, nbar, nbar * (unsigned)a.nctas, tid, owned_running(), &alive,
+                          a.trace != nullptr, tr ? &tt[TR_IMB] : nullptr,
+                          tr ? &tt[TR_REL] : nullptr)) {
             failed = true;
             break;
         }

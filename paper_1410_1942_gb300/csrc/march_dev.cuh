@@ -208,16 +208,28 @@ __device__ __forceinline__ bool barrier_spin(MarchCtl* ctl, unsigned target) {
 
 // Grid barrier m (target = m * nctas arrivals).  add: this CTA's unfinished owned solves; *alive
 // (every thread): the unfinished solves of the whole launch as of this barrier.
+// Tracing (stamp): the last CTA to arrive stamps the time, and a thread passing imb/rel adds its
+// wait for the last arrival and the release latency after it (ns).
 __device__ __forceinline__ bool grid_barrier(MarchCtl* ctl, unsigned m, unsigned target, int tid,
-                                             int add, int* alive) {
+                                             int add, int* alive, bool stamp = false,
+                                             unsigned long long* imb = nullptr,
+                                             unsigned long long* rel = nullptr) {
     __shared__ int s_ok, s_alive;
     // generic-proxy stores of this phase must be ordered before the next phase's TMA reads
     asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
     if (tid == 0) {
         barrier_arrive(ctl, m, add);
-        atomicAdd(&ctl->bar, 1u);
+        const unsigned long long t_arr = imb ? globaltimer() : 0;
+        const unsigned old = atomicAdd(&ctl->bar, 1u);
+        if (stamp && old + 1 == target) *(volatile unsigned long long*)&ctl->t_last = globaltimer();
         const int ok = barrier_spin(ctl, target) ? 1 : 0;
+        if (imb) {
+            const unsigned long long tl = *(volatile unsigned long long*)&ctl->t_last;
+            const unsigned long long tn = globaltimer();
+            if (tl > t_arr) *imb += tl - t_arr;
+            if (tn > tl) *rel += tn - tl;
+        }
         __threadfence();
         asm volatile("fence.proxy.async.global;" ::: "memory");
         s_alive = *(volatile int*)&ctl->alive[m % 3];
