@@ -69,6 +69,9 @@ def parse():
     ap.add_argument("--shape", type=int, nargs=3, default=(256, 128, 128),
                     help="grid of the strut workload (profiling of smaller cases)")
     ap.add_argument("--tile", type=int, default=0, help="FP32 kernel tile option (0 = autotuned)")
+    ap.add_argument("--walls", type=int, default=0,
+                    help="Dirichlet side/bottom walls bitmask (1 x-, 2 x+, 4 y-, 8 y+, 16 z-)")
+    ap.add_argument("--periodic-x", action="store_true", help="periodic x boundaries")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, batched and served measurements")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -362,7 +365,8 @@ def main():
     p_d = torch.zeros(g.shape, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
     solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision, precond=args.precond,
-                          stream=stream.cuda_stream, tile=args.tile)
+                          stream=stream.cuda_stream, tile=args.tile, dirichlet_walls=args.walls,
+                          periodic_x=args.periodic_x)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -447,7 +451,8 @@ def main():
         s_h = torch.from_numpy(case.s).pin_memory()
         p_h = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
         solver_h = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision,
-                                precond=args.precond, stream=stream.cuda_stream, tile=args.tile)
+                                precond=args.precond, stream=stream.cuda_stream, tile=args.tile,
+                                dirichlet_walls=args.walls, periodic_x=args.periodic_x)
 
         def step_e2e():
             p_h.zero_()
@@ -501,6 +506,9 @@ def main():
                         (WORKLOAD if tuple(args.shape) == (256, 128, 128)
                          else "strut %dx%dx%d (profiling case)" % tuple(args.shape)), "cells": g.n, "precision": args.precision,
                        "precond": args.precond, "tol": case.tol,
+                       "boundaries": ("periodic x, " if args.periodic_x else "") +
+                                     ("Dirichlet walls mask %d" % args.walls if args.walls
+                                      else "zero-gradient side/bottom walls") + ", p = 0 on top",
                        "l2": "flushed between steps (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "kernels": solver.describe(),
