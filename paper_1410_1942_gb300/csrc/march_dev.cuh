@@ -225,10 +225,13 @@ __device__ __forceinline__ bool grid_barrier(MarchCtl* ctl, unsigned m, unsigned
         if (stamp && old + 1 == target) *(volatile unsigned long long*)&ctl->t_last = globaltimer();
         const int ok = barrier_spin(ctl, target) ? 1 : 0;
         if (imb) {
+            // (a stamp older than this CTA's arrival is the previous barrier's: not counted)
             const unsigned long long tl = *(volatile unsigned long long*)&ctl->t_last;
             const unsigned long long tn = globaltimer();
-            if (tl > t_arr) *imb += tl - t_arr;
-            if (tn > tl) *rel += tn - tl;
+            if (tl >= t_arr && tn >= tl) {
+                *imb += tl - t_arr;
+                *rel += tn - tl;
+            }
         }
         __threadfence();
         asm volatile("fence.proxy.async.global;" ::: "memory");
