@@ -69,6 +69,13 @@ def _load():
         lib.oracle_faces.restype = i
         lib.oracle_faces_bc.argtypes = [i, i, i, P, d, d, i, i, P, P, P, P]
         lib.oracle_faces_bc.restype = i
+        lib.oracle_faces_cut.argtypes = [i, i, i, P, d, d, i, i, P, P, P, P, P, P, P, P]
+        lib.oracle_faces_cut.restype = i
+        lib.oracle_divergence_cut.argtypes = [i, i, i, d, d, P, P, P, P, P, P, P, P]
+        lib.oracle_divergence_cut.restype = None
+        lib.oracle_project_cut.argtypes = [i, i, i, d, d, P, d, d, i, P, P, P, P, P, P, P, P, P,
+                                           P, P]
+        lib.oracle_project_cut.restype = None
         lib.oracle_apply.argtypes = [i, i, i, P, P, P, P, P, P]
         lib.oracle_apply.restype = None
         lib.oracle_precond.argtypes = [i, i, i, P, P, P, P, i, d, P, P]
@@ -121,6 +128,7 @@ class Operator:
     bz: np.ndarray
     diag: np.ndarray
     walls: int = 0
+    apertures: tuple | None = None  # (ax, ay, az, vol) of a cut-cell operator
 
     @property
     def shape(self):
@@ -136,23 +144,35 @@ WALL_XM, WALL_XP, WALL_YM, WALL_YP, WALL_ZM = 1, 2, 4, 8, 16
 PERIODIC_X = 32  # in ``walls``: x periodic (no x walls)
 
 
-def operator(F, rho_air=1.0, rho_water=1000.0, mean="harmonic", walls=0):
+def operator(F, rho_air=1.0, rho_water=1000.0, mean="harmonic", walls=0, apertures=None):
     """Assemble the operator from the water fraction ``F`` (shape ``(nz, ny, nx)``).  ``walls``:
     bitmask of side/bottom walls with p = 0 on the wall face (WALL_XM | ...); the others, as in
     the paper's configuration, have a zero normal gradient; the top face always has p = 0.
     ``PERIODIC_X`` in ``walls`` makes x periodic (the strut run of the Results), with no x
-    walls; red-black SSOR then needs an even nx."""
+    walls; red-black SSOR then needs an even nx.  ``apertures = (ax, ay, az, vol)``: open
+    fractions of the MAC faces (shapes of u, v, w) and fluid fractions of the cells for free-slip
+    cut cells (Enforcement of Body Boundary Conditions): every face coefficient is scaled by its
+    open fraction, a face of a cell with vol = 0 is closed, and such a cell is inactive
+    (diagonal 1, no coupling)."""
     if walls & PERIODIC_X and walls & (WALL_XM | WALL_XP):
         raise ValueError("periodic x has no x walls")
     F = _f64(F)
     nz, ny, nx = F.shape
     bx, by, bz, dg = (np.empty_like(F) for _ in range(4))
     m = MEAN_HARMONIC if mean == "harmonic" else MEAN_ARITHMETIC
-    rc = _load().oracle_faces_bc(nx, ny, nz, _ptr(F), float(rho_air), float(rho_water), m,
-                                 int(walls), _ptr(bx), _ptr(by), _ptr(bz), _ptr(dg))
+    if apertures is None:
+        rc = _load().oracle_faces_bc(nx, ny, nz, _ptr(F), float(rho_air), float(rho_water), m,
+                                     int(walls), _ptr(bx), _ptr(by), _ptr(bz), _ptr(dg))
+    else:
+        ap = tuple(_f64(a) for a in apertures)
+        assert tuple(a.shape for a in ap[:3]) == _faces_shapes(nx, ny, nz) and ap[3].shape == F.shape
+        rc = _load().oracle_faces_cut(nx, ny, nz, _ptr(F), float(rho_air), float(rho_water), m,
+                                      int(walls), *(_ptr(a) for a in ap), _ptr(bx), _ptr(by),
+                                      _ptr(bz), _ptr(dg))
+        apertures = ap
     if rc != OK:
         raise RuntimeError("oracle_faces failed: %d" % rc)
-    return Operator(nx, ny, nz, bx, by, bz, dg, int(walls))
+    return Operator(nx, ny, nz, bx, by, bz, dg, int(walls), apertures)
 
 
 def apply(op: Operator, x):
@@ -269,17 +289,24 @@ def _faces_shapes(nx, ny, nz):
     return (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)
 
 
-def divergence(u, v, w, h, dt):
+def divergence(u, v, w, h, dt, apertures=None):
     """``s = div_h(u) / dt`` at cell centres from MAC face velocities ``u`` ``(nz, ny, nx+1)``,
     ``v`` ``(nz, ny+1, nx)``, ``w`` ``(nz+1, ny, nx)`` (w's last plane is the top boundary):
     the flux difference of each cell divided by ``h dt`` (Numerical Time Integration: the
-    pressure equation's source)."""
+    pressure equation's source).  With ``apertures = (ax, ay, az, vol)`` the fluxes are
+    ``a u`` and the difference is divided by ``vol`` as well (0 in inactive cells)."""
     u, v, w = _f64(u), _f64(v), _f64(w)
     nz, ny, nx1 = u.shape
     nx = nx1 - 1
     assert (v.shape, w.shape) == _faces_shapes(nx, ny, nz)[1:]
     s = np.empty((nz, ny, nx))
-    _load().oracle_divergence(nx, ny, nz, float(h), float(dt), _ptr(u), _ptr(v), _ptr(w), _ptr(s))
+    if apertures is None:
+        _load().oracle_divergence(nx, ny, nz, float(h), float(dt), _ptr(u), _ptr(v), _ptr(w),
+                                  _ptr(s))
+    else:
+        ap = tuple(_f64(a) for a in apertures)
+        _load().oracle_divergence_cut(nx, ny, nz, float(h), float(dt), _ptr(u), _ptr(v), _ptr(w),
+                                      *(_ptr(a) for a in ap), _ptr(s))
     return s
 
 
@@ -292,15 +319,24 @@ def project(op: Operator, F, u, v, w, p, h, dt, rho_air=1.0, rho_water=1000.0):
     u, v, w = _f64(u).copy(), _f64(v).copy(), _f64(w).copy()
     p, F = _f64(p).reshape(op.shape), _f64(F).reshape(op.shape)
     assert (u.shape, v.shape, w.shape) == _faces_shapes(op.nx, op.ny, op.nz)
-    _load().oracle_project_bc(op.nx, op.ny, op.nz, float(h), float(dt), _ptr(F), float(rho_air),
-                              float(rho_water), op.walls, _ptr(op.bx), _ptr(op.by), _ptr(op.bz),
-                              _ptr(p), _ptr(u), _ptr(v), _ptr(w))
+    if op.apertures is None:
+        _load().oracle_project_bc(op.nx, op.ny, op.nz, float(h), float(dt), _ptr(F),
+                                  float(rho_air), float(rho_water), op.walls, _ptr(op.bx),
+                                  _ptr(op.by), _ptr(op.bz), _ptr(p), _ptr(u), _ptr(v), _ptr(w))
+    else:
+        _load().oracle_project_cut(op.nx, op.ny, op.nz, float(h), float(dt), _ptr(F),
+                                   float(rho_air), float(rho_water), op.walls,
+                                   *(_ptr(a) for a in op.apertures), _ptr(op.bx), _ptr(op.by),
+                                   _ptr(op.bz), _ptr(p), _ptr(u), _ptr(v), _ptr(w))
     return u, v, w
 
 
-def rhs(s, h):
-    """``b = -h^2 s``: the right side of ``A p = b`` for ``div((1/rho) grad p) = s``."""
-    return -(h * h) * _f64(s)
+def rhs(s, h, vol=None):
+    """``b = -h^2 s``: the right side of ``A p = b`` for ``div((1/rho) grad p) = s``; with cut
+    cells ``b = -h^2 (vol s)`` (the cell's fluid fraction times its source)."""
+    if vol is None:
+        return -(h * h) * _f64(s)
+    return -(h * h) * (_f64(vol) * _f64(s))
 
 
 def solve(F, s, h, tol=1e-12, precond="jacobi", omega=1.0, x0=None, rho_air=1.0,

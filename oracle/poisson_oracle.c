@@ -90,8 +90,17 @@ void oracle_set_threads(int n) {
  * periodicity). */
 #define OR_PERIODIC_X 32
 
-int oracle_faces_bc(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
-                    int mean, int walls, double* bx, double* by, double* bz, double* diag) {
+/* Cut cells (free-slip bodies, Enforcement of Body Boundary Conditions): ax, ay, az are the open
+ * fractions of the faces on the MAC face arrays ((nx+1) x ny x nz, nx x (ny+1) x nz,
+ * nx x ny x (nz+1), x fastest) and vol the fluid fraction of each cell.  Every face coefficient
+ * (interior, top, Dirichlet wall) is multiplied by its face's open fraction; a face of a cell with
+ * vol = 0 counts as closed; a cell with vol = 0 is inactive: diagonal 1, no coupling (its pressure
+ * is 0 for a zero right side).  NULL apertures: all faces open, all cells active. */
+static double face_open(const double* a, idx_t f) { return a ? a[f] : 1.0; }
+
+int oracle_faces_cut(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
+                     int mean, int walls, const double* ax, const double* ay, const double* az,
+                     const double* vol, double* bx, double* by, double* bz, double* diag) {
     if (nx <= 0 || ny <= 0 || nz <= 0 || !F || !bx || !by || !bz || !diag) return OR_EINVAL;
     const idx_t n = (idx_t)nx * ny * nz;
     double* rho = (double*)malloc(sizeof(double) * (size_t)n);
@@ -117,6 +126,15 @@ int oracle_faces_bc(int nx, int ny, int nz, const double* F, double rho_air, dou
                     double rn = rho[c - (idx_t)nx * ny];
                     fz = (mean == OR_MEAN_HARMONIC) ? 2.0 / (rc + rn) : 0.5 * (1.0 / rc + 1.0 / rn);
                 }
+                if (ax) {
+                    const idx_t fu = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                    const idx_t fv = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
+                    const int act = vol[c] > 0.0;
+                    const idx_t cxm = i > 0 ? c - 1 : c + nx - 1;
+                    fx = (act && vol[cxm] > 0.0) ? ax[fu] * fx : 0.0;
+                    fy = (act && j > 0 && vol[c - nx] > 0.0) ? ay[fv] * fy : 0.0;
+                    fz = (act && k > 0 && vol[c - (idx_t)nx * ny] > 0.0) ? az[c] * fz : 0.0;
+                }
                 bx[c] = fx;
                 by[c] = fy;
                 bz[c] = fz;
@@ -128,21 +146,34 @@ int oracle_faces_bc(int nx, int ny, int nz, const double* F, double rho_air, dou
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 idx_t c = i + (idx_t)nx * (j + (idx_t)ny * k);
+                if (vol && !(vol[c] > 0.0)) {
+                    diag[c] = 1.0; /* inactive cell */
+                    continue;
+                }
+                const idx_t fu = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                const idx_t fv = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
+                const idx_t sxy = (idx_t)nx * ny;
                 double d = bx[c] + by[c] + bz[c];
                 if (i + 1 < nx) d += bx[c + 1];
                 else if (walls & OR_PERIODIC_X) d += bx[c + 1 - nx];
                 if (j + 1 < ny) d += by[c + nx];
-                if (k + 1 < nz) d += bz[c + (idx_t)nx * ny];
-                else d += 2.0 / rho[c];
-                if ((walls & OR_WALL_XM) && i == 0) d += 2.0 / rho[c];
-                if ((walls & OR_WALL_XP) && i == nx - 1) d += 2.0 / rho[c];
-                if ((walls & OR_WALL_YM) && j == 0) d += 2.0 / rho[c];
-                if ((walls & OR_WALL_YP) && j == ny - 1) d += 2.0 / rho[c];
-                if ((walls & OR_WALL_ZM) && k == 0) d += 2.0 / rho[c];
+                if (k + 1 < nz) d += bz[c + sxy];
+                else d += face_open(az, c + sxy) * (2.0 / rho[c]);
+                if ((walls & OR_WALL_XM) && i == 0) d += face_open(ax, fu) * (2.0 / rho[c]);
+                if ((walls & OR_WALL_XP) && i == nx - 1) d += face_open(ax, fu + 1) * (2.0 / rho[c]);
+                if ((walls & OR_WALL_YM) && j == 0) d += face_open(ay, fv) * (2.0 / rho[c]);
+                if ((walls & OR_WALL_YP) && j == ny - 1) d += face_open(ay, fv + nx) * (2.0 / rho[c]);
+                if ((walls & OR_WALL_ZM) && k == 0) d += face_open(az, c) * (2.0 / rho[c]);
                 diag[c] = d;
             }
     free(rho);
     return OR_OK;
+}
+
+int oracle_faces_bc(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
+                    int mean, int walls, double* bx, double* by, double* bz, double* diag) {
+    return oracle_faces_cut(nx, ny, nz, F, rho_air, rho_water, mean, walls, NULL, NULL, NULL, NULL,
+                            bx, by, bz, diag);
 }
 
 int oracle_faces(int nx, int ny, int nz, const double* F, double rho_air, double rho_water,
@@ -343,6 +374,31 @@ done:
  * (2/rho_c) ((0 - p_c)/h); wall faces keep their value (beta = 0 there).  With these faces
  * div_h(u_new)/dt = div_h(u*)/dt - L p, i.e. divergence(u_new) = (A p - b) / h^2 for b = -h^2 s.
  */
+/* With cut cells: s_c = (((a u)_{i+1} - (a u)_i + ... ) / (h dt)) / vol_c, 0 for inactive cells,
+ * so that -h^2 vol s is the right side of the cut operator. */
+void oracle_divergence_cut(int nx, int ny, int nz, double h, double dt, const double* u,
+                           const double* v, const double* w, const double* ax, const double* ay,
+                           const double* az, const double* vol, double* s) {
+    const double hd = h * dt;
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const idx_t fu = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                const idx_t fv = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
+                const idx_t fw = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)ny * k);
+                const idx_t up = fw + (idx_t)nx * ny;
+                if (!(vol[fw] > 0.0)) {
+                    s[fw] = 0.0;
+                    continue;
+                }
+                const double du = ax[fu + 1] * u[fu + 1] - ax[fu] * u[fu];
+                const double dv = ay[fv + nx] * v[fv + nx] - ay[fv] * v[fv];
+                const double dw = az[up] * w[up] - az[fw] * w[fw];
+                s[fw] = (((du + dv) + dw) / hd) / vol[fw];
+            }
+}
+
 void oracle_divergence(int nx, int ny, int nz, double h, double dt, const double* u,
                        const double* v, const double* w, double* s) {
     const double hd = h * dt;
@@ -360,47 +416,73 @@ void oracle_divergence(int nx, int ny, int nz, double h, double dt, const double
             }
 }
 
+/* With cut cells (ax non-NULL; bx, by, bz the cut operator's faces): an open face of two active
+ * cells is corrected with its own coefficient, the cut face coefficient over the open fraction
+ * (bx / a); a top or Dirichlet wall face of an active cell with a > 0 with 2/rho_c; every other
+ * face keeps its value.  Then the flux divergence sum_f a_f u_f of the corrected field is that of
+ * u* minus dt (L p) h: the cut operator's residual again. */
+static double cut_beta(const double* a, idx_t f, double b) { return a ? (b != 0.0 ? b / a[f] : 0.0) : b; }
+
+void oracle_project_cut(int nx, int ny, int nz, double h, double dt, const double* F,
+                        double rho_air, double rho_water, int walls, const double* ax,
+                        const double* ay, const double* az, const double* vol, const double* bx,
+                        const double* by, const double* bz, const double* p, double* u,
+                        double* v, double* w);
+
 void oracle_project_bc(int nx, int ny, int nz, double h, double dt, const double* F,
                        double rho_air, double rho_water, int walls, const double* bx,
                        const double* by, const double* bz, const double* p, double* u, double* v,
                        double* w) {
+    oracle_project_cut(nx, ny, nz, h, dt, F, rho_air, rho_water, walls, NULL, NULL, NULL, NULL, bx,
+                       by, bz, p, u, v, w);
+}
+
+void oracle_project_cut(int nx, int ny, int nz, double h, double dt, const double* F,
+                        double rho_air, double rho_water, int walls, const double* ax,
+                        const double* ay, const double* az, const double* vol, const double* bx,
+                        const double* by, const double* bz, const double* p, double* u,
+                        double* v, double* w) {
 #pragma omp parallel for schedule(static)
     for (int k = 0; k < nz; ++k)
         for (int j = 0; j < ny; ++j)
             for (int i = 0; i < nx; ++i) {
                 const idx_t c = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)ny * k);
                 const idx_t sxy = (idx_t)nx * ny;
+                const idx_t fu = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                const idx_t fv = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
                 if (i > 0) {
-                    const idx_t f = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
-                    u[f] = u[f] - dt * (bx[c] * ((p[c] - p[c - 1]) / h));
+                    const double b = cut_beta(ax, fu, bx[c]);
+                    u[fu] = u[fu] - dt * (b * ((p[c] - p[c - 1]) / h));
                 } else if (walls & OR_PERIODIC_X) {
                     /* faces 0 and nx are one face: corrected from face 0, written to both */
-                    const idx_t f = (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
-                    u[f] = u[f] - dt * (bx[c] * ((p[c] - p[c + nx - 1]) / h));
-                    u[f + nx] = u[f];
+                    const double b = cut_beta(ax, fu, bx[c]);
+                    u[fu] = u[fu] - dt * (b * ((p[c] - p[c + nx - 1]) / h));
+                    u[fu + nx] = u[fu];
                 }
                 if (j > 0) {
-                    const idx_t f = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
-                    v[f] = v[f] - dt * (by[c] * ((p[c] - p[c - nx]) / h));
+                    const double b = cut_beta(ay, fv, by[c]);
+                    v[fv] = v[fv] - dt * (b * ((p[c] - p[c - nx]) / h));
                 }
-                if (k > 0) w[c] = w[c] - dt * (bz[c] * ((p[c] - p[c - sxy]) / h));
+                if (k > 0) {
+                    const double b = cut_beta(az, c, bz[c]);
+                    w[c] = w[c] - dt * (b * ((p[c] - p[c - sxy]) / h));
+                }
+                if (vol && !(vol[c] > 0.0)) continue; /* inactive: no boundary faces */
                 const double rho = rho_air + F[c] * (rho_water - rho_air);
-                if (k == nz - 1) {
+                if (k == nz - 1 && face_open(az, c + sxy) > 0.0) {
                     const idx_t f = c + sxy;
                     w[f] = w[f] - dt * ((2.0 / rho) * ((0.0 - p[c]) / h));
                 }
                 /* Dirichlet walls: p = 0 on the wall face, half a cell from the centre */
-                const idx_t fu = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
-                const idx_t fv = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
-                if ((walls & OR_WALL_XM) && i == 0)
+                if ((walls & OR_WALL_XM) && i == 0 && face_open(ax, fu) > 0.0)
                     u[fu] = u[fu] - dt * ((2.0 / rho) * ((p[c] - 0.0) / h));
-                if ((walls & OR_WALL_XP) && i == nx - 1)
+                if ((walls & OR_WALL_XP) && i == nx - 1 && face_open(ax, fu + 1) > 0.0)
                     u[fu + 1] = u[fu + 1] - dt * ((2.0 / rho) * ((0.0 - p[c]) / h));
-                if ((walls & OR_WALL_YM) && j == 0)
+                if ((walls & OR_WALL_YM) && j == 0 && face_open(ay, fv) > 0.0)
                     v[fv] = v[fv] - dt * ((2.0 / rho) * ((p[c] - 0.0) / h));
-                if ((walls & OR_WALL_YP) && j == ny - 1)
+                if ((walls & OR_WALL_YP) && j == ny - 1 && face_open(ay, fv + nx) > 0.0)
                     v[fv + nx] = v[fv + nx] - dt * ((2.0 / rho) * ((0.0 - p[c]) / h));
-                if ((walls & OR_WALL_ZM) && k == 0)
+                if ((walls & OR_WALL_ZM) && k == 0 && face_open(az, c) > 0.0)
                     w[c] = w[c] - dt * ((2.0 / rho) * ((p[c] - 0.0) / h));
             }
 }

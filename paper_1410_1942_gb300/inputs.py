@@ -198,6 +198,50 @@ def wedge_sdf(x, y, xa, yc, half_angle):
     return np.maximum(yp * cs - xp * sn, -yp * cs - xp * sn)
 
 
+def cut_apertures(grid: Grid, psi_fn, sub=4):
+    """Open fractions of the MAC faces and fluid fractions of the cells for a body given by a
+    signed distance ``psi(x, y, z)`` (positive outside, in the fluid): the share of ``sub x sub``
+    sample points on each face (``sub^3`` in each cell) where ``psi > 0``.  Returns
+    ``(ax, ay, az, vol)`` with the shapes of ``u, v, w`` and of the cells.  Geometry input for
+    free-slip cut cells; no part of the solve."""
+    nx, ny, nz, h = grid.nx, grid.ny, grid.nz, grid.h
+    o = (np.arange(sub) + 0.5) / sub  # sample offsets inside a cell / face, in cells
+
+    def frac(x, y, z):
+        return (psi_fn(x, y, z) > 0).mean(axis=-1)
+
+    def grid3(a, b, c):
+        return np.meshgrid(a, b, c, indexing="ij")
+
+    xf, yf, zf = np.arange(nx + 1) * h, np.arange(ny + 1) * h, np.arange(nz + 1) * h
+    xs = ((np.arange(nx)[:, None] + o[None, :]) * h)  # (nx, sub) sample x inside each cell
+    ys = ((np.arange(ny)[:, None] + o[None, :]) * h)
+    zs = ((np.arange(nz)[:, None] + o[None, :]) * h)
+    ax = np.empty((nz, ny, nx + 1))
+    ay = np.empty((nz, ny + 1, nx))
+    az = np.empty((nz + 1, ny, nx))
+    vol = np.empty((nz, ny, nx))
+    for k in range(nz):
+        Z = zs[k]
+        # x faces: samples over (y, z) of each face
+        Y, Zg = np.meshgrid(ys.ravel(), Z, indexing="ij")  # (ny*sub, sub)
+        for i in range(nx + 1):
+            v = (psi_fn(np.full_like(Y, xf[i]), Y, Zg) > 0).reshape(ny, sub * sub)
+            ax[k, :, i] = v.mean(axis=1)
+        X, Zg = np.meshgrid(xs.ravel(), Z, indexing="ij")  # (nx*sub, sub)
+        for j in range(ny + 1):
+            v = (psi_fn(X, np.full_like(X, yf[j]), Zg) > 0).reshape(nx, sub * sub)
+            ay[k, j, :] = v.mean(axis=1)
+        X, Y, Zg = grid3(xs.ravel(), ys.ravel(), Z)  # (nx*sub, ny*sub, sub)
+        v = (psi_fn(X, Y, Zg) > 0).reshape(nx, sub, ny, sub, sub)
+        vol[k] = v.mean(axis=(1, 3, 4)).T
+    for k in range(nz + 1):
+        X, Y = np.meshgrid(xs.ravel(), ys.ravel(), indexing="ij")
+        v = (psi_fn(X, Y, np.full_like(X, zf[k])) > 0).reshape(nx, sub, ny, sub)
+        az[k] = v.mean(axis=(1, 3)).T
+    return ax, ay, az, vol
+
+
 def water_fraction(grid: Grid, eta_fn, psi_fn=None, z0=None, eps_cells=1.5, breaking=None,
                    zchunk=32):
     """Water fraction ``F = H_eps(z0 + eta(x, y) - z)`` at cell centres, with ``eps = 1.5 h``;

@@ -477,6 +477,94 @@ def test_projection_with_periodic_x_leaves_the_residual():
     assert np.abs(div + r / h ** 2).max() <= 1e-13 * scale
 
 
+# ------------------------------------------------------------------------------- cut cells
+def _open_apertures(shape):
+    nz, ny, nx = shape
+    return (np.ones((nz, ny, nx + 1)), np.ones((nz, ny + 1, nx)), np.ones((nz + 1, ny, nx)),
+            np.ones(shape))
+
+
+def test_cut_cells_all_open_is_the_plain_operator():
+    shape = (5, 6, 7)
+    F = _rand_F(shape, 101)
+    for walls in (0, 31, oracle.PERIODIC_X | 16):
+        a = oracle.operator(F, RHO_A, RHO_W, walls=walls)
+        b = oracle.operator(F, RHO_A, RHO_W, walls=walls, apertures=_open_apertures(shape))
+        for x, y in ((a.bx, b.bx), (a.by, b.by), (a.bz, b.bz), (a.diag, b.diag)):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_cut_cells_grid_aligned_body_is_a_wall_of_the_fluid_box(axis):
+    """A body filling the cells beyond a grid plane (vol 0 there, the plane's faces closed)
+    leaves the fluid box with a zero-gradient wall on that plane: the cut solve equals the plain
+    solve on the fluid box, and the body's cells hold p = 0."""
+    shape = (6, 7, 8)  # (nz, ny, nx)
+    F = _rand_F(shape, 102)
+    ax, ay, az, vol = _open_apertures(shape)
+    cut = 4  # fluid: index < cut along the axis (x, y) or index >= cut (z: a bottom body)
+    if axis == 0:
+        vol[:, :, cut:] = 0
+        ax[:, :, cut] = 0
+        sub = (slice(None), slice(None), slice(0, cut))
+    elif axis == 1:
+        vol[:, cut:, :] = 0
+        ay[:, cut, :] = 0
+        sub = (slice(None), slice(0, cut), slice(None))
+    else:
+        vol[:cut - 2] = 0
+        az[cut - 2] = 0
+        sub = (slice(cut - 2, None), slice(None), slice(None))
+    op = oracle.operator(F, RHO_A, RHO_W, apertures=(ax, ay, az, vol))
+    s = np.random.default_rng(103).standard_normal(shape)
+    b = oracle.rhs(s, 0.125, vol)
+    res = oracle.pcg(op, b, tol=1e-13)
+    assert res.status == oracle.OK
+    ref = oracle.pcg(oracle.operator(np.ascontiguousarray(F[sub]), RHO_A, RHO_W),
+                     oracle.rhs(np.ascontiguousarray(s[sub]), 0.125), tol=1e-13).x
+    assert np.linalg.norm(res.x[sub] - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert not np.any(res.x[vol == 0])
+
+
+def test_cut_cells_operator_symmetric_positive_and_matches_dense_lu():
+    shape = (4, 5, 6)
+    rng = np.random.default_rng(104)
+    F = _rand_F(shape, 105)
+    ax, ay, az, vol = (rng.uniform(0.05, 1.0, a.shape) for a in _open_apertures(shape))
+    vol[rng.random(shape) < 0.15] = 0.0
+    op = oracle.operator(F, RHO_A, RHO_W, walls=3, apertures=(ax, ay, az, vol))
+    A = _dense(op)
+    assert np.allclose(A, A.T, rtol=0, atol=1e-13)
+    assert np.linalg.eigvalsh(A).min() > 0
+    b = oracle.rhs(rng.standard_normal(shape), 0.25, vol)
+    ref = scipy.linalg.solve(A, b.ravel(), assume_a="sym").reshape(shape)
+    res = oracle.pcg(op, b, tol=1e-14)
+    assert np.linalg.norm(res.x - ref) / np.linalg.norm(ref) <= 1e-10
+
+
+@pytest.mark.parametrize("walls", [0, 16 | 1])
+def test_cut_cells_projection_leaves_the_residual(walls):
+    """vol s(u_new) = (A p - b)/h^2 in the active cells for any p (s the cut divergence over
+    dt): the projection's open-face coefficients and boundary faces are the cut operator's."""
+    shape, h, dt = (5, 6, 7), 1.0 / 8, 2e-3
+    rng = np.random.default_rng(106)
+    F = _rand_F(shape, 107)
+    ax, ay, az, vol = (rng.uniform(0.05, 1.0, a.shape) for a in _open_apertures(shape))
+    vol[rng.random(shape) < 0.15] = 0.0
+    aps = (ax, ay, az, vol)
+    op = oracle.operator(F, RHO_A, RHO_W, walls=walls, apertures=aps)
+    u, v, w = _faces(shape, 108)
+    p = rng.standard_normal(shape)
+    b = oracle.rhs(oracle.divergence(u, v, w, h, dt, aps), h, vol)
+    un, vn, wn = oracle.project(op, F, u, v, w, p, h, dt, RHO_A, RHO_W)
+    r, _ = oracle.residual(op, b, p)
+    lhs = vol * oracle.divergence(un, vn, wn, h, dt, aps)
+    act = vol > 0
+    scale = (np.abs(b) + np.abs(oracle.apply(op, p))).max() / h ** 2
+    assert np.abs(lhs[act] + r[act] / h ** 2).max() <= 1e-12 * scale
+    assert not np.any(lhs[~act])
+
+
 # ------------------------------------------------------------------------------- projection
 def _faces(shape, seed):
     nz, ny, nx = shape
