@@ -198,6 +198,24 @@ int poisson_profile(poisson_t* h, int enable);
 /* Copy out the accumulated per-class launch counts and event times (since poisson_profile). */
 int poisson_profile_read(poisson_t* h, poisson_kernel_times* out);
 
+/* ------------------------------------------------------------------ cut cells
+ * Free-slip bodies as cut cells (Enforcement of Body Boundary Conditions: area and volume
+ * fractions enter the Poisson equation and the projection, which sets the velocity normal to the
+ * hull to zero).  ax, ay, az: open fractions in [0, 1] of the MAC faces (the shapes of the face
+ * arrays of poisson_divergence: (nx+1) x ny x nz, nx x (ny+1) x nz, nx x ny x (nz+1), x fastest);
+ * vol: fluid fractions in [0, 1] of the cells (nx*ny*nz).  Every face coefficient (interior, top,
+ * Dirichlet wall) is scaled by its face's open fraction; a face of a cell with vol = 0 is closed
+ * and such a cell is inactive (its pressure comes out 0); the solve's right side becomes
+ * -h^2 vol rhs, poisson_divergence returns the open-fraction-weighted flux difference over
+ * (h dt vol), and poisson_project corrects each open face with the face's own coefficient.  The
+ * arrays are copied (host or device, as mem says; the caller keeps ownership).  Call before
+ * poisson_set_density (a later call needs set_density again: ENOTREADY until then); all four
+ * NULL returns to the plain operator.  With cut cells the inner FP32 solve runs on the column
+ * kernels with FP32 copies of the cut faces (also for POISSON_FP32_BF16COEF).
+ * Errors: EINVAL (some NULL, mem mismatch), ENOMEM, ECUDA. */
+int poisson_set_apertures(poisson_t* h, const double* ax, const double* ay, const double* az,
+                          const double* vol, int mem);
+
 /* ------------------------------------------------------------------ projection
  * Numerical Time Integration: each stage forms a provisional velocity u* on the cell faces
  * (MAC grid), solves div((1/rho) grad p) = div(u*)/dt, and corrects u = u* - dt (1/rho) grad p.

@@ -31,7 +31,8 @@ EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson
            "poisson_solve", "poisson_apply", "poisson_precond_apply", "poisson_get_operator",
            "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
            "poisson_profile_read", "poisson_describe", "poisson_residual_noalloc",
-           "poisson_divergence", "poisson_project", "poisson_strerror", "poisson_version"]
+           "poisson_divergence", "poisson_project", "poisson_set_apertures", "poisson_strerror",
+           "poisson_version"]
 K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER, K_PCG = 0, 1, 2, 3, 4
 K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 
@@ -109,6 +110,8 @@ def load(path=None):
     lib.poisson_divergence.restype = i
     lib.poisson_project.argtypes = [vp, vp, vp, vp, vp, d]
     lib.poisson_project.restype = i
+    lib.poisson_set_apertures.argtypes = [vp, vp, vp, vp, vp, i]
+    lib.poisson_set_apertures.restype = i
     for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read", "poisson_describe"]:
         getattr(lib, name).restype = i
     _lib = lib
@@ -223,6 +226,17 @@ class Poisson:
         buf = ctypes.create_string_buffer(256)
         _check(load().poisson_describe(self._h, buf, 256), "poisson_describe")
         return buf.value.decode()
+
+    def set_apertures(self, ax=None, ay=None, az=None, vol=None):
+        """Free-slip cut cells: open fractions of the MAC faces and fluid fractions of the cells
+        (numpy or CUDA float64); call set_density afterwards.  No arguments: the plain operator."""
+        if ax is None:
+            _check(load().poisson_set_apertures(self._h, None, None, None, None, MEM_HOST),
+                   "poisson_set_apertures")
+            return
+        mem = MEM_HOST if isinstance(ax, np.ndarray) or not getattr(ax, "is_cuda", False) else MEM_DEVICE
+        _check(load().poisson_set_apertures(self._h, _addr(ax), _addr(ay), _addr(az), _addr(vol),
+                                            mem), "poisson_set_apertures")
 
     def divergence(self, u, v, w, dt, s):
         """``s = div_h(u) / dt`` from face velocities ``u`` ``(nz, ny, nx+1)``, ``v``

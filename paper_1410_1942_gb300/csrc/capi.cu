@@ -237,7 +237,8 @@ static int setup_march(poisson_t* H) {
 }
 
 static void free_state(poisson_t* H) {
-    void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->top64, H->rinv2, H->eta32, H->eta16, H->x64,
+    void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->top64, H->rinv2, H->ax64, H->ay64,
+                    H->az64, H->vol64, H->bx32, H->by32, H->bz32, H->diag32, H->eta32, H->eta16, H->x64,
                     H->b64, H->r64, H->z64, H->p64a, H->p64b, H->d32, H->r32, H->z32,
                     H->p32a, H->p32b, H->s32a, H->s32b, H->w32a, H->w32b, H->sc,
                     H->partials, H->io_a, H->io_b, H->io_c, H->io_c32};
@@ -363,10 +364,62 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
         Fd = H->b64;
     }
     launch_setup(H->d, Fd, rho_air, rho_water, H->bx, H->by, H->bz, H->diag, H->dinv, H->top64,
-                 H->rinv2, H->eta32, H->eta16, H->st);
+                 H->rinv2, H->eta32, H->eta16, H->apertures(), H->st);
+    if (H->cut() && H->bx32) {
+        const long long n = H->d.n;
+        launch_narrow_f32(n, H->bx, H->bx32, H->st);
+        launch_narrow_f32(n, H->by, H->by32, H->st);
+        launch_narrow_f32(n, H->bz, H->bz32, H->st);
+        launch_narrow_f32(n, H->diag, H->diag32, H->st);
+    }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(H->st));
     H->ready = true;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_set_apertures(poisson_t* H, const double* ax, const double* ay,
+                                     const double* az, const double* vol, int mem) {
+    if (!H) return POISSON_EINVAL;
+    const Dims d = H->d;
+    const size_t nu = (size_t)(d.nx + 1) * d.ny * d.nz, nv = (size_t)d.nx * (d.ny + 1) * d.nz,
+                 nw = (size_t)d.sxy * (d.nz + 1), n = (size_t)d.n;
+    if (!ax && !ay && !az && !vol) {
+        // back to the plain operator
+        for (double** q : {&H->ax64, &H->ay64, &H->az64, &H->vol64}) {
+            dfree(*q);
+            *q = nullptr;
+        }
+        H->d.walls &= ~CUT_CELLS;
+        H->march = H->plan.segs != nullptr;  // the plan built at create, if any
+        H->ready = false;
+        return POISSON_OK;
+    }
+    if (!ax || !ay || !az || !vol) return POISSON_EINVAL;
+    if (mem != POISSON_MEM_HOST && mem != POISSON_MEM_DEVICE) return POISSON_EINVAL;
+    for (const double* q : {ax, ay, az, vol})
+        if (is_device_ptr(q) != (mem == POISSON_MEM_DEVICE)) return POISSON_EINVAL;
+    int rc = POISSON_OK;
+    auto A = [&](int r) { if (rc == POISSON_OK) rc = r; };
+    if (!H->ax64) {
+        A(dalloc(&H->ax64, nu)); A(dalloc(&H->ay64, nv)); A(dalloc(&H->az64, nw));
+        A(dalloc(&H->vol64, n));
+    }
+    if (H->opts.precision != POISSON_FP64 && !H->bx32) {
+        A(dalloc(&H->bx32, n)); A(dalloc(&H->by32, n)); A(dalloc(&H->bz32, n));
+        A(dalloc(&H->diag32, n));
+    }
+    if (rc != POISSON_OK) return rc;
+    const cudaMemcpyKind kind = mem == POISSON_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                          : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(H->ax64, ax, sizeof(double) * nu, kind, H->st));
+    CK(cudaMemcpyAsync(H->ay64, ay, sizeof(double) * nv, kind, H->st));
+    CK(cudaMemcpyAsync(H->az64, az, sizeof(double) * nw, kind, H->st));
+    CK(cudaMemcpyAsync(H->vol64, vol, sizeof(double) * n, kind, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    H->d.walls |= CUT_CELLS;
+    H->march = false;  // the marching kernels form faces from rho/2 and cannot carry fractions
+    H->ready = false;  // poisson_set_density builds the cut operator
     return POISSON_OK;
 }
 
@@ -534,11 +587,10 @@ static int solve_fp64(poisson_t* H, double tol, int* outer, int* inner, double* 
 // FP32 inner PCG on the reduced-precision operator inside FP64 iterative refinement:
 //   r = b - A64 x (FP64); stop when ||r||/||b|| <= tol; solve A32 d = r (FP32 PCG, relative
 //   reduction inner_tol); x += d.
-template <typename E>
-static int solve_mixed(poisson_t* H, const E* eta, double tol, int* outer, int* inner,
+template <typename C32>
+static int solve_mixed(poisson_t* H, const C32& c32, bool bf16, double tol, int* outer, int* inner,
                        double* rel_out) {
     const CoefFaces64 c64{H->bx, H->by, H->bz, H->diag, nullptr};
-    const CoefEta<E> c32{eta};
     const size_t bytes32 = sizeof(float) * (size_t)H->d.n;
     int total = 0, status = POISSON_ENOTCONV, k = 0;
     double rel = INFINITY, prev = INFINITY;
@@ -570,11 +622,11 @@ static int solve_mixed(poisson_t* H, const E* eta, double tol, int* outer, int* 
         Scalars res;
         rc = POISSON_ECUDA;
         if (H->march && H->opts.precond == POISSON_JACOBI) {
-            rc = march_run(H, sizeof(E) == 2, target * target, H->opts.max_iters - total, &res);
+            rc = march_run(H, bf16, target * target, H->opts.max_iters - total, &res);
             if (rc == POISSON_ECUDA) H->march = false;  // launch refused: use the column kernels
         }
         if (!H->march || H->opts.precond != POISSON_JACOBI)
-            rc = cg_loop_columns<float, CoefEta<E>>(H, c32, H->d32, H->r32, H->z32, H->p32a,
+            rc = cg_loop_columns<float, C32>(H, c32, H->d32, H->r32, H->z32, H->p32a,
                                                     H->p32b, target * target, 0,
                                                     H->opts.max_iters - total, &res);
         if (rc) return rc;
@@ -599,10 +651,10 @@ extern "C" int poisson_solve(poisson_t* H, const double* rhs, double* p, double 
     const bool drhs = is_device_ptr(rhs), dp = is_device_ptr(p);
     const double a = -(H->h * H->h);
     if (drhs) {
-        launch_scale((long long)n, rhs, a, H->b64, H->st);
+        launch_scale((long long)n, rhs, a, H->b64, H->st, H->vol64);
     } else {
         CK(cudaMemcpyAsync(H->b64, rhs, bytes, cudaMemcpyHostToDevice, H->st));
-        launch_scale((long long)n, H->b64, a, H->b64, H->st);
+        launch_scale((long long)n, H->b64, a, H->b64, H->st, H->vol64);
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(H->x64, p, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -612,8 +664,16 @@ extern "C" int poisson_solve(poisson_t* H, const double* rhs, double* p, double 
     int status;
     switch (H->opts.precision) {
         case POISSON_FP64: status = solve_fp64(H, tol, &outer, &inner, &rel); break;
-        case POISSON_FP32: status = solve_mixed<float>(H, H->eta32, tol, &outer, &inner, &rel); break;
-        default: status = solve_mixed<__nv_bfloat16>(H, H->eta16, tol, &outer, &inner, &rel); break;
+        default:
+            if (H->cut())  // the open fractions live in the stored faces
+                status = solve_mixed(H, CoefFaces32{H->bx32, H->by32, H->bz32, H->diag32}, false,
+                                     tol, &outer, &inner, &rel);
+            else if (H->opts.precision == POISSON_FP32)
+                status = solve_mixed(H, CoefEta<float>{H->eta32}, false, tol, &outer, &inner, &rel);
+            else
+                status = solve_mixed(H, CoefEta<__nv_bfloat16>{H->eta16}, true, tol, &outer, &inner,
+                                     &rel);
+            break;
     }
     if (status == POISSON_ECUDA) return status;
     CK(cudaMemcpyAsync(p, H->x64, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
@@ -672,18 +732,25 @@ extern "C" int poisson_apply(poisson_t* H, const double* x, double* y, int preci
                 launch_apply<double, CoefFaces64>(d, kc, c, a, b, st);
             });
         }
-        case POISSON_FP32: {
-            const CoefEta<float> c{H->eta32};
-            return with_io(H, x, y, [&](const double* a, double* b) {
-                launch_apply<float, CoefEta<float>>(d, kc, c, a, b, st);
-            });
-        }
-        case POISSON_FP32_BF16COEF: {
-            const CoefEta<__nv_bfloat16> c{H->eta16};
-            return with_io(H, x, y, [&](const double* a, double* b) {
-                launch_apply<float, CoefEta<__nv_bfloat16>>(d, kc, c, a, b, st);
-            });
-        }
+        case POISSON_FP32:
+        case POISSON_FP32_BF16COEF:
+            if (H->cut()) {
+                const CoefFaces32 c{H->bx32, H->by32, H->bz32, H->diag32};
+                return with_io(H, x, y, [&](const double* a, double* b) {
+                    launch_apply<float, CoefFaces32>(d, kc, c, a, b, st);
+                });
+            }
+            if (precision == POISSON_FP32_BF16COEF) {
+                const CoefEta<__nv_bfloat16> c{H->eta16};
+                return with_io(H, x, y, [&](const double* a, double* b) {
+                    launch_apply<float, CoefEta<__nv_bfloat16>>(d, kc, c, a, b, st);
+                });
+            } else {
+                const CoefEta<float> c{H->eta32};
+                return with_io(H, x, y, [&](const double* a, double* b) {
+                    launch_apply<float, CoefEta<float>>(d, kc, c, a, b, st);
+                });
+            }
         default: return POISSON_EINVAL;
     }
 }
@@ -721,6 +788,15 @@ extern "C" int poisson_precond_apply(poisson_t* H, const double* r, double* z, i
             });
         }
         case POISSON_FP32: {
+            if (H->cut()) {
+                const CoefFaces32 c{H->bx32, H->by32, H->bz32, H->diag32};
+                return with_io(H, r, z, [&](const double* a, double* b) {
+                    if (kind == POISSON_RBSSOR)
+                        launch_ssor_apply<float, CoefFaces32>(d, kc, c, a, H->io_c32, om, b, st);
+                    else
+                        launch_jacobi<float, CoefFaces32>(d, kc, c, a, b, st);
+                });
+            }
             const CoefEta<float> c{H->eta32};
             return with_io(H, r, z, [&](const double* a, double* b) {
                 if (kind == POISSON_RBSSOR)
@@ -799,7 +875,8 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
                  : H->plan.strategy == MARCH_SPLIT_LOCKSTEP ? "lockstep"
                                                             : "equal");
     } else {
-        snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d", prec, TX, TY, H->kc);
+        snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d%s", prec, TX, TY, H->kc,
+                 H->cut() ? " cut-cells" : "");
     }
     return POISSON_OK;
 }

@@ -28,6 +28,13 @@ struct poisson_s {
     // 2/rho_c per cell, only when the handle has Dirichlet side/bottom walls (their faces in
     // poisson_project)
     double* rinv2 = nullptr;
+    // free-slip cut cells (poisson_set_apertures): open fractions of the MAC faces, fluid
+    // fractions of the cells, and the FP32 copies of the cut faces and diagonal for the inner
+    // solve (all null without cut cells)
+    double *ax64 = nullptr, *ay64 = nullptr, *az64 = nullptr, *vol64 = nullptr;
+    float *bx32 = nullptr, *by32 = nullptr, *bz32 = nullptr, *diag32 = nullptr;
+    pcg::Apertures apertures() const { return pcg::Apertures{ax64, ay64, az64, vol64}; }
+    bool cut() const { return vol64 != nullptr; }
     // rho / 2 per cell for the reduced-precision inner operator
     float* eta32 = nullptr;
     __nv_bfloat16* eta16 = nullptr;

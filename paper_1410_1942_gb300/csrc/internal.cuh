@@ -29,6 +29,13 @@ struct Dims {
 };
 
 constexpr int PERIODIC_X = 32;
+constexpr int CUT_CELLS = 64;  // face open fractions and cell fluid fractions are in use
+
+// Open fractions of the MAC faces and fluid fractions of the cells (free-slip cut cells); all
+// null when the handle has none.
+struct Apertures {
+    const double *ax, *ay, *az, *vol;
+};
 
 // A Dirichlet side/bottom wall (Dims::walls bit) puts p = 0 on its face: the wall face gets the
 // coefficient 2/rho_c = 1/eta_c, which counts in the diagonal, while the value beyond the wall
@@ -151,6 +158,25 @@ struct CoefFaces64 {
         w.yp = (j + 1 < d.ny) ? by[c + d.nx] : 0.0;
         w.zm = bz[c];
         w.zp = (k + 1 < d.nz) ? bz[c + d.sxy] : 0.0;
+        w.D = diag[c];
+    }
+};
+
+// The FP32 copies of the FP64 faces and diagonal: the inner operator of cut-cell handles (their
+// face coefficients carry the open fractions, which the on-the-fly faces from rho/2 cannot).
+struct CoefFaces32 {
+    const float* bx;
+    const float* by;
+    const float* bz;
+    const float* diag;
+    __device__ __forceinline__ void weights(const Dims& d, int c, int i, int j, int k,
+                                            Stencil<float>& w) const {
+        w.xm = bx[c];
+        w.xp = (i + 1 < d.nx) ? bx[c + 1] : ((d.walls & PERIODIC_X) ? bx[c + 1 - d.nx] : 0.f);
+        w.ym = by[c];
+        w.yp = (j + 1 < d.ny) ? by[c + d.nx] : 0.f;
+        w.zm = bz[c];
+        w.zp = (k + 1 < d.nz) ? bz[c + d.sxy] : 0.f;
         w.D = diag[c];
     }
 };

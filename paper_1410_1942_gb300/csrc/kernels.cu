@@ -30,7 +30,7 @@ __device__ __forceinline__ double rho_of(double F, double ra, double rw) {
 __global__ void k_setup_faces(Dims d, const double* __restrict__ F, double ra, double rw,
                               double* __restrict__ bx, double* __restrict__ by,
                               double* __restrict__ bz, float* __restrict__ eta32,
-                              __nv_bfloat16* __restrict__ eta16) {
+                              __nv_bfloat16* __restrict__ eta16, Apertures ap) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= d.n) return;
     const int c = (int)tid;
@@ -42,6 +42,16 @@ __global__ void k_setup_faces(Dims d, const double* __restrict__ F, double ra, d
                 : 0.0;
     by[c] = (j > 0) ? 2.0 / __dadd_rn(rc, rho_of(F[c - d.nx], ra, rw)) : 0.0;
     bz[c] = (k > 0) ? 2.0 / __dadd_rn(rc, rho_of(F[c - d.sxy], ra, rw)) : 0.0;
+    if (ap.ax) {
+        // cut cells: each face scaled by its open fraction; closed next to a cell with no fluid
+        const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+        const long long fv = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+        const bool act = ap.vol[c] > 0.0;
+        const int cxm = i > 0 ? c - 1 : c + d.nx - 1;
+        bx[c] = (act && ap.vol[cxm] > 0.0) ? __dmul_rn(ap.ax[fu], bx[c]) : 0.0;
+        by[c] = (act && j > 0 && ap.vol[c - d.nx] > 0.0) ? __dmul_rn(ap.ay[fv], by[c]) : 0.0;
+        bz[c] = (act && k > 0 && ap.vol[c - d.sxy] > 0.0) ? __dmul_rn(ap.az[c], bz[c]) : 0.0;
+    }
     const double e = 0.5 * rc;
     if (eta32) eta32[c] = (float)e;
     if (eta16) eta16[c] = __float2bfloat16_rn((float)e);
@@ -54,38 +64,44 @@ __global__ void k_setup_diag(Dims d, const double* __restrict__ F, double ra, do
                              const double* __restrict__ bx, const double* __restrict__ by,
                              const double* __restrict__ bz, double* __restrict__ diag,
                              double* __restrict__ dinv, double* __restrict__ top,
-                             double* __restrict__ rinv2) {
+                             double* __restrict__ rinv2, Apertures ap) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= d.n) return;
     const int c = (int)tid;
     const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
+    const double t = 2.0 / rho_of(F[c], ra, rw);  // a boundary face's coefficient (unscaled)
+    if (k + 1 == d.nz && top) top[c - k * d.sxy] = t;
+    if (rinv2) rinv2[c] = t;
+    if (ap.vol && !(ap.vol[c] > 0.0)) {
+        // cut cells: a cell with no fluid is inactive
+        diag[c] = 1.0;
+        if (dinv) dinv[c] = 1.0;
+        return;
+    }
+    const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+    const long long fv = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+    // a boundary term, scaled by its face's open fraction with cut cells
+    auto bnd = [&](const double* a, long long f) { return a ? __dmul_rn(a[f], t) : t; };
     double s = __dadd_rn(__dadd_rn(bx[c], by[c]), bz[c]);
     if (i + 1 < d.nx) s = __dadd_rn(s, bx[c + 1]);
     else if (d.walls & PERIODIC_X) s = __dadd_rn(s, bx[c + 1 - d.nx]);
     if (j + 1 < d.ny) s = __dadd_rn(s, by[c + d.nx]);
-    if (k + 1 < d.nz) {
-        s = __dadd_rn(s, bz[c + d.sxy]);
-    } else {
-        const double t = 2.0 / rho_of(F[c], ra, rw);
-        s = __dadd_rn(s, t);
-        if (top) top[c - k * d.sxy] = t;
-    }
-    if (d.walls) {
-        const double t = 2.0 / rho_of(F[c], ra, rw);
-        if ((d.walls & 1) && i == 0) s = __dadd_rn(s, t);
-        if ((d.walls & 2) && i == d.nx - 1) s = __dadd_rn(s, t);
-        if ((d.walls & 4) && j == 0) s = __dadd_rn(s, t);
-        if ((d.walls & 8) && j == d.ny - 1) s = __dadd_rn(s, t);
-        if ((d.walls & 16) && k == 0) s = __dadd_rn(s, t);
-        if (rinv2) rinv2[c] = t;
-    }
+    if (k + 1 < d.nz) s = __dadd_rn(s, bz[c + d.sxy]);
+    else s = __dadd_rn(s, bnd(ap.az, c + (long long)d.sxy));
+    if ((d.walls & 1) && i == 0) s = __dadd_rn(s, bnd(ap.ax, fu));
+    if ((d.walls & 2) && i == d.nx - 1) s = __dadd_rn(s, bnd(ap.ax, fu + 1));
+    if ((d.walls & 4) && j == 0) s = __dadd_rn(s, bnd(ap.ay, fv));
+    if ((d.walls & 8) && j == d.ny - 1) s = __dadd_rn(s, bnd(ap.ay, fv + d.nx));
+    if ((d.walls & 16) && k == 0) s = __dadd_rn(s, bnd(ap.az, c));
     diag[c] = s;
     if (dinv) dinv[c] = 1.0 / s;
 }
 
-__global__ void k_scale(long long n, const double* __restrict__ s, double a, double* __restrict__ b) {
+// b = a s, or a (vol s) with cut cells (vol: fluid fractions, may be null)
+__global__ void k_scale(long long n, const double* __restrict__ s, double a,
+                        const double* __restrict__ vol, double* __restrict__ b) {
     const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (t < n) b[t] = __dmul_rn(a, s[t]);
+    if (t < n) b[t] = __dmul_rn(a, vol ? __dmul_rn(vol[t], s[t]) : s[t]);
 }
 
 __global__ void k_update64(long long n, double* __restrict__ x, const float* __restrict__ dlt) {
@@ -139,6 +155,11 @@ __device__ __forceinline__ float inv_diag<float, CoefEta<float>>(const CoefEta<f
 template <>
 __device__ __forceinline__ float inv_diag<float, CoefEta<__nv_bfloat16>>(
     const CoefEta<__nv_bfloat16>&, int, const Stencil<float>& w) {
+    return rcp_approx(w.D);
+}
+template <>
+__device__ __forceinline__ float inv_diag<float, CoefFaces32>(const CoefFaces32&, int,
+                                                              const Stencil<float>& w) {
     return rcp_approx(w.D);
 }
 
@@ -602,14 +623,16 @@ static inline unsigned blocks1d(long long n) { return (unsigned)((n + 255) / 256
 
 void launch_setup(const Dims& d, const double* F, double ra, double rw, double* bx, double* by,
                   double* bz, double* diag, double* dinv, double* top, double* rinv2,
-                  float* eta32, __nv_bfloat16* eta16, cudaStream_t st) {
-    k_setup_faces<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, eta32, eta16);
-    k_setup_diag<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, diag, dinv, top, rinv2);
+                  float* eta32, __nv_bfloat16* eta16, const Apertures& ap, cudaStream_t st) {
+    k_setup_faces<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, eta32, eta16, ap);
+    k_setup_diag<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, diag, dinv, top, rinv2,
+                                                ap);
     counted(2);
 }
 
-void launch_scale(long long n, const double* s, double a, double* b, cudaStream_t st) {
-    k_scale<<<blocks1d(n), 256, 0, st>>>(n, s, a, b);
+void launch_scale(long long n, const double* s, double a, double* b, cudaStream_t st,
+                  const double* vol) {
+    k_scale<<<blocks1d(n), 256, 0, st>>>(n, s, a, vol, b);
     counted(1);
 }
 
@@ -749,5 +772,6 @@ void launch_batch_init(const JobDev* jobs, int njobs, int blocks, cudaStream_t s
 INSTANTIATE(double, CoefFaces64)
 INSTANTIATE(float, CoefEta<float>)
 INSTANTIATE(float, CoefEta<__nv_bfloat16>)
+INSTANTIATE(float, CoefFaces32)
 
 }  // namespace pcg

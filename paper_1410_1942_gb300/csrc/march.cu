@@ -892,7 +892,7 @@ static bool encode3d(CUtensorMap* m, const void* base, CUtensorMapDataType dt, i
 bool march_supported(const Dims& d) {
     // global strides must be multiples of 16 bytes for FP32 and BF16 rows
     // (periodic x: the tiles' TMA halo boxes do not wrap; the column kernels serve it)
-    return (d.nx % 8) == 0 && !(d.walls & PERIODIC_X) && encode_fn() != nullptr;
+    return (d.nx % 8) == 0 && !(d.walls & (PERIODIC_X | CUT_CELLS)) && encode_fn() != nullptr;
 }
 
 // ------------------------------------------------------------------ variant table

@@ -31,13 +31,27 @@ inline unsigned blocks_of(long long n) { return (unsigned)((n + PT - 1) / PT); }
 __global__ void __launch_bounds__(PT) k_divergence(Dims d, double hd, const double* __restrict__ u,
                                                    const double* __restrict__ v,
                                                    const double* __restrict__ w,
-                                                   double* __restrict__ s) {
+                                                   double* __restrict__ s, pcg::Apertures ap) {
     const long long t = blockIdx.x * (long long)PT + threadIdx.x;
     if (t >= d.n) return;
     const int c = (int)t;
     const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
     const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
     const long long fv = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+    if (ap.vol) {
+        // cut cells: fluxes a u, divided by the cell's fluid fraction; 0 in inactive cells
+        if (!(ap.vol[c] > 0.0)) {
+            s[c] = 0.0;
+            return;
+        }
+        const long long up = c + (long long)d.sxy;
+        const double du = __dsub_rn(__dmul_rn(ap.ax[fu + 1], u[fu + 1]), __dmul_rn(ap.ax[fu], u[fu]));
+        const double dv = __dsub_rn(__dmul_rn(ap.ay[fv + d.nx], v[fv + d.nx]),
+                                    __dmul_rn(ap.ay[fv], v[fv]));
+        const double dw = __dsub_rn(__dmul_rn(ap.az[up], w[up]), __dmul_rn(ap.az[c], w[c]));
+        s[c] = __ddiv_rn(__ddiv_rn(__dadd_rn(__dadd_rn(du, dv), dw), hd), ap.vol[c]);
+        return;
+    }
     const double du = __dsub_rn(u[fu + 1], u[fu]);
     const double dv = __dsub_rn(v[fv + d.nx], v[fv]);
     const double dw = __dsub_rn(w[c + (long long)d.sxy], w[c]);
@@ -57,28 +71,32 @@ __global__ void __launch_bounds__(PT) k_project(Dims d, double h, double dt,
                                                 const double* __restrict__ top,
                                                 const double* __restrict__ rinv2,
                                                 const double* __restrict__ p, double* __restrict__ u,
-                                                double* __restrict__ v, double* __restrict__ w) {
+                                                double* __restrict__ v, double* __restrict__ w,
+                                                pcg::Apertures ap) {
     const long long t = blockIdx.x * (long long)PT + threadIdx.x;
     if (t >= d.n) return;
     const int c = (int)t;
     const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
     const double pc = p[c];
+    const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+    const long long fv = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+    // cut cells: an open face's own coefficient is the cut coefficient over its open fraction
+    auto beta = [&](const double* a, long long f, double b) {
+        return a ? (b != 0.0 ? __ddiv_rn(b, a[f]) : 0.0) : b;
+    };
     if (i > 0) {
-        const long long f = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
-        u[f] = corrected(u[f], dt, bx[c], pc, p[c - 1], h);
+        u[fu] = corrected(u[fu], dt, beta(ap.ax, fu, bx[c]), pc, p[c - 1], h);
     } else if (d.walls & pcg::PERIODIC_X) {
         // periodic x: faces 0 and nx are one face, corrected from face 0 and written to both
-        const long long f = (long long)(d.nx + 1) * (j + (long long)d.ny * k);
-        const double q = corrected(u[f], dt, bx[c], pc, p[c + d.nx - 1], h);
-        u[f] = q;
-        u[f + d.nx] = q;
+        const double q = corrected(u[fu], dt, beta(ap.ax, fu, bx[c]), pc, p[c + d.nx - 1], h);
+        u[fu] = q;
+        u[fu + d.nx] = q;
     }
-    if (j > 0) {
-        const long long f = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
-        v[f] = corrected(v[f], dt, by[c], pc, p[c - d.nx], h);
-    }
-    if (k > 0) w[c] = corrected(w[c], dt, bz[c], pc, p[c - d.sxy], h);
-    if (k + 1 == d.nz) {
+    if (j > 0) v[fv] = corrected(v[fv], dt, beta(ap.ay, fv, by[c]), pc, p[c - d.nx], h);
+    if (k > 0) w[c] = corrected(w[c], dt, beta(ap.az, c, bz[c]), pc, p[c - d.sxy], h);
+    if (ap.vol && !(ap.vol[c] > 0.0)) return;  // inactive: no boundary faces
+    auto open = [&](const double* a, long long f) { return !a || a[f] > 0.0; };
+    if (k + 1 == d.nz && open(ap.az, c + (long long)d.sxy)) {
         // top face: p = 0 there; (1/rho_c) (0 - p_c) / (h/2) = (2/rho_c) ((0 - p_c) / h)
         const long long f = c + (long long)d.sxy;
         w[f] = corrected(w[f], dt, top[c - k * d.sxy], 0.0, pc, h);
@@ -86,13 +104,13 @@ __global__ void __launch_bounds__(PT) k_project(Dims d, double h, double dt,
     if (d.walls & POISSON_WALLS_ALL) {
         // Dirichlet walls: p = 0 on the wall face, (2/rho_c) times the difference to 0 over h
         const double t = rinv2[c];
-        const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
-        const long long fv = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
-        if ((d.walls & 1) && i == 0) u[fu] = corrected(u[fu], dt, t, pc, 0.0, h);
-        if ((d.walls & 2) && i == d.nx - 1) u[fu + 1] = corrected(u[fu + 1], dt, t, 0.0, pc, h);
-        if ((d.walls & 4) && j == 0) v[fv] = corrected(v[fv], dt, t, pc, 0.0, h);
-        if ((d.walls & 8) && j == d.ny - 1) v[fv + d.nx] = corrected(v[fv + d.nx], dt, t, 0.0, pc, h);
-        if ((d.walls & 16) && k == 0) w[c] = corrected(w[c], dt, t, pc, 0.0, h);
+        if ((d.walls & 1) && i == 0 && open(ap.ax, fu)) u[fu] = corrected(u[fu], dt, t, pc, 0.0, h);
+        if ((d.walls & 2) && i == d.nx - 1 && open(ap.ax, fu + 1))
+            u[fu + 1] = corrected(u[fu + 1], dt, t, 0.0, pc, h);
+        if ((d.walls & 4) && j == 0 && open(ap.ay, fv)) v[fv] = corrected(v[fv], dt, t, pc, 0.0, h);
+        if ((d.walls & 8) && j == d.ny - 1 && open(ap.ay, fv + d.nx))
+            v[fv + d.nx] = corrected(v[fv + d.nx], dt, t, 0.0, pc, h);
+        if ((d.walls & 16) && k == 0 && open(ap.az, c)) w[c] = corrected(w[c], dt, t, pc, 0.0, h);
     }
 }
 
@@ -161,7 +179,8 @@ extern "C" int poisson_divergence(poisson_t* H, const double* u, const double* v
         finish(H->st);
         return rc;
     }
-    k_divergence<<<blocks_of(d.n), PT, 0, H->st>>>(d, H->h * dt, U.dev, V.dev, W.dev, S.dev);
+    k_divergence<<<blocks_of(d.n), PT, 0, H->st>>>(d, H->h * dt, U.dev, V.dev, W.dev, S.dev,
+                                                  H->apertures());
     pcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     if (cudaGetLastError() != cudaSuccess) rc = POISSON_ECUDA;
     if (rc == POISSON_OK) rc = S.flush(H->st);
@@ -186,7 +205,8 @@ extern "C" int poisson_project(poisson_t* H, double* u, double* v, double* w, co
         return rc;
     }
     k_project<<<blocks_of(d.n), PT, 0, H->st>>>(d, H->h, dt, H->bx, H->by, H->bz, H->top64,
-                                                H->rinv2, P.dev, U.dev, V.dev, W.dev);
+                                                H->rinv2, P.dev, U.dev, V.dev, W.dev,
+                                                H->apertures());
     pcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     if (cudaGetLastError() != cudaSuccess) rc = POISSON_ECUDA;
     if (rc == POISSON_OK) rc = U.flush(H->st);
