@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--walls", type=int, default=0,
                     help="Dirichlet side/bottom walls bitmask (1 x-, 2 x+, 4 y-, 8 y+, 16 z-)")
     ap.add_argument("--periodic-x", action="store_true", help="periodic x boundaries")
+    ap.add_argument("--cut-body", action="store_true",
+                    help="the strut as a free-slip cut-cell body (face and volume fractions)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 comparison, batched and served measurements")
     ap.add_argument("--serve-requests", type=int, default=24)
@@ -367,6 +369,12 @@ def main():
     solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision, precond=args.precond,
                           stream=stream.cuda_stream, tile=args.tile, dirichlet_walls=args.walls,
                           periodic_x=args.periodic_x)
+    apertures = None
+    if args.cut_body:
+        Lx, Ly, _ = g.lengths
+        psi = lambda x, y, z: inputs.ellipse_sdf(x, y, 0.5 * Lx, 0.5 * Ly, 0.1, 0.02)
+        apertures = inputs.cut_apertures(g, psi)
+        solver.set_apertures(*apertures)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
@@ -453,6 +461,8 @@ def main():
         solver_h = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision,
                                 precond=args.precond, stream=stream.cuda_stream, tile=args.tile,
                                 dirichlet_walls=args.walls, periodic_x=args.periodic_x)
+        if apertures is not None:
+            solver_h.set_apertures(*apertures)
 
         def step_e2e():
             p_h.zero_()
@@ -506,7 +516,8 @@ def main():
                         (WORKLOAD if tuple(args.shape) == (256, 128, 128)
                          else "strut %dx%dx%d (profiling case)" % tuple(args.shape)), "cells": g.n, "precision": args.precision,
                        "precond": args.precond, "tol": case.tol,
-                       "boundaries": ("periodic x, " if args.periodic_x else "") +
+                       "boundaries": ("strut as a free-slip cut-cell body, " if args.cut_body
+                                      else "") + ("periodic x, " if args.periodic_x else "") +
                                      ("Dirichlet walls mask %d" % args.walls if args.walls
                                       else "zero-gradient side/bottom walls") + ", p = 0 on top",
                        "l2": "flushed between steps (256 MiB write)",
