@@ -432,8 +432,9 @@ Executor* g_exec[2] = {nullptr, nullptr};  // FP32 and BF16 coefficients
 uint64_t g_next = 1;
 
 bool batchable(const poisson_t* H) {
+    // (periodic handles run their own padded one-sweep plans: solved one by one)
     return H->opts.precision != POISSON_FP64 && H->opts.precond == POISSON_JACOBI &&
-           march_supported(H->d) && H->march;
+           march_supported(H->d) && H->march && !H->periodic();
 }
 
 }  // namespace

@@ -122,6 +122,10 @@ static int num_sms() {
 
 static MarchSolve march_solve_of(poisson_t* H) {
     const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
+    if (H->periodic())  // the one-sweep kernels on padded rows (u: pu, s^: ps, w^: pw)
+        return MarchSolve{H->d, H->d32, H->r32, H->pu[0], H->p32a, H->pu[1],
+                          bf16 ? (const void*)H->peta16 : (const void*)H->peta32, H->sc,
+                          H->ps[0], H->ps[1], H->pw[0], H->pw[1]};
     return MarchSolve{H->d, H->d32, H->r32, H->z32, H->p32a, H->p32b,
                       bf16 ? (const void*)H->eta16 : (const void*)H->eta32, H->sc,
                       H->s32a, H->s32b, H->w32a, H->w32b};
@@ -144,8 +148,14 @@ static int march_run(poisson_t* H, bool bf16, double tol2, int max_iter, Scalars
     cudaMemsetAsync(H->p32a, 0, sizeof(float) * (size_t)d.n, st);
     if (march_variant(H->plan.variant).family == 1) {
         // the start-up sweep reads s^ and w^ (times alpha = beta = 0): they must be finite
-        cudaMemsetAsync(H->s32a, 0, sizeof(float) * (size_t)d.n, st);
-        cudaMemsetAsync(H->w32a, 0, sizeof(float) * (size_t)d.n, st);
+        if (H->periodic()) {
+            const size_t np = (size_t)(d.nx + 2 * PAD_V) * d.ny * d.nz;
+            cudaMemsetAsync(H->ps[0], 0, sizeof(float) * np, st);
+            cudaMemsetAsync(H->pw[0], 0, sizeof(float) * np, st);
+        } else {
+            cudaMemsetAsync(H->s32a, 0, sizeof(float) * (size_t)d.n, st);
+            cudaMemsetAsync(H->w32a, 0, sizeof(float) * (size_t)d.n, st);
+        }
     }
     if (bf16)
         launch_cg_init<float, CoefEta<__nv_bfloat16>>(d, H->kc, CoefEta<__nv_bfloat16>{H->eta16},
@@ -154,6 +164,7 @@ static int march_run(poisson_t* H, bool bf16, double tol2, int max_iter, Scalars
     else
         launch_cg_init<float, CoefEta<float>>(d, H->kc, CoefEta<float>{H->eta32}, H->r32, H->z32,
                                               H->sc, H->partials, tol2, 0, max_iter, st);
+    if (H->periodic()) launch_pad_rows_f32(d, PAD_V, H->z32, H->pu[0], st);  // u = D^-1 r, padded
     *H->ctl_host = MarchCtl{0u, 1, 0, 0, 0ull};
     CK(cudaMemcpyAsync(H->plan.ctl, H->ctl_host, sizeof(MarchCtl), cudaMemcpyHostToDevice, st));
     const bool prof = H->prof_on && result;
@@ -174,6 +185,8 @@ static int setup_march(poisson_t* H) {
     if (forced > 0) {
         var = march_variant_of_tile(forced);
         strategy = march_split_of_tile(forced);
+        // periodic x runs on the one-sweep kernels only (others: the column kernels)
+        if (H->periodic() && march_variant(var).family != 1) return POISSON_OK;
     } else {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(tune_key(d, bf16));
@@ -189,6 +202,10 @@ static int setup_march(poisson_t* H) {
         cudaStream_t st = H->st;
         if (bf16) launch_fill_bf16(n, H->eta16, 0.5f, st);
         else launch_fill_f32(n, H->eta32, 0.5f, st);
+        if (H->periodic()) {  // the one-sweep kernels read rho/2 from padded rows
+            if (H->peta32) launch_pad_rows_f32(d, 4, H->eta32, H->peta32, st);
+            if (H->peta16) launch_pad_rows_bf16(d, 8, H->eta16, H->peta16, st);
+        }
         launch_fill_f32(n, H->r32, 1.0f, st);
         cudaEvent_t e0, e1;
         cudaEventCreate(&e0);
@@ -200,6 +217,7 @@ static int setup_march(poisson_t* H) {
         for (int cand = 0; cand < march_variant_count(); ++cand) {
             const MarchVariant mv = march_variant(cand);
             if (mv.cx != 2 || mv.family == 2 || march_occupancy(cand, bf16) <= 0) continue;
+            if (H->periodic() && mv.family != 1) continue;  // only the one-sweep kernels wrap
             for (int strat = 0; strat < MARCH_SPLITS; ++strat) {
                 if (build_plan(H, cand, strat) != 0) continue;
                 float t[2];
@@ -238,7 +256,8 @@ static int setup_march(poisson_t* H) {
 
 static void free_state(poisson_t* H) {
     void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->top64, H->rinv2, H->ax64, H->ay64,
-                    H->az64, H->vol64, H->bx32, H->by32, H->bz32, H->diag32, H->eta32, H->eta16, H->x64,
+                    H->az64, H->vol64, H->bx32, H->by32, H->bz32, H->diag32, H->pu[0], H->pu[1],
+                    H->ps[0], H->ps[1], H->pw[0], H->pw[1], H->peta32, H->peta16, H->eta32, H->eta16, H->x64,
                     H->b64, H->r64, H->z64, H->p64a, H->p64b, H->d32, H->r32, H->z32,
                     H->p32a, H->p32b, H->s32a, H->s32b, H->w32a, H->w32b, H->sc,
                     H->partials, H->io_a, H->io_b, H->io_c, H->io_c32};
@@ -302,6 +321,15 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     const size_t N = (size_t)n;
     A(dalloc(&H->bx, N)); A(dalloc(&H->by, N)); A(dalloc(&H->bz, N)); A(dalloc(&H->diag, N));
     A(dalloc(&H->top64, (size_t)nx * ny));
+    if (o.periodic_x && o.precision != POISSON_FP64 && nx % 8 == 0) {
+        // padded rows for the one-sweep marching kernels (ghost columns, PAD_V each side)
+        const size_t np = (size_t)(nx + 2 * PAD_V) * ny * nz;
+        for (int b = 0; b < 2; ++b) {
+            A(dalloc(&H->pu[b], np)); A(dalloc(&H->ps[b], np)); A(dalloc(&H->pw[b], np));
+        }
+        if (o.precision == POISSON_FP32) A(dalloc(&H->peta32, (size_t)(nx + 8) * ny * nz));
+        else A(dalloc(&H->peta16, (size_t)(nx + 16) * ny * nz));
+    }
     if (o.dirichlet_walls) A(dalloc(&H->rinv2, N));  // (not needed for periodic x)
     A(dalloc(&H->eta32, N)); A(dalloc(&H->eta16, N));
     A(dalloc(&H->x64, N)); A(dalloc(&H->b64, N));
@@ -365,6 +393,11 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
     }
     launch_setup(H->d, Fd, rho_air, rho_water, H->bx, H->by, H->bz, H->diag, H->dinv, H->top64,
                  H->rinv2, H->eta32, H->eta16, H->apertures(), H->st);
+    if (H->periodic() && H->pu[0]) {
+        // rho/2 in rows padded by its halo width (4 FP32 / 8 BF16 columns, 16 bytes)
+        if (H->peta32) launch_pad_rows_f32(H->d, 4, H->eta32, H->peta32, H->st);
+        if (H->peta16) launch_pad_rows_bf16(H->d, 8, H->eta16, H->peta16, H->st);
+    }
     if (H->cut() && H->bx32) {
         const long long n = H->d.n;
         launch_narrow_f32(n, H->bx, H->bx32, H->st);

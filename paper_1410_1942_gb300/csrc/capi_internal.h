@@ -34,6 +34,12 @@ struct poisson_s {
     double *ax64 = nullptr, *ay64 = nullptr, *az64 = nullptr, *vol64 = nullptr;
     float *bx32 = nullptr, *by32 = nullptr, *bz32 = nullptr, *diag32 = nullptr;
     pcg::Apertures apertures() const { return pcg::Apertures{ax64, ay64, az64, vol64}; }
+    // periodic x on the one-sweep marching kernels: u, s^, w^ (both buffers) and rho/2 in rows
+    // padded with ghost columns (PAD_V each side; rho/2 by its halo width)
+    float *pu[2] = {nullptr, nullptr}, *ps[2] = {nullptr, nullptr}, *pw[2] = {nullptr, nullptr};
+    float* peta32 = nullptr;
+    __nv_bfloat16* peta16 = nullptr;
+    bool periodic() const { return (d.walls & pcg::PERIODIC_X) != 0; }
     bool cut() const { return vol64 != nullptr; }
     // rho / 2 per cell for the reduced-precision inner operator
     float* eta32 = nullptr;

@@ -612,6 +612,21 @@ __global__ void __launch_bounds__(TX * TY) k_batch_init(const JobDev* jobs, int 
     }
 }
 
+// Rows padded with `pad` ghost columns on each side (periodic x): the data at column i + pad,
+// the ghosts holding the other end of the row.
+template <typename T>
+__global__ void k_pad_rows(Dims d, int pad, const T* __restrict__ src, T* __restrict__ dst) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (t >= d.n) return;
+    const int c = (int)t;
+    const int i = c % d.nx, row = c / d.nx;
+    const long long base = (long long)(d.nx + 2 * pad) * row + pad;
+    const T v = src[c];
+    dst[base + i] = v;
+    if (i < pad) dst[base + i + d.nx] = v;
+    if (i >= d.nx - pad) dst[base + i - d.nx] = v;
+}
+
 // ------------------------------------------------------------------ host launchers
 std::atomic<unsigned long long> g_kernel_launches{0};
 static inline void counted(int k) { g_kernel_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
@@ -648,6 +663,17 @@ void launch_fill_f32(long long n, float* p, float v, cudaStream_t st) {
 
 void launch_fill_bf16(long long n, __nv_bfloat16* p, float v, cudaStream_t st) {
     k_fill<__nv_bfloat16><<<blocks1d(n), 256, 0, st>>>(n, p, v);
+    counted(1);
+}
+
+void launch_pad_rows_f32(const Dims& d, int pad, const float* src, float* dst, cudaStream_t st) {
+    k_pad_rows<float><<<blocks1d(d.n), 256, 0, st>>>(d, pad, src, dst);
+    counted(1);
+}
+
+void launch_pad_rows_bf16(const Dims& d, int pad, const __nv_bfloat16* src, __nv_bfloat16* dst,
+                          cudaStream_t st) {
+    k_pad_rows<__nv_bfloat16><<<blocks1d(d.n), 256, 0, st>>>(d, pad, src, dst);
     counted(1);
 }
 

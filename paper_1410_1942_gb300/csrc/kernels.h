@@ -17,6 +17,10 @@ void launch_scale(long long n, const double* s, double a, double* b, cudaStream_
                   const double* vol = nullptr);
 void launch_update64(long long n, double* x, const float* dlt, cudaStream_t st);
 void launch_narrow_f32(long long n, const double* a, float* b, cudaStream_t st);
+// rows padded with `pad` ghost columns each side holding the other end of the row (periodic x)
+void launch_pad_rows_f32(const Dims& d, int pad, const float* src, float* dst, cudaStream_t st);
+void launch_pad_rows_bf16(const Dims& d, int pad, const __nv_bfloat16* src, __nv_bfloat16* dst,
+                          cudaStream_t st);
 void launch_fill_f32(long long n, float* p, float v, cudaStream_t st);
 void launch_fill_bf16(long long n, __nv_bfloat16* p, float v, cudaStream_t st);
 void launch_residual64(const Dims& d, int kc, const CoefFaces64& c, const double* b,

@@ -892,7 +892,9 @@ static bool encode3d(CUtensorMap* m, const void* base, CUtensorMapDataType dt, i
 bool march_supported(const Dims& d) {
     // global strides must be multiples of 16 bytes for FP32 and BF16 rows
     // (periodic x: the tiles' TMA halo boxes do not wrap; the column kernels serve it)
-    return (d.nx % 8) == 0 && !(d.walls & (PERIODIC_X | CUT_CELLS)) && encode_fn() != nullptr;
+    // (cut cells: the faces carry open fractions the kernels cannot form from rho/2; periodic x
+    // runs on the one-sweep kernels with padded rows)
+    return (d.nx % 8) == 0 && !(d.walls & CUT_CELLS) && encode_fn() != nullptr;
 }
 
 // ------------------------------------------------------------------ variant table
@@ -1009,6 +1011,7 @@ bool march_encode_solve(CUtensorMap (&m)[MAPS_PER_SOLVE], const MarchSolve& s, i
     const CUtensorMapDataType edt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : f32;
     const Dims& d = s.d;
     bool ok = true;
+    if ((d.walls & PERIODIC_X) && v.family != 1) return false;  // no wrapped halos there
     if (v.family == 2) {
         const int bw = v.width + 8, bh = v.height + 4;
         ok = ok && s.sa;
@@ -1022,14 +1025,21 @@ bool march_encode_solve(CUtensorMap (&m)[MAPS_PER_SOLVE], const MarchSolve& s, i
     }
     if (v.family == 1) {
         const int bw = v.width + 8, bh = v.height + 2;
+        // periodic x: u, s^, w^ and eta in rows padded with ghost columns
+        const bool per = d.walls & PERIODIC_X;
+        Dims dv = d, de = d;
+        if (per) {
+            dv.nx = d.nx + 2 * PAD_V;
+            de.nx = d.nx + 2 * eoff;
+        }
         ok = ok && s.sa && s.sb && s.wa && s.wb;
-        ok = ok && encode3d(&m[MAP1_U0], s.z, f32, 4, d, bw, bh);
-        ok = ok && encode3d(&m[MAP1_U1], s.pb, f32, 4, d, bw, bh);
-        ok = ok && encode3d(&m[MAP1_S0], s.sa, f32, 4, d, bw, bh);
-        ok = ok && encode3d(&m[MAP1_S1], s.sb, f32, 4, d, bw, bh);
-        ok = ok && encode3d(&m[MAP1_W0], s.wa, f32, 4, d, bw, bh);
-        ok = ok && encode3d(&m[MAP1_W1], s.wb, f32, 4, d, bw, bh);
-        ok = ok && encode3d(&m[MAP1_ETA], s.eta, edt, bf16 ? 2 : 4, d, v.width + 2 * eoff, bh);
+        ok = ok && encode3d(&m[MAP1_U0], s.z, f32, 4, dv, bw, bh);
+        ok = ok && encode3d(&m[MAP1_U1], s.pb, f32, 4, dv, bw, bh);
+        ok = ok && encode3d(&m[MAP1_S0], s.sa, f32, 4, dv, bw, bh);
+        ok = ok && encode3d(&m[MAP1_S1], s.sb, f32, 4, dv, bw, bh);
+        ok = ok && encode3d(&m[MAP1_W0], s.wa, f32, 4, dv, bw, bh);
+        ok = ok && encode3d(&m[MAP1_W1], s.wb, f32, 4, dv, bw, bh);
+        ok = ok && encode3d(&m[MAP1_ETA], s.eta, edt, bf16 ? 2 : 4, de, v.width + 2 * eoff, bh);
         ok = ok && encode3d(&m[MAP1_X], s.x, f32, 4, d, v.width, v.height);
         ok = ok && encode3d(&m[MAP1_P], s.pa, f32, 4, d, v.width, v.height);
         return ok;

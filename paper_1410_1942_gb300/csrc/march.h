@@ -30,6 +30,12 @@ enum { MAP1_U0 = 0, MAP1_U1 = 1, MAP1_S0 = 2, MAP1_S1 = 3, MAP1_W0 = 4, MAP1_W1 
 enum { MAP2_U0 = 0, MAP2_U1 = 1, MAP2_P0 = 2, MAP2_P1 = 3, MAP2_ETA = 4, MAP2_X = 5 };
 constexpr int MAPS_PER_SOLVE = 9;
 
+// Periodic x in the one-sweep kernels: u, s^, w^ live in rows padded with PAD_V ghost columns on
+// each side (eta with its halo width: 4 FP32 / 8 BF16 columns), the ghosts holding the other end
+// of the row, so the TMA halo boxes read wrapped values; the CTAs writing the first and last
+// PAD_V columns of a row also write their ghost copies.
+constexpr int PAD_V = 4;
+
 // One solve of a plan as the host describes it.
 struct MarchSolve {
     Dims d;

@@ -62,6 +62,8 @@ struct LocalSolve1 {
     double gamma, alpha, beta, rr, stop2;
     double alpha_prev;  // alpha of the previous iteration (odd iterations update x with it)
     double den;         // delta - beta gamma / alpha of the last iteration: (p, A p)
+    int per;            // periodic x: u, s^, w^ and eta live in padded rows with ghost columns
+    int nxp;            // row length of u, s^, w^ (nx + 2 PAD_V when periodic)
     double ginv[2];     // 1/gamma, by the parity of the grid barrier it was formed at
     int done, iter, max_iter, finished, owner, first;
     int xfix;           // stopped after an even iteration: x still lacks alpha p
@@ -133,6 +135,8 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
         L.finished = 0;
         L.first = 1;
         L.xfix = 0;
+        L.per = (sv.d.walls & PERIODIC_X) ? 1 : 0;
+        L.nxp = sv.d.nx + (L.per ? 2 * PAD_V : 0);
         L.owner = 0;
         for (int q = 0; q < nseg; ++q)
             if (s_seg[q].slot == sv.seg_begin) L.owner = 1;
@@ -155,6 +159,9 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             const int L = sg.k1 - sg.k0;
             const CUtensorMap* m = a.maps + MAPS_PER_SOLVE * sg.solve;
             const bool xs = s_nextxs[sg.solve - first] != 0;
+            // periodic x: the padded rows start PAD_V (eta: EOFF) columns before x = 0
+            const bool per = s_sol[sg.solve - first].per != 0;
+            const int xv = sg.x0 - G::VOFF + (per ? PAD_V : 0), xe = sg.x0 - G::EOFF + (per ? G::EOFF : 0);
             for (int off = 0; off < L + 2; ++off) {
                 if (s_fail) return;
                 const int st = np % NS, kk = sg.k0 - 1 + off;
@@ -166,10 +173,10 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                 const bool centre = off > 0 && off <= L;
                 uint64_t* bar = &full[st];
                 mbar_arrive_expect_tx(bar, centre ? (xs ? G::TX : G::TX - G::CB) : G::TX_HALO);
-                tma_load_3d(dst + G::U, m + MAP1_U0 + in, bar, sg.x0 - G::VOFF, sg.y0 - 1, kk);
-                tma_load_3d(dst + G::S, m + MAP1_S0 + in, bar, sg.x0 - G::VOFF, sg.y0 - 1, kk);
-                tma_load_3d(dst + G::WV, m + MAP1_W0 + in, bar, sg.x0 - G::VOFF, sg.y0 - 1, kk);
-                tma_load_3d(dst + G::ETA, m + MAP1_ETA, bar, sg.x0 - G::EOFF, sg.y0 - 1, kk);
+                tma_load_3d(dst + G::U, m + MAP1_U0 + in, bar, xv, sg.y0 - 1, kk);
+                tma_load_3d(dst + G::S, m + MAP1_S0 + in, bar, xv, sg.y0 - 1, kk);
+                tma_load_3d(dst + G::WV, m + MAP1_W0 + in, bar, xv, sg.y0 - 1, kk);
+                tma_load_3d(dst + G::ETA, m + MAP1_ETA, bar, xe, sg.y0 - 1, kk);
                 if (centre) {
                     if (xs) tma_load_3d(dst + G::X, m + MAP1_X, bar, sg.x0, sg.y0, kk);
                     tma_load_3d(dst + G::P, m + MAP1_P, bar, sg.x0, sg.y0, kk);
@@ -296,9 +303,20 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                                     (size_t)i0 + (size_t)d.nx * (j0 + y + (size_t)d.ny * k);
                                 if (xs) st_row<CX>(s_sol[l].x + c, xn);
                                 st_row<CX>(s_sol[l].p + c, pn);
-                                st_row<CX>(s_sol[l].u[out] + c, uc[y]);
-                                st_row<CX>(s_sol[l].s[out] + c, sn);
-                                st_row<CX>(s_sol[l].w[out] + c, wn);
+                                const LocalSolve1& Ls = s_sol[l];
+                                const size_t row = (size_t)Ls.nxp * (j0 + y + (size_t)d.ny * k);
+                                const size_t cp = row + i0 + (Ls.per ? PAD_V : 0);
+                                st_row<CX>(Ls.u[out] + cp, uc[y]);
+                                st_row<CX>(Ls.s[out] + cp, sn);
+                                st_row<CX>(Ls.w[out] + cp, wn);
+                                if (Ls.per && (i0 < PAD_V || i0 >= d.nx - PAD_V)) {
+                                    // the ghost copy at the other end of the padded row
+                                    const long long cg = (long long)row + i0 + PAD_V +
+                                                         (i0 < PAD_V ? d.nx : -d.nx);
+                                    st_row<CX>(Ls.u[out] + cg, uc[y]);
+                                    st_row<CX>(Ls.s[out] + cg, sn);
+                                    st_row<CX>(Ls.w[out] + cg, wn);
+                                }
                             }
                         }
                     }

@@ -86,8 +86,8 @@ __device__ __forceinline__ void st_row(float* g, const float (&v)[CX]) {
 template <int CX, int CY>
 __device__ __forceinline__ unsigned block_edges(const Dims& d, int i0, int j0) {
     unsigned e = 0;
-    if (i0 > 0 || (d.walls & 1)) e |= 1u;
-    if (i0 + CX < d.nx || (d.walls & 2)) e |= 2u;
+    if (i0 > 0 || (d.walls & (1 | PERIODIC_X))) e |= 1u;
+    if (i0 + CX < d.nx || (d.walls & (2 | PERIODIC_X))) e |= 2u;
     if (j0 > 0 || (d.walls & 4)) e |= 4u;
 #pragma unroll
     for (int a = 1; a <= CY; ++a)

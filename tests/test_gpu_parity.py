@@ -468,6 +468,27 @@ def test_periodic_x_solve_matches_oracle(walls, prec, precond):
     _check_solution(c, op, b, xref, p, st, c.tol)
 
 
+@pytest.mark.parametrize("walls", PERIODIC_CASES)
+@pytest.mark.parametrize("prec,tile", [("fp32", 0), ("fp32", 10012204), ("fp32", 12012204),
+                                       ("bf16", 10312208), ("fp32", -1), ("fp32", 12204)])
+@pytest.mark.parametrize("shape", [(48, 24, 20), (96, 40, 18), (8, 9, 12)])
+def test_periodic_x_marching_matches_oracle(walls, prec, tile, shape):
+    """Periodic x on the one-sweep marching kernels (rows padded with wrapped ghost columns; the
+    tuner and forced one-sweep tiles) and on the column kernels (tile -1, or a two-sweep tile,
+    which cannot wrap), on shapes with one tile, a ragged last tile, and nx = 8."""
+    c = inputs.flat_case(*shape, seed=7, tol=1e-9)
+    op = oracle.operator(c.F, walls=walls | oracle.PERIODIC_X)
+    b = oracle.rhs(c.s, c.grid.h)
+    xref = oracle.pcg(op, b, tol=REF_TOL, precond="ssor").x
+    with solver(c, prec, tile=tile, dirichlet_walls=walls, periodic_x=True) as s:
+        p = np.zeros(c.grid.shape)
+        rc, st = s.solve(c.s, p, c.tol)
+        desc = s.describe()
+    assert rc == capi.OK
+    assert ("one-sweep" in desc) == (tile not in (-1, 12204)), desc
+    _check_solution(c, op, b, xref, p, st, c.tol)
+
+
 def test_periodic_x_rejects_x_walls_and_odd_ssor():
     for kw in ({"dirichlet_walls": capi.WALL_XM}, {"precond": "rbssor"}):
         with pytest.raises(capi.PoissonError) as e:
