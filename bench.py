@@ -51,6 +51,35 @@ BYTES_PER_CELL_ONE_SWEEP = {"fp32": 16 + 4 + 16 + 4, "bf16": 16 + 2 + 16 + 4}
 # one-sweep kernels that form A p in the sweep: read u, p (8 B) + eta, write u, p (8 B), x every
 # other iteration (4 B on average)
 BYTES_PER_CELL_AP_FORMED = {"fp32": 8 + 4 + 8 + 4, "bf16": 8 + 2 + 8 + 4}
+# MG-preconditioned phase B (POISSON_MG), per fine cell: the CG update (read p, x, r, eta; write
+# x, r, the pre-smoothed x0 = 7 vec-equivalents with eta), the fine restriction (read r, x0, eta;
+# write r_c, x_c: 2 values per 8 cells) and the fine prolongation + smoothing (read x0, r, eta and
+# e_c (1 value per 8 cells); write z); every coarse level l adds, per cell of its own, the
+# restriction (read r, x, four stored operator arrays; write 2 values per 8 cells) and the
+# smoothing (read r, x, four operator arrays, 1 value per 8 cells; write y).
+def mg_phase_b_bytes(precision, level_cells, n):
+    v = 8 if precision == "fp64" else 4
+    eta = 8 * 4 if precision == "fp64" else (4 if precision == "fp32" else 2)
+    fine = (4 * v + eta + 3 * v) + (2 * v + eta + 2 * v / 8) + (2 * v + eta + v / 8 + v)
+    coarse = sum(nl * ((6 * v + 2 * v / 8) + (6 * v + v / 8 + v)) for nl in level_cells[1:-1])
+    coarse += level_cells[-1] * 6 * v  # coarsest: r, x, operator (sweeps stay on chip)
+    return fine + coarse / n
+
+
+def mg_levels(nx, ny, nz, periodic, coarse_max=512):
+    """Cell counts of the V-cycle's levels: 2x2x2 aggregation (an axis of one cell stays; a
+    periodic x axis only while nx is even and >= 4), level 0 always coarsened once, stop at
+    coarse_max cells."""
+    cells = [nx * ny * nz]
+    while True:
+        fx = (2 if nx % 2 == 0 and nx >= 4 else 1) if periodic else (2 if nx > 1 else 1)
+        fy, fz = (2 if ny > 1 else 1), (2 if nz > 1 else 1)
+        if fx * fy * fz == 1 or (len(cells) > 1 and nx * ny * nz <= coarse_max):
+            return cells
+        nx, ny, nz = -(-nx // fx), -(-ny // fy), -(-nz // fz)
+        cells.append(nx * ny * nz)
+
+
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -61,7 +90,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
-    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "rbssor"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "rbssor", "mg"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -319,9 +348,15 @@ def cpu_baseline(case, seconds, precond):
     op = oracle.operator(case.F)
     b = oracle.rhs(case.s, case.grid.h)
     x = np.zeros(case.grid.shape)
+    if precond == "mg":
+        from oracle import multigrid
+        levels = multigrid.hierarchy(op)
     its, t0 = 0, time.perf_counter()
     while True:
-        r = oracle.pcg(op, b, x0=x, tol=0.0, precond=precond, max_iters=20)
+        if precond == "mg":
+            r = multigrid.pcg_mg(op, b, x0=x, tol=0.0, max_iters=20, levels=levels)
+        else:
+            r = oracle.pcg(op, b, x0=x, tol=0.0, precond=precond, max_iters=20)
         its += r.iters
         if time.perf_counter() - t0 >= seconds:
             break
@@ -435,6 +470,11 @@ def main():
         bpi = BYTES_PER_CELL_AP_FORMED[args.precision]
     elif "one-sweep" in desc:
         bpi = BYTES_PER_CELL_ONE_SWEEP[args.precision]
+    elif args.precond == "mg":
+        bpc = dict(bpc)
+        bpc["cg_phase_b"] = mg_phase_b_bytes(args.precision,
+                                             mg_levels(g.nx, g.ny, g.nz, args.periodic_x), g.n)
+        bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]
     else:
         bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]  # algorithmic bytes per cell-iteration
     if dom == "pcg_persistent":
@@ -502,7 +542,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(case, args.cpu_seconds, "ssor" if args.precond == "rbssor" else "jacobi")
+        cpu = cpu_baseline(case, args.cpu_seconds, {"rbssor": "ssor"}.get(args.precond, args.precond))
 
     if rank == 0:
         line = {

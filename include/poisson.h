@@ -12,7 +12,8 @@
  *   zero normal gradient on the walls x = 0, x = nx h, y = 0, y = ny h, z = 0;
  *   p = 0 on the top face z = nz h (second order: ghost value -p_c).
  * The Introduction states that this second-order variable-coefficient Poisson equation is solved by
- * preconditioned conjugate gradients; the preconditioner is Jacobi or red-black SSOR.
+ * preconditioned conjugate gradients; the preconditioner is Jacobi or red-black SSOR (the paper
+ * names neither), or a multigrid V-cycle (POISSON_MG, beyond the paper, below).
  *
  * Conventions for every call:
  *   - 3-D arrays are float64, nx*ny*nz elements, x fastest: element (i, j, k) at i + nx*(j + ny*k).
@@ -62,6 +63,16 @@ extern "C" {
 
 #define POISSON_JACOBI 0
 #define POISSON_RBSSOR 1
+/* Multigrid V-cycle (column kernels, any precision).  Level l+1 aggregates the cells of level l
+ * in 2x2x2 blocks (an axis of one cell is not coarsened; a periodic x axis only while nx is even
+ * and >= 4; the last block of an odd axis has one cell) and carries the Galerkin operator
+ * P^T A P of that aggregation; levels stop at 512 cells.  One cycle: x = 0.9 D^-1 r;
+ * e = V(P^T (r - A x)) on the next level; x += 1.5 P e; z = x + 0.9 D^-1 (r - A x); 16 damped
+ * Jacobi sweeps (0.9) from zero on the coarsest level.  Symmetric positive definite.  The
+ * coarse levels are built from the FP64 operator by poisson_set_density and stored in FP64
+ * (POISSON_FP64 handles) or FP32.  poisson_create returns EINVAL when the grid has no coarser
+ * level (every axis of one cell, or periodic x of odd nx with ny = nz = 1). */
+#define POISSON_MG 2
 
 #define POISSON_MEM_HOST 0
 #define POISSON_MEM_DEVICE 1
@@ -70,7 +81,7 @@ typedef struct poisson_s poisson_t; /* opaque; the library owns all device state
 
 typedef struct {
     int precision;     /* POISSON_FP64 | POISSON_FP32 | POISSON_FP32_BF16COEF (default FP32)     */
-    int precond;       /* POISSON_JACOBI | POISSON_RBSSOR (default JACOBI)                        */
+    int precond;       /* POISSON_JACOBI | POISSON_RBSSOR | POISSON_MG (default JACOBI)           */
     double omega;      /* SSOR relaxation factor in (0, 2) (default 1.0)                           */
     int max_iters;     /* cap on total CG iterations of one solve (default 20000)                  */
     double inner_tol;  /* FP32 inner solve: relative residual reduction per refinement step
@@ -143,9 +154,11 @@ int poisson_solve(poisson_t* h, const double* rhs, double* p, double tol, poisso
 int poisson_apply(poisson_t* h, const double* x, double* y, int precision);
 
 /* z = M^{-1} r for the preconditioner kind (POISSON_JACOBI, POISSON_RBSSOR with the handle's
- * omega) at the given precision, with M built from the operator of that precision:
+ * omega, POISSON_MG) at the given precision, with M built from the operator of that precision:
  * Jacobi M = D; SSOR M = (D - wE) D^{-1} (D - wE^T) / (w (2 - w)) in red-black order (red =
- * (i+j+k) even first, A = D - E - E^T).  Errors: ENOTREADY, EINVAL, ECUDA. */
+ * (i+j+k) even first, A = D - E - E^T); MG one V-cycle of the handle's hierarchy (only on a
+ * POISSON_MG handle and at its own precision, else EINVAL; the FP32 cycle uses the handle's
+ * inner FP32 vectors as scratch).  Errors: ENOTREADY, EINVAL, ECUDA. */
 int poisson_precond_apply(poisson_t* h, const double* r, double* z, int kind, int precision);
 
 /* Copy out the FP64 operator: low-side face coefficients bx, by, bz (bx[c] couples cell c with

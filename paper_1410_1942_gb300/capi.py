@@ -20,11 +20,11 @@ EINVAL, ENOMEM, ENOTCONV, EBREAKDOWN, ETIMEOUT, ENOTREADY, ECUDA, ENOMEM_BUDGET,
     -1, -2, -3, -4, -5, -6, -7, -8, -9
 ETOOLARGE = -10
 FP64, FP32, FP32_BF16COEF = 0, 1, 2
-JACOBI, RBSSOR = 0, 1
+JACOBI, RBSSOR, MG = 0, 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
 
 PRECISION = {"fp64": FP64, "fp32": FP32, "bf16": FP32_BF16COEF}
-PRECOND = {"jacobi": JACOBI, "rbssor": RBSSOR, "ssor": RBSSOR}
+PRECOND = {"jacobi": JACOBI, "rbssor": RBSSOR, "ssor": RBSSOR, "mg": MG}
 
 # every symbol include/poisson.h declares
 EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson_set_density",

@@ -283,6 +283,7 @@ static void free_state(poisson_t* H) {
         cudaGetLastError();
     }
     march_plan_free(&H->plan);
+    mg_free(&H->mg);
 }
 
 extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_opts* opts,
@@ -295,7 +296,8 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     poisson_default_opts(&o);
     if (opts) o = *opts;
     if (o.precision < POISSON_FP64 || o.precision > POISSON_FP32_BF16COEF) return POISSON_EINVAL;
-    if (o.precond != POISSON_JACOBI && o.precond != POISSON_RBSSOR) return POISSON_EINVAL;
+    if (o.precond != POISSON_JACOBI && o.precond != POISSON_RBSSOR && o.precond != POISSON_MG)
+        return POISSON_EINVAL;
     if (!(o.omega > 0.0 && o.omega < 2.0)) return POISSON_EINVAL;
     if (o.max_iters <= 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return POISSON_EINVAL;
     if (o.tile < -1 || (o.tile > 0 && march_variant_of_tile(o.tile) < 0))
@@ -305,9 +307,17 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (o.periodic_x && (o.dirichlet_walls & (POISSON_WALL_XM | POISSON_WALL_XP))) return POISSON_EINVAL;
     if (o.periodic_x && o.precond == POISSON_RBSSOR && nx % 2) return POISSON_EINVAL;
 
+    const Dims dims{nx, ny, nz, nx * ny, (int)n,
+                    o.dirichlet_walls | (o.periodic_x ? PERIODIC_X : 0)};
+    if (o.precond == POISSON_MG) {
+        // the V-cycle needs at least one coarser level
+        MgHier probe;
+        if (mg_plan(dims, &probe) < 2) return POISSON_EINVAL;
+    }
+
     poisson_t* H = new (std::nothrow) poisson_t();
     if (!H) return POISSON_ENOMEM;
-    H->d = Dims{nx, ny, nz, nx * ny, (int)n, o.dirichlet_walls | (o.periodic_x ? PERIODIC_X : 0)};
+    H->d = dims;
     H->h = h;
     H->opts = o;
     H->st = (cudaStream_t)o.stream;
@@ -340,6 +350,10 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
         A(dalloc(&H->d32, N)); A(dalloc(&H->r32, N)); A(dalloc(&H->z32, N));
         A(dalloc(&H->p32a, N)); A(dalloc(&H->p32b, N));
         A(dalloc(&H->s32a, N)); A(dalloc(&H->s32b, N)); A(dalloc(&H->w32a, N)); A(dalloc(&H->w32b, N));
+    }
+    if (o.precond == POISSON_MG && rc == POISSON_OK) {
+        mg_plan(H->d, &H->mg);
+        A(mg_alloc(&H->mg, o.precision == POISSON_FP64));
     }
     A(dalloc(&H->sc, 1));
     A(dalloc(&H->partials, 2 * H->nblocks + 64));
@@ -405,6 +419,7 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
         launch_narrow_f32(n, H->bz, H->bz32, H->st);
         launch_narrow_f32(n, H->diag, H->diag32, H->st);
     }
+    if (H->opts.precond == POISSON_MG) mg_setup(&H->mg, H->bx, H->by, H->bz, H->diag, H->st);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(H->st));
     H->ready = true;
@@ -485,7 +500,10 @@ static int cg_loop(poisson_t* H, const Coef& coef, V* r, V* z, double tol2, int 
     const int K = CG_CHUNK;
     cudaStream_t st = H->st;
     const bool prof = H->prof_on;
-    if (H->opts.precond == POISSON_RBSSOR)
+    if (H->opts.precond == POISSON_MG)
+        mg_init<V, Coef>(&H->mg, H->d, H->kc, coef, r, z, H->sc, H->partials, tol2, rel_to_b,
+                         max_iter, st);
+    else if (H->opts.precond == POISSON_RBSSOR)
         launch_ssor_init<V, Coef>(H->d, H->kc, coef, r, z, H->opts.omega, H->sc, H->partials, tol2,
                                   rel_to_b, max_iter, st);
     else
@@ -544,7 +562,7 @@ static int cg_loop(poisson_t* H, const Coef& coef, V* r, V* z, double tol2, int 
     }
 }
 
-// Column-kernel passes (any shape, any precision; Jacobi or red-black SSOR).
+// Column-kernel passes (any shape, any precision; Jacobi, red-black SSOR or the V-cycle).
 template <typename V, typename Coef>
 static int cg_loop_columns(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* pa, V* pb,
                            double tol2, int rel_to_b, int max_iter, Scalars* result) {
@@ -555,9 +573,12 @@ static int cg_loop_columns(poisson_t* H, const Coef& coef, V* x, V* r, V* z, V* 
         launch_cg_a<V, Coef>(d, kc, coef, z, in_a ? pa : pb, in_a ? pb : pa, H->sc, H->partials, st);
     };
     const bool ssor = H->opts.precond == POISSON_RBSSOR;
+    const bool mg = H->opts.precond == POISSON_MG;
     const double omega = H->opts.omega;
     auto B = [=](bool p_a) {
-        if (ssor)
+        if (mg)
+            mg_cg_b<V, Coef>(&H->mg, d, kc, coef, p_a ? pa : pb, x, r, z, H->sc, H->partials, st);
+        else if (ssor)
             launch_cg_b_ssor<V, Coef>(d, kc, coef, p_a ? pa : pb, x, r, z, omega, H->sc,
                                       H->partials, st);
         else
@@ -792,11 +813,37 @@ extern "C" int poisson_precond_apply(poisson_t* H, const double* r, double* z, i
                                      int precision) {
     if (!H || !r || !z || r == z) return POISSON_EINVAL;
     if (!H->ready) return POISSON_ENOTREADY;
-    if (kind != POISSON_JACOBI && kind != POISSON_RBSSOR) return POISSON_EINVAL;
+    if (kind != POISSON_JACOBI && kind != POISSON_RBSSOR && kind != POISSON_MG)
+        return POISSON_EINVAL;
     if (precision < POISSON_FP64 || precision > POISSON_FP32_BF16COEF) return POISSON_EINVAL;
     const Dims d = H->d;
     const int kc = H->kc;
     cudaStream_t st = H->st;
+    if (kind == POISSON_MG) {
+        // the handle's own hierarchy, in the handle's own precision
+        if (H->opts.precond != POISSON_MG || precision != H->opts.precision) return POISSON_EINVAL;
+        if (precision == POISSON_FP64) {
+            const CoefFaces64 c{H->bx, H->by, H->bz, H->diag, nullptr};
+            return with_io(H, r, z, [&](const double* a, double* b) {
+                mg_apply<double, CoefFaces64>(&H->mg, d, kc, c, a, b, st);
+            });
+        }
+        // FP32 V-cycle on narrowed copies (r32 and d32 are rebuilt by every solve)
+        return with_io(H, r, z, [&](const double* a, double* b) {
+            launch_narrow_f32(d.n, a, H->r32, st);
+            if (H->cut())
+                mg_apply<float, CoefFaces32>(&H->mg, d, kc,
+                                             CoefFaces32{H->bx32, H->by32, H->bz32, H->diag32},
+                                             H->r32, H->d32, st);
+            else if (precision == POISSON_FP32)
+                mg_apply<float, CoefEta<float>>(&H->mg, d, kc, CoefEta<float>{H->eta32}, H->r32,
+                                                H->d32, st);
+            else
+                mg_apply<float, CoefEta<__nv_bfloat16>>(
+                    &H->mg, d, kc, CoefEta<__nv_bfloat16>{H->eta16}, H->r32, H->d32, st);
+            launch_widen_f32(d.n, H->d32, b, st);
+        });
+    }
     const double om = H->opts.omega;
     if (kind == POISSON_RBSSOR) {
         // sweeps in the precision's arithmetic on a scratch vector of that type
@@ -908,8 +955,10 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
                  : H->plan.strategy == MARCH_SPLIT_LOCKSTEP ? "lockstep"
                                                             : "equal");
     } else {
-        snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d%s", prec, TX, TY, H->kc,
-                 H->cut() ? " cut-cells" : "");
+        char mgs[48] = "";
+        if (H->opts.precond == POISSON_MG) snprintf(mgs, sizeof mgs, " mg-vcycle levels=%d", H->mg.nlev);
+        snprintf(buf, (size_t)len, "%s columns (%dx%d threads) zchunk=%d%s%s", prec, TX, TY, H->kc,
+                 H->cut() ? " cut-cells" : "", mgs);
     }
     return POISSON_OK;
 }

@@ -9,6 +9,7 @@
 #include "poisson.h"
 #include "internal.cuh"
 #include "march.h"
+#include "mg.h"
 
 struct poisson_s {
     pcg::Dims d{};
@@ -61,6 +62,8 @@ struct poisson_s {
     double *io_a = nullptr, *io_b = nullptr;
     double* io_c = nullptr;   // SSOR apply scratch (FP64)
     float* io_c32 = nullptr;  // SSOR apply scratch (FP32)
+    // multigrid V-cycle hierarchy (POISSON_MG): Galerkin levels in the inner precision
+    pcg::MgHier mg{};
     // TMA plane-marching kernels for the FP32 inner solve (when the shape allows them)
     bool march = false;
     pcg::MarchPlan plan{};  // persistent work-list launch over this handle's grid

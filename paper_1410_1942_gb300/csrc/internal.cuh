@@ -181,6 +181,23 @@ struct CoefFaces32 {
     }
 };
 
+// sum_n w_cn v_n with v = load(e)
+template <typename V, typename L>
+__device__ __forceinline__ V nb_sum(const Dims& d, const Stencil<V>& w, int c, int i, int j,
+                                    int k, L load) {
+    V s = 0;
+    const bool per = d.walls & PERIODIC_X;
+    if (i > 0) s += w.xm * load(c - 1);
+    else if (per) s += w.xm * load(c + d.nx - 1);
+    if (i + 1 < d.nx) s += w.xp * load(c + 1);
+    else if (per) s += w.xp * load(c + 1 - d.nx);
+    if (j > 0) s += w.ym * load(c - d.nx);
+    if (j + 1 < d.ny) s += w.yp * load(c + d.nx);
+    if (k > 0) s += w.zm * load(c - d.sxy);
+    if (k + 1 < d.nz) s += w.zp * load(c + d.sxy);
+    return s;
+}
+
 template <typename E>
 __device__ __forceinline__ float eta_load(const E* p, int c);
 template <>

@@ -163,23 +163,6 @@ __device__ __forceinline__ float inv_diag<float, CoefFaces32>(const CoefFaces32&
     return rcp_approx(w.D);
 }
 
-// sum_n w_cn v_n with v = load(e)
-template <typename V, typename L>
-__device__ __forceinline__ V nb_sum(const Dims& d, const Stencil<V>& w, int c, int i, int j,
-                                    int k, L load) {
-    V s = 0;
-    const bool per = d.walls & PERIODIC_X;
-    if (i > 0) s += w.xm * load(c - 1);
-    else if (per) s += w.xm * load(c + d.nx - 1);
-    if (i + 1 < d.nx) s += w.xp * load(c + 1);
-    else if (per) s += w.xp * load(c + 1 - d.nx);
-    if (j > 0) s += w.ym * load(c - d.nx);
-    if (j + 1 < d.ny) s += w.yp * load(c + d.nx);
-    if (k > 0) s += w.zm * load(c - d.sxy);
-    if (k + 1 < d.nz) s += w.zp * load(c + d.sxy);
-    return s;
-}
-
 // ------------------------------------------------------------------ FP64 residual
 // r = b - A x with the FP64 operator; writes r (as R) and reduces (r.r, b.b) into sc->rr, sc->bb.
 template <typename R>
@@ -679,6 +662,11 @@ void launch_pad_rows_bf16(const Dims& d, int pad, const __nv_bfloat16* src, __nv
 
 void launch_narrow_f32(long long n, const double* a, float* b, cudaStream_t st) {
     k_narrow<float><<<blocks1d(n), 256, 0, st>>>(n, a, b);
+    counted(1);
+}
+
+void launch_widen_f32(long long n, const float* a, double* b, cudaStream_t st) {
+    k_widen<float><<<blocks1d(n), 256, 0, st>>>(n, a, b);
     counted(1);
 }
 

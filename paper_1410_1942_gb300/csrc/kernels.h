@@ -17,6 +17,7 @@ void launch_scale(long long n, const double* s, double a, double* b, cudaStream_
                   const double* vol = nullptr);
 void launch_update64(long long n, double* x, const float* dlt, cudaStream_t st);
 void launch_narrow_f32(long long n, const double* a, float* b, cudaStream_t st);
+void launch_widen_f32(long long n, const float* a, double* b, cudaStream_t st);
 // rows padded with `pad` ghost columns each side holding the other end of the row (periodic x)
 void launch_pad_rows_f32(const Dims& d, int pad, const float* src, float* dst, cudaStream_t st);
 void launch_pad_rows_bf16(const Dims& d, int pad, const __nv_bfloat16* src, __nv_bfloat16* dst,

@@ -1,0 +1,458 @@
+// mg.cu -- the multigrid V-cycle preconditioner of the column-kernel PCG (see mg.h).
+//
+// All kernels are elementwise over the cells of one level.  The restriction and the Galerkin
+// setup run one thread per coarse cell over its (up to 8) fine cells; the prolongation +
+// post-smoothing runs in the column layout of the PCG kernels (the fine one carries the (r, z)
+// reduction, so its blocks must match the handle's reduction partials); the coarsest level is
+// one block.  Every kernel of a PCG iteration returns at once when the solve has finished.
+#include <atomic>
+
+#include "poisson.h"
+#include "mg.h"
+#include "kernels.h"
+
+namespace pcg {
+namespace {
+
+constexpr int MT = 256;         // threads of the one-thread-per-coarse-cell kernels
+constexpr int COARSE_T = 1024;  // threads of the coarsest-level block
+
+inline unsigned blocks_of(long long n) { return (unsigned)((n + MT - 1) / MT); }
+inline dim3 cols(const Dims& d, int kc) {
+    return dim3((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, (d.nz + kc - 1) / kc);
+}
+inline void counted(int k) {
+    g_kernel_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed);
+}
+
+// The stored operator of a coarse level, in the handle's inner precision.
+template <typename V>
+struct LevelCoef;
+template <>
+struct LevelCoef<double> {
+    using type = CoefFaces64;
+    static type of(const MgHier& m, int l) {
+        return CoefFaces64{(const double*)m.bx[l], (const double*)m.by[l], (const double*)m.bz[l],
+                           (const double*)m.diag[l], nullptr};
+    }
+};
+template <>
+struct LevelCoef<float> {
+    using type = CoefFaces32;
+    static type of(const MgHier& m, int l) {
+        return CoefFaces32{(const float*)m.bx[l], (const float*)m.by[l], (const float*)m.bz[l],
+                           (const float*)m.diag[l]};
+    }
+};
+
+__device__ __forceinline__ void coarse_index(const Dims& dc, int I, int& ic, int& jc, int& kc) {
+    ic = I % dc.nx;
+    jc = (I / dc.nx) % dc.ny;
+    kc = I / dc.sxy;
+}
+
+// A_c = P^T A P: the coarse low face is the sum of the fine low faces of the block's first layer;
+// the diagonal is the sum of the block's diagonals minus twice the faces inside the block.
+// Accumulated in FP64.
+template <typename T, typename V>
+__global__ void __launch_bounds__(MT) k_mg_galerkin(Dims df, const T* __restrict__ bx,
+                                                    const T* __restrict__ by,
+                                                    const T* __restrict__ bz,
+                                                    const T* __restrict__ diag, Dims dc, int fx,
+                                                    int fy, int fz, V* __restrict__ cbx,
+                                                    V* __restrict__ cby, V* __restrict__ cbz,
+                                                    V* __restrict__ cdiag) {
+    const long long t = blockIdx.x * (long long)MT + threadIdx.x;
+    if (t >= dc.n) return;
+    const int I = (int)t;
+    int ic, jc, kc;
+    coarse_index(dc, I, ic, jc, kc);
+    const int i0 = ic * fx, j0 = jc * fy, k0 = kc * fz;
+    const int i1 = min(i0 + fx, df.nx), j1 = min(j0 + fy, df.ny), k1 = min(k0 + fz, df.nz);
+    double BX = 0.0, BY = 0.0, BZ = 0.0, D = 0.0;
+    for (int k = k0; k < k1; ++k)
+        for (int j = j0; j < j1; ++j)
+            for (int i = i0; i < i1; ++i) {
+                const int c = i + df.nx * (j + df.ny * k);
+                D += (double)diag[c];
+                if (i == i0) BX += (double)bx[c]; else D -= 2.0 * (double)bx[c];
+                if (j == j0) BY += (double)by[c]; else D -= 2.0 * (double)by[c];
+                if (k == k0) BZ += (double)bz[c]; else D -= 2.0 * (double)bz[c];
+            }
+    cbx[I] = (V)BX;
+    cby[I] = (V)BY;
+    cbz[I] = (V)BZ;
+    cdiag[I] = (V)D;
+}
+
+// r_c = P^T (r - A x) over the block of each coarse cell; x_c = w r_c / D_c (the coarse level's
+// pre-smoothing from zero).
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(MT) k_mg_restrict(Dims df, Coef coef, const V* __restrict__ r,
+                                                    const V* __restrict__ x, Dims dc, int fx,
+                                                    int fy, int fz, const V* __restrict__ cdiag,
+                                                    V* __restrict__ rc, V* __restrict__ xc,
+                                                    V omega, const Scalars* sc) {
+    if (sc && sc->done) return;
+    const long long t = blockIdx.x * (long long)MT + threadIdx.x;
+    if (t >= dc.n) return;
+    const int I = (int)t;
+    int ic, jc, kc;
+    coarse_index(dc, I, ic, jc, kc);
+    const int i0 = ic * fx, j0 = jc * fy, k0 = kc * fz;
+    const int i1 = min(i0 + fx, df.nx), j1 = min(j0 + fy, df.ny), k1 = min(k0 + fz, df.nz);
+    auto ld = [&](int e) { return x[e]; };
+    V s = 0;
+    for (int k = k0; k < k1; ++k)
+        for (int j = j0; j < j1; ++j)
+            for (int i = i0; i < i1; ++i) {
+                const int c = i + df.nx * (j + df.ny * k);
+                Stencil<V> w;
+                coef.weights(df, c, i, j, k, w);
+                s += r[c] - (w.D * x[c] - nb_sum(df, w, c, i, j, k, ld));
+            }
+    rc[I] = s;
+    xc[I] = omega * s / cdiag[I];
+}
+
+// Coarsest level: x holds the first damped Jacobi sweep from zero; sweeps - 1 more follow,
+// alternating between x and y (one block, so __syncthreads orders them); the result ends in y.
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(COARSE_T) k_mg_coarsest(Dims d, Coef coef, const V* r, V* x,
+                                                          V* y, V omega, int sweeps,
+                                                          const Scalars* sc) {
+    if (sc && sc->done) return;
+    V* src = x;
+    V* dst = y;
+    for (int m = 1; m < sweeps; ++m) {
+        auto ld = [&](int e) { return src[e]; };
+        for (int c = threadIdx.x; c < d.n; c += blockDim.x) {
+            const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
+            Stencil<V> w;
+            coef.weights(d, c, i, j, k, w);
+            const V xc = src[c];
+            dst[c] = xc + omega * (r[c] - (w.D * xc - nb_sum(d, w, c, i, j, k, ld))) / w.D;
+        }
+        __syncthreads();
+        V* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != y)
+        for (int c = threadIdx.x; c < d.n; c += blockDim.x) y[c] = src[c];
+}
+
+// Prolongation + post-smoothing: xt = x + a P e;  y = xt + w D^-1 (r - A xt).  On the fine
+// level (mode >= 0) also sums (r, y) and, like the SSOR red sweep, either stores rz after the
+// start (mode 0) or sets beta and the stopping state (mode 1).
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_mg_smooth(Dims d, Coef coef, int kc,
+                                                      const V* __restrict__ r,
+                                                      const V* __restrict__ x,
+                                                      const V* __restrict__ e, Dims dc, int sx,
+                                                      int sy, int sz, V alpha, V omega,
+                                                      V* __restrict__ y, Scalars* sc,
+                                                      double* partials, int mode) {
+    __shared__ double smem[64];
+    if (sc && sc->done) return;
+    const bool per = d.walls & PERIODIC_X;
+    auto xt = [&](int ii, int jj, int kk) -> V {
+        return x[ii + d.nx * (jj + d.ny * kk)] +
+               alpha * e[(ii >> sx) + dc.nx * ((jj >> sy) + dc.ny * (kk >> sz))];
+    };
+    V rz = 0;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    if (i < d.nx && j < d.ny)
+        for (int k = k0; k < k1; ++k) {
+            const int c = i + d.nx * (j + d.ny * k);
+            Stencil<V> w;
+            coef.weights(d, c, i, j, k, w);
+            V s = 0;
+            if (i > 0) s += w.xm * xt(i - 1, j, k);
+            else if (per) s += w.xm * xt(d.nx - 1, j, k);
+            if (i + 1 < d.nx) s += w.xp * xt(i + 1, j, k);
+            else if (per) s += w.xp * xt(0, j, k);
+            if (j > 0) s += w.ym * xt(i, j - 1, k);
+            if (j + 1 < d.ny) s += w.yp * xt(i, j + 1, k);
+            if (k > 0) s += w.zm * xt(i, j, k - 1);
+            if (k + 1 < d.nz) s += w.zp * xt(i, j, k + 1);
+            const V xc = xt(i, j, k);
+            const V rc = r[c];
+            const V yc = xc + omega * (rc - (w.D * xc - s)) / w.D;
+            y[c] = yc;
+            rz += rc * yc;
+        }
+    if (mode < 0 || !sc) return;
+    double v[1] = {(double)rz}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double rz_new = tot[0];
+            if (mode == 0) {
+                sc->rz = rz_new;
+                if (!isfinite(rz_new) || !(rz_new > 0.0)) sc->done = BREAKDOWN;
+            } else {
+                sc->iter += 1;
+                if (!isfinite(rz_new) || rz_new < 0.0 || !isfinite(sc->rr)) {
+                    sc->done = BREAKDOWN;
+                } else if (sc->rr <= sc->stop2) {
+                    sc->done = CONVERGED;
+                } else if (sc->iter >= sc->max_iter) {
+                    sc->done = CAPPED;
+                } else {
+                    sc->beta = rz_new / sc->rz;
+                    sc->rz = rz_new;
+                }
+            }
+        }
+    }
+}
+
+// Start of the preconditioned solve: x0 = w D^-1 r on the fine level; with scalars, sums r.r
+// and sets them like k_cg_init (rz follows from the V-cycle's last kernel).
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_mg_first(Dims d, Coef coef, int kc,
+                                                     const V* __restrict__ r,
+                                                     V* __restrict__ x0, V omega, Scalars* sc,
+                                                     double* partials, double tol2, int rel_to_b,
+                                                     int max_iter) {
+    __shared__ double smem[64];
+    V rr = 0;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    if (i < d.nx && j < d.ny)
+        for (int k = k0; k < k1; ++k) {
+            const int c = i + d.nx * (j + d.ny * k);
+            Stencil<V> w;
+            coef.weights(d, c, i, j, k, w);
+            const V rc = r[c];
+            x0[c] = omega * rc / w.D;
+            rr += rc * rc;
+        }
+    if (!sc) return;
+    double v[1] = {(double)rr}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            sc->rr = tot[0];
+            sc->rr0 = tot[0];
+            sc->beta = 0.0;
+            sc->alpha = 0.0;
+            sc->iter = 0;
+            sc->max_iter = max_iter;
+            sc->stop2 = tol2 * (rel_to_b ? sc->bb : tot[0]);
+            sc->done = (tot[0] <= sc->stop2) ? CONVERGED : RUNNING;
+            if (!isfinite(tot[0])) sc->done = BREAKDOWN;
+            sc->rz = 0.0;
+        }
+    }
+}
+
+// Phase B of MG-PCG: q = A p (recomputed); x += alpha p; r -= alpha q; x0 = w D^-1 r; sums r.r.
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(TX * TY) k_mg_cg_b(Dims d, Coef coef, int kc,
+                                                    const V* __restrict__ p, V* __restrict__ x,
+                                                    V* __restrict__ r, V* __restrict__ x0,
+                                                    V omega, Scalars* sc, double* partials) {
+    __shared__ double smem[64];
+    if (sc->done) return;
+    const V alpha = (V)sc->alpha;
+    auto ld = [&](int e) { return p[e]; };
+    V rr = 0;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    if (i < d.nx && j < d.ny)
+        for (int k = k0; k < k1; ++k) {
+            const int c = i + d.nx * (j + d.ny * k);
+            Stencil<V> w;
+            coef.weights(d, c, i, j, k, w);
+            const V pc = p[c];
+            const V q = w.D * pc - nb_sum(d, w, c, i, j, k, ld);
+            x[c] += alpha * pc;
+            const V rn = r[c] - alpha * q;
+            r[c] = rn;
+            x0[c] = omega * rn / w.D;
+            rr += rn * rn;
+        }
+    double v[1] = {(double)rr}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sc->rr = tot[0];
+    }
+}
+
+// z = V_0(r) given x[0] = w D^-1 r: restrictions down, the coarsest sweeps, prolongation +
+// post-smoothing up; the fine smoothing writes z (and reduces r.z when mode >= 0).
+template <typename V, typename Coef>
+void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z, Scalars* sc,
+            double* part, int mode, cudaStream_t st) {
+    using LC = LevelCoef<V>;
+    const int L = m->nlev;
+    const V om = (V)MG_OMEGA, al = (V)MG_ALPHA;
+    for (int l = 0; l + 1 < L; ++l) {
+        const Dims& df = m->d[l];
+        const Dims& dc = m->d[l + 1];
+        const int* f = m->f[l];
+        const V* rl = l == 0 ? r : (const V*)m->r[l];
+        if (l == 0)
+            k_mg_restrict<V, Coef><<<blocks_of(dc.n), MT, 0, st>>>(
+                df, coef, rl, (const V*)m->x[0], dc, f[0], f[1], f[2], (const V*)m->diag[1],
+                (V*)m->r[1], (V*)m->x[1], om, sc);
+        else
+            k_mg_restrict<V, typename LC::type><<<blocks_of(dc.n), MT, 0, st>>>(
+                df, LC::of(*m, l), rl, (const V*)m->x[l], dc, f[0], f[1], f[2],
+                (const V*)m->diag[l + 1], (V*)m->r[l + 1], (V*)m->x[l + 1], om, sc);
+    }
+    const int c = L - 1;
+    k_mg_coarsest<V, typename LC::type><<<1, COARSE_T, 0, st>>>(
+        m->d[c], LC::of(*m, c), (const V*)m->r[c], (V*)m->x[c], (V*)m->y[c], om, MG_COARSE_SWEEPS,
+        sc);
+    for (int l = L - 2; l >= 1; --l) {
+        const int* f = m->f[l];
+        k_mg_smooth<V, typename LC::type><<<cols(m->d[l], 1), dim3(TX, TY), 0, st>>>(
+            m->d[l], LC::of(*m, l), 1, (const V*)m->r[l], (const V*)m->x[l],
+            (const V*)m->y[l + 1], m->d[l + 1], f[0] - 1, f[1] - 1, f[2] - 1, al, om,
+            (V*)m->y[l], sc, nullptr, -1);
+    }
+    const int* f = m->f[0];
+    k_mg_smooth<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+        d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
+        f[2] - 1, al, om, z, sc, part, mode);
+    counted(2 * L);
+}
+
+}  // namespace
+
+int mg_plan(const Dims& fine, MgHier* m) {
+    *m = MgHier{};
+    m->d[0] = fine;
+    int L = 1;
+    while (L < MG_MAX_LEVELS) {
+        const Dims& c = m->d[L - 1];
+        const bool per = c.walls & PERIODIC_X;
+        const int fx = per ? ((c.nx % 2 == 0 && c.nx >= 4) ? 2 : 1) : (c.nx > 1 ? 2 : 1);
+        const int fy = c.ny > 1 ? 2 : 1, fz = c.nz > 1 ? 2 : 1;
+        if (fx * fy * fz == 1) break;
+        if (L > 1 && c.n <= MG_COARSE_MAX) break;
+        m->f[L - 1][0] = fx;
+        m->f[L - 1][1] = fy;
+        m->f[L - 1][2] = fz;
+        Dims nd{};
+        nd.nx = (c.nx + fx - 1) / fx;
+        nd.ny = (c.ny + fy - 1) / fy;
+        nd.nz = (c.nz + fz - 1) / fz;
+        nd.sxy = nd.nx * nd.ny;
+        nd.n = nd.sxy * nd.nz;
+        nd.walls = c.walls & PERIODIC_X;  // wall terms live in the Galerkin diagonal
+        m->d[L++] = nd;
+    }
+    m->nlev = L;
+    return L;
+}
+
+int mg_alloc(MgHier* m, bool dbl) {
+    m->dbl = dbl;
+    const size_t es = dbl ? sizeof(double) : sizeof(float);
+    auto al = [&](void** p, size_t n) {
+        if (cudaMalloc(p, es * n) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return false;
+        }
+        return true;
+    };
+    bool ok = al(&m->x[0], (size_t)m->d[0].n);
+    for (int l = 1; ok && l < m->nlev; ++l) {
+        const size_t n = (size_t)m->d[l].n;
+        ok = al(&m->bx[l], n) && al(&m->by[l], n) && al(&m->bz[l], n) && al(&m->diag[l], n) &&
+             al(&m->r[l], n) && al(&m->x[l], n) && al(&m->y[l], n);
+    }
+    if (!ok) {
+        mg_free(m);
+        return POISSON_ENOMEM;
+    }
+    return POISSON_OK;
+}
+
+void mg_free(MgHier* m) {
+    for (int l = 0; l < MG_MAX_LEVELS; ++l)
+        for (void** p : {&m->bx[l], &m->by[l], &m->bz[l], &m->diag[l], &m->r[l], &m->x[l], &m->y[l]})
+            if (*p) {
+                cudaFree(*p);
+                *p = nullptr;
+            }
+}
+
+template <typename V>
+static void setup_typed(MgHier* m, const double* bx, const double* by, const double* bz,
+                        const double* diag, cudaStream_t st) {
+    for (int l = 0; l + 1 < m->nlev; ++l) {
+        const Dims& df = m->d[l];
+        const Dims& dc = m->d[l + 1];
+        const int* f = m->f[l];
+        V *cbx = (V*)m->bx[l + 1], *cby = (V*)m->by[l + 1], *cbz = (V*)m->bz[l + 1],
+          *cd = (V*)m->diag[l + 1];
+        if (l == 0)
+            k_mg_galerkin<double, V><<<blocks_of(dc.n), MT, 0, st>>>(
+                df, bx, by, bz, diag, dc, f[0], f[1], f[2], cbx, cby, cbz, cd);
+        else
+            k_mg_galerkin<V, V><<<blocks_of(dc.n), MT, 0, st>>>(
+                df, (const V*)m->bx[l], (const V*)m->by[l], (const V*)m->bz[l],
+                (const V*)m->diag[l], dc, f[0], f[1], f[2], cbx, cby, cbz, cd);
+    }
+    counted(m->nlev - 1);
+}
+
+void mg_setup(MgHier* m, const double* bx, const double* by, const double* bz,
+              const double* diag, cudaStream_t st) {
+    if (m->dbl)
+        setup_typed<double>(m, bx, by, bz, diag, st);
+    else
+        setup_typed<float>(m, bx, by, bz, diag, st);
+}
+
+template <typename V, typename Coef>
+void mg_init(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z, Scalars* sc,
+             double* part, double tol2, int rel_to_b, int max_iter, cudaStream_t st) {
+    k_mg_first<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+        d, coef, kc, r, (V*)m->x[0], (V)MG_OMEGA, sc, part, tol2, rel_to_b, max_iter);
+    counted(1);
+    vcycle<V, Coef>(m, d, kc, coef, r, z, sc, part, 0, st);
+}
+
+template <typename V, typename Coef>
+void mg_cg_b(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* p, V* x, V* r, V* z,
+             Scalars* sc, double* part, cudaStream_t st) {
+    k_mg_cg_b<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r, (V*)m->x[0],
+                                                            (V)MG_OMEGA, sc, part);
+    counted(1);
+    vcycle<V, Coef>(m, d, kc, coef, r, z, sc, part, 1, st);
+}
+
+template <typename V, typename Coef>
+void mg_apply(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z,
+              cudaStream_t st) {
+    k_mg_first<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+        d, coef, kc, r, (V*)m->x[0], (V)MG_OMEGA, nullptr, nullptr, 0.0, 0, 0);
+    counted(1);
+    vcycle<V, Coef>(m, d, kc, coef, r, z, nullptr, nullptr, -1, st);
+}
+
+#define MG_INSTANTIATE(V, C)                                                                   \
+    template void mg_init<V, C>(MgHier*, const Dims&, int, const C&, const V*, V*, Scalars*,   \
+                                double*, double, int, int, cudaStream_t);                      \
+    template void mg_cg_b<V, C>(MgHier*, const Dims&, int, const C&, const V*, V*, V*, V*,     \
+                                Scalars*, double*, cudaStream_t);                              \
+    template void mg_apply<V, C>(MgHier*, const Dims&, int, const C&, const V*, V*,            \
+                                 cudaStream_t);
+
+MG_INSTANTIATE(double, CoefFaces64)
+MG_INSTANTIATE(float, CoefEta<float>)
+MG_INSTANTIATE(float, CoefEta<__nv_bfloat16>)
+MG_INSTANTIATE(float, CoefFaces32)
+
+}  // namespace pcg

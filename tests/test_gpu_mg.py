@@ -1,0 +1,190 @@
+"""Parity of the multigrid V-cycle preconditioner (POISSON_MG) with the FP64 oracle, through the
+C ABI: the hierarchy's depth, one V-cycle applied to a random vector (FP64 to rounding, FP32
+within its rounding), and full MG-preconditioned solves in every precision mode, with Dirichlet
+walls, periodic x and cut cells, against both acceptance criteria."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import multigrid as mg
+from paper_1410_1942_gb300 import build, capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+L2_TOL = 1e-6
+# one V-cycle, relative L2 distance from the oracle's FP64 cycle: FP64 differs only in the order
+# of the sums (a few ulp per level); FP32 carries the FP32 inner operator (rho/2 rounded to 24
+# bits, approximate reciprocals: ~1e-7 per face) and FP32 rounding through some 40 chained
+# sweeps and sums.
+VCYCLE_TOL = {"fp64": 1e-12, "fp32": 2e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    capi.load()
+
+
+def _rand_F(shape, seed):
+    rng = np.random.default_rng(seed)
+    F = rng.random(shape)
+    F[rng.random(shape) < 0.3] = 0.0
+    F[rng.random(shape) < 0.3] = 1.0
+    return F
+
+
+def _strut_apertures(grid):
+    Lx, Ly = grid.nx * grid.h, grid.ny * grid.h
+    psi = lambda x, y, z: inputs.ellipse_sdf(x, y, 0.5 * Lx, 0.5 * Ly, 0.3 * Lx, 0.2 * Ly)
+    return inputs.cut_apertures(grid, psi)
+
+
+# (shape nx, ny, nz; walls) -- several tiles, ragged tails, odd sizes, walls, periodic x
+APPLY_CASES = [((37, 23, 19), 0), ((64, 16, 8), 0), ((8, 9, 33), 0), ((40, 24, 20), 31),
+               ((48, 24, 20), oracle.PERIODIC_X), ((30, 12, 10), oracle.PERIODIC_X | 16),
+               ((3, 1, 70), 0)]
+
+
+def _walls_kw(walls):
+    return dict(dirichlet_walls=walls & 31, periodic_x=bool(walls & oracle.PERIODIC_X))
+
+
+@pytest.mark.parametrize("shape,walls", APPLY_CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_vcycle_apply_matches_oracle(shape, walls, prec):
+    nx, ny, nz = shape
+    F = _rand_F((nz, ny, nx), 1)
+    op = oracle.operator(F, walls=walls)
+    levels = mg.hierarchy(op)
+    r = np.random.default_rng(2).standard_normal(op.shape)
+    want = mg.vcycle(levels, r)
+    with capi.Poisson(nx, ny, nz, 1.0 / nz, precision=prec, precond="mg", **_walls_kw(walls)) as s:
+        s.set_density(F)
+        assert "mg-vcycle levels=%d" % len(levels) in s.describe()
+        got = np.empty_like(r)
+        s.precond_apply(r, got, kind="mg", precision=prec)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= VCYCLE_TOL[prec], err
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_vcycle_apply_with_cut_cells_matches_oracle(prec):
+    g = inputs.Grid(40, 24, 12, 1.0 / 12)
+    ap = _strut_apertures(g)
+    F = _rand_F(g.shape, 3)
+    op = oracle.operator(F, apertures=ap)
+    r = np.random.default_rng(4).standard_normal(g.shape)
+    want = mg.vcycle(mg.hierarchy(op), r)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg") as s:
+        s.set_apertures(*ap)
+        s.set_density(F)
+        got = np.empty_like(r)
+        s.precond_apply(r, got, kind="mg", precision=prec)
+    assert np.linalg.norm(got - want) <= VCYCLE_TOL[prec] * np.linalg.norm(want)
+
+
+def _reference(F, s, h, walls=0, apertures=None, vol=None):
+    op = oracle.operator(F, walls=walls, apertures=apertures)
+    b = oracle.rhs(s, h, vol)
+    ref = oracle.pcg(op, b, tol=1e-12, precond="ssor" if not walls & oracle.PERIODIC_X or
+                     op.nx % 2 == 0 else "jacobi")
+    assert ref.status == oracle.OK
+    return op, b, ref.x
+
+
+def _check(op, b, xref, p, st, tol):
+    rel = oracle.rel_residual(op, b, p)
+    assert rel <= tol * (1 + 1e-6), rel
+    err = np.linalg.norm(p - xref) / np.linalg.norm(xref)
+    assert err <= L2_TOL, err
+    assert abs(st["rel_residual"] - rel) <= 1e-3 * rel + 1e-15
+
+
+SOLVE_CASES = {
+    "flat": lambda: inputs.flat_case(32, 32, 32, seed=0, tol=1e-10),
+    "ragged": lambda: inputs.flat_case(37, 23, 19, seed=2, tol=1e-10),
+    "strut": lambda: inputs.strut_case(96, 48, 40, seed=1),
+    "column": lambda: inputs.flat_case(3, 5, 70, seed=4, tol=1e-10),
+}
+
+
+@pytest.mark.parametrize("name", list(SOLVE_CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_mg_solve_matches_oracle(name, prec):
+    c = SOLVE_CASES[name]()
+    g = c.grid
+    op, b, xref = _reference(c.F, c.s, g.h)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg") as s:
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, c.tol)
+    assert rc == capi.OK
+    _check(op, b, xref, p, st, c.tol)
+
+
+@pytest.mark.parametrize("walls", [31, oracle.PERIODIC_X, oracle.PERIODIC_X | 16])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mg_solve_with_boundary_variants(walls, prec):
+    c = inputs.strut_case(48, 24, 20, seed=3)
+    g = c.grid
+    op, b, xref = _reference(c.F, c.s, g.h, walls=walls)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg",
+                      **_walls_kw(walls)) as s:
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, 1e-9)
+    assert rc == capi.OK
+    _check(op, b, xref, p, st, 1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mg_solve_with_cut_cells(prec):
+    c = inputs.flat_case(48, 24, 16, seed=5, tol=1e-9)
+    g = c.grid
+    ap = _strut_apertures(g)
+    op, b, xref = _reference(c.F, c.s, g.h, apertures=ap, vol=ap[3])
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg") as s:
+        s.set_apertures(*ap)
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, 1e-9)
+    assert rc == capi.OK
+    _check(op, b, xref, p, st, 1e-9)
+
+
+def test_mg_needs_far_fewer_iterations_than_jacobi():
+    c = inputs.strut_case(128, 64, 64, seed=0)
+    g = c.grid
+    its = {}
+    for pc in ("jacobi", "mg"):
+        with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond=pc, tile=-1) as s:
+            s.set_density(c.F)
+            p = np.zeros(g.shape)
+            rc, st = s.solve(c.s, p, 1e-9)
+        assert rc == capi.OK
+        its[pc] = st["inner_iters"]
+    assert its["mg"] * 10 <= its["jacobi"], its
+
+
+def test_mg_errors():
+    with pytest.raises(capi.PoissonError) as e:
+        capi.Poisson(1, 1, 1, 1.0, precond="mg")
+    assert e.value.status == capi.EINVAL
+    F = _rand_F((4, 4, 4), 6)
+    r = np.ones((4, 4, 4))
+    z = np.empty_like(r)
+    with capi.Poisson(4, 4, 4, 0.25, precision="fp32") as s:
+        s.set_density(F)
+        with pytest.raises(capi.PoissonError) as e:
+            s.precond_apply(r, z, kind="mg", precision="fp32")
+        assert e.value.status == capi.EINVAL
+    with capi.Poisson(4, 4, 4, 0.25, precision="fp32", precond="mg") as s:
+        with pytest.raises(capi.PoissonError) as e:
+            s.precond_apply(r, z, kind="mg", precision="fp32")
+        assert e.value.status == capi.ENOTREADY
+        s.set_density(F)
+        with pytest.raises(capi.PoissonError) as e:
+            s.precond_apply(r, z, kind="mg", precision="fp64")
+        assert e.value.status == capi.EINVAL
