@@ -91,6 +91,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "rbssor", "mg"])
+    ap.add_argument("--inner-tol", type=float, default=1e-4,
+                    help="FP32 inner solve: relative reduction per refinement step")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -403,7 +405,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
     solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision, precond=args.precond,
                           stream=stream.cuda_stream, tile=args.tile, dirichlet_walls=args.walls,
-                          periodic_x=args.periodic_x)
+                          periodic_x=args.periodic_x, inner_tol=args.inner_tol)
     apertures = None
     if args.cut_body:
         Lx, Ly, _ = g.lengths
@@ -500,7 +502,8 @@ def main():
         p_h = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
         solver_h = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision,
                                 precond=args.precond, stream=stream.cuda_stream, tile=args.tile,
-                                dirichlet_walls=args.walls, periodic_x=args.periodic_x)
+                                dirichlet_walls=args.walls, periodic_x=args.periodic_x,
+                                inner_tol=args.inner_tol)
         if apertures is not None:
             solver_h.set_apertures(*apertures)
 
@@ -555,7 +558,7 @@ def main():
                                     % (g.nx, g.ny, g.nz)) if args.case == "wedge" else
                         (WORKLOAD if tuple(args.shape) == (256, 128, 128)
                          else "strut %dx%dx%d (profiling case)" % tuple(args.shape)), "cells": g.n, "precision": args.precision,
-                       "precond": args.precond, "tol": case.tol,
+                       "precond": args.precond, "tol": case.tol, "inner_tol": args.inner_tol,
                        "boundaries": ("strut as a free-slip cut-cell body, " if args.cut_body
                                       else "") + ("periodic x, " if args.periodic_x else "") +
                                      ("Dirichlet walls mask %d" % args.walls if args.walls
