@@ -207,28 +207,46 @@ __device__ __forceinline__ float eta_load<__nv_bfloat16>(const __nv_bfloat16* p,
     return __bfloat162float(p[c]);
 }
 
+// The face coefficients and diagonal of cell (i, j, k) from rho/2 of the cell (ec) and of its six
+// neighbours (a value across a wall or the top face is not used).  At a Dirichlet wall the face
+// coefficient is 1/eta_c, and nb_sum never reads past the wall.
+__device__ __forceinline__ void eta_stencil(const Dims& d, int i, int j, int k, float ec,
+                                            float exm, float exp_, float eym, float eyp,
+                                            float ezm, float ezp, Stencil<float>& w) {
+    const float ew = rcp_approx(ec);
+    const bool per = d.walls & PERIODIC_X;
+    w.xm = (i > 0 || per) ? rcp_approx(ec + exm) : ((d.walls & 1) ? ew : 0.f);
+    w.xp = (i + 1 < d.nx || per) ? rcp_approx(ec + exp_) : ((d.walls & 2) ? ew : 0.f);
+    w.ym = (j > 0) ? rcp_approx(ec + eym) : ((d.walls & 4) ? ew : 0.f);
+    w.yp = (j + 1 < d.ny) ? rcp_approx(ec + eyp) : ((d.walls & 8) ? ew : 0.f);
+    w.zm = (k > 0) ? rcp_approx(ec + ezm) : ((d.walls & 16) ? ew : 0.f);
+    const bool top = (k + 1 == d.nz);
+    const float wzp = top ? ew : rcp_approx(ec + ezp);
+    w.zp = top ? 0.f : wzp;
+    w.D = w.xm + w.xp + w.ym + w.yp + w.zm + wzp;
+}
+
 template <typename E>
 struct CoefEta {
     const E* eta;
     __device__ __forceinline__ void weights(const Dims& d, int c, int i, int j, int k,
                                             Stencil<float>& w) const {
-        const float ec = eta_load(eta, c);
-        // at a Dirichlet wall the face coefficient is 1/eta_c (nb_sum never reads past the wall)
-        const float ew = rcp_approx(ec);
         const bool per = d.walls & PERIODIC_X;
-        w.xm = (i > 0 || per) ? rcp_approx(ec + eta_load(eta, i > 0 ? c - 1 : c + d.nx - 1))
-                              : ((d.walls & 1) ? ew : 0.f);
-        w.xp = (i + 1 < d.nx || per)
-                   ? rcp_approx(ec + eta_load(eta, i + 1 < d.nx ? c + 1 : c + 1 - d.nx))
-                   : ((d.walls & 2) ? ew : 0.f);
-        w.ym = (j > 0) ? rcp_approx(ec + eta_load(eta, c - d.nx)) : ((d.walls & 4) ? ew : 0.f);
-        w.yp = (j + 1 < d.ny) ? rcp_approx(ec + eta_load(eta, c + d.nx)) : ((d.walls & 8) ? ew : 0.f);
-        w.zm = (k > 0) ? rcp_approx(ec + eta_load(eta, c - d.sxy)) : ((d.walls & 16) ? ew : 0.f);
-        const bool top = (k + 1 == d.nz);
-        const float wzp = top ? rcp_approx(ec) : rcp_approx(ec + eta_load(eta, c + d.sxy));
-        w.zp = top ? 0.f : wzp;
-        w.D = w.xm + w.xp + w.ym + w.yp + w.zm + wzp;
+        const float ec = eta_load(eta, c);
+        const float exm = (i > 0 || per) ? eta_load(eta, i > 0 ? c - 1 : c + d.nx - 1) : 0.f;
+        const float exp_ = (i + 1 < d.nx || per) ? eta_load(eta, i + 1 < d.nx ? c + 1 : c + 1 - d.nx)
+                                                 : 0.f;
+        const float eym = (j > 0) ? eta_load(eta, c - d.nx) : 0.f;
+        const float eyp = (j + 1 < d.ny) ? eta_load(eta, c + d.nx) : 0.f;
+        const float ezm = (k > 0) ? eta_load(eta, c - d.sxy) : 0.f;
+        const float ezp = (k + 1 < d.nz) ? eta_load(eta, c + d.sxy) : 0.f;
+        eta_stencil(d, i, j, k, ec, exm, exp_, eym, eyp, ezm, ezp, w);
     }
 };
+
+template <typename C>
+struct is_coef_eta { static constexpr bool value = false; };
+template <typename E>
+struct is_coef_eta<CoefEta<E>> { static constexpr bool value = true; };
 
 }  // namespace pcg

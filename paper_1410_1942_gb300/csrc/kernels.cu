@@ -285,6 +285,69 @@ __global__ void __launch_bounds__(TX * TY) k_cg_a(Dims d, Coef coef, int kc,
     }
 }
 
+// Phase A on the rho/2 operator, marching the thread's column in z with the values of the planes
+// k-1, k, k+1 in registers and the loads of plane k+2 issued before plane k is computed (the
+// plain k_cg_a leaves one plane's loads in flight per thread, which bounds it by latency).  Same
+// arithmetic, in the same order, as k_cg_a with CoefEta.
+template <typename E>
+__global__ void __launch_bounds__(TX * TY) k_cg_a_eta(Dims d, CoefEta<E> coef, int kc,
+                                                     const float* __restrict__ z,
+                                                     const float* __restrict__ p_in,
+                                                     float* __restrict__ p_out, Scalars* sc,
+                                                     double* partials) {
+    __shared__ double smem[64];
+    if (sc->done) return;
+    const float beta = (float)sc->beta;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    float acc = 0.f;
+    if (i < d.nx && j < d.ny) {
+        const bool per = d.walls & PERIODIC_X;
+        const bool hxm = i > 0 || per, hxp = i + 1 < d.nx || per, hym = j > 0, hyp = j + 1 < d.ny;
+        const int oxm = i > 0 ? -1 : d.nx - 1, oxp = i + 1 < d.nx ? 1 : 1 - d.nx;
+        auto pn = [&](int e) { return z[e] + beta * p_in[e]; };
+        auto et = [&](int e) { return eta_load(coef.eta, e); };
+        int c = i + d.nx * (j + d.ny * k0);
+        float pm = 0.f, em = 0.f, pp = 0.f, ep = 0.f, pq = 0.f, eq = 0.f;
+        if (k0 > 0) { pm = pn(c - d.sxy); em = et(c - d.sxy); }
+        float p0 = pn(c), e0 = et(c);
+        if (k0 + 1 < d.nz) { pp = pn(c + d.sxy); ep = et(c + d.sxy); }
+        for (int k = k0; k < k1; ++k, c += d.sxy) {
+            if (k + 1 < k1 && k + 2 < d.nz) { pq = pn(c + 2 * d.sxy); eq = et(c + 2 * d.sxy); }
+            Stencil<float> w;
+            eta_stencil(d, i, j, k, e0, hxm ? et(c + oxm) : 0.f, hxp ? et(c + oxp) : 0.f,
+                        hym ? et(c - d.nx) : 0.f, hyp ? et(c + d.nx) : 0.f, em, ep, w);
+            float s = 0.f;
+            if (hxm) s += w.xm * pn(c + oxm);
+            if (hxp) s += w.xp * pn(c + oxp);
+            if (hym) s += w.ym * pn(c - d.nx);
+            if (hyp) s += w.yp * pn(c + d.nx);
+            if (k > 0) s += w.zm * pm;
+            if (k + 1 < d.nz) s += w.zp * pp;
+            const float q = w.D * p0 - s;
+            acc += p0 * q;
+            p_out[c] = p0;
+            pm = p0; em = e0;
+            p0 = pp; e0 = ep;
+            pp = pq; ep = eq;
+        }
+    }
+    double v[1] = {(double)acc}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double pq2 = tot[0];
+            if (!(pq2 > 0.0) || !isfinite(pq2)) {
+                sc->done = BREAKDOWN;
+            } else {
+                sc->pq = pq2;
+                sc->alpha = sc->rz / pq2;
+            }
+        }
+    }
+}
+
 template <typename V, typename Coef>
 __global__ void __launch_bounds__(TX * TY) k_cg_b(Dims d, Coef coef, int kc,
                                                  const V* __restrict__ p, V* __restrict__ x,
@@ -707,7 +770,10 @@ void launch_cg_init(const Dims& d, int kc, const Coef& c, const V* r, V* z, Scal
 template <typename V, typename Coef>
 void launch_cg_a(const Dims& d, int kc, const Coef& c, const V* z, const V* p_in, V* p_out,
                  Scalars* sc, double* part, cudaStream_t st) {
-    k_cg_a<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
+    if constexpr (is_coef_eta<Coef>::value)
+        k_cg_a_eta<<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
+    else
+        k_cg_a<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
     counted(1);
 }
 

@@ -142,6 +142,35 @@ __global__ void __launch_bounds__(COARSE_T) k_mg_coarsest(Dims d, Coef coef, con
         for (int c = threadIdx.x; c < d.n; c += blockDim.x) y[c] = src[c];
 }
 
+// Sums (r, z) over the grid; the last block stores rz after the start (mode 0) or, inside PCG
+// (mode 1), counts the iteration and sets beta or the stopping state, like the SSOR red sweep.
+template <typename V>
+__device__ __forceinline__ void reduce_rz(V rz, Scalars* sc, double* partials, double* smem,
+                                          int mode) {
+    double v[1] = {(double)rz}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double rz_new = tot[0];
+            if (mode == 0) {
+                sc->rz = rz_new;
+                if (!isfinite(rz_new) || !(rz_new > 0.0)) sc->done = BREAKDOWN;
+            } else {
+                sc->iter += 1;
+                if (!isfinite(rz_new) || rz_new < 0.0 || !isfinite(sc->rr)) {
+                    sc->done = BREAKDOWN;
+                } else if (sc->rr <= sc->stop2) {
+                    sc->done = CONVERGED;
+                } else if (sc->iter >= sc->max_iter) {
+                    sc->done = CAPPED;
+                } else {
+                    sc->beta = rz_new / sc->rz;
+                    sc->rz = rz_new;
+                }
+            }
+        }
+    }
+}
+
 // Prolongation + post-smoothing: xt = x + a P e;  y = xt + w D^-1 (r - A xt).  On the fine
 // level (mode >= 0) also sums (r, y) and, like the SSOR red sweep, either stores rz after the
 // start (mode 0) or sets beta and the stopping state (mode 1).
@@ -186,28 +215,129 @@ __global__ void __launch_bounds__(TX * TY) k_mg_smooth(Dims d, Coef coef, int kc
             rz += rc * yc;
         }
     if (mode < 0 || !sc) return;
-    double v[1] = {(double)rz}, tot[1];
-    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            const double rz_new = tot[0];
-            if (mode == 0) {
-                sc->rz = rz_new;
-                if (!isfinite(rz_new) || !(rz_new > 0.0)) sc->done = BREAKDOWN;
-            } else {
-                sc->iter += 1;
-                if (!isfinite(rz_new) || rz_new < 0.0 || !isfinite(sc->rr)) {
-                    sc->done = BREAKDOWN;
-                } else if (sc->rr <= sc->stop2) {
-                    sc->done = CONVERGED;
-                } else if (sc->iter >= sc->max_iter) {
-                    sc->done = CAPPED;
-                } else {
-                    sc->beta = rz_new / sc->rz;
-                    sc->rz = rz_new;
-                }
+    reduce_rz(rz, sc, partials, smem, mode);
+}
+
+// The fine-level kernels on the rho/2 operator, marching the thread's column in z with planes
+// k-1, k, k+1 in registers and the loads of the next planes issued before plane k is computed
+// (the plain versions leave one plane's loads in flight per thread).  Same arithmetic, in the
+// same order, as k_mg_cg_b and k_mg_smooth with CoefEta.
+template <typename E>
+__global__ void __launch_bounds__(TX * TY) k_mg_cg_b_eta(Dims d, CoefEta<E> coef, int kc,
+                                                        const float* __restrict__ p,
+                                                        float* __restrict__ x,
+                                                        float* __restrict__ r,
+                                                        float* __restrict__ x0, float omega,
+                                                        Scalars* sc, double* partials) {
+    __shared__ double smem[64];
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    float rr = 0.f;
+    if (i < d.nx && j < d.ny) {
+        const bool per = d.walls & PERIODIC_X;
+        const bool hxm = i > 0 || per, hxp = i + 1 < d.nx || per, hym = j > 0, hyp = j + 1 < d.ny;
+        const int oxm = i > 0 ? -1 : d.nx - 1, oxp = i + 1 < d.nx ? 1 : 1 - d.nx;
+        auto et = [&](int e) { return eta_load(coef.eta, e); };
+        int c = i + d.nx * (j + d.ny * k0);
+        float pm = 0.f, em = 0.f, pp = 0.f, ep = 0.f, pq = 0.f, eq = 0.f, xn = 0.f, rn = 0.f;
+        if (k0 > 0) { pm = p[c - d.sxy]; em = et(c - d.sxy); }
+        float p0 = p[c], e0 = et(c), xc = x[c], rc = r[c];
+        if (k0 + 1 < d.nz) { pp = p[c + d.sxy]; ep = et(c + d.sxy); }
+        for (int k = k0; k < k1; ++k, c += d.sxy) {
+            if (k + 1 < k1) {
+                xn = x[c + d.sxy];
+                rn = r[c + d.sxy];
+                if (k + 2 < d.nz) { pq = p[c + 2 * d.sxy]; eq = et(c + 2 * d.sxy); }
             }
+            Stencil<float> w;
+            eta_stencil(d, i, j, k, e0, hxm ? et(c + oxm) : 0.f, hxp ? et(c + oxp) : 0.f,
+                        hym ? et(c - d.nx) : 0.f, hyp ? et(c + d.nx) : 0.f, em, ep, w);
+            float s = 0.f;
+            if (hxm) s += w.xm * p[c + oxm];
+            if (hxp) s += w.xp * p[c + oxp];
+            if (hym) s += w.ym * p[c - d.nx];
+            if (hyp) s += w.yp * p[c + d.nx];
+            if (k > 0) s += w.zm * pm;
+            if (k + 1 < d.nz) s += w.zp * pp;
+            const float q = w.D * p0 - s;
+            x[c] = xc + alpha * p0;
+            const float rnew = rc - alpha * q;
+            r[c] = rnew;
+            x0[c] = omega * rnew / w.D;
+            rr += rnew * rnew;
+            pm = p0; em = e0;
+            p0 = pp; e0 = ep;
+            pp = pq; ep = eq;
+            xc = xn; rc = rn;
         }
     }
+    double v[1] = {(double)rr}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sc->rr = tot[0];
+    }
+}
+
+template <typename E>
+__global__ void __launch_bounds__(TX * TY) k_mg_smooth_eta(Dims d, CoefEta<E> coef, int kc,
+                                                          const float* __restrict__ r,
+                                                          const float* __restrict__ x,
+                                                          const float* __restrict__ e, Dims dc,
+                                                          int sx, int sy, int sz, float alpha,
+                                                          float omega, float* __restrict__ y,
+                                                          Scalars* sc, double* partials,
+                                                          int mode) {
+    __shared__ double smem[64];
+    if (sc && sc->done) return;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    float rz = 0.f;
+    if (i < d.nx && j < d.ny) {
+        const bool per = d.walls & PERIODIC_X;
+        const bool hxm = i > 0 || per, hxp = i + 1 < d.nx || per, hym = j > 0, hyp = j + 1 < d.ny;
+        const int oxm = i > 0 ? -1 : d.nx - 1, oxp = i + 1 < d.nx ? 1 : 1 - d.nx;
+        const int im = i > 0 ? i - 1 : d.nx - 1, ip = i + 1 < d.nx ? i + 1 : 0;
+        auto et = [&](int q) { return eta_load(coef.eta, q); };
+        auto xt = [&](int ii, int jj, int kk) {
+            return x[ii + d.nx * (jj + d.ny * kk)] +
+                   alpha * e[(ii >> sx) + dc.nx * ((jj >> sy) + dc.ny * (kk >> sz))];
+        };
+        int c = i + d.nx * (j + d.ny * k0);
+        float tm = 0.f, em = 0.f, tp = 0.f, ep = 0.f, tq = 0.f, eq = 0.f, rn = 0.f;
+        if (k0 > 0) { tm = xt(i, j, k0 - 1); em = et(c - d.sxy); }
+        float t0 = xt(i, j, k0), e0 = et(c), rc = r[c];
+        if (k0 + 1 < d.nz) { tp = xt(i, j, k0 + 1); ep = et(c + d.sxy); }
+        for (int k = k0; k < k1; ++k, c += d.sxy) {
+            if (k + 1 < k1) {
+                rn = r[c + d.sxy];
+                if (k + 2 < d.nz) { tq = xt(i, j, k + 2); eq = et(c + 2 * d.sxy); }
+            }
+            Stencil<float> w;
+            eta_stencil(d, i, j, k, e0, hxm ? et(c + oxm) : 0.f, hxp ? et(c + oxp) : 0.f,
+                        hym ? et(c - d.nx) : 0.f, hyp ? et(c + d.nx) : 0.f, em, ep, w);
+            float s = 0.f;
+            if (hxm) s += w.xm * xt(im, j, k);
+            if (hxp) s += w.xp * xt(ip, j, k);
+            if (hym) s += w.ym * xt(i, j - 1, k);
+            if (hyp) s += w.yp * xt(i, j + 1, k);
+            if (k > 0) s += w.zm * tm;
+            if (k + 1 < d.nz) s += w.zp * tp;
+            const float yc = t0 + omega * (rc - (w.D * t0 - s)) / w.D;
+            y[c] = yc;
+            rz += rc * yc;
+            tm = t0; em = e0;
+            t0 = tp; e0 = ep;
+            tp = tq; ep = eq;
+            rc = rn;
+        }
+    }
+    if (mode < 0 || !sc) return;
+    reduce_rz(rz, sc, partials, smem, mode);
 }
 
 // Start of the preconditioned solve: x0 = w D^-1 r on the fine level; with scalars, sums r.r
@@ -319,9 +449,14 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
             (V*)m->y[l], sc, nullptr, -1);
     }
     const int* f = m->f[0];
-    k_mg_smooth<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
-        d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
-        f[2] - 1, al, om, z, sc, part, mode);
+    if constexpr (is_coef_eta<Coef>::value)
+        k_mg_smooth_eta<<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+            d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
+            f[2] - 1, al, om, z, sc, part, mode);
+    else
+        k_mg_smooth<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+            d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
+            f[2] - 1, al, om, z, sc, part, mode);
     counted(2 * L);
 }
 
@@ -427,8 +562,13 @@ void mg_init(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* 
 template <typename V, typename Coef>
 void mg_cg_b(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* p, V* x, V* r, V* z,
              Scalars* sc, double* part, cudaStream_t st) {
-    k_mg_cg_b<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r, (V*)m->x[0],
+    if constexpr (is_coef_eta<Coef>::value)
+        k_mg_cg_b_eta<<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r, (V*)m->x[0],
                                                             (V)MG_OMEGA, sc, part);
+    else
+        k_mg_cg_b<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r,
+                                                                (V*)m->x[0], (V)MG_OMEGA, sc,
+                                                                part);
     counted(1);
     vcycle<V, Coef>(m, d, kc, coef, r, z, sc, part, 1, st);
 }
