@@ -1,10 +1,10 @@
 // mg.cu -- the multigrid V-cycle preconditioner of the column-kernel PCG (see mg.h).
 //
-// All kernels are elementwise over the cells of one level.  The restriction and the Galerkin
-// setup run one thread per coarse cell over its (up to 8) fine cells; the prolongation +
-// post-smoothing runs in the column layout of the PCG kernels (the fine one carries the (r, z)
-// reduction, so its blocks must match the handle's reduction partials); the coarsest level is
-// one block.  Every kernel of a PCG iteration returns at once when the solve has finished.
+// All kernels are elementwise over the cells of one level.  The Galerkin setup runs one thread per
+// coarse cell over its (up to 8) fine cells, the restriction one thread per coarse cell on the
+// finest level and one per fine cell below; the prolongation + post-smoothing runs in the column
+// layout of the PCG kernels (the fine one carries the (r, z) reduction, so its blocks must match
+// the handle's reduction partials); the coarsest level is one block.  Every kernel of a PCG iteration returns at once when the solve has finished.
 #include <atomic>
 
 #include "poisson.h"
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(MT) k_mg_galerkin(Dims df, const T* __restrict
 }
 
 // r_c = P^T (r - A x) over the block of each coarse cell; x_c = w r_c / D_c (the coarse level's
-// pre-smoothing from zero).
+// pre-smoothing from zero).  One thread per coarse cell: the finest level.
 template <typename V, typename Coef>
 __global__ void __launch_bounds__(MT) k_mg_restrict(Dims df, Coef coef, const V* __restrict__ r,
                                                     const V* __restrict__ x, Dims dc, int fx,
@@ -115,15 +115,62 @@ __global__ void __launch_bounds__(MT) k_mg_restrict(Dims df, Coef coef, const V*
     xc[I] = omega * s / cdiag[I];
 }
 
-// Coarsest level: x holds the first damped Jacobi sweep from zero; sweeps - 1 more follow,
-// alternating between x and y (one block, so __syncthreads orders them); the result ends in y.
+// The same with eight consecutive threads per coarse cell, one per child (bit 0 of the lane: +x,
+// bit 1: +y, bit 2: +z), the children's residuals added by a fixed shuffle tree: the coarse
+// levels, whose few cells would leave one thread per coarse cell walking eight stencils alone.
+// (On the finest level the eight-lane pattern halves the coalescing and is slower.)
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(MT) k_mg_restrict8(Dims df, Coef coef, const V* __restrict__ r,
+                                                    const V* __restrict__ x, Dims dc, int fx,
+                                                    int fy, int fz, const V* __restrict__ cdiag,
+                                                    V* __restrict__ rc, V* __restrict__ xc,
+                                                    V omega, const Scalars* sc) {
+    if (sc && sc->done) return;
+    const long long t = blockIdx.x * (long long)MT + threadIdx.x;
+    const long long I = t >> 3;
+    const int q = threadIdx.x & 7;
+    const int qx = q & 1, qy = (q >> 1) & 1, qz = q >> 2;
+    V s = 0;
+    if (I < dc.n) {
+        int ic, jc, kc;
+        coarse_index(dc, (int)I, ic, jc, kc);
+        const int i = ic * fx + qx, j = jc * fy + qy, k = kc * fz + qz;
+        if (qx < fx && qy < fy && qz < fz && i < df.nx && j < df.ny && k < df.nz) {
+            const int c = i + df.nx * (j + df.ny * k);
+            auto ld = [&](int e) { return x[e]; };
+            Stencil<V> w;
+            coef.weights(df, c, i, j, k, w);
+            s = r[c] - (w.D * x[c] - nb_sum(df, w, c, i, j, k, ld));
+        }
+    }
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (q == 0 && I < dc.n) {
+        rc[I] = s;
+        xc[I] = omega * s / cdiag[I];
+    }
+}
+
+// Coarsest level: x holds the first damped Jacobi sweep from zero; sweeps - 1 more follow in one
+// block (__syncthreads between sweeps), the iterates alternating between two shared-memory
+// buffers when the level fits (at most MG_COARSE_MAX cells), else between x and y; the result
+// ends in y.
 template <typename V, typename Coef>
 __global__ void __launch_bounds__(COARSE_T) k_mg_coarsest(Dims d, Coef coef, const V* r, V* x,
                                                           V* y, V omega, int sweeps,
                                                           const Scalars* sc) {
+    __shared__ V buf[2][MG_COARSE_MAX];
     if (sc && sc->done) return;
+    const bool in_smem = d.n <= MG_COARSE_MAX;
     V* src = x;
     V* dst = y;
+    if (in_smem) {
+        for (int c = threadIdx.x; c < d.n; c += blockDim.x) buf[0][c] = x[c];
+        __syncthreads();
+        src = buf[0];
+        dst = buf[1];
+    }
     for (int m = 1; m < sweeps; ++m) {
         auto ld = [&](int e) { return src[e]; };
         for (int c = threadIdx.x; c < d.n; c += blockDim.x) {
@@ -282,14 +329,14 @@ __global__ void __launch_bounds__(TX * TY) k_mg_cg_b_eta(Dims d, CoefEta<E> coef
 }
 
 template <typename E>
-__global__ void __launch_bounds__(TX * TY) k_mg_smooth_eta(Dims d, CoefEta<E> coef, int kc,
-                                                          const float* __restrict__ r,
-                                                          const float* __restrict__ x,
-                                                          const float* __restrict__ e, Dims dc,
-                                                          int sx, int sy, int sz, float alpha,
-                                                          float omega, float* __restrict__ y,
-                                                          Scalars* sc, double* partials,
-                                                          int mode) {
+__global__ void __launch_bounds__(TX * TY, 5) k_mg_smooth_eta(Dims d, CoefEta<E> coef, int kc,
+                                                             const float* __restrict__ r,
+                                                             const float* __restrict__ x,
+                                                             const float* __restrict__ e,
+                                                             Dims dc, int sx, int sy, int sz,
+                                                             float alpha, float omega,
+                                                             float* __restrict__ y, Scalars* sc,
+                                                             double* partials, int mode) {
     __shared__ double smem[64];
     if (sc && sc->done) return;
     const int i = blockIdx.x * TX + threadIdx.x;
@@ -301,30 +348,36 @@ __global__ void __launch_bounds__(TX * TY) k_mg_smooth_eta(Dims d, CoefEta<E> co
         const bool per = d.walls & PERIODIC_X;
         const bool hxm = i > 0 || per, hxp = i + 1 < d.nx || per, hym = j > 0, hyp = j + 1 < d.ny;
         const int oxm = i > 0 ? -1 : d.nx - 1, oxp = i + 1 < d.nx ? 1 : 1 - d.nx;
-        const int im = i > 0 ? i - 1 : d.nx - 1, ip = i + 1 < d.nx ? i + 1 : 0;
+        // parents: x and y offsets of the cell's and its x/y neighbours' aggregates
+        const int pc = (i >> sx) + dc.nx * (j >> sy);
+        const int pxm = ((i + oxm) >> sx) + dc.nx * (j >> sy);
+        const int pxp = ((i + oxp) >> sx) + dc.nx * (j >> sy);
+        const int pym = (i >> sx) + dc.nx * ((hym ? j - 1 : j) >> sy);
+        const int pyp = (i >> sx) + dc.nx * ((hyp ? j + 1 : j) >> sy);
         auto et = [&](int q) { return eta_load(coef.eta, q); };
-        auto xt = [&](int ii, int jj, int kk) {
-            return x[ii + d.nx * (jj + d.ny * kk)] +
-                   alpha * e[(ii >> sx) + dc.nx * ((jj >> sy) + dc.ny * (kk >> sz))];
-        };
+        auto xt = [&](int c, int pk) { return x[c] + alpha * e[pc + pk]; };
         int c = i + d.nx * (j + d.ny * k0);
         float tm = 0.f, em = 0.f, tp = 0.f, ep = 0.f, tq = 0.f, eq = 0.f, rn = 0.f;
-        if (k0 > 0) { tm = xt(i, j, k0 - 1); em = et(c - d.sxy); }
-        float t0 = xt(i, j, k0), e0 = et(c), rc = r[c];
-        if (k0 + 1 < d.nz) { tp = xt(i, j, k0 + 1); ep = et(c + d.sxy); }
+        if (k0 > 0) { tm = xt(c - d.sxy, dc.sxy * ((k0 - 1) >> sz)); em = et(c - d.sxy); }
+        float t0 = xt(c, dc.sxy * (k0 >> sz)), e0 = et(c), rc = r[c];
+        if (k0 + 1 < d.nz) { tp = xt(c + d.sxy, dc.sxy * ((k0 + 1) >> sz)); ep = et(c + d.sxy); }
         for (int k = k0; k < k1; ++k, c += d.sxy) {
             if (k + 1 < k1) {
                 rn = r[c + d.sxy];
-                if (k + 2 < d.nz) { tq = xt(i, j, k + 2); eq = et(c + 2 * d.sxy); }
+                if (k + 2 < d.nz) {
+                    tq = xt(c + 2 * d.sxy, dc.sxy * ((k + 2) >> sz));
+                    eq = et(c + 2 * d.sxy);
+                }
             }
+            const int pk = dc.sxy * (k >> sz);
             Stencil<float> w;
             eta_stencil(d, i, j, k, e0, hxm ? et(c + oxm) : 0.f, hxp ? et(c + oxp) : 0.f,
                         hym ? et(c - d.nx) : 0.f, hyp ? et(c + d.nx) : 0.f, em, ep, w);
             float s = 0.f;
-            if (hxm) s += w.xm * xt(im, j, k);
-            if (hxp) s += w.xp * xt(ip, j, k);
-            if (hym) s += w.ym * xt(i, j - 1, k);
-            if (hyp) s += w.yp * xt(i, j + 1, k);
+            if (hxm) s += w.xm * (x[c + oxm] + alpha * e[pxm + pk]);
+            if (hxp) s += w.xp * (x[c + oxp] + alpha * e[pxp + pk]);
+            if (hym) s += w.ym * (x[c - d.nx] + alpha * e[pym + pk]);
+            if (hyp) s += w.yp * (x[c + d.nx] + alpha * e[pyp + pk]);
             if (k > 0) s += w.zm * tm;
             if (k + 1 < d.nz) s += w.zp * tp;
             const float yc = t0 + omega * (rc - (w.D * t0 - s)) / w.D;
@@ -433,7 +486,7 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
                 df, coef, rl, (const V*)m->x[0], dc, f[0], f[1], f[2], (const V*)m->diag[1],
                 (V*)m->r[1], (V*)m->x[1], om, sc);
         else
-            k_mg_restrict<V, typename LC::type><<<blocks_of(dc.n), MT, 0, st>>>(
+            k_mg_restrict8<V, typename LC::type><<<blocks_of(8LL * dc.n), MT, 0, st>>>(
                 df, LC::of(*m, l), rl, (const V*)m->x[l], dc, f[0], f[1], f[2],
                 (const V*)m->diag[l + 1], (V*)m->r[l + 1], (V*)m->x[l + 1], om, sc);
     }
