@@ -31,6 +31,9 @@ struct LevelCoef;
 template <>
 struct LevelCoef<double> {
     using type = CoefFaces64;
+    __host__ __device__ static type make(const double* bx, const double* by, const double* bz, const double* dg) {
+        return CoefFaces64{bx, by, bz, dg, nullptr};
+    }
     static type of(const MgHier& m, int l) {
         return CoefFaces64{(const double*)m.bx[l], (const double*)m.by[l], (const double*)m.bz[l],
                            (const double*)m.diag[l], nullptr};
@@ -39,6 +42,9 @@ struct LevelCoef<double> {
 template <>
 struct LevelCoef<float> {
     using type = CoefFaces32;
+    __host__ __device__ static type make(const float* bx, const float* by, const float* bz, const float* dg) {
+        return CoefFaces32{bx, by, bz, dg};
+    }
     static type of(const MgHier& m, int l) {
         return CoefFaces32{(const float*)m.bx[l], (const float*)m.by[l], (const float*)m.bz[l],
                            (const float*)m.diag[l]};
@@ -85,18 +91,10 @@ __global__ void __launch_bounds__(MT) k_mg_galerkin(Dims df, const T* __restrict
     cdiag[I] = (V)D;
 }
 
-// r_c = P^T (r - A x) over the block of each coarse cell; x_c = w r_c / D_c (the coarse level's
-// pre-smoothing from zero).  One thread per coarse cell: the finest level.
+// P^T (r - A x) at coarse cell I: the residuals of its (up to 8) fine cells, added x fastest.
 template <typename V, typename Coef>
-__global__ void __launch_bounds__(MT) k_mg_restrict(Dims df, Coef coef, const V* __restrict__ r,
-                                                    const V* __restrict__ x, Dims dc, int fx,
-                                                    int fy, int fz, const V* __restrict__ cdiag,
-                                                    V* __restrict__ rc, V* __restrict__ xc,
-                                                    V omega, const Scalars* sc) {
-    if (sc && sc->done) return;
-    const long long t = blockIdx.x * (long long)MT + threadIdx.x;
-    if (t >= dc.n) return;
-    const int I = (int)t;
+__device__ __forceinline__ V restrict_at(const Dims& df, const Coef& coef, const V* r, const V* x,
+                                         const Dims& dc, int fx, int fy, int fz, int I) {
     int ic, jc, kc;
     coarse_index(dc, I, ic, jc, kc);
     const int i0 = ic * fx, j0 = jc * fy, k0 = kc * fz;
@@ -111,6 +109,22 @@ __global__ void __launch_bounds__(MT) k_mg_restrict(Dims df, Coef coef, const V*
                 coef.weights(df, c, i, j, k, w);
                 s += r[c] - (w.D * x[c] - nb_sum(df, w, c, i, j, k, ld));
             }
+    return s;
+}
+
+// r_c = P^T (r - A x) over the block of each coarse cell; x_c = w r_c / D_c (the coarse level's
+// pre-smoothing from zero).  One thread per coarse cell: the finest level.
+template <typename V, typename Coef>
+__global__ void __launch_bounds__(MT) k_mg_restrict(Dims df, Coef coef, const V* __restrict__ r,
+                                                    const V* __restrict__ x, Dims dc, int fx,
+                                                    int fy, int fz, const V* __restrict__ cdiag,
+                                                    V* __restrict__ rc, V* __restrict__ xc,
+                                                    V omega, const Scalars* sc) {
+    if (sc && sc->done) return;
+    const long long t = blockIdx.x * (long long)MT + threadIdx.x;
+    if (t >= dc.n) return;
+    const int I = (int)t;
+    const V s = restrict_at(df, coef, r, x, dc, fx, fy, fz, I);
     rc[I] = s;
     xc[I] = omega * s / cdiag[I];
 }
@@ -152,16 +166,14 @@ __global__ void __launch_bounds__(MT) k_mg_restrict8(Dims df, Coef coef, const V
     }
 }
 
-// Coarsest level: x holds the first damped Jacobi sweep from zero; sweeps - 1 more follow in one
-// block (__syncthreads between sweeps), the iterates alternating between two shared-memory
-// buffers when the level fits (at most MG_COARSE_MAX cells), else between x and y; the result
-// ends in y.
+// Coarsest level, inside one block: x holds the first damped Jacobi sweep from zero; sweeps - 1
+// more follow (__syncthreads between sweeps), the iterates alternating between the two
+// shared-memory buffers when the level fits (at most MG_COARSE_MAX cells), else between x and y;
+// the result ends in y.
 template <typename V, typename Coef>
-__global__ void __launch_bounds__(COARSE_T) k_mg_coarsest(Dims d, Coef coef, const V* r, V* x,
-                                                          V* y, V omega, int sweeps,
-                                                          const Scalars* sc) {
-    __shared__ V buf[2][MG_COARSE_MAX];
-    if (sc && sc->done) return;
+__device__ __forceinline__ void coarsest_sweeps(const Dims& d, const Coef& coef, const V* r, V* x,
+                                                V* y, V omega, int sweeps,
+                                                V (*buf)[MG_COARSE_MAX]) {
     const bool in_smem = d.n <= MG_COARSE_MAX;
     V* src = x;
     V* dst = y;
@@ -187,6 +199,84 @@ __global__ void __launch_bounds__(COARSE_T) k_mg_coarsest(Dims d, Coef coef, con
     }
     if (src != y)
         for (int c = threadIdx.x; c < d.n; c += blockDim.x) y[c] = src[c];
+}
+
+// y = xt + w D^-1 (r - A xt) at cell c = (i, j, k), with xt = x + a e(parent) at the cell and its
+// neighbours: one cell of the prolongation + post-smoothing, terms in nb_sum's order.
+template <typename V, typename Coef>
+__device__ __forceinline__ V smooth_at(const Dims& d, const Coef& coef, const V* r, const V* x,
+                                       const V* e, const Dims& dc, int sx, int sy, int sz,
+                                       V alpha, V omega, int c, int i, int j, int k) {
+    const bool per = d.walls & PERIODIC_X;
+    auto xt = [&](int ii, int jj, int kk) -> V {
+        return x[ii + d.nx * (jj + d.ny * kk)] +
+               alpha * e[(ii >> sx) + dc.nx * ((jj >> sy) + dc.ny * (kk >> sz))];
+    };
+    Stencil<V> w;
+    coef.weights(d, c, i, j, k, w);
+    V s = 0;
+    if (i > 0) s += w.xm * xt(i - 1, j, k);
+    else if (per) s += w.xm * xt(d.nx - 1, j, k);
+    if (i + 1 < d.nx) s += w.xp * xt(i + 1, j, k);
+    else if (per) s += w.xp * xt(0, j, k);
+    if (j > 0) s += w.ym * xt(i, j - 1, k);
+    if (j + 1 < d.ny) s += w.yp * xt(i, j + 1, k);
+    if (k > 0) s += w.zm * xt(i, j, k - 1);
+    if (k + 1 < d.nz) s += w.zp * xt(i, j, k + 1);
+    const V xc = xt(i, j, k);
+    return xc + omega * (r[c] - (w.D * xc - s)) / w.D;
+}
+
+// The bottom of the V-cycle in one block: the levels from b (whose r and pre-smoothed x the
+// previous restriction wrote) to the coarsest -- restrictions down, the coarsest sweeps,
+// prolongation + post-smoothing up to level b, whose y it leaves for the next finer level.  The
+// level arrays are written and read by the same block between __syncthreads, so they are read
+// with plain loads.
+constexpr int MG_BOTTOM_LEVELS = 8;
+constexpr int MG_BOTTOM_CELLS = 2048;  // largest level handled in the block
+
+template <typename V>
+struct Bottom {
+    int nb;  // levels b .. b + nb - 1 (the coarsest)
+    Dims d[MG_BOTTOM_LEVELS];
+    int f[MG_BOTTOM_LEVELS][3];
+    const V *bx[MG_BOTTOM_LEVELS], *by[MG_BOTTOM_LEVELS], *bz[MG_BOTTOM_LEVELS],
+        *diag[MG_BOTTOM_LEVELS];
+    V *r[MG_BOTTOM_LEVELS], *x[MG_BOTTOM_LEVELS], *y[MG_BOTTOM_LEVELS];
+};
+
+template <typename V>
+__global__ void __launch_bounds__(COARSE_T) k_mg_bottom(Bottom<V> B, V omega, V alpha, int sweeps,
+                                                        const Scalars* sc) {
+    __shared__ V buf[2][MG_COARSE_MAX];
+    if (sc && sc->done) return;
+    using LC = LevelCoef<V>;
+    for (int q = 0; q + 1 < B.nb; ++q) {
+        const auto cf = LC::make(B.bx[q], B.by[q], B.bz[q], B.diag[q]);
+        const Dims& dc = B.d[q + 1];
+        for (int I = threadIdx.x; I < dc.n; I += blockDim.x) {
+            const V v = restrict_at(B.d[q], cf, (const V*)B.r[q], (const V*)B.x[q], dc, B.f[q][0],
+                                    B.f[q][1], B.f[q][2], I);
+            B.r[q + 1][I] = v;
+            B.x[q + 1][I] = omega * v / B.diag[q + 1][I];
+        }
+        __syncthreads();
+    }
+    const int cq = B.nb - 1;
+    coarsest_sweeps(B.d[cq], LC::make(B.bx[cq], B.by[cq], B.bz[cq], B.diag[cq]),
+                    (const V*)B.r[cq], B.x[cq], B.y[cq], omega, sweeps, buf);
+    __syncthreads();
+    for (int q = B.nb - 2; q >= 0; --q) {
+        const auto cf = LC::make(B.bx[q], B.by[q], B.bz[q], B.diag[q]);
+        const Dims& d = B.d[q];
+        for (int c = threadIdx.x; c < d.n; c += blockDim.x) {
+            const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
+            B.y[q][c] = smooth_at(d, cf, (const V*)B.r[q], (const V*)B.x[q], (const V*)B.y[q + 1],
+                                  B.d[q + 1], B.f[q][0] - 1, B.f[q][1] - 1, B.f[q][2] - 1, alpha,
+                                  omega, c, i, j, k);
+        }
+        __syncthreads();
+    }
 }
 
 // Sums (r, z) over the grid; the last block stores rz after the start (mode 0) or, inside PCG
@@ -231,11 +321,6 @@ __global__ void __launch_bounds__(TX * TY) k_mg_smooth(Dims d, Coef coef, int kc
                                                       double* partials, int mode) {
     __shared__ double smem[64];
     if (sc && sc->done) return;
-    const bool per = d.walls & PERIODIC_X;
-    auto xt = [&](int ii, int jj, int kk) -> V {
-        return x[ii + d.nx * (jj + d.ny * kk)] +
-               alpha * e[(ii >> sx) + dc.nx * ((jj >> sy) + dc.ny * (kk >> sz))];
-    };
     V rz = 0;
     const int i = blockIdx.x * TX + threadIdx.x;
     const int j = blockIdx.y * TY + threadIdx.y;
@@ -244,22 +329,9 @@ __global__ void __launch_bounds__(TX * TY) k_mg_smooth(Dims d, Coef coef, int kc
     if (i < d.nx && j < d.ny)
         for (int k = k0; k < k1; ++k) {
             const int c = i + d.nx * (j + d.ny * k);
-            Stencil<V> w;
-            coef.weights(d, c, i, j, k, w);
-            V s = 0;
-            if (i > 0) s += w.xm * xt(i - 1, j, k);
-            else if (per) s += w.xm * xt(d.nx - 1, j, k);
-            if (i + 1 < d.nx) s += w.xp * xt(i + 1, j, k);
-            else if (per) s += w.xp * xt(0, j, k);
-            if (j > 0) s += w.ym * xt(i, j - 1, k);
-            if (j + 1 < d.ny) s += w.yp * xt(i, j + 1, k);
-            if (k > 0) s += w.zm * xt(i, j, k - 1);
-            if (k + 1 < d.nz) s += w.zp * xt(i, j, k + 1);
-            const V xc = xt(i, j, k);
-            const V rc = r[c];
-            const V yc = xc + omega * (rc - (w.D * xc - s)) / w.D;
+            const V yc = smooth_at(d, coef, r, x, e, dc, sx, sy, sz, alpha, omega, c, i, j, k);
             y[c] = yc;
-            rz += rc * yc;
+            rz += r[c] * yc;
         }
     if (mode < 0 || !sc) return;
     reduce_rz(rz, sc, partials, smem, mode);
@@ -476,25 +548,38 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
     using LC = LevelCoef<V>;
     const int L = m->nlev;
     const V om = (V)MG_OMEGA, al = (V)MG_ALPHA;
-    for (int l = 0; l + 1 < L; ++l) {
+    // levels b .. L-1 run in one block (at most MG_BOTTOM_CELLS cells each, b >= 1)
+    int b = L - 1;
+    while (b - 1 >= 1 && m->d[b - 1].n <= MG_BOTTOM_CELLS && L - (b - 1) <= MG_BOTTOM_LEVELS) --b;
+    for (int l = 0; l < b; ++l) {
         const Dims& df = m->d[l];
         const Dims& dc = m->d[l + 1];
         const int* f = m->f[l];
-        const V* rl = l == 0 ? r : (const V*)m->r[l];
         if (l == 0)
             k_mg_restrict<V, Coef><<<blocks_of(dc.n), MT, 0, st>>>(
-                df, coef, rl, (const V*)m->x[0], dc, f[0], f[1], f[2], (const V*)m->diag[1],
+                df, coef, r, (const V*)m->x[0], dc, f[0], f[1], f[2], (const V*)m->diag[1],
                 (V*)m->r[1], (V*)m->x[1], om, sc);
         else
             k_mg_restrict8<V, typename LC::type><<<blocks_of(8LL * dc.n), MT, 0, st>>>(
-                df, LC::of(*m, l), rl, (const V*)m->x[l], dc, f[0], f[1], f[2],
+                df, LC::of(*m, l), (const V*)m->r[l], (const V*)m->x[l], dc, f[0], f[1], f[2],
                 (const V*)m->diag[l + 1], (V*)m->r[l + 1], (V*)m->x[l + 1], om, sc);
     }
-    const int c = L - 1;
-    k_mg_coarsest<V, typename LC::type><<<1, COARSE_T, 0, st>>>(
-        m->d[c], LC::of(*m, c), (const V*)m->r[c], (V*)m->x[c], (V*)m->y[c], om, MG_COARSE_SWEEPS,
-        sc);
-    for (int l = L - 2; l >= 1; --l) {
+    Bottom<V> B{};
+    B.nb = L - b;
+    for (int q = 0; q < B.nb; ++q) {
+        const int l = b + q;
+        B.d[q] = m->d[l];
+        for (int a = 0; a < 3; ++a) B.f[q][a] = m->f[l][a];
+        B.bx[q] = (const V*)m->bx[l];
+        B.by[q] = (const V*)m->by[l];
+        B.bz[q] = (const V*)m->bz[l];
+        B.diag[q] = (const V*)m->diag[l];
+        B.r[q] = (V*)m->r[l];
+        B.x[q] = (V*)m->x[l];
+        B.y[q] = (V*)m->y[l];
+    }
+    k_mg_bottom<V><<<1, COARSE_T, 0, st>>>(B, om, al, MG_COARSE_SWEEPS, sc);
+    for (int l = b - 1; l >= 1; --l) {
         const int* f = m->f[l];
         k_mg_smooth<V, typename LC::type><<<cols(m->d[l], 1), dim3(TX, TY), 0, st>>>(
             m->d[l], LC::of(*m, l), 1, (const V*)m->r[l], (const V*)m->x[l],
@@ -510,7 +595,7 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
         k_mg_smooth<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
             d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
             f[2] - 1, al, om, z, sc, part, mode);
-    counted(2 * L);
+    counted(2 * b + 1);
 }
 
 }  // namespace
