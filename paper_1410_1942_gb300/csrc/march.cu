@@ -904,6 +904,7 @@ struct VariantOps {
     int smem32, smem16;
     const void *k32, *k16;
     int family;
+    const void *k32p = nullptr, *k16p = nullptr;  // periodic-x instantiations (family 1)
 };
 
 template <int CX, int CY, int TYT, int WS, int NS, int F>
@@ -911,7 +912,7 @@ static VariantOps make_ops() {
     if constexpr (F == 1 || F == 2) {
         static_assert(WS == 1, "the one-sweep kernels have a producer warp");
         const Cg1Kernel k = F == 1 ? cg1_kernel(CX, CY, TYT, NS) : cg2_kernel(CX, CY, TYT, NS);
-        return VariantOps{CX, CY, TYT, 1, NS, k.smem32, k.smem16, k.k32, k.k16, F};
+        return VariantOps{CX, CY, TYT, 1, NS, k.smem32, k.smem16, k.k32, k.k16, F, k.k32p, k.k16p};
     } else if constexpr (WS)
         return VariantOps{CX, CY, TYT, 1, NS, NS * Geo<CX, CY, TYT, float>::STAGE,
                           NS * Geo<CX, CY, TYT, __nv_bfloat16>::STAGE,
@@ -941,6 +942,10 @@ static const VariantOps* variants(int* count) {
         for (const auto& v : table) {
             cudaFuncSetAttribute(v.k32, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem32);
             cudaFuncSetAttribute(v.k16, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem16);
+            if (v.k32p)
+                cudaFuncSetAttribute(v.k32p, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem32);
+            if (v.k16p)
+                cudaFuncSetAttribute(v.k16p, cudaFuncAttributeMaxDynamicSharedMemorySize, v.smem16);
         }
         cudaGetLastError();
     });
@@ -999,7 +1004,15 @@ int march_occupancy(int variant, bool bf16) {
         cudaGetLastError();
         return 0;
     }
-    return o;
+    // a plan sized here may launch the periodic instantiation: take the smaller residency
+    const void* kp = bf16 ? v.k16p : v.k32p;
+    int op = o;
+    if (kp && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, kp, threads_of(v),
+                                                            bf16 ? v.smem16 : v.smem32) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return o < op ? o : op;
 }
 
 // ------------------------------------------------------------------ plans
@@ -1229,9 +1242,13 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
         if (!march_encode_solve(m, solves[s], variant, bf16)) return -1;
         for (int q = 0; q < MAPS_PER_SOLVE; ++q) maps[MAPS_PER_SOLVE * (size_t)s + q] = m[q];
     }
+    int nper = 0;
+    for (int s = 0; s < nsolves; ++s) nper += (solves[s].d.walls & PERIODIC_X) ? 1 : 0;
+    if (nper != 0 && nper != nsolves) return -1;  // one instantiation per launch
     p->variant = variant;
     p->strategy = strategy;
     p->bf16 = bf16;
+    p->periodic = nper > 0;
     p->nctas = nctas;
     p->nsolves = nsolves;
     p->nsegs = (int)segs.size();
@@ -1266,7 +1283,9 @@ int launch_march_pcg(const MarchPlan& p, cudaStream_t st) {
     const VariantOps& v = variants(&n)[p.variant];
     PcgArgs args{p.solves, p.segs, p.cta_seg, p.maps, p.part_a, p.part_b, p.ctl, p.nctas, p.trace};
     void* params[] = {&args};
-    const cudaError_t e = cudaLaunchCooperativeKernel(p.bf16 ? v.k16 : v.k32, dim3(p.nctas),
+    const void* k = p.periodic ? (p.bf16 ? v.k16p : v.k32p) : (p.bf16 ? v.k16 : v.k32);
+    if (!k) return -1;
+    const cudaError_t e = cudaLaunchCooperativeKernel(k, dim3(p.nctas),
                                                       dim3(32, v.tyt + v.ws), params,
                                                       (size_t)(p.bf16 ? v.smem16 : v.smem32), st);
     g_kernel_launches.fetch_add(1, std::memory_order_relaxed);

@@ -86,6 +86,7 @@ struct MarchPlan {
     int variant = 0;
     int strategy = 0;
     bool bf16 = false;
+    bool periodic = false;  // the solves have periodic x (the kernel's periodic instantiation)
     int nctas = 0, nsolves = 0, nsegs = 0;
     SolveDev* solves = nullptr;
     Seg* segs = nullptr;

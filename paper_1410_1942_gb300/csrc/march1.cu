@@ -78,7 +78,9 @@ __device__ __forceinline__ float u_next(float u, float s, float w, float al, flo
 // leave x as it is).
 __device__ __forceinline__ bool x_sweep(const LocalSolve1& L) { return !L.first && (L.iter & 1); }
 
-template <int CX, int CY, int TYT, typename E, int NS>
+// PER: the solves have periodic x (padded rows with ghost columns); a separate instantiation so
+// that the plain kernel carries none of it.
+template <int CX, int CY, int TYT, typename E, int NS, bool PER>
 __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1_ws(PcgArgs a) {
     using G = Geo1<CX, CY, TYT, E>;
     constexpr int NT = 32 * (TYT + 1);
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
             const CUtensorMap* m = a.maps + MAPS_PER_SOLVE * sg.solve;
             const bool xs = s_nextxs[sg.solve - first] != 0;
             // periodic x: the padded rows start PAD_V (eta: EOFF) columns before x = 0
-            const bool per = s_sol[sg.solve - first].per != 0;
+            constexpr bool per = PER;
             const int xv = sg.x0 - G::VOFF + (per ? PAD_V : 0), xe = sg.x0 - G::EOFF + (per ? G::EOFF : 0);
             for (int off = 0; off < L + 2; ++off) {
                 if (s_fail) return;
@@ -304,12 +306,13 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
                                 if (xs) st_row<CX>(s_sol[l].x + c, xn);
                                 st_row<CX>(s_sol[l].p + c, pn);
                                 const LocalSolve1& Ls = s_sol[l];
-                                const size_t row = (size_t)Ls.nxp * (j0 + y + (size_t)d.ny * k);
-                                const size_t cp = row + i0 + (Ls.per ? PAD_V : 0);
+                                const size_t row = (size_t)(PER ? Ls.nxp : d.nx) *
+                                                   (j0 + y + (size_t)d.ny * k);
+                                const size_t cp = row + i0 + (PER ? PAD_V : 0);
                                 st_row<CX>(Ls.u[out] + cp, uc[y]);
                                 st_row<CX>(Ls.s[out] + cp, sn);
                                 st_row<CX>(Ls.w[out] + cp, wn);
-                                if (Ls.per && (i0 < PAD_V || i0 >= d.nx - PAD_V)) {
+                                if (PER && (i0 < PAD_V || i0 >= d.nx - PAD_V)) {
                                     // the ghost copy at the other end of the padded row
                                     const long long cg = (long long)row + i0 + PAD_V +
                                                          (i0 < PAD_V ? d.nx : -d.nx);
@@ -514,10 +517,12 @@ __global__ void __launch_bounds__(32 * (TYT + 1), WsMinBlocks<TYT>::value) k_cg1
 
 template <int CX, int CY, int TYT, int NS>
 static Cg1Kernel cg1_of() {
-    return Cg1Kernel{(const void*)k_cg1_ws<CX, CY, TYT, float, NS>,
-                     (const void*)k_cg1_ws<CX, CY, TYT, __nv_bfloat16, NS>,
+    return Cg1Kernel{(const void*)k_cg1_ws<CX, CY, TYT, float, NS, false>,
+                     (const void*)k_cg1_ws<CX, CY, TYT, __nv_bfloat16, NS, false>,
                      NS * Geo1<CX, CY, TYT, float>::STAGE,
-                     NS * Geo1<CX, CY, TYT, __nv_bfloat16>::STAGE};
+                     NS * Geo1<CX, CY, TYT, __nv_bfloat16>::STAGE,
+                     (const void*)k_cg1_ws<CX, CY, TYT, float, NS, true>,
+                     (const void*)k_cg1_ws<CX, CY, TYT, __nv_bfloat16, NS, true>};
 }
 
 Cg1Kernel cg1_kernel(int cx, int cy, int tyt, int ns) {

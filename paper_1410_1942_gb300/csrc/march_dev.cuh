@@ -425,6 +425,7 @@ struct LocalSolve {
 struct Cg1Kernel {
     const void *k32, *k16;
     int smem32, smem16;
+    const void *k32p = nullptr, *k16p = nullptr;  // periodic-x instantiations (one-sweep family)
 };
 Cg1Kernel cg1_kernel(int cx, int cy, int tyt, int ns);  // null kernels if not instantiated
 // Kernels of the one-sweep family with A p formed in the sweep (march2.cu).
