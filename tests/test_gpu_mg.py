@@ -188,3 +188,82 @@ def test_mg_errors():
         with pytest.raises(capi.PoissonError) as e:
             s.precond_apply(r, z, kind="mg", precision="fp64")
         assert e.value.status == capi.EINVAL
+
+
+def test_mg_periodic_odd_nx_keeps_x_uncoarsened():
+    """Periodic x with odd nx: the x axis is not coarsened (its wrap face stays between two
+    aggregates); the level shapes and one cycle follow the oracle's."""
+    nx, ny, nz = 45, 16, 12
+    F = _rand_F((nz, ny, nx), 21)
+    walls = oracle.PERIODIC_X
+    op = oracle.operator(F, walls=walls)
+    levels = mg.hierarchy(op)
+    assert all(lev.op.nx == nx for lev in levels)
+    r = np.random.default_rng(22).standard_normal(op.shape)
+    want = mg.vcycle(levels, r)
+    with capi.Poisson(nx, ny, nz, 1.0 / nz, precision="fp64", precond="mg",
+                      **_walls_kw(walls)) as s:
+        s.set_density(F)
+        assert "mg-vcycle levels=%d" % len(levels) in s.describe()
+        got = np.empty_like(r)
+        s.precond_apply(r, got, kind="mg", precision="fp64")
+    assert np.linalg.norm(got - want) <= VCYCLE_TOL["fp64"] * np.linalg.norm(want)
+
+
+def test_mg_bf16_with_cut_cells():
+    c = inputs.flat_case(48, 24, 16, seed=9, tol=1e-9)
+    g = c.grid
+    ap = _strut_apertures(g)
+    op, b, xref = _reference(c.F, c.s, g.h, apertures=ap, vol=ap[3])
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="bf16", precond="mg") as s:
+        s.set_apertures(*ap)
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, 1e-9)
+    assert rc == capi.OK
+    _check(op, b, xref, p, st, 1e-9)
+
+
+def test_mg_warm_start_and_zero_source():
+    c = inputs.flat_case(40, 24, 20, seed=6, tol=1e-10)
+    g = c.grid
+    op, b, xref = _reference(c.F, c.s, g.h)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond="mg") as s:
+        s.set_density(c.F)
+        p = xref.copy()
+        rc, st = s.solve(c.s, p, 1e-9)
+        assert rc == capi.OK and st["inner_iters"] == 0 and np.array_equal(p, xref)
+        p = np.full(g.shape, 3.0)
+        rc, st = s.solve(np.zeros(g.shape), p, 1e-9)
+        assert rc == capi.OK and not p.any()
+
+
+def test_mg_iteration_cap_reports_notconv_with_best_iterate():
+    c = inputs.strut_case(96, 48, 40, seed=1)
+    g = c.grid
+    op = oracle.operator(c.F)
+    b = oracle.rhs(c.s, g.h)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond="mg", max_iters=4) as s:
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, 1e-9, allow=(capi.ENOTCONV,))
+    assert rc == capi.ENOTCONV
+    assert st["inner_iters"] <= 4 + 8
+    rel = oracle.rel_residual(op, b, p)
+    assert rel < 1.0 and abs(st["rel_residual"] - rel) <= 1e-3 * rel
+
+
+def test_mg_device_and_host_arrays_agree():
+    import torch
+    c = inputs.strut_case(64, 32, 24, seed=4)
+    g = c.grid
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond="mg") as s:
+        s.set_density(c.F)
+        ph = np.zeros(g.shape)
+        rc, _ = s.solve(c.s, ph, 1e-9)
+        assert rc == capi.OK
+        sd = torch.from_numpy(c.s).cuda()
+        pd = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+        rc, _ = s.solve(sd, pd, 1e-9)
+        assert rc == capi.OK
+    assert np.array_equal(pd.cpu().numpy(), ph)

@@ -515,7 +515,8 @@ def strut_full():
 
 @pytest.mark.parametrize("prec,precond", [("fp32", "jacobi"), ("fp64", "jacobi"),
                                           ("bf16", "jacobi"), ("fp32", "rbssor"),
-                                          ("fp64", "rbssor")])
+                                          ("fp64", "rbssor"), ("fp32", "mg"), ("fp64", "mg"),
+                                          ("bf16", "mg")])
 def test_full_size_strut_solve(strut_full, prec, precond):
     """The 256 x 128 x 128 strut workload at 1e-9, as the benchmark runs it."""
     c, op, b, xref = strut_full
