@@ -322,7 +322,7 @@ def batched(n=64, seed=0):
 def served(nreq, seed=0):
     """The request stream: capacity with every request waiting at t = 0 (6 steps each), then
     Poisson arrivals at 70 % of that capacity, 20 steps per request; FP32 inner solve, and the
-    plain FP64 PCG's capacity on the same stream for comparison."""
+    plain FP64 PCG's and the multigrid-preconditioned solve's capacities for comparison."""
     import math as _m
     from paper_1410_1942_gb300 import inputs, serve
     # warm the device-side input generators (torch compiles its complex kernels on first use)
@@ -333,13 +333,18 @@ def served(nreq, seed=0):
     st = serve.Server(budget, steps=20).serve(serve.request_stream(nreq, rate, seed=seed))
     cap64 = serve.Server(budget, precision="fp64", steps=3).serve(
         serve.request_stream(max(4, nreq // 4), _m.inf, seed=seed + 2))
+    # the same capacity stream with the multigrid preconditioner (unbatched handles)
+    capmg = serve.Server(budget, steps=6, precond="mg").serve(
+        serve.request_stream(max(4, nreq // 2), _m.inf, seed=seed + 1))
     return {"capacity_solves_per_s": cap["solves_per_s"], "arrival_rate_per_s": rate,
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "solves": st["solves"], "requests": nreq, "steps_per_request": 20,
             "max_rel_residual": st["max_rel_residual"], "all_ok": st["all_ok"],
             "peak_active": st["peak_active"],
             "fp64_capacity_solves_per_s": cap64["solves_per_s"],
-            "fp64_p50_ms": cap64["p50_ms"], "fp64_p99_ms": cap64["p99_ms"]}
+            "fp64_p50_ms": cap64["p50_ms"], "fp64_p99_ms": cap64["p99_ms"],
+            "mg_capacity_solves_per_s": capmg["solves_per_s"],
+            "mg_max_rel_residual": capmg["max_rel_residual"], "mg_all_ok": capmg["all_ok"]}
 
 
 def cpu_baseline(case, seconds, precond):

@@ -27,12 +27,18 @@ from . import capi, inputs
 
 # device bytes per cell of a handle (capi.cu allocations) plus the request's own F, s, p arrays
 HANDLE_BYTES_PER_CELL = {"fp32": 32 + 16 + 6 + 36, "bf16": 32 + 16 + 6 + 36, "fp64": 32 + 16 + 6 + 8 + 32}
+# the multigrid hierarchy: the fine pre-smoothed vector and seven arrays per coarse cell (levels
+# shrink by 8: under 1/7 of the fine count in all), in the handle's inner precision
+MG_BYTES_PER_CELL = {"fp32": 4 + 4, "bf16": 4 + 4, "fp64": 8 + 8}
 REQUEST_BYTES_PER_CELL = 3 * 8
 
 
-def request_bytes(shape, precision):
+def request_bytes(shape, precision, precond="jacobi"):
     n = shape[0] * shape[1] * shape[2]
-    return n * (HANDLE_BYTES_PER_CELL[precision] + REQUEST_BYTES_PER_CELL) + (1 << 20)
+    per = HANDLE_BYTES_PER_CELL[precision] + REQUEST_BYTES_PER_CELL
+    if precond == "mg":
+        per += MG_BYTES_PER_CELL[precision]
+    return n * per + (1 << 20)
 
 
 @dataclasses.dataclass
@@ -75,10 +81,13 @@ def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
 
 class Server:
     def __init__(self, budget_bytes, precision="fp32", tol=1e-9, steps=20, device="cuda",
-                 keep_results=False, tile=12204):
+                 keep_results=False, tile=12204, precond="jacobi"):
         # tile: kernel variant of every request's handle (fixed, so admission does not run the
-        # autotuner; the batch executor uses the variant of its largest solve)
+        # autotuner; the batch executor uses the variant of its largest solve).  precond "mg":
+        # the V-cycle preconditioner; such handles are not batched, the executor solves them one
+        # by one when they are polled.
         self.tile = tile
+        self.precond = precond
         self.budget = int(budget_bytes)
         self.precision = precision
         self.tol = tol
@@ -93,7 +102,8 @@ class Server:
         import torch
         r.p = torch.zeros(g.shape, dtype=torch.float64, device=self.device)
         r.solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=self.precision,
-                                tile=self.tile if self.precision != "fp64" else 0)
+                                tile=self.tile if self.precision != "fp64" else 0,
+                                precond=self.precond)
         r.solver.set_density(F)
         r.admitted_at = now
         self._submit(r, r.arrival)
@@ -120,7 +130,7 @@ class Server:
         while pending or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
-                need = request_bytes(pending[0].shape, self.precision)
+                need = request_bytes(pending[0].shape, self.precision, self.precond)
                 if used + need > self.budget and active:
                     break  # wait for memory to free up
                 r = pending.popleft()
@@ -153,7 +163,7 @@ class Server:
                     r.solver.close()
                     r.solver = None
                     r.F = r.s = r.p = None
-                    used -= request_bytes(r.shape, self.precision)
+                    used -= request_bytes(r.shape, self.precision, self.precond)
                     active.remove(r)
         wall = time.perf_counter() - t0
         lat = np.array(lat) if lat else np.zeros(1)

@@ -56,3 +56,20 @@ def test_result_alone_equals_result_in_the_mix():
     assert st["all_ok"] and st["peak_active"] >= 2
     a, m = alone.results[target.rid], mixed.results[mix[2].rid]
     assert np.linalg.norm(a - m) / np.linalg.norm(a) <= L2_TOL
+
+
+def test_stream_with_the_multigrid_preconditioner():
+    """MG handles are not batched (the executor solves them one by one at poll): every step
+    converges, warm starts still pay, and a request's result equals the Jacobi stream's to the
+    solves' accuracy."""
+    reqs = _stream(4, math.inf, seed=4)
+    jac = serve.Server(budget_bytes=8 << 30, steps=3, keep_results=True)
+    jac.serve(copy.deepcopy(reqs))
+    srv = serve.Server(budget_bytes=8 << 30, steps=3, keep_results=True, precond="mg")
+    st = srv.serve(reqs)
+    assert st["all_ok"] and st["solves"] == 12
+    assert st["max_rel_residual"] <= 1e-9 * (1 + 1e-6)
+    for r in reqs:
+        assert max(r.iters) <= 60
+        a, m = jac.results[r.rid], srv.results[r.rid]
+        assert np.linalg.norm(a - m) / np.linalg.norm(a) <= 2 * L2_TOL
