@@ -206,6 +206,20 @@ def dist_env():
     return world, rank, local
 
 
+def combine_ranks(t, units, device, world):
+    """Whole-job figures of a replicated run: the slowest rank's time and the units of all ranks
+    (two all-reduces over the process group; world 1: unchanged)."""
+    if world <= 1:
+        return t, units
+    import torch
+    import torch.distributed as tdist
+    tt = torch.tensor([t, units], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
+    tdist.all_reduce(tt, op=tdist.ReduceOp.SUM)
+    return float(mx[0]), float(tt[1])
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
     """The oracle (plain FP64 CPU PCG) timed on this host's cores, same workload and metric."""
@@ -458,13 +472,7 @@ def main():
     prof = solver.profile_read()
     solver.profile(False)
     units = float(g.n) * iters                     # cell-iterations of this rank
-    t_max = dev_ms
-    if world > 1:
-        tt = torch.tensor([dev_ms, units], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.SUM)
-        t_max, units = float(mx[0]), float(tt[1])
+    t_max, units = combine_ranks(dev_ms, units, dev, world)
     value = units / (t_max * 1e-3) / 1e9
 
     # dominant CG kernel and its roofline
@@ -529,12 +537,7 @@ def main():
         barrier()
         te = time.perf_counter() - t0
         ue = float(g.n) * its_e
-        if world > 1:
-            tt = torch.tensor([te, ue], dtype=torch.float64, device=dev)
-            mx = tt.clone()
-            tdist.all_reduce(mx, op=tdist.ReduceOp.MAX)
-            tdist.all_reduce(tt, op=tdist.ReduceOp.SUM)
-            te, ue = float(mx[0]), float(tt[1])
+        te, ue = combine_ranks(te, ue, dev, world)
         e2e = {"value": ue / te / 1e9, "unit": "Gcell-iters/s",
                "h2d_bytes_per_step": 3 * 8 * g.n, "d2h_bytes_per_step": 8 * g.n,
                "ms_per_step": 1e3 * te / args.steps}
