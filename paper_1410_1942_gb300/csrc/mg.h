@@ -13,8 +13,9 @@
 //     y = x + w D^-1 (r - A x); on the coarsest level MG_COARSE_SWEEPS damped Jacobi sweeps
 //     from zero.  Symmetric and positive definite (0 < w < 1), so PCG keeps its theory.
 //
-// Kernels per V-cycle: one restriction per level pair (the fine one reads r and the pre-smoothed
-// x), one single-block coarsest solve, one prolongation + post-smoothing per level; the fine
+// Kernels per V-cycle: one restriction per level pair down to the bottom levels (the fine one
+// reads r and the pre-smoothed x), one single-block kernel for the levels of at most 2048 cells
+// and the coarsest sweeps, one prolongation + post-smoothing per level above them; the fine
 // post-smoothing writes z and reduces (r, z) into the CG scalars.
 #pragma once
 
