@@ -4,7 +4,8 @@
 // coarse cell over its (up to 8) fine cells, the restriction one thread per coarse cell on the
 // finest level and one per fine cell below; the prolongation + post-smoothing runs in the column
 // layout of the PCG kernels (the fine one carries the (r, z) reduction, so its blocks must match
-// the handle's reduction partials); the coarsest level is one block.  Every kernel of a PCG iteration returns at once when the solve has finished.
+// the handle's reduction partials); the bottom levels and the coarsest run in one block.  Every
+// kernel of a PCG iteration returns at once when the solve has finished.
 #include <atomic>
 
 #include "poisson.h"
