@@ -2,15 +2,22 @@
 
 One step = one pass of the whole solve path over one synthetic input: set the density from the
 water fraction (operator set-up) and solve div((1/rho) grad p) = s to relative residual 1e-9 from
-a zero start (FP32 inner PCG inside FP64 refinement by default).  The workload is the
-surface-piercing elliptic strut on a 256 x 128 x 128 grid (4,194,304 cells, density ratio 1000).
+a zero start (FP32 inner PCG inside FP64 refinement by default).  The default workload is the
+largest single-GPU configuration: a wedge-like hull (signed-distance half-plane pair, seeded
+entrance half-angle) in a two-phase surface with breaking-like patches on a 1024 x 512 x 256 grid
+(134,217,728 cells, density ratio 1000).  ``--case strut`` runs the 256 x 128 x 128 strut instead.
 
 value  = cells x CG iterations / device seconds, summed over ranks (Gcell-iters/s), inputs
-         resident in HBM, L2 flushed between steps.
+         resident in HBM (and far larger than L2; a 256 MiB buffer is also written between steps).
 e2e    = the same metric through the C ABI with pinned HOST arrays: the H2D copy of F, s and the
          start p and the D2H copy of the solution are inside the timed region.
-roofline: the dominant CG kernel's algorithmic bytes per launch / its mean CUDA-event duration.
+roofline: the dominant CG kernel's algorithmic bytes per launch / its mean CUDA-event duration;
+         traffic = the DRAM bytes per cell-iteration of the committed ncu capture (taken on the
+         current sources of that kernel) times the cell-iterations of a launch.
 cpu_baseline: the FP64 CPU oracle timed on this host on a bounded sample of the same workload.
+extras (rank 0): the wedge with BF16 densities in the inner operator and with the multigrid
+         preconditioner, and the strut workload's line with its plain-FP64 comparison, its
+         64-solve batch and its served request stream.
 
 --impl reference times the oracle instead (the reference arm: a plain CPU program).
 Multi-GPU (torchrun): independent replicas, one solve per rank per step (weak scaling).
@@ -31,10 +38,24 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-CELLS_NOTE = "strut 256x128x128"
-WORKLOAD = ("surface-piercing elliptic strut (0.1 x 0.02, water density) in a Kelvin-like "
-            "two-phase surface, 256x128x128 cells, h = 1/128, rho 1/1000, source div(u*)/dt of "
-            "8 random modes; tol 1e-9 rel. residual, zero start")
+METRIC = "Poisson PCG Gcell-iters/s"
+SHAPES = {"wedge": (1024, 512, 256), "strut": (256, 128, 128)}
+TOL = 1e-9
+
+
+def workload(kind, shape):
+    nx, ny, nz = shape
+    if kind == "wedge":
+        return ("wedge-like hull (signed-distance half-plane pair, seeded entrance half-angle "
+                "10-30 deg, full depth, water density) in a two-phase surface with breaking-like "
+                "patches (5 %% of the cells within 2h of the surface set to 0 or 1), %dx%dx%d "
+                "cells, h = 1/%d, rho 1/1000, source div(u*)/dt of 8 random modes; tol 1e-9 rel. "
+                "residual, zero start" % (nx, ny, nz, nz))
+    return ("surface-piercing elliptic strut (0.1 x 0.02, water density) in a Kelvin-like "
+            "two-phase surface, %dx%dx%d cells, h = 1/%d, rho 1/1000, source div(u*)/dt of 8 "
+            "random modes; tol 1e-9 rel. residual, zero start" % (nx, ny, nz, nz))
+
+
 # Algorithmic bytes per cell of one launch of each CG pass (FP32 vectors; rho/2 per cell as the
 # coefficient array, FP32 = 4 B, BF16 = 2 B; neighbour re-reads served on chip, not counted):
 #   phase A: read z, p_old, eta; write p                     = 3 vec + eta + 1 vec
@@ -51,6 +72,13 @@ BYTES_PER_CELL_ONE_SWEEP = {"fp32": 16 + 4 + 16 + 4, "bf16": 16 + 2 + 16 + 4}
 # one-sweep kernels that form A p in the sweep: read u, p (8 B) + eta, write u, p (8 B), x every
 # other iteration (4 B on average)
 BYTES_PER_CELL_AP_FORMED = {"fp32": 8 + 4 + 8 + 4, "bf16": 8 + 2 + 8 + 4}
+# The face-array schedule that the stencil's byte model counts per cell-iteration (Jacobi, FP32
+# vectors): three stored face arrays and 1/D read, q = A p stored and re-read -- 14 words = 56 B.
+# The kernels here store rho/2 instead of faces and never store q, so they move less; the line
+# reports the fraction at both counts.
+BYTES_PER_CELL_FACE_SCHEDULE = 56
+
+
 # MG-preconditioned phase B (POISSON_MG), per fine cell: the CG update (read p, x, r, eta; write
 # x, r, the pre-smoothed x0 = 7 vec-equivalents with eta), the fine restriction (read r, x0, eta;
 # write r_c, x_c: 2 values per 8 cells) and the fine prolongation + smoothing (read x0, r, eta and
@@ -81,14 +109,20 @@ def mg_levels(nx, ny, nz, periodic, coarse_max=512):
 
 
 L2_FLUSH_BYTES = 256 << 20
+E2E_MAX_STEPS = 5     # end-to-end steps (each moves 4 GiB between host and device on the wedge)
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default="wedge", choices=["wedge", "strut"],
+                    help="wedge 1024x512x256 (default; fields made on the device) or the "
+                         "256x128x128 strut")
+    ap.add_argument("--shape", type=int, nargs=3, default=None,
+                    help="grid of the workload (smaller cases for profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "rbssor", "mg"])
     ap.add_argument("--inner-tol", type=float, default=1e-4,
@@ -97,21 +131,24 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--shape", type=int, nargs=3, default=(256, 128, 128),
-                    help="grid of the strut workload (profiling of smaller cases)")
     ap.add_argument("--tile", type=int, default=0, help="FP32 kernel tile option (0 = autotuned)")
     ap.add_argument("--walls", type=int, default=0,
                     help="Dirichlet side/bottom walls bitmask (1 x-, 2 x+, 4 y-, 8 y+, 16 z-)")
     ap.add_argument("--periodic-x", action="store_true", help="periodic x boundaries")
     ap.add_argument("--cut-body", action="store_true",
                     help="the strut as a free-slip cut-cell body (face and volume fractions)")
+    ap.add_argument("--cap-iters", type=int, default=0,
+                    help="profiling: cap each solve at this many CG iterations (one inner launch "
+                         "of exactly that many; the solve ends not converged)")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the FP64 comparison, batched and served measurements")
+                    help="skip the BF16 / multigrid wedge lines and the strut line with its FP64 "
+                         "comparison, batched and served measurements")
     ap.add_argument("--serve-requests", type=int, default=24)
-    ap.add_argument("--case", default="strut", choices=["strut", "wedge"],
-                    help="strut 256x128x128 (default) or the 1024x512x256 wedge (fields made on "
-                         "the device)")
-    return ap.parse_args()
+    args = ap.parse_args(argv)
+    if args.shape is None:
+        args.shape = SHAPES[args.case]
+    args.shape = tuple(args.shape)
+    return args
 
 
 def peaks():
@@ -123,25 +160,32 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def source_hash():
+# Sources that define each persistent kernel family (device code and the host code that plans
+# its launches): a committed ncu figure counts only while these files are unchanged.
+KERNEL_SOURCES = {
+    "one-sweep": ["march1.cu", "march_dev.cuh", "tma.cuh", "internal.cuh", "march.h", "march.cu"],
+}
+
+
+def source_hash(family="one-sweep"):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1410_1942_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in sorted(KERNEL_SOURCES[family]):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, precision, workload):
-    """DRAM bytes per cell-iteration of `kernel` on `workload` from the committed ncu summary, if
-    it was taken on the current kernel sources; else None."""
+def ncu_traffic(family, precision, kind):
+    """DRAM bytes per cell-iteration of the persistent kernel `family` on workload `kind`, from
+    the committed ncu summary if it was taken on the kernel's current sources; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(path):
+    if family not in KERNEL_SOURCES or not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    e = d.get("%s/%s/%s" % (precision, kernel, workload))
-    if not e or e.get("source_hash") != source_hash():
+    e = d.get("%s/%s/%s" % (precision, family, kind))
+    if not e or e.get("source_hash") != source_hash(family):
         return None
     return e.get("dram_bytes_per_cell_iter")
 
@@ -220,21 +264,32 @@ def combine_ranks(t, units, device, world):
     return float(mx[0]), float(tt[1])
 
 
+def make_fields(kind, shape, seed, device):
+    """(grid, F, s, meta) of the workload as float64 torch tensors on `device`."""
+    import torch
+    from paper_1410_1942_gb300 import inputs
+    if kind == "wedge":
+        return inputs.wedge_fields_t(shape, seed=seed, device=device)
+    c = inputs.strut_case(*shape, seed=seed)
+    return (c.grid, torch.from_numpy(c.F).to(device), torch.from_numpy(c.s).to(device), c.meta)
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args):
-    """The oracle (plain FP64 CPU PCG) timed on this host's cores, same workload and metric."""
+    """The oracle (plain FP64 CPU PCG) timed on this host's cores, same workload and metric:
+    each step is a fixed window of FP64 PCG iterations from the zero start."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
     import oracle
-    from paper_1410_1942_gb300 import inputs
     oracle.build()
-    c = inputs.strut_case(256, 128, 128, seed=args.seed)
-    op = oracle.operator(c.F)
-    b = oracle.rhs(c.s, c.grid.h)
+    g, F, s, _ = make_fields(args.case, args.shape, args.seed, "cpu")
+    op = oracle.operator(F.numpy())
+    b = oracle.rhs(s.numpy(), g.h)
+    del F, s
     iters_per_step = 20
     precond = "ssor" if args.precond == "rbssor" else "jacobi"
-    x = np.zeros(c.grid.shape)
+    x = np.zeros(g.shape)
     for _ in range(args.warmup):
         oracle.pcg(op, b, x0=x, tol=0.0, precond=precond, max_iters=iters_per_step)
     t0 = time.perf_counter()
@@ -243,17 +298,18 @@ def run_reference(args):
         r = oracle.pcg(op, b, x0=x, tol=0.0, precond=precond, max_iters=iters_per_step)
         its += r.iters
     dt = time.perf_counter() - t0
-    val = c.grid.n * its / dt / 1e9
+    val = g.n * its / dt / 1e9
     line = {
-        "impl": "reference", "metric": "Poisson PCG Gcell-iters/s", "value": val,
+        "impl": "reference", "metric": METRIC, "value": val,
         "unit": "Gcell-iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precond": precond},
+        "config": {"workload": workload(args.case, args.shape), "precond": precond},
         "cpu_baseline": {"value": val, "unit": "Gcell-iters/s", "cores": oracle.threads(),
                          "kind": "oracle",
-                         "sample": "%d FP64 %s-PCG iterations per step of the CPU oracle on the "
-                                   "%s workload" % (iters_per_step, precond, CELLS_NOTE)},
+                         "sample": "%d FP64 %s-PCG iterations per step of the CPU oracle (zero "
+                                   "start) on the %s %dx%dx%d workload" %
+                                   ((iters_per_step, precond, args.case) + args.shape)},
         "e2e": {"value": val, "unit": "Gcell-iters/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -261,24 +317,143 @@ def run_reference(args):
     return 0
 
 
-def fp64_baseline(case, steps, stream):
+# ----------------------------------------------------------------------------- measurements
+def timed_solves(solver, F, s, p, tol, steps, warmup, stream, sync, clocks=None, flush=None,
+                 allow=None):
+    """`warmup` untimed then `steps` timed solves (set_density + solve from p = 0), each
+    bracketed by CUDA events on the solver's stream; returns the device time and the counts."""
+    from paper_1410_1942_gb300 import capi
+    allow = allow or (capi.OK,)
+
+    def step():
+        solver.set_density(F)
+        p.zero_()
+        rc, st = solver.solve(s, p, tol, allow=allow)
+        return st
+
+    import torch
+    for _ in range(warmup):
+        step()
+    solver.profile(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    iters, outer, rels = 0, 0, []
+    sync()
+    if clocks:
+        clocks.start()
+    l0 = capi.kernel_launches()
+    for q in range(steps):
+        if flush is not None:
+            flush.fill_(q & 0xFF)
+        evs[q][0].record(stream)
+        st = step()
+        evs[q][1].record(stream)
+        iters += st["inner_iters"]
+        outer += st["outer_iters"]
+        rels.append(st["rel_residual"])
+    sync()
+    launches = capi.kernel_launches() - l0
+    clk = clocks.stop() if clocks else None
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    prof = solver.profile_read()
+    solver.profile(False)
+    return {"dev_ms": dev_ms, "iters": iters, "outer": outer, "rels": rels,
+            "launches": launches, "clocks": clk, "prof": prof}
+
+
+def roofline(prof, desc, precision, precond, g, iters, periodic, kind):
+    """The dominant CG kernel's algorithmic bytes per launch over its mean event time."""
+    bpc = BYTES_PER_CELL[precision]
+    cands = [k for k in ("pcg_persistent", "cg_phase_a", "cg_phase_b") if prof[k]["launches"]]
+    dom = max(cands, key=lambda k: prof[k]["ms"])
+    per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
+    family = None
+    if "A p formed" in desc:
+        bpi = BYTES_PER_CELL_AP_FORMED[precision]
+    elif "one-sweep" in desc:
+        bpi = BYTES_PER_CELL_ONE_SWEEP[precision]
+        family = "one-sweep"
+    elif precond == "mg":
+        bpc = dict(bpc)
+        bpc["cg_phase_b"] = mg_phase_b_bytes(precision, mg_levels(g.nx, g.ny, g.nz, periodic), g.n)
+        bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]
+    else:
+        bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]  # algorithmic bytes per cell-iteration
+    if dom == "pcg_persistent":
+        # one launch runs every CG iteration of one inner solve
+        cell_iters = g.n * iters / prof[dom]["launches"]
+        alg_bytes = bpi * cell_iters
+    else:
+        cell_iters = g.n
+        alg_bytes = bpc[dom] * g.n
+    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    bpci = ncu_traffic(family, precision, kind) if family and dom == "pcg_persistent" else None
+    out = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+           "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+           # DRAM bytes per launch, like alg_bytes: the measured bytes per cell-iteration times
+           # the cell-iterations of an average launch
+           "traffic": bpci * cell_iters if bpci is not None else None,
+           "traffic_bytes_per_cell_iter": bpci,
+           "alg_bytes_per_launch": alg_bytes, "alg_bytes_per_cell_iter": bpi,
+           "ms_per_launch": per_launch_ms, "cell_iters_per_launch": cell_iters}
+    if family == "one-sweep" and precision == "fp32":
+        out["frac_at_face_schedule_bytes"] = (BYTES_PER_CELL_FACE_SCHEDULE * cell_iters /
+                                              (per_launch_ms * 1e-3) / 1e9 / peak)
+    return out
+
+
+def e2e_line(make_solver, F, s, g, tol, steps, warmup, dev, world, apertures=None):
+    """The metric end to end through the C ABI with pinned host arrays (H2D of F, s and the
+    start p, D2H of the solution inside every step)."""
+    import torch
+    from paper_1410_1942_gb300 import capi
+    F_h = F.cpu().pin_memory()
+    s_h = s.cpu().pin_memory()
+    p_h = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+    sv = make_solver()
+    if apertures is not None:
+        sv.set_apertures(*apertures)
+
+    def step():
+        p_h.zero_()
+        sv.set_density(F_h)
+        rc, st = sv.solve(s_h, p_h, tol)
+        if rc != capi.OK:
+            raise RuntimeError("e2e solve failed: %s" % capi.strerror(rc))
+        return st
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    its, t0 = 0, time.perf_counter()
+    for _ in range(steps):
+        its += step()["inner_iters"]
+    torch.cuda.synchronize(dev)
+    te = time.perf_counter() - t0
+    ue = float(g.n) * its
+    te, ue = combine_ranks(te, ue, dev, world)
+    sv.close()
+    return {"value": ue / te / 1e9, "unit": "Gcell-iters/s",
+            "h2d_bytes_per_step": 3 * 8 * g.n, "d2h_bytes_per_step": 8 * g.n,
+            "ms_per_step": 1e3 * te / steps, "steps": steps}
+
+
+def fp64_baseline(F, s, g, steps, stream):
     """Plain FP64 GPU PCG (Jacobi) on the same workload: solves/s at the same tolerance."""
     import torch
     from paper_1410_1942_gb300 import capi
-    g = case.grid
-    F = torch.from_numpy(case.F).cuda()
-    s = torch.from_numpy(case.s).cuda()
-    p = torch.zeros(g.shape, dtype=torch.float64, device="cuda")
+    p = torch.zeros(g.shape, dtype=torch.float64, device=F.device)
     with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp64", stream=stream.cuda_stream) as sv:
         sv.set_density(F)
-        sv.solve(s, p, case.tol)  # warm-up
+        sv.solve(s, p, TOL)  # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         its, rel = 0, 0.0
         for _ in range(steps):
             sv.set_density(F)
             p.zero_()
-            rc, st = sv.solve(s, p, case.tol)
+            rc, st = sv.solve(s, p, TOL)
             its += st["inner_iters"]
             rel = max(rel, st["rel_residual"])
         torch.cuda.synchronize()
@@ -308,7 +483,7 @@ def batched(n=64, seed=0):
             p.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        tickets = capi.batch_submit(solvers, rhs, ps, 1e-9)
+        tickets = capi.batch_submit(solvers, rhs, ps, TOL)
         res, pending = {}, list(tickets)
         while pending:
             nxt = []
@@ -336,39 +511,41 @@ def batched(n=64, seed=0):
 def served(nreq, seed=0):
     """The request stream: capacity with every request waiting at t = 0 (6 steps each), then
     Poisson arrivals at 70 % of that capacity, 20 steps per request; FP32 inner solve, and the
-    plain FP64 PCG's and the multigrid-preconditioned solve's capacities for comparison."""
+    plain FP64 PCG's and the multigrid-preconditioned solve's capacities on the same stream."""
     import math as _m
     from paper_1410_1942_gb300 import inputs, serve
     # warm the device-side input generators (torch compiles its complex kernels on first use)
     inputs.mixed_fields_t((32, 32, 32), 1, device="cuda")
     budget = 48 << 30
-    cap = serve.Server(budget, steps=6).serve(serve.request_stream(max(4, nreq // 2), _m.inf, seed=seed + 1))
+    cap_stream = lambda: serve.request_stream(max(4, nreq // 2), _m.inf, seed=seed + 1)
+    cap = serve.Server(budget, steps=6).serve(cap_stream())
     rate = 0.7 * cap["solves_per_s"] / 20.0
     st = serve.Server(budget, steps=20).serve(serve.request_stream(nreq, rate, seed=seed))
-    cap64 = serve.Server(budget, precision="fp64", steps=3).serve(
-        serve.request_stream(max(4, nreq // 4), _m.inf, seed=seed + 2))
+    cap64 = serve.Server(budget, precision="fp64", steps=6).serve(cap_stream())
     # the same capacity stream with the multigrid preconditioner (unbatched handles)
-    capmg = serve.Server(budget, steps=6, precond="mg").serve(
-        serve.request_stream(max(4, nreq // 2), _m.inf, seed=seed + 1))
+    capmg = serve.Server(budget, steps=6, precond="mg").serve(cap_stream())
     return {"capacity_solves_per_s": cap["solves_per_s"], "arrival_rate_per_s": rate,
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "solves": st["solves"], "requests": nreq, "steps_per_request": 20,
             "max_rel_residual": st["max_rel_residual"], "all_ok": st["all_ok"],
             "peak_active": st["peak_active"],
+            "capacity_stream": "%d requests x 6 steps, all waiting at t = 0" % max(4, nreq // 2),
             "fp64_capacity_solves_per_s": cap64["solves_per_s"],
             "fp64_p50_ms": cap64["p50_ms"], "fp64_p99_ms": cap64["p99_ms"],
+            "fp64_all_ok": cap64["all_ok"],
+            "mixed_vs_fp64_capacity_ratio": cap["solves_per_s"] / cap64["solves_per_s"],
             "mg_capacity_solves_per_s": capmg["solves_per_s"],
             "mg_max_rel_residual": capmg["max_rel_residual"], "mg_all_ok": capmg["all_ok"]}
 
 
-def cpu_baseline(case, seconds, precond):
-    """The oracle as it stands on this host's cores: fixed 20-iteration PCG windows of the same
-    workload until `seconds` of CPU work have run."""
+def cpu_baseline(F, s, g, kind, seconds, precond):
+    """The oracle as it stands on this host's cores: fixed 20-iteration PCG windows from the zero
+    start on the same fields until `seconds` of CPU work have run."""
     import oracle
     oracle.build()
-    op = oracle.operator(case.F)
-    b = oracle.rhs(case.s, case.grid.h)
-    x = np.zeros(case.grid.shape)
+    op = oracle.operator(F)
+    b = oracle.rhs(s, g.h)
+    x = np.zeros(g.shape)
     if precond == "mg":
         from oracle import multigrid
         levels = multigrid.hierarchy(op)
@@ -382,15 +559,64 @@ def cpu_baseline(case, seconds, precond):
         if time.perf_counter() - t0 >= seconds:
             break
     dt = time.perf_counter() - t0
-    return {"value": case.grid.n * its / dt / 1e9, "unit": "Gcell-iters/s",
+    return {"value": g.n * its / dt / 1e9, "unit": "Gcell-iters/s",
             "cores": oracle.threads(), "kind": "oracle",
-            "sample": "%d FP64 %s-PCG iterations (windows of 20) of the CPU oracle on the %s "
-                      "workload, %.1f s" % (its, precond, CELLS_NOTE, dt)}
+            "sample": "%d FP64 %s-PCG iterations (windows of 20 from the zero start) of the CPU "
+                      "oracle on the %s %dx%dx%d workload, %.1f s" %
+                      (its, precond, kind, g.nx, g.ny, g.nz, dt)}
+
+
+def solver_line(sv, F, s, g, steps, warmup, stream, precision, precond, kind, flush):
+    """A secondary line (rank 0): Gcell-iters/s, solves/s and the roofline of one handle."""
+    import torch
+    p = torch.zeros(g.shape, dtype=torch.float64, device=F.device)
+    r = timed_solves(sv, F, s, p, TOL, steps, warmup, stream, torch.cuda.synchronize, flush=flush)
+    value = g.n * r["iters"] / (r["dev_ms"] * 1e-3) / 1e9
+    desc = sv.describe()
+    roof = roofline(r["prof"], desc, precision, precond, g, r["iters"], False, kind)
+    return {"value": value, "unit": "Gcell-iters/s", "precision": precision, "precond": precond,
+            "solves_per_s": steps / (r["dev_ms"] * 1e-3), "ms_per_solve": r["dev_ms"] / steps,
+            "cg_iters_per_solve": r["iters"] / steps, "outer_iters_per_solve": r["outer"] / steps,
+            "max_rel_residual": max(r["rels"]), "kernels": desc, "steps": steps,
+            "roofline_frac": roof["frac"], "roofline_kernel": roof["kernel"],
+            "alg_bytes_per_cell_iter": roof["alg_bytes_per_cell_iter"]}
+
+
+def extras_for(kind, args, F_d, s_d, g, stream, flush):
+    import torch
+    from paper_1410_1942_gb300 import capi
+    out = {}
+
+    def handle(gg, **kw):
+        return capi.Poisson(gg.nx, gg.ny, gg.nz, gg.h, stream=stream.cuda_stream, **kw)
+
+    few = max(1, min(args.steps, 2))
+    if kind == "wedge":
+        with handle(g, precision="bf16") as sv:
+            out["wedge_bf16"] = solver_line(sv, F_d, s_d, g, few, 1, stream, "bf16", "jacobi",
+                                            kind, flush)
+        with handle(g, precision="fp32", precond="mg", inner_tol=1e-5) as sv:
+            out["wedge_mg"] = solver_line(sv, F_d, s_d, g, few, 1, stream, "fp32", "mg", kind,
+                                          flush)
+        torch.cuda.empty_cache()
+        gs, Fs, ss, _ = make_fields("strut", SHAPES["strut"], args.seed, F_d.device)
+    else:
+        gs, Fs, ss = g, F_d, s_d
+    with handle(gs, precision="fp32") as sv:
+        line = solver_line(sv, Fs, ss, gs, max(1, min(args.steps, 10)), 3, stream, "fp32",
+                           "jacobi", "strut", flush)
+    fb = fp64_baseline(Fs, ss, gs, 2, stream)
+    line["fp64_baseline"] = fb
+    line["mixed_vs_fp64_solves_ratio"] = line["solves_per_s"] / fb["solves_per_s"]
+    line["batched"] = batched()
+    line["served"] = served(args.serve_requests)
+    out["strut"] = line
+    return out
 
 
 # ----------------------------------------------------------------------------- our arm
-def main():
-    args = parse()
+def main(argv=None):
+    args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
     import torch
@@ -408,23 +634,20 @@ def main():
     _build.build()
     capi.load()
 
-    if args.case == "wedge":
-        shape = (1024, 512, 256) if tuple(args.shape) == (256, 128, 128) else tuple(args.shape)
-        g, F_d, s_d, _ = inputs.wedge_fields_t(shape, seed=args.seed + rank, device=dev)
-        case = inputs.Case("wedge", g, None, None, 1e-9, {})
-        args.no_extras = True
-        args.no_cpu_baseline = True
-        args.no_e2e = True
-    else:
-        case = inputs.strut_case(*args.shape, seed=args.seed + rank)
-        g = case.grid
-        F_d = torch.from_numpy(case.F).to(dev)
-        s_d = torch.from_numpy(case.s).to(dev)
+    kind = args.case
+    g, F_d, s_d, meta = make_fields(kind, args.shape, args.seed + rank, dev)
     p_d = torch.zeros(g.shape, dtype=torch.float64, device=dev)
     stream = torch.cuda.current_stream(dev)
-    solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision, precond=args.precond,
-                          stream=stream.cuda_stream, tile=args.tile, dirichlet_walls=args.walls,
-                          periodic_x=args.periodic_x, inner_tol=args.inner_tol)
+    skw = dict(precision=args.precision, precond=args.precond, stream=stream.cuda_stream,
+               tile=args.tile, dirichlet_walls=args.walls, periodic_x=args.periodic_x,
+               inner_tol=args.inner_tol)
+    if args.cap_iters:
+        skw["max_iters"] = args.cap_iters
+
+    def make_solver():
+        return capi.Poisson(g.nx, g.ny, g.nz, g.h, **skw)
+
+    solver = make_solver()
     apertures = None
     if args.cut_body:
         Lx, Ly, _ = g.lengths
@@ -438,161 +661,70 @@ def main():
             tdist.barrier()
         torch.cuda.synchronize(dev)
 
-    def step():
-        solver.set_density(F_d)
-        p_d.zero_()
-        rc, st = solver.solve(s_d, p_d, case.tol)
-        if rc != capi.OK:
-            raise RuntimeError("solve failed: %s" % capi.strerror(rc))
-        return st
-
-    for _ in range(args.warmup):
-        step()
-    solver.profile(True)
+    allow = (capi.OK, capi.ENOTCONV) if args.cap_iters else (capi.OK,)
     clocks = Clocks(torch.cuda.current_device()) if rank == 0 else None
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    iters, outer, rels = 0, 0, []
-    barrier()
-    if clocks:
-        clocks.start()
-    l0 = capi.kernel_launches()
-    for q in range(args.steps):
-        flush.fill_(q & 0xFF)
-        evs[q][0].record(stream)
-        st = step()
-        evs[q][1].record(stream)
-        iters += st["inner_iters"]
-        outer += st["outer_iters"]
-        rels.append(st["rel_residual"])
-    barrier()
-    launches = capi.kernel_launches() - l0
-    clk = clocks.stop() if clocks else None
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    prof = solver.profile_read()
-    solver.profile(False)
-    units = float(g.n) * iters                     # cell-iterations of this rank
-    t_max, units = combine_ranks(dev_ms, units, dev, world)
+    r = timed_solves(solver, F_d, s_d, p_d, TOL, args.steps, args.warmup, stream, barrier,
+                     clocks=clocks, flush=flush, allow=allow)
+    units = float(g.n) * r["iters"]                     # cell-iterations of this rank
+    t_max, units = combine_ranks(r["dev_ms"], units, dev, world)
     value = units / (t_max * 1e-3) / 1e9
-
-    # dominant CG kernel and its roofline
-    bpc = BYTES_PER_CELL[args.precision]
-    cands = [k for k in ("pcg_persistent", "cg_phase_a", "cg_phase_b") if prof[k]["launches"]]
-    dom = max(cands, key=lambda k: prof[k]["ms"])
-    per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
     desc = solver.describe()
-    if "A p formed" in desc:
-        bpi = BYTES_PER_CELL_AP_FORMED[args.precision]
-    elif "one-sweep" in desc:
-        bpi = BYTES_PER_CELL_ONE_SWEEP[args.precision]
-    elif args.precond == "mg":
-        bpc = dict(bpc)
-        bpc["cg_phase_b"] = mg_phase_b_bytes(args.precision,
-                                             mg_levels(g.nx, g.ny, g.nz, args.periodic_x), g.n)
-        bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]
-    else:
-        bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]  # algorithmic bytes per cell-iteration
-    if dom == "pcg_persistent":
-        # one launch runs every CG iteration of one inner solve
-        alg_bytes = bpi * g.n * iters / prof[dom]["launches"]
-    else:
-        alg_bytes = bpc[dom] * g.n
-    achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
-    peak, peak_kind = peaks()
-    wl_key = "%s%dx%dx%d" % (args.case, g.nx, g.ny, g.nz)
-    bpci = ncu_traffic(dom, args.precision, wl_key)
-    # DRAM bytes per launch, like alg_bytes: the measured bytes per cell-iteration times the
-    # cell-iterations of an average launch
-    traffic = (bpci * g.n * iters / prof[dom]["launches"]
-               if bpci is not None and dom == "pcg_persistent" else None)
-    hbm_alg = value * bpi  # GB/s of CG-pass algorithmic traffic
+    roof = roofline(r["prof"], desc, args.precision, args.precond, g, r["iters"],
+                    args.periodic_x, kind)
+    solver.close()
+    del p_d
 
-    # end to end through the C ABI with pinned host arrays
     e2e = None
     if not args.no_e2e:
-        F_h = torch.from_numpy(case.F).pin_memory()
-        s_h = torch.from_numpy(case.s).pin_memory()
-        p_h = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
-        solver_h = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=args.precision,
-                                precond=args.precond, stream=stream.cuda_stream, tile=args.tile,
-                                dirichlet_walls=args.walls, periodic_x=args.periodic_x,
-                                inner_tol=args.inner_tol)
-        if apertures is not None:
-            solver_h.set_apertures(*apertures)
-
-        def step_e2e():
-            p_h.zero_()
-            solver_h.set_density(F_h)
-            rc, st = solver_h.solve(s_h, p_h, case.tol)
-            if rc != capi.OK:
-                raise RuntimeError("e2e solve failed: %s" % capi.strerror(rc))
-            return st
-
-        for _ in range(min(2, args.warmup)):
-            step_e2e()
-        barrier()
-        its_e, t0 = 0, time.perf_counter()
-        for _ in range(args.steps):
-            its_e += step_e2e()["inner_iters"]
-        barrier()
-        te = time.perf_counter() - t0
-        ue = float(g.n) * its_e
-        te, ue = combine_ranks(te, ue, dev, world)
-        e2e = {"value": ue / te / 1e9, "unit": "Gcell-iters/s",
-               "h2d_bytes_per_step": 3 * 8 * g.n, "d2h_bytes_per_step": 8 * g.n,
-               "ms_per_step": 1e3 * te / args.steps}
-        solver_h.close()
+        e2e = e2e_line(make_solver, F_d, s_d, g, TOL, min(args.steps, E2E_MAX_STEPS),
+                       min(1, args.warmup), dev, world, apertures)
 
     extras = {}
-    if rank == 0 and not args.no_extras and tuple(args.shape) == (256, 128, 128):
-        fb = fp64_baseline(case, 2, stream)
-        extras["fp64_baseline"] = fb
-        extras["mixed_vs_fp64_solves_ratio"] = (world * args.steps / (t_max * 1e-3)) / fb["solves_per_s"]
-        extras["batched"] = batched()
-        extras["served"] = served(args.serve_requests)
+    if rank == 0 and not args.no_extras and args.shape == SHAPES[kind] and not args.cap_iters:
+        extras = extras_for(kind, args, F_d, s_d, g, stream, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(case, args.cpu_seconds, {"rbssor": "ssor"}.get(args.precond, args.precond))
+        Fh, sh = F_d.cpu().numpy(), s_d.cpu().numpy()
+        del F_d, s_d
+        torch.cuda.empty_cache()
+        cpu = cpu_baseline(Fh, sh, g, kind, args.cpu_seconds,
+                           {"rbssor": "ssor"}.get(args.precond, args.precond))
 
     if rank == 0:
         line = {
-            "metric": "Poisson PCG Gcell-iters/s", "value": value, "unit": "Gcell-iters/s",
+            "metric": METRIC, "value": value, "unit": "Gcell-iters/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic",
-            "config": {"workload": ("wedge %dx%dx%d (hull half-plane pair, breaking patches)"
-                                    % (g.nx, g.ny, g.nz)) if args.case == "wedge" else
-                        (WORKLOAD if tuple(args.shape) == (256, 128, 128)
-                         else "strut %dx%dx%d (profiling case)" % tuple(args.shape)), "cells": g.n, "precision": args.precision,
-                       "precond": args.precond, "tol": case.tol, "inner_tol": args.inner_tol,
+            "config": {"workload": workload(kind, args.shape), "cells": g.n,
+                       "precision": args.precision, "precond": args.precond, "tol": TOL,
+                       "inner_tol": args.inner_tol,
                        "boundaries": ("strut as a free-slip cut-cell body, " if args.cut_body
                                       else "") + ("periodic x, " if args.periodic_x else "") +
                                      ("Dirichlet walls mask %d" % args.walls if args.walls
                                       else "zero-gradient side/bottom walls") + ", p = 0 on top",
-                       "l2": "flushed between steps (256 MiB write)",
+                       "l2": ("inputs larger than L2 (%.1f GB of FP64 fields); a 256 MiB buffer "
+                              "is also written between steps" % (3 * 8 * g.n / 1e9)),
                        "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "kernels": solver.describe(),
-                       "cg_iters_per_step": iters / args.steps,
-                       "outer_iters_per_step": outer / args.steps,
-                       "max_rel_residual": max(rels)},
-            "hbm_gbs_algorithmic": hbm_alg,
+                       "kernels": desc,
+                       "cg_iters_per_step": r["iters"] / args.steps,
+                       "outer_iters_per_step": r["outer"] / args.steps,
+                       "max_rel_residual": max(r["rels"]),
+                       "cap_iters": args.cap_iters or None,
+                       "fields": {k: v for k, v in meta.items() if k != "modes"}},
+            "hbm_gbs_algorithmic": value * roof["alg_bytes_per_cell_iter"],
             "solves_per_s": world * args.steps / (t_max * 1e-3),
-            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": traffic, "alg_bytes_per_launch": alg_bytes,
-                         "alg_bytes_per_cell_iter": bpi,
-                         "ms_per_launch": per_launch_ms},
-            "kernel_times": prof,
+            "roofline": roof,
+            "kernel_times": r["prof"],
             **extras,
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": launches,
-            "clocks": clk,
+            "gpu_launches": r["launches"],
+            "clocks": r["clocks"],
         }
         print(json.dumps(line), flush=True)
-    solver.close()
     if world > 1:
         tdist.destroy_process_group()
     return 0

@@ -264,12 +264,17 @@ int poisson_project(poisson_t* h, double* u, double* v, double* w, const double*
  * device memory when they check a pressure field: a step loop that must not pay cudaMalloc's
  * latency or cudaFree's implicit device synchronisation, a process whose device memory belongs
  * to another allocator under a fixed budget, or code that forbids dynamic allocation after
- * initialisation.  It computes the FP64 relative residual ||b - A p||_2 / ||b||_2 (b = -h^2 rhs,
- * A the FP64 operator of eq. (pois) built on the fly from F, rho_air, rho_water as in
- * poisson_set_density, with the paper's walls: zero normal gradient on the sides and bottom) -- the figure poisson_solve reports in stats->rel_residual -- without any
- * handle and without allocating: its only scratch is a 64 KiB static device array of the
- * library, which every GPU that loads the library holds until the process exits.
+ * initialisation.  Without any handle and without allocating, it computes the FP64 relative
+ * residual ||b - A p||_2 / ||b||_2 with b = -h^2 rhs and A the operator of the paper's
+ * configuration built on the fly from F: rho = rho_air + F (rho_water - rho_air), interior face
+ * coefficients 2/(rho_c + rho_n), zero normal gradient on the side and bottom walls, and p = 0
+ * on the top face, which adds 2/rho_c to the diagonal.  For a handle created with
+ * dirichlet_walls = 0, periodic_x = 0 and no cut-cell geometry this is the figure poisson_solve
+ * reports in stats->rel_residual; for other handles the two figures differ.  Its only scratch is
+ * a 64 KiB static device array of the library, which every GPU that loads the library holds
+ * until the process exits.
  *   F, rhs, p: device arrays of nx*ny*nz doubles (x fastest); host arrays give EINVAL.
+ *   rho_air, rho_water: finite and > 0, else EINVAL.
  *   rel_residual: one double, host or device memory (a device output is written on the stream
  *     without waiting; a host output waits for the stream).  0 for an all-zero rhs.
  *   stream: cudaStream_t to run on (NULL = legacy default stream).
@@ -281,6 +286,18 @@ int poisson_project(poisson_t* h, double* u, double* v, double* w, const double*
 int poisson_residual_noalloc(int nx, int ny, int nz, double h, const double* F, double rho_air,
                              double rho_water, const double* rhs, const double* p,
                              double* rel_residual, void* stream);
+
+/* ------------------------------------------------------------------ failure-path test aid
+ * A testing aid with no counterpart in the paper.  extra > 0 makes the grid barriers of the
+ * handle's persistent FP32 PCG launches wait for `extra` more CTAs than are launched, so the
+ * first barrier of the next solve can never complete: every CTA gives up when the barrier's
+ * deadline (1 s of the GPU's global timer) runs out, lets its TMA copies in flight land and
+ * leaves, and poisson_solve returns POISSON_ETIMEOUT with p holding the iterate reached.  The
+ * CUDA context stays usable; extra = 0 restores normal launches.  It exists so that tests can
+ * exercise the bounded-wait failure path without faulting or hanging the GPU.
+ * Errors: EINVAL (NULL, extra < 0 or > 1024, or a handle whose inner solve does not use a
+ * persistent launch: POISSON_FP64, RBSSOR, MG, cut cells, nx % 8 != 0, tile = -1). */
+int poisson_test_unreachable_barrier(poisson_t* h, int extra);
 
 /* Write a one-line description of the handle's kernel choice (family, tile, z-chunk) into buf
  * (NUL-terminated, at most len bytes). */

@@ -232,59 +232,6 @@ def pcg(op: Operator, b, x0=None, tol=1e-12, precond="jacobi", omega=1.0, max_it
     return PCGResult(x, it.value, rr.value, st, hist[:it.value] if history else None)
 
 
-def pcg_single_reduction(op: Operator, b, tol=1e-12, max_iters=100000):
-    """Jacobi-preconditioned CG in the Chronopoulos-Gear form: both inner products of an
-    iteration are taken together, after the vector updates, so one reduction per iteration
-    suffices.  In exact arithmetic its iterates are those of ``pcg(..., precond="jacobi")`` (the
-    Introduction's preconditioned conjugate-gradient solve); this is the form the GPU library's
-    one-sweep kernels follow, written in their variables (M = D):
-
-        u = M^-1 r,  s^ = M^-1 A p,  w^ = M^-1 A u
-        p = u + beta p;  s^ = w^ + beta s^;  x += alpha p;  u = u - alpha s^;  w^ = M^-1 A u
-        gamma = (D u, u);  delta = (A u, u);  |r|^2 = |D u|^2
-        beta = gamma / gamma_old;  alpha = gamma / (delta - beta gamma / alpha_old)
-
-    Plain numpy, FP64, zero start; stops when ``|r| <= tol |r_0|`` (``tol <= 0``: exactly
-    ``max_iters`` iterations)."""
-    b = _f64(b).reshape(op.shape)
-    D = op.diag
-    x = np.zeros_like(b)
-    u = b / D
-    Au = apply(op, u)
-    w = Au / D
-    gamma = float(np.sum(D * u * u))
-    delta = float(np.sum(Au * u))
-    rr0 = float(np.sum((D * u) ** 2))
-    stop2 = (tol * tol) * rr0 if tol > 0 else -1.0
-    if rr0 <= stop2 or rr0 == 0.0:
-        return PCGResult(x, 0, 0.0 if rr0 == 0.0 else 1.0, OK)
-    p = np.zeros_like(b)
-    s = np.zeros_like(b)
-    alpha, beta = gamma / delta, 0.0
-    it, rr = 0, rr0
-    while it < max_iters:
-        p = u + beta * p
-        s = w + beta * s
-        x = x + alpha * p
-        u = u - alpha * s
-        Au = apply(op, u)
-        w = Au / D
-        g_new = float(np.sum(D * u * u))
-        delta = float(np.sum(Au * u))
-        rr = float(np.sum((D * u) ** 2))
-        it += 1
-        if rr <= stop2:
-            break
-        beta = g_new / gamma
-        den = delta - beta * g_new / alpha
-        if not den > 0.0:
-            return PCGResult(x, it, float(np.sqrt(rr / rr0)), EBREAKDOWN)
-        alpha = g_new / den
-        gamma = g_new
-    st = OK if (tol <= 0 or rr <= stop2) else ENOTCONV
-    return PCGResult(x, it, float(np.sqrt(rr / rr0)), st)
-
-
 def _faces_shapes(nx, ny, nz):
     return (nz, ny, nx + 1), (nz, ny + 1, nx), (nz + 1, ny, nx)
 

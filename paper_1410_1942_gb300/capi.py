@@ -32,7 +32,7 @@ EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson
            "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
            "poisson_profile_read", "poisson_describe", "poisson_residual_noalloc",
            "poisson_divergence", "poisson_project", "poisson_set_apertures", "poisson_strerror",
-           "poisson_version"]
+           "poisson_version", "poisson_test_unreachable_barrier"]
 K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER, K_PCG = 0, 1, 2, 3, 4
 K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 
@@ -112,6 +112,8 @@ def load(path=None):
     lib.poisson_project.restype = i
     lib.poisson_set_apertures.argtypes = [vp, vp, vp, vp, vp, i]
     lib.poisson_set_apertures.restype = i
+    lib.poisson_test_unreachable_barrier.argtypes = [vp, i]
+    lib.poisson_test_unreachable_barrier.restype = i
     for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read", "poisson_describe"]:
         getattr(lib, name).restype = i
     _lib = lib
@@ -221,6 +223,12 @@ class Poisson:
         t = KernelTimes()
         _check(load().poisson_profile_read(self._h, ctypes.byref(t)), "poisson_profile_read")
         return t.as_dict()
+
+    def test_unreachable_barrier(self, extra):
+        """Testing aid: the next persistent launches wait at their grid barriers for ``extra``
+        CTAs more than they launch (0 restores), so a solve ends with ETIMEOUT."""
+        _check(load().poisson_test_unreachable_barrier(self._h, int(extra)),
+               "poisson_test_unreachable_barrier")
 
     def describe(self):
         buf = ctypes.create_string_buffer(256)

@@ -698,6 +698,13 @@ static int solve_mixed(poisson_t* H, const C32& c32, bool bf16, double tol, int*
     return status;
 }
 
+extern "C" int poisson_test_unreachable_barrier(poisson_t* H, int extra) {
+    if (!H || extra < 0 || extra > 1024) return POISSON_EINVAL;
+    if (!H->march || H->cut() || H->opts.precond != POISSON_JACOBI) return POISSON_EINVAL;
+    H->plan.barrier_extra = extra;
+    return POISSON_OK;
+}
+
 extern "C" int poisson_solve(poisson_t* H, const double* rhs, double* p, double tol,
                              poisson_stats* stats) {
     if (!H || !rhs || !p || !(tol > 0.0)) return POISSON_EINVAL;

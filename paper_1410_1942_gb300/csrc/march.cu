@@ -1281,7 +1281,8 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
 int launch_march_pcg(const MarchPlan& p, cudaStream_t st) {
     int n;
     const VariantOps& v = variants(&n)[p.variant];
-    PcgArgs args{p.solves, p.segs, p.cta_seg, p.maps, p.part_a, p.part_b, p.ctl, p.nctas, p.trace};
+    PcgArgs args{p.solves, p.segs, p.cta_seg, p.maps, p.part_a,         p.part_b,
+                 p.ctl,    p.nctas + p.barrier_extra,          p.trace};
     void* params[] = {&args};
     const void* k = p.periodic ? (p.bf16 ? v.k16p : v.k32p) : (p.bf16 ? v.k16 : v.k32);
     if (!k) return -1;

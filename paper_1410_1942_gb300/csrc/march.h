@@ -97,6 +97,9 @@ struct MarchPlan {
     float2* part_b = nullptr;  // per segment: r.z, r.r (family 1: gamma, delta, r.r)
     MarchCtl* ctl = nullptr;
     unsigned long long* trace = nullptr;  // TRACE_PARTS counters when tracing is on
+    // testing aid (poisson_test_unreachable_barrier): the grid barriers wait for this many CTAs
+    // beyond the nctas launched, so the first one can only end by its deadline
+    int barrier_extra = 0;
     // allocated bytes of the buffers above (a rebuild reuses them when they suffice)
     size_t cap_solves = 0, cap_segs = 0, cap_cta = 0, cap_maps = 0, cap_pa = 0, cap_pb = 0,
            cap_ctl = 0;

@@ -115,7 +115,8 @@ extern "C" int poisson_residual_noalloc(int nx, int ny, int nz, double h, const 
                                         double rho_air, double rho_water, const double* rhs,
                                         const double* p, double* rel_residual, void* stream) {
     if (nx <= 0 || ny <= 0 || nz <= 0 || !(h > 0.0) || !std::isfinite(h) || !(rho_air > 0.0) ||
-        !(rho_water > 0.0) || !F || !rhs || !p || !rel_residual)
+        !(rho_water > 0.0) || !std::isfinite(rho_air) || !std::isfinite(rho_water) || !F ||
+        !rhs || !p || !rel_residual)
         return POISSON_EINVAL;
     const long long n = (long long)nx * ny * nz;
     if (n >= (1LL << 31)) return POISSON_EINVAL;

@@ -454,7 +454,8 @@ def mixed_fields_t(shape, seed, device="cpu"):
 
 def wedge_fields_t(shape=(1024, 512, 256), seed=0, device="cpu"):
     """The wedge workload of :func:`wedge_case` computed with torch on ``device``: same hull,
-    surface and source; the breaking patches are drawn with a seeded torch generator (so they
+    surface and source; the breaking patches come from their own numpy generator (seed + 12345,
+    one float32 pair per cell, z-chunk by z-chunk), so every device gets the same patches (they
     differ from the numpy version's).  Returns (grid, F, s, meta)."""
     torch = _torch()
     nx, ny, nz = shape
@@ -476,14 +477,14 @@ def wedge_fields_t(shape=(1024, 512, 256), seed=0, device="cpu"):
     z = (torch.arange(nz, dtype=f64, device=device) + 0.5) * h
     surf = 0.5 * grid.lengths[2] + eta(x[None, :], y[:, None])
     body = smoothed_step_t(-psi(x[None, :], y[:, None]), 1.5 * h)
-    gen = torch.Generator(device=device)
-    gen.manual_seed(int(seed) + 12345)
+    gen = np.random.default_rng(int(seed) + 12345)
     for k0 in range(0, nz, 32):
         k1 = min(nz, k0 + 32)
         d = surf[None, :, :] - z[k0:k1, None, None]
         near = torch.abs(d) <= 2.0 * h
-        flip = near & (torch.rand(d.shape, generator=gen, device=device) < 0.05)
-        vals = (torch.rand(d.shape, generator=gen, device=device) < 0.5).to(f64)
+        u = torch.from_numpy(gen.random((2,) + tuple(d.shape), dtype=np.float32)).to(device)
+        flip = near & (u[0] < 0.05)
+        vals = (u[1] < 0.5).to(f64)
         F[k0:k1] = torch.maximum(torch.where(flip, vals, F[k0:k1]), body[None, :, :])
     modes = fourier_modes(rng)
     s = divergence_source_t(grid, modes, device=device)

@@ -81,7 +81,7 @@ def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
 
 class Server:
     def __init__(self, budget_bytes, precision="fp32", tol=1e-9, steps=20, device="cuda",
-                 keep_results=False, tile=12204, precond="jacobi"):
+                 keep_results=False, tile=12204, precond="jacobi", record_steps=False):
         # tile: kernel variant of every request's handle (fixed, so admission does not run the
         # autotuner; the batch executor uses the variant of its largest solve).  precond "mg":
         # the V-cycle preconditioner; such handles are not batched, the executor solves them one
@@ -95,6 +95,10 @@ class Server:
         self.device = device
         self.keep = keep_results
         self.results = {}
+        # record_steps: host copies of every step's inputs and result, for checking served solves
+        # one by one (rid -> {"grid", "F", "steps": [(s, p, status)]}); costs a device-to-host
+        # copy per step inside the loop, so it is for tests, not for timing
+        self.record = {} if record_steps else None
 
     def _admit(self, r, now):
         g, F, s, modes = inputs.mixed_fields_t(r.shape, r.seed, device=self.device)
@@ -106,6 +110,8 @@ class Server:
                                 precond=self.precond)
         r.solver.set_density(F)
         r.admitted_at = now
+        if self.record is not None:
+            self.record[r.rid] = {"grid": g, "F": F.cpu().numpy(), "steps": []}
         self._submit(r, r.arrival)
 
     def _submit(self, r, t_from):
@@ -152,6 +158,8 @@ class Server:
                 r.residuals.append(st["rel_residual"] if st else float("nan"))
                 r.iters.append(st["inner_iters"] if st else 0)
                 lat.append(t - r.t_submit)
+                if self.record is not None:
+                    self.record[r.rid]["steps"].append((r.s.cpu().numpy(), r.p.cpu().numpy(), rc))
                 r.step += 1
                 if r.step < self.steps and rc == capi.OK:
                     self._advance(r)

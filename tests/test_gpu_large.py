@@ -1,6 +1,13 @@
-"""The large wedge workload (1024 x 512 x 256 = 134M cells) at full size: every precision mode
-reaches the tolerance under the oracle's FP64 operator, and the FP32- and BF16-coefficient
-inner solves agree with each other."""
+"""The wedge workload (hull half-plane pair, breaking-like patches, density ratio 1000).
+
+At half resolution (512 x 256 x 128, 16.8M cells) every precision mode -- plain FP64 PCG, FP32
+inner PCG and BF16-coefficient inner PCG, both inside FP64 refinement -- is checked against the
+oracle on both acceptance criteria: relative residual <= 1e-9 under the oracle's FP64 operator,
+and relative L2 distance <= 1e-6 from the oracle's 1e-12 solution.  At full size (1024 x 512 x
+256 = 134M cells, the benchmark's workload) the oracle's 1e-12 solve is too slow for a test, so
+every precision mode is checked on criterion (i) with the oracle's operator, and the three
+solutions against each other on criterion (ii)'s tolerance.
+"""
 import numpy as np
 import pytest
 
@@ -9,28 +16,62 @@ from paper_1410_1942_gb300 import build, capi, inputs
 
 pytestmark = pytest.mark.gpu
 
+TOL = 1e-9
+L2_TOL = 1e-6
 
-def test_wedge_full_size_solves():
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
     import torch
     assert torch.cuda.is_available()
     build.build()
     capi.load()
+
+
+@pytest.fixture(scope="module")
+def wedge_half():
+    grid, F, s, _ = inputs.wedge_fields_t((512, 256, 128), seed=0, device="cuda")
+    Fh, sh = F.cpu().numpy(), s.cpu().numpy()
+    op = oracle.operator(Fh)
+    b = oracle.rhs(sh, grid.h)
+    ref = oracle.pcg(op, b, tol=1e-12, precond="ssor")
+    assert ref.status == oracle.OK
+    return grid, Fh, sh, op, b, ref.x
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_wedge_half_size_meets_both_criteria(wedge_half, prec):
+    grid, F, s, op, b, xref = wedge_half
+    p = np.zeros(grid.shape)
+    with capi.Poisson(grid.nx, grid.ny, grid.nz, grid.h, precision=prec) as sv:
+        sv.set_density(F)
+        rc, st = sv.solve(s, p, TOL)
+    assert rc == capi.OK, prec
+    rel = oracle.rel_residual(op, b, p)
+    assert rel <= TOL * (1 + 1e-6), (prec, rel)
+    err = np.linalg.norm(p - xref) / np.linalg.norm(xref)
+    assert err <= L2_TOL, (prec, err)
+
+
+def test_wedge_full_size_solves():
+    import torch
     grid, F, s, _ = inputs.wedge_fields_t((1024, 512, 256), seed=0, device="cuda")
     op = oracle.operator(F.cpu().numpy())
     b = oracle.rhs(s.cpu().numpy(), grid.h)
     sols = {}
-    for prec in ("fp32", "bf16"):
+    for prec in ("fp32", "bf16", "fp64"):
         p = torch.zeros(grid.shape, dtype=torch.float64, device="cuda")
         with capi.Poisson(grid.nx, grid.ny, grid.nz, grid.h, precision=prec) as sv:
             sv.set_density(F)
-            rc, st = sv.solve(s, p, 1e-9)
+            rc, st = sv.solve(s, p, TOL)
         assert rc == capi.OK, prec
         x = p.cpu().numpy()
         rel = oracle.rel_residual(op, b, x)
-        assert rel <= 1e-9 * (1 + 1e-6), (prec, rel)
+        assert rel <= TOL * (1 + 1e-6), (prec, rel)
         assert abs(st["rel_residual"] - rel) <= 1e-3 * rel
         sols[prec] = x
         del p
         torch.cuda.empty_cache()
-    d = np.linalg.norm(sols["fp32"] - sols["bf16"]) / np.linalg.norm(sols["fp32"])
-    assert d <= 1e-6, d
+    for a, c in (("fp32", "bf16"), ("fp32", "fp64")):
+        d = np.linalg.norm(sols[a] - sols[c]) / np.linalg.norm(sols[c])
+        assert d <= L2_TOL, (a, c, d)

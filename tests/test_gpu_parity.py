@@ -289,6 +289,26 @@ def test_batch_of_uneven_solves_matches_oracle(tile):
         s.close()
 
 
+def test_batch_of_64_uneven_solves_matches_oracle():
+    """The batched workload at its full specification: 64 solves of sizes drawn between 32^3
+    and 128 x 64 x 64 (aspect <= 4), each with its own surface, strut and source, submitted
+    together (one persistent launch per refinement step over every unfinished solve); every
+    result meets both acceptance criteria against the oracle."""
+    cases = inputs.batch_cases(64, seed=0)
+    assert max(c.grid.n for c in cases) <= 128 * 64 * 64
+    solvers = [solver(c) for c in cases]
+    ps = [np.zeros(c.grid.shape) for c in cases]
+    tickets = capi.batch_submit(solvers, [c.s for c in cases], ps, 1e-9)
+    res = _poll_all(tickets)
+    for t, c, p in zip(tickets, cases, ps):
+        rc, st = res[t]
+        assert rc == capi.OK
+        op, b, xref = _oracle_ref(c)
+        _check_solution(c, op, b, xref, p, st, 1e-9)
+    for s in solvers:
+        s.close()
+
+
 def test_solve_alone_and_in_the_mix_agree():
     """The same solve run alone and inside a batch of others gives the same pressure within the
     acceptance tolerance (both meet it against the oracle)."""
@@ -382,15 +402,17 @@ def test_one_sweep_kernel_takes_the_iterations_of_standard_pcg(prec):
 @pytest.mark.parametrize("k", [7, 8])
 def test_capped_solve_returns_the_k_th_iterate(tile, k):
     """With the iteration cap at k, the FP32 inner solve stops after k CG iterations and p holds
-    the k-th iterate: the FP64 oracle's k-th iterate to FP32 accuracy.  An odd k ends the
-    one-sweep kernel on an iteration that leaves x to a closing pass (x is stored every other
-    iteration), an even k on one that stores it."""
+    the k-th iterate: the k-th iterate of the oracle's textbook Jacobi PCG (FP64) to FP32
+    accuracy, whichever arrangement of CG the kernel runs (the two-sweep kernels take the
+    textbook form; the one-sweep kernels the Chronopoulos-Gear recurrences, the same iterates in
+    exact arithmetic).  An odd k ends the one-sweep kernel on an iteration that leaves x to a
+    closing pass (x is stored every other iteration), an even k on one that stores it."""
     c, op, b, _ = case("strut")
     with solver(c, "fp32", tile=tile, max_iters=k) as s:
         p = np.zeros(c.grid.shape)
         rc, st = s.solve(c.s, p, 1e-9, allow=(capi.OK, capi.ENOTCONV))
     assert rc == capi.ENOTCONV and st["inner_iters"] == k
-    ref = oracle.pcg_single_reduction(op, b, tol=0.0, max_iters=k).x
+    ref = oracle.pcg(op, b, tol=0.0, precond="jacobi", max_iters=k).x
     assert np.linalg.norm(p - ref) <= 1e-4 * np.linalg.norm(ref)
 
 

@@ -303,35 +303,6 @@ def test_pcg_iterations_bounded_by_dimension_and_recurrence_tracks_truth():
     assert abs(res.history[-1] - res.rel_residual) <= 1e-12
 
 
-@pytest.mark.parametrize("shape,sharp", [((4, 4, 4), False), ((5, 5, 5), True), ((3, 5, 4), True)])
-def test_single_reduction_cg_matches_dense_lu(shape, sharp):
-    F = _rand_F(shape, 13, sharp)
-    op = oracle.operator(F, RHO_A, RHO_W)
-    b = np.random.default_rng(14).standard_normal(shape)
-    ref = scipy.linalg.solve(_dense(op), b.ravel(), assume_a="sym").reshape(shape)
-    res = oracle.pcg_single_reduction(op, b, tol=1e-13)
-    assert res.status == oracle.OK
-    assert np.linalg.norm(res.x - ref) / np.linalg.norm(ref) <= 1e-10
-
-
-def test_single_reduction_cg_has_the_iterates_of_jacobi_pcg():
-    """Chronopoulos-Gear is a rearrangement of CG: the same x_k at every k (to rounding), so the
-    energy-norm error also decreases monotonically."""
-    shape = (6, 5, 7)
-    op = oracle.operator(_rand_F(shape, 63), RHO_A, RHO_W)
-    A = _dense(op)
-    b = np.random.default_rng(64).standard_normal(shape)
-    xs = scipy.linalg.solve(A, b.ravel(), assume_a="sym")
-    errs = []
-    for it in range(1, 25):
-        a1 = oracle.pcg_single_reduction(op, b, tol=0.0, max_iters=it).x
-        a2 = oracle.pcg(op, b, tol=0.0, precond="jacobi", max_iters=it).x
-        assert np.linalg.norm(a1 - a2) <= 1e-9 * np.linalg.norm(a2), it
-        e = a1.ravel() - xs
-        errs.append(float(e @ A @ e))
-    assert np.all(np.diff(errs) <= 1e-12 * errs[0])
-
-
 def test_zero_source_gives_zero_solution():
     op = oracle.operator(_rand_F((4, 5, 6), 81), RHO_A, RHO_W)
     res = oracle.pcg(op, np.zeros((4, 5, 6)), x0=np.ones((4, 5, 6)), tol=1e-10)
