@@ -91,6 +91,8 @@ def _load():
         lib.oracle_project.restype = None
         lib.oracle_project_bc.argtypes = [i, i, i, d, d, P, d, d, i, P, P, P, P, P, P, P]
         lib.oracle_project_bc.restype = None
+        lib.oracle_hydrostatic_force.argtypes = [i, i, i, d, P, d, d, d, d, i, d, P, P, P]
+        lib.oracle_hydrostatic_force.restype = None
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = i
         lib.oracle_set_threads.argtypes = [i]
@@ -275,6 +277,23 @@ def project(op: Operator, F, u, v, w, p, h, dt, rho_air=1.0, rho_water=1000.0):
                                    float(rho_air), float(rho_water), op.walls,
                                    *(_ptr(a) for a in op.apertures), _ptr(op.bx), _ptr(op.by),
                                    _ptr(op.bz), _ptr(p), _ptr(u), _ptr(v), _ptr(w))
+    return u, v, w
+
+
+def hydrostatic_force(F, u, v, w, h, g, z_o, dt=1.0, rho_air=1.0, rho_water=1000.0, walls=0):
+    """The face velocities plus ``dt`` times the force of the reduced-pressure formulation (new
+    arrays; Entrance and Exit Boundary Conditions, hydrostatic-pressure method).  The solve is
+    then for ``P_r = P - rho g (z - z_o)``; the force on the face between cells c and n (n on the
+    +axis side) is ``-(z_f - z_o) g beta_f (rho_n - rho_c) / h`` with the operator's face
+    coefficient ``beta_f = 2/(rho_c + rho_n)`` and ``z_f`` the face's height; boundary faces get
+    none; ``walls`` matters only through ``PERIODIC_X`` (the wrap face)."""
+    F = _f64(F)
+    nz, ny, nx = F.shape
+    u, v, w = _f64(u).copy(), _f64(v).copy(), _f64(w).copy()
+    assert (u.shape, v.shape, w.shape) == _faces_shapes(nx, ny, nz)
+    _load().oracle_hydrostatic_force(nx, ny, nz, float(h), _ptr(F), float(rho_air),
+                                     float(rho_water), float(g), float(z_o), int(walls), float(dt),
+                                     _ptr(u), _ptr(v), _ptr(w))
     return u, v, w
 
 

@@ -492,3 +492,62 @@ void oracle_project(int nx, int ny, int nz, double h, double dt, const double* F
                     const double* p, double* u, double* v, double* w) {
     oracle_project_bc(nx, ny, nz, h, dt, F, rho_air, rho_water, 0, bx, by, bz, p, u, v, w);
 }
+
+/* ---------------------------------------------------------------------------- reduced pressure
+ * Hydrostatic-pressure method (Entrance and Exit Boundary Conditions).  The solve is for the
+ * reduced pressure P_r = P - rho g (z - z_o), z_o the static free-surface height.  The momentum
+ * equations then carry the force -(z - z_o) (1/rho) d(rho g)/dx_i, which in the paper's units
+ * (rho = lambda + (1 - lambda) H) is -(z - z_o)(1 - lambda) g (1/rho) dH/dx_i and which makes P_r
+ * jump by (z - z_o)(1 - lambda) g across the interface.  The force is one of the terms R_i of the
+ * provisional velocity, so its divergence joins the source of the pressure equation and the
+ * projection removes its gradient part.
+ *
+ * Reading on the MAC faces (the paper leaves the discretisation to a cited scheme): for the face
+ * between cells c and n, n on the +axis side,
+ *     f = -(z_f - z_o) g beta_f (rho_n - rho_c) / h,     beta_f = 2 / (rho_c + rho_n),
+ * with rho from F as for the operator and z_f the face's height: (k + 1/2) h on the x and y faces
+ * of layer k, k h on the z face below layer k.  beta_f is the operator's face coefficient, so on
+ * every interior face f = -beta_f (Psi_n - Psi_c)/h + g [z face], Psi_c = rho_c g (z_c - z_o):
+ * the reduced form of the face-centred gravity g e_z and the total pressure P = P_r + Psi.
+ * Every boundary face (walls of either kind, the top) gets no force: H is continued beyond the
+ * boundary without change along its normal.  With periodic x the wrap face (cells nx-1 and 0)
+ * carries its force on faces 0 and nx.  The call adds dt f to the face velocities u, v, w (shapes
+ * as in oracle_divergence): u_f <- u_f + dt f.  g is the coefficient as the paper writes it. */
+static double reduced_force(double rc, double rn, double zf, double z_o, double g, double h) {
+    const double a = (zf - z_o) * g;
+    const double b = (2.0 / (rc + rn)) * (rn - rc);
+    return -(a * b) / h;
+}
+
+void oracle_hydrostatic_force(int nx, int ny, int nz, double h, const double* F, double rho_air,
+                              double rho_water, double g, double z_o, int walls, double dt,
+                              double* u, double* v, double* w) {
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const idx_t c = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)ny * k);
+                const idx_t sxy = (idx_t)nx * ny;
+                const idx_t fu = (idx_t)i + (idx_t)(nx + 1) * ((idx_t)j + (idx_t)ny * k);
+                const idx_t fv = (idx_t)i + (idx_t)nx * ((idx_t)j + (idx_t)(ny + 1) * k);
+                const double rc = rho_air + F[c] * (rho_water - rho_air);
+                const double zc = ((double)k + 0.5) * h; /* height of the layer's x, y faces */
+                if (i > 0) {
+                    const double rn = rho_air + F[c - 1] * (rho_water - rho_air);
+                    /* face between c - 1 (low side) and c (high side) */
+                    u[fu] = u[fu] + dt * reduced_force(rn, rc, zc, z_o, g, h);
+                } else if (walls & OR_PERIODIC_X) {
+                    const double rn = rho_air + F[c + nx - 1] * (rho_water - rho_air);
+                    u[fu] = u[fu] + dt * reduced_force(rn, rc, zc, z_o, g, h);
+                    u[fu + nx] = u[fu];
+                }
+                if (j > 0) {
+                    const double rn = rho_air + F[c - nx] * (rho_water - rho_air);
+                    v[fv] = v[fv] + dt * reduced_force(rn, rc, zc, z_o, g, h);
+                }
+                if (k > 0) {
+                    const double rn = rho_air + F[c - sxy] * (rho_water - rho_air);
+                    w[c] = w[c] + dt * reduced_force(rn, rc, (double)k * h, z_o, g, h);
+                }
+            }
+}
