@@ -160,10 +160,10 @@ def peaks():
     return 6800.0, "fallback"
 
 
-# Sources that define each persistent kernel family (device code and the host code that plans
-# its launches): a committed ncu figure counts only while these files are unchanged.
+# Device sources of each persistent kernel family: a committed ncu figure counts only while
+# these files are unchanged and the line runs the tile (variant and split) it was taken on.
 KERNEL_SOURCES = {
-    "one-sweep": ["march1.cu", "march_dev.cuh", "tma.cuh", "internal.cuh", "march.h", "march.cu"],
+    "one-sweep": ["march1.cu", "march_dev.cuh", "tma.cuh", "internal.cuh", "march.h"],
 }
 
 
@@ -176,9 +176,10 @@ def source_hash(family="one-sweep"):
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(family, precision, kind):
+def ncu_traffic(family, precision, kind, desc):
     """DRAM bytes per cell-iteration of the persistent kernel `family` on workload `kind`, from
-    the committed ncu summary if it was taken on the kernel's current sources; else None."""
+    the committed ncu summary if it was taken on the kernel's current sources and on the tile the
+    handle runs (`desc`: its description); else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if family not in KERNEL_SOURCES or not os.path.exists(path):
         return None
@@ -186,6 +187,8 @@ def ncu_traffic(family, precision, kind):
         d = json.load(f)
     e = d.get("%s/%s/%s" % (precision, family, kind))
     if not e or e.get("source_hash") != source_hash(family):
+        return None
+    if "tile=%d " % e.get("tile", -1) not in desc:
         return None
     return e.get("dram_bytes_per_cell_iter")
 
@@ -388,7 +391,7 @@ def roofline(prof, desc, precision, precond, g, iters, periodic, kind):
         alg_bytes = bpc[dom] * g.n
     achieved = alg_bytes / (per_launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    bpci = ncu_traffic(family, precision, kind) if family and dom == "pcg_persistent" else None
+    bpci = ncu_traffic(family, precision, kind, desc) if family and dom == "pcg_persistent" else None
     out = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
            # DRAM bytes per launch, like alg_bytes: the measured bytes per cell-iteration times
