@@ -72,11 +72,15 @@ BYTES_PER_CELL_ONE_SWEEP = {"fp32": 16 + 4 + 16 + 4, "bf16": 16 + 2 + 16 + 4}
 # one-sweep kernels that form A p in the sweep: read u, p (8 B) + eta, write u, p (8 B), x every
 # other iteration (4 B on average)
 BYTES_PER_CELL_AP_FORMED = {"fp32": 8 + 4 + 8 + 4, "bf16": 8 + 2 + 8 + 4}
-# The face-array schedule that the stencil's byte model counts per cell-iteration (Jacobi, FP32
-# vectors): three stored face arrays and 1/D read, q = A p stored and re-read -- 14 words = 56 B.
-# The kernels here store rho/2 instead of faces and never store q, so they move less; the line
+# red-black SSOR kernels (CG on the black Schur complement): per black cell read u, s^, w^, p,
+# x and write them (40 B), per cell eta -- per cell of the grid 20 B of vectors + eta
+BYTES_PER_CELL_RB = {"fp32": 20 + 4, "bf16": 20 + 2}
+# The face-array schedule that the stencil's byte model counts per cell-iteration (FP32 vectors):
+# Jacobi, three stored face arrays and 1/D read, q = A p stored and re-read -- 14 words = 56 B;
+# red-black SSOR with the faces read again by the sweeps and z stored -- 17 words = 68 B.  The
+# kernels here store rho/2 instead of faces and never store q, so they move less; the line
 # reports the fraction at both counts.
-BYTES_PER_CELL_FACE_SCHEDULE = 56
+BYTES_PER_CELL_FACE_SCHEDULE = {"one-sweep": 56, "red-black": 68}
 
 
 # MG-preconditioned phase B (POISSON_MG), per fine cell: the CG update (read p, x, r, eta; write
@@ -164,6 +168,8 @@ def peaks():
 # these files are unchanged and the line runs the tile (variant and split) it was taken on.
 KERNEL_SOURCES = {
     "one-sweep": ["march1.cu", "march_dev.cuh", "tma.cuh", "internal.cuh", "march.h"],
+    "red-black": ["march_rb.cu", "march_rb.h", "march_dev.cuh", "tma.cuh", "internal.cuh",
+                  "march.h"],
 }
 
 
@@ -371,7 +377,10 @@ def roofline(prof, desc, precision, precond, g, iters, periodic, kind):
     dom = max(cands, key=lambda k: prof[k]["ms"])
     per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
     family = None
-    if "A p formed" in desc:
+    if "red-black" in desc:
+        bpi = BYTES_PER_CELL_RB[precision]
+        family = "red-black"
+    elif "A p formed" in desc:
         bpi = BYTES_PER_CELL_AP_FORMED[precision]
     elif "one-sweep" in desc:
         bpi = BYTES_PER_CELL_ONE_SWEEP[precision]
@@ -400,8 +409,8 @@ def roofline(prof, desc, precision, precond, g, iters, periodic, kind):
            "traffic_bytes_per_cell_iter": bpci,
            "alg_bytes_per_launch": alg_bytes, "alg_bytes_per_cell_iter": bpi,
            "ms_per_launch": per_launch_ms, "cell_iters_per_launch": cell_iters}
-    if family == "one-sweep" and precision == "fp32":
-        out["frac_at_face_schedule_bytes"] = (BYTES_PER_CELL_FACE_SCHEDULE * cell_iters /
+    if family in ("one-sweep", "red-black") and precision == "fp32":
+        out["frac_at_face_schedule_bytes"] = (BYTES_PER_CELL_FACE_SCHEDULE[family] * cell_iters /
                                               (per_launch_ms * 1e-3) / 1e9 / peak)
     return out
 

@@ -259,6 +259,27 @@ int poisson_divergence(poisson_t* h, const double* u, const double* v, const dou
  * doubles.  Errors: EINVAL, ENOTREADY (before set_density), ENOMEM, ECUDA. */
 int poisson_project(poisson_t* h, double* u, double* v, double* w, const double* p, double dt);
 
+/* Reduced pressure (Entrance and Exit Boundary Conditions, hydrostatic-pressure method).  Solving
+ * for P_r = P - rho g (z - z_o), z_o the static free-surface height, puts the force
+ * -(z - z_o) (1/rho) d(rho g)/dx_i into the momentum equations -- in the paper's units
+ * (rho = lambda + (1 - lambda) H) -(z - z_o)(1 - lambda) g (1/rho) dH/dx_i -- which gives P_r a
+ * jump of (z - z_o)(1 - lambda) g across the interface.  The force is a term of the provisional
+ * velocity: this call adds dt f to the face velocities u, v, w in place (shapes as for
+ * poisson_divergence), after which poisson_divergence gives the source for P_r and
+ * poisson_project removes the force's gradient part.  On the face between cells c and n (n on the
+ * +axis side): f = -(z_f - z_o) g (2/(rho_c + rho_n)) (rho_n - rho_c) / h, rho from F as in
+ * poisson_set_density, z_f the face's height ((k + 1/2) h on the x and y faces of layer k, k h
+ * on the z face below layer k; the grid's z = 0 is the bottom); no force on the walls and the
+ * top face (H continued beyond the boundary without change along its normal); with periodic x
+ * the wrap face is written to faces 0 and nx.  g is the coefficient as the paper writes it: the
+ * gravity term this replaces is +g in the z momentum equation (g < 0 for z pointing up).  At rest
+ * (u* = 0, a layered density) the projected velocity vanishes and P_r is the column with those
+ * jumps and P_r = 0 in the top layer.  F: nx*ny*nz doubles; host or device pointers (host arrays
+ * are staged through temporary device buffers); the call waits for the handle's stream.
+ * Errors: EINVAL (NULL, rho <= 0, a non-finite argument), ENOMEM, ECUDA. */
+int poisson_hydrostatic_force(poisson_t* h, const double* F, double rho_air, double rho_water,
+                              double g, double z_o, double dt, double* u, double* v, double* w);
+
 /* ------------------------------------------------------------------ allocation-free check
  * The paper has no counterpart to this entry point.  It is for callers that cannot allocate
  * device memory when they check a pressure field: a step loop that must not pay cudaMalloc's

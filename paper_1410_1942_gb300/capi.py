@@ -32,7 +32,7 @@ EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson
            "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
            "poisson_profile_read", "poisson_describe", "poisson_residual_noalloc",
            "poisson_divergence", "poisson_project", "poisson_set_apertures", "poisson_strerror",
-           "poisson_version", "poisson_test_unreachable_barrier"]
+           "poisson_version", "poisson_test_unreachable_barrier", "poisson_hydrostatic_force"]
 K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER, K_PCG = 0, 1, 2, 3, 4
 K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 
@@ -112,6 +112,8 @@ def load(path=None):
     lib.poisson_project.restype = i
     lib.poisson_set_apertures.argtypes = [vp, vp, vp, vp, vp, i]
     lib.poisson_set_apertures.restype = i
+    lib.poisson_hydrostatic_force.argtypes = [vp, vp, d, d, d, d, d, vp, vp, vp]
+    lib.poisson_hydrostatic_force.restype = i
     lib.poisson_test_unreachable_barrier.argtypes = [vp, i]
     lib.poisson_test_unreachable_barrier.restype = i
     for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read", "poisson_describe"]:
@@ -256,6 +258,12 @@ class Poisson:
         """In place: ``u -= dt beta_f grad_h p`` on every face (walls unchanged)."""
         _check(load().poisson_project(self._h, _addr(u), _addr(v), _addr(w), _addr(p), dt),
                "poisson_project")
+
+    def hydrostatic_force(self, F, u, v, w, g, z_o, dt, rho_air=1.0, rho_water=1000.0):
+        """Adds dt times the reduced-pressure force to the face velocities in place."""
+        _check(load().poisson_hydrostatic_force(self._h, _addr(F), rho_air, rho_water, g, z_o, dt,
+                                                _addr(u), _addr(v), _addr(w)),
+               "poisson_hydrostatic_force")
 
     def projection_step(self, u, v, w, dt, p, tol, s=None):
         """One pressure projection of a provisional face velocity, in place: ``s =

@@ -16,6 +16,7 @@
 #include "kernels.h"
 #include "capi_internal.h"
 #include "march.h"
+#include "march_rb.h"
 
 using namespace pcg;
 
@@ -218,7 +219,7 @@ static int setup_march(poisson_t* H) {
         // variant and family 2 (A p formed in the sweep, bound by its arithmetic) never won
         for (int cand = 0; cand < march_variant_count(); ++cand) {
             const MarchVariant mv = march_variant(cand);
-            if (mv.cx != 2 || mv.family == 2 || march_occupancy(cand, bf16) <= 0) continue;
+            if (mv.cx != 2 || mv.family >= 2 || march_occupancy(cand, bf16) <= 0) continue;
             if (H->periodic() && mv.family != 1) continue;  // only the one-sweep kernels wrap
             for (int strat = 0; strat < MARCH_SPLITS; ++strat) {
                 if (build_plan(H, cand, strat) != 0) continue;
@@ -253,6 +254,135 @@ static int setup_march(poisson_t* H) {
     const int rc = build_plan(H, var, strategy);
     if (rc == -2) return POISSON_ENOMEM;
     H->march = (rc == 0);
+    return POISSON_OK;
+}
+
+// ------------------------------------------------------------------ red-black SSOR marching
+// The compressed black vectors of the red-black kernels, carved from the handle's FP32 inner
+// vectors (each holds n floats, two black vectors of n/2; n is a multiple of 8, so both halves
+// start on 16-byte boundaries as the tensor maps need).
+struct RbBuffers {
+    float *x, *p, *u0, *u1, *s0, *s1, *w0, *w1;
+};
+static RbBuffers rb_buffers(poisson_t* H) {
+    const size_t nh = (size_t)H->d.n / 2;
+    return RbBuffers{H->z32, H->z32 + nh, H->p32a, H->p32a + nh,
+                     H->p32b, H->p32b + nh, H->s32a, H->s32a + nh};
+}
+
+static MarchSolve rb_solve_of(poisson_t* H) {
+    const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
+    const RbBuffers b = rb_buffers(H);
+    return MarchSolve{H->d, b.x, H->r32, b.u0, b.p, b.u1,
+                      bf16 ? (const void*)H->eta16 : (const void*)H->eta32, H->sc,
+                      b.s0, b.s1, b.w0, b.w1};
+}
+
+// One FP32 inner solve A32 d = r32 by red-black SSOR PCG (omega = 1) as CG on the black Schur
+// complement: start (red relaxation, reduced right side, scalars), the persistent launch, then
+// d = (x_B, D_R^-1 (r_R + C x_B)) into d32.  POISSON_ECUDA if the launch is refused.
+static int march_rb_run(poisson_t* H, bool bf16, double tol2, int max_iter,
+                        Scalars* result = nullptr) {
+    cudaStream_t st = H->st;
+    const Dims d = H->d;
+    const RbBuffers b = rb_buffers(H);
+    if (bf16)
+        launch_rb_init<__nv_bfloat16>(d, H->eta16, H->r32, b.u0, b.s0, b.w0, b.p, b.x, H->sc,
+                                      H->partials, tol2, max_iter, st);
+    else
+        launch_rb_init<float>(d, H->eta32, H->r32, b.u0, b.s0, b.w0, b.p, b.x, H->sc, H->partials,
+                              tol2, max_iter, st);
+    *H->ctl_host = MarchCtl{0u, 1, 0, 0, 0ull};
+    CK(cudaMemcpyAsync(H->plan.ctl, H->ctl_host, sizeof(MarchCtl), cudaMemcpyHostToDevice, st));
+    const bool prof = H->prof_on && result;
+    if (prof) CK(cudaEventRecord(H->prof_ev[PROF_PCG], st));
+    if (launch_march_pcg(H->plan, st) != 0) return POISSON_ECUDA;
+    if (prof) CK(cudaEventRecord(H->prof_ev[PROF_PCG + 1], st));
+    if (bf16) launch_rb_finish<__nv_bfloat16>(d, H->eta16, H->r32, b.x, H->d32, st);
+    else launch_rb_finish<float>(d, H->eta32, H->r32, b.x, H->d32, st);
+    CK(cudaStreamSynchronize(st));
+    if (prof) prof_add(H, POISSON_K_PCG, H->prof_ev[PROF_PCG], H->prof_ev[PROF_PCG + 1]);
+    if (result) CK(cudaMemcpy(result, H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost));
+    return POISSON_OK;
+}
+
+static std::map<TuneKey, std::pair<int, int>> g_tuned_rb;  // (variant, split), under g_tune_mu
+
+static int build_rb_plan(poisson_t* H, int var, int strategy) {
+    const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
+    const MarchSolve s = rb_solve_of(H);
+    const int nctas = march_occupancy(var, bf16) * num_sms();
+    if (nctas <= 0) return -1;
+    return march_plan_build(&H->plan, &s, 1, var, bf16, nctas, strategy, H->st);
+}
+
+// Variant and split of the red-black kernels: a forced family-3 tile, else the fastest of every
+// family-3 variant and split on a constant-density model problem (16 iterations per try, cached
+// per size class like the Jacobi kernels).  A forced tile of another family keeps the column
+// kernels.
+static int setup_rb(poisson_t* H) {
+    const bool bf16 = H->opts.precision == POISSON_FP32_BF16COEF;
+    const Dims d = H->d;
+    const int forced = H->opts.tile;
+    int var = -1, strategy = MARCH_SPLIT_LOCKSTEP;
+    if (forced > 0) {
+        var = march_variant_of_tile(forced);
+        strategy = march_split_of_tile(forced);
+        if (var < 0 || march_variant(var).family != 3) return POISSON_OK;
+    } else {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned_rb.find(tune_key(d, bf16));
+        if (it != g_tuned_rb.end()) {
+            var = it->second.first;
+            strategy = it->second.second;
+        }
+    }
+    if (var < 0) {
+        constexpr int TUNE_ITERS = 16;
+        cudaStream_t st = H->st;
+        const long long n = d.n;
+        if (bf16) launch_fill_bf16(n, H->eta16, 0.5f, st);
+        else launch_fill_f32(n, H->eta32, 0.5f, st);
+        launch_fill_f32(n, H->r32, 1.0f, st);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (int cand = 0; cand < march_variant_count(); ++cand) {
+            if (march_variant(cand).family != 3 || march_occupancy(cand, bf16) <= 0) continue;
+            for (int strat = 0; strat < MARCH_SPLITS; ++strat) {
+                if (build_rb_plan(H, cand, strat) != 0) continue;
+                float t[2];
+                bool good = true;
+                for (int rep = 0; rep < 2 && good; ++rep) {
+                    cudaEventRecord(e0, st);
+                    good = march_rb_run(H, bf16, 0.0, TUNE_ITERS) == POISSON_OK;
+                    cudaEventRecord(e1, st);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&t[rep], e0, e1);
+                }
+                if (!good || cudaGetLastError() != cudaSuccess) continue;
+                const float tt = std::min(t[0], t[1]);
+                if (tt < best) {
+                    best = tt;
+                    var = cand;
+                    strategy = strat;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaMemsetAsync(H->sc, 0, sizeof(Scalars), st);
+        cudaStreamSynchronize(st);
+        if (var >= 0) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned_rb[tune_key(d, bf16)] = {var, strategy};
+        }
+    }
+    if (var < 0) return POISSON_OK;  // stay on the column kernels
+    const int rc = build_rb_plan(H, var, strategy);
+    if (rc == -2) return POISSON_ENOMEM;
+    H->rb = (rc == 0);
     return POISSON_OK;
 }
 
@@ -303,6 +433,10 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (!(o.omega > 0.0 && o.omega < 2.0)) return POISSON_EINVAL;
     if (o.max_iters <= 0 || !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return POISSON_EINVAL;
     if (o.tile < -1 || (o.tile > 0 && march_variant_of_tile(o.tile) < 0))
+        return POISSON_EINVAL;
+    // the red-black kernels (tile codes 3xxxxxxx) run only the red-black SSOR preconditioner
+    if (o.tile > 0 && march_variant(march_variant_of_tile(o.tile)).family == 3 &&
+        o.precond != POISSON_RBSSOR)
         return POISSON_EINVAL;
     if (o.dirichlet_walls < 0 || o.dirichlet_walls > POISSON_WALLS_ALL) return POISSON_EINVAL;
     if (o.periodic_x != 0 && o.periodic_x != 1) return POISSON_EINVAL;
@@ -358,7 +492,7 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
         A(mg_alloc(&H->mg, o.precision == POISSON_FP64));
     }
     A(dalloc(&H->sc, 1));
-    A(dalloc(&H->partials, 2 * H->nblocks + 64));
+    A(dalloc(&H->partials, std::max<size_t>(2 * H->nblocks + 64, 4096)));
     if (rc == POISSON_OK && cudaMallocHost((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
         cudaGetLastError();
         H->sc_host = nullptr;
@@ -377,6 +511,9 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.precond == POISSON_JACOBI &&
         o.tile != -1 && march_supported(H->d))
         A(setup_march(H));
+    if (rc == POISSON_OK && o.precision != POISSON_FP64 && o.precond == POISSON_RBSSOR &&
+        o.omega == 1.0 && o.tile != -1 && march_supported(H->d) && !o.periodic_x)
+        A(setup_rb(H));
     if (rc != POISSON_OK) {
         free_state(H);
         delete H;
@@ -441,7 +578,9 @@ extern "C" int poisson_set_apertures(poisson_t* H, const double* ax, const doubl
             *q = nullptr;
         }
         H->d.walls &= ~CUT_CELLS;
-        H->march = H->plan.segs != nullptr;  // the plan built at create, if any
+        // the plan built at create, if any
+        H->march = H->plan.segs != nullptr && H->opts.precond == POISSON_JACOBI;
+        H->rb = H->plan.segs != nullptr && H->opts.precond == POISSON_RBSSOR;
         H->ready = false;
         return POISSON_OK;
     }
@@ -469,6 +608,7 @@ extern "C" int poisson_set_apertures(poisson_t* H, const double* ax, const doubl
     CK(cudaStreamSynchronize(H->st));
     H->d.walls |= CUT_CELLS;
     H->march = false;  // the marching kernels form faces from rho/2 and cannot carry fractions
+    H->rb = false;
     H->ready = false;  // poisson_set_density builds the cut operator
     return POISSON_OK;
 }
@@ -677,17 +817,26 @@ static int solve_mixed(poisson_t* H, const C32& c32, bool bf16, double tol, int*
         CK(cudaMemsetAsync(H->p32a, 0, bytes32, H->st));
         Scalars res;
         rc = POISSON_ECUDA;
-        if (H->march && H->opts.precond == POISSON_JACOBI) {
+        bool inner_done = false, rb_used = false;
+        if (H->rb && H->opts.precond == POISSON_RBSSOR) {
+            rb_used = true;
+            rc = march_rb_run(H, bf16, target * target, H->opts.max_iters - total, &res);
+            if (rc == POISSON_ECUDA) H->rb = false;  // launch refused: use the column kernels
+            else inner_done = true;
+        } else if (H->march && H->opts.precond == POISSON_JACOBI) {
             rc = march_run(H, bf16, target * target, H->opts.max_iters - total, &res);
             if (rc == POISSON_ECUDA) H->march = false;  // launch refused: use the column kernels
+            else inner_done = true;
         }
-        if (!H->march || H->opts.precond != POISSON_JACOBI)
+        if (!inner_done)
             rc = cg_loop_columns<float, C32>(H, c32, H->d32, H->r32, H->z32, H->p32a,
                                                     H->p32b, target * target, 0,
                                                     H->opts.max_iters - total, &res);
         if (rc) return rc;
         total += res.iter;
-        if (res.iter > 0) launch_update64(H->d.n, H->x64, H->d32, H->st);
+        // (the red-black solve's correction holds its red relaxation even after 0 iterations)
+        if (res.iter > 0 || (rb_used && inner_done && res.done != BREAKDOWN && res.done != TIMEDOUT))
+            launch_update64(H->d.n, H->x64, H->d32, H->st);
         CK(cudaGetLastError());
         if (res.done == TIMEDOUT) { status = POISSON_ETIMEOUT; break; }
         if (res.done == BREAKDOWN && res.iter == 0) { status = POISSON_EBREAKDOWN; break; }
@@ -700,7 +849,7 @@ static int solve_mixed(poisson_t* H, const C32& c32, bool bf16, double tol, int*
 
 extern "C" int poisson_test_unreachable_barrier(poisson_t* H, int extra) {
     if (!H || extra < 0 || extra > 1024) return POISSON_EINVAL;
-    if (!H->march || H->cut() || H->opts.precond != POISSON_JACOBI) return POISSON_EINVAL;
+    if (!(H->march || H->rb) || H->cut()) return POISSON_EINVAL;
     H->plan.barrier_extra = extra;
     return POISSON_OK;
 }
@@ -949,14 +1098,15 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
     if (!H || !buf || len <= 0) return POISSON_EINVAL;
     const char* prec = H->opts.precision == POISSON_FP64 ? "fp64"
                        : H->opts.precision == POISSON_FP32 ? "fp32" : "fp32/bf16-coef";
-    if (H->march) {
+    if (H->march || H->rb) {
         const MarchVariant v = march_variant(H->plan.variant);
         snprintf(buf, (size_t)len,
                  "%s march tile=%d (%dx%d cells, %dx%d per thread%s, %d stages) persistent %s "
                  "ctas=%d segments=%d split=%s",
                  prec, march_tile_of(H->plan.variant) + 1000000 * H->plan.strategy, v.width,
                  v.height, v.cx, v.cy, v.ws ? ", producer warp" : "", v.ns,
-                 v.family == 2   ? "one-sweep (A p formed)"
+                 v.family == 3   ? "one-sweep red-black SSOR (black Schur complement)"
+                 : v.family == 2 ? "one-sweep (A p formed)"
                  : v.family == 1 ? "one-sweep"
                                  : "two-sweep",
                  H->plan.nctas, H->plan.nsegs,

@@ -66,6 +66,10 @@ struct poisson_s {
     pcg::MgHier mg{};
     // TMA plane-marching kernels for the FP32 inner solve (when the shape allows them)
     bool march = false;
+    // red-black SSOR (omega = 1) inner solve on the plane-marching kernels of march_rb.cu: CG on
+    // the black Schur complement, compressed black vectors in the first and second halves of
+    // z32 (x, p), p32a (u, both buffers), p32b (s^), s32a (w^); plan in `plan`
+    bool rb = false;
     pcg::MarchPlan plan{};  // persistent work-list launch over this handle's grid
     pcg::MarchCtl* ctl_host = nullptr;  // pinned staging of plan.ctl
     // poisson_profile: event pairs around the timed kernels, accumulated times

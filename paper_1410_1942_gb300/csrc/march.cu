@@ -25,6 +25,7 @@
 #include "kernels.h"
 #include "march.h"
 #include "march_dev.cuh"
+#include "march_rb.h"
 #include "tma.cuh"
 
 #include <cudaTypedefs.h>
@@ -909,7 +910,11 @@ struct VariantOps {
 
 template <int CX, int CY, int TYT, int WS, int NS, int F>
 static VariantOps make_ops() {
-    if constexpr (F == 1 || F == 2) {
+    if constexpr (F == 3) {
+        static_assert(WS == 1, "the red-black kernels have a producer warp");
+        const Cg1Kernel k = rb_kernel(CX, CY, TYT, NS);
+        return VariantOps{CX, CY, TYT, 1, NS, k.smem32, k.smem16, k.k32, k.k16, F};
+    } else if constexpr (F == 1 || F == 2) {
         static_assert(WS == 1, "the one-sweep kernels have a producer warp");
         const Cg1Kernel k = F == 1 ? cg1_kernel(CX, CY, TYT, NS) : cg2_kernel(CX, CY, TYT, NS);
         return VariantOps{CX, CY, TYT, 1, NS, k.smem32, k.smem16, k.k32, k.k16, F, k.k32p, k.k16p};
@@ -925,13 +930,14 @@ static VariantOps make_ops() {
                           (const void*)k_pcg<CX, CY, TYT, __nv_bfloat16, NS>, 0};
 }
 
-// (CX, CY, TYT, warp-specialised, ring stages, family); family 1 and 2 rows must be in
-// CG1_CONFIGS and CG2_CONFIGS
+// (CX, CY, TYT, warp-specialised, ring stages, family); family 1, 2 and 3 rows must be in
+// CG1_CONFIGS, CG2_CONFIGS and RB_CONFIGS
 #define MARCH_VARIANTS(X)                                                                       \
     X(1, 1, 8, 0, 4, 0) X(2, 2, 4, 0, 4, 0) X(2, 2, 8, 0, 4, 0) X(2, 2, 4, 1, 4, 0)             \
     X(2, 2, 8, 1, 4, 0) X(2, 2, 4, 0, 3, 0) X(2, 2, 8, 0, 3, 0) X(2, 2, 8, 1, 3, 0)             \
     X(2, 2, 4, 0, 6, 0) X(2, 2, 8, 1, 6, 0) X(2, 2, 4, 1, 4, 1) X(2, 2, 4, 1, 3, 1)             \
-    X(2, 2, 8, 1, 3, 1) X(2, 2, 4, 1, 4, 2) X(2, 2, 4, 1, 5, 2) X(2, 2, 8, 1, 4, 2)
+    X(2, 2, 8, 1, 3, 1) X(2, 2, 4, 1, 4, 2) X(2, 2, 4, 1, 5, 2) X(2, 2, 8, 1, 4, 2)             \
+    X(2, 2, 4, 1, 6, 3) X(2, 2, 4, 1, 5, 3) X(2, 2, 8, 1, 5, 3)
 
 static const VariantOps* variants(int* count) {
 #define ROW(CX, CY, TYT, WS, NS, F) make_ops<CX, CY, TYT, WS, NS, F>(),
@@ -979,7 +985,7 @@ int march_find_variant(int cx, int cy, int tyt, int ws, int ns, int family) {
 }
 
 int march_variant_of_tile(int tile) {
-    if (tile < 0 || tile / 10000000 > 2 || (tile / 1000000) % 10 >= MARCH_SPLITS) return -1;
+    if (tile < 0 || tile / 10000000 > 3 || (tile / 1000000) % 10 >= MARCH_SPLITS) return -1;
     const int family = tile / 10000000;
     tile %= 1000000;
     const int ns = tile / 100000 ? tile / 100000 : 4;
@@ -1025,6 +1031,25 @@ bool march_encode_solve(CUtensorMap (&m)[MAPS_PER_SOLVE], const MarchSolve& s, i
     const Dims& d = s.d;
     bool ok = true;
     if ((d.walls & PERIODIC_X) && v.family != 1) return false;  // no wrapped halos there
+    if (v.family == 3) {
+        // compressed black vectors (nx/2 per row) with 2-row halo boxes; eta at full size
+        Dims db = d;
+        db.nx = d.nx / 2;
+        db.sxy = db.nx * d.ny;
+        db.n = d.n / 2;
+        const int wb = v.width / 2, bw = wb + 8, bh = v.height + 4;
+        ok = ok && s.sa && s.sb && s.wa && s.wb && (d.nx % 8) == 0;
+        ok = ok && encode3d(&m[MAP1_U0], s.z, f32, 4, db, bw, bh);
+        ok = ok && encode3d(&m[MAP1_U1], s.pb, f32, 4, db, bw, bh);
+        ok = ok && encode3d(&m[MAP1_S0], s.sa, f32, 4, db, bw, bh);
+        ok = ok && encode3d(&m[MAP1_S1], s.sb, f32, 4, db, bw, bh);
+        ok = ok && encode3d(&m[MAP1_W0], s.wa, f32, 4, db, bw, bh);
+        ok = ok && encode3d(&m[MAP1_W1], s.wb, f32, 4, db, bw, bh);
+        ok = ok && encode3d(&m[MAP1_ETA], s.eta, edt, bf16 ? 2 : 4, d, v.width + 2 * eoff, bh);
+        ok = ok && encode3d(&m[MAP1_X], s.x, f32, 4, db, wb, v.height);
+        ok = ok && encode3d(&m[MAP1_P], s.pa, f32, 4, db, wb, v.height);
+        return ok;
+    }
     if (v.family == 2) {
         const int bw = v.width + 8, bh = v.height + 4;
         ok = ok && s.sa;

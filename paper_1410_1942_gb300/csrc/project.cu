@@ -114,6 +114,53 @@ __global__ void __launch_bounds__(PT) k_project(Dims d, double h, double dt,
     }
 }
 
+// The reduced-pressure force (Entrance and Exit Boundary Conditions, hydrostatic-pressure
+// method): the solve is for P_r = P - rho g (z - z_o), and the momentum equations carry
+// -(z - z_o) (1/rho) d(rho g)/dx_i.  On the face between the low cell (density rl) and the high
+// cell (rh) at height zf: f = -(zf - z_o) g (2/(rl + rh)) (rh - rl) / h, with the operator's face
+// coefficient 2/(rl + rh), evaluated in this order.  Boundary faces get none (H continued beyond
+// the boundary without change along its normal).
+__device__ __forceinline__ double reduced_force(double rl, double rh, double zf, double zo,
+                                                double g, double h) {
+    const double a = __dmul_rn(__dsub_rn(zf, zo), g);
+    const double b = __dmul_rn(__ddiv_rn(2.0, __dadd_rn(rl, rh)), __dsub_rn(rh, rl));
+    return __ddiv_rn(-__dmul_rn(a, b), h);
+}
+
+__device__ __forceinline__ double rho_of(const double* F, long long c, double ra, double rw) {
+    return __dadd_rn(ra, __dmul_rn(F[c], __dsub_rn(rw, ra)));
+}
+
+// u_f <- u_f + dt f on the low faces of every cell (one thread per cell); the periodic wrap face
+// is written to faces 0 and nx.
+__global__ void __launch_bounds__(PT) k_hydrostatic_force(Dims d, double h, const double* __restrict__ F,
+                                                          double ra, double rw, double g, double zo,
+                                                          double dt, double* __restrict__ u,
+                                                          double* __restrict__ v,
+                                                          double* __restrict__ w) {
+    const long long t = blockIdx.x * (long long)PT + threadIdx.x;
+    if (t >= d.n) return;
+    const int c = (int)t;
+    const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
+    const long long fu = i + (long long)(d.nx + 1) * (j + (long long)d.ny * k);
+    const long long fv = i + (long long)d.nx * (j + (long long)(d.ny + 1) * k);
+    const double rc = rho_of(F, c, ra, rw);
+    const double zc = __dmul_rn(__dadd_rn((double)k, 0.5), h);  // height of the x and y faces
+    if (i > 0) {
+        u[fu] = __dadd_rn(u[fu], __dmul_rn(dt, reduced_force(rho_of(F, c - 1, ra, rw), rc, zc, zo, g, h)));
+    } else if (d.walls & pcg::PERIODIC_X) {
+        const double q = __dadd_rn(
+            u[fu], __dmul_rn(dt, reduced_force(rho_of(F, c + d.nx - 1, ra, rw), rc, zc, zo, g, h)));
+        u[fu] = q;
+        u[fu + d.nx] = q;
+    }
+    if (j > 0)
+        v[fv] = __dadd_rn(v[fv], __dmul_rn(dt, reduced_force(rho_of(F, c - d.nx, ra, rw), rc, zc, zo, g, h)));
+    if (k > 0)
+        w[c] = __dadd_rn(w[c], __dmul_rn(dt, reduced_force(rho_of(F, c - d.sxy, ra, rw), rc,
+                                                           __dmul_rn((double)k, h), zo, g, h)));
+}
+
 // Device copies of caller arrays: the caller's pointer if it is device memory, else a temporary
 // filled from the host (and, for outputs, copied back by flush()).
 struct Staged {
@@ -207,6 +254,36 @@ extern "C" int poisson_project(poisson_t* H, double* u, double* v, double* w, co
     k_project<<<blocks_of(d.n), PT, 0, H->st>>>(d, H->h, dt, H->bx, H->by, H->bz, H->top64,
                                                 H->rinv2, P.dev, U.dev, V.dev, W.dev,
                                                 H->apertures());
+    pcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    if (cudaGetLastError() != cudaSuccess) rc = POISSON_ECUDA;
+    if (rc == POISSON_OK) rc = U.flush(H->st);
+    if (rc == POISSON_OK) rc = V.flush(H->st);
+    if (rc == POISSON_OK) rc = W.flush(H->st);
+    const int rs = finish(H->st);
+    return rc != POISSON_OK ? rc : rs;
+}
+
+extern "C" int poisson_hydrostatic_force(poisson_t* H, const double* F, double rho_air,
+                                         double rho_water, double g, double z_o, double dt,
+                                         double* u, double* v, double* w) {
+    if (!H || !F || !u || !v || !w || !(rho_air > 0.0) || !(rho_water > 0.0) ||
+        !std::isfinite(rho_air) || !std::isfinite(rho_water) || !std::isfinite(g) ||
+        !std::isfinite(z_o) || !std::isfinite(dt))
+        return POISSON_EINVAL;
+    const Dims d = H->d;
+    const size_t nu = (size_t)(d.nx + 1) * d.ny * d.nz, nv = (size_t)d.nx * (d.ny + 1) * d.nz,
+                 nw = (size_t)d.sxy * (d.nz + 1);
+    Staged Fs, U, V, W;
+    int rc = Fs.stage(F, (size_t)d.n, true, H->st);
+    if (rc == POISSON_OK) rc = U.stage(u, nu, true, H->st);
+    if (rc == POISSON_OK) rc = V.stage(v, nv, true, H->st);
+    if (rc == POISSON_OK) rc = W.stage(w, nw, true, H->st);
+    if (rc != POISSON_OK) {
+        finish(H->st);
+        return rc;
+    }
+    k_hydrostatic_force<<<blocks_of(d.n), PT, 0, H->st>>>(d, H->h, Fs.dev, rho_air, rho_water, g,
+                                                          z_o, dt, U.dev, V.dev, W.dev);
     pcg::g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     if (cudaGetLastError() != cudaSuccess) rc = POISSON_ECUDA;
     if (rc == POISSON_OK) rc = U.flush(H->st);

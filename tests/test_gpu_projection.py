@@ -198,3 +198,78 @@ def test_two_stage_projection_cycle(precond):
             assert np.linalg.norm(div) * g.h ** 2 <= tol * (1 + 1e-6) * np.linalg.norm(b)
     # the second stage starts from the first stage's pressure: the warm start pays
     assert iters[1] < iters[0]
+
+
+# ----------------------------------------------------------------------------- reduced pressure
+@pytest.mark.parametrize("dev", [False, True])
+@pytest.mark.parametrize("nx,ny,nz,walls", [(37, 23, 19, 0), (64, 16, 1, 0), (8, 9, 33, 31),
+                                            (1, 5, 7, 0), (48, 24, 20, oracle.PERIODIC_X),
+                                            (6, 4, 5, oracle.PERIODIC_X | 16)])
+def test_hydrostatic_force_bit_exact(nx, ny, nz, walls, dev):
+    """The reduced-pressure force added to the face velocities, bit for bit against the oracle
+    (every face of random fields, boundary faces included; the periodic wrap face on faces 0
+    and nx)."""
+    import torch
+    shape = (nz, ny, nx)
+    F = _rand_F(shape, 5)
+    u, v, w = _faces(shape, 6)
+    h, dt, g, zo = 1.0 / nz, 1.3e-3, -9.81, 0.47
+    ref = oracle.hydrostatic_force(F, u, v, w, h, g, zo, dt=dt, walls=walls)
+    kw = {"dirichlet_walls": walls & 31, "periodic_x": bool(walls & oracle.PERIODIC_X)}
+    with capi.Poisson(nx, ny, nz, h, **kw) as s:
+        if dev:
+            Fd, ud, vd, wd = (torch.from_numpy(a.copy()).cuda() for a in (F, u, v, w))
+            s.hydrostatic_force(Fd, ud, vd, wd, g, zo, dt)
+            got = [a.cpu().numpy() for a in (ud, vd, wd)]
+        else:
+            got = [u.copy(), v.copy(), w.copy()]
+            s.hydrostatic_force(F, *got, g, zo, dt)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_hydrostatic_rest_through_the_library(prec):
+    """A layered density at rest (surface above the static level, no flow): force, divergence,
+    solve and projection all through the C ABI leave no velocity, and the reduced pressure is
+    the column with the paper's jumps (z_f - z_o) g (rho_above - rho_below), 0 in the top layer."""
+    nx, ny, nz = 32, 16, 48
+    h = 1.0 / nz
+    g_, zo, dt = -9.81, 0.43, 1e-3
+    zc = (np.arange(nz) + 0.5) * h
+    eps, zs = 1.5 * h, 0.55
+    d = zs - zc
+    Fz = np.where(d > eps, 1.0, np.where(d < -eps, 0.0,
+                                         0.5 * (1 + d / eps + np.sin(np.pi * d / eps) / np.pi)))
+    F = np.broadcast_to(Fz[:, None, None], (nz, ny, nx)).copy()
+    rho = 1.0 + Fz * 999.0
+    col = np.zeros(nz)
+    for k in range(nz - 1, 0, -1):
+        col[k - 1] = col[k] + (k * h - zo) * g_ * (rho[k] - rho[k - 1])
+    u, v, w = (np.zeros(a.shape) for a in _faces((nz, ny, nx), 0))
+    p = np.zeros((nz, ny, nx))
+    s_ = np.empty((nz, ny, nx))
+    with capi.Poisson(nx, ny, nz, h, precision=prec) as s:
+        s.set_density(F)
+        s.hydrostatic_force(F, u, v, w, g_, zo, dt)
+        ref = np.abs(w).max()
+        assert ref > 0
+        s.divergence(u, v, w, dt, s_)
+        rc, st = s.solve(s_, p, 1e-12)
+        assert rc == capi.OK
+        s.project(u, v, w, p, dt)
+    assert np.abs(p - col[:, None, None]).max() <= 1e-8 * np.abs(col).max()
+    for a in (u, v, w):
+        assert np.abs(a).max() <= 1e-7 * ref
+
+
+def test_hydrostatic_force_errors():
+    with capi.Poisson(8, 8, 8, 0.125) as s:
+        F = np.zeros((8, 8, 8))
+        u, v, w = _faces((8, 8, 8), 0)
+        for bad in ((0.0, 1000.0, -9.8, 0.5, 1e-3), (1.0, 1000.0, float("nan"), 0.5, 1e-3),
+                    (1.0, 1000.0, -9.8, float("inf"), 1e-3)):
+            with pytest.raises(capi.PoissonError) as e:
+                s.hydrostatic_force(F, u, v, w, bad[2], bad[3], bad[4], rho_air=bad[0],
+                                    rho_water=bad[1])
+            assert e.value.status == capi.EINVAL

@@ -26,13 +26,15 @@ def _lib():
     capi.load()
 
 
-# one-sweep (producer warp, lockstep split), two-sweep with a producer warp, two-sweep without
-@pytest.mark.parametrize("tile", [12012204, 12204, 2204])
-def test_unreachable_barrier_times_out_and_the_handle_recovers(tile):
+# one-sweep (producer warp, lockstep split), two-sweep with a producer warp, two-sweep without,
+# and the red-black SSOR kernel
+@pytest.mark.parametrize("tile,precond", [(12012204, "jacobi"), (12204, "jacobi"),
+                                          (2204, "jacobi"), (32612204, "rbssor")])
+def test_unreachable_barrier_times_out_and_the_handle_recovers(tile, precond):
     c = inputs.strut_case(64, 32, 32, seed=2)
     g = c.grid
     op, b = oracle.operator(c.F), oracle.rhs(c.s, g.h)
-    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", tile=tile) as sv:
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", tile=tile, precond=precond) as sv:
         sv.set_density(c.F)
         assert "persistent" in sv.describe() or "one-sweep" in sv.describe(), sv.describe()
         sv.test_unreachable_barrier(1)
