@@ -937,7 +937,7 @@ static VariantOps make_ops() {
     X(2, 2, 8, 1, 4, 0) X(2, 2, 4, 0, 3, 0) X(2, 2, 8, 0, 3, 0) X(2, 2, 8, 1, 3, 0)             \
     X(2, 2, 4, 0, 6, 0) X(2, 2, 8, 1, 6, 0) X(2, 2, 4, 1, 4, 1) X(2, 2, 4, 1, 3, 1)             \
     X(2, 2, 8, 1, 3, 1) X(2, 2, 4, 1, 4, 2) X(2, 2, 4, 1, 5, 2) X(2, 2, 8, 1, 4, 2)             \
-    X(2, 2, 4, 1, 6, 3) X(2, 2, 4, 1, 5, 3) X(2, 2, 8, 1, 5, 3)
+    X(2, 2, 4, 1, 8, 3) X(2, 2, 4, 1, 7, 3) X(2, 1, 8, 1, 8, 3) X(2, 2, 8, 1, 7, 3)
 
 static const VariantOps* variants(int* count) {
 #define ROW(CX, CY, TYT, WS, NS, F) make_ops<CX, CY, TYT, WS, NS, F>(),

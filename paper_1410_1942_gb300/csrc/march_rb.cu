@@ -25,18 +25,22 @@
 // grid 10 half-cells of FP32 vectors plus eta, 24 bytes (22 with BF16 eta) against 40 for the
 // Jacobi one-sweep kernel, at about half its iteration count.
 //
-// Per plane the consumers (TYT warps; a producer warp streams the planes by TMA) do three steps,
-// each over the whole tile from shared memory:
-//   1. u' = u - alpha (w^ + beta s^) of plane q on the black cells of the tile and two rings
-//      (full-resolution shared plane, a ring of 4 planes);
-//   2. t = D_r^-1 sum_faces beta u' of plane q-1 on the red cells of the tile and one ring;
-//   3. S u' = D_b u' - sum_faces beta t of plane q-2 on the tile's black cells, then
+// The consumer warps (TYT; a producer warp streams planes by TMA) do three steps per arriving
+// plane q, each over the whole tile from shared memory, skewed by two planes so that one barrier
+// per plane separates every write from its reads:
+//   1. u' = u - alpha (w^ + beta s^) of plane q on the black cells of the tile and two rings;
+//   2. t = D_r^-1 sum_faces beta u' of plane q-2 on the red cells of the tile and one ring;
+//   3. S u' = D_b u' - sum_faces beta t of plane q-4 on the tile's black cells, then
 //      p = u + beta p, s^ = w^ + beta s^, x += alpha p, w^' = D_b^-1 S u' and the three sums.
-// The faces are 1/(eta_c + eta_n) (eta = rho/2) formed on the fly exactly as in the Jacobi
-// kernels, so S is the Schur complement of the same inner operator.  A segment of planes
-// [k0, k1) streams planes k0-2 .. k1+1; a stage is released after step 3 of the plane three
-// above it.  Work list, producer/consumer roles, bounded waits, fixed-order float-float
-// reductions and the finishing protocol are those of march1.cu.
+// u' and t live in shared memory compressed like the black vectors (a red cell (i, j, k) at
+// m = i / 2 as well), so a warp's lanes, one per m, read neighbours at consecutive addresses: the
+// x neighbours of a cell of parity bit c (i = 2m + c) sit at m - 1 + c and m + c of the other
+// colour, its y and z neighbours at m.  Rings of 5 u' planes and 4 t planes; a segment of planes
+// [k0, k1) streams planes k0-2 .. k1+1 and runs two more steps without a new plane.  Tiles whose
+// cells and rings lie inside the grid in x and y take a stencil without boundary tests.  The
+// faces are 1/(eta_c + eta_n) (eta = rho/2) formed on the fly as in the Jacobi kernels, so S is
+// the Schur complement of the same inner operator.  Work list, producer/consumer roles, bounded
+// waits, fixed-order float-float reductions and the finishing protocol are those of march1.cu.
 #include "march_rb.h"
 
 #include <cudaTypedefs.h>
@@ -48,7 +52,7 @@ namespace pcg {
 template <int CX, int CY, int TYT, typename E>
 struct GeoRB {
     static constexpr int W = 32 * CX;    // tile width (cells)
-    static constexpr int WB = W / 2;     // black cells per tile row
+    static constexpr int WB = W / 2;     // black (and red) cells per tile row: one per lane
     static constexpr int HT = CY * TYT;  // tile height (rows)
     static constexpr int VOFF = 4;       // halo of the compressed boxes in x (16 bytes)
     static constexpr int VW = WB + 2 * VOFF;
@@ -65,12 +69,11 @@ struct GeoRB {
     static constexpr int TX_HALO = 3 * VB + EB;  // planes outside [k0, k1): no x, p
     static constexpr int TX_P = TX_HALO + CB;    // a centre plane without x (start-up sweep)
     static constexpr int TX = TX_HALO + 2 * CB;
-    // on-chip planes at full resolution: u' over the tile and two rings, t over the tile and
-    // one ring; RING planes of each
-    static constexpr int RING = 4;
-    static constexpr int UW = W + 4, UH = HT + 4, UPL = UW * UH;
-    static constexpr int TW = W + 2, TH = HT + 2, TPL = TW * TH;
-    static constexpr int ON_CHIP = RING * (UPL + TPL) * 4;
+    // compressed on-chip planes: u' at m = x0/2 - 2 .. x0/2 + WB + 1 on rows y0 - 2 .. y0 + HT + 1;
+    // t at m = x0/2 - 1 .. x0/2 + WB on rows y0 - 1 .. y0 + HT
+    static constexpr int UC = WB + 4, UR = HT + 4, UPL = UC * UR, RINGU = 5;
+    static constexpr int TC = WB + 2, TR = HT + 2, TPL = TC * TR, RINGT = 4;
+    static constexpr int ON_CHIP = (RINGU * UPL + RINGT * TPL) * 4;
 };
 
 struct LocalSolveRB {
@@ -88,16 +91,33 @@ __device__ __forceinline__ float u_next_rb(float u, float s, float w, float al, 
     return __fmaf_rn(-al, __fmaf_rn(be, s, w), u);
 }
 
-__device__ __forceinline__ int ring4(int k) { return (k + 8) & 3; }
+__device__ __forceinline__ int ring(int k, int n) { return (k + 4 * n) % n; }
+
+// The faces and diagonal of a cell whose x and y neighbours are all inside the grid (the
+// expressions of eta_stencil with its x and y tests dropped; the z tests are uniform per plane).
+__device__ __forceinline__ void eta_stencil_inner(const Dims& d, int k, float ec, float exm,
+                                                  float exp_, float eym, float eyp, float ezm,
+                                                  float ezp, Stencil<float>& w) {
+    w.xm = rcp_approx(ec + exm);
+    w.xp = rcp_approx(ec + exp_);
+    w.ym = rcp_approx(ec + eym);
+    w.yp = rcp_approx(ec + eyp);
+    w.zm = (k > 0) ? rcp_approx(ec + ezm) : ((d.walls & 16) ? rcp_approx(ec) : 0.f);
+    const bool top = (k + 1 == d.nz);
+    const float wzt = top ? rcp_approx(ec) : rcp_approx(ec + ezp);
+    w.zp = top ? 0.f : wzt;
+    w.D = w.xm + w.xp + w.ym + w.yp + w.zm + wzt;
+}
 
 template <int CX, int CY, int TYT, typename E, int NS>
 __global__ void __launch_bounds__(32 * (TYT + 1), 2) k_rb_ws(PcgArgs a) {
     using G = GeoRB<CX, CY, TYT, E>;
-    static_assert(NS >= 5, "four stages are held while a fifth is filled");
+    static_assert(G::WB == 32, "one lane per compressed column of the tile");
+    static_assert(NS >= 7, "six stages are held while a seventh is filled");
     constexpr int NC = 32 * TYT;
     extern __shared__ __align__(128) unsigned char sm[];
-    float* const Ur = reinterpret_cast<float*>(sm + NS * G::STAGE);  // RING planes of u'
-    float* const Tr = Ur + G::RING * G::UPL;                         // RING planes of t
+    float* const Ur = reinterpret_cast<float*>(sm + NS * G::STAGE);  // RINGU planes of u'
+    float* const Tr = Ur + G::RINGU * G::UPL;                        // RINGT planes of t
     __shared__ __align__(8) uint64_t full[NS];
     __shared__ __align__(8) uint64_t empty[NS];
     __shared__ double red[64];
@@ -155,7 +175,7 @@ __global__ void __launch_bounds__(32 * (TYT + 1), 2) k_rb_ws(PcgArgs a) {
     }
     __syncthreads();
 
-    const int lane = tx;
+    const int lane = tx, warp = ty;
     auto stage = [&](int q) { return sm + (q % NS) * G::STAGE; };
     int np = 0;  // planes issued (producer lane 0)
     int nc = 0;  // planes acquired (each consumer warp)
@@ -193,6 +213,47 @@ __global__ void __launch_bounds__(32 * (TYT + 1), 2) k_rb_ws(PcgArgs a) {
         }
     };
 
+    // step 1 on plane q: u' at compressed column jc (m = x0/2 - 2 + jc) of on-chip row r
+    auto step1 = [&](const unsigned char* S, float* Uq, float al, float be, int r, int jc) {
+        const int si = r * G::VW + G::VOFF - 2 + jc;
+        const float* Su = (const float*)(S + G::U);
+        const float* Ss = (const float*)(S + G::S);
+        const float* Sw = (const float*)(S + G::WV);
+        Uq[r * G::UC + jc] = u_next_rb(Su[si], Ss[si], Sw[si], al, be);
+    };
+
+    // step 2 on plane kt: t of the red cell at compressed column jt (m = x0/2 - 1 + jt) of
+    // on-chip row rt (y = y0 - 1 + rt); 0 outside the grid
+    auto step2 = [&](const Dims& d, const Seg& sg, bool inner, int kt, const E* Em, const E* Ec,
+                     const E* Ep, const float* Um, const float* Uc, const float* Up, float* Tt,
+                     int rt, int jt) {
+        const int y = sg.y0 - 1 + rt;
+        const int pr = (y + kt) & 1;  // red: i + j + k even, i = 2m + pr
+        const int x = sg.x0 - 2 + 2 * jt + pr;
+        float t = 0.f;
+        if (inner || (x >= 0 && x < d.nx && y >= 0 && y < d.ny)) {
+            const int ei = (rt + 1) * G::EW + 2 * jt - 2 + pr + G::EOFF;
+            Stencil<float> w;
+            if (inner)
+                eta_stencil_inner(d, kt, ld1(Ec + ei), ld1(Ec + ei - 1), ld1(Ec + ei + 1),
+                                  ld1(Ec + ei - G::EW), ld1(Ec + ei + G::EW), ld1(Em + ei),
+                                  ld1(Ep + ei), w);
+            else
+                eta_stencil(d, x, y, kt, ld1(Ec + ei), ld1(Ec + ei - 1), ld1(Ec + ei + 1),
+                            ld1(Ec + ei - G::EW), ld1(Ec + ei + G::EW), ld1(Em + ei), ld1(Ep + ei),
+                            w);
+            const int ui = (rt + 1) * G::UC + jt;  // u' column of m - 1
+            float s = w.xm * Uc[ui + pr];
+            s += w.xp * Uc[ui + 1 + pr];
+            s += w.ym * Uc[ui + 1 - G::UC];
+            s += w.yp * Uc[ui + 1 + G::UC];
+            s += w.zm * Um[ui + 1];
+            s += w.zp * Up[ui + 1];
+            t = s * rcp_approx(w.D);
+        }
+        Tt[rt * G::TC + jt] = t;
+    };
+
     auto consume = [&](int in) {
         auto acquire = [&]() -> bool {
             const int q = nc++;
@@ -214,119 +275,115 @@ __global__ void __launch_bounds__(32 * (TYT + 1), 2) k_rb_ws(PcgArgs a) {
             if (!s_member[l]) continue;
             const bool work = s_sol[l].done == RUNNING;
             const Dims d = s_sol[l].d;
+            const LocalSolveRB& Ls = s_sol[l];
             const int nxh = d.nx >> 1;
-            const float al = (float)s_sol[l].alpha, be = (float)s_sol[l].beta;
-            const bool xs = !s_sol[l].first;
+            const float al = (float)Ls.alpha, be = (float)Ls.beta;
+            const bool xs = !Ls.first;
             const int L = sg.k1 - sg.k0;
+            // the tile, its two rings of u' and the neighbours of its ring of t inside the grid
+            const bool inner = sg.x0 >= 4 && sg.x0 + G::W + 4 <= d.nx && sg.y0 >= 3 &&
+                               sg.y0 + G::HT + 3 <= d.ny;
             const int p0 = nc;  // sequence number of plane k0 - 2
             float ag = 0.f, ad = 0.f, ar = 0.f;
-            for (int off = 0; off < L + 4; ++off) {
+            for (int off = 0; off < L + 6; ++off) {
                 const int q = sg.k0 - 2 + off, qs = p0 + off;
-                const bool ok = acquire();
+                const bool arrives = off < L + 4;
+                const bool ok = arrives ? acquire() : !s_fail;
                 if (ok && work) {
-                    // step 1: u' of plane q on the black cells of the tile and two rings
-                    const unsigned char* S = stage(qs);
-                    const float* Su = (const float*)(S + G::U);
-                    const float* Ss = (const float*)(S + G::S);
-                    const float* Sw = (const float*)(S + G::WV);
-                    float* Uq = Ur + ring4(q) * G::UPL;
-                    for (int e = tid; e < G::UH * (G::WB + 2); e += NC) {
-                        const int r = e / (G::WB + 2), mm = e - r * (G::WB + 2) - 1;
-                        const int par = (sg.y0 - 2 + r + q + 1) & 1;  // black: i + j + k odd
-                        const int si = r * G::VW + G::VOFF + mm;
-                        Uq[r * G::UW + 2 * mm + par + 2] = u_next_rb(Su[si], Ss[si], Sw[si], al, be);
-                    }
-                }
-                named_sync(1, NC);
-                if (ok && work && q >= sg.k0) {
-                    // step 2: t = D_r^-1 sum beta u' of plane kt = q - 1 on the red cells of the
-                    // tile and one ring (0 outside the grid)
-                    const int kt = q - 1;
-                    const float* Um = Ur + ring4(kt - 1) * G::UPL;
-                    const float* Uc = Ur + ring4(kt) * G::UPL;
-                    const float* Up = Ur + ring4(kt + 1) * G::UPL;
-                    const E* Em = (const E*)(stage(qs - 2) + G::ETA);
-                    const E* Ec = (const E*)(stage(qs - 1) + G::ETA);
-                    const E* Ep = (const E*)(stage(qs) + G::ETA);
-                    float* Tt = Tr + ring4(kt) * G::TPL;
-                    for (int e = tid; e < G::TH * (G::WB + 1); e += NC) {
-                        const int r = e / (G::WB + 1), hh = e - r * (G::WB + 1);
-                        const int y = sg.y0 - 1 + r;
-                        const int c = 2 * hh + ((sg.x0 - 1 + y + kt) & 1);  // red: i + j + k even
-                        const int x = sg.x0 - 1 + c;
-                        float t = 0.f;
-                        if (x >= 0 && x < d.nx && y >= 0 && y < d.ny && kt >= 0 && kt < d.nz) {
-                            const int ei = (r + 1) * G::EW + c - 1 + G::EOFF;
-                            Stencil<float> w;
-                            eta_stencil(d, x, y, kt, ld1(Ec + ei), ld1(Ec + ei - 1), ld1(Ec + ei + 1),
-                                        ld1(Ec + ei - G::EW), ld1(Ec + ei + G::EW), ld1(Em + ei),
-                                        ld1(Ep + ei), w);
-                            const int ui = (r + 1) * G::UW + c + 1;
-                            float s = w.xm * Uc[ui - 1];
-                            s += w.xp * Uc[ui + 1];
-                            s += w.ym * Uc[ui - G::UW];
-                            s += w.yp * Uc[ui + G::UW];
-                            s += w.zm * Um[ui];
-                            s += w.zp * Up[ui];
-                            t = s * rcp_approx(w.D);
+                    // Steps 1 and 2 are spread over all consumer threads by flat element index
+                    // (consecutive threads on consecutive columns); step 2 from the first thread
+                    // and step 1 from the last, so the threads left with one t fewer take the
+                    // extra u' values.
+                    if (arrives) {
+                        // step 1: u' of plane q on the tile and two rings
+                        const unsigned char* S = stage(qs);
+                        float* Uq = Ur + ring(q, G::RINGU) * G::UPL;
+                        for (int e = NC - 1 - tid; e < G::UPL; e += NC) {
+                            const int r = e / G::UC;
+                            step1(S, Uq, al, be, r, e - r * G::UC);
                         }
-                        Tt[r * G::TW + c] = t;
+                    }
+                    const int kt = q - 2;
+                    if (off >= 3 && off <= L + 4) {
+                        // step 2: t of plane kt = q - 2 on the red cells of the tile and one ring
+                        float* Tt = Tr + ring(kt, G::RINGT) * G::TPL;
+                        if (kt < 0 || kt >= d.nz) {
+                            for (int e = tid; e < G::TPL; e += NC) Tt[e] = 0.f;
+                        } else {
+                            const float* Um = Ur + ring(kt - 1, G::RINGU) * G::UPL;
+                            const float* Uc = Ur + ring(kt, G::RINGU) * G::UPL;
+                            const float* Up = Ur + ring(kt + 1, G::RINGU) * G::UPL;
+                            const E* Em = (const E*)(stage(qs - 3) + G::ETA);
+                            const E* Ec = (const E*)(stage(qs - 2) + G::ETA);
+                            const E* Ep = (const E*)(stage(qs - 1) + G::ETA);
+                            for (int e = tid; e < G::TPL; e += NC) {
+                                const int rt = e / G::TC;
+                                step2(d, sg, inner, kt, Em, Ec, Ep, Um, Uc, Up, Tt, rt,
+                                      e - rt * G::TC);
+                            }
+                        }
+                    }
+                    const int k = q - 4;
+                    if (off >= 6) {
+                        // step 3: S u' of plane k = q - 4 on the tile's black cells and updates
+                        const unsigned char* S = stage(qs - 4);
+                        const float* Su = (const float*)(S + G::U);
+                        const float* Ss = (const float*)(S + G::S);
+                        const float* Sw = (const float*)(S + G::WV);
+                        const float* Sx = (const float*)(S + G::X);
+                        const float* Sp = (const float*)(S + G::P);
+                        const E* Em = (const E*)(stage(qs - 5) + G::ETA);
+                        const E* Ec = (const E*)(S + G::ETA);
+                        const E* Ep = (const E*)(stage(qs - 3) + G::ETA);
+                        const float* Tm = Tr + ring(k - 1, G::RINGT) * G::TPL;
+                        const float* Tc = Tr + ring(k, G::RINGT) * G::TPL;
+                        const float* Tp = Tr + ring(k + 1, G::RINGT) * G::TPL;
+                        const float* Uc = Ur + ring(k, G::RINGU) * G::UPL;
+                        const int m = sg.x0 / 2 + lane;
+                        for (int r = warp; r < G::HT; r += TYT) {
+                            const int y = sg.y0 + r;
+                            if (!inner && (y >= d.ny || m >= nxh)) continue;
+                            const int pb = (y + k + 1) & 1;  // black: i = 2m + pb
+                            const int ei = (r + 2) * G::EW + 2 * lane + pb + G::EOFF;
+                            Stencil<float> w;
+                            if (inner)
+                                eta_stencil_inner(d, k, ld1(Ec + ei), ld1(Ec + ei - 1),
+                                                  ld1(Ec + ei + 1), ld1(Ec + ei - G::EW),
+                                                  ld1(Ec + ei + G::EW), ld1(Em + ei),
+                                                  ld1(Ep + ei), w);
+                            else
+                                eta_stencil(d, sg.x0 + 2 * lane + pb, y, k, ld1(Ec + ei),
+                                            ld1(Ec + ei - 1), ld1(Ec + ei + 1),
+                                            ld1(Ec + ei - G::EW), ld1(Ec + ei + G::EW),
+                                            ld1(Em + ei), ld1(Ep + ei), w);
+                            const int ti = (r + 1) * G::TC + lane;  // t column of m - 1
+                            float s = w.xm * Tc[ti + pb];
+                            s += w.xp * Tc[ti + 1 + pb];
+                            s += w.ym * Tc[ti + 1 - G::TC];
+                            s += w.yp * Tc[ti + 1 + G::TC];
+                            s += w.zm * Tm[ti + 1];
+                            s += w.zp * Tp[ti + 1];
+                            const float ub = Uc[(r + 2) * G::UC + lane + 2];
+                            const float su = w.D * ub - s;
+                            const int si = (r + 2) * G::VW + G::VOFF + lane;
+                            const float pn = __fmaf_rn(be, Sp[r * G::WB + lane], Su[si]);
+                            const float sn = __fmaf_rn(be, Ss[si], Sw[si]);
+                            const float wn = su * rcp_approx(w.D);
+                            const size_t cb = (size_t)m + (size_t)nxh * (y + (size_t)d.ny * k);
+                            if (xs) Ls.x[cb] = __fmaf_rn(al, pn, Sx[r * G::WB + lane]);
+                            Ls.p[cb] = pn;
+                            Ls.u[out][cb] = ub;
+                            Ls.s[out][cb] = sn;
+                            Ls.w[out][cb] = wn;
+                            const float du = w.D * ub;
+                            ag += du * ub;
+                            ad += su * ub;
+                            ar += du * du;
+                        }
                     }
                 }
                 named_sync(1, NC);
-                if (ok && work && q >= sg.k0 + 2) {
-                    // step 3: S u' of plane k = q - 2 on the tile's black cells and the updates
-                    const int k = q - 2;
-                    const unsigned char* S = stage(qs - 2);
-                    const float* Su = (const float*)(S + G::U);
-                    const float* Ss = (const float*)(S + G::S);
-                    const float* Sw = (const float*)(S + G::WV);
-                    const float* Sx = (const float*)(S + G::X);
-                    const float* Sp = (const float*)(S + G::P);
-                    const E* Em = (const E*)(stage(qs - 3) + G::ETA);
-                    const E* Ec = (const E*)(S + G::ETA);
-                    const E* Ep = (const E*)(stage(qs - 1) + G::ETA);
-                    const float* Tm = Tr + ring4(k - 1) * G::TPL;
-                    const float* Tc = Tr + ring4(k) * G::TPL;
-                    const float* Tp = Tr + ring4(k + 1) * G::TPL;
-                    const float* Uc = Ur + ring4(k) * G::UPL;
-                    const LocalSolveRB& Ls = s_sol[l];
-                    for (int e = tid; e < G::HT * G::WB; e += NC) {
-                        const int r = e / G::WB, mm = e - r * G::WB;
-                        const int y = sg.y0 + r, m = sg.x0 / 2 + mm;
-                        if (y >= d.ny || m >= nxh) continue;
-                        const int xr = 2 * mm + ((y + k + 1) & 1);  // column within the tile
-                        const int ei = (r + 2) * G::EW + xr + G::EOFF;
-                        Stencil<float> w;
-                        eta_stencil(d, sg.x0 + xr, y, k, ld1(Ec + ei), ld1(Ec + ei - 1),
-                                    ld1(Ec + ei + 1), ld1(Ec + ei - G::EW), ld1(Ec + ei + G::EW),
-                                    ld1(Em + ei), ld1(Ep + ei), w);
-                        const int ti = (r + 1) * G::TW + xr + 1;
-                        float s = w.xm * Tc[ti - 1];
-                        s += w.xp * Tc[ti + 1];
-                        s += w.ym * Tc[ti - G::TW];
-                        s += w.yp * Tc[ti + G::TW];
-                        s += w.zm * Tm[ti];
-                        s += w.zp * Tp[ti];
-                        const float ub = Uc[(r + 2) * G::UW + xr + 2];
-                        const float su = w.D * ub - s;
-                        const int si = (r + 2) * G::VW + G::VOFF + mm;
-                        const float pn = __fmaf_rn(be, Sp[r * G::WB + mm], Su[si]);
-                        const float sn = __fmaf_rn(be, Ss[si], Sw[si]);
-                        const float wn = su * rcp_approx(w.D);
-                        const size_t cb = (size_t)m + (size_t)nxh * (y + (size_t)d.ny * k);
-                        if (xs) Ls.x[cb] = __fmaf_rn(al, pn, Sx[r * G::WB + mm]);
-                        Ls.p[cb] = pn;
-                        Ls.u[out][cb] = ub;
-                        Ls.s[out][cb] = sn;
-                        Ls.w[out][cb] = wn;
-                        const float du = w.D * ub;
-                        ag += du * ub;
-                        ad += su * ub;
-                        ar += du * du;
-                    }
-                }
-                if (off >= 3) release(qs - 3);
+                if (off >= 5) release(qs - 5);
             }
             release(p0 + L + 1);
             release(p0 + L + 2);

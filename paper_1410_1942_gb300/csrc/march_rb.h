@@ -6,9 +6,9 @@
 namespace pcg {
 
 // Kernels of the red-black family (variant family 3): (CX, CY, TYT, NS) of each instantiation;
-// tile 32 CX x CY TYT cells (full resolution), TYT consumer warps and a producer warp, an
-// NS-stage ring (at least 5).
-#define RB_CONFIGS(X) X(2, 2, 4, 6) X(2, 2, 4, 5) X(2, 2, 8, 5)
+// tile 64 x CY TYT cells (full resolution; CX = 2: one lane per compressed column), TYT consumer
+// warps and a producer warp, an NS-stage ring (at least 7).
+#define RB_CONFIGS(X) X(2, 2, 4, 8) X(2, 2, 4, 7) X(2, 1, 8, 8) X(2, 2, 8, 7)
 Cg1Kernel rb_kernel(int cx, int cy, int tyt, int ns);  // null kernels if not instantiated
 
 // Start of an inner solve on the black Schur complement: from the full-size right side r, the

@@ -82,9 +82,10 @@ def test_rb_solve_matches_oracle(name, prec, walls):
     _check(c, op, b, xref, p, st, c.tol)
 
 
-# every red-black variant (64x8 tiles with 6- or 5-stage rings, 64x16 tiles) and split
-@pytest.mark.parametrize("tile", [30612204, 31612204, 32612204, 30512204, 32512204, 30512208,
-                                  32512208])
+# every red-black variant (64x8 tiles with 4 or 8 consumer warps and 8- or 7-stage rings, 64x16
+# tiles) and split
+@pytest.mark.parametrize("tile", [30812204, 31812204, 32812204, 30712204, 32712204, 30812108,
+                                  32812108, 30712208, 32712208])
 @pytest.mark.parametrize("name", ["strut", "ragged"])
 def test_rb_variants_match_oracle(tile, name):
     c = _case(name)
@@ -155,7 +156,7 @@ def test_rb_warm_start_and_zero_source():
 
 def test_family3_tiles_need_the_rbssor_preconditioner():
     with pytest.raises(capi.PoissonError) as e:
-        capi.Poisson(64, 32, 16, 1.0 / 16, precision="fp32", tile=30612204)
+        capi.Poisson(64, 32, 16, 1.0 / 16, precision="fp32", tile=30812204)
     assert e.value.status == capi.EINVAL
     # omega != 1, FP64 and periodic x keep the column kernels
     for kw in ({"omega": 1.3}, {"precision": "fp64"}, {"periodic_x": True}):

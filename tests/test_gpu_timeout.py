@@ -29,7 +29,7 @@ def _lib():
 # one-sweep (producer warp, lockstep split), two-sweep with a producer warp, two-sweep without,
 # and the red-black SSOR kernel
 @pytest.mark.parametrize("tile,precond", [(12012204, "jacobi"), (12204, "jacobi"),
-                                          (2204, "jacobi"), (32612204, "rbssor")])
+                                          (2204, "jacobi"), (32812204, "rbssor")])
 def test_unreachable_barrier_times_out_and_the_handle_recovers(tile, precond):
     c = inputs.strut_case(64, 32, 32, seed=2)
     g = c.grid
