@@ -534,8 +534,11 @@ def served(nreq, seed=0):
     rate = 0.7 * cap["solves_per_s"] / 20.0
     st = serve.Server(budget, steps=20).serve(serve.request_stream(nreq, rate, seed=seed))
     cap64 = serve.Server(budget, precision="fp64", steps=6).serve(cap_stream())
-    # the same capacity stream with the multigrid preconditioner (unbatched handles)
+    # the same capacity stream and the same open-loop stream with the multigrid preconditioner
+    # (unbatched handles)
     capmg = serve.Server(budget, steps=6, precond="mg").serve(cap_stream())
+    stmg = serve.Server(budget, steps=20, precond="mg").serve(
+        serve.request_stream(nreq, rate, seed=seed))
     return {"capacity_solves_per_s": cap["solves_per_s"], "arrival_rate_per_s": rate,
             "solves_per_s": st["solves_per_s"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
             "solves": st["solves"], "requests": nreq, "steps_per_request": 20,
@@ -547,7 +550,11 @@ def served(nreq, seed=0):
             "fp64_all_ok": cap64["all_ok"],
             "mixed_vs_fp64_capacity_ratio": cap["solves_per_s"] / cap64["solves_per_s"],
             "mg_capacity_solves_per_s": capmg["solves_per_s"],
-            "mg_max_rel_residual": capmg["max_rel_residual"], "mg_all_ok": capmg["all_ok"]}
+            "mg_max_rel_residual": max(capmg["max_rel_residual"], stmg["max_rel_residual"]),
+            "mg_all_ok": capmg["all_ok"] and stmg["all_ok"],
+            "mg_open_loop": {"solves_per_s": stmg["solves_per_s"], "p50_ms": stmg["p50_ms"],
+                             "p99_ms": stmg["p99_ms"], "peak_active": stmg["peak_active"]},
+            "served_tile": serve.SERVE_TILE}
 
 
 def cpu_baseline(F, s, g, kind, seconds, precond):

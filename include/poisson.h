@@ -52,7 +52,7 @@ extern "C" {
 #define POISSON_ETIMEOUT (-5)        /* a device-side wait exceeded its deadline */
 #define POISSON_ENOTREADY (-6)       /* solve before set_density */
 #define POISSON_ECUDA (-7)           /* a CUDA runtime call failed */
-#define POISSON_ENOMEM_BUDGET (-8)   /* admission refused: over the device-memory budget */
+#define POISSON_ENOMEM_BUDGET (-8)   /* poisson_required_bytes: over the device-memory budget */
 #define POISSON_ENOTICKET (-9)       /* poisson_poll: unknown or already collected ticket */
 #define POISSON_ETOOLARGE (-10)      /* poisson_residual_noalloc: grid beyond its static scratch */
 
@@ -133,6 +133,23 @@ int poisson_create(int nx, int ny, int nz, double h, const poisson_opts* opts, p
 
 /* Release the handle and its device memory (after synchronising its stream).  NULL is a no-op. */
 int poisson_destroy(poisson_t* h);
+
+/* ------------------------------------------------------------------ device-memory budget
+ * For admission by a device-memory budget (a served request loop creates handles as memory
+ * frees up).  poisson_required_bytes: the device bytes a handle of this grid and these options
+ * (NULL = defaults) holds once poisson_create has returned -- its arrays, its multigrid hierarchy
+ * (POISSON_MG), and an upper bound on its persistent-launch plan -- counted from the same list of
+ * arrays that poisson_create allocates; the caller's own arrays are not included.  budget > 0:
+ * returns POISSON_ENOMEM_BUDGET when the bytes exceed it (*bytes is still set); budget 0: no
+ * check.  No device memory is touched.  Errors: EINVAL (NULL bytes, bad sizes or options as for
+ * poisson_create). */
+int poisson_required_bytes(int nx, int ny, int nz, const poisson_opts* opts, uint64_t budget,
+                           uint64_t* bytes);
+
+/* The device bytes the handle holds now: the arrays of poisson_required_bytes (its plan at its
+ * actual size) plus what later calls added (cut-cell fractions, staging buffers of the checking
+ * entry points given host arrays).  Errors: EINVAL. */
+int poisson_handle_bytes(poisson_t* h, uint64_t* bytes);
 
 /* Set the density from the water fraction F (eq. (density), rho = rho_air + F (rho_water -
  * rho_air)) and build the operator: face coefficients (harmonic means), diagonal, and the

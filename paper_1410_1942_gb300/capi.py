@@ -32,7 +32,8 @@ EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson
            "poisson_batch_submit", "poisson_poll", "poisson_kernel_launches", "poisson_profile",
            "poisson_profile_read", "poisson_describe", "poisson_residual_noalloc",
            "poisson_divergence", "poisson_project", "poisson_set_apertures", "poisson_strerror",
-           "poisson_version", "poisson_test_unreachable_barrier", "poisson_hydrostatic_force"]
+           "poisson_version", "poisson_test_unreachable_barrier", "poisson_hydrostatic_force",
+           "poisson_required_bytes", "poisson_handle_bytes"]
 K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER, K_PCG = 0, 1, 2, 3, 4
 K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 
@@ -112,6 +113,11 @@ def load(path=None):
     lib.poisson_project.restype = i
     lib.poisson_set_apertures.argtypes = [vp, vp, vp, vp, vp, i]
     lib.poisson_set_apertures.restype = i
+    lib.poisson_required_bytes.argtypes = [i, i, i, ctypes.POINTER(Opts), ctypes.c_uint64,
+                                           ctypes.POINTER(ctypes.c_uint64)]
+    lib.poisson_required_bytes.restype = i
+    lib.poisson_handle_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
+    lib.poisson_handle_bytes.restype = i
     lib.poisson_hydrostatic_force.argtypes = [vp, vp, d, d, d, d, d, vp, vp, vp]
     lib.poisson_hydrostatic_force.restype = i
     lib.poisson_test_unreachable_barrier.argtypes = [vp, i]
@@ -157,6 +163,28 @@ def default_opts():
     return o
 
 
+def make_opts(precision="fp32", precond="jacobi", omega=1.0, max_iters=20000, inner_tol=1e-4,
+              tile=0, stream=None, dirichlet_walls=0, periodic_x=False):
+    o = default_opts()
+    o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    o.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
+    o.omega, o.max_iters, o.inner_tol, o.tile = omega, max_iters, inner_tol, tile
+    o.stream = stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream
+    o.dirichlet_walls = dirichlet_walls
+    o.periodic_x = 1 if periodic_x else 0
+    return o
+
+
+def required_bytes(nx, ny, nz, budget=0, **opts):
+    """(status, bytes): the device bytes a handle of this grid and options would hold, and
+    ENOMEM_BUDGET when they exceed ``budget`` (> 0); OK otherwise."""
+    b = ctypes.c_uint64(0)
+    rc = load().poisson_required_bytes(nx, ny, nz, ctypes.byref(make_opts(**opts)),
+                                       ctypes.c_uint64(int(budget)), ctypes.byref(b))
+    _check(rc, "poisson_required_bytes", ok=(OK, ENOMEM_BUDGET))
+    return rc, int(b.value)
+
+
 class Poisson:
     """One grid: ``poisson_create`` ... ``poisson_destroy``."""
 
@@ -164,13 +192,8 @@ class Poisson:
                  max_iters=20000, inner_tol=1e-4, tile=0, stream=None, dirichlet_walls=0,
                  periodic_x=False):
         lib = load()
-        o = default_opts()
-        o.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
-        o.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
-        o.omega, o.max_iters, o.inner_tol, o.tile = omega, max_iters, inner_tol, tile
-        o.stream = stream if (stream is None or isinstance(stream, int)) else stream.cuda_stream
-        o.dirichlet_walls = dirichlet_walls
-        o.periodic_x = 1 if periodic_x else 0
+        o = make_opts(precision, precond, omega, max_iters, inner_tol, tile, stream,
+                      dirichlet_walls, periodic_x)
         self.shape = (nz, ny, nx)
         self.h = h
         self.opts = o
@@ -231,6 +254,12 @@ class Poisson:
         CTAs more than they launch (0 restores), so a solve ends with ETIMEOUT."""
         _check(load().poisson_test_unreachable_barrier(self._h, int(extra)),
                "poisson_test_unreachable_barrier")
+
+    def device_bytes(self):
+        """Device bytes the handle holds (poisson_handle_bytes)."""
+        b = ctypes.c_uint64(0)
+        _check(load().poisson_handle_bytes(self._h, ctypes.byref(b)), "poisson_handle_bytes")
+        return int(b.value)
 
     def describe(self):
         buf = ctypes.create_string_buffer(256)

@@ -418,10 +418,11 @@ static void free_state(poisson_t* H) {
     mg_free(&H->mg);
 }
 
-extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_opts* opts,
-                              poisson_t** out) {
-    if (!out || nx <= 0 || ny <= 0 || nz <= 0 || !(h > 0.0) || !std::isfinite(h))
-        return POISSON_EINVAL;
+// The options of a new handle (defaults for NULL) and its grid, checked; POISSON_EINVAL if any is
+// out of range.
+static int check_create(int nx, int ny, int nz, const poisson_opts* opts, poisson_opts* out,
+                        Dims* out_dims) {
+    if (nx <= 0 || ny <= 0 || nz <= 0) return POISSON_EINVAL;
     const long long n = (long long)nx * ny * nz;
     if (n >= (1LL << 31)) return POISSON_EINVAL;
     poisson_opts o;
@@ -450,6 +451,82 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
         MgHier probe;
         if (mg_plan(dims, &probe) < 2) return POISSON_EINVAL;
     }
+    *out = o;
+    *out_dims = dims;
+    return POISSON_OK;
+}
+
+// Reduction partial slots of one column-kernel launch of the handle's grid.
+static size_t column_blocks(const Dims& d, int kc) {
+    const dim3 g((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY, (d.nz + kc - 1) / kc);
+    return (size_t)g.x * g.y * g.z;
+}
+
+// Every device array a handle allocates at creation, in allocation order: f(&pointer, count,
+// element size).  poisson_create allocates with this list and poisson_required_bytes counts it,
+// so the two cannot drift apart.
+template <typename F>
+static void for_each_array(poisson_t* H, F&& f) {
+    const Dims& d = H->d;
+    const poisson_opts& o = H->opts;
+    const size_t N = (size_t)d.n, D8 = sizeof(double), F4 = sizeof(float);
+    f((void**)&H->bx, N, D8); f((void**)&H->by, N, D8); f((void**)&H->bz, N, D8);
+    f((void**)&H->diag, N, D8);
+    f((void**)&H->top64, (size_t)d.sxy, D8);
+    if (o.periodic_x && o.precision != POISSON_FP64 && d.nx % 8 == 0) {
+        // padded rows for the one-sweep marching kernels (ghost columns, PAD_V each side)
+        const size_t np = (size_t)(d.nx + 2 * PAD_V) * d.ny * d.nz;
+        for (int b = 0; b < 2; ++b) {
+            f((void**)&H->pu[b], np, F4); f((void**)&H->ps[b], np, F4);
+            f((void**)&H->pw[b], np, F4);
+        }
+        if (o.precision == POISSON_FP32)
+            f((void**)&H->peta32, (size_t)(d.nx + 8) * d.ny * d.nz, F4);
+        else
+            f((void**)&H->peta16, (size_t)(d.nx + 16) * d.ny * d.nz, sizeof(__nv_bfloat16));
+    }
+    if (o.dirichlet_walls) f((void**)&H->rinv2, N, D8);  // (not needed for periodic x)
+    f((void**)&H->eta32, N, F4); f((void**)&H->eta16, N, sizeof(__nv_bfloat16));
+    f((void**)&H->x64, N, D8); f((void**)&H->b64, N, D8);
+    if (o.precision == POISSON_FP64) {
+        f((void**)&H->dinv, N, D8);
+        f((void**)&H->r64, N, D8); f((void**)&H->z64, N, D8); f((void**)&H->p64a, N, D8);
+        f((void**)&H->p64b, N, D8);
+    } else {
+        for (float** q : {&H->d32, &H->r32, &H->z32, &H->p32a, &H->p32b, &H->s32a, &H->s32b,
+                          &H->w32a, &H->w32b})
+            f((void**)q, N, F4);
+    }
+    f((void**)&H->sc, 1, sizeof(Scalars));
+    f((void**)&H->partials, std::max<size_t>(2 * H->nblocks + 64, 4096), D8);
+}
+
+// Device bytes of the multigrid hierarchy of a planned MgHier (the fine pre-smoothed vector and
+// seven arrays per coarse cell).
+static size_t mg_bytes(const MgHier& m, bool dbl) {
+    const size_t es = dbl ? sizeof(double) : sizeof(float);
+    size_t b = es * (size_t)m.d[0].n;
+    for (int l = 1; l < m.nlev; ++l) b += 7 * es * (size_t)m.d[l].n;
+    return b;
+}
+
+// Upper bound on the persistent-launch plan of one handle (work list, tensor maps, partial
+// sums, control words): MAXSEG segments per CTA, at most 8 resident CTAs per SM.
+static size_t plan_bytes_max() {
+    const size_t ctas = 8 * (size_t)num_sms();
+    const size_t segs = ctas * MAXSEG;
+    return sizeof(SolveDev) + segs * (sizeof(Seg) + 4 * sizeof(float2)) +
+           (ctas + 1) * sizeof(int) + MAPS_PER_SOLVE * sizeof(CUtensorMap) + sizeof(MarchCtl) +
+           4096;
+}
+
+extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_opts* opts,
+                              poisson_t** out) {
+    if (!out || !(h > 0.0) || !std::isfinite(h)) return POISSON_EINVAL;
+    poisson_opts o;
+    Dims dims;
+    const int cr = check_create(nx, ny, nz, opts, &o, &dims);
+    if (cr != POISSON_OK) return cr;
 
     poisson_t* H = new (std::nothrow) poisson_t();
     if (!H) return POISSON_ENOMEM;
@@ -459,40 +536,24 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
     H->st = (cudaStream_t)o.stream;
     H->kc = choose_kc(H->d);
     cudaGetDevice(&H->device);
-    const dim3 g((nx + TX - 1) / TX, (ny + TY - 1) / TY, (nz + H->kc - 1) / H->kc);
-    H->nblocks = (size_t)g.x * g.y * g.z;
+    H->nblocks = column_blocks(H->d, H->kc);
 
     int rc = POISSON_OK;
     auto A = [&](int r) { if (rc == POISSON_OK) rc = r; };
-    const size_t N = (size_t)n;
-    A(dalloc(&H->bx, N)); A(dalloc(&H->by, N)); A(dalloc(&H->bz, N)); A(dalloc(&H->diag, N));
-    A(dalloc(&H->top64, (size_t)nx * ny));
-    if (o.periodic_x && o.precision != POISSON_FP64 && nx % 8 == 0) {
-        // padded rows for the one-sweep marching kernels (ghost columns, PAD_V each side)
-        const size_t np = (size_t)(nx + 2 * PAD_V) * ny * nz;
-        for (int b = 0; b < 2; ++b) {
-            A(dalloc(&H->pu[b], np)); A(dalloc(&H->ps[b], np)); A(dalloc(&H->pw[b], np));
+    for_each_array(H, [&](void** p, size_t count, size_t es) {
+        if (rc != POISSON_OK) return;
+        *p = nullptr;
+        if (count == 0) return;
+        if (cudaMalloc(p, es * count) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            rc = POISSON_ENOMEM;
         }
-        if (o.precision == POISSON_FP32) A(dalloc(&H->peta32, (size_t)(nx + 8) * ny * nz));
-        else A(dalloc(&H->peta16, (size_t)(nx + 16) * ny * nz));
-    }
-    if (o.dirichlet_walls) A(dalloc(&H->rinv2, N));  // (not needed for periodic x)
-    A(dalloc(&H->eta32, N)); A(dalloc(&H->eta16, N));
-    A(dalloc(&H->x64, N)); A(dalloc(&H->b64, N));
-    if (o.precision == POISSON_FP64) {
-        A(dalloc(&H->dinv, N));
-        A(dalloc(&H->r64, N)); A(dalloc(&H->z64, N)); A(dalloc(&H->p64a, N)); A(dalloc(&H->p64b, N));
-    } else {
-        A(dalloc(&H->d32, N)); A(dalloc(&H->r32, N)); A(dalloc(&H->z32, N));
-        A(dalloc(&H->p32a, N)); A(dalloc(&H->p32b, N));
-        A(dalloc(&H->s32a, N)); A(dalloc(&H->s32b, N)); A(dalloc(&H->w32a, N)); A(dalloc(&H->w32b, N));
-    }
+    });
     if (o.precond == POISSON_MG && rc == POISSON_OK) {
         mg_plan(H->d, &H->mg);
         A(mg_alloc(&H->mg, o.precision == POISSON_FP64));
     }
-    A(dalloc(&H->sc, 1));
-    A(dalloc(&H->partials, std::max<size_t>(2 * H->nblocks + 64, 4096)));
     if (rc == POISSON_OK && cudaMallocHost((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
         cudaGetLastError();
         H->sc_host = nullptr;
@@ -528,6 +589,51 @@ extern "C" int poisson_destroy(poisson_t* H) {
     cudaStreamSynchronize(H->st);
     free_state(H);
     delete H;
+    return POISSON_OK;
+}
+
+extern "C" int poisson_required_bytes(int nx, int ny, int nz, const poisson_opts* opts,
+                                      uint64_t budget, uint64_t* bytes) {
+    if (!bytes) return POISSON_EINVAL;
+    poisson_opts o;
+    Dims dims;
+    const int cr = check_create(nx, ny, nz, opts, &o, &dims);
+    if (cr != POISSON_OK) return cr;
+    poisson_t probe;
+    probe.d = dims;
+    probe.opts = o;
+    probe.nblocks = column_blocks(dims, choose_kc(dims));
+    size_t b = 0;
+    for_each_array(&probe, [&](void**, size_t count, size_t es) { b += count * es; });
+    if (o.precond == POISSON_MG) {
+        MgHier m;
+        mg_plan(dims, &m);
+        b += mg_bytes(m, o.precision == POISSON_FP64);
+    }
+    if (o.precision != POISSON_FP64) b += plan_bytes_max();
+    *bytes = (uint64_t)b;
+    return (budget > 0 && b > budget) ? POISSON_ENOMEM_BUDGET : POISSON_OK;
+}
+
+extern "C" int poisson_handle_bytes(poisson_t* H, uint64_t* bytes) {
+    if (!H || !bytes) return POISSON_EINVAL;
+    size_t b = 0;
+    poisson_t* Hc = H;
+    for_each_array(Hc, [&](void** p, size_t count, size_t es) { b += (*p) ? count * es : 0; });
+    if (H->mg.nlev >= 2) b += mg_bytes(H->mg, H->mg.dbl);
+    const MarchPlan& pl = H->plan;
+    b += pl.cap_solves + pl.cap_segs + pl.cap_cta + pl.cap_maps + pl.cap_pa + pl.cap_pb + pl.cap_ctl;
+    const size_t n = (size_t)H->d.n, nu = (size_t)(H->d.nx + 1) * H->d.ny * H->d.nz,
+                 nv = (size_t)H->d.nx * (H->d.ny + 1) * H->d.nz,
+                 nw = (size_t)H->d.sxy * (H->d.nz + 1);
+    if (H->ax64) b += sizeof(double) * (nu + nv + nw + n);  // cut-cell fractions
+    if (H->bx32) b += 4 * sizeof(float) * n;                 // their FP32 faces and diagonal
+    if (H->io_a) b += sizeof(double) * n;                    // staging of the checking calls
+    if (H->io_b) b += sizeof(double) * n;
+    if (H->io_c) b += sizeof(double) * n;
+    if (H->io_c32) b += sizeof(float) * n;
+    if (H->plan.trace) b += sizeof(unsigned long long) * TRACE_PARTS;
+    *bytes = (uint64_t)b;
     return POISSON_OK;
 }
 

@@ -25,20 +25,24 @@ import numpy as np
 
 from . import capi, inputs
 
-# device bytes per cell of a handle (capi.cu allocations) plus the request's own F, s, p arrays
-HANDLE_BYTES_PER_CELL = {"fp32": 32 + 16 + 6 + 36, "bf16": 32 + 16 + 6 + 36, "fp64": 32 + 16 + 6 + 8 + 32}
-# the multigrid hierarchy: the fine pre-smoothed vector and seven arrays per coarse cell (levels
-# shrink by 8: under 1/7 of the fine count in all), in the handle's inner precision
-MG_BYTES_PER_CELL = {"fp32": 4 + 4, "bf16": 4 + 4, "fp64": 8 + 8}
+# the request's own arrays on the device: F, s, p (FP64)
 REQUEST_BYTES_PER_CELL = 3 * 8
+# kernel variant of served Jacobi handles: the one-sweep persistent kernel, 64x8 tiles, lockstep
+# split (fixed, so admission does not run the autotuner)
+SERVE_TILE = 12012204
 
 
-def request_bytes(shape, precision, precond="jacobi"):
-    n = shape[0] * shape[1] * shape[2]
-    per = HANDLE_BYTES_PER_CELL[precision] + REQUEST_BYTES_PER_CELL
-    if precond == "mg":
-        per += MG_BYTES_PER_CELL[precision]
-    return n * per + (1 << 20)
+def _handle_opts(precision, precond, tile):
+    return {"precision": precision, "precond": precond,
+            "tile": tile if (precision != "fp64" and precond == "jacobi") else 0}
+
+
+def request_bytes(shape, precision, precond="jacobi", tile=SERVE_TILE):
+    """Device bytes of one admitted request: the library's figure for its handle
+    (poisson_required_bytes) plus its F, s and p arrays."""
+    nx, ny, nz = shape
+    _, b = capi.required_bytes(nx, ny, nz, **_handle_opts(precision, precond, tile))
+    return b + REQUEST_BYTES_PER_CELL * nx * ny * nz
 
 
 @dataclasses.dataclass
@@ -63,6 +67,7 @@ class Request:
     statuses: list = dataclasses.field(default_factory=list)
     admitted_at: float = -1.0
     done_at: float = -1.0
+    bytes: int = 0        # device bytes counted against the budget while admitted
 
 
 def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
@@ -81,11 +86,12 @@ def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
 
 class Server:
     def __init__(self, budget_bytes, precision="fp32", tol=1e-9, steps=20, device="cuda",
-                 keep_results=False, tile=12204, precond="jacobi", record_steps=False):
-        # tile: kernel variant of every request's handle (fixed, so admission does not run the
-        # autotuner; the batch executor uses the variant of its largest solve).  precond "mg":
-        # the V-cycle preconditioner; such handles are not batched, the executor solves them one
-        # by one when they are polled.
+                 keep_results=False, tile=SERVE_TILE, precond="jacobi", record_steps=False):
+        # tile: kernel variant of every Jacobi request's handle (fixed, so admission does not run
+        # the autotuner; the batch executor uses the variant of its largest solve).  precond
+        # "mg": the V-cycle preconditioner; such handles are not batched, the executor solves
+        # them one by one when they are polled.  Admission asks the library whether a request's
+        # handle fits the memory left (poisson_required_bytes, POISSON_ENOMEM_BUDGET if not).
         self.tile = tile
         self.precond = precond
         self.budget = int(budget_bytes)
@@ -105,9 +111,8 @@ class Server:
         r.grid, r.F, r.s, r.modes = g, F, s, modes
         import torch
         r.p = torch.zeros(g.shape, dtype=torch.float64, device=self.device)
-        r.solver = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=self.precision,
-                                tile=self.tile if self.precision != "fp64" else 0,
-                                precond=self.precond)
+        r.solver = capi.Poisson(g.nx, g.ny, g.nz, g.h,
+                                **_handle_opts(self.precision, self.precond, self.tile))
         r.solver.set_density(F)
         r.admitted_at = now
         if self.record is not None:
@@ -136,11 +141,16 @@ class Server:
         while pending or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
-                need = request_bytes(pending[0].shape, self.precision, self.precond)
-                if used + need > self.budget and active:
+                nx, ny, nz = pending[0].shape
+                arrays = REQUEST_BYTES_PER_CELL * nx * ny * nz
+                left = self.budget - used - arrays
+                rc, hb = capi.required_bytes(nx, ny, nz, budget=max(1, left),
+                                             **_handle_opts(self.precision, self.precond, self.tile))
+                if (left <= 0 or rc == capi.ENOMEM_BUDGET) and active:
                     break  # wait for memory to free up
                 r = pending.popleft()
-                used += need
+                r.bytes = hb + arrays
+                used += r.bytes
                 self._admit(r, now)
                 active.append(r)
             peak_active = max(peak_active, len(active))
@@ -171,7 +181,7 @@ class Server:
                     r.solver.close()
                     r.solver = None
                     r.F = r.s = r.p = None
-                    used -= request_bytes(r.shape, self.precision, self.precond)
+                    used -= r.bytes
                     active.remove(r)
         wall = time.perf_counter() - t0
         lat = np.array(lat) if lat else np.zeros(1)

@@ -45,6 +45,25 @@ def test_admission_respects_the_memory_budget():
     assert st["peak_active"] < len(reqs)  # some requests waited for memory
 
 
+@pytest.mark.parametrize("kw", [{}, {"precision": "bf16"}, {"precision": "fp64"},
+                                {"precond": "mg"}, {"precond": "rbssor"},
+                                {"periodic_x": True}, {"dirichlet_walls": 31},
+                                {"tile": serve.SERVE_TILE}])
+def test_library_budget_matches_the_handle(kw):
+    """poisson_required_bytes bounds what a created handle holds (its plan is counted at an
+    upper bound, at most a few MiB over) and refuses a budget it exceeds."""
+    for shape in ((96, 48, 40), (64, 32, 32), (40, 23, 19)):
+        rc, need = capi.required_bytes(*shape, **kw)
+        assert rc == capi.OK
+        with capi.Poisson(*shape, 1.0 / shape[2], **kw) as s:
+            have = s.device_bytes()
+        assert have <= need <= have + (4 << 20), (shape, kw, need, have)
+        rc, _ = capi.required_bytes(*shape, budget=need - 1, **kw)
+        assert rc == capi.ENOMEM_BUDGET
+        rc, _ = capi.required_bytes(*shape, budget=need, **kw)
+        assert rc == capi.OK
+
+
 def test_every_served_solve_matches_the_oracle():
     """Continuous batching with requests overlapping on the device: the result of every step of
     every request (its own density, its drifted source, warm-started from the previous step's
