@@ -617,6 +617,9 @@ def extras_for(kind, args, F_d, s_d, g, stream, flush):
         with handle(g, precision="fp32", precond="mg", inner_tol=1e-5) as sv:
             out["wedge_mg"] = solver_line(sv, F_d, s_d, g, few, 1, stream, "fp32", "mg", kind,
                                           flush)
+        with handle(g, precision="fp32", precond="rbssor") as sv:
+            out["wedge_rbssor"] = solver_line(sv, F_d, s_d, g, few, 1, stream, "fp32", "rbssor",
+                                              kind, flush)
         torch.cuda.empty_cache()
         gs, Fs, ss, _ = make_fields("strut", SHAPES["strut"], args.seed, F_d.device)
     else:
