@@ -99,9 +99,11 @@ typedef struct {
                           sweep per iteration (Chronopoulos-Gear recurrences): 12204, 312204,
                           312208 (plus 10000000); F = 2, one sweep with A p formed in it (2-cell
                           halos, u, p, x and eta in memory): 12204, 512204, 12208 (plus
-                          20000000).  P = split of the tile columns over the CTAs:
-                          0 equal planes per CTA, 1 balanced (segment start cost counted), 2
-                          lockstep (neighbouring tiles on the same planes) (default 0)          */
+                          20000000); F = 3, red-black SSOR in reduced form (RBSSOR handles
+                          only): 812204, 712204, 812108, 712208.  P = split of the tile columns
+                          over the CTAs: 0 equal planes per CTA, 1 balanced (segment start cost
+                          counted), 2 lockstep (neighbouring tiles on the same planes), 3 lockstep
+                          then the leftover columns cut evenly over all CTAs (default 0)        */
     void* stream;      /* cudaStream_t to run on; NULL = the legacy default stream                 */
     int dirichlet_walls; /* side/bottom walls with p = 0 on the wall face instead of a zero normal
                           gradient: a bitmask of POISSON_WALL_* (default 0, the paper's walls);

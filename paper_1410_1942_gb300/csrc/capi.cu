@@ -1216,9 +1216,10 @@ extern "C" int poisson_describe(poisson_t* H, char* buf, int len) {
                  : v.family == 1 ? "one-sweep"
                                  : "two-sweep",
                  H->plan.nctas, H->plan.nsegs,
-                 H->plan.strategy == MARCH_SPLIT_BALANCED   ? "balanced"
-                 : H->plan.strategy == MARCH_SPLIT_LOCKSTEP ? "lockstep"
-                                                            : "equal");
+                 H->plan.strategy == MARCH_SPLIT_BALANCED        ? "balanced"
+                 : H->plan.strategy == MARCH_SPLIT_LOCKSTEP      ? "lockstep"
+                 : H->plan.strategy == MARCH_SPLIT_LOCKSTEP_FILL ? "lockstep-fill"
+                                                                 : "equal");
     } else {
         char mgs[48] = "";
         if (H->opts.precond == POISSON_MG) snprintf(mgs, sizeof mgs, " mg-vcycle levels=%d", H->mg.nlev);

@@ -1136,7 +1136,52 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
     std::vector<int> cta_seg;
     long long ntiles = 0;
     for (int s = 0; s < nsolves; ++s) ntiles += (long long)tiles_x[s] * tiles_y[s];
-    if (strategy == MARCH_SPLIT_LOCKSTEP) {
+    if (strategy == MARCH_SPLIT_LOCKSTEP_FILL && ntiles > nctas && ntiles % nctas != 0) {
+        // One round of whole columns in lockstep (CTA c: tiles c, c + nctas, ... for ntiles /
+        // nctas rounds), then the columns left over as one pool of planes cut into nctas equal
+        // ranges in (solve, tile, plane) order: CTA c takes range c after its whole columns.
+        std::vector<std::pair<int, int>> tl;  // (solve, tile)
+        for (int s = 0; s < nsolves; ++s)
+            for (int t = 0; t < tiles_x[s] * tiles_y[s]; ++t) tl.push_back({s, t});
+        const long long rounds = ntiles / nctas, first_left = rounds * nctas;
+        std::vector<long long> lbase(1, 0);  // first pool plane of each leftover column
+        for (long long t = first_left; t < ntiles; ++t)
+            lbase.push_back(lbase.back() + solves[tl[t].first].d.nz);
+        const long long pool = lbase.back();
+        auto seg_of = [&](long long t, int k0, int k1) {
+            Seg g{};
+            g.solve = tl[t].first;
+            g.x0 = (tl[t].second % tiles_x[g.solve]) * v.width;
+            g.y0 = (tl[t].second / tiles_x[g.solve]) * v.height;
+            g.k0 = k0;
+            g.k1 = k1;
+            return g;
+        };
+        for (int c = 0; c < nctas; ++c) {
+            cta_seg.push_back((int)segs.size());
+            std::vector<Seg> mine;
+            for (long long r = 0; r < rounds; ++r) {
+                const long long t = c + r * nctas;
+                mine.push_back(seg_of(t, 0, solves[tl[t].first].d.nz));
+            }
+            const long long a = pool * c / nctas, b = pool * (c + 1) / nctas;
+            for (long long t = first_left; t < ntiles && a < b; ++t) {
+                const long long lo = lbase[t - first_left], hi = lbase[t - first_left + 1];
+                const long long s0 = std::max(a, lo), s1 = std::min(b, hi);
+                if (s0 < s1) mine.push_back(seg_of(t, (int)(s0 - lo), (int)(s1 - lo)));
+            }
+            // a CTA's segments ordered by solve (the kernel's local records)
+            std::stable_sort(mine.begin(), mine.end(),
+                             [](const Seg& x, const Seg& y) { return x.solve < y.solve; });
+            for (const Seg& g : mine) segs.push_back(g);
+        }
+        cta_seg.push_back((int)segs.size());
+        // partial-sum slots contiguous per solve
+        std::vector<int> per(nsolves + 1, 0);
+        for (const Seg& g : segs) ++per[g.solve + 1];
+        for (int q = 0; q < nsolves; ++q) per[q + 1] += per[q];
+        for (Seg& g : segs) g.slot = per[g.solve]++;
+    } else if (strategy == MARCH_SPLIT_LOCKSTEP || strategy == MARCH_SPLIT_LOCKSTEP_FILL) {
         // Whole columns dealt round-robin when there are at least as many tile columns as CTAs
         // (CTA c: tiles c, c + G, c + 2G, ... of the (solve, tile) list); otherwise every column
         // is cut into q equal z-chunks and CTA c * ntiles + t takes chunk c of tile t.  Either

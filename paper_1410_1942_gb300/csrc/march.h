@@ -79,7 +79,11 @@ struct MarchCtl {
 // Work-split strategies of march_plan_build.
 // LOCKSTEP deals whole tile columns round-robin (CTA c: tiles c, c + G, ...) so that all CTAs
 // march the same planes at the same time (halo rows of neighbouring tiles stay in L2).
-enum { MARCH_SPLIT_EQUAL = 0, MARCH_SPLIT_BALANCED = 1, MARCH_SPLIT_LOCKSTEP = 2, MARCH_SPLITS = 3 };
+// LOCKSTEP_FILL deals one round of whole columns to every CTA in lockstep and cuts the columns
+// left over into equal plane counts over all CTAs, so that every CTA of the launch has work
+// when the columns do not divide evenly.
+enum { MARCH_SPLIT_EQUAL = 0, MARCH_SPLIT_BALANCED = 1, MARCH_SPLIT_LOCKSTEP = 2,
+       MARCH_SPLIT_LOCKSTEP_FILL = 3, MARCH_SPLITS = 4 };
 
 // A persistent launch: nctas CTAs, CTA c owns segments [cta_seg[c], cta_seg[c+1]).
 struct MarchPlan {

@@ -266,7 +266,7 @@ def _oracle_ref(c):
     return op, b, oracle.pcg(op, b, tol=REF_TOL, precond="ssor").x
 
 
-@pytest.mark.parametrize("tile", [0, 2012204, 10012204, 12012204, 22012204])
+@pytest.mark.parametrize("tile", [0, 2012204, 10012204, 12012204, 22012204, 13012204])
 def test_batch_of_uneven_solves_matches_oracle(tile):
     """A batch of solves of uneven size, FP32 and BF16 coefficients, plus handles that run one
     by one (FP64, SSOR): every result meets both acceptance criteria, with the persistent
@@ -359,7 +359,8 @@ def test_batch_rejects_a_handle_twice():
             capi.batch_submit([s, s], [c.s, c.s], [p, p.copy()], 1e-9)
 
 
-@pytest.mark.parametrize("tile", [2002204, 2012208, 12012204, 22012204])
+@pytest.mark.parametrize("tile", [2002204, 2012208, 12012204, 22012204, 3012204, 13012204,
+                                  13312208])
 def test_lockstep_round_robin_split(tile):
     """More tile columns than CTAs (1024 x 512 planes): the lockstep split deals whole columns
     round-robin.  Checked by the oracle's FP64 residual (a property at any size) and against the
