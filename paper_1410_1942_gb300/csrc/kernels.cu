@@ -15,6 +15,7 @@
 #include "internal.cuh"
 #include "kernels.h"
 #include "jobs.cuh"
+#include "plane_tile.cuh"
 
 #include <atomic>
 
@@ -333,6 +334,89 @@ __global__ void __launch_bounds__(TX * TY) k_cg_a_eta(Dims d, CoefEta<E> coef, i
             p0 = pp; e0 = ep;
             pp = pq; ep = eq;
         }
+    }
+    double v[1] = {(double)acc}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double pq2 = tot[0];
+            if (!(pq2 > 0.0) || !isfinite(pq2)) {
+                sc->done = BREAKDOWN;
+            } else {
+                sc->pq = pq2;
+                sc->alpha = sc->rz / pq2;
+            }
+        }
+    }
+}
+
+// k_cg_a_eta with the x and y neighbours of plane k from a shared plane (plane_tile.cuh): the
+// same arithmetic in the same order, two global loads of p per cell and plane (z, p_in) plus the
+// halo's share.  Grids with plane_tiles_fit only.
+template <typename E>
+__global__ void __launch_bounds__(TX * TY) k_cg_a_sm(Dims d, CoefEta<E> coef, int kc,
+                                                    const float* __restrict__ z,
+                                                    const float* __restrict__ p_in,
+                                                    float* __restrict__ p_out, Scalars* sc,
+                                                    double* partials) {
+    __shared__ double smem[64];
+    __shared__ float Ps[2][PT_N], Es[2][PT_N];
+    if (sc->done) return;
+    const float beta = (float)sc->beta;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    const bool act = j < d.ny;  // i < nx: whole tiles along x
+    const int ci = pt_index(threadIdx.x, threadIdx.y);
+    int hx, hy;
+    const bool hs = pt_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
+    const int gx = blockIdx.x * TX + hx, gy = blockIdx.y * TY + hy;
+    const bool hv = hs && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+    const int hi = hs ? pt_index(hx, hy) : 0;
+    const bool hxm = i > 0, hxp = i + 1 < d.nx, hym = j > 0, hyp = j + 1 < d.ny;
+    auto pn = [&](int e) { return z[e] + beta * p_in[e]; };
+    auto et = [&](int e) { return eta_load(coef.eta, e); };
+    int c = i + d.nx * (j + d.ny * k0);
+    int h = gx + d.nx * (gy + d.ny * k0);
+    float pm = 0.f, em = 0.f, p0 = 0.f, e0 = 0.f, pp = 0.f, ep = 0.f, pq = 0.f, eq = 0.f;
+    if (act) {
+        if (k0 > 0) { pm = pn(c - d.sxy); em = et(c - d.sxy); }
+        p0 = pn(c);
+        e0 = et(c);
+        if (k0 + 1 < d.nz) { pp = pn(c + d.sxy); ep = et(c + d.sxy); }
+    }
+    float hp = 0.f, he = 0.f, hpn = 0.f, hen = 0.f;
+    if (hv) { hp = pn(h); he = et(h); }
+    float acc = 0.f;
+    for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
+        const int b = (k - k0) & 1;
+        Ps[b][ci] = p0;
+        Es[b][ci] = e0;
+        if (hs) { Ps[b][hi] = hp; Es[b][hi] = he; }
+        if (act && k + 1 < k1 && k + 2 < d.nz) { pq = pn(c + 2 * d.sxy); eq = et(c + 2 * d.sxy); }
+        if (hv && k + 1 < k1) { hpn = pn(h + d.sxy); hen = et(h + d.sxy); }
+        __syncthreads();
+        if (act) {
+            const float* P = Ps[b];
+            const float* Ee = Es[b];
+            Stencil<float> w;
+            eta_stencil(d, i, j, k, e0, hxm ? Ee[ci - 1] : 0.f, hxp ? Ee[ci + 1] : 0.f,
+                        hym ? Ee[ci - PT_W] : 0.f, hyp ? Ee[ci + PT_W] : 0.f, em, ep, w);
+            float s = 0.f;
+            if (hxm) s += w.xm * P[ci - 1];
+            if (hxp) s += w.xp * P[ci + 1];
+            if (hym) s += w.ym * P[ci - PT_W];
+            if (hyp) s += w.yp * P[ci + PT_W];
+            if (k > 0) s += w.zm * pm;
+            if (k + 1 < d.nz) s += w.zp * pp;
+            const float q = w.D * p0 - s;
+            acc += p0 * q;
+            p_out[c] = p0;
+        }
+        pm = p0; em = e0;
+        p0 = pp; e0 = ep;
+        pp = pq; ep = eq;
+        hp = hpn; he = hen;
     }
     double v[1] = {(double)acc}, tot[1];
     if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
@@ -770,9 +854,13 @@ void launch_cg_init(const Dims& d, int kc, const Coef& c, const V* r, V* z, Scal
 template <typename V, typename Coef>
 void launch_cg_a(const Dims& d, int kc, const Coef& c, const V* z, const V* p_in, V* p_out,
                  Scalars* sc, double* part, cudaStream_t st) {
-    if constexpr (is_coef_eta<Coef>::value)
-        k_cg_a_eta<<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
-    else
+    if constexpr (is_coef_eta<Coef>::value) {
+        if (plane_tiles_fit(d))
+            k_cg_a_sm<<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
+        else
+            k_cg_a_eta<<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc,
+                                                                part);
+    } else
         k_cg_a<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
     counted(1);
 }

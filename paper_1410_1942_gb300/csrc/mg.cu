@@ -11,6 +11,7 @@
 #include "poisson.h"
 #include "mg.h"
 #include "kernels.h"
+#include "plane_tile.cuh"
 
 namespace pcg {
 namespace {
@@ -466,6 +467,180 @@ __global__ void __launch_bounds__(TX * TY, 5) k_mg_smooth_eta(Dims d, CoefEta<E>
     reduce_rz(rz, sc, partials, smem, mode);
 }
 
+// k_mg_cg_b_eta and k_mg_smooth_eta with the x and y neighbours of plane k from a shared plane
+// (plane_tile.cuh): the same arithmetic in the same order.  Grids with plane_tiles_fit only.
+template <typename E>
+__global__ void __launch_bounds__(TX * TY) k_mg_cg_b_sm(Dims d, CoefEta<E> coef, int kc,
+                                                       const float* __restrict__ p,
+                                                       float* __restrict__ x,
+                                                       float* __restrict__ r,
+                                                       float* __restrict__ x0, float omega,
+                                                       Scalars* sc, double* partials) {
+    __shared__ double smem[64];
+    __shared__ float Ps[2][PT_N], Es[2][PT_N];
+    if (sc->done) return;
+    const float alpha = (float)sc->alpha;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    const bool act = j < d.ny;
+    const int ci = pt_index(threadIdx.x, threadIdx.y);
+    int hx, hy;
+    const bool hs = pt_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
+    const int gx = blockIdx.x * TX + hx, gy = blockIdx.y * TY + hy;
+    const bool hv = hs && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+    const int hi = hs ? pt_index(hx, hy) : 0;
+    const bool hxm = i > 0, hxp = i + 1 < d.nx, hym = j > 0, hyp = j + 1 < d.ny;
+    auto et = [&](int e) { return eta_load(coef.eta, e); };
+    int c = i + d.nx * (j + d.ny * k0);
+    int h = gx + d.nx * (gy + d.ny * k0);
+    float pm = 0.f, em = 0.f, p0 = 0.f, e0 = 0.f, pp = 0.f, ep = 0.f, pq = 0.f, eq = 0.f;
+    float xc = 0.f, rc = 0.f, xn = 0.f, rn = 0.f;
+    if (act) {
+        if (k0 > 0) { pm = p[c - d.sxy]; em = et(c - d.sxy); }
+        p0 = p[c];
+        e0 = et(c);
+        xc = x[c];
+        rc = r[c];
+        if (k0 + 1 < d.nz) { pp = p[c + d.sxy]; ep = et(c + d.sxy); }
+    }
+    float hp = 0.f, he = 0.f, hpn = 0.f, hen = 0.f;
+    if (hv) { hp = p[h]; he = et(h); }
+    float rr = 0.f;
+    for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
+        const int b = (k - k0) & 1;
+        Ps[b][ci] = p0;
+        Es[b][ci] = e0;
+        if (hs) { Ps[b][hi] = hp; Es[b][hi] = he; }
+        if (act && k + 1 < k1) {
+            xn = x[c + d.sxy];
+            rn = r[c + d.sxy];
+            if (k + 2 < d.nz) { pq = p[c + 2 * d.sxy]; eq = et(c + 2 * d.sxy); }
+        }
+        if (hv && k + 1 < k1) { hpn = p[h + d.sxy]; hen = et(h + d.sxy); }
+        __syncthreads();
+        if (act) {
+            const float* P = Ps[b];
+            const float* Ee = Es[b];
+            Stencil<float> w;
+            eta_stencil(d, i, j, k, e0, hxm ? Ee[ci - 1] : 0.f, hxp ? Ee[ci + 1] : 0.f,
+                        hym ? Ee[ci - PT_W] : 0.f, hyp ? Ee[ci + PT_W] : 0.f, em, ep, w);
+            float s = 0.f;
+            if (hxm) s += w.xm * P[ci - 1];
+            if (hxp) s += w.xp * P[ci + 1];
+            if (hym) s += w.ym * P[ci - PT_W];
+            if (hyp) s += w.yp * P[ci + PT_W];
+            if (k > 0) s += w.zm * pm;
+            if (k + 1 < d.nz) s += w.zp * pp;
+            const float q = w.D * p0 - s;
+            x[c] = xc + alpha * p0;
+            const float rnew = rc - alpha * q;
+            r[c] = rnew;
+            x0[c] = omega * rnew / w.D;
+            rr += rnew * rnew;
+        }
+        pm = p0; em = e0;
+        p0 = pp; e0 = ep;
+        pp = pq; ep = eq;
+        xc = xn; rc = rn;
+        hp = hpn; he = hen;
+    }
+    double v[1] = {(double)rr}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sc->rr = tot[0];
+    }
+}
+
+template <typename E>
+__global__ void __launch_bounds__(TX * TY) k_mg_smooth_sm(Dims d, CoefEta<E> coef, int kc,
+                                                         const float* __restrict__ r,
+                                                         const float* __restrict__ x,
+                                                         const float* __restrict__ e, Dims dc,
+                                                         int sx, int sy, int sz, float alpha,
+                                                         float omega, float* __restrict__ y,
+                                                         Scalars* sc, double* partials,
+                                                         int mode) {
+    __shared__ double smem[64];
+    __shared__ float Ts[2][PT_N], Es[2][PT_N];
+    if (sc && sc->done) return;
+    const int i = blockIdx.x * TX + threadIdx.x;
+    const int j = blockIdx.y * TY + threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    const bool act = j < d.ny;
+    const int ci = pt_index(threadIdx.x, threadIdx.y);
+    int hx, hy;
+    const bool hs = pt_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
+    const int gx = blockIdx.x * TX + hx, gy = blockIdx.y * TY + hy;
+    const bool hv = hs && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+    const int hi = hs ? pt_index(hx, hy) : 0;
+    const bool hxm = i > 0, hxp = i + 1 < d.nx, hym = j > 0, hyp = j + 1 < d.ny;
+    // parents (x and y offsets of the aggregates) of the cell and of the halo cell
+    const int pc = (i >> sx) + dc.nx * (j >> sy);
+    const int ph = hv ? (gx >> sx) + dc.nx * (gy >> sy) : 0;
+    auto et = [&](int q) { return eta_load(coef.eta, q); };
+    int c = i + d.nx * (j + d.ny * k0);
+    int h = gx + d.nx * (gy + d.ny * k0);
+    float tm = 0.f, em = 0.f, t0 = 0.f, e0 = 0.f, tp = 0.f, ep = 0.f, tq = 0.f, eq = 0.f;
+    float rc = 0.f, rn = 0.f;
+    if (act) {
+        if (k0 > 0) { tm = x[c - d.sxy] + alpha * e[pc + dc.sxy * ((k0 - 1) >> sz)]; em = et(c - d.sxy); }
+        t0 = x[c] + alpha * e[pc + dc.sxy * (k0 >> sz)];
+        e0 = et(c);
+        rc = r[c];
+        if (k0 + 1 < d.nz) {
+            tp = x[c + d.sxy] + alpha * e[pc + dc.sxy * ((k0 + 1) >> sz)];
+            ep = et(c + d.sxy);
+        }
+    }
+    float ht = 0.f, he = 0.f, htn = 0.f, hen = 0.f;
+    if (hv) { ht = x[h] + alpha * e[ph + dc.sxy * (k0 >> sz)]; he = et(h); }
+    float rz = 0.f;
+    for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
+        const int b = (k - k0) & 1;
+        Ts[b][ci] = t0;
+        Es[b][ci] = e0;
+        if (hs) { Ts[b][hi] = ht; Es[b][hi] = he; }
+        if (act && k + 1 < k1) {
+            rn = r[c + d.sxy];
+            if (k + 2 < d.nz) {
+                tq = x[c + 2 * d.sxy] + alpha * e[pc + dc.sxy * ((k + 2) >> sz)];
+                eq = et(c + 2 * d.sxy);
+            }
+        }
+        if (hv && k + 1 < k1) {
+            htn = x[h + d.sxy] + alpha * e[ph + dc.sxy * ((k + 1) >> sz)];
+            hen = et(h + d.sxy);
+        }
+        __syncthreads();
+        if (act) {
+            const float* T = Ts[b];
+            const float* Ee = Es[b];
+            Stencil<float> w;
+            eta_stencil(d, i, j, k, e0, hxm ? Ee[ci - 1] : 0.f, hxp ? Ee[ci + 1] : 0.f,
+                        hym ? Ee[ci - PT_W] : 0.f, hyp ? Ee[ci + PT_W] : 0.f, em, ep, w);
+            float s = 0.f;
+            if (hxm) s += w.xm * T[ci - 1];
+            if (hxp) s += w.xp * T[ci + 1];
+            if (hym) s += w.ym * T[ci - PT_W];
+            if (hyp) s += w.yp * T[ci + PT_W];
+            if (k > 0) s += w.zm * tm;
+            if (k + 1 < d.nz) s += w.zp * tp;
+            const float yc = t0 + omega * (rc - (w.D * t0 - s)) / w.D;
+            y[c] = yc;
+            rz += rc * yc;
+        }
+        tm = t0; em = e0;
+        t0 = tp; e0 = ep;
+        tp = tq; ep = eq;
+        rc = rn;
+        ht = htn; he = hen;
+    }
+    if (mode < 0 || !sc) return;
+    reduce_rz(rz, sc, partials, smem, mode);
+}
+
 // Start of the preconditioned solve: x0 = w D^-1 r on the fine level; with scalars, sums r.r
 // and sets them like k_cg_init (rz follows from the V-cycle's last kernel).
 template <typename V, typename Coef>
@@ -588,11 +763,16 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
             (V*)m->y[l], sc, nullptr, -1);
     }
     const int* f = m->f[0];
-    if constexpr (is_coef_eta<Coef>::value)
-        k_mg_smooth_eta<<<cols(d, kc), dim3(TX, TY), 0, st>>>(
-            d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
-            f[2] - 1, al, om, z, sc, part, mode);
-    else
+    if constexpr (is_coef_eta<Coef>::value) {
+        if (plane_tiles_fit(d))
+            k_mg_smooth_sm<<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+                d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1,
+                f[1] - 1, f[2] - 1, al, om, z, sc, part, mode);
+        else
+            k_mg_smooth_eta<<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+                d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1,
+                f[1] - 1, f[2] - 1, al, om, z, sc, part, mode);
+    } else
         k_mg_smooth<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
             d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
             f[2] - 1, al, om, z, sc, part, mode);
@@ -701,10 +881,16 @@ void mg_init(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* 
 template <typename V, typename Coef>
 void mg_cg_b(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* p, V* x, V* r, V* z,
              Scalars* sc, double* part, cudaStream_t st) {
-    if constexpr (is_coef_eta<Coef>::value)
-        k_mg_cg_b_eta<<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r, (V*)m->x[0],
-                                                            (V)MG_OMEGA, sc, part);
-    else
+    if constexpr (is_coef_eta<Coef>::value) {
+        if (plane_tiles_fit(d))
+            k_mg_cg_b_sm<<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r,
+                                                               (V*)m->x[0], (V)MG_OMEGA, sc,
+                                                               part);
+        else
+            k_mg_cg_b_eta<<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r,
+                                                                (V*)m->x[0], (V)MG_OMEGA, sc,
+                                                                part);
+    } else
         k_mg_cg_b<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r,
                                                                 (V*)m->x[0], (V)MG_OMEGA, sc,
                                                                 part);

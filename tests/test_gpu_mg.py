@@ -124,10 +124,13 @@ def test_mg_solve_matches_oracle(name, prec):
     _check(op, b, xref, p, st, c.tol)
 
 
-@pytest.mark.parametrize("walls", [31, oracle.PERIODIC_X, oracle.PERIODIC_X | 16])
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_mg_solve_with_boundary_variants(walls, prec):
-    c = inputs.strut_case(48, 24, 20, seed=3)
+# 48 wide: the fine passes on plain loads; 64 wide with a ragged last row of tiles (ny = 20): the
+# fine passes with shared-memory planes (whole 32-cell tiles along x, no periodic wrap)
+@pytest.mark.parametrize("shape", [(48, 24, 20), (64, 20, 12)])
+@pytest.mark.parametrize("walls", [0, 31, 16 | 1, oracle.PERIODIC_X, oracle.PERIODIC_X | 16])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_mg_solve_with_boundary_variants(shape, walls, prec):
+    c = inputs.strut_case(*shape, seed=3)
     g = c.grid
     op, b, xref = _reference(c.F, c.s, g.h, walls=walls)
     with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg",
