@@ -85,6 +85,44 @@ def test_vcycle_apply_with_cut_cells_matches_oracle(prec):
     assert np.linalg.norm(got - want) <= VCYCLE_TOL[prec] * np.linalg.norm(want)
 
 
+# 256 x 84 x 49: the fine passes on shared-memory planes (whole 32-cell tiles along x) with two
+# planes per thread (z-chunk 2), a ragged last row of tiles (84 = 10 x 8 + 4) and an odd plane
+# count (the last coarse plane has one fine plane).
+STAGED = (256, 84, 49)
+
+
+@pytest.mark.parametrize("walls", [0, 31])
+def test_vcycle_apply_with_staged_fine_passes(walls):
+    nx, ny, nz = STAGED
+    F = _rand_F((nz, ny, nx), 7)
+    with capi.Poisson(nx, ny, nz, 1.0 / nz, precision="fp32", precond="mg",
+                      **_walls_kw(walls)) as s:
+        assert "zchunk=2" in s.describe(), s.describe()
+        s.set_density(F)
+        r = np.random.default_rng(8).standard_normal((nz, ny, nx))
+        got = np.empty_like(r)
+        s.precond_apply(r, got, kind="mg", precision="fp32")
+    op = oracle.operator(F, walls=walls)
+    want = mg.vcycle(mg.hierarchy(op), r)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= VCYCLE_TOL["fp32"], err
+
+
+@pytest.mark.parametrize("walls", [0, 31])
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mg_solve_with_staged_fine_passes(walls, prec):
+    c = inputs.strut_case(*STAGED, seed=9)
+    g = c.grid
+    op, b, xref = _reference(c.F, c.s, g.h, walls=walls)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg", inner_tol=1e-5,
+                      **_walls_kw(walls)) as s:
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, 1e-9)
+    assert rc == capi.OK
+    _check(op, b, xref, p, st, 1e-9)
+
+
 def _reference(F, s, h, walls=0, apertures=None, vol=None):
     op = oracle.operator(F, walls=walls, apertures=apertures)
     b = oracle.rhs(s, h, vol)
