@@ -157,7 +157,9 @@ int poisson_handle_bytes(poisson_t* h, uint64_t* bytes);
  * rho_air)) and build the operator: face coefficients (harmonic means), diagonal, and the
  * reduced-precision copies.  F: nx*ny*nz doubles; mem = POISSON_MEM_HOST or POISSON_MEM_DEVICE
  * says where F lives (checked against the pointer).  F is read during the call only.
- * Errors: EINVAL (NULL, rho <= 0, mem mismatch), ECUDA. */
+ * Errors: EINVAL (NULL, rho <= 0, mem mismatch; or some cell's density is not a positive finite
+ * number -- F non-finite, or far enough outside [0, 1] -- in which case the handle is left not
+ * ready and solves return ENOTREADY until a valid density is set), ECUDA. */
 int poisson_set_density(poisson_t* h, const double* F, double rho_air, double rho_water, int mem);
 
 /* Solve div((1/rho) grad p) = rhs (eq. (pois)) to relative residual ||b - A p|| / ||b|| <= tol,
@@ -165,7 +167,8 @@ int poisson_set_density(poisson_t* h, const double* F, double rho_air, double rh
  * doubles.  p: on entry the initial guess (warm start; zeros for none), on exit the solution.
  * stats may be NULL.  An all-zero rhs returns p = 0 and OK.  Errors: ENOTREADY (no density set),
  * EINVAL (NULL, tol <= 0), ENOTCONV (cap reached: p = best iterate, stats = its residual),
- * EBREAKDOWN, ECUDA. */
+ * EBREAKDOWN (also for a non-finite rhs or initial guess: the first residual norm is then not
+ * finite; p is unspecified), ECUDA.  The handle stays usable after any of these. */
 int poisson_solve(poisson_t* h, const double* rhs, double* p, double tol, poisson_stats* stats);
 
 /* y = A x with the handle's operator at the given precision (A = -h^2 div_h((1/rho) grad_h)).

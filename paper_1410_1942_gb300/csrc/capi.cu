@@ -12,6 +12,8 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "poisson.h"
 #include "kernels.h"
 #include "capi_internal.h"
@@ -28,6 +30,15 @@ using namespace pcg;
             return POISSON_ECUDA;                                  \
         }                                                          \
     } while (0)
+
+// NVTX ranges around the phases of a solve (set-up, refinement steps, inner solves), for
+// timeline tools; without a tool attached they cost a few instructions each.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 cudaError_t& last_cuda_error() {
     static thread_local cudaError_t e = cudaSuccess;
@@ -640,6 +651,7 @@ extern "C" int poisson_handle_bytes(poisson_t* H, uint64_t* bytes) {
 extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air,
                                    double rho_water, int mem) {
     if (!H || !F || !(rho_air > 0.0) || !(rho_water > 0.0)) return POISSON_EINVAL;
+    NvtxRange range("poisson_set_density");
     if (mem != POISSON_MEM_HOST && mem != POISSON_MEM_DEVICE) return POISSON_EINVAL;
     const bool dev = is_device_ptr(F);
     if (dev != (mem == POISSON_MEM_DEVICE)) return POISSON_EINVAL;
@@ -650,8 +662,16 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
         CK(cudaMemcpyAsync(H->b64, F, bytes, cudaMemcpyHostToDevice, H->st));
         Fd = H->b64;
     }
+    // the density check's flag lives in the reduction partials (free between solves)
+    unsigned* bad = reinterpret_cast<unsigned*>(H->partials);
+    CK(cudaMemsetAsync(bad, 0, sizeof(unsigned), H->st));
+    H->ready = false;
     launch_setup(H->d, Fd, rho_air, rho_water, H->bx, H->by, H->bz, H->diag, H->dinv, H->top64,
-                 H->rinv2, H->eta32, H->eta16, H->apertures(), H->st);
+                 H->rinv2, H->eta32, H->eta16, H->apertures(), bad, H->st);
+    unsigned bad_host = 0;
+    CK(cudaMemcpyAsync(&bad_host, bad, sizeof(unsigned), cudaMemcpyDeviceToHost, H->st));
+    CK(cudaStreamSynchronize(H->st));
+    if (bad_host) return POISSON_EINVAL;  // left not ready: solves give ENOTREADY
     if (H->periodic() && H->pu[0]) {
         // rho/2 in rows padded by its halo width (4 FP32 / 8 BF16 columns, 16 bytes)
         if (H->peta32) launch_pad_rows_f32(H->d, 4, H->eta32, H->peta32, H->st);
@@ -921,6 +941,7 @@ static int solve_mixed(poisson_t* H, const C32& c32, bool bf16, double tol, int*
         target = std::min(target, 0.5);
         CK(cudaMemsetAsync(H->d32, 0, bytes32, H->st));
         CK(cudaMemsetAsync(H->p32a, 0, bytes32, H->st));
+        NvtxRange inner_range("inner solve");
         Scalars res;
         rc = POISSON_ECUDA;
         bool inner_done = false, rb_used = false;
@@ -964,6 +985,7 @@ extern "C" int poisson_solve(poisson_t* H, const double* rhs, double* p, double 
                              poisson_stats* stats) {
     if (!H || !rhs || !p || !(tol > 0.0)) return POISSON_EINVAL;
     if (!H->ready) return POISSON_ENOTREADY;
+    NvtxRange range("poisson_solve");
     const double t0 = now_s();
     const size_t n = (size_t)H->d.n, bytes = sizeof(double) * n;
     const bool drhs = is_device_ptr(rhs), dp = is_device_ptr(p);

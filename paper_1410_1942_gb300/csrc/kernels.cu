@@ -28,15 +28,19 @@ __device__ __forceinline__ double rho_of(double F, double ra, double rw) {
     return __dadd_rn(ra, __dmul_rn(F, __dadd_rn(rw, -ra)));
 }
 
+// bad: set to 1 when some cell's density is not a positive finite number (F non-finite, or so
+// far outside [0, 1] that rho <= 0): the operator is then not SPD
 __global__ void k_setup_faces(Dims d, const double* __restrict__ F, double ra, double rw,
                               double* __restrict__ bx, double* __restrict__ by,
                               double* __restrict__ bz, float* __restrict__ eta32,
-                              __nv_bfloat16* __restrict__ eta16, Apertures ap) {
+                              __nv_bfloat16* __restrict__ eta16, Apertures ap,
+                              unsigned* __restrict__ bad) {
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= d.n) return;
     const int c = (int)tid;
     const int i = c % d.nx, j = (c / d.nx) % d.ny, k = c / d.sxy;
     const double rc = rho_of(F[c], ra, rw);
+    if (!(rc > 0.0) || !isfinite(rc)) *bad = 1u;
     // periodic x: the low face of cell 0 couples it to cell nx-1 of its row
     bx[c] = (i > 0 || (d.walls & PERIODIC_X))
                 ? 2.0 / __dadd_rn(rc, rho_of(F[i > 0 ? c - 1 : c + d.nx - 1], ra, rw))
@@ -768,8 +772,9 @@ static inline unsigned blocks1d(long long n) { return (unsigned)((n + 255) / 256
 
 void launch_setup(const Dims& d, const double* F, double ra, double rw, double* bx, double* by,
                   double* bz, double* diag, double* dinv, double* top, double* rinv2,
-                  float* eta32, __nv_bfloat16* eta16, const Apertures& ap, cudaStream_t st) {
-    k_setup_faces<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, eta32, eta16, ap);
+                  float* eta32, __nv_bfloat16* eta16, const Apertures& ap, unsigned* bad,
+                  cudaStream_t st) {
+    k_setup_faces<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, eta32, eta16, ap, bad);
     k_setup_diag<<<blocks1d(d.n), 256, 0, st>>>(d, F, ra, rw, bx, by, bz, diag, dinv, top, rinv2,
                                                 ap);
     counted(2);

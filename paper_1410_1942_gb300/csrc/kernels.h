@@ -12,7 +12,8 @@ constexpr int TY = 8;   // ... along y
 
 void launch_setup(const Dims& d, const double* F, double ra, double rw, double* bx, double* by,
                   double* bz, double* diag, double* dinv, double* top, double* rinv2,
-                  float* eta32, __nv_bfloat16* eta16, const Apertures& ap, cudaStream_t st);
+                  float* eta32, __nv_bfloat16* eta16, const Apertures& ap, unsigned* bad,
+                  cudaStream_t st);
 void launch_scale(long long n, const double* s, double a, double* b, cudaStream_t st,
                   const double* vol = nullptr);
 void launch_update64(long long n, double* x, const float* dlt, cudaStream_t st);
