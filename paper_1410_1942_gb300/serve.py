@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import json
 import math
 import time
 
@@ -68,6 +69,8 @@ class Request:
     admitted_at: float = -1.0
     done_at: float = -1.0
     bytes: int = 0        # device bytes counted against the budget while admitted
+    cancel_after: int = 0  # > 0: the client cancels the request after this many steps
+    cancelled: bool = False
 
 
 def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
@@ -86,7 +89,8 @@ def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
 
 class Server:
     def __init__(self, budget_bytes, precision="fp32", tol=1e-9, steps=20, device="cuda",
-                 keep_results=False, tile=SERVE_TILE, precond="jacobi", record_steps=False):
+                 keep_results=False, tile=SERVE_TILE, precond="jacobi", record_steps=False,
+                 log=None):
         # tile: kernel variant of every Jacobi request's handle (fixed, so admission does not run
         # the autotuner; the batch executor uses the variant of its largest solve).  precond
         # "mg": the V-cycle preconditioner; such handles are not batched, the executor solves
@@ -105,6 +109,9 @@ class Server:
         # one by one (rid -> {"grid", "F", "steps": [(s, p, status)]}); costs a device-to-host
         # copy per step inside the loop, so it is for tests, not for timing
         self.record = {} if record_steps else None
+        # log: a path or a writable text file; one JSON line per finished solve (request, step,
+        # shape, status, residual, CG iterations, latency)
+        self.log = log
 
     def _admit(self, r, now):
         g, F, s, modes = inputs.mixed_fields_t(r.shape, r.seed, device=self.device)
@@ -129,8 +136,32 @@ class Server:
         r.modes = inputs.advect_modes(r.modes, r.grid, inputs.DT)
         r.s = inputs.divergence_source_t(r.grid, r.modes, device=self.device)
 
+    def cancel(self, r):
+        """The client gives up on request r.  Not yet admitted: it is dropped unallocated.
+        Admitted: its step in flight still finishes (a batch is not interrupted mid-solve), then
+        it leaves (handle destroyed, memory returned to the budget) without further steps."""
+        r.cancelled = True
+
+    def _log(self, out, r, rc, st, lat, t):
+        if out is None:
+            return
+        out.write(json.dumps({"rid": r.rid, "step": r.step, "shape": list(r.shape),
+                              "status": capi.strerror(rc) if rc != capi.OK else "ok",
+                              "rel_residual": st["rel_residual"] if st else None,
+                              "inner_iters": st["inner_iters"] if st else None,
+                              "latency_ms": 1e3 * lat, "t_s": t}) + "\n")
+
     def serve(self, requests):
         """Runs the stream to completion (wall clock); returns the statistics."""
+        own_log = isinstance(self.log, str)
+        out = open(self.log, "w") if own_log else self.log
+        try:
+            return self._serve(requests, out)
+        finally:
+            if own_log:
+                out.close()
+
+    def _serve(self, requests, out):
         pending = collections.deque(sorted(requests, key=lambda q: q.arrival))
         active = []
         used = 0
@@ -141,6 +172,9 @@ class Server:
         while pending or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
+                if pending[0].cancelled:  # cancelled before admission: never allocated
+                    pending.popleft()
+                    continue
                 nx, ny, nz = pending[0].shape
                 arrays = REQUEST_BYTES_PER_CELL * nx * ny * nz
                 left = self.budget - used - arrays
@@ -156,7 +190,8 @@ class Server:
             peak_active = max(peak_active, len(active))
             peak_used = max(peak_used, used)
             if not active:
-                time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
+                if pending:
+                    time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                 continue
             for r in list(active):
                 rc, st = capi.poll(r.ticket)
@@ -170,8 +205,11 @@ class Server:
                 lat.append(t - r.t_submit)
                 if self.record is not None:
                     self.record[r.rid]["steps"].append((r.s.cpu().numpy(), r.p.cpu().numpy(), rc))
+                self._log(out, r, rc, st, t - r.t_submit, t)
                 r.step += 1
-                if r.step < self.steps and rc == capi.OK:
+                if r.cancel_after and r.step >= r.cancel_after:
+                    r.cancelled = True
+                if r.step < self.steps and rc == capi.OK and not r.cancelled:
                     self._advance(r)
                     self._submit(r, t)
                 else:
@@ -192,8 +230,10 @@ class Server:
             "solves_per_s": nsolves / wall, "cell_solves_per_s": cells / wall,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "max_rel_residual": max((max(r.residuals) for r in requests if r.residuals), default=0.0),
-            "all_ok": all(all(s == capi.OK for s in r.statuses) and len(r.statuses) == self.steps
-                          for r in requests),
+            "all_ok": all(all(s == capi.OK for s in r.statuses) and
+                          (len(r.statuses) == self.steps or r.cancelled) for r in requests),
+            "cancelled": sum(1 for r in requests if r.cancelled),
+            "used_bytes_at_end": used,
             "peak_active": peak_active, "peak_used_bytes": peak_used, "budget_bytes": self.budget,
             "precision": self.precision,
         }

@@ -122,3 +122,27 @@ def test_stream_with_the_multigrid_preconditioner():
         assert max(r.iters) <= 60
         a, m = jac.results[r.rid], srv.results[r.rid]
         assert np.linalg.norm(a - m) / np.linalg.norm(a) <= 2 * L2_TOL
+
+
+def test_cancelled_requests_leave_and_free_their_memory(tmp_path):
+    """A request cancelled after k steps stops there (its step in flight finished, handle and
+    memory given back); one cancelled before arrival is never admitted; the others run all
+    their steps.  The JSON-lines log holds one line per finished solve."""
+    reqs = _stream(5, math.inf, seed=6)
+    reqs[1].cancel_after = 1
+    reqs[3].cancel_after = 2
+    srv = serve.Server(budget_bytes=8 << 30, steps=4, log=str(tmp_path / "solves.jsonl"))
+    srv.cancel(reqs[4])
+    st = srv.serve(reqs)
+    assert st["all_ok"] and st["cancelled"] == 3
+    assert st["used_bytes_at_end"] == 0
+    assert [len(r.statuses) for r in reqs] == [4, 1, 4, 2, 0]
+    assert st["solves"] == 11
+    import json
+    lines = [json.loads(x) for x in (tmp_path / "solves.jsonl").read_text().splitlines()]
+    assert len(lines) == 11
+    assert all(x["status"] == "ok" and x["rel_residual"] <= 1e-9 * (1 + 1e-6) for x in lines)
+    for r in reqs:
+        mine = [x for x in lines if x["rid"] == r.rid]
+        assert [x["step"] for x in mine] == list(range(len(r.statuses)))
+        assert all(x["shape"] == list(r.shape) and x["latency_ms"] > 0 for x in mine)
