@@ -35,4 +35,147 @@ __device__ __forceinline__ int pt_index(int x, int y) { return (y + 1) * PT_W + 
 // cell is in its tile or its halo) and no periodic wrap.
 inline bool plane_tiles_fit(const Dims& d) { return d.nx % TX == 0 && !(d.walls & PERIODIC_X); }
 
+// ------------------------------------------------------------------ 2x2 cells per thread
+// The quad kernels (k_cg_a_q in kernels.cu; k_mg_cg_b_q, k_mg_restrict_q, k_mg_smooth_q in
+// mg.cu) march QX x QY tiles of a plane with TX x TY threads, each thread owning the 2 x 2 cells
+// (2 tx + {0, 1}, 2 ty + {0, 1}) of every plane of its z-chunk: loads and stores of a row pair are
+// float2, the face between two cells of a thread is formed once for both, and the z face between
+// planes k and k+1 is carried to plane k+1.  Rounding is that of the single-cell kernels (a face
+// is rcp(eta_a + eta_b), and the addition commutes).  Shared planes have a row stride of QS floats
+// and the tile's first cell at column 2, so a thread's row pair is 8-byte aligned.
+constexpr int QX = 2 * TX, QY = 2 * TY, QS = QX + 4, QN = QS * (QY + 2);
+
+// Index in a quad shared plane of the tile cell (x, y), x in [-1, QX], y in [-1, QY].
+__device__ __forceinline__ int q_index(int x, int y) { return (y + 1) * QS + x + 2; }
+
+// Halo slot of thread t = threadIdx.x + TX threadIdx.y: a pair of the row below the tile
+// (t < TX: cells x = 2t, 2t + 1, y = -1), a pair of the row above (next TX: y = QY), one cell of
+// the column to the left (next QY: x = -1) or to the right (next QY: x = QX).
+__device__ __forceinline__ int q_halo_slot(int t, int& hx, int& hy) {
+    if (t < TX) { hx = 2 * t; hy = -1; return 2; }
+    if (t < 2 * TX) { hx = 2 * (t - TX); hy = QY; return 2; }
+    if (t < 2 * TX + QY) { hx = -1; hy = t - 2 * TX; return 1; }
+    if (t < 2 * TX + 2 * QY) { hx = QX; hy = t - 2 * TX - QY; return 1; }
+    hx = hy = 0;
+    return 0;
+}
+
+// Whether the quad kernels serve a grid: whole tiles along x, whole row pairs, no periodic wrap
+// (and, for the V-cycle's fine passes, aggregates of 2 x 2 cells in x-y, which these imply).
+inline bool quad_tiles_fit(const Dims& d) {
+    return d.nx % QX == 0 && d.ny % 2 == 0 && !(d.walls & PERIODIC_X);
+}
+
+// z-chunk of the quad kernels: even (a coarse plane of the restriction never straddles two
+// chunks), about four blocks per SM of 152 on the plane tiles.
+inline int quad_kc(const Dims& d) {
+    const long long tiles = (long long)(d.nx / QX) * ((d.ny + QY - 1) / QY);
+    long long kc = (tiles * d.nz) / 608;
+    kc &= ~1LL;
+    if (kc < 2) kc = 2;
+    if (kc > 64) kc = 64;
+    return (int)kc;
+}
+
+inline dim3 quad_grid(const Dims& d, int kc) {
+    return dim3(d.nx / QX, (d.ny + QY - 1) / QY, (d.nz + kc - 1) / kc);
+}
+
+template <typename E>
+__device__ __forceinline__ float2 eta_load2(const E* p, int c);
+template <>
+__device__ __forceinline__ float2 eta_load2<float>(const float* p, int c) {
+    return __ldg(reinterpret_cast<const float2*>(p + c));
+}
+template <>
+__device__ __forceinline__ float2 eta_load2<__nv_bfloat16>(const __nv_bfloat16* p, int c) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p + c));
+}
+
+__device__ __forceinline__ float2 ld2(const float* p, int c) {
+    return *reinterpret_cast<const float2*>(p + c);
+}
+__device__ __forceinline__ void st2(float* p, int c, float a, float b) {
+    *reinterpret_cast<float2*>(p + c) = make_float2(a, b);
+}
+
+// One plane of a thread's 2 x 2 cells: values [r][q] at (x0 + q, y0 + r).
+struct Quad {
+    float v[2][2];
+};
+
+// A u and the diagonal D on the thread's 2 x 2 cells of plane k of the rho/2 operator.  u, e:
+// the cells' values and rho/2 on plane k; um, up: u on planes k - 1 and k + 1; ep: rho/2 on plane
+// k + 1; U, Es: the shared planes of u and rho/2 (k), si = q_index of cell (0, 0); fzd: in, the z
+// faces below plane k (used when k > 0), out, the faces above it.  xlo/xhi/ylo/yhi: the block's
+// outer x/y neighbours exist (else a wall or nothing, as `walls` says).  Per cell the weights,
+// the diagonal and the neighbour sum are formed as in eta_stencil / the single-cell kernels.
+__device__ __forceinline__ void quad_apply(const Dims& d, int k, bool xlo, bool xhi, bool ylo,
+                                           bool yhi, const Quad& u, const Quad& e, const Quad& um,
+                                           const Quad& up, const Quad& ep, const float* U,
+                                           const float* Es, int si, Quad& fzd, Quad& q, Quad& D) {
+    const float2 ub = *reinterpret_cast<const float2*>(U + si - QS);
+    const float2 ua = *reinterpret_cast<const float2*>(U + si + 2 * QS);
+    const float2 eb = *reinterpret_cast<const float2*>(Es + si - QS);
+    const float2 ea = *reinterpret_cast<const float2*>(Es + si + 2 * QS);
+    const float ul[2] = {U[si - 1], U[si + QS - 1]}, ur[2] = {U[si + 2], U[si + QS + 2]};
+    const float el[2] = {Es[si - 1], Es[si + QS - 1]}, er[2] = {Es[si + 2], Es[si + QS + 2]};
+    const float ubq[2] = {ub.x, ub.y}, uaq[2] = {ua.x, ua.y};
+    const float ebq[2] = {eb.x, eb.y}, eaq[2] = {ea.x, ea.y};
+    const bool zlo = k > 0, top = k + 1 == d.nz;
+    // the y faces between the thread's two rows
+    const float fym[2] = {rcp_approx(e.v[0][0] + e.v[1][0]), rcp_approx(e.v[0][1] + e.v[1][1])};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const float fxm = rcp_approx(e.v[r][0] + e.v[r][1]);  // between the row's two cells
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const float ec = e.v[r][c];
+            const float ew = rcp_approx(ec);
+            float xm, xp, ym, yp;
+            bool hxm, hxp, hym, hyp;
+            if (c == 0) {
+                hxm = xlo;
+                xm = xlo ? rcp_approx(ec + el[r]) : ((d.walls & 1) ? ew : 0.f);
+                hxp = true;
+                xp = fxm;
+            } else {
+                hxm = true;
+                xm = fxm;
+                hxp = xhi;
+                xp = xhi ? rcp_approx(ec + er[r]) : ((d.walls & 2) ? ew : 0.f);
+            }
+            if (r == 0) {
+                hym = ylo;
+                ym = ylo ? rcp_approx(ec + ebq[c]) : ((d.walls & 4) ? ew : 0.f);
+                hyp = true;
+                yp = fym[c];
+            } else {
+                hym = true;
+                ym = fym[c];
+                hyp = yhi;
+                yp = yhi ? rcp_approx(ec + eaq[c]) : ((d.walls & 8) ? ew : 0.f);
+            }
+            const float zm = zlo ? fzd.v[r][c] : ((d.walls & 16) ? ew : 0.f);
+            const float fzu = rcp_approx(ec + ep.v[r][c]);
+            const float wzp = top ? ew : fzu;
+            const float zp = top ? 0.f : wzp;
+            fzd.v[r][c] = fzu;
+            D.v[r][c] = xm + xp + ym + yp + zm + wzp;
+            const float uxm = c == 0 ? ul[r] : u.v[r][0];
+            const float uxp = c == 0 ? u.v[r][1] : ur[r];
+            const float uym = r == 0 ? ubq[c] : u.v[0][c];
+            const float uyp = r == 0 ? u.v[1][c] : uaq[c];
+            float s = 0.f;
+            if (hxm) s += xm * uxm;
+            if (hxp) s += xp * uxp;
+            if (hym) s += ym * uym;
+            if (hyp) s += yp * uyp;
+            if (zlo) s += zm * um.v[r][c];
+            if (!top) s += zp * up.v[r][c];
+            q.v[r][c] = D.v[r][c] * u.v[r][c] - s;
+        }
+    }
+}
+
 }  // namespace pcg
