@@ -17,6 +17,7 @@
 #include "jobs.cuh"
 #include "plane_tile.cuh"
 
+#include <algorithm>
 #include <atomic>
 
 namespace pcg {
@@ -436,99 +437,37 @@ __global__ void __launch_bounds__(TX * TY) k_cg_a_sm(Dims d, CoefEta<E> coef, in
     }
 }
 
-// k_cg_a_sm with 2 x 2 cells per thread (plane_tile.cuh): p = z + beta p_in and (p, A p) on
-// QX x QY tiles of kc planes.  Grids with quad_tiles_fit only.
-template <typename E>
-__global__ void __launch_bounds__(TX * TY, 3) k_cg_a_q(Dims d, CoefEta<E> coef, int kc,
-                                                      const float* __restrict__ z,
-                                                      const float* __restrict__ p_in,
-                                                      float* __restrict__ p_out, Scalars* sc,
-                                                      double* partials) {
-    __shared__ double smem[64];
-    __shared__ __align__(16) float Us[2][QN];
-    __shared__ __align__(16) float Ess[2][QN];
-    if (sc->done) return;
-    const float beta = (float)sc->beta;
-    const int x0 = blockIdx.x * QX + 2 * threadIdx.x, y0 = blockIdx.y * QY + 2 * threadIdx.y;
-    const int k0 = blockIdx.z * kc;
-    const int k1 = min(d.nz, k0 + kc);
-    const bool act = y0 < d.ny;
-    const int si = q_index(2 * threadIdx.x, 2 * threadIdx.y);
-    int hx, hy;
-    const int hk = q_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
-    const int gx = blockIdx.x * QX + hx, gy = blockIdx.y * QY + hy;
-    const bool hv = hk && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
-    const int hi = hk ? q_index(hx, hy) : 0;
-    const bool xlo = x0 > 0, xhi = x0 + 2 < d.nx, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
-    auto u2 = [&](int e) {
-        const float2 a = ld2(z, e), b = ld2(p_in, e);
-        return make_float2(a.x + beta * b.x, a.y + beta * b.y);
-    };
-    auto ldq = [&](Quad& U, Quad& Et, int e) {
-        const float2 a = u2(e), b = u2(e + d.nx);
-        const float2 ea = eta_load2(coef.eta, e), eb = eta_load2(coef.eta, e + d.nx);
-        U.v[0][0] = a.x; U.v[0][1] = a.y; U.v[1][0] = b.x; U.v[1][1] = b.y;
-        Et.v[0][0] = ea.x; Et.v[0][1] = ea.y; Et.v[1][0] = eb.x; Et.v[1][1] = eb.y;
-    };
-    auto ldh = [&](float2& hu, float2& he, int e) {
-        if (hk == 2) {
-            hu = u2(e);
-            he = eta_load2(coef.eta, e);
-        } else {
-            hu.x = z[e] + beta * p_in[e];
-            he.x = eta_load(coef.eta, e);
-        }
-    };
-    int c = x0 + d.nx * (y0 + d.ny * k0);
-    int h = gx + d.nx * (gy + d.ny * k0);
-    Quad um{}, em{}, u0{}, e0{}, up{}, ep{}, uq{}, eq{}, fzd{};
-    if (act) {
-        if (k0 > 0) ldq(um, em, c - d.sxy);
-        ldq(u0, e0, c);
-        if (k0 + 1 < d.nz) ldq(up, ep, c + d.sxy);
-        if (k0 > 0)
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) fzd.v[r][q] = rcp_approx(e0.v[r][q] + em.v[r][q]);
-    }
-    float2 hu = make_float2(0.f, 0.f), he = hu, hun = hu, hen = hu;
-    if (hv) ldh(hu, he, h);
+// k_cg_a_sm with 2 x 2 cells per thread (quad_march, plane_tile.cuh): p = z + beta p_in and
+// (p, A p) on QX x QY tiles of kc planes.  Grids with quad_tiles_fit only.
+struct BodyCgA {
+    static constexpr int NX = 0;
+    const float* in[1];
+    float* p_out;
+    int nx;
     float acc = 0.f;
-    for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
-        const int b = (k - k0) & 1;
-        float* U = Us[b];
-        float* Es = Ess[b];
-        st2(U, si, u0.v[0][0], u0.v[0][1]);
-        st2(U, si + QS, u0.v[1][0], u0.v[1][1]);
-        st2(Es, si, e0.v[0][0], e0.v[0][1]);
-        st2(Es, si + QS, e0.v[1][0], e0.v[1][1]);
-        if (hk == 2) {
-            st2(U, hi, hu.x, hu.y);
-            st2(Es, hi, he.x, he.y);
-        } else if (hk == 1) {
-            U[hi] = hu.x;
-            Es[hi] = he.x;
-        }
-        if (act && k + 1 < k1 && k + 2 < d.nz) ldq(uq, eq, c + 2 * d.sxy);
-        if (hv && k + 1 < k1) ldh(hun, hen, h + d.sxy);
-        __syncthreads();
-        if (act) {
-            Quad q, D;
-            quad_apply(d, k, xlo, xhi, ylo, yhi, u0, e0, um, up, ep, U, Es, si, fzd, q, D);
+    __device__ __forceinline__ void cell(int c, int, int, int, const Quad& u, const Quad& q,
+                                         const Quad&, const Quad*) {
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
+        for (int a = 0; a < 2; ++a)
 #pragma unroll
-                for (int cc = 0; cc < 2; ++cc) acc += u0.v[r][cc] * q.v[r][cc];
-            st2(p_out, c, u0.v[0][0], u0.v[0][1]);
-            st2(p_out, c + d.nx, u0.v[1][0], u0.v[1][1]);
-        }
-        um = u0; em = e0;
-        u0 = up; e0 = ep;
-        up = uq; ep = eq;
-        hu = hun; he = hen;
+            for (int b = 0; b < 2; ++b) acc += u.v[a][b] * q.v[a][b];
+        st2(p_out, c, u.v[0][0], u.v[0][1]);
+        st2(p_out, c + nx, u.v[1][0], u.v[1][1]);
     }
-    double v[1] = {(double)acc}, tot[1];
+};
+
+template <typename E>
+__global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_cg_a_q(Dims d, CoefEta<E> coef, int kc,
+                                                                const float* __restrict__ z,
+                                                                const float* __restrict__ p_in,
+                                                                float* __restrict__ p_out,
+                                                                Scalars* sc, double* partials) {
+    __shared__ double smem[64];
+    if (sc->done) return;
+    FieldSum F{z, p_in, (float)sc->beta};
+    BodyCgA B{{nullptr}, p_out, d.nx};
+    quad_march(d, coef.eta, kc, F, B);
+    double v[1] = {(double)B.acc}, tot[1];
     if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
         if (threadIdx.x == 0 && threadIdx.y == 0) {
             const double pq2 = tot[0];
@@ -868,6 +807,32 @@ __global__ void k_pad_rows(Dims d, int pad, const T* __restrict__ src, T* __rest
 }
 
 // ------------------------------------------------------------------ host launchers
+int quad_kc(const Dims& d) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0, n = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 152;
+        }
+        sms = n;
+    }
+    // blocks take time ~ kc + 2 (their planes plus the two look-ahead planes of the prologue);
+    // the grid takes ceil(blocks / resident blocks) of those
+    const long long tiles = (long long)(d.nx / QX) * ((d.ny + QY - 1) / QY);
+    const long long slots = (long long)sms * QUAD_BLOCKS;
+    long long kc = 64, best = -1;
+    for (long long k = 2; k <= 64; k += 2) {
+        const long long blocks = tiles * ((d.nz + k - 1) / k);
+        const long long t = ((blocks + slots - 1) / slots) * (k + 2);
+        // (a handle's reduction partials hold at least 4096 blocks)
+        if (blocks <= 4096 && (best < 0 || t < best)) { best = t; kc = k; }
+        if (k >= d.nz) break;
+    }
+    return (int)kc;
+}
+
 std::atomic<unsigned long long> g_kernel_launches{0};
 static inline void counted(int k) { g_kernel_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
 

@@ -643,97 +643,10 @@ __global__ void __launch_bounds__(TX * TY) k_mg_smooth_sm(Dims d, CoefEta<E> coe
 
 // ------------------------------------------------------------------ fine passes, 2 x 2 per thread
 // The fine-level passes of the V-cycle PCG on QX x QY tiles with 2 x 2 cells per thread
-// (plane_tile.cuh): the same arithmetic per cell as k_mg_cg_b_sm, the finest k_mg_restrict and
-// k_mg_smooth_sm.  Grids with quad_tiles_fit only (their aggregates are 2 x 2 in x-y).  A shared
-// skeleton marches the chunk: F supplies the stencil field u (own row pairs and halo cells) and
-// the per-cell inputs of the next plane, B the pass's use of u, A u and D on each plane.
-template <typename E, typename Field, typename Body>
-__device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, Field& F,
-                                           Body& B) {
-    __shared__ __align__(16) float Us[2][QN];
-    __shared__ __align__(16) float Ess[2][QN];
-    const int x0 = blockIdx.x * QX + 2 * threadIdx.x, y0 = blockIdx.y * QY + 2 * threadIdx.y;
-    const int k0 = blockIdx.z * kc;
-    const int k1 = min(d.nz, k0 + kc);
-    const bool act = y0 < d.ny;
-    const int si = q_index(2 * threadIdx.x, 2 * threadIdx.y);
-    int hx, hy;
-    const int hk = q_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
-    const int gx = blockIdx.x * QX + hx, gy = blockIdx.y * QY + hy;
-    const bool hv = hk && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
-    const int hi = hk ? q_index(hx, hy) : 0;
-    const bool xlo = x0 > 0, xhi = x0 + 2 < d.nx, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
-    auto ldq = [&](Quad& U, Quad& Et, int e, int k) {
-        const float2 a = F.pair(e, x0, y0, k), b = F.pair(e + d.nx, x0, y0 + 1, k);
-        const float2 ea = eta_load2(eta, e), eb = eta_load2(eta, e + d.nx);
-        U.v[0][0] = a.x; U.v[0][1] = a.y; U.v[1][0] = b.x; U.v[1][1] = b.y;
-        Et.v[0][0] = ea.x; Et.v[0][1] = ea.y; Et.v[1][0] = eb.x; Et.v[1][1] = eb.y;
-    };
-    auto ldh = [&](float2& hu, float2& he, int e, int k) {
-        if (hk == 2) {
-            hu = F.pair(e, gx, gy, k);
-            he = eta_load2(eta, e);
-        } else {
-            hu.x = F.one(e, gx, gy, k);
-            he.x = eta_load(eta, e);
-        }
-    };
-    int c = x0 + d.nx * (y0 + d.ny * k0);
-    int h = gx + d.nx * (gy + d.ny * k0);
-    Quad um{}, em{}, u0{}, e0{}, up{}, ep{}, uq{}, eq{}, fzd{};
-    if (act) {
-        if (k0 > 0) ldq(um, em, c - d.sxy, k0 - 1);
-        ldq(u0, e0, c, k0);
-        if (k0 + 1 < d.nz) ldq(up, ep, c + d.sxy, k0 + 1);
-        B.load(c, k0);
-        if (k0 > 0)
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-#pragma unroll
-                for (int q = 0; q < 2; ++q) fzd.v[r][q] = rcp_approx(e0.v[r][q] + em.v[r][q]);
-    }
-    float2 hu = make_float2(0.f, 0.f), he = hu, hun = hu, hen = hu;
-    if (hv) ldh(hu, he, h, k0);
-    for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
-        const int b = (k - k0) & 1;
-        float* U = Us[b];
-        float* Es = Ess[b];
-        st2(U, si, u0.v[0][0], u0.v[0][1]);
-        st2(U, si + QS, u0.v[1][0], u0.v[1][1]);
-        st2(Es, si, e0.v[0][0], e0.v[0][1]);
-        st2(Es, si + QS, e0.v[1][0], e0.v[1][1]);
-        if (hk == 2) {
-            st2(U, hi, hu.x, hu.y);
-            st2(Es, hi, he.x, he.y);
-        } else if (hk == 1) {
-            U[hi] = hu.x;
-            Es[hi] = he.x;
-        }
-        if (act && k + 1 < k1) {
-            B.prefetch(c + d.sxy, k + 1);
-            if (k + 2 < d.nz) ldq(uq, eq, c + 2 * d.sxy, k + 2);
-        }
-        if (hv && k + 1 < k1) ldh(hun, hen, h + d.sxy, k + 1);
-        __syncthreads();
-        if (act) {
-            Quad q, D;
-            quad_apply(d, k, xlo, xhi, ylo, yhi, u0, e0, um, up, ep, U, Es, si, fzd, q, D);
-            B.cell(c, x0, y0, k, u0, q, D);
-        }
-        um = u0; em = e0;
-        u0 = up; e0 = ep;
-        up = uq; ep = eq;
-        hu = hun; he = hen;
-        B.advance();
-    }
-}
-
-// Stencil fields: u = v, and u = x + alpha e(parent) (the prolongation of the smoothing).
-struct FieldPlain {
-    const float* v;
-    __device__ __forceinline__ float2 pair(int c, int, int, int) const { return ld2(v, c); }
-    __device__ __forceinline__ float one(int c, int, int, int) const { return v[c]; }
-};
+// (quad_march in plane_tile.cuh): the same arithmetic per cell as k_mg_cg_b_sm, the finest
+// k_mg_restrict and k_mg_smooth_sm.  Grids with quad_tiles_fit only (their aggregates are 2 x 2
+// in x-y).
+// Stencil field of the post-smoothing: u = x + alpha e(parent) (the prolongation).
 struct FieldProlong {
     const float* x;
     const float* e;
@@ -753,35 +666,25 @@ struct FieldProlong {
     }
 };
 
-// One per-cell input (r) or two (x, r), loaded a plane ahead as row pairs.
-struct Pair2 {
-    Quad cur{}, nxt{};
-    __device__ __forceinline__ void get(const float* a, int c, int nx, Quad& Q) {
-        const float2 p = ld2(a, c), q = ld2(a, c + nx);
-        Q.v[0][0] = p.x; Q.v[0][1] = p.y; Q.v[1][0] = q.x; Q.v[1][1] = q.y;
-    }
-};
-
-// Phase B of MG-PCG: x += alpha p; r -= alpha A p; x0 = w D^-1 r; (r, r).
+// Phase B of MG-PCG: x += alpha p; r -= alpha A p; x0 = w D^-1 r; (r, r).  Inputs x, r.
 struct BodyCgB {
+    static constexpr int NX = 2;
+    const float* in[NX];
     float* x;
     float* r;
     float* x0;
     float alpha, omega;
     int nx;
-    Pair2 X, R;
     float rr = 0.f;
-    __device__ __forceinline__ void load(int c, int) { X.get(x, c, nx, X.cur); R.get(r, c, nx, R.cur); }
-    __device__ __forceinline__ void prefetch(int c, int) { X.get(x, c, nx, X.nxt); R.get(r, c, nx, R.nxt); }
     __device__ __forceinline__ void cell(int c, int, int, int, const Quad& u, const Quad& q,
-                                         const Quad& D) {
+                                         const Quad& D, const Quad* X) {
         Quad xn, rn, zn;
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
-                xn.v[a][b] = X.cur.v[a][b] + alpha * u.v[a][b];
-                rn.v[a][b] = R.cur.v[a][b] - alpha * q.v[a][b];
+                xn.v[a][b] = X[0].v[a][b] + alpha * u.v[a][b];
+                rn.v[a][b] = X[1].v[a][b] - alpha * q.v[a][b];
                 zn.v[a][b] = omega * rn.v[a][b] / D.v[a][b];
                 rr += rn.v[a][b] * rn.v[a][b];
             }
@@ -792,29 +695,26 @@ struct BodyCgB {
         st2(x0, c, zn.v[0][0], zn.v[0][1]);
         st2(x0, c + nx, zn.v[1][0], zn.v[1][1]);
     }
-    __device__ __forceinline__ void advance() { X.cur = X.nxt; R.cur = R.nxt; }
 };
 
 // The finest restriction: r_c = P^T (r - A x0) over each 2 x 2 x fz block (children added x
-// fastest, then y, then z, as restrict_at), x_c = w r_c / D_c.
+// fastest, then y, then z, as restrict_at), x_c = w r_c / D_c.  Input r.
 struct BodyRestrict {
-    const float* r;
+    static constexpr int NX = 1;
+    const float* in[NX];
     float* rc;
     float* xc;
     const float* cdiag;
     Dims dc;
-    int nz, fz, nx;
+    int nz, fz;
     float omega;
-    Pair2 R;
     float s = 0.f;
-    __device__ __forceinline__ void load(int c, int) { R.get(r, c, nx, R.cur); }
-    __device__ __forceinline__ void prefetch(int c, int) { R.get(r, c, nx, R.nxt); }
     __device__ __forceinline__ void cell(int, int x0, int y0, int k, const Quad&, const Quad& q,
-                                         const Quad&) {
+                                         const Quad&, const Quad* X) {
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
-            for (int b = 0; b < 2; ++b) s += R.cur.v[a][b] - q.v[a][b];
+            for (int b = 0; b < 2; ++b) s += X[0].v[a][b] - q.v[a][b];
         if (fz == 1 || (k & 1) || k + 1 == nz) {
             const int I = (x0 >> 1) + dc.nx * ((y0 >> 1) + dc.ny * (fz == 1 ? k : k >> 1));
             rc[I] = s;
@@ -822,37 +722,33 @@ struct BodyRestrict {
             s = 0.f;
         }
     }
-    __device__ __forceinline__ void advance() { R.cur = R.nxt; }
 };
 
-// The fine post-smoothing: y = t + w D^-1 (r - A t), t = x0 + alpha e(parent); (r, y).
+// The fine post-smoothing: y = t + w D^-1 (r - A t), t = x0 + alpha e(parent); (r, y).  Input r.
 struct BodySmooth {
-    const float* r;
+    static constexpr int NX = 1;
+    const float* in[NX];
     float* y;
     float omega;
     int nx;
-    Pair2 R;
     float rz = 0.f;
-    __device__ __forceinline__ void load(int c, int) { R.get(r, c, nx, R.cur); }
-    __device__ __forceinline__ void prefetch(int c, int) { R.get(r, c, nx, R.nxt); }
     __device__ __forceinline__ void cell(int c, int, int, int, const Quad& u, const Quad& q,
-                                         const Quad& D) {
+                                         const Quad& D, const Quad* X) {
         Quad yn;
 #pragma unroll
         for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
-                yn.v[a][b] = u.v[a][b] + omega * (R.cur.v[a][b] - q.v[a][b]) / D.v[a][b];
-                rz += R.cur.v[a][b] * yn.v[a][b];
+                yn.v[a][b] = u.v[a][b] + omega * (X[0].v[a][b] - q.v[a][b]) / D.v[a][b];
+                rz += X[0].v[a][b] * yn.v[a][b];
             }
         st2(y, c, yn.v[0][0], yn.v[0][1]);
         st2(y, c + nx, yn.v[1][0], yn.v[1][1]);
     }
-    __device__ __forceinline__ void advance() { R.cur = R.nxt; }
 };
 
 template <typename E>
-__global__ void __launch_bounds__(TX * TY, 3) k_mg_cg_b_q(Dims d, CoefEta<E> coef, int kc,
+__global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_cg_b_q(Dims d, CoefEta<E> coef, int kc,
                                                          const float* __restrict__ p,
                                                          float* __restrict__ x,
                                                          float* __restrict__ r,
@@ -861,7 +757,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_mg_cg_b_q(Dims d, CoefEta<E> coe
     __shared__ double smem[64];
     if (sc->done) return;
     FieldPlain F{p};
-    BodyCgB B{x, r, x0, (float)sc->alpha, omega, d.nx};
+    BodyCgB B{{x, r}, x, r, x0, (float)sc->alpha, omega, d.nx};
     quad_march(d, coef.eta, kc, F, B);
     double v[1] = {(double)B.rr}, tot[1];
     if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
@@ -870,7 +766,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_mg_cg_b_q(Dims d, CoefEta<E> coe
 }
 
 template <typename E>
-__global__ void __launch_bounds__(TX * TY, 3) k_mg_restrict_q(Dims d, CoefEta<E> coef, int kc,
+__global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_restrict_q(Dims d, CoefEta<E> coef, int kc,
                                                              const float* __restrict__ r,
                                                              const float* __restrict__ x, Dims dc,
                                                              int fz, const float* __restrict__ cdiag,
@@ -879,12 +775,12 @@ __global__ void __launch_bounds__(TX * TY, 3) k_mg_restrict_q(Dims d, CoefEta<E>
                                                              const Scalars* sc) {
     if (sc && sc->done) return;
     FieldPlain F{x};
-    BodyRestrict B{r, rc, xc, cdiag, dc, d.nz, fz, d.nx, omega};
+    BodyRestrict B{{r}, rc, xc, cdiag, dc, d.nz, fz, omega};
     quad_march(d, coef.eta, kc, F, B);
 }
 
 template <typename E>
-__global__ void __launch_bounds__(TX * TY, 3) k_mg_smooth_q(Dims d, CoefEta<E> coef, int kc,
+__global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_smooth_q(Dims d, CoefEta<E> coef, int kc,
                                                            const float* __restrict__ r,
                                                            const float* __restrict__ x,
                                                            const float* __restrict__ e, Dims dc,
@@ -894,7 +790,7 @@ __global__ void __launch_bounds__(TX * TY, 3) k_mg_smooth_q(Dims d, CoefEta<E> c
     __shared__ double smem[64];
     if (sc && sc->done) return;
     FieldProlong F{x, e, dc, sz, alpha};
-    BodySmooth B{r, y, omega, d.nx};
+    BodySmooth B{{r}, y, omega, d.nx};
     quad_march(d, coef.eta, kc, F, B);
     if (mode < 0 || !sc) return;
     reduce_rz(B.rz, sc, partials, smem, mode);

@@ -67,15 +67,9 @@ inline bool quad_tiles_fit(const Dims& d) {
 }
 
 // z-chunk of the quad kernels: even (a coarse plane of the restriction never straddles two
-// chunks), about four blocks per SM of 152 on the plane tiles.
-inline int quad_kc(const Dims& d) {
-    const long long tiles = (long long)(d.nx / QX) * ((d.ny + QY - 1) / QY);
-    long long kc = (tiles * d.nz) / 608;
-    kc &= ~1LL;
-    if (kc < 2) kc = 2;
-    if (kc > 64) kc = 64;
-    return (int)kc;
-}
+// chunks), at most 64 planes, chosen for the fewest block-waves (QUAD_BLOCKS per SM) times the
+// planes a block walks.
+int quad_kc(const Dims& d);
 
 inline dim3 quad_grid(const Dims& d, int kc) {
     return dim3(d.nx / QX, (d.ny + QY - 1) / QY, (d.nz + kc - 1) / kc);
@@ -174,6 +168,150 @@ __device__ __forceinline__ void quad_apply(const Dims& d, int k, bool xlo, bool 
             if (zlo) s += zm * um.v[r][c];
             if (!top) s += zp * up.v[r][c];
             q.v[r][c] = D.v[r][c] * u.v[r][c] - s;
+        }
+    }
+}
+
+
+// Blocks per SM the quad kernels are built for (their register budget) and planes of look-ahead
+// of their loads: the stencil field and rho/2 are loaded QUAD_DEPTH planes ahead of the plane
+// being computed, the per-cell inputs and the halo QUAD_DEPTH - 1 planes ahead.
+constexpr int QUAD_BLOCKS = 3;
+constexpr int QUAD_DEPTH = 2;
+
+// Stencil fields of the quad kernels: u = v, and u = a + beta b (CG phase A: p = z + beta p).
+struct FieldPlain {
+    const float* v;
+    __device__ __forceinline__ float2 pair(int c, int, int, int) const { return ld2(v, c); }
+    __device__ __forceinline__ float one(int c, int, int, int) const { return v[c]; }
+};
+struct FieldSum {
+    const float* a;
+    const float* b;
+    float beta;
+    __device__ __forceinline__ float2 pair(int c, int, int, int) const {
+        const float2 p = ld2(a, c), q = ld2(b, c);
+        return make_float2(p.x + beta * q.x, p.y + beta * q.y);
+    }
+    __device__ __forceinline__ float one(int c, int, int, int) const { return a[c] + beta * b[c]; }
+};
+
+// The quad kernels' march over one block's tile and z-chunk.  F gives the stencil field u at a
+// cell pair (float2) or one cell; Body has NX per-cell inputs in[] (loaded as row pairs) and
+// cell(c, x0, y0, k, u, A u, D, inputs) for the thread's 2 x 2 cells of plane k.  The block's
+// threads publish plane k (their own cells and the halo) in a shared plane, one barrier per plane
+// (two buffers); planes k - 1 and k + 1 of the own cells stay in registers.
+template <typename E, typename Field, typename Body>
+__device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, const Field& F,
+                                           Body& B) {
+    constexpr int D = QUAD_DEPTH;
+    constexpr int NX = Body::NX > 0 ? Body::NX : 1;
+    __shared__ __align__(16) float Us[2][QN];
+    __shared__ __align__(16) float Ess[2][QN];
+    const int x0 = blockIdx.x * QX + 2 * threadIdx.x, y0 = blockIdx.y * QY + 2 * threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    const bool act = y0 < d.ny;
+    const int si = q_index(2 * threadIdx.x, 2 * threadIdx.y);
+    int hx, hy;
+    const int hk = q_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
+    const int gx = blockIdx.x * QX + hx, gy = blockIdx.y * QY + hy;
+    const bool hv = hk && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+    const int hi = hk ? q_index(hx, hy) : 0;
+    const bool xlo = x0 > 0, xhi = x0 + 2 < d.nx, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
+    auto ldq = [&](Quad& U, Quad& Et, int e, int k) {
+        const float2 a = F.pair(e, x0, y0, k), b = F.pair(e + d.nx, x0, y0 + 1, k);
+        const float2 ea = eta_load2(eta, e), eb = eta_load2(eta, e + d.nx);
+        U.v[0][0] = a.x; U.v[0][1] = a.y; U.v[1][0] = b.x; U.v[1][1] = b.y;
+        Et.v[0][0] = ea.x; Et.v[0][1] = ea.y; Et.v[1][0] = eb.x; Et.v[1][1] = eb.y;
+    };
+    auto ldx = [&](Quad (&X)[NX][D], int t, int e) {
+#pragma unroll
+        for (int q = 0; q < Body::NX; ++q) {
+            const float2 a = ld2(B.in[q], e), b = ld2(B.in[q], e + d.nx);
+            X[q][t].v[0][0] = a.x; X[q][t].v[0][1] = a.y;
+            X[q][t].v[1][0] = b.x; X[q][t].v[1][1] = b.y;
+        }
+    };
+    auto ldh = [&](float2& hu, float2& he, int e, int k) {
+        if (hk == 2) {
+            hu = F.pair(e, gx, gy, k);
+            he = eta_load2(eta, e);
+        } else {
+            hu.x = F.one(e, gx, gy, k);
+            he.x = eta_load(eta, e);
+        }
+    };
+    int c = x0 + d.nx * (y0 + d.ny * k0);
+    int h = gx + d.nx * (gy + d.ny * k0);
+    // U[s], Et[s]: planes k - 1 + s (s = 0 .. D + 1); X[.][t], HU[t], HE[t]: planes k + t
+    Quad U[D + 2], Et[D + 2], X[NX][D], fzd{};
+    float2 HU[D], HE[D];
+#pragma unroll
+    for (int s2 = 0; s2 < D + 2; ++s2) { U[s2] = Quad{}; Et[s2] = Quad{}; }
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+        HU[t] = make_float2(0.f, 0.f);
+        HE[t] = HU[t];
+#pragma unroll
+        for (int q = 0; q < NX; ++q) X[q][t] = Quad{};
+    }
+    if (act) {
+#pragma unroll
+        for (int s2 = 0; s2 <= D; ++s2) {
+            const int m = k0 - 1 + s2;
+            if (m >= 0 && m < d.nz && m <= k1) ldq(U[s2], Et[s2], c + (s2 - 1) * d.sxy, m);
+        }
+#pragma unroll
+        for (int t = 0; t + 1 < D; ++t)
+            if (k0 + t < k1) ldx(X, t, c + t * d.sxy);
+        if (k0 > 0)
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int q = 0; q < 2; ++q) fzd.v[r][q] = rcp_approx(Et[1].v[r][q] + Et[0].v[r][q]);
+    }
+    if (hv)
+#pragma unroll
+        for (int t = 0; t + 1 < D; ++t)
+            if (k0 + t < k1) ldh(HU[t], HE[t], h + t * d.sxy, k0 + t);
+    for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
+        const int b = (k - k0) & 1;
+        float* Up = Us[b];
+        float* Es = Ess[b];
+        st2(Up, si, U[1].v[0][0], U[1].v[0][1]);
+        st2(Up, si + QS, U[1].v[1][0], U[1].v[1][1]);
+        st2(Es, si, Et[1].v[0][0], Et[1].v[0][1]);
+        st2(Es, si + QS, Et[1].v[1][0], Et[1].v[1][1]);
+        if (hk == 2) {
+            st2(Up, hi, HU[0].x, HU[0].y);
+            st2(Es, hi, HE[0].x, HE[0].y);
+        } else if (hk == 1) {
+            Up[hi] = HU[0].x;
+            Es[hi] = HE[0].x;
+        }
+        if (act) {
+            if (k + D <= k1 && k + D < d.nz) ldq(U[D + 1], Et[D + 1], c + D * d.sxy, k + D);
+            if (k + D - 1 < k1) ldx(X, D - 1, c + (D - 1) * d.sxy);
+        }
+        if (hv && k + D - 1 < k1) ldh(HU[D - 1], HE[D - 1], h + (D - 1) * d.sxy, k + D - 1);
+        __syncthreads();
+        if (act) {
+            Quad q, Dg, Xc[NX];
+#pragma unroll
+            for (int t = 0; t < NX; ++t) Xc[t] = X[t][0];
+            quad_apply(d, k, xlo, xhi, ylo, yhi, U[1], Et[1], U[0], U[2], Et[2], Up, Es, si, fzd,
+                       q, Dg);
+            B.cell(c, x0, y0, k, U[1], q, Dg, Xc);
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < D + 1; ++s2) { U[s2] = U[s2 + 1]; Et[s2] = Et[s2 + 1]; }
+#pragma unroll
+        for (int t = 0; t + 1 < D; ++t) {
+            HU[t] = HU[t + 1];
+            HE[t] = HE[t + 1];
+#pragma unroll
+            for (int q = 0; q < NX; ++q) X[q][t] = X[q][t + 1];
         }
     }
 }
