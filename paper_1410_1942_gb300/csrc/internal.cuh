@@ -14,6 +14,8 @@
 //     symmetric weighted graph Laplacian whose diagonal is the sum of its own faces.
 #pragma once
 
+#include <type_traits>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -63,6 +65,16 @@ __device__ __forceinline__ float rcp_approx(float x) {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// (launch_pdl) may start while the kernel before it in the stream is still running.  It waits
+// here, before touching global memory, until that kernel has completed and its writes are
+// visible, and lets the next kernel of the stream begin launching.  Without the launch attribute
+// both instructions do nothing.
+__device__ __forceinline__ void pdl_entry() {
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
 // ------------------------------------------------------------------ block reductions (FP64)
@@ -243,6 +255,10 @@ struct CoefEta {
         eta_stencil(d, i, j, k, ec, exm, exp_, eym, eyp, ezm, ezp, w);
     }
 };
+
+// rho/2's element type of a CoefEta policy
+template <typename C>
+using EtaOf = std::remove_const_t<std::remove_pointer_t<decltype(C::eta)>>;
 
 template <typename C>
 struct is_coef_eta { static constexpr bool value = false; };

@@ -264,6 +264,7 @@ __global__ void __launch_bounds__(TX * TY) k_cg_a(Dims d, Coef coef, int kc,
                                                  const V* __restrict__ p_in,
                                                  V* __restrict__ p_out, Scalars* sc,
                                                  double* partials) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc->done) return;
     const V beta = (V)sc->beta;
@@ -301,6 +302,7 @@ __global__ void __launch_bounds__(TX * TY) k_cg_a_eta(Dims d, CoefEta<E> coef, i
                                                      const float* __restrict__ p_in,
                                                      float* __restrict__ p_out, Scalars* sc,
                                                      double* partials) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc->done) return;
     const float beta = (float)sc->beta;
@@ -363,6 +365,7 @@ __global__ void __launch_bounds__(TX * TY) k_cg_a_sm(Dims d, CoefEta<E> coef, in
                                                     const float* __restrict__ p_in,
                                                     float* __restrict__ p_out, Scalars* sc,
                                                     double* partials) {
+    pdl_entry();
     __shared__ double smem[64];
     __shared__ float Ps[2][PT_N], Es[2][PT_N];
     if (sc->done) return;
@@ -462,6 +465,7 @@ __global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_cg_a_q(Dims d, CoefEta
                                                                 const float* __restrict__ p_in,
                                                                 float* __restrict__ p_out,
                                                                 Scalars* sc, double* partials) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc->done) return;
     FieldSum F{z, p_in, (float)sc->beta};
@@ -932,15 +936,15 @@ void launch_cg_a(const Dims& d, int kc, const Coef& c, const V* z, const V* p_in
                  Scalars* sc, double* part, cudaStream_t st) {
     if constexpr (is_coef_eta<Coef>::value) {
         if (quad_tiles_fit(d))
-            k_cg_a_q<<<quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st>>>(d, c, quad_kc(d), z, p_in,
+            launch_pdl(k_cg_a_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st, d, c, quad_kc(d), z, p_in,
                                                                        p_out, sc, part);
         else if (plane_tiles_fit(d))
-            k_cg_a_sm<<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
+            launch_pdl(k_cg_a_sm<EtaOf<Coef>>, grid_of(d, kc), dim3(TX, TY), 0, st, d, c, kc, z, p_in, p_out, sc, part);
         else
-            k_cg_a_eta<<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc,
+            launch_pdl(k_cg_a_eta<EtaOf<Coef>>, grid_of(d, kc), dim3(TX, TY), 0, st, d, c, kc, z, p_in, p_out, sc,
                                                                 part);
     } else
-        k_cg_a<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, z, p_in, p_out, sc, part);
+        launch_pdl(k_cg_a<V, Coef>, grid_of(d, kc), dim3(TX, TY), 0, st, d, c, kc, z, p_in, p_out, sc, part);
     counted(1);
 }
 

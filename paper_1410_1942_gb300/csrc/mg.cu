@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(MT) k_mg_restrict(Dims df, Coef coef, const V*
                                                     int fy, int fz, const V* __restrict__ cdiag,
                                                     V* __restrict__ rc, V* __restrict__ xc,
                                                     V omega, const Scalars* sc) {
+    pdl_entry();
     if (sc && sc->done) return;
     const long long t = blockIdx.x * (long long)MT + threadIdx.x;
     if (t >= dc.n) return;
@@ -141,6 +142,7 @@ __global__ void __launch_bounds__(MT) k_mg_restrict8(Dims df, Coef coef, const V
                                                     int fy, int fz, const V* __restrict__ cdiag,
                                                     V* __restrict__ rc, V* __restrict__ xc,
                                                     V omega, const Scalars* sc) {
+    pdl_entry();
     if (sc && sc->done) return;
     const long long t = blockIdx.x * (long long)MT + threadIdx.x;
     const long long I = t >> 3;
@@ -250,6 +252,7 @@ struct Bottom {
 template <typename V>
 __global__ void __launch_bounds__(COARSE_T) k_mg_bottom(Bottom<V> B, V omega, V alpha, int sweeps,
                                                         const Scalars* sc) {
+    pdl_entry();
     __shared__ V buf[2][MG_COARSE_MAX];
     if (sc && sc->done) return;
     using LC = LevelCoef<V>;
@@ -321,6 +324,7 @@ __global__ void __launch_bounds__(TX * TY) k_mg_smooth(Dims d, Coef coef, int kc
                                                       int sy, int sz, V alpha, V omega,
                                                       V* __restrict__ y, Scalars* sc,
                                                       double* partials, int mode) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc && sc->done) return;
     V rz = 0;
@@ -350,6 +354,7 @@ __global__ void __launch_bounds__(TX * TY) k_mg_cg_b_eta(Dims d, CoefEta<E> coef
                                                         float* __restrict__ r,
                                                         float* __restrict__ x0, float omega,
                                                         Scalars* sc, double* partials) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc->done) return;
     const float alpha = (float)sc->alpha;
@@ -411,6 +416,7 @@ __global__ void __launch_bounds__(TX * TY, 5) k_mg_smooth_eta(Dims d, CoefEta<E>
                                                              float alpha, float omega,
                                                              float* __restrict__ y, Scalars* sc,
                                                              double* partials, int mode) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc && sc->done) return;
     const int i = blockIdx.x * TX + threadIdx.x;
@@ -476,6 +482,7 @@ __global__ void __launch_bounds__(TX * TY) k_mg_cg_b_sm(Dims d, CoefEta<E> coef,
                                                        float* __restrict__ r,
                                                        float* __restrict__ x0, float omega,
                                                        Scalars* sc, double* partials) {
+    pdl_entry();
     __shared__ double smem[64];
     __shared__ float Ps[2][PT_N], Es[2][PT_N];
     if (sc->done) return;
@@ -561,6 +568,7 @@ __global__ void __launch_bounds__(TX * TY) k_mg_smooth_sm(Dims d, CoefEta<E> coe
                                                          float omega, float* __restrict__ y,
                                                          Scalars* sc, double* partials,
                                                          int mode) {
+    pdl_entry();
     __shared__ double smem[64];
     __shared__ float Ts[2][PT_N], Es[2][PT_N];
     if (sc && sc->done) return;
@@ -754,6 +762,7 @@ __global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_cg_b_q(Dims d, Coef
                                                          float* __restrict__ r,
                                                          float* __restrict__ x0, float omega,
                                                          Scalars* sc, double* partials) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc->done) return;
     FieldPlain F{p};
@@ -773,6 +782,7 @@ __global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_restrict_q(Dims d, 
                                                              float* __restrict__ rc,
                                                              float* __restrict__ xc, float omega,
                                                              const Scalars* sc) {
+    pdl_entry();
     if (sc && sc->done) return;
     FieldPlain F{x};
     BodyRestrict B{{r}, rc, xc, cdiag, dc, d.nz, fz, omega};
@@ -787,6 +797,7 @@ __global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_smooth_q(Dims d, Co
                                                            int sz, float alpha, float omega,
                                                            float* __restrict__ y, Scalars* sc,
                                                            double* partials, int mode) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc && sc->done) return;
     FieldProlong F{x, e, dc, sz, alpha};
@@ -804,6 +815,7 @@ __global__ void __launch_bounds__(TX * TY) k_mg_first(Dims d, Coef coef, int kc,
                                                      V* __restrict__ x0, V omega, Scalars* sc,
                                                      double* partials, double tol2, int rel_to_b,
                                                      int max_iter) {
+    pdl_entry();
     __shared__ double smem[64];
     V rr = 0;
     const int i = blockIdx.x * TX + threadIdx.x;
@@ -843,6 +855,7 @@ __global__ void __launch_bounds__(TX * TY) k_mg_cg_b(Dims d, Coef coef, int kc,
                                                     const V* __restrict__ p, V* __restrict__ x,
                                                     V* __restrict__ r, V* __restrict__ x0,
                                                     V omega, Scalars* sc, double* partials) {
+    pdl_entry();
     __shared__ double smem[64];
     if (sc->done) return;
     const V alpha = (V)sc->alpha;
@@ -889,7 +902,7 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
         bool done = false;
         if constexpr (is_coef_eta<Coef>::value) {
             if (l == 0 && quad_tiles_fit(df)) {
-                k_mg_restrict_q<<<quad_grid(df, quad_kc(df)), dim3(TX, TY), 0, st>>>(
+                launch_pdl(k_mg_restrict_q<EtaOf<Coef>>, quad_grid(df, quad_kc(df)), dim3(TX, TY), 0, st,
                     df, coef, quad_kc(df), r, (const V*)m->x[0], dc, f[2], (const V*)m->diag[1],
                     (V*)m->r[1], (V*)m->x[1], om, sc);
                 done = true;
@@ -897,11 +910,11 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
         }
         if (done) {
         } else if (l == 0)
-            k_mg_restrict<V, Coef><<<blocks_of(dc.n), MT, 0, st>>>(
+            launch_pdl(k_mg_restrict<V, Coef>, blocks_of(dc.n), MT, 0, st,
                 df, coef, r, (const V*)m->x[0], dc, f[0], f[1], f[2], (const V*)m->diag[1],
                 (V*)m->r[1], (V*)m->x[1], om, sc);
         else
-            k_mg_restrict8<V, typename LC::type><<<blocks_of(8LL * dc.n), MT, 0, st>>>(
+            launch_pdl(k_mg_restrict8<V, typename LC::type>, blocks_of(8LL * dc.n), MT, 0, st,
                 df, LC::of(*m, l), (const V*)m->r[l], (const V*)m->x[l], dc, f[0], f[1], f[2],
                 (const V*)m->diag[l + 1], (V*)m->r[l + 1], (V*)m->x[l + 1], om, sc);
     }
@@ -919,10 +932,10 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
         B.x[q] = (V*)m->x[l];
         B.y[q] = (V*)m->y[l];
     }
-    k_mg_bottom<V><<<1, COARSE_T, 0, st>>>(B, om, al, MG_COARSE_SWEEPS, sc);
+    launch_pdl(k_mg_bottom<V>, 1, COARSE_T, 0, st, B, om, al, MG_COARSE_SWEEPS, sc);
     for (int l = b - 1; l >= 1; --l) {
         const int* f = m->f[l];
-        k_mg_smooth<V, typename LC::type><<<cols(m->d[l], 1), dim3(TX, TY), 0, st>>>(
+        launch_pdl(k_mg_smooth<V, typename LC::type>, cols(m->d[l], 1), dim3(TX, TY), 0, st,
             m->d[l], LC::of(*m, l), 1, (const V*)m->r[l], (const V*)m->x[l],
             (const V*)m->y[l + 1], m->d[l + 1], f[0] - 1, f[1] - 1, f[2] - 1, al, om,
             (V*)m->y[l], sc, nullptr, -1);
@@ -930,19 +943,19 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
     const int* f = m->f[0];
     if constexpr (is_coef_eta<Coef>::value) {
         if (quad_tiles_fit(d))
-            k_mg_smooth_q<<<quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st>>>(
+            launch_pdl(k_mg_smooth_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st,
                 d, coef, quad_kc(d), r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[2] - 1,
                 al, om, z, sc, part, mode);
         else if (plane_tiles_fit(d))
-            k_mg_smooth_sm<<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+            launch_pdl(k_mg_smooth_sm<EtaOf<Coef>>, cols(d, kc), dim3(TX, TY), 0, st,
                 d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1,
                 f[1] - 1, f[2] - 1, al, om, z, sc, part, mode);
         else
-            k_mg_smooth_eta<<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+            launch_pdl(k_mg_smooth_eta<EtaOf<Coef>>, cols(d, kc), dim3(TX, TY), 0, st,
                 d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1,
                 f[1] - 1, f[2] - 1, al, om, z, sc, part, mode);
     } else
-        k_mg_smooth<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+        launch_pdl(k_mg_smooth<V, Coef>, cols(d, kc), dim3(TX, TY), 0, st,
             d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
             f[2] - 1, al, om, z, sc, part, mode);
     counted(2 * b + 1);
@@ -1041,7 +1054,7 @@ void mg_setup(MgHier* m, const double* bx, const double* by, const double* bz,
 template <typename V, typename Coef>
 void mg_init(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z, Scalars* sc,
              double* part, double tol2, int rel_to_b, int max_iter, cudaStream_t st) {
-    k_mg_first<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+    launch_pdl(k_mg_first<V, Coef>, cols(d, kc), dim3(TX, TY), 0, st,
         d, coef, kc, r, (V*)m->x[0], (V)MG_OMEGA, sc, part, tol2, rel_to_b, max_iter);
     counted(1);
     vcycle<V, Coef>(m, d, kc, coef, r, z, sc, part, 0, st);
@@ -1052,18 +1065,18 @@ void mg_cg_b(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* p, V* 
              Scalars* sc, double* part, cudaStream_t st) {
     if constexpr (is_coef_eta<Coef>::value) {
         if (quad_tiles_fit(d))
-            k_mg_cg_b_q<<<quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st>>>(
+            launch_pdl(k_mg_cg_b_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st,
                 d, coef, quad_kc(d), p, x, r, (V*)m->x[0], (V)MG_OMEGA, sc, part);
         else if (plane_tiles_fit(d))
-            k_mg_cg_b_sm<<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r,
+            launch_pdl(k_mg_cg_b_sm<EtaOf<Coef>>, cols(d, kc), dim3(TX, TY), 0, st, d, coef, kc, p, x, r,
                                                                (V*)m->x[0], (V)MG_OMEGA, sc,
                                                                part);
         else
-            k_mg_cg_b_eta<<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r,
+            launch_pdl(k_mg_cg_b_eta<EtaOf<Coef>>, cols(d, kc), dim3(TX, TY), 0, st, d, coef, kc, p, x, r,
                                                                 (V*)m->x[0], (V)MG_OMEGA, sc,
                                                                 part);
     } else
-        k_mg_cg_b<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(d, coef, kc, p, x, r,
+        launch_pdl(k_mg_cg_b<V, Coef>, cols(d, kc), dim3(TX, TY), 0, st, d, coef, kc, p, x, r,
                                                                 (V*)m->x[0], (V)MG_OMEGA, sc,
                                                                 part);
     counted(1);
@@ -1073,7 +1086,7 @@ void mg_cg_b(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* p, V* 
 template <typename V, typename Coef>
 void mg_apply(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z,
               cudaStream_t st) {
-    k_mg_first<V, Coef><<<cols(d, kc), dim3(TX, TY), 0, st>>>(
+    launch_pdl(k_mg_first<V, Coef>, cols(d, kc), dim3(TX, TY), 0, st,
         d, coef, kc, r, (V*)m->x[0], (V)MG_OMEGA, nullptr, nullptr, 0.0, 0, 0);
     counted(1);
     vcycle<V, Coef>(m, d, kc, coef, r, z, nullptr, nullptr, -1, st);
