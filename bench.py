@@ -327,10 +327,20 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- measurements
+def persistent_path(desc):
+    """Whether a handle's inner solve is one persistent launch (its per-kernel events bracket
+    whole solves and cost nothing between kernels)."""
+    return any(w in desc for w in ("one-sweep", "red-black", "persistent"))
+
+
 def timed_solves(solver, F, s, p, tol, steps, warmup, stream, sync, clocks=None, flush=None,
                  allow=None):
     """`warmup` untimed then `steps` timed solves (set_density + solve from p = 0), each
-    bracketed by CUDA events on the solver's stream; returns the device time and the counts."""
+    bracketed by CUDA events on the solver's stream; returns the device time and the counts.
+    The library's per-kernel events (poisson_profile) record during the timed solves when the
+    inner solve is one persistent launch.  For the column kernels they are off while timing
+    (between two kernels they would stop the next launch from overlapping the previous one's
+    tail) and the per-kernel times come from one more solve, profiled, after the timed region."""
     from paper_1410_1942_gb300 import capi
     allow = allow or (capi.OK,)
 
@@ -343,7 +353,9 @@ def timed_solves(solver, F, s, p, tol, steps, warmup, stream, sync, clocks=None,
     import torch
     for _ in range(warmup):
         step()
-    solver.profile(True)
+    live = persistent_path(solver.describe())
+    if live:
+        solver.profile(True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
     iters, outer, rels = 0, 0, []
@@ -364,14 +376,24 @@ def timed_solves(solver, F, s, p, tol, steps, warmup, stream, sync, clocks=None,
     launches = capi.kernel_launches() - l0
     clk = clocks.stop() if clocks else None
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if live:
+        prof_iters = iters
+    else:
+        solver.profile(True)
+        prof_iters = step()["inner_iters"]
+        sync()
     prof = solver.profile_read()
     solver.profile(False)
+    prof["from"] = ("the timed solves" if live else
+                    "one solve after the timed region (events between column kernels would "
+                    "serialise their launches)")
     return {"dev_ms": dev_ms, "iters": iters, "outer": outer, "rels": rels,
-            "launches": launches, "clocks": clk, "prof": prof}
+            "launches": launches, "clocks": clk, "prof": prof, "prof_iters": prof_iters}
 
 
 def roofline(prof, desc, precision, precond, g, iters, periodic, kind):
-    """The dominant CG kernel's algorithmic bytes per launch over its mean event time."""
+    """The dominant CG kernel's algorithmic bytes per launch over its mean event time (prof: the
+    per-kernel times of one profiled solve of `iters` CG iterations)."""
     bpc = BYTES_PER_CELL[precision]
     cands = [k for k in ("pcg_persistent", "cg_phase_a", "cg_phase_b") if prof[k]["launches"]]
     dom = max(cands, key=lambda k: prof[k]["ms"])
@@ -592,7 +614,7 @@ def solver_line(sv, F, s, g, steps, warmup, stream, precision, precond, kind, fl
     r = timed_solves(sv, F, s, p, TOL, steps, warmup, stream, torch.cuda.synchronize, flush=flush)
     value = g.n * r["iters"] / (r["dev_ms"] * 1e-3) / 1e9
     desc = sv.describe()
-    roof = roofline(r["prof"], desc, precision, precond, g, r["iters"], False, kind)
+    roof = roofline(r["prof"], desc, precision, precond, g, r["prof_iters"], False, kind)
     return {"value": value, "unit": "Gcell-iters/s", "precision": precision, "precond": precond,
             "solves_per_s": steps / (r["dev_ms"] * 1e-3), "ms_per_solve": r["dev_ms"] / steps,
             "cg_iters_per_solve": r["iters"] / steps, "outer_iters_per_solve": r["outer"] / steps,
@@ -691,7 +713,7 @@ def main(argv=None):
     t_max, units = combine_ranks(r["dev_ms"], units, dev, world)
     value = units / (t_max * 1e-3) / 1e9
     desc = solver.describe()
-    roof = roofline(r["prof"], desc, args.precision, args.precond, g, r["iters"],
+    roof = roofline(r["prof"], desc, args.precision, args.precond, g, r["prof_iters"],
                     args.periodic_x, kind)
     solver.close()
     del p_d

@@ -460,7 +460,7 @@ struct BodyCgA {
 };
 
 template <typename E>
-__global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_cg_a_q(Dims d, CoefEta<E> coef, int kc,
+__global__ void __launch_bounds__(TX * TY, QB_CG_A) k_cg_a_q(Dims d, CoefEta<E> coef, int kc,
                                                                 const float* __restrict__ z,
                                                                 const float* __restrict__ p_in,
                                                                 float* __restrict__ p_out,
@@ -811,7 +811,7 @@ __global__ void k_pad_rows(Dims d, int pad, const T* __restrict__ src, T* __rest
 }
 
 // ------------------------------------------------------------------ host launchers
-int quad_kc(const Dims& d) {
+int quad_kc(const Dims& d, int blocks_per_sm) {
     static int sms = 0;
     if (sms == 0) {
         int dev = 0, n = 0;
@@ -825,7 +825,7 @@ int quad_kc(const Dims& d) {
     // blocks take time ~ kc + 2 (their planes plus the two look-ahead planes of the prologue);
     // the grid takes ceil(blocks / resident blocks) of those
     const long long tiles = (long long)(d.nx / QX) * ((d.ny + QY - 1) / QY);
-    const long long slots = (long long)sms * QUAD_BLOCKS;
+    const long long slots = (long long)sms * blocks_per_sm;
     long long kc = 64, best = -1;
     for (long long k = 2; k <= 64; k += 2) {
         const long long blocks = tiles * ((d.nz + k - 1) / k);
@@ -936,7 +936,8 @@ void launch_cg_a(const Dims& d, int kc, const Coef& c, const V* z, const V* p_in
                  Scalars* sc, double* part, cudaStream_t st) {
     if constexpr (is_coef_eta<Coef>::value) {
         if (quad_tiles_fit(d))
-            launch_pdl(k_cg_a_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st, d, c, quad_kc(d), z, p_in,
+            launch_pdl(k_cg_a_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d, QB_CG_A)), dim3(TX, TY), 0, st, d, c,
+                       quad_kc(d, QB_CG_A), z, p_in,
                                                                        p_out, sc, part);
         else if (plane_tiles_fit(d))
             launch_pdl(k_cg_a_sm<EtaOf<Coef>>, grid_of(d, kc), dim3(TX, TY), 0, st, d, c, kc, z, p_in, p_out, sc, part);

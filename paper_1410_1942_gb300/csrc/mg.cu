@@ -756,7 +756,7 @@ struct BodySmooth {
 };
 
 template <typename E>
-__global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_cg_b_q(Dims d, CoefEta<E> coef, int kc,
+__global__ void __launch_bounds__(TX * TY, QB_CG_B) k_mg_cg_b_q(Dims d, CoefEta<E> coef, int kc,
                                                          const float* __restrict__ p,
                                                          float* __restrict__ x,
                                                          float* __restrict__ r,
@@ -775,7 +775,7 @@ __global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_cg_b_q(Dims d, Coef
 }
 
 template <typename E>
-__global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_restrict_q(Dims d, CoefEta<E> coef, int kc,
+__global__ void __launch_bounds__(TX * TY, QB_RESTRICT) k_mg_restrict_q(Dims d, CoefEta<E> coef, int kc,
                                                              const float* __restrict__ r,
                                                              const float* __restrict__ x, Dims dc,
                                                              int fz, const float* __restrict__ cdiag,
@@ -790,7 +790,7 @@ __global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_restrict_q(Dims d, 
 }
 
 template <typename E>
-__global__ void __launch_bounds__(TX * TY, QUAD_BLOCKS) k_mg_smooth_q(Dims d, CoefEta<E> coef, int kc,
+__global__ void __launch_bounds__(TX * TY, QB_SMOOTH) k_mg_smooth_q(Dims d, CoefEta<E> coef, int kc,
                                                            const float* __restrict__ r,
                                                            const float* __restrict__ x,
                                                            const float* __restrict__ e, Dims dc,
@@ -902,8 +902,8 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
         bool done = false;
         if constexpr (is_coef_eta<Coef>::value) {
             if (l == 0 && quad_tiles_fit(df)) {
-                launch_pdl(k_mg_restrict_q<EtaOf<Coef>>, quad_grid(df, quad_kc(df)), dim3(TX, TY), 0, st,
-                    df, coef, quad_kc(df), r, (const V*)m->x[0], dc, f[2], (const V*)m->diag[1],
+                launch_pdl(k_mg_restrict_q<EtaOf<Coef>>, quad_grid(df, quad_kc(df, QB_RESTRICT)),
+                           dim3(TX, TY), 0, st, df, coef, quad_kc(df, QB_RESTRICT), r, (const V*)m->x[0], dc, f[2], (const V*)m->diag[1],
                     (V*)m->r[1], (V*)m->x[1], om, sc);
                 done = true;
             }
@@ -943,8 +943,8 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
     const int* f = m->f[0];
     if constexpr (is_coef_eta<Coef>::value) {
         if (quad_tiles_fit(d))
-            launch_pdl(k_mg_smooth_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st,
-                d, coef, quad_kc(d), r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[2] - 1,
+            launch_pdl(k_mg_smooth_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d, QB_SMOOTH)), dim3(TX, TY),
+                       0, st, d, coef, quad_kc(d, QB_SMOOTH), r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[2] - 1,
                 al, om, z, sc, part, mode);
         else if (plane_tiles_fit(d))
             launch_pdl(k_mg_smooth_sm<EtaOf<Coef>>, cols(d, kc), dim3(TX, TY), 0, st,
@@ -1065,8 +1065,8 @@ void mg_cg_b(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* p, V* 
              Scalars* sc, double* part, cudaStream_t st) {
     if constexpr (is_coef_eta<Coef>::value) {
         if (quad_tiles_fit(d))
-            launch_pdl(k_mg_cg_b_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d)), dim3(TX, TY), 0, st,
-                d, coef, quad_kc(d), p, x, r, (V*)m->x[0], (V)MG_OMEGA, sc, part);
+            launch_pdl(k_mg_cg_b_q<EtaOf<Coef>>, quad_grid(d, quad_kc(d, QB_CG_B)), dim3(TX, TY), 0,
+                       st, d, coef, quad_kc(d, QB_CG_B), p, x, r, (V*)m->x[0], (V)MG_OMEGA, sc, part);
         else if (plane_tiles_fit(d))
             launch_pdl(k_mg_cg_b_sm<EtaOf<Coef>>, cols(d, kc), dim3(TX, TY), 0, st, d, coef, kc, p, x, r,
                                                                (V*)m->x[0], (V)MG_OMEGA, sc,

@@ -67,9 +67,9 @@ inline bool quad_tiles_fit(const Dims& d) {
 }
 
 // z-chunk of the quad kernels: even (a coarse plane of the restriction never straddles two
-// chunks), at most 64 planes, chosen for the fewest block-waves (QUAD_BLOCKS per SM) times the
-// planes a block walks.
-int quad_kc(const Dims& d);
+// chunks), at most 64 planes, chosen for the fewest block-waves (blocks_per_sm resident) times
+// the planes a block walks.
+int quad_kc(const Dims& d, int blocks_per_sm);
 
 inline dim3 quad_grid(const Dims& d, int kc) {
     return dim3(d.nx / QX, (d.ny + QY - 1) / QY, (d.nz + kc - 1) / kc);
@@ -173,10 +173,11 @@ __device__ __forceinline__ void quad_apply(const Dims& d, int k, bool xlo, bool 
 }
 
 
-// Blocks per SM the quad kernels are built for (their register budget) and planes of look-ahead
-// of their loads: the stencil field and rho/2 are loaded QUAD_DEPTH planes ahead of the plane
-// being computed, the per-cell inputs and the halo QUAD_DEPTH - 1 planes ahead.
-constexpr int QUAD_BLOCKS = 3;
+// Planes of look-ahead of the quad kernels' loads: the stencil field and rho/2 are loaded
+// QUAD_DEPTH planes ahead of the plane being computed, the per-cell inputs and the halo
+// QUAD_DEPTH - 1 planes ahead.
+// resident blocks per SM of each quad kernel (its register budget)
+constexpr int QB_CG_A = 4, QB_CG_B = 3, QB_RESTRICT = 3, QB_SMOOTH = 3;
 constexpr int QUAD_DEPTH = 2;
 
 // Stencil fields of the quad kernels: u = v, and u = a + beta b (CG phase A: p = z + beta p).
