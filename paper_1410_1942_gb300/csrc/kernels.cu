@@ -485,6 +485,97 @@ __global__ void __launch_bounds__(TX * TY, QB_CG_A) k_cg_a_q(Dims d, CoefEta<E> 
     }
 }
 
+// Phase A on FP32 faces (cut-cell handles), 2 x 2 cells per thread: as k_cg_a_q.
+__global__ void __launch_bounds__(TX * TY, QB_FACES) k_cg_a_fq(Dims d, CoefFaces32 coef, int kc,
+                                                              const float* __restrict__ z,
+                                                              const float* __restrict__ p_in,
+                                                              float* __restrict__ p_out,
+                                                              Scalars* sc, double* partials) {
+    pdl_entry();
+    __shared__ double smem[64];
+    if (sc->done) return;
+    FieldSum F{z, p_in, (float)sc->beta};
+    BodyCgA B{{nullptr}, p_out, d.nx};
+    quad_march_faces(d, coef, kc, F, B);
+    double v[1] = {(double)B.acc}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double pq2 = tot[0];
+            if (!(pq2 > 0.0) || !isfinite(pq2)) {
+                sc->done = BREAKDOWN;
+            } else {
+                sc->pq = pq2;
+                sc->alpha = sc->rz / pq2;
+            }
+        }
+    }
+}
+
+// Jacobi phase B on FP32 faces, 2 x 2 cells per thread: x += alpha p; r -= alpha A p;
+// z = r rcp(D); sums (r, z), (r, r) and the decision, as k_cg_b.
+struct BodyCgBJ {
+    static constexpr int NX = 2;
+    const float* in[NX];
+    float* x;
+    float* r;
+    float* z;
+    float alpha;
+    int nx;
+    float rz = 0.f, rr = 0.f;
+    __device__ __forceinline__ void cell(int c, int, int, int, const Quad& u, const Quad& q,
+                                         const Quad& D, const Quad* X) {
+        Quad xn, rn, zn;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                xn.v[a][b] = X[0].v[a][b] + alpha * u.v[a][b];
+                rn.v[a][b] = X[1].v[a][b] - alpha * q.v[a][b];
+                zn.v[a][b] = rn.v[a][b] * rcp_approx(D.v[a][b]);
+                rz += rn.v[a][b] * zn.v[a][b];
+                rr += rn.v[a][b] * rn.v[a][b];
+            }
+        st2(x, c, xn.v[0][0], xn.v[0][1]);
+        st2(x, c + nx, xn.v[1][0], xn.v[1][1]);
+        st2(r, c, rn.v[0][0], rn.v[0][1]);
+        st2(r, c + nx, rn.v[1][0], rn.v[1][1]);
+        st2(z, c, zn.v[0][0], zn.v[0][1]);
+        st2(z, c + nx, zn.v[1][0], zn.v[1][1]);
+    }
+};
+
+__global__ void __launch_bounds__(TX * TY, QB_FACES) k_cg_b_fq(Dims d, CoefFaces32 coef, int kc,
+                                                              const float* __restrict__ p,
+                                                              float* __restrict__ x,
+                                                              float* __restrict__ r,
+                                                              float* __restrict__ z, Scalars* sc,
+                                                              double* partials) {
+    pdl_entry();
+    __shared__ double smem[64];
+    if (sc->done) return;
+    FieldPlain F{p};
+    BodyCgBJ B{{x, r}, x, r, z, (float)sc->alpha, d.nx};
+    quad_march_faces(d, coef, kc, F, B);
+    double v[2] = {(double)B.rz, (double)B.rr}, tot[2];
+    if (grid_sum<2>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            const double rz_new = tot[0], rr_new = tot[1];
+            sc->iter += 1;
+            sc->rr = rr_new;
+            if (!isfinite(rz_new) || !isfinite(rr_new) || rz_new < 0.0) {
+                sc->done = BREAKDOWN;
+            } else if (rr_new <= sc->stop2) {
+                sc->done = CONVERGED;
+            } else if (sc->iter >= sc->max_iter) {
+                sc->done = CAPPED;
+            } else {
+                sc->beta = rz_new / sc->rz;
+                sc->rz = rz_new;
+            }
+        }
+    }
+}
+
 template <typename V, typename Coef>
 __global__ void __launch_bounds__(TX * TY) k_cg_b(Dims d, Coef coef, int kc,
                                                  const V* __restrict__ p, V* __restrict__ x,
@@ -944,6 +1035,13 @@ void launch_cg_a(const Dims& d, int kc, const Coef& c, const V* z, const V* p_in
         else
             launch_pdl(k_cg_a_eta<EtaOf<Coef>>, grid_of(d, kc), dim3(TX, TY), 0, st, d, c, kc, z, p_in, p_out, sc,
                                                                 part);
+    } else if constexpr (std::is_same<Coef, CoefFaces32>::value) {
+        if (quad_tiles_fit(d))
+            launch_pdl(k_cg_a_fq, quad_grid(d, quad_kc(d, QB_FACES)), dim3(TX, TY), 0, st, d, c,
+                       quad_kc(d, QB_FACES), z, p_in, p_out, sc, part);
+        else
+            launch_pdl(k_cg_a<V, Coef>, grid_of(d, kc), dim3(TX, TY), 0, st, d, c, kc, z, p_in,
+                       p_out, sc, part);
     } else
         launch_pdl(k_cg_a<V, Coef>, grid_of(d, kc), dim3(TX, TY), 0, st, d, c, kc, z, p_in, p_out, sc, part);
     counted(1);
@@ -952,6 +1050,14 @@ void launch_cg_a(const Dims& d, int kc, const Coef& c, const V* z, const V* p_in
 template <typename V, typename Coef>
 void launch_cg_b(const Dims& d, int kc, const Coef& c, const V* p, V* x, V* r, V* z,
                  Scalars* sc, double* part, cudaStream_t st) {
+    if constexpr (std::is_same<Coef, CoefFaces32>::value) {
+        if (quad_tiles_fit(d)) {
+            launch_pdl(k_cg_b_fq, quad_grid(d, quad_kc(d, QB_FACES)), dim3(TX, TY), 0, st, d, c,
+                       quad_kc(d, QB_FACES), p, x, r, z, sc, part);
+            counted(1);
+            return;
+        }
+    }
     k_cg_b<V, Coef><<<grid_of(d, kc), dim3(TX, TY), 0, st>>>(d, c, kc, p, x, r, z, sc, part);
     counted(1);
 }

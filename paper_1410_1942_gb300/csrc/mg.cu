@@ -53,6 +53,18 @@ struct LevelCoef<float> {
     }
 };
 
+// The policy as CoefFaces32 where it is one (the quad face kernels' launches are compiled for
+// every policy but taken only for FP32 faces).
+template <typename Coef>
+inline CoefFaces32 faces32_of(const Coef& c) {
+    if constexpr (std::is_same<Coef, CoefFaces32>::value) {
+        return c;
+    } else {
+        (void)c;
+        return CoefFaces32{};
+    }
+}
+
 __device__ __forceinline__ void coarse_index(const Dims& dc, int I, int& ic, int& jc, int& kc) {
     ic = I % dc.nx;
     jc = (I / dc.nx) % dc.ny;
@@ -807,6 +819,64 @@ __global__ void __launch_bounds__(TX * TY, QB_SMOOTH) k_mg_smooth_q(Dims d, Coef
     reduce_rz(B.rz, sc, partials, smem, mode);
 }
 
+// The same three passes on FP32 faces (quad_march_faces): the fine level of cut-cell handles
+// and the coarse levels of every FP32/BF16 hierarchy whose grid takes quad tiles.
+__global__ void __launch_bounds__(TX * TY, QB_FACES) k_mg_cg_b_fq(Dims d, CoefFaces32 coef, int kc,
+                                                                 const float* __restrict__ p,
+                                                                 float* __restrict__ x,
+                                                                 float* __restrict__ r,
+                                                                 float* __restrict__ x0,
+                                                                 float omega, Scalars* sc,
+                                                                 double* partials) {
+    pdl_entry();
+    __shared__ double smem[64];
+    if (sc->done) return;
+    FieldPlain F{p};
+    BodyCgB B{{x, r}, x, r, x0, (float)sc->alpha, omega, d.nx};
+    quad_march_faces(d, coef, kc, F, B);
+    double v[1] = {(double)B.rr}, tot[1];
+    if (grid_sum<1>(v, partials, &sc->ticket, tot, smem)) {
+        if (threadIdx.x == 0 && threadIdx.y == 0) sc->rr = tot[0];
+    }
+}
+
+__global__ void __launch_bounds__(TX * TY, QB_FACES) k_mg_restrict_fq(Dims d, CoefFaces32 coef,
+                                                                     int kc,
+                                                                     const float* __restrict__ r,
+                                                                     const float* __restrict__ x,
+                                                                     Dims dc, int fz,
+                                                                     const float* __restrict__ cdiag,
+                                                                     float* __restrict__ rc,
+                                                                     float* __restrict__ xc,
+                                                                     float omega,
+                                                                     const Scalars* sc) {
+    pdl_entry();
+    if (sc && sc->done) return;
+    FieldPlain F{x};
+    BodyRestrict B{{r}, rc, xc, cdiag, dc, d.nz, fz, omega};
+    quad_march_faces(d, coef, kc, F, B);
+}
+
+__global__ void __launch_bounds__(TX * TY, QB_FACES) k_mg_smooth_fq(Dims d, CoefFaces32 coef,
+                                                                   int kc,
+                                                                   const float* __restrict__ r,
+                                                                   const float* __restrict__ x,
+                                                                   const float* __restrict__ e,
+                                                                   Dims dc, int sz, float alpha,
+                                                                   float omega,
+                                                                   float* __restrict__ y,
+                                                                   Scalars* sc, double* partials,
+                                                                   int mode) {
+    pdl_entry();
+    __shared__ double smem[64];
+    if (sc && sc->done) return;
+    FieldProlong F{x, e, dc, sz, alpha};
+    BodySmooth B{{r}, y, omega, d.nx};
+    quad_march_faces(d, coef, kc, F, B);
+    if (mode < 0 || !sc) return;
+    reduce_rz(B.rz, sc, partials, smem, mode);
+}
+
 // Start of the preconditioned solve: x0 = w D^-1 r on the fine level; with scalars, sums r.r
 // and sets them like k_cg_init (rz follows from the V-cycle's last kernel).
 template <typename V, typename Coef>
@@ -900,8 +970,19 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
         const Dims& dc = m->d[l + 1];
         const int* f = m->f[l];
         bool done = false;
+        if constexpr (std::is_same<V, float>::value) {
+            // FP32 faces: the fine level of a cut-cell handle, or a coarse level
+            if (quad_tiles_fit(df) && (l > 0 || std::is_same<Coef, CoefFaces32>::value)) {
+                const CoefFaces32 cf = l > 0 ? LevelCoef<float>::of(*m, l) : faces32_of(coef);
+                launch_pdl(k_mg_restrict_fq, quad_grid(df, quad_kc(df, QB_FACES)), dim3(TX, TY), 0,
+                           st, df, cf, quad_kc(df, QB_FACES), l > 0 ? (const V*)m->r[l] : r,
+                           (const V*)m->x[l], dc, f[2], (const V*)m->diag[l + 1],
+                           (V*)m->r[l + 1], (V*)m->x[l + 1], om, sc);
+                done = true;
+            }
+        }
         if constexpr (is_coef_eta<Coef>::value) {
-            if (l == 0 && quad_tiles_fit(df)) {
+            if (!done && l == 0 && quad_tiles_fit(df)) {
                 launch_pdl(k_mg_restrict_q<EtaOf<Coef>>, quad_grid(df, quad_kc(df, QB_RESTRICT)),
                            dim3(TX, TY), 0, st, df, coef, quad_kc(df, QB_RESTRICT), r, (const V*)m->x[0], dc, f[2], (const V*)m->diag[1],
                     (V*)m->r[1], (V*)m->x[1], om, sc);
@@ -935,6 +1016,16 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
     launch_pdl(k_mg_bottom<V>, 1, COARSE_T, 0, st, B, om, al, MG_COARSE_SWEEPS, sc);
     for (int l = b - 1; l >= 1; --l) {
         const int* f = m->f[l];
+        if constexpr (std::is_same<V, float>::value) {
+            if (quad_tiles_fit(m->d[l])) {
+                launch_pdl(k_mg_smooth_fq, quad_grid(m->d[l], quad_kc(m->d[l], QB_FACES)),
+                           dim3(TX, TY), 0, st, m->d[l], LevelCoef<float>::of(*m, l),
+                           quad_kc(m->d[l], QB_FACES), (const V*)m->r[l], (const V*)m->x[l],
+                           (const V*)m->y[l + 1], m->d[l + 1], f[2] - 1, al, om, (V*)m->y[l], sc,
+                           nullptr, -1);
+                continue;
+            }
+        }
         launch_pdl(k_mg_smooth<V, typename LC::type>, cols(m->d[l], 1), dim3(TX, TY), 0, st,
             m->d[l], LC::of(*m, l), 1, (const V*)m->r[l], (const V*)m->x[l],
             (const V*)m->y[l + 1], m->d[l + 1], f[0] - 1, f[1] - 1, f[2] - 1, al, om,
@@ -954,6 +1045,11 @@ void vcycle(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* r, V* z
             launch_pdl(k_mg_smooth_eta<EtaOf<Coef>>, cols(d, kc), dim3(TX, TY), 0, st,
                 d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1,
                 f[1] - 1, f[2] - 1, al, om, z, sc, part, mode);
+    } else if (std::is_same<Coef, CoefFaces32>::value && quad_tiles_fit(d)) {
+        launch_pdl(k_mg_smooth_fq, quad_grid(d, quad_kc(d, QB_FACES)), dim3(TX, TY), 0, st, d,
+                   faces32_of(coef), quad_kc(d, QB_FACES), (const float*)r,
+                   (const float*)m->x[0], (const float*)m->y[1], m->d[1], f[2] - 1, (float)al,
+                   (float)om, (float*)z, sc, part, mode);
     } else
         launch_pdl(k_mg_smooth<V, Coef>, cols(d, kc), dim3(TX, TY), 0, st,
             d, coef, kc, r, (const V*)m->x[0], (const V*)m->y[1], m->d[1], f[0] - 1, f[1] - 1,
@@ -1075,6 +1171,10 @@ void mg_cg_b(MgHier* m, const Dims& d, int kc, const Coef& coef, const V* p, V* 
             launch_pdl(k_mg_cg_b_eta<EtaOf<Coef>>, cols(d, kc), dim3(TX, TY), 0, st, d, coef, kc, p, x, r,
                                                                 (V*)m->x[0], (V)MG_OMEGA, sc,
                                                                 part);
+    } else if (std::is_same<Coef, CoefFaces32>::value && quad_tiles_fit(d)) {
+        launch_pdl(k_mg_cg_b_fq, quad_grid(d, quad_kc(d, QB_FACES)), dim3(TX, TY), 0, st, d,
+                   faces32_of(coef), quad_kc(d, QB_FACES), (const float*)p, (float*)x, (float*)r,
+                   (float*)m->x[0], (float)MG_OMEGA, sc, part);
     } else
         launch_pdl(k_mg_cg_b<V, Coef>, cols(d, kc), dim3(TX, TY), 0, st, d, coef, kc, p, x, r,
                                                                 (V*)m->x[0], (V)MG_OMEGA, sc,

@@ -178,6 +178,8 @@ __device__ __forceinline__ void quad_apply(const Dims& d, int k, bool xlo, bool 
 // QUAD_DEPTH - 1 planes ahead.
 // resident blocks per SM of each quad kernel (its register budget)
 constexpr int QB_CG_A = 4, QB_CG_B = 3, QB_RESTRICT = 3, QB_SMOOTH = 3;
+// ... and of the quad kernels on FP32 faces
+constexpr int QB_FACES = 2;
 constexpr int QUAD_DEPTH = 2;
 
 // Stencil fields of the quad kernels: u = v, and u = a + beta b (CG phase A: p = z + beta p).
@@ -314,6 +316,166 @@ __device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, 
 #pragma unroll
             for (int q = 0; q < NX; ++q) X[q][t] = X[q][t + 1];
         }
+    }
+}
+
+
+// quad_march on an operator stored as FP32 faces (CoefFaces32: cut-cell handles and the V-cycle's
+// coarse levels).  Per cell: xm = bx[c], xp = bx[c + 1] (0 past the last cell), ym = by[c],
+// yp = by[c + nx], zm = bz[c], zp = bz[c + sxy], D = diag[c], as CoefFaces32::weights, and the
+// neighbour sum in nb_sum's order.  Shared planes: u with the one-cell halo, bx with the column
+// right of the tile, by with the row above it; bz and diag stay in registers (bz of plane k + 1 is
+// plane k's zp: loaded two planes ahead, the other coefficients one plane ahead).
+template <typename Field, typename Body>
+__device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces32& cf, int kc,
+                                                 const Field& F, Body& B) {
+    constexpr int NX = Body::NX > 0 ? Body::NX : 1;
+    __shared__ __align__(16) float Us[2][QN];
+    __shared__ __align__(16) float Bxs[2][QN];
+    __shared__ __align__(16) float Bys[2][QN];
+    const int x0 = blockIdx.x * QX + 2 * threadIdx.x, y0 = blockIdx.y * QY + 2 * threadIdx.y;
+    const int k0 = blockIdx.z * kc;
+    const int k1 = min(d.nz, k0 + kc);
+    const bool act = y0 < d.ny;
+    const int si = q_index(2 * threadIdx.x, 2 * threadIdx.y);
+    int hx, hy;
+    const int hk = q_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
+    const int gx = blockIdx.x * QX + hx, gy = blockIdx.y * QY + hy;
+    const bool hv = hk && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
+    const int hi = hk ? q_index(hx, hy) : 0;
+    const bool hbx = hk == 1 && hx == QX;  // the slot's cell is right of the tile: its bx
+    const bool hby = hk == 2 && hy == QY;  // above the tile: its by (a pair)
+    const bool xlo = x0 > 0, xhi = x0 + 2 < d.nx, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
+    auto quad_ld = [&](const float* a, int e, Quad& Q) {
+        const float2 p = ld2(a, e), q = ld2(a, e + d.nx);
+        Q.v[0][0] = p.x; Q.v[0][1] = p.y; Q.v[1][0] = q.x; Q.v[1][1] = q.y;
+    };
+    auto ldu = [&](Quad& U, int e, int k) {
+        const float2 a = F.pair(e, x0, y0, k), b = F.pair(e + d.nx, x0, y0 + 1, k);
+        U.v[0][0] = a.x; U.v[0][1] = a.y; U.v[1][0] = b.x; U.v[1][1] = b.y;
+    };
+    auto ldh = [&](float2& hu, float2& hc, int e, int k) {
+        if (hk == 2) {
+            hu = F.pair(e, gx, gy, k);
+            if (hby) hc = ld2(cf.by, e);
+        } else {
+            hu.x = F.one(e, gx, gy, k);
+            if (hbx) hc.x = cf.bx[e];
+        }
+    };
+    int c = x0 + d.nx * (y0 + d.ny * k0);
+    int h = gx + d.nx * (gy + d.ny * k0);
+    // U[s]: planes k - 1 + s; BZ[s]: planes k + s; BX, BY, DG, X, HU, HC: planes k, k + 1
+    Quad U[4], BZ[3], BX[2], BY[2], DG[2], X[NX][2];
+#pragma unroll
+    for (int s2 = 0; s2 < 4; ++s2) U[s2] = Quad{};
+#pragma unroll
+    for (int s2 = 0; s2 < 3; ++s2) BZ[s2] = Quad{};
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        BX[t] = Quad{}; BY[t] = Quad{}; DG[t] = Quad{};
+#pragma unroll
+        for (int q = 0; q < NX; ++q) X[q][t] = Quad{};
+    }
+    float2 HU[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, HC[2] = {HU[0], HU[1]};
+    if (act) {
+        if (k0 > 0) ldu(U[0], c - d.sxy, k0 - 1);
+        ldu(U[1], c, k0);
+        if (k0 + 1 < d.nz) {
+            ldu(U[2], c + d.sxy, k0 + 1);
+            quad_ld(cf.bz, c + d.sxy, BZ[1]);
+        }
+        quad_ld(cf.bz, c, BZ[0]);
+        quad_ld(cf.bx, c, BX[0]);
+        quad_ld(cf.by, c, BY[0]);
+        quad_ld(cf.diag, c, DG[0]);
+#pragma unroll
+        for (int q = 0; q < Body::NX; ++q) quad_ld(B.in[q], c, X[q][0]);
+    }
+    if (hv) ldh(HU[0], HC[0], h, k0);
+    for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
+        const int b = (k - k0) & 1;
+        float* Up = Us[b];
+        float* Bx = Bxs[b];
+        float* By = Bys[b];
+        st2(Up, si, U[1].v[0][0], U[1].v[0][1]);
+        st2(Up, si + QS, U[1].v[1][0], U[1].v[1][1]);
+        st2(Bx, si, BX[0].v[0][0], BX[0].v[0][1]);
+        st2(Bx, si + QS, BX[0].v[1][0], BX[0].v[1][1]);
+        st2(By, si, BY[0].v[0][0], BY[0].v[0][1]);
+        st2(By, si + QS, BY[0].v[1][0], BY[0].v[1][1]);
+        if (hk == 2) {
+            st2(Up, hi, HU[0].x, HU[0].y);
+            if (hby) st2(By, hi, HC[0].x, HC[0].y);
+        } else if (hk == 1) {
+            Up[hi] = HU[0].x;
+            if (hbx) Bx[hi] = HC[0].x;
+        }
+        if (act) {
+            if (k + 2 <= k1 && k + 2 < d.nz) {
+                ldu(U[3], c + 2 * d.sxy, k + 2);
+                quad_ld(cf.bz, c + 2 * d.sxy, BZ[2]);
+            }
+            if (k + 1 < k1) {
+                quad_ld(cf.bx, c + d.sxy, BX[1]);
+                quad_ld(cf.by, c + d.sxy, BY[1]);
+                quad_ld(cf.diag, c + d.sxy, DG[1]);
+#pragma unroll
+                for (int q = 0; q < Body::NX; ++q) quad_ld(B.in[q], c + d.sxy, X[q][1]);
+            }
+        }
+        if (hv && k + 1 < k1) ldh(HU[1], HC[1], h + d.sxy, k + 1);
+        __syncthreads();
+        if (act) {
+            const bool zlo = k > 0, top = k + 1 == d.nz;
+            const float2 ub = *reinterpret_cast<const float2*>(Up + si - QS);
+            const float2 ua = *reinterpret_cast<const float2*>(Up + si + 2 * QS);
+            const float2 bya = *reinterpret_cast<const float2*>(By + si + 2 * QS);
+            const float ul[2] = {Up[si - 1], Up[si + QS - 1]}, ur[2] = {Up[si + 2], Up[si + QS + 2]};
+            const float bxr[2] = {Bx[si + 2], Bx[si + QS + 2]};
+            const float ubq[2] = {ub.x, ub.y}, uaq[2] = {ua.x, ua.y}, byq[2] = {bya.x, bya.y};
+            Quad q, Dg, Xc[NX];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    const float xm = BX[0].v[r][cc];
+                    const float xp = cc == 0 ? BX[0].v[r][1] : (xhi ? bxr[r] : 0.f);
+                    const float ym = BY[0].v[r][cc];
+                    const float yp = r == 0 ? BY[0].v[1][cc] : (yhi ? byq[cc] : 0.f);
+                    const float zm = BZ[0].v[r][cc];
+                    const float zp = top ? 0.f : BZ[1].v[r][cc];
+                    const bool hxm = cc == 0 ? xlo : true, hxp = cc == 0 ? true : xhi;
+                    const bool hym = r == 0 ? ylo : true, hyp = r == 0 ? true : yhi;
+                    const float uxm = cc == 0 ? ul[r] : U[1].v[r][0];
+                    const float uxp = cc == 0 ? U[1].v[r][1] : ur[r];
+                    const float uym = r == 0 ? ubq[cc] : U[1].v[0][cc];
+                    const float uyp = r == 0 ? U[1].v[1][cc] : uaq[cc];
+                    float s = 0.f;
+                    if (hxm) s += xm * uxm;
+                    if (hxp) s += xp * uxp;
+                    if (hym) s += ym * uym;
+                    if (hyp) s += yp * uyp;
+                    if (zlo) s += zm * U[0].v[r][cc];
+                    if (!top) s += zp * U[2].v[r][cc];
+                    Dg.v[r][cc] = DG[0].v[r][cc];
+                    q.v[r][cc] = Dg.v[r][cc] * U[1].v[r][cc] - s;
+                }
+#pragma unroll
+            for (int t = 0; t < NX; ++t) Xc[t] = X[t][0];
+            B.cell(c, x0, y0, k, U[1], q, Dg, Xc);
+        }
+#pragma unroll
+        for (int s2 = 0; s2 < 3; ++s2) U[s2] = U[s2 + 1];
+        BZ[0] = BZ[1];
+        BZ[1] = BZ[2];
+        BX[0] = BX[1];
+        BY[0] = BY[1];
+        DG[0] = DG[1];
+#pragma unroll
+        for (int t = 0; t < NX; ++t) X[t][0] = X[t][1];
+        HU[0] = HU[1];
+        HC[0] = HC[1];
     }
 }
 

@@ -53,12 +53,17 @@ def test_cut_operator_bit_exact(walls):
         assert np.array_equal(got, ref)
 
 
-@pytest.mark.parametrize("prec,precond", [("fp64", "jacobi"), ("fp64", "rbssor"), ("fp32", "jacobi"),
-                                          ("fp32", "rbssor"), ("bf16", "jacobi")])
-def test_cut_solve_matches_oracle(prec, precond):
+@pytest.mark.parametrize("prec,precond,shape", [
+    ("fp64", "jacobi", (48, 32, 24)), ("fp64", "rbssor", (48, 32, 24)),
+    ("fp32", "jacobi", (48, 32, 24)), ("fp32", "rbssor", (48, 32, 24)),
+    ("bf16", "jacobi", (48, 32, 24)),
+    # whole 64-cell tiles along x: the inner CG phases on the 2 x 2-cell kernels for FP32 faces
+    # (ragged tile rows: 36 = 2 x 16 + 4; odd plane count)
+    ("fp32", "jacobi", (128, 36, 21)), ("bf16", "jacobi", (128, 36, 21))])
+def test_cut_solve_matches_oracle(prec, precond, shape):
     """A strut body through a two-phase surface: both acceptance criteria against the oracle's
     cut operator; the body's cells come out 0."""
-    c = inputs.flat_case(48, 32, 24, seed=5, tol=1e-9)
+    c = inputs.flat_case(*shape, seed=5, tol=1e-9)
     aps = _strut_body(c.grid)
     op = oracle.operator(c.F, apertures=aps)
     b = oracle.rhs(c.s, c.grid.h, aps[3])

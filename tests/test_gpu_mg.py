@@ -123,6 +123,74 @@ def test_mg_solve_with_staged_fine_passes(walls, prec):
     _check(op, b, xref, p, st, 1e-9)
 
 
+# 256 x 96 x 28: the fine passes on 2 x 2-cell quad tiles and the first two coarse levels
+# (128 x 48 x 14, 64 x 24 x 7) on the quad kernels for FP32 faces (odd plane count on level 2);
+# 128 x 36 x 21: a cut-cell body, whose fine level takes the face kernels too (ragged tile rows:
+# 36 = 2 x 16 + 4), as does its first coarse level (64 x 18 x 11).
+FACES = (256, 96, 28)
+CUT_FACES = (128, 36, 21)
+
+
+@pytest.mark.parametrize("walls", [0, 31])
+def test_vcycle_apply_with_quad_face_levels(walls):
+    nx, ny, nz = FACES
+    F = _rand_F((nz, ny, nx), 17)
+    with capi.Poisson(nx, ny, nz, 1.0 / nz, precision="fp32", precond="mg",
+                      **_walls_kw(walls)) as s:
+        s.set_density(F)
+        r = np.random.default_rng(18).standard_normal((nz, ny, nx))
+        got = np.empty_like(r)
+        s.precond_apply(r, got, kind="mg", precision="fp32")
+    op = oracle.operator(F, walls=walls)
+    want = mg.vcycle(mg.hierarchy(op), r)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= VCYCLE_TOL["fp32"], err
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mg_solve_with_quad_face_levels(prec):
+    c = inputs.strut_case(*FACES, seed=19)
+    g = c.grid
+    op, b, xref = _reference(c.F, c.s, g.h)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg", inner_tol=1e-5) as s:
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, 1e-9)
+    assert rc == capi.OK
+    _check(op, b, xref, p, st, 1e-9)
+
+
+def test_vcycle_apply_cut_cells_on_quad_faces():
+    nx, ny, nz = CUT_FACES
+    c = inputs.flat_case(nx, ny, nz, seed=21, tol=1e-9)
+    ap = _strut_apertures(c.grid)
+    with capi.Poisson(nx, ny, nz, c.grid.h, precision="fp32", precond="mg") as s:
+        s.set_apertures(*ap)
+        s.set_density(c.F)
+        r = np.random.default_rng(22).standard_normal((nz, ny, nx))
+        got = np.empty_like(r)
+        s.precond_apply(r, got, kind="mg", precision="fp32")
+    op = oracle.operator(c.F, apertures=ap)
+    want = mg.vcycle(mg.hierarchy(op), r)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= VCYCLE_TOL["fp32"], err
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_mg_solve_cut_cells_on_quad_faces(prec):
+    c = inputs.flat_case(*CUT_FACES, seed=23, tol=1e-9)
+    g = c.grid
+    ap = _strut_apertures(g)
+    op, b, xref = _reference(c.F, c.s, g.h, apertures=ap, vol=ap[3])
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg") as s:
+        s.set_apertures(*ap)
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, 1e-9)
+    assert rc == capi.OK
+    _check(op, b, xref, p, st, 1e-9)
+
+
 def _reference(F, s, h, walls=0, apertures=None, vol=None):
     op = oracle.operator(F, walls=walls, apertures=apertures)
     b = oracle.rhs(s, h, vol)
