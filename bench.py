@@ -66,6 +66,9 @@ BYTES_PER_CELL = {
     # FP64 PCG: vectors 8 B, stored FP64 faces bx, by, bz + diag (+ dinv in phase B)
     "fp64": {"cg_phase_a": 8 * 3 + 8 * 4, "cg_phase_b": 8 * 6 + 8 * 5},
 }
+# cut-cell handles (FP32 or BF16 precision): the inner operator is four stored FP32 arrays (the
+# faces bx, by, bz, each scaled by its open fraction, and the diagonal) in place of rho/2
+BYTES_PER_CELL_CUT = {"cg_phase_a": 4 * 3 + 16, "cg_phase_b": 4 * 6 + 16}
 # one-sweep persistent kernels (Chronopoulos-Gear): reads p, u, s^, w^ (16 B) + eta, writes p,
 # u, s^, w^ (16 B) every iteration; x read and written every other iteration (4 B on average)
 BYTES_PER_CELL_ONE_SWEEP = {"fp32": 16 + 4 + 16 + 4, "bf16": 16 + 2 + 16 + 4}
@@ -89,9 +92,11 @@ BYTES_PER_CELL_FACE_SCHEDULE = {"one-sweep": 56, "red-black": 68}
 # e_c (1 value per 8 cells); write z); every coarse level l adds, per cell of its own, the
 # restriction (read r, x, four stored operator arrays; write 2 values per 8 cells) and the
 # smoothing (read r, x, four operator arrays, 1 value per 8 cells; write y).
-def mg_phase_b_bytes(precision, level_cells, n):
+def mg_phase_b_bytes(precision, level_cells, n, cut=False):
     v = 8 if precision == "fp64" else 4
     eta = 8 * 4 if precision == "fp64" else (4 if precision == "fp32" else 2)
+    if cut and precision != "fp64":
+        eta = 4 * 4  # FP32 faces bx, by, bz and diag stand in for rho/2
     fine = (4 * v + eta + 3 * v) + (2 * v + eta + 2 * v / 8) + (2 * v + eta + v / 8 + v)
     coarse = sum(nl * ((6 * v + 2 * v / 8) + (6 * v + v / 8 + v)) for nl in level_cells[1:-1])
     coarse += level_cells[-1] * 6 * v  # coarsest: r, x, operator (sweeps stay on chip)
@@ -391,10 +396,12 @@ def timed_solves(solver, F, s, p, tol, steps, warmup, stream, sync, clocks=None,
             "launches": launches, "clocks": clk, "prof": prof, "prof_iters": prof_iters}
 
 
-def roofline(prof, desc, precision, precond, g, iters, periodic, kind):
+def roofline(prof, desc, precision, precond, g, iters, periodic, kind, cut=False):
     """The dominant CG kernel's algorithmic bytes per launch over its mean event time (prof: the
     per-kernel times of one profiled solve of `iters` CG iterations)."""
     bpc = BYTES_PER_CELL[precision]
+    if cut and precision != "fp64":
+        bpc = BYTES_PER_CELL_CUT
     cands = [k for k in ("pcg_persistent", "cg_phase_a", "cg_phase_b") if prof[k]["launches"]]
     dom = max(cands, key=lambda k: prof[k]["ms"])
     per_launch_ms = prof[dom]["ms"] / prof[dom]["launches"]
@@ -409,7 +416,8 @@ def roofline(prof, desc, precision, precond, g, iters, periodic, kind):
         family = "one-sweep"
     elif precond == "mg":
         bpc = dict(bpc)
-        bpc["cg_phase_b"] = mg_phase_b_bytes(precision, mg_levels(g.nx, g.ny, g.nz, periodic), g.n)
+        bpc["cg_phase_b"] = mg_phase_b_bytes(precision, mg_levels(g.nx, g.ny, g.nz, periodic), g.n,
+                                             cut)
         bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]
     else:
         bpi = bpc["cg_phase_a"] + bpc["cg_phase_b"]  # algorithmic bytes per cell-iteration
@@ -714,7 +722,7 @@ def main(argv=None):
     value = units / (t_max * 1e-3) / 1e9
     desc = solver.describe()
     roof = roofline(r["prof"], desc, args.precision, args.precond, g, r["prof_iters"],
-                    args.periodic_x, kind)
+                    args.periodic_x, kind, cut=args.cut_body)
     solver.close()
     del p_d
 
