@@ -60,11 +60,9 @@ __device__ __forceinline__ int q_halo_slot(int t, int& hx, int& hy) {
     return 0;
 }
 
-// Whether the quad kernels serve a grid: whole tiles along x, whole row pairs, no periodic wrap
-// (and, for the V-cycle's fine passes, aggregates of 2 x 2 cells in x-y, which these imply).
-inline bool quad_tiles_fit(const Dims& d) {
-    return d.nx % QX == 0 && d.ny % 2 == 0 && !(d.walls & PERIODIC_X);
-}
+// Whether the quad kernels serve a grid: whole tiles along x and whole row pairs (and, for the
+// V-cycle's passes, aggregates of 2 x 2 cells in x-y, which these imply, periodic x included).
+inline bool quad_tiles_fit(const Dims& d) { return d.nx % QX == 0 && d.ny % 2 == 0; }
 
 // z-chunk of the quad kernels: even (a coarse plane of the restriction never straddles two
 // chunks), at most 64 planes, chosen for the fewest block-waves (blocks_per_sm resident) times
@@ -218,10 +216,14 @@ __device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, 
     const int si = q_index(2 * threadIdx.x, 2 * threadIdx.y);
     int hx, hy;
     const int hk = q_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
-    const int gx = blockIdx.x * QX + hx, gy = blockIdx.y * QY + hy;
+    // periodic x: the halo columns hold the other end of their rows
+    const bool per = d.walls & PERIODIC_X;
+    int gx = blockIdx.x * QX + hx;
+    if (per && hk == 1) gx = (gx + d.nx) % d.nx;
+    const int gy = blockIdx.y * QY + hy;
     const bool hv = hk && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
     const int hi = hk ? q_index(hx, hy) : 0;
-    const bool xlo = x0 > 0, xhi = x0 + 2 < d.nx, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
+    const bool xlo = x0 > 0 || per, xhi = x0 + 2 < d.nx || per, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
     auto ldq = [&](Quad& U, Quad& Et, int e, int k) {
         const float2 a = F.pair(e, x0, y0, k), b = F.pair(e + d.nx, x0, y0 + 1, k);
         const float2 ea = eta_load2(eta, e), eb = eta_load2(eta, e + d.nx);
@@ -340,12 +342,16 @@ __device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces3
     const int si = q_index(2 * threadIdx.x, 2 * threadIdx.y);
     int hx, hy;
     const int hk = q_halo_slot(threadIdx.x + TX * threadIdx.y, hx, hy);
-    const int gx = blockIdx.x * QX + hx, gy = blockIdx.y * QY + hy;
+    // periodic x: the halo columns hold the other end of their rows
+    const bool per = d.walls & PERIODIC_X;
+    int gx = blockIdx.x * QX + hx;
+    if (per && hk == 1) gx = (gx + d.nx) % d.nx;
+    const int gy = blockIdx.y * QY + hy;
     const bool hv = hk && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
     const int hi = hk ? q_index(hx, hy) : 0;
     const bool hbx = hk == 1 && hx == QX;  // the slot's cell is right of the tile: its bx
     const bool hby = hk == 2 && hy == QY;  // above the tile: its by (a pair)
-    const bool xlo = x0 > 0, xhi = x0 + 2 < d.nx, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
+    const bool xlo = x0 > 0 || per, xhi = x0 + 2 < d.nx || per, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
     auto quad_ld = [&](const float* a, int e, Quad& Q) {
         const float2 p = ld2(a, e), q = ld2(a, e + d.nx);
         Q.v[0][0] = p.x; Q.v[0][1] = p.y; Q.v[1][0] = q.x; Q.v[1][1] = q.y;

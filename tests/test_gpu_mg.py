@@ -131,7 +131,7 @@ FACES = (256, 96, 28)
 CUT_FACES = (128, 36, 21)
 
 
-@pytest.mark.parametrize("walls", [0, 31])
+@pytest.mark.parametrize("walls", [0, 31, oracle.PERIODIC_X, oracle.PERIODIC_X | 16])
 def test_vcycle_apply_with_quad_face_levels(walls):
     nx, ny, nz = FACES
     F = _rand_F((nz, ny, nx), 17)
@@ -147,12 +147,16 @@ def test_vcycle_apply_with_quad_face_levels(walls):
     assert err <= VCYCLE_TOL["fp32"], err
 
 
+@pytest.mark.parametrize("walls", [0, oracle.PERIODIC_X])
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_mg_solve_with_quad_face_levels(prec):
+def test_mg_solve_with_quad_face_levels(prec, walls):
+    """Periodic x: the halo columns of the first and last tiles wrap (the 64-wide second coarse
+    level is one tile wrapping onto itself)."""
     c = inputs.strut_case(*FACES, seed=19)
     g = c.grid
-    op, b, xref = _reference(c.F, c.s, g.h)
-    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg", inner_tol=1e-5) as s:
+    op, b, xref = _reference(c.F, c.s, g.h, walls=walls)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision=prec, precond="mg", inner_tol=1e-5,
+                      **_walls_kw(walls)) as s:
         s.set_density(c.F)
         p = np.zeros(g.shape)
         rc, st = s.solve(c.s, p, 1e-9)

@@ -494,11 +494,12 @@ def test_periodic_x_solve_matches_oracle(walls, prec, precond):
 @pytest.mark.parametrize("walls", PERIODIC_CASES)
 @pytest.mark.parametrize("prec,tile", [("fp32", 0), ("fp32", 10012204), ("fp32", 12012204),
                                        ("bf16", 10312208), ("fp32", -1), ("fp32", 12204)])
-@pytest.mark.parametrize("shape", [(48, 24, 20), (96, 40, 18), (8, 9, 12)])
+@pytest.mark.parametrize("shape", [(48, 24, 20), (96, 40, 18), (8, 9, 12), (128, 20, 9)])
 def test_periodic_x_marching_matches_oracle(walls, prec, tile, shape):
     """Periodic x on the one-sweep marching kernels (rows padded with wrapped ghost columns; the
     tuner and forced one-sweep tiles) and on the column kernels (tile -1, or a two-sweep tile,
-    which cannot wrap), on shapes with one tile, a ragged last tile, and nx = 8."""
+    which cannot wrap), on shapes with one tile, a ragged last tile, nx = 8, and two 64-cell
+    tiles (the column path's phase A on the 2x2-cell kernel, its halo columns wrapped)."""
     c = inputs.flat_case(*shape, seed=7, tol=1e-9)
     op = oracle.operator(c.F, walls=walls | oracle.PERIODIC_X)
     b = oracle.rhs(c.s, c.grid.h)
