@@ -505,16 +505,18 @@ def fp64_baseline(F, s, g, steps, stream):
             "max_rel_residual": rel}
 
 
-def batched(n=64, seed=0):
+def batched(n=64, seed=0, precond="jacobi"):
     """64 independent solves of uneven size (32^3 .. 128x64x64) submitted together and driven
-    by the batch executor (one persistent PCG launch per refinement step)."""
+    by the batch executor: Jacobi handles in one persistent PCG launch per refinement step,
+    multigrid handles on its worker threads (several solves at once, each on its own stream)."""
     import torch
     from paper_1410_1942_gb300 import capi, inputs
     cases = inputs.batch_cases(n, seed=seed)
     solvers, ps, rhs = [], [], []
     for c in cases:
         g = c.grid
-        sv = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32")
+        kw = {"inner_tol": 1e-5} if precond == "mg" else {}
+        sv = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond=precond, **kw)
         sv.set_density(torch.from_numpy(c.F).cuda())
         solvers.append(sv)
         rhs.append(torch.from_numpy(c.s).cuda())
@@ -661,6 +663,7 @@ def extras_for(kind, args, F_d, s_d, g, stream, flush):
     line["fp64_baseline"] = fb
     line["mixed_vs_fp64_solves_ratio"] = line["solves_per_s"] / fb["solves_per_s"]
     line["batched"] = batched()
+    line["batched_mg"] = batched(precond="mg")
     line["served"] = served(args.serve_requests)
     out["strut"] = line
     return out

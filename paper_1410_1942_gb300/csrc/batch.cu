@@ -11,16 +11,23 @@
 // out and its ticket finishes) and sets the next inner tolerance.  Jobs submitted while a batch
 // runs join it at the next outer step (continuous batching): the job table, the work list and
 // the graphs are rebuilt then.  Finished jobs stay in the table, inactive, until the next
-// rebuild.  Jobs that cannot run in the persistent kernel (FP64 precision, SSOR, nx % 8 != 0)
-// are solved one by one with poisson_solve when polled.
+// rebuild.  Jobs that cannot run in the batch's persistent kernel are solved with poisson_solve:
+// those whose solves launch only ordinary kernels (multigrid, FP64, column kernels) on worker
+// threads, several at once, each on its handle's own stream, so that small solves overlap on
+// the GPU; those that run a persistent cooperative launch of their own (periodic one-sweep,
+// red-black) one by one when polled -- two grid-filling cooperative launches in flight at once
+// could keep each other's CTAs from becoming resident, and their grid barriers would end by
+// deadline.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -45,7 +52,9 @@ struct Job {
     double* p = nullptr;
     double tol = 0.0;
     uint64_t ticket = 0;
-    bool batched = false;   // runs in the persistent batch (else poisson_solve at poll)
+    bool batched = false;   // runs in the persistent batch (else poisson_solve)
+    bool pooled = false;    // poisson_solve on a worker thread (else one by one at poll)
+    cudaEvent_t ready = nullptr;  // pooled: the caller's work on the handle's stream at submit
     bool admitted = false;  // data staged on the device
     bool finished = false;
     int status = POISSON_PENDING;
@@ -437,6 +446,85 @@ bool batchable(const poisson_t* H) {
            march_supported(H->d) && H->march && !H->periodic();
 }
 
+// A handle whose solve launches no persistent cooperative kernel (see the header comment).
+bool poolable(const poisson_t* H) { return !H->march && !H->rb; }
+
+// Worker threads for the pooled jobs, started with the first one.  Each takes a job, makes the
+// handle's device current and runs poisson_solve on a non-blocking stream of its own (ordered
+// after the caller's work on the handle's stream by an event recorded at submit; the handle's
+// stream is restored afterwards), then publishes the result under g_mu.  Own streams let the
+// jobs overlap on the GPU even when their handles run on the legacy default stream, and let the
+// CG loop replay its chunk graph (a legacy stream cannot be captured).
+constexpr int N_WORKERS = 8;
+
+struct Pool {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Job*> queue;
+    std::vector<std::thread> threads;
+    bool stop = false;
+
+    void push(Job* j);
+    ~Pool() {
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        for (auto& t : threads)
+            if (t.joinable()) t.join();
+    }
+};
+Pool g_pool;
+
+void worker() {
+    for (;;) {
+        Job* j = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(g_pool.mu);
+            g_pool.cv.wait(lk, [] { return g_pool.stop || !g_pool.queue.empty(); });
+            if (g_pool.queue.empty()) return;  // stopping
+            j = g_pool.queue.front();
+            g_pool.queue.pop_front();
+        }
+        static thread_local std::unordered_map<int, cudaStream_t> own;  // per device
+        const int dev = j->h->device;
+        cudaSetDevice(dev);
+        cudaStream_t& w = own[dev];
+        if (!w && cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            w = nullptr;
+        }
+        poisson_stats st{};
+        int rc;
+        if (w) {
+            cudaStreamWaitEvent(w, j->ready, 0);
+            const cudaStream_t hs = j->h->st;
+            j->h->st = w;
+            rc = poisson_solve(j->h, j->rhs, j->p, j->tol, &st);
+            j->h->st = hs;
+        } else {
+            cudaEventSynchronize(j->ready);
+            rc = poisson_solve(j->h, j->rhs, j->p, j->tol, &st);
+        }
+        cudaEventDestroy(j->ready);
+        std::lock_guard<std::mutex> lk(g_mu);  // poll reads the job under g_mu
+        j->stats = st;
+        j->status = rc;
+        j->finished = true;
+    }
+}
+
+void Pool::push(Job* j) {
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        queue.push_back(j);
+        if (threads.empty())
+            for (int i = 0; i < N_WORKERS; ++i) threads.emplace_back(worker);
+    }
+    cv.notify_one();
+}
+
 }  // namespace
 
 extern "C" int poisson_batch_submit(poisson_t* const* handles, const double* const* rhs,
@@ -460,6 +548,7 @@ extern "C" int poisson_batch_submit(poisson_t* const* handles, const double* con
         j->tol = tol[i];
         j->ticket = g_next++;
         j->batched = batchable(handles[i]);
+        j->pooled = !j->batched && poolable(handles[i]);
         g_jobs[j->ticket] = j;
         if (j->batched) {
             const int e = handles[i]->opts.precision == POISSON_FP32_BF16COEF ? 1 : 0;
@@ -468,6 +557,17 @@ extern "C" int poisson_batch_submit(poisson_t* const* handles, const double* con
                 g_exec[e]->bf16 = (e == 1);
             }
             g_exec[e]->waiting.push_back(j);
+        } else if (j->pooled) {
+            if (cudaEventCreateWithFlags(&j->ready, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventRecord(j->ready, handles[i]->st) != cudaSuccess) {
+                cudaGetLastError();
+                if (j->ready) cudaEventDestroy(j->ready);
+                j->ready = nullptr;
+                j->pooled = false;  // solved at poll on the handle's stream
+                g_serial.push_back(j);
+            } else {
+                g_pool.push(j);
+            }
         } else {
             g_serial.push_back(j);
         }
@@ -489,6 +589,8 @@ extern "C" int poisson_poll(uint64_t ticket, poisson_stats* stats) {
                 j->finished = true;
                 j->status = rc;
             }
+        } else if (j->pooled) {
+            // a worker publishes the result
         } else {
             // solve the serial jobs in submission order up to this one
             while (!g_serial.empty()) {

@@ -124,13 +124,12 @@ static std::mutex g_tune_mu;
 static std::map<TuneKey, std::pair<int, int>> g_tuned;  // (variant, split strategy)
 
 static int num_sms() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {  // (initialised once, thread-safe)
+        int dev = 0, m = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+        return m > 0 ? m : 1;
+    }();
     return n;
 }
 
@@ -397,7 +396,17 @@ static int setup_rb(poisson_t* H) {
     return POISSON_OK;
 }
 
+static void drop_chunk_graph(poisson_t* H) {
+    if (H->chunk_exec) cudaGraphExecDestroy(H->chunk_exec);
+    if (H->chunk_graph) cudaGraphDestroy(H->chunk_graph);
+    H->chunk_exec = nullptr;
+    H->chunk_graph = nullptr;
+    H->chunk_tag = nullptr;
+    H->chunk_nodes = 0;
+}
+
 static void free_state(poisson_t* H) {
+    drop_chunk_graph(H);
     void* ptrs[] = {H->bx, H->by, H->bz, H->diag, H->dinv, H->top64, H->rinv2, H->ax64, H->ay64,
                     H->az64, H->vol64, H->bx32, H->by32, H->bz32, H->diag32, H->pu[0], H->pu[1],
                     H->ps[0], H->ps[1], H->pw[0], H->pw[1], H->peta32, H->peta16, H->eta32, H->eta16, H->x64,
@@ -694,6 +703,7 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
 extern "C" int poisson_set_apertures(poisson_t* H, const double* ax, const double* ay,
                                      const double* az, const double* vol, int mem) {
     if (!H) return POISSON_EINVAL;
+    drop_chunk_graph(H);  // the inner operator (and its arrays) may change
     const Dims d = H->d;
     const size_t nu = (size_t)(d.nx + 1) * d.ny * d.nz, nv = (size_t)d.nx * (d.ny + 1) * d.nz,
                  nw = (size_t)d.sxy * (d.nz + 1), n = (size_t)d.n;
@@ -762,6 +772,46 @@ static void prof_add(poisson_t* H, int cls, cudaEvent_t a, cudaEvent_t b) {
 // ------------------------------------------------------------------ inner CG loop
 // Queues chunks of CG_CHUNK iterations; reads the scalars of chunk n while chunk n+1 runs.
 // pass_a(p_in_is_a) and pass_b(p_is_a) launch one CG phase each on the handle's stream.
+// A stream that can be captured into a graph (not the legacy or per-thread default stream).
+static bool capturable(cudaStream_t st) {
+    return st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread;
+}
+
+// Captures `passes` (the launches of one CG chunk) on the handle's stream as a graph for code
+// path `tag`.  The passes' launch arguments (buffers, scalars, sizes) are the handle's own and do
+// not change between chunks, and a chunk has an even number of iterations, so every chunk starts
+// on the same p buffer and one graph serves them all.  false (nothing launched, no graph) when
+// the capture fails; the caller then launches the passes directly.
+template <typename F>
+static bool capture_chunk(poisson_t* H, const void* tag, F&& passes) {
+    drop_chunk_graph(H);
+    if (cudaStreamBeginCapture(H->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    passes();
+    cudaGraph_t g = nullptr;
+    if (cudaStreamEndCapture(H->st, &g) != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return false;
+    }
+    size_t n = 0;
+    cudaGraphGetNodes(g, nullptr, &n);
+    g_kernel_launches.fetch_sub((unsigned long long)n, std::memory_order_relaxed);  // not run
+    cudaGraphExec_t x = nullptr;
+    if (cudaGraphInstantiate(&x, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        return false;
+    }
+    H->chunk_graph = g;
+    H->chunk_exec = x;
+    H->chunk_tag = tag;
+    H->chunk_nodes = n;
+    return true;
+}
+
 template <typename V, typename Coef, typename PassA, typename PassB>
 static int cg_loop(poisson_t* H, const Coef& coef, V* r, V* z, double tol2, int rel_to_b,
                    int max_iter, Scalars* result, PassA pass_a, PassB pass_b) {
@@ -777,9 +827,30 @@ static int cg_loop(poisson_t* H, const Coef& coef, V* r, V* z, double tol2, int 
     else
         launch_cg_init<V, Coef>(H->d, H->kc, coef, r, z, H->sc, H->partials, tol2, rel_to_b,
                                 max_iter, st);
+    static_assert(CG_CHUNK % 2 == 0, "a chunk returns to the p buffer it started from");
+    static const char tag = 0;  // this code path (one per instantiation of the loop)
     bool in_is_a = true;
+    auto passes = [&] {
+        bool a = true;
+        for (int q = 0; q < K; ++q) {
+            pass_a(a);
+            pass_b(!a);
+            a = !a;
+        }
+    };
     auto enqueue_chunk = [&](int slot) -> int {
         cudaEvent_t* ev = prof ? &H->prof_ev[slot * PROF_PER_CHUNK] : nullptr;
+        // without per-phase events, on a capturable stream: one graph launch per chunk
+        if (!prof && capturable(st) &&
+            (H->chunk_tag == &tag || capture_chunk(H, &tag, passes))) {
+            CK(cudaGraphLaunch(H->chunk_exec, st));
+            g_kernel_launches.fetch_add((unsigned long long)H->chunk_nodes,
+                                        std::memory_order_relaxed);
+            CK(cudaMemcpyAsync(&H->sc_host[slot], H->sc, sizeof(Scalars), cudaMemcpyDeviceToHost,
+                               st));
+            CK(cudaEventRecord(H->ev[slot], st));
+            return POISSON_OK;
+        }
         for (int q = 0; q < K; ++q) {
             if (prof) CK(cudaEventRecord(ev[3 * q], st));
             pass_a(in_is_a);

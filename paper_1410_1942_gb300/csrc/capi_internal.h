@@ -72,6 +72,13 @@ struct poisson_s {
     bool rb = false;
     pcg::MarchPlan plan{};  // persistent work-list launch over this handle's grid
     pcg::MarchCtl* ctl_host = nullptr;  // pinned staging of plan.ctl
+    // the column-kernel CG chunk (CG_CHUNK iterations of phases A and B) as a CUDA graph,
+    // captured on the first chunk run on a capturable stream; chunk_tag names the code path it
+    // was captured for, chunk_nodes its kernels
+    cudaGraph_t chunk_graph = nullptr;
+    cudaGraphExec_t chunk_exec = nullptr;
+    const void* chunk_tag = nullptr;
+    size_t chunk_nodes = 0;
     // poisson_profile: event pairs around the timed kernels, accumulated times
     bool prof_on = false;
     poisson_kernel_times prof{};

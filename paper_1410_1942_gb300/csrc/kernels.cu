@@ -903,16 +903,15 @@ __global__ void k_pad_rows(Dims d, int pad, const T* __restrict__ src, T* __rest
 
 // ------------------------------------------------------------------ host launchers
 int quad_kc(const Dims& d, int blocks_per_sm) {
-    static int sms = 0;
-    if (sms == 0) {
+    static const int sms = [] {  // (initialised once, thread-safe)
         int dev = 0, n = 0;
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
             cudaGetLastError();
             n = 152;
         }
-        sms = n;
-    }
+        return n;
+    }();
     // blocks take time ~ kc + 2 (their planes plus the two look-ahead planes of the prologue);
     // the grid takes ceil(blocks / resident blocks) of those
     const long long tiles = (long long)(d.nx / QX) * ((d.ny + QY - 1) / QY);

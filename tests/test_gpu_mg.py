@@ -195,6 +195,40 @@ def test_mg_solve_cut_cells_on_quad_faces(prec):
     _check(op, b, xref, p, st, 1e-9)
 
 
+def test_mg_chunk_graphs_on_a_stream():
+    """On a stream of its own (capturable, unlike the legacy default stream) the CG loop runs each
+    chunk of iterations as one replay of a captured graph: two solves in a row (capture, then
+    replay) meet both criteria; new apertures drop the graph, and the cut operator's solve and
+    the plain one after them are right too."""
+    import torch
+    c = inputs.strut_case(128, 36, 21, seed=31)
+    g = c.grid
+    op, b, xref = _reference(c.F, c.s, g.h)
+    ap = _strut_apertures(g)
+    cop, cb, cxref = _reference(c.F, c.s, g.h, apertures=ap, vol=ap[3])
+    st = torch.cuda.Stream()
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond="mg", stream=st) as s:
+        s.set_density(c.F)
+        for _ in range(2):
+            p = np.zeros(g.shape)
+            l0 = capi.kernel_launches()
+            rc, info = s.solve(c.s, p, 1e-9)
+            assert rc == capi.OK and capi.kernel_launches() > l0
+            _check(op, b, xref, p, info, 1e-9)
+        s.set_apertures(*ap)
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, info = s.solve(c.s, p, 1e-9)
+        assert rc == capi.OK
+        _check(cop, cb, cxref, p, info, 1e-9)
+        s.set_apertures(None, None, None, None)
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, info = s.solve(c.s, p, 1e-9)
+        assert rc == capi.OK
+        _check(op, b, xref, p, info, 1e-9)
+
+
 def _reference(F, s, h, walls=0, apertures=None, vol=None):
     op = oracle.operator(F, walls=walls, apertures=apertures)
     b = oracle.rhs(s, h, vol)

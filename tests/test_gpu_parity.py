@@ -289,6 +289,27 @@ def test_batch_of_uneven_solves_matches_oracle(tile):
         s.close()
 
 
+def test_batch_runs_multigrid_and_fp64_solves_on_workers():
+    """Handles whose solves use only ordinary launches (multigrid in every precision, FP64) run
+    on the executor's worker threads, several at once on their own streams, beside a Jacobi
+    handle in the persistent batch: polls never block on them, and every result meets both
+    acceptance criteria against the oracle."""
+    cases = inputs.batch_cases(10, seed=5, hi=(96, 64, 48))
+    kinds = ([("fp32", "mg")] * 5 + [("bf16", "mg")] * 2 + [("fp64", "mg"), ("fp64", "jacobi"),
+                                                            ("fp32", "jacobi")])
+    solvers = [solver(c, pr, precond=pc) for c, (pr, pc) in zip(cases, kinds)]
+    ps = [np.zeros(c.grid.shape) for c in cases]
+    tickets = capi.batch_submit(solvers, [c.s for c in cases], ps, 1e-9)
+    res = _poll_all(tickets)
+    for t, c, p in zip(tickets, cases, ps):
+        rc, st = res[t]
+        assert rc == capi.OK
+        op, b, xref = _oracle_ref(c)
+        _check_solution(c, op, b, xref, p, st, 1e-9)
+    for s in solvers:
+        s.close()
+
+
 def test_batch_of_64_uneven_solves_matches_oracle():
     """The batched workload at its full specification: 64 solves of sizes drawn between 32^3
     and 128 x 64 x 64 (aspect <= 4), each with its own surface, strut and source, submitted
