@@ -676,14 +676,17 @@ struct FieldProlong {
     __device__ __forceinline__ float par(int i, int j, int k) const {
         return e[(i >> 1) + dc.nx * ((j >> 1) + dc.ny * (k >> sz))];
     }
-    __device__ __forceinline__ float2 pair(int c, int i, int j, int k) const {
-        const float2 a = ld2(x, c);
-        const float pe = par(i, j, k);  // one parent for the pair (i even)
-        return make_float2(a.x + alpha * pe, a.y + alpha * pe);
+    // raw parts: a = x, b = e(parent) (one parent for a pair, i even)
+    __device__ __forceinline__ void raw(int c, int i, int j, int k, float2& a, float2& b) const {
+        a = ld2(x, c);
+        const float pe = par(i, j, k);
+        b = make_float2(pe, pe);
     }
-    __device__ __forceinline__ float one(int c, int i, int j, int k) const {
-        return x[c] + alpha * par(i, j, k);
+    __device__ __forceinline__ void raw1(int c, int i, int j, int k, float& a, float& b) const {
+        a = x[c];
+        b = par(i, j, k);
     }
+    __device__ __forceinline__ float comb(float a, float b) const { return a + alpha * b; }
 };
 
 // Phase B of MG-PCG: x += alpha p; r -= alpha A p; x0 = w D^-1 r; (r, r).  Inputs x, r.

@@ -175,27 +175,51 @@ __device__ __forceinline__ void quad_apply(const Dims& d, int k, bool xlo, bool 
 // QUAD_DEPTH planes ahead of the plane being computed, the per-cell inputs and the halo
 // QUAD_DEPTH - 1 planes ahead.
 // resident blocks per SM of each quad kernel (its register budget)
-constexpr int QB_CG_A = 4, QB_CG_B = 3, QB_RESTRICT = 3, QB_SMOOTH = 3;
+constexpr int QB_CG_A = 3, QB_CG_B = 3, QB_RESTRICT = 3, QB_SMOOTH = 3;
 // ... and of the quad kernels on FP32 faces
 constexpr int QB_FACES = 2;
 constexpr int QUAD_DEPTH = 2;
 
 // Stencil fields of the quad kernels: u = v, and u = a + beta b (CG phase A: p = z + beta p).
+// A field is loaded in up to two raw parts, a and b (raw(), raw1()), and formed by comb()
+// only when its plane is next needed, so that the arithmetic does not wait for loads still in
+// flight: the own cells of a plane loaded two planes ahead are formed after the next plane's
+// barrier, the halo when it is stored.  FieldPlain: u = a; FieldSum: u = a + beta b.
 struct FieldPlain {
     const float* v;
-    __device__ __forceinline__ float2 pair(int c, int, int, int) const { return ld2(v, c); }
-    __device__ __forceinline__ float one(int c, int, int, int) const { return v[c]; }
+    __device__ __forceinline__ void raw(int c, int, int, int, float2& a, float2& b) const {
+        a = ld2(v, c);
+        b = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void raw1(int c, int, int, int, float& a, float& b) const {
+        a = v[c];
+        b = 0.f;
+    }
+    __device__ __forceinline__ float comb(float a, float) const { return a; }
 };
 struct FieldSum {
     const float* a;
     const float* b;
     float beta;
-    __device__ __forceinline__ float2 pair(int c, int, int, int) const {
-        const float2 p = ld2(a, c), q = ld2(b, c);
-        return make_float2(p.x + beta * q.x, p.y + beta * q.y);
+    __device__ __forceinline__ void raw(int c, int, int, int, float2& p, float2& q) const {
+        p = ld2(a, c);
+        q = ld2(b, c);
     }
-    __device__ __forceinline__ float one(int c, int, int, int) const { return a[c] + beta * b[c]; }
+    __device__ __forceinline__ void raw1(int c, int, int, int, float& p, float& q) const {
+        p = a[c];
+        q = b[c];
+    }
+    __device__ __forceinline__ float comb(float p, float q) const { return p + beta * q; }
 };
+
+// u of the thread's 2 x 2 cells from its raw parts A, B
+template <typename Field>
+__device__ __forceinline__ void quad_comb(const Field& F, Quad& A, const Quad& B) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) A.v[r][q] = F.comb(A.v[r][q], B.v[r][q]);
+}
 
 // The quad kernels' march over one block's tile and z-chunk.  F gives the stencil field u at a
 // cell pair (float2) or one cell; Body has NX per-cell inputs in[] (loaded as row pairs) and
@@ -224,10 +248,15 @@ __device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, 
     const bool hv = hk && gx >= 0 && gx < d.nx && gy >= 0 && gy < d.ny;
     const int hi = hk ? q_index(hx, hy) : 0;
     const bool xlo = x0 > 0 || per, xhi = x0 + 2 < d.nx || per, ylo = y0 > 0, yhi = y0 + 2 < d.ny;
-    auto ldq = [&](Quad& U, Quad& Et, int e, int k) {
-        const float2 a = F.pair(e, x0, y0, k), b = F.pair(e + d.nx, x0, y0 + 1, k);
+    static_assert(QUAD_DEPTH == 2, "the deferred field forming assumes two planes of look-ahead");
+    // the field's raw parts (U, Ub) and rho/2 of the own cells of plane k
+    auto ldq = [&](Quad& U, Quad& Ub, Quad& Et, int e, int k) {
+        float2 a, b, a1, b1;
+        F.raw(e, x0, y0, k, a, b);
+        F.raw(e + d.nx, x0, y0 + 1, k, a1, b1);
         const float2 ea = eta_load2(eta, e), eb = eta_load2(eta, e + d.nx);
-        U.v[0][0] = a.x; U.v[0][1] = a.y; U.v[1][0] = b.x; U.v[1][1] = b.y;
+        U.v[0][0] = a.x; U.v[0][1] = a.y; U.v[1][0] = a1.x; U.v[1][1] = a1.y;
+        Ub.v[0][0] = b.x; Ub.v[0][1] = b.y; Ub.v[1][0] = b1.x; Ub.v[1][1] = b1.y;
         Et.v[0][0] = ea.x; Et.v[0][1] = ea.y; Et.v[1][0] = eb.x; Et.v[1][1] = eb.y;
     };
     auto ldx = [&](Quad (&X)[NX][D], int t, int e) {
@@ -238,25 +267,30 @@ __device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, 
             X[q][t].v[1][0] = b.x; X[q][t].v[1][1] = b.y;
         }
     };
-    auto ldh = [&](float2& hu, float2& he, int e, int k) {
+    // the halo cell's raw parts (hu, hb) and rho/2
+    auto ldh = [&](float2& hu, float2& hb, float2& he, int e, int k) {
         if (hk == 2) {
-            hu = F.pair(e, gx, gy, k);
+            F.raw(e, gx, gy, k, hu, hb);
             he = eta_load2(eta, e);
         } else {
-            hu.x = F.one(e, gx, gy, k);
+            F.raw1(e, gx, gy, k, hu.x, hb.x);
             he.x = eta_load(eta, e);
         }
     };
     int c = x0 + d.nx * (y0 + d.ny * k0);
     int h = gx + d.nx * (gy + d.ny * k0);
-    // U[s], Et[s]: planes k - 1 + s (s = 0 .. D + 1); X[.][t], HU[t], HE[t]: planes k + t
-    Quad U[D + 2], Et[D + 2], X[NX][D], fzd{};
-    float2 HU[D], HE[D];
+    // U[s], Et[s]: planes k - 1 + s (s = 0 .. D + 1), U[D + 1] raw (its second part in Ub) and
+    // U[D] raw until formed after the barrier (its second part in Ubq); X[.][t], HU/HB/HE[t]:
+    // planes k + t (the halo raw until stored)
+    Quad U[D + 2], Et[D + 2], X[NX][D], fzd{}, Ub{}, Ubq{};
+    float2 HU[D], HB[D], HE[D];
+    bool pend = false;  // U[D] is raw
 #pragma unroll
     for (int s2 = 0; s2 < D + 2; ++s2) { U[s2] = Quad{}; Et[s2] = Quad{}; }
 #pragma unroll
     for (int t = 0; t < D; ++t) {
         HU[t] = make_float2(0.f, 0.f);
+        HB[t] = HU[t];
         HE[t] = HU[t];
 #pragma unroll
         for (int q = 0; q < NX; ++q) X[q][t] = Quad{};
@@ -265,7 +299,11 @@ __device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, 
 #pragma unroll
         for (int s2 = 0; s2 <= D; ++s2) {
             const int m = k0 - 1 + s2;
-            if (m >= 0 && m < d.nz && m <= k1) ldq(U[s2], Et[s2], c + (s2 - 1) * d.sxy, m);
+            if (m >= 0 && m < d.nz && m <= k1) {
+                Quad b2;
+                ldq(U[s2], b2, Et[s2], c + (s2 - 1) * d.sxy, m);
+                quad_comb(F, U[s2], b2);
+            }
         }
 #pragma unroll
         for (int t = 0; t + 1 < D; ++t)
@@ -279,7 +317,7 @@ __device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, 
     if (hv)
 #pragma unroll
         for (int t = 0; t + 1 < D; ++t)
-            if (k0 + t < k1) ldh(HU[t], HE[t], h + t * d.sxy, k0 + t);
+            if (k0 + t < k1) ldh(HU[t], HB[t], HE[t], h + t * d.sxy, k0 + t);
     for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
         const int b = (k - k0) & 1;
         float* Up = Us[b];
@@ -289,19 +327,25 @@ __device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, 
         st2(Es, si, Et[1].v[0][0], Et[1].v[0][1]);
         st2(Es, si + QS, Et[1].v[1][0], Et[1].v[1][1]);
         if (hk == 2) {
-            st2(Up, hi, HU[0].x, HU[0].y);
+            st2(Up, hi, F.comb(HU[0].x, HB[0].x), F.comb(HU[0].y, HB[0].y));
             st2(Es, hi, HE[0].x, HE[0].y);
         } else if (hk == 1) {
-            Up[hi] = HU[0].x;
+            Up[hi] = F.comb(HU[0].x, HB[0].x);
             Es[hi] = HE[0].x;
         }
+        bool loaded = false;
         if (act) {
-            if (k + D <= k1 && k + D < d.nz) ldq(U[D + 1], Et[D + 1], c + D * d.sxy, k + D);
+            if (k + D <= k1 && k + D < d.nz) {
+                ldq(U[D + 1], Ub, Et[D + 1], c + D * d.sxy, k + D);
+                loaded = true;
+            }
             if (k + D - 1 < k1) ldx(X, D - 1, c + (D - 1) * d.sxy);
         }
-        if (hv && k + D - 1 < k1) ldh(HU[D - 1], HE[D - 1], h + (D - 1) * d.sxy, k + D - 1);
+        if (hv && k + D - 1 < k1)
+            ldh(HU[D - 1], HB[D - 1], HE[D - 1], h + (D - 1) * d.sxy, k + D - 1);
         __syncthreads();
         if (act) {
+            if (pend) quad_comb(F, U[D], Ubq);  // plane k + 1, loaded an iteration ago
             Quad q, Dg, Xc[NX];
 #pragma unroll
             for (int t = 0; t < NX; ++t) Xc[t] = X[t][0];
@@ -311,9 +355,12 @@ __device__ __forceinline__ void quad_march(const Dims& d, const E* eta, int kc, 
         }
 #pragma unroll
         for (int s2 = 0; s2 < D + 1; ++s2) { U[s2] = U[s2 + 1]; Et[s2] = Et[s2 + 1]; }
+        Ubq = Ub;
+        pend = loaded;
 #pragma unroll
         for (int t = 0; t + 1 < D; ++t) {
             HU[t] = HU[t + 1];
+            HB[t] = HB[t + 1];
             HE[t] = HE[t + 1];
 #pragma unroll
             for (int q = 0; q < NX; ++q) X[q][t] = X[q][t + 1];
@@ -356,23 +403,29 @@ __device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces3
         const float2 p = ld2(a, e), q = ld2(a, e + d.nx);
         Q.v[0][0] = p.x; Q.v[0][1] = p.y; Q.v[1][0] = q.x; Q.v[1][1] = q.y;
     };
-    auto ldu = [&](Quad& U, int e, int k) {
-        const float2 a = F.pair(e, x0, y0, k), b = F.pair(e + d.nx, x0, y0 + 1, k);
-        U.v[0][0] = a.x; U.v[0][1] = a.y; U.v[1][0] = b.x; U.v[1][1] = b.y;
+    // the field's raw parts of the own cells (U, Ub) and of the halo cell (hu, hb); formed later
+    // (see quad_march)
+    auto ldu = [&](Quad& U, Quad& Ub, int e, int k) {
+        float2 a, b, a1, b1;
+        F.raw(e, x0, y0, k, a, b);
+        F.raw(e + d.nx, x0, y0 + 1, k, a1, b1);
+        U.v[0][0] = a.x; U.v[0][1] = a.y; U.v[1][0] = a1.x; U.v[1][1] = a1.y;
+        Ub.v[0][0] = b.x; Ub.v[0][1] = b.y; Ub.v[1][0] = b1.x; Ub.v[1][1] = b1.y;
     };
-    auto ldh = [&](float2& hu, float2& hc, int e, int k) {
+    auto ldh = [&](float2& hu, float2& hb, float2& hc, int e, int k) {
         if (hk == 2) {
-            hu = F.pair(e, gx, gy, k);
+            F.raw(e, gx, gy, k, hu, hb);
             if (hby) hc = ld2(cf.by, e);
         } else {
-            hu.x = F.one(e, gx, gy, k);
+            F.raw1(e, gx, gy, k, hu.x, hb.x);
             if (hbx) hc.x = cf.bx[e];
         }
     };
     int c = x0 + d.nx * (y0 + d.ny * k0);
     int h = gx + d.nx * (gy + d.ny * k0);
     // U[s]: planes k - 1 + s; BZ[s]: planes k + s; BX, BY, DG, X, HU, HC: planes k, k + 1
-    Quad U[4], BZ[3], BX[2], BY[2], DG[2], X[NX][2];
+    Quad U[4], BZ[3], BX[2], BY[2], DG[2], X[NX][2], Ub{}, Ubq{};
+    bool pend = false;  // U[2] is raw (its second part in Ubq)
 #pragma unroll
     for (int s2 = 0; s2 < 4; ++s2) U[s2] = Quad{};
 #pragma unroll
@@ -384,11 +437,18 @@ __device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces3
         for (int q = 0; q < NX; ++q) X[q][t] = Quad{};
     }
     float2 HU[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, HC[2] = {HU[0], HU[1]};
+    float2 HB[2] = {HU[0], HU[1]};
     if (act) {
-        if (k0 > 0) ldu(U[0], c - d.sxy, k0 - 1);
-        ldu(U[1], c, k0);
+        Quad b2;
+        if (k0 > 0) {
+            ldu(U[0], b2, c - d.sxy, k0 - 1);
+            quad_comb(F, U[0], b2);
+        }
+        ldu(U[1], b2, c, k0);
+        quad_comb(F, U[1], b2);
         if (k0 + 1 < d.nz) {
-            ldu(U[2], c + d.sxy, k0 + 1);
+            ldu(U[2], b2, c + d.sxy, k0 + 1);
+            quad_comb(F, U[2], b2);
             quad_ld(cf.bz, c + d.sxy, BZ[1]);
         }
         quad_ld(cf.bz, c, BZ[0]);
@@ -398,7 +458,7 @@ __device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces3
 #pragma unroll
         for (int q = 0; q < Body::NX; ++q) quad_ld(B.in[q], c, X[q][0]);
     }
-    if (hv) ldh(HU[0], HC[0], h, k0);
+    if (hv) ldh(HU[0], HB[0], HC[0], h, k0);
     for (int k = k0; k < k1; ++k, c += d.sxy, h += d.sxy) {
         const int b = (k - k0) & 1;
         float* Up = Us[b];
@@ -411,16 +471,18 @@ __device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces3
         st2(By, si, BY[0].v[0][0], BY[0].v[0][1]);
         st2(By, si + QS, BY[0].v[1][0], BY[0].v[1][1]);
         if (hk == 2) {
-            st2(Up, hi, HU[0].x, HU[0].y);
+            st2(Up, hi, F.comb(HU[0].x, HB[0].x), F.comb(HU[0].y, HB[0].y));
             if (hby) st2(By, hi, HC[0].x, HC[0].y);
         } else if (hk == 1) {
-            Up[hi] = HU[0].x;
+            Up[hi] = F.comb(HU[0].x, HB[0].x);
             if (hbx) Bx[hi] = HC[0].x;
         }
+        bool loaded = false;
         if (act) {
             if (k + 2 <= k1 && k + 2 < d.nz) {
-                ldu(U[3], c + 2 * d.sxy, k + 2);
+                ldu(U[3], Ub, c + 2 * d.sxy, k + 2);
                 quad_ld(cf.bz, c + 2 * d.sxy, BZ[2]);
+                loaded = true;
             }
             if (k + 1 < k1) {
                 quad_ld(cf.bx, c + d.sxy, BX[1]);
@@ -430,9 +492,10 @@ __device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces3
                 for (int q = 0; q < Body::NX; ++q) quad_ld(B.in[q], c + d.sxy, X[q][1]);
             }
         }
-        if (hv && k + 1 < k1) ldh(HU[1], HC[1], h + d.sxy, k + 1);
+        if (hv && k + 1 < k1) ldh(HU[1], HB[1], HC[1], h + d.sxy, k + 1);
         __syncthreads();
         if (act) {
+            if (pend) quad_comb(F, U[2], Ubq);  // plane k + 1, loaded an iteration ago
             const bool zlo = k > 0, top = k + 1 == d.nz;
             const float2 ub = *reinterpret_cast<const float2*>(Up + si - QS);
             const float2 ua = *reinterpret_cast<const float2*>(Up + si + 2 * QS);
@@ -473,6 +536,8 @@ __device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces3
         }
 #pragma unroll
         for (int s2 = 0; s2 < 3; ++s2) U[s2] = U[s2 + 1];
+        Ubq = Ub;
+        pend = loaded;
         BZ[0] = BZ[1];
         BZ[1] = BZ[2];
         BX[0] = BX[1];
@@ -481,6 +546,7 @@ __device__ __forceinline__ void quad_march_faces(const Dims& d, const CoefFaces3
 #pragma unroll
         for (int t = 0; t < NX; ++t) X[t][0] = X[t][1];
         HU[0] = HU[1];
+        HB[0] = HB[1];
         HC[0] = HC[1];
     }
 }
