@@ -505,7 +505,7 @@ def fp64_baseline(F, s, g, steps, stream):
             "max_rel_residual": rel}
 
 
-def batched(n=64, seed=0, precond="jacobi"):
+def batched(n=64, seed=0, precond="jacobi", tile=0):
     """64 independent solves of uneven size (32^3 .. 128x64x64) submitted together and driven
     by the batch executor: Jacobi handles in one persistent PCG launch per refinement step,
     multigrid handles on its worker threads (several solves at once, each on its own stream)."""
@@ -516,7 +516,8 @@ def batched(n=64, seed=0, precond="jacobi"):
     for c in cases:
         g = c.grid
         kw = {"inner_tol": 1e-5} if precond == "mg" else {}
-        sv = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond=precond, **kw)
+        sv = capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond=precond, tile=tile,
+                          **kw)
         sv.set_density(torch.from_numpy(c.F).cuda())
         solvers.append(sv)
         rhs.append(torch.from_numpy(c.s).cuda())
