@@ -342,6 +342,16 @@ int poisson_residual_noalloc(int nx, int ny, int nz, double h, const double* F, 
  * persistent launch: POISSON_FP64, RBSSOR, MG, cut cells, nx % 8 != 0, tile = -1). */
 int poisson_test_unreachable_barrier(poisson_t* h, int extra);
 
+/* Testing aids for the allocation error paths (the failure is injected on the host; nothing
+ * faults on the GPU).  poisson_test_fail_alloc(n): the n-th device or pinned-host allocation the
+ * library makes from now on, in any thread, fails as if memory were exhausted, and the call that
+ * made it returns POISSON_ENOMEM after releasing what it had allocated (n = 0: no failure;
+ * process-wide; EINVAL for n < 0).  poisson_test_live_allocations: the number of the library's
+ * device and pinned-host allocations made and not yet released (every handle, plan, staging
+ * buffer and batch table counts).  Errors: EINVAL (NULL). */
+int poisson_test_fail_alloc(int n);
+int poisson_test_live_allocations(long long* out);
+
 /* Write a one-line description of the handle's kernel choice (family, tile, z-chunk) into buf
  * (NUL-terminated, at most len bytes). */
 int poisson_describe(poisson_t* h, char* buf, int len);

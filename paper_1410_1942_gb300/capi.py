@@ -33,7 +33,8 @@ EXPORTS = ["poisson_default_opts", "poisson_create", "poisson_destroy", "poisson
            "poisson_profile_read", "poisson_describe", "poisson_residual_noalloc",
            "poisson_divergence", "poisson_project", "poisson_set_apertures", "poisson_strerror",
            "poisson_version", "poisson_test_unreachable_barrier", "poisson_hydrostatic_force",
-           "poisson_required_bytes", "poisson_handle_bytes"]
+           "poisson_required_bytes", "poisson_handle_bytes", "poisson_test_fail_alloc",
+           "poisson_test_live_allocations"]
 K_CG_A, K_CG_B, K_RESIDUAL, K_OTHER, K_PCG = 0, 1, 2, 3, 4
 K_NAMES = ["cg_phase_a", "cg_phase_b", "residual64", "other", "pcg_persistent"]
 
@@ -122,6 +123,10 @@ def load(path=None):
     lib.poisson_hydrostatic_force.restype = i
     lib.poisson_test_unreachable_barrier.argtypes = [vp, i]
     lib.poisson_test_unreachable_barrier.restype = i
+    lib.poisson_test_fail_alloc.argtypes = [i]
+    lib.poisson_test_fail_alloc.restype = i
+    lib.poisson_test_live_allocations.argtypes = [ctypes.POINTER(ctypes.c_longlong)]
+    lib.poisson_test_live_allocations.restype = i
     for name in EXPORTS[1:10] + ["poisson_profile", "poisson_profile_read", "poisson_describe"]:
         getattr(lib, name).restype = i
     _lib = lib
@@ -332,6 +337,19 @@ def residual_noalloc(nx, ny, nz, h, F, rho_air, rho_water, rhs, p, out=None, str
 def kernel_launches():
     """CUDA kernels launched by the library since it was loaded."""
     return int(load().poisson_kernel_launches())
+
+
+def test_fail_alloc(n):
+    """Testing aid: the n-th device or pinned-host allocation of the library from now on fails
+    as if memory were exhausted (0: none)."""
+    _check(load().poisson_test_fail_alloc(int(n)), "poisson_test_fail_alloc")
+
+
+def live_allocations():
+    """The library's device and pinned-host allocations not yet released."""
+    v = ctypes.c_longlong()
+    _check(load().poisson_test_live_allocations(ctypes.byref(v)), "poisson_test_live_allocations")
+    return int(v.value)
 
 
 def batch_submit(solvers, rhs, p, tol):

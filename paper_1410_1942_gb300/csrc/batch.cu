@@ -31,6 +31,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "alloc.h"
 #include "poisson.h"
 #include "capi_internal.h"
 #include "jobs.cuh"
@@ -110,12 +111,12 @@ struct Executor {
     void release() {
         release_graphs();
         march_plan_free(&plan);
-        if (d_jobs) cudaFree(d_jobs);
-        if (d_sc) cudaFree(d_sc);
-        if (d_part) cudaFree(d_part);
-        if (h_jobs) cudaFreeHost(h_jobs);
-        if (h_sc) cudaFreeHost(h_sc);
-        if (h_ctl) cudaFreeHost(h_ctl);
+        if (d_jobs) lib_free(d_jobs);
+        if (d_sc) lib_free(d_sc);
+        if (d_part) lib_free(d_part);
+        if (h_jobs) lib_free_host(h_jobs);
+        if (h_sc) lib_free_host(h_sc);
+        if (h_ctl) lib_free_host(h_ctl);
         d_jobs = nullptr;
         d_sc = nullptr;
         d_part = nullptr;
@@ -237,24 +238,24 @@ struct Executor {
         if (nj > cap || part > part_cap) {
             const int ncap = std::max(nj, 2 * cap);
             const size_t npart = std::max(part, 2 * part_cap);
-            if (d_jobs) cudaFree(d_jobs);
-            if (d_sc) cudaFree(d_sc);
-            if (d_part) cudaFree(d_part);
-            if (h_jobs) cudaFreeHost(h_jobs);
-            if (h_sc) cudaFreeHost(h_sc);
+            if (d_jobs) lib_free(d_jobs);
+            if (d_sc) lib_free(d_sc);
+            if (d_part) lib_free(d_part);
+            if (h_jobs) lib_free_host(h_jobs);
+            if (h_sc) lib_free_host(h_sc);
             d_jobs = nullptr; d_sc = nullptr; d_part = nullptr; h_jobs = nullptr; h_sc = nullptr;
-            if (cudaMalloc((void**)&d_jobs, sizeof(JobDev) * ncap) != cudaSuccess ||
-                cudaMalloc((void**)&d_sc, sizeof(Scalars) * ncap) != cudaSuccess ||
-                cudaMalloc((void**)&d_part, sizeof(double) * npart) != cudaSuccess ||
-                cudaMallocHost((void**)&h_jobs, sizeof(JobDev) * ncap) != cudaSuccess ||
-                cudaMallocHost((void**)&h_sc, sizeof(Scalars) * ncap) != cudaSuccess) {
+            if (lib_malloc((void**)&d_jobs, sizeof(JobDev) * ncap) != cudaSuccess ||
+                lib_malloc((void**)&d_sc, sizeof(Scalars) * ncap) != cudaSuccess ||
+                lib_malloc((void**)&d_part, sizeof(double) * npart) != cudaSuccess ||
+                lib_malloc_host((void**)&h_jobs, sizeof(JobDev) * ncap) != cudaSuccess ||
+                lib_malloc_host((void**)&h_sc, sizeof(Scalars) * ncap) != cudaSuccess) {
                 cudaGetLastError();
                 return POISSON_ENOMEM;
             }
             cap = ncap;
             part_cap = npart;
         }
-        if (!h_ctl && cudaMallocHost((void**)&h_ctl, sizeof(MarchCtl)) != cudaSuccess) {
+        if (!h_ctl && lib_malloc_host((void**)&h_ctl, sizeof(MarchCtl)) != cudaSuccess) {
             cudaGetLastError();
             h_ctl = nullptr;
             return POISSON_ENOMEM;

@@ -14,6 +14,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include "alloc.h"
 #include "poisson.h"
 #include "kernels.h"
 #include "capi_internal.h"
@@ -63,7 +64,7 @@ template <typename T>
 static int dalloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) return POISSON_OK;
-    if (cudaMalloc((void**)p, sizeof(T) * count) != cudaSuccess) {
+    if (lib_malloc((void**)p, sizeof(T) * count) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return POISSON_ENOMEM;
@@ -72,7 +73,7 @@ static int dalloc(T** p, size_t count) {
 }
 
 static void dfree(void* p) {
-    if (p) cudaFree(p);
+    if (p) lib_free(p);
 }
 
 extern "C" void poisson_default_opts(poisson_opts* o) {
@@ -414,8 +415,8 @@ static void free_state(poisson_t* H) {
                     H->p32a, H->p32b, H->s32a, H->s32b, H->w32a, H->w32b, H->sc,
                     H->partials, H->io_a, H->io_b, H->io_c, H->io_c32};
     for (void* p : ptrs) dfree(p);
-    if (H->sc_host) cudaFreeHost(H->sc_host);
-    if (H->ctl_host) cudaFreeHost(H->ctl_host);
+    if (H->sc_host) lib_free_host(H->sc_host);
+    if (H->ctl_host) lib_free_host(H->ctl_host);
     for (auto& e : H->ev) if (e) cudaEventDestroy(e);
     for (auto& e : H->prof_ev) if (e) cudaEventDestroy(e);
     if (H->plan.trace) {
@@ -564,7 +565,7 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
         if (rc != POISSON_OK) return;
         *p = nullptr;
         if (count == 0) return;
-        if (cudaMalloc(p, es * count) != cudaSuccess) {
+        if (lib_malloc(p, es * count) != cudaSuccess) {
             cudaGetLastError();
             *p = nullptr;
             rc = POISSON_ENOMEM;
@@ -574,12 +575,12 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
         mg_plan(H->d, &H->mg);
         A(mg_alloc(&H->mg, o.precision == POISSON_FP64));
     }
-    if (rc == POISSON_OK && cudaMallocHost((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
+    if (rc == POISSON_OK && lib_malloc_host((void**)&H->sc_host, 2 * sizeof(Scalars)) != cudaSuccess) {
         cudaGetLastError();
         H->sc_host = nullptr;
         rc = POISSON_ENOMEM;
     }
-    if (rc == POISSON_OK && cudaMallocHost((void**)&H->ctl_host, sizeof(MarchCtl)) != cudaSuccess) {
+    if (rc == POISSON_OK && lib_malloc_host((void**)&H->ctl_host, sizeof(MarchCtl)) != cudaSuccess) {
         cudaGetLastError();
         H->ctl_host = nullptr;
         rc = POISSON_ENOMEM;

@@ -21,6 +21,7 @@
 // between planes k and k+1 is reused as the lower face of plane k+1.  The arithmetic is the
 // column kernels' (kernels.cu): face 1/(eta_c + eta_n), top term 1/eta_c, D = xm + xp + ym + yp +
 // zm + (zp or top), q = D p_c - sum_n w_n p_n.
+#include "alloc.h"
 #include "internal.cuh"
 #include "kernels.h"
 #include "march.h"
@@ -1095,17 +1096,17 @@ void march_plan_free(MarchPlan* p) {
     void* ptrs[] = {p->solves, p->segs, p->cta_seg, p->maps, p->part_a, p->part_b, p->ctl,
                     p->trace};
     for (void* q : ptrs)
-        if (q) cudaFree(q);
+        if (q) lib_free(q);
     *p = MarchPlan{};
 }
 
 // Device buffer of at least `bytes`, reallocated only when it must grow.
 static bool plan_buffer(void** buf, size_t* cap, size_t bytes) {
     if (*buf && *cap >= bytes) return true;
-    if (*buf) cudaFree(*buf);
+    if (*buf) lib_free(*buf);
     *buf = nullptr;
     *cap = 0;
-    if (cudaMalloc(buf, bytes) != cudaSuccess) {
+    if (lib_malloc(buf, bytes) != cudaSuccess) {
         cudaGetLastError();
         *buf = nullptr;
         return false;
@@ -1334,9 +1335,10 @@ int march_plan_build(MarchPlan* p, const MarchSolve* solves, int nsolves, int va
          plan_buffer((void**)&p->part_b, &p->cap_pb, sizeof(float2) * 3 * segs.size()) &&
          plan_buffer((void**)&p->ctl, &p->cap_ctl, sizeof(MarchCtl));
     if (ok && getenv("POISSON_TRACE") && !p->trace) {
-        if (cudaMalloc((void**)&p->trace, sizeof(unsigned long long) * TRACE_PARTS) != cudaSuccess ||
+        if (lib_malloc((void**)&p->trace, sizeof(unsigned long long) * TRACE_PARTS) != cudaSuccess ||
             cudaMemsetAsync(p->trace, 0, sizeof(unsigned long long) * TRACE_PARTS, st) != cudaSuccess) {
             cudaGetLastError();
+            lib_free(p->trace);
             p->trace = nullptr;
         }
     }

@@ -8,6 +8,7 @@
 // kernel of a PCG iteration returns at once when the solve has finished.
 #include <atomic>
 
+#include "alloc.h"
 #include "poisson.h"
 #include "mg.h"
 #include "kernels.h"
@@ -1093,7 +1094,7 @@ int mg_alloc(MgHier* m, bool dbl) {
     m->dbl = dbl;
     const size_t es = dbl ? sizeof(double) : sizeof(float);
     auto al = [&](void** p, size_t n) {
-        if (cudaMalloc(p, es * n) != cudaSuccess) {
+        if (lib_malloc(p, es * n) != cudaSuccess) {
             cudaGetLastError();
             *p = nullptr;
             return false;
@@ -1117,7 +1118,7 @@ void mg_free(MgHier* m) {
     for (int l = 0; l < MG_MAX_LEVELS; ++l)
         for (void** p : {&m->bx[l], &m->by[l], &m->bz[l], &m->diag[l], &m->r[l], &m->x[l], &m->y[l]})
             if (*p) {
-                cudaFree(*p);
+                lib_free(*p);
                 *p = nullptr;
             }
 }

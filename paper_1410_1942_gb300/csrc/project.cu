@@ -14,6 +14,7 @@
 // results do not depend on FMA contraction.
 #include <cmath>
 
+#include "alloc.h"
 #include "poisson.h"
 #include "capi_internal.h"
 #include "internal.cuh"
@@ -22,6 +23,8 @@
 namespace {
 
 using pcg::Dims;
+using pcg::lib_free;
+using pcg::lib_malloc;
 
 constexpr int PT = 256;
 
@@ -175,7 +178,7 @@ struct Staged {
             return POISSON_OK;
         }
         host = const_cast<double*>(p);
-        if (cudaMalloc((void**)&dev, bytes) != cudaSuccess) {
+        if (lib_malloc((void**)&dev, bytes) != cudaSuccess) {
             cudaGetLastError();
             dev = nullptr;
             return POISSON_ENOMEM;
@@ -196,7 +199,7 @@ struct Staged {
         return POISSON_OK;
     }
     ~Staged() {
-        if (owned && dev) cudaFree(dev);
+        if (owned && dev) lib_free(dev);
     }
 };
 
