@@ -71,6 +71,10 @@ class Request:
     bytes: int = 0        # device bytes counted against the budget while admitted
     cancel_after: int = 0  # > 0: the client cancels the request after this many steps
     cancelled: bool = False
+    # checkpoint/resume: a request parked at a stop keeps its next step's modes and its warm
+    # start on the host (resume_p) and takes its device state back when it is admitted again
+    resume_p: object = None
+    finished: bool = False  # all its steps ran (before a checkpoint)
 
 
 def request_stream(n, rate, seed=0, lo=(32, 32, 32), hi=(256, 128, 128)):
@@ -115,9 +119,16 @@ class Server:
 
     def _admit(self, r, now):
         g, F, s, modes = inputs.mixed_fields_t(r.shape, r.seed, device=self.device)
-        r.grid, r.F, r.s, r.modes = g, F, s, modes
         import torch
-        r.p = torch.zeros(g.shape, dtype=torch.float64, device=self.device)
+        if r.resume_p is not None:
+            # a resumed request: its next step's modes and its warm start from the checkpoint
+            r.grid, r.F = g, F
+            r.s = inputs.divergence_source_t(g, r.modes, device=self.device)
+            r.p = torch.from_numpy(r.resume_p).to(self.device)
+            r.resume_p = None
+        else:
+            r.grid, r.F, r.s, r.modes = g, F, s, modes
+            r.p = torch.zeros(g.shape, dtype=torch.float64, device=self.device)
         r.solver = capi.Poisson(g.nx, g.ny, g.nz, g.h,
                                 **_handle_opts(self.precision, self.precond, self.tile))
         r.solver.set_density(F)
@@ -151,27 +162,78 @@ class Server:
                               "inner_iters": st["inner_iters"] if st else None,
                               "latency_ms": 1e3 * lat, "t_s": t}) + "\n")
 
-    def serve(self, requests):
-        """Runs the stream to completion (wall clock); returns the statistics."""
+    def serve(self, requests, stop_after=None):
+        """Runs the stream to completion (wall clock); returns the statistics.  stop_after: stop
+        once that many solves have finished -- no request is admitted and no step submitted
+        after it, the steps in flight finish, and every unfinished admitted request is parked
+        (its next step's source modes and its pressure copied to the host, its handle and device
+        memory released), so that checkpoint() can save the stream and a new Server resume it."""
         own_log = isinstance(self.log, str)
         out = open(self.log, "w") if own_log else self.log
         try:
-            return self._serve(requests, out)
+            return self._serve(requests, out, stop_after)
         finally:
             if own_log:
                 out.close()
 
-    def _serve(self, requests, out):
-        pending = collections.deque(sorted(requests, key=lambda q: q.arrival))
+    @staticmethod
+    def checkpoint(path, requests):
+        """Saves a stopped stream (after serve(..., stop_after=n)): every request's identity,
+        progress and statistics so far, and for parked ones their source modes and warm start.
+        A .npz file of plain arrays; the metadata is one JSON string."""
+        meta, arrays = [], {}
+        for r in requests:
+            meta.append({"rid": r.rid, "arrival": r.arrival, "shape": list(r.shape), "seed": r.seed,
+                         "step": r.step, "cancel_after": r.cancel_after, "cancelled": r.cancelled,
+                         "finished": r.finished or r.done_at >= 0,
+                         "latencies": r.latencies, "residuals": r.residuals, "iters": r.iters,
+                         "statuses": r.statuses, "parked": r.resume_p is not None})
+            if r.resume_p is not None:
+                arrays["p_%d" % r.rid] = r.resume_p
+                arrays["modes_a_%d" % r.rid] = np.array([m.a for m in r.modes], dtype=np.float64)
+                arrays["modes_k_%d" % r.rid] = np.array([m.k for m in r.modes], dtype=np.int64)
+                arrays["modes_phase_%d" % r.rid] = np.array([m.phase for m in r.modes])
+        np.savez(path, meta=np.array(json.dumps(meta)), **arrays)
+
+    @staticmethod
+    def load_checkpoint(path):
+        """The requests of a checkpoint, ready for serve(): finished ones are kept for the
+        statistics and not run again, parked ones resume at their next step from their saved
+        pressure, the others start from the beginning."""
+        with np.load(path) as z:
+            meta = json.loads(str(z["meta"]))
+            out = []
+            for m in meta:
+                r = Request(m["rid"], m["arrival"], tuple(m["shape"]), m["seed"])
+                r.step, r.cancel_after, r.cancelled = m["step"], m["cancel_after"], m["cancelled"]
+                r.finished = m["finished"]
+                r.latencies, r.residuals = list(m["latencies"]), list(m["residuals"])
+                r.iters, r.statuses = list(m["iters"]), list(m["statuses"])
+                if m["parked"]:
+                    rid = r.rid
+                    r.resume_p = np.array(z["p_%d" % rid])
+                    r.modes = [inputs.Mode(tuple(float(v) for v in a), tuple(int(v) for v in k),
+                                           float(ph))
+                               for a, k, ph in zip(z["modes_a_%d" % rid], z["modes_k_%d" % rid],
+                                                   z["modes_phase_%d" % rid])]
+                out.append(r)
+        return out
+
+    def _serve(self, requests, out, stop_after=None):
+        pending = collections.deque(sorted((q for q in requests if not q.finished),
+                                           key=lambda q: q.arrival))
+        done_solves = cells_done = 0
+        stopping = False
+        parked = 0
         active = []
         used = 0
         t0 = time.perf_counter()
         lat = []
         peak_active = 0
         peak_used = 0
-        while pending or active:
+        while (pending and not stopping) or active:
             now = time.perf_counter() - t0
-            while pending and pending[0].arrival <= now:
+            while pending and pending[0].arrival <= now and not stopping:
                 if pending[0].cancelled:  # cancelled before admission: never allocated
                     pending.popleft()
                     continue
@@ -190,7 +252,7 @@ class Server:
             peak_active = max(peak_active, len(active))
             peak_used = max(peak_used, used)
             if not active:
-                if pending:
+                if pending and not stopping:
                     time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
                 continue
             for r in list(active):
@@ -207,14 +269,26 @@ class Server:
                     self.record[r.rid]["steps"].append((r.s.cpu().numpy(), r.p.cpu().numpy(), rc))
                 self._log(out, r, rc, st, t - r.t_submit, t)
                 r.step += 1
+                done_solves += 1
+                cells_done += r.shape[0] * r.shape[1] * r.shape[2]
+                if stop_after is not None and done_solves >= stop_after:
+                    stopping = True
                 if r.cancel_after and r.step >= r.cancel_after:
                     r.cancelled = True
-                if r.step < self.steps and rc == capi.OK and not r.cancelled:
+                more = r.step < self.steps and rc == capi.OK and not r.cancelled
+                if more and not stopping:
                     self._advance(r)
                     self._submit(r, t)
                 else:
-                    r.done_at = t
-                    if self.keep:
+                    if more:  # parked at the stop: the next step's modes and warm start
+                        self._advance(r)
+                        r.resume_p = r.p.cpu().numpy()
+                        parked += 1
+                    else:
+                        r.finished = True
+                    if r.finished:
+                        r.done_at = t
+                    if self.keep and r.finished:
                         self.results[r.rid] = r.p.cpu().numpy()
                     r.solver.close()
                     r.solver = None
@@ -223,17 +297,21 @@ class Server:
                     active.remove(r)
         wall = time.perf_counter() - t0
         lat = np.array(lat) if lat else np.zeros(1)
-        nsolves = sum(len(r.latencies) for r in requests)
-        cells = sum(r.shape[0] * r.shape[1] * r.shape[2] * len(r.latencies) for r in requests)
+        # this run's solves (a resumed stream's requests carry their earlier steps' records)
+        nsolves = done_solves
+        cells = cells_done
+        complete = lambda r: r.finished or r.cancelled
         return {
             "requests": len(requests), "solves": nsolves, "wall_s": wall,
             "solves_per_s": nsolves / wall, "cell_solves_per_s": cells / wall,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "max_rel_residual": max((max(r.residuals) for r in requests if r.residuals), default=0.0),
             "all_ok": all(all(s == capi.OK for s in r.statuses) and
-                          (len(r.statuses) == self.steps or r.cancelled) for r in requests),
+                          (len(r.statuses) == self.steps or r.cancelled or not complete(r))
+                          for r in requests),
             "cancelled": sum(1 for r in requests if r.cancelled),
             "used_bytes_at_end": used,
+            "stopped": stopping, "parked": parked,
             "peak_active": peak_active, "peak_used_bytes": peak_used, "budget_bytes": self.budget,
             "precision": self.precision,
         }

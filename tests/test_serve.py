@@ -146,3 +146,34 @@ def test_cancelled_requests_leave_and_free_their_memory(tmp_path):
         mine = [x for x in lines if x["rid"] == r.rid]
         assert [x["step"] for x in mine] == list(range(len(r.statuses)))
         assert all(x["shape"] == list(r.shape) and x["latency_ms"] > 0 for x in mine)
+
+
+def test_checkpoint_and_resume_give_the_uninterrupted_results(tmp_path):
+    """A stream stopped after some solves (steps in flight finish, unfinished requests parked
+    with their next step's source and their pressure on the host), saved, loaded into a new
+    server and run to the end runs every step exactly once, and each request's final pressure
+    is the uninterrupted stream's within the acceptance tolerance."""
+    reqs = _stream(5, math.inf, seed=8)
+    whole = serve.Server(budget_bytes=8 << 30, steps=4, keep_results=True)
+    st_whole = whole.serve(copy.deepcopy(reqs))
+    assert st_whole["all_ok"] and st_whole["solves"] == 20
+    first = serve.Server(budget_bytes=8 << 30, steps=4, keep_results=True)
+    part = copy.deepcopy(reqs)
+    st1 = first.serve(part, stop_after=7)
+    assert st1["stopped"] and st1["all_ok"] and st1["used_bytes_at_end"] == 0
+    assert 7 <= st1["solves"] < 20 and st1["parked"] >= 1
+    path = str(tmp_path / "stream.npz")
+    serve.Server.checkpoint(path, part)
+    resumed = serve.Server.load_checkpoint(path)
+    assert [r.step for r in resumed] == [r.step for r in part]
+    second = serve.Server(budget_bytes=8 << 30, steps=4, keep_results=True)
+    st2 = second.serve(resumed)
+    assert st2["all_ok"] and not st2["stopped"]
+    assert st1["solves"] + st2["solves"] == 20
+    assert all(len(r.statuses) == 4 for r in resumed)
+    for r in reqs:
+        got = first.results.get(r.rid)
+        if got is None:
+            got = second.results[r.rid]
+        want = whole.results[r.rid]
+        assert np.linalg.norm(got - want) / np.linalg.norm(want) <= L2_TOL
