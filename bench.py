@@ -447,22 +447,20 @@ def roofline(prof, desc, precision, precond, g, iters, periodic, kind, cut=False
 
 def e2e_line(make_solver, F, s, g, tol, steps, warmup, dev, world, apertures=None):
     """The metric end to end through the C ABI with pinned host arrays (H2D of F, s and the
-    zero start p, D2H of the solution inside every step; the zero starts are prepared before
-    the timed region)."""
+    start p, D2H of the solution inside every step)."""
     import torch
     from paper_1410_1942_gb300 import capi
     F_h = F.cpu().pin_memory()
     s_h = s.cpu().pin_memory()
-    # one zeroed pinned start pressure per timed step, prepared before the timed region (each
-    # step copies its start in and its solution out through it; zeroing 1 GiB on the host is
-    # input preparation, not transfer)
-    starts = [torch.zeros(g.shape, dtype=torch.float64).pin_memory() for _ in range(steps)]
-    p_w = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
+    p_h = torch.zeros(g.shape, dtype=torch.float64).pin_memory()
     sv = make_solver()
     if apertures is not None:
         sv.set_apertures(*apertures)
 
-    def step(p_h):
+    def step():
+        # (one pinned start reused: a fresh pinned buffer per step was slower -- its pages are
+        # cold for the GPU's address translation -- than zeroing this one on the host)
+        p_h.zero_()
         sv.set_density(F_h)
         rc, st = sv.solve(s_h, p_h, tol)
         if rc != capi.OK:
@@ -470,12 +468,11 @@ def e2e_line(make_solver, F, s, g, tol, steps, warmup, dev, world, apertures=Non
         return st
 
     for _ in range(warmup):
-        p_w.zero_()
-        step(p_w)
+        step()
     torch.cuda.synchronize(dev)
     its, t0 = 0, time.perf_counter()
-    for q in range(steps):
-        its += step(starts[q])["inner_iters"]
+    for _ in range(steps):
+        its += step()["inner_iters"]
     torch.cuda.synchronize(dev)
     te = time.perf_counter() - t0
     ue = float(g.n) * its
