@@ -133,7 +133,9 @@ void poisson_default_opts(poisson_opts* opts);
  * bad option), ENOMEM, ECUDA.  *out is set only on success. */
 int poisson_create(int nx, int ny, int nz, double h, const poisson_opts* opts, poisson_t** out);
 
-/* Release the handle and its device memory (after synchronising its stream).  NULL is a no-op. */
+/* Release the handle and its device memory (after synchronising its stream).  NULL is a no-op.
+ * Errors: EINVAL while the handle is in a batch job that poisson_poll has not reported (the
+ * handle is left as it was). */
 int poisson_destroy(poisson_t* h);
 
 /* ------------------------------------------------------------------ device-memory budget

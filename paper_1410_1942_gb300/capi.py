@@ -211,8 +211,10 @@ class Poisson:
         return self._h
 
     def close(self):
+        """Destroys the handle; refused (PoissonError EINVAL, handle kept) while a batch job
+        that poll() has not reported uses it."""
         if self._h:
-            load().poisson_destroy(self._h)
+            _check(load().poisson_destroy(self._h), "poisson_destroy")
             self._h = ctypes.c_void_p()
 
     def __del__(self):

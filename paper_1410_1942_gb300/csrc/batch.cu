@@ -528,6 +528,13 @@ void Pool::push(Job* j) {
 
 }  // namespace
 
+bool batch_handle_busy(const poisson_t* H) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto& kv : g_jobs)
+        if (kv.second->h == H) return true;
+    return false;
+}
+
 extern "C" int poisson_batch_submit(poisson_t* const* handles, const double* const* rhs,
                                     double* const* p, const double* tol, int n,
                                     uint64_t* tickets) {

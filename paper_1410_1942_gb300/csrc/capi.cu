@@ -607,6 +607,8 @@ extern "C" int poisson_create(int nx, int ny, int nz, double h, const poisson_op
 
 extern "C" int poisson_destroy(poisson_t* H) {
     if (!H) return POISSON_OK;
+    // a job of a batch (possibly running on a worker thread) still uses the handle
+    if (batch_handle_busy(H)) return POISSON_EINVAL;
     cudaStreamSynchronize(H->st);
     free_state(H);
     delete H;

@@ -93,3 +93,5 @@ constexpr int PROF_EVENTS = PROF_PCG + 2;
 
 cudaError_t& last_cuda_error();
 bool is_device_ptr(const void* p);
+// Whether a handle is in a batch job not yet reported by poisson_poll (batch.cu).
+bool batch_handle_busy(const poisson_t* H);

@@ -310,6 +310,28 @@ def test_batch_runs_multigrid_and_fp64_solves_on_workers():
         s.close()
 
 
+def test_a_handle_in_an_unreported_job_cannot_be_destroyed():
+    """While a batch job uses a handle -- in the persistent batch, or on a worker thread -- its
+    destruction is refused (EINVAL) and the job completes; after poll reports it, destroy
+    succeeds."""
+    cases = inputs.batch_cases(2, seed=7, hi=(96, 64, 48))
+    svs = [solver(cases[0]), solver(cases[1], precond="mg")]
+    ps = [np.zeros(c.grid.shape) for c in cases]
+    tickets = capi.batch_submit(svs, [c.s for c in cases], ps, 1e-9)
+    for s in svs:
+        with pytest.raises(capi.PoissonError) as e:
+            s.close()
+        assert e.value.status == capi.EINVAL
+    res = _poll_all(tickets)
+    for t, c, p in zip(tickets, cases, ps):
+        rc, st = res[t]
+        assert rc == capi.OK
+        op, b, xref = _oracle_ref(c)
+        _check_solution(c, op, b, xref, p, st, 1e-9)
+    for s in svs:
+        s.close()
+
+
 def test_batch_of_64_uneven_solves_matches_oracle():
     """The batched workload at its full specification: 64 solves of sizes drawn between 32^3
     and 128 x 64 x 64 (aspect <= 4), each with its own surface, strut and source, submitted
