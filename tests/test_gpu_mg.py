@@ -229,6 +229,44 @@ def test_mg_chunk_graphs_on_a_stream():
         _check(op, b, xref, p, info, 1e-9)
 
 
+# Edge layouts of the 2x2-cells-per-thread kernels: one row pair (ny = 2), one plane (nz = 1:
+# aggregates of one plane, fz = 1), two planes, a single 64-wide tile wrapping onto itself
+# (periodic x), and a last tile row holding one row pair (ny = 18).
+QUAD_EDGES = [((64, 2, 1), 0), ((128, 2, 5), 0), ((64, 16, 2), 31), ((64, 18, 3), 0),
+              ((64, 18, 3), oracle.PERIODIC_X), ((192, 4, 7), oracle.PERIODIC_X | 16)]
+
+
+@pytest.mark.parametrize("shape,walls", QUAD_EDGES)
+def test_vcycle_apply_quad_edge_layouts(shape, walls):
+    nx, ny, nz = shape
+    F = _rand_F((nz, ny, nx), 41)
+    with capi.Poisson(nx, ny, nz, 1.0 / max(nz, 8), precision="fp32", precond="mg",
+                      **_walls_kw(walls)) as s:
+        s.set_density(F)
+        r = np.random.default_rng(42).standard_normal((nz, ny, nx))
+        got = np.empty_like(r)
+        s.precond_apply(r, got, kind="mg", precision="fp32")
+    op = oracle.operator(F, walls=walls)
+    want = mg.vcycle(mg.hierarchy(op), r)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    assert err <= VCYCLE_TOL["fp32"], err
+
+
+@pytest.mark.parametrize("shape,walls", QUAD_EDGES)
+@pytest.mark.parametrize("precond,tile", [("mg", 0), ("jacobi", -1)])
+def test_solves_on_quad_edge_layouts(shape, walls, precond, tile):
+    c = inputs.strut_case(*shape, seed=43)
+    g = c.grid
+    op, b, xref = _reference(c.F, c.s, g.h, walls=walls)
+    with capi.Poisson(g.nx, g.ny, g.nz, g.h, precision="fp32", precond=precond, tile=tile,
+                      **_walls_kw(walls)) as s:
+        s.set_density(c.F)
+        p = np.zeros(g.shape)
+        rc, st = s.solve(c.s, p, 1e-9)
+    assert rc == capi.OK
+    _check(op, b, xref, p, st, 1e-9)
+
+
 def _reference(F, s, h, walls=0, apertures=None, vol=None):
     op = oracle.operator(F, walls=walls, apertures=apertures)
     b = oracle.rhs(s, h, vol)
