@@ -479,16 +479,23 @@ struct Pool {
 Pool g_pool;
 
 void worker() {
+    std::unordered_map<int, cudaStream_t> own;  // the worker's stream on each device
     for (;;) {
         Job* j = nullptr;
         {
             std::unique_lock<std::mutex> lk(g_pool.mu);
             g_pool.cv.wait(lk, [] { return g_pool.stop || !g_pool.queue.empty(); });
-            if (g_pool.queue.empty()) return;  // stopping
+            if (g_pool.queue.empty()) {  // stopping
+                for (auto& kv : own)
+                    if (kv.second) {
+                        cudaSetDevice(kv.first);
+                        cudaStreamDestroy(kv.second);
+                    }
+                return;
+            }
             j = g_pool.queue.front();
             g_pool.queue.pop_front();
         }
-        static thread_local std::unordered_map<int, cudaStream_t> own;  // per device
         const int dev = j->h->device;
         cudaSetDevice(dev);
         cudaStream_t& w = own[dev];
