@@ -20,6 +20,10 @@
  *   - A pointer argument may be host memory or device memory of the current CUDA device; the
  *     library tells them apart with cudaPointerGetAttributes (pageable, pinned and device memory
  *     are all accepted).  The caller owns every array it passes; the library never frees them.
+ *     A host array of at least 1 MiB in pinned memory (mapped into the device's address space,
+ *     as cudaHostAlloc and cudaHostRegister memory is) is read or written by a copy kernel
+ *     through that mapping, which stays fast when the host pages' translations have gone cold;
+ *     other host arrays go through cudaMemcpyAsync.
  *   - Device pointers are read or written on the handle's stream (poisson_opts.stream); calls that
  *     return results on the host synchronise that stream before returning.
  *   - Every call returns POISSON_OK (0) or a negative status; poisson_strerror names it.

@@ -37,6 +37,7 @@
 #include "jobs.cuh"
 #include "kernels.h"
 #include "march.h"
+#include "xfer.h"
 
 using namespace pcg;
 
@@ -151,11 +152,11 @@ struct Executor {
         if (drhs) {
             launch_scale((long long)n, j->rhs, -(H->h * H->h), H->b64, st);
         } else {
-            if (cudaMemcpyAsync(H->b64, j->rhs, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+            if (copy_user(H->b64, j->rhs, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
                 return POISSON_ECUDA;
             launch_scale((long long)n, H->b64, -(H->h * H->h), H->b64, st);
         }
-        if (cudaMemcpyAsync(H->x64, j->p, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+        if (copy_user(H->x64, j->p, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                             st) != cudaSuccess)
             return POISSON_ECUDA;
         if (cudaMemsetAsync(H->d32, 0, n * sizeof(float), st) != cudaSuccess ||
@@ -170,7 +171,7 @@ struct Executor {
         poisson_t* H = j->h;
         const size_t bytes = sizeof(double) * (size_t)H->d.n;
         const bool dp = is_device_ptr(j->p);
-        if (cudaMemcpyAsync(j->p, H->x64, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+        if (copy_user(j->p, H->x64, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                             st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             cudaGetLastError();

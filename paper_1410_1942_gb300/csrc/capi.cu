@@ -20,6 +20,7 @@
 #include "capi_internal.h"
 #include "march.h"
 #include "march_rb.h"
+#include "xfer.h"
 
 using namespace pcg;
 
@@ -671,7 +672,7 @@ extern "C" int poisson_set_density(poisson_t* H, const double* F, double rho_air
     const double* Fd = F;
     if (!dev) {
         // stage F through b64 (overwritten by every solve)
-        CK(cudaMemcpyAsync(H->b64, F, bytes, cudaMemcpyHostToDevice, H->st));
+        CK(copy_user(H->b64, F, bytes, cudaMemcpyHostToDevice, H->st));
         Fd = H->b64;
     }
     // the density check's flag lives in the reduction partials (free between solves)
@@ -740,10 +741,10 @@ extern "C" int poisson_set_apertures(poisson_t* H, const double* ax, const doubl
     if (rc != POISSON_OK) return rc;
     const cudaMemcpyKind kind = mem == POISSON_MEM_DEVICE ? cudaMemcpyDeviceToDevice
                                                           : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(H->ax64, ax, sizeof(double) * nu, kind, H->st));
-    CK(cudaMemcpyAsync(H->ay64, ay, sizeof(double) * nv, kind, H->st));
-    CK(cudaMemcpyAsync(H->az64, az, sizeof(double) * nw, kind, H->st));
-    CK(cudaMemcpyAsync(H->vol64, vol, sizeof(double) * n, kind, H->st));
+    CK(copy_user(H->ax64, ax, sizeof(double) * nu, kind, H->st));
+    CK(copy_user(H->ay64, ay, sizeof(double) * nv, kind, H->st));
+    CK(copy_user(H->az64, az, sizeof(double) * nw, kind, H->st));
+    CK(copy_user(H->vol64, vol, sizeof(double) * n, kind, H->st));
     CK(cudaStreamSynchronize(H->st));
     H->d.walls |= CUT_CELLS;
     H->march = false;  // the marching kernels form faces from rho/2 and cannot carry fractions
@@ -1067,11 +1068,11 @@ extern "C" int poisson_solve(poisson_t* H, const double* rhs, double* p, double 
     if (drhs) {
         launch_scale((long long)n, rhs, a, H->b64, H->st, H->vol64);
     } else {
-        CK(cudaMemcpyAsync(H->b64, rhs, bytes, cudaMemcpyHostToDevice, H->st));
+        CK(copy_user(H->b64, rhs, bytes, cudaMemcpyHostToDevice, H->st));
         launch_scale((long long)n, H->b64, a, H->b64, H->st, H->vol64);
     }
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(H->x64, p, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+    CK(copy_user(H->x64, p, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                        H->st));
     int outer = 0, inner = 0;
     double rel = 0.0;
@@ -1090,7 +1091,7 @@ extern "C" int poisson_solve(poisson_t* H, const double* rhs, double* p, double 
             break;
     }
     if (status == POISSON_ECUDA) return status;
-    CK(cudaMemcpyAsync(p, H->x64, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+    CK(copy_user(p, H->x64, bytes, dp ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                        H->st));
     CK(cudaStreamSynchronize(H->st));
     if (stats) {
@@ -1122,13 +1123,13 @@ static int with_io(poisson_t* H, const double* in, double* out, Fn fn) {
     const double* xi = in;
     double* yo = out;
     if (!din) {
-        CK(cudaMemcpyAsync(H->io_a, in, bytes, cudaMemcpyHostToDevice, H->st));
+        CK(copy_user(H->io_a, in, bytes, cudaMemcpyHostToDevice, H->st));
         xi = H->io_a;
     }
     if (!dout) yo = H->io_b;
     fn(xi, yo);
     CK(cudaGetLastError());
-    if (!dout) CK(cudaMemcpyAsync(out, yo, bytes, cudaMemcpyDeviceToHost, H->st));
+    if (!dout) CK(copy_user(out, yo, bytes, cudaMemcpyDeviceToHost, H->st));
     CK(cudaStreamSynchronize(H->st));
     return POISSON_OK;
 }
@@ -1267,7 +1268,7 @@ extern "C" int poisson_get_operator(poisson_t* H, double* bx, double* by, double
     double* dst[4] = {bx, by, bz, diag};
     for (int q = 0; q < 4; ++q) {
         if (!dst[q]) continue;
-        CK(cudaMemcpyAsync(dst[q], src[q], bytes,
+        CK(copy_user(dst[q], src[q], bytes,
                            is_device_ptr(dst[q]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                            H->st));
     }

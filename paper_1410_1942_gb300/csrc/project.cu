@@ -19,9 +19,11 @@
 #include "capi_internal.h"
 #include "internal.cuh"
 #include "kernels.h"
+#include "xfer.h"
 
 namespace {
 
+using pcg::copy_user;
 using pcg::Dims;
 using pcg::lib_free;
 using pcg::lib_malloc;
@@ -184,7 +186,7 @@ struct Staged {
             return POISSON_ENOMEM;
         }
         owned = true;
-        if (load && cudaMemcpyAsync(dev, p, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        if (load && copy_user(dev, p, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
             cudaGetLastError();
             return POISSON_ECUDA;
         }
@@ -192,7 +194,7 @@ struct Staged {
     }
     int flush(cudaStream_t st) {
         if (!owned) return POISSON_OK;
-        if (cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+        if (copy_user(host, dev, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
             cudaGetLastError();
             return POISSON_ECUDA;
         }
